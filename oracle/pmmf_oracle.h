@@ -1,0 +1,102 @@
+/*
+ * pmmf_oracle.h -- plain, slow FP64 CPU reference of parallel MMF (pMMF).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only the test-suite, the smoke check and the
+ * CPU-baseline leg of the benchmark may load this library.  The CUDA library
+ * never links, includes or calls it, and it includes nothing from the CUDA
+ * library.
+ *
+ * It follows the paper step by step: Algorithm 1 (stages: cluster, reblock,
+ * per-cluster rotation search, blocked update, H), Algorithm 2 (per-cluster
+ * randomized greedy Givens / k-point rotation search with the Gram recursion
+ * of Sec. 2 and the elimination rule of Sec. 2.2), the matrix-free product and
+ * inverse of Sec. 2.4 and the preconditioned CG of Sec. 4.  The places where the
+ * paper is silent or garbled are resolved by fixed readings stated next to the
+ * code that uses them.
+ */
+#ifndef PMMF_ORACLE_H
+#define PMMF_ORACLE_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+    OR_OK = 0,
+    OR_ERR_INVALID_ARG = 1,
+    OR_ERR_NOT_SYMMETRIC = 2,
+    OR_ERR_NONFINITE = 3,
+    OR_ERR_OOM = 4,
+    OR_ERR_NOT_SPD = 6,
+    OR_ERR_NOT_CONVERGED = 8
+};
+
+enum { OR_OP_A = 0, OR_OP_A_INV = 1, OR_OP_U = 2, OR_OP_UT = 3, OR_OP_H = 4, OR_OP_H_INV = 5 };
+
+typedef struct {
+    int k;              /* rotation order, 2..8 (Sec. 2, k-point rotations) */
+    double eta;         /* fraction of a cluster eliminated per stage (Alg. 2) */
+    int cluster_size;   /* target cluster size c (Sec. 2.1) */
+    int core_size;      /* stop once |S| <= core_size (delta_L, Sec. 2) */
+    uint64_t seed;      /* seed of the counter-based random pick of Alg. 2 */
+    int max_stages;     /* <= 0: no limit */
+    int lloyd_iters;    /* Lloyd iterations of the clustering step */
+} or_params;
+
+typedef struct or_fact or_fact;
+
+/* Factor a symmetric CSR matrix (rows' columns ascending, no exact zeros).
+ * coords: n x dim points used by the clustering step, or NULL for one
+ * cluster per stage.  record != 0 keeps every stage's compacted A_p.
+ * Never returns NULL for an allocation-free failure: check or_status(). */
+or_fact *or_factor(int64_t n, const int64_t *rowptr, const int32_t *col, const double *val,
+                   const double *coords, int dim, const or_params *p, int record);
+void or_free(or_fact *f);
+int or_status(const or_fact *f);
+
+int or_num_stages(const or_fact *f);
+int64_t or_stage_active(const or_fact *f, int p);          /* |S_{p-1}| */
+int64_t or_stage_clusters(const or_fact *f, int p);        /* m_p */
+void or_stage_cluster_offsets(const or_fact *f, int p, int64_t *out);   /* m_p + 1 */
+void or_stage_members(const or_fact *f, int p, int32_t *out);           /* |S_{p-1}| */
+int64_t or_stage_rotations(const or_fact *f, int p);
+/* per rotation in (cluster, step) order: cluster ordinal, tuple size,
+ * tuple (global ids, k slots, unused = -1), k x k block (row-major, k*k slots),
+ * eliminated global id */
+void or_stage_rotation_data(const or_fact *f, int p, int32_t *cluster, int32_t *kk,
+                            int32_t *idx, double *O, int32_t *elim);
+double or_stage_contrib(const or_fact *f, int p);
+int64_t or_stage_nnz(const or_fact *f, int p);              /* nnz of A_p[S_p,S_p] */
+/* recorded A_p[S_p, S_p] (record != 0): CSR over global ids, rows of S_p */
+int64_t or_stage_matrix(const or_fact *f, int p, int64_t *rowptr_n1, int32_t *col, double *val);
+
+double or_error(const or_fact *f);          /* ||A - U^T H U||_F / ||A||_F */
+double or_norm_a(const or_fact *f);
+int64_t or_core_size(const or_fact *f);
+void or_core(const or_fact *f, int32_t *idx, double *core);
+void or_hdiag(const or_fact *f, double *hdiag);
+/* x, y: n x nrhs row-major */
+int or_apply(const or_fact *f, int op, const double *x, double *y, int64_t nrhs);
+int or_pcg(const or_fact *f, int64_t n, const int64_t *rowptr, const int32_t *col,
+           const double *val, const double *b, double *x, int64_t nrhs, double rtol,
+           int maxit, int32_t *iters, double *relres);
+
+/* building blocks, exposed for the pins */
+uint64_t or_splitmix64_next(uint64_t *state);
+uint64_t or_draw(uint64_t seed, int64_t p, int64_t u, int64_t t);
+int64_t or_pick(uint64_t r, int64_t count);
+void or_jacobi2(double a, double b, double d, double *c, double *s);
+int or_jacobik(int k, const double *g, double *O);
+void or_sym_rotate(double *X, int64_t ld, int64_t nn, int kk, const int64_t *T, const double *O);
+void or_gram(int64_t n, const int64_t *rowptr, const int32_t *col, const double *val,
+             int64_t cu, const int32_t *members, double *G, double *M);
+int or_partition(int64_t n, const double *coords, int dim, int64_t s, const int32_t *active,
+                 int64_t m, int iters, int32_t *label);
+void or_quantize(int64_t n, const double *coords, int dim, uint32_t *q);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,68 @@
+"""The oracle's pins catch plausible mistakes.
+
+Each case plants one mistake in a private copy of the oracle source (a
+flipped sign, a transposed operand, a dropped term, a wrong index or
+comparison), compiles it on the CPU and runs the pin suite against it in a
+child process: the suite must fail.  The real oracle is never modified.
+"""
+
+import os
+import shutil
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+SRC = os.path.join(ROOT, "oracle", "pmmf_oracle.c")
+
+MUTANTS = [
+    ("transposed Givens block",
+     "O[0] = c; O[1] = -s; O[2] = s; O[3] = c;",
+     "O[0] = c; O[1] = s; O[2] = -s; O[3] = c;"),
+    ("Gram uses one row twice",
+     "acc = fma(val[pa], val[pb], acc);",
+     "acc = fma(val[pa], val[pa], acc);"),
+    ("eliminates the larger off-diagonal norm",
+     "if (d <= dbest) { dbest = d; bi = a; }",
+     "if (d >= dbest) { dbest = d; bi = a; }"),
+    ("residual drops the active-row terms",
+     "                            contrib = contrib + w->val[e2] * w->val[e2];\n                        } else {",
+     "                        } else {"),
+    ("inverse sweep uses untransposed blocks",
+     "for (int b = 0; b < kk; ++b) Ot[a * kk + b] = O[b * kk + a];",
+     "for (int b = 0; b < kk; ++b) Ot[a * kk + b] = O[a * kk + b];"),
+    ("Jacobi sign of zeta flipped",
+     "t = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + r);",
+     "t = (zeta >= 0.0 ? -1.0 : 1.0) / (fabs(zeta) + r);"),
+    ("symmetric update forgets the column mirror",
+     "            X[y * ld + T[a]] = out[a];\n",
+     ""),
+    ("clustering distance ignores the last dimension",
+     "for (int d = 0; d < dim; ++d) {\n        int64_t t = (int64_t)q[d] - c[d];",
+     "for (int d = 0; d + 1 < dim; ++d) {\n        int64_t t = (int64_t)q[d] - c[d];"),
+    ("partner score not normalised",
+     "double sc = fabs(G[i * cu + j]) * w;",
+     "double sc = fabs(G[i * cu + j]);"),
+    ("H keeps the wrong diagonal",
+     "if (w->col[e2] == x) f->hdiag[x] = w->val[e2];",
+     "if (w->col[e2] == x) f->hdiag[x] = 0.0;"),
+]
+
+
+@pytest.mark.parametrize("name,old,new", MUTANTS, ids=[m[0] for m in MUTANTS])
+def test_pins_catch_mutant(name, old, new, tmp_path):
+    src = open(SRC).read()
+    assert src.count(old) == 1, f"mutation site for '{name}' not found exactly once"
+    mdir = tmp_path / "oracle"
+    mdir.mkdir()
+    shutil.copy(os.path.join(ROOT, "oracle", "pmmf_oracle.h"), mdir)
+    (mdir / "pmmf_oracle.c").write_text(src.replace(old, new))
+    so = str(mdir / "libmutant.so")
+    subprocess.check_call(["gcc", "-std=c11", "-O2", "-ffp-contract=off", "-fPIC", "-shared",
+                           "-w", "-o", so, str(mdir / "pmmf_oracle.c"), "-lm"])
+    env = dict(os.environ, PMMF_ORACLE_SO=so)
+    r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider",
+                        os.path.join(ROOT, "tests", "test_oracle_pins.py")],
+                       cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
+    assert r.returncode != 0, f"mutant '{name}' survived the pins:\n{r.stdout[-2000:]}"
