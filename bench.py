@@ -1,0 +1,331 @@
+#!/usr/bin/env python
+"""pMMF benchmark: factor throughput (nnz/s) at the stated Frobenius error, plus
+matrix-free apply GB/s against the HBM peak.
+
+Workload (the metric's configuration): the Laplacian + 1e-3 I of the
+symmetrised 10-nearest-neighbour graph of 65,536 uniform points in the unit
+square (seed 1, about 12 nonzeros per row), FP64 CSR; clusters of about 256
+coordinates by k-means on the points, Givens rotations (k = 2), eta = 0.5,
+core size 256.  One step = one full factorization (every stage: clustering,
+Gram, rotation search, blocked update, accounting) with the input resident in
+device memory.  A 256 MiB buffer is written between timed steps to flush L2.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gpu|reference]
+
+--impl reference times the plain CPU oracle (the reference arm) on the host.
+With N > 1 (torchrun) every rank factors its own replica: the factorization
+of one matrix has no data-parallel split without an exchange step, so the job
+scales by replicas (weak scaling).
+"""
+
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "pMMF factor time & nnz/s at stated Frobenius error; apply GB/s vs HBM peak"
+UNIT = "nnz/s"
+WORK = dict(n=65536, knn=10, gen_seed=1, k=2, eta=0.5, cluster_size=256, core_size=256, seed=0)
+FP64_NOMINAL_TFLOPS = 1.25   # GB300 nominal FP64 rate (vector), used for ALU-bound kernels
+NRHS_APPLY = 8
+
+
+def workload_name(n):
+    return (f"knn_laplacian n={n} (10-NN, 2-D uniform points, seed 1) + 1e-3 I, FP64 CSR; "
+            f"k-means clusters ~{WORK['cluster_size']}, k=2 Givens, eta={WORK['eta']}, "
+            f"core {WORK['core_size']}")
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            p = json.load(fh)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, dev):
+        self.dev = dev
+        self.p = None
+
+    def start(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                                       "-lms", "200", "-i", str(self.dev)],
+                                      stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return None
+        self.p.terminate()
+        try:
+            out, _ = self.p.communicate(timeout=10)
+        except Exception:
+            self.p.kill()
+            return None
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def cpu_oracle_run(a, runs=3):
+    from oracle import oracle as O
+    ts = []
+    err = None
+    for _ in range(runs):
+        t0 = time.perf_counter()
+        f = O.factor(a.n, a.rowptr, a.col, a.val, a.coords, k=WORK["k"], eta=WORK["eta"],
+                     cluster_size=WORK["cluster_size"], core_size=WORK["core_size"], seed=WORK["seed"])
+        ts.append(time.perf_counter() - t0)
+        assert f.status == 0
+        err = f.error
+    return statistics.median(ts), err
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    from paper_1507_04396_gb300 import inputs as I
+    a = I.knn_laplacian(args.n, WORK["knn"], seed=WORK["gen_seed"])
+    from oracle import oracle as O
+    O.build()
+    kw = dict(k=WORK["k"], eta=WORK["eta"], cluster_size=WORK["cluster_size"],
+              core_size=WORK["core_size"], seed=WORK["seed"])
+    for _ in range(args.warmup):
+        O.factor(a.n, a.rowptr, a.col, a.val, a.coords, **kw)
+    t0 = time.perf_counter()
+    err = None
+    for _ in range(args.steps):
+        f = O.factor(a.n, a.rowptr, a.col, a.val, a.coords, **kw)
+        err = f.error
+    dt = time.perf_counter() - t0
+    value = a.nnz * args.steps / dt
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": workload_name(a.n), "n": a.n, "nnz": a.nnz,
+                   "frobenius_error": err},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": f"full workload, {args.steps} factorizations, single thread"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+    return 0
+
+
+def run_gpu(args):
+    import numpy as np
+    import torch
+
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    from paper_1507_04396_gb300 import build, inputs as I, pmmf
+    build.build()
+    pmmf.load()
+
+    a = I.knn_laplacian(args.n, WORK["knn"], seed=WORK["gen_seed"])
+    kw = dict(k=WORK["k"], eta=WORK["eta"], cluster_size=WORK["cluster_size"],
+              core_size=WORK["core_size"], seed=WORK["seed"])
+    rp = torch.from_numpy(a.rowptr).to(dev)
+    ci = torch.from_numpy(a.col).to(dev)
+    va = torch.from_numpy(a.val).to(dev)
+    co = torch.from_numpy(a.coords).to(dev)
+    A = I.SymCSR(a.n, rp, ci, va)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def factor():
+        return pmmf.factor(A, coords=co, stream=stream, **kw)
+
+    for _ in range(max(args.warmup, 0)):
+        factor().close()
+
+    # which kernel family dominates (one untimed profiled factorization)
+    pmmf.pmmf_profile_begin(pmmf.FAMILIES)
+    factor().close()
+    breakdown = pmmf.pmmf_profile_end()
+    dominant = max((f for f in breakdown if breakdown[f]["launches"] > 0),
+                   key=lambda f: breakdown[f]["ms"])
+
+    # timed region
+    clocks = Clocks(local)
+    l0 = pmmf.pmmf_launch_count()
+    total_ms = 0.0
+    err = None
+    info = None
+    if ws > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    pmmf.pmmf_profile_begin([dominant])
+    for _ in range(args.steps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        f = factor()
+        e1.record(stream)
+        e1.synchronize()
+        total_ms += e0.elapsed_time(e1)
+        info = f.info()
+        err = info.error
+        f.close()
+    prof = pmmf.pmmf_profile_end()[dominant]
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    launches = pmmf.pmmf_launch_count() - l0
+    if ws > 1:
+        t = torch.tensor([total_ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(t.item())
+    value = a.nnz * args.steps * ws / (total_ms / 1e3)
+
+    hbm, hbm_kind = peaks()
+    if dominant in ("gram", "rows", "apply"):
+        ach = prof["bytes"] / (prof["ms"] / 1e3) / 1e9
+        roof = {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
+                "traffic": None, "kernel_family": dominant, "peak_kind": hbm_kind}
+    else:
+        ach = prof["flops"] / (prof["ms"] / 1e3) / 1e12
+        roof = {"bound": "alu", "achieved": ach, "peak": FP64_NOMINAL_TFLOPS, "unit": "TFLOP/s",
+                "frac": ach / FP64_NOMINAL_TFLOPS, "traffic": None, "kernel_family": dominant,
+                "peak_kind": "nominal FP64"}
+    roof["launches_timed"] = prof["launches"]
+    roof["avg_launch_ms"] = prof["ms"] / max(prof["launches"], 1)
+
+    # matrix-free apply: y = U^T H U x on 8 right-hand sides
+    f = factor()
+    x = torch.randn(a.n, NRHS_APPLY, dtype=torch.float64, device=dev)
+    y = torch.empty_like(x)
+    for _ in range(3):
+        f.apply(pmmf.OP_A, x, y, stream)
+    torch.cuda.synchronize()
+    pmmf.pmmf_profile_begin(["apply"])
+    reps = 20
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(reps):
+        f.apply(pmmf.OP_A, x, y, stream)
+    e1.record(stream)
+    e1.synchronize()
+    ap = pmmf.pmmf_profile_end()["apply"]
+    apply_ms = e0.elapsed_time(e1) / reps
+    apply_gbs = ap["bytes"] / (ap["ms"] / 1e3) / 1e9 if ap["ms"] > 0 else None
+    f.close()
+
+    # end to end through the C-ABI with host buffers (pinned), H diagonal read back
+    hp = [torch.from_numpy(v).pin_memory() for v in (a.rowptr, a.col, a.val, a.coords)]
+    Ah = I.SymCSR(a.n, hp[0], hp[1], hp[2])
+    h2d = sum(t.numel() * t.element_size() for t in hp)
+    hd = np.empty(a.n)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        g = pmmf.factor(Ah, coords=hp[3], stream=stream, **kw)
+        hd[:] = g.h()[0]
+        g.close()
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    e2e = {"value": a.nnz * args.steps * ws / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+           "d2h_bytes_per_step": int(hd.nbytes)}
+
+    cpu = None
+    oracle_err = None
+    if rank == 0 and ws == 1 and not args.no_cpu:
+        from oracle import oracle as O
+        O.build()
+        t, oracle_err = cpu_oracle_run(a, runs=3)
+        cpu = {"value": a.nnz / t, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": "full workload, median of 3 single-thread factorizations"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": workload_name(a.n), "n": a.n, "nnz": a.nnz,
+                       "stages": info.stages, "rotations": info.rotations,
+                       "frobenius_error": err, "oracle_frobenius_error": oracle_err,
+                       "l2": "256 MiB buffer written between timed steps",
+                       "parallelism": "replicas" if ws > 1 else "single GPU"},
+            "roofline": roof,
+            "apply": {"op": "U^T H U x", "nrhs": NRHS_APPLY, "ms": apply_ms,
+                      "rotation_pass_gbs": apply_gbs,
+                      "frac_of_hbm": (apply_gbs / hbm) if apply_gbs else None},
+            "kernel_breakdown_ms": {k: round(v["ms"], 4) for k, v in breakdown.items() if v["launches"]},
+            "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches), "clocks": clk,
+        }
+        print(json.dumps(line))
+    if ws > 1:
+        torch.distributed.barrier()
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["gpu", "reference"], default="gpu")
+    ap.add_argument("--n", type=int, default=WORK["n"])
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gpu(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,213 @@
+/*
+ * pmmf.h -- C-ABI of the GB300 (sm_103a) implementation of parallel
+ * Multiresolution Matrix Factorization (pMMF).
+ *
+ * Paper: R. Kondor, N. Teneva, P. K. Mudrakarta, "Parallel MMF: a Multiresolution
+ * Approach to Matrix Computation", arXiv 1507.04396.  The factorization is
+ *     A ~= Q_1^T ... Q_L^T H Q_L ... Q_1            (Eq. 1, Sec. 2)
+ * with the rotations grouped into stages Qbar_p that share one clustering
+ * (Sec. 2.1, Algorithm 1) and found by the randomized greedy search of
+ * Algorithm 2 (Sec. 2.2).  H is core-diagonal (Sec. 2, condition 3).
+ *
+ * Conventions shared by every entry point
+ *   - Every function returns pmmf_status and never throws or aborts.  On a
+ *     non-OK status pmmf_last_error() returns a message for the calling thread.
+ *   - Floating point data is IEEE binary64 (double); indices are int32
+ *     (global coordinate ids) and int64 (offsets).
+ *   - Pointers are caller-owned unless stated; the library never frees them.
+ *     Device pointers must be CUDA device memory of the current device.
+ *   - "stream" is a cudaStream_t passed as void* (NULL = legacy default stream).
+ *     Work is ordered on that stream.  pmmf_factor synchronizes that stream
+ *     internally (it reads stage sizes back to size buffers); pmmf_apply is
+ *     asynchronous; pmmf_solve_precond synchronizes once per CG iteration.
+ *   - Rotations use the convention x_i' = c x_i - s x_j, x_j' = s x_i + c x_j
+ *     for a Givens rotation on (i, j) (Sec. 2; the printed entries are garbled).
+ */
+#ifndef PMMF_H
+#define PMMF_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    PMMF_OK = 0,
+    PMMF_ERR_INVALID_ARG = 1,     /* a parameter is out of range or a pointer is NULL */
+    PMMF_ERR_NOT_SYMMETRIC = 2,   /* A is not exactly symmetric (structure or bits) */
+    PMMF_ERR_NONFINITE = 3,       /* A holds NaN or Inf */
+    PMMF_ERR_OOM = 4,             /* device or host allocation failed; nothing leaked */
+    PMMF_ERR_CUDA = 5,            /* a CUDA runtime call failed */
+    PMMF_ERR_NOT_SPD = 6,         /* H is not positive definite (inverse requested) */
+    PMMF_ERR_SINGULAR_CORE = 7,
+    PMMF_ERR_NOT_CONVERGED = 8,   /* CG reached maxit, or a k x k Jacobi did not converge */
+    PMMF_ERR_TIMEOUT = 9,
+    PMMF_ERR_UNSUPPORTED = 10     /* valid input outside what this build handles */
+} pmmf_status;
+
+enum { PMMF_HOST = 0, PMMF_DEVICE = 1 };
+enum { PMMF_CSR = 0, PMMF_DENSE = 1 };
+
+/* Operations of pmmf_apply (Sec. 2.4, matrix-free arithmetic):
+ *   PMMF_OP_A      y = U^T H U x          (the factorized matrix A~)
+ *   PMMF_OP_A_INV  y = U^T H^{-1} U x     (its inverse; wavelet diagonal
+ *                                          inverted, core inverted)
+ *   PMMF_OP_U      y = U x,   U = Qbar_P ... Qbar_1
+ *   PMMF_OP_UT     y = U^T x
+ *   PMMF_OP_H      y = H x
+ *   PMMF_OP_H_INV  y = H^{-1} x */
+enum { PMMF_OP_A = 0, PMMF_OP_A_INV = 1, PMMF_OP_U = 2, PMMF_OP_UT = 3, PMMF_OP_H = 4,
+       PMMF_OP_H_INV = 5 };
+
+/* A symmetric n x n matrix (Sec. 2: "a symmetric matrix A").
+ *   PMMF_CSR:   rowptr[n+1] (int64), colidx[nnz] (int32, strictly ascending
+ *               inside each row), val[nnz].  Stored exact zeros are allowed
+ *               and ignored.
+ *   PMMF_DENSE: val is n x ld row-major (ld >= n); rowptr/colidx unused.
+ * location says whether the arrays live in host or device memory.
+ * Symmetry must be exact: entry (i, j) and (j, i) carry identical bits. */
+typedef struct {
+    int64_t n;
+    int format;
+    int location;
+    const int64_t *rowptr;
+    const int32_t *colidx;
+    const double *val;
+    int64_t ld;
+} pmmf_matrix;
+
+/* Parameters, named as in the paper.
+ *   k             rotation order (Sec. 2, k-point rotations), 2 <= k <= 8.
+ *                 This build runs k = 2 (Givens, Algorithm 2) on the GPU;
+ *                 k > 2 returns PMMF_ERR_UNSUPPORTED.
+ *   eta           compression ratio of Algorithm 2: floor(eta c_u) rotations
+ *                 (one elimination each) per cluster per stage, 0 < eta < 1.
+ *   cluster_size  typical cluster size c (Sec. 2.1), >= k; a stage with s
+ *                 active coordinates uses m = max(1, round(s / c)) clusters.
+ *   core_size     delta_L: stages run while more than core_size coordinates
+ *                 are active (1 <= core_size <= n).
+ *   seed          seed of the counter-based random pick of Algorithm 2.
+ *   max_stages    stop after this many stages (<= 0: no limit).
+ *   lloyd_iters   Lloyd iterations of the clustering step (0 -> 10).
+ *   coords        optional n x coord_dim row-major points (coord_dim 1..3)
+ *                 that the clustering step (Algorithm 1, "cluster") groups by
+ *                 k-means; NULL -> one cluster per stage.
+ *   coords_location  PMMF_HOST or PMMF_DEVICE for coords.
+ *   record_stages nonzero keeps a device copy of every stage's compacted
+ *                 A_p (for inspection with pmmf_stage_matrix). */
+typedef struct {
+    int k;
+    double eta;
+    int cluster_size;
+    int core_size;
+    uint64_t seed;
+    int max_stages;
+    int lloyd_iters;
+    const double *coords;
+    int coord_dim;
+    int coords_location;
+    int record_stages;
+} pmmf_params;
+
+typedef struct pmmf_handle pmmf_handle;
+
+typedef struct {
+    int64_t n;
+    int32_t stages;
+    int64_t core_size;        /* |S_L| */
+    int64_t rotations;        /* total number of rotations (= n - |S_L|) */
+    int64_t nnz_input;
+    double norm_a;            /* ||A||_F */
+    double error;             /* ||A - U^T H U||_F / ||A||_F (residual of Sec. 2) */
+} pmmf_info;
+
+typedef struct {
+    int64_t active;           /* |S_{p-1}| at the start of the stage */
+    int64_t clusters;         /* m_p */
+    int64_t rotations;
+    int64_t nnz_after;        /* nnz of A_p[S_p, S_p] */
+    int32_t max_levels;       /* depth of the stage's rotation dependency graph */
+    double contrib;           /* this stage's share of ||A - A~||_F^2 */
+} pmmf_stage_info;
+
+/* Factor A (Algorithm 1).  On PMMF_OK *out receives a handle owning every
+ * device buffer of the factorization (rotations, H); free it with pmmf_free.
+ * On error *out is NULL and no memory is leaked.  The input is only read. */
+pmmf_status pmmf_factor(const pmmf_matrix *A, const pmmf_params *p, pmmf_handle **out,
+                        void *stream);
+
+/* Matrix-free product with the factorization (Sec. 2.4), O(k p n) work.
+ * x and y are DEVICE pointers to n x nrhs row-major blocks with leading
+ * dimension ld >= nrhs; x == y (in place) is allowed.  Asynchronous.
+ * PMMF_OP_A_INV / PMMF_OP_H_INV return PMMF_ERR_NOT_SPD when a wavelet
+ * diagonal entry of H is <= 0 or the core is not positive definite; that check
+ * runs on the first inverse request and synchronizes the stream once. */
+pmmf_status pmmf_apply(const pmmf_handle *f, int op, const double *x, double *y, int64_t nrhs,
+                       int64_t ld, void *stream);
+
+/* Preconditioned conjugate gradients for A x = b with M^{-1} = A~^{-1}
+ * (Sec. 4, xi = 1), every column of b independently, x_0 = 0.  A is the
+ * system matrix (any location; CSR or dense); b and x are DEVICE n x nrhs
+ * row-major (ld = nrhs).  Stops a column when ||r||/||b|| <= rtol (recurrence
+ * residual).  iters[nrhs] and relres[nrhs] (HOST) receive the iteration count
+ * and the true residual ||b - A x|| / ||b|| at exit.  Returns
+ * PMMF_ERR_NOT_CONVERGED if a column did not reach rtol in maxit steps. */
+pmmf_status pmmf_solve_precond(const pmmf_handle *f, const pmmf_matrix *A, const double *b,
+                               double *x, int64_t nrhs, double rtol, int maxit, int32_t *iters,
+                               double *relres, void *stream);
+
+/* Release a handle (NULL-safe). */
+void pmmf_free(pmmf_handle *f);
+
+/* Message of the last failed call on this thread ("" if none). */
+const char *pmmf_last_error(void);
+
+/* ---- inspection (copies into HOST buffers; synchronous) ------------------ */
+
+pmmf_status pmmf_get_info(const pmmf_handle *f, pmmf_info *info);
+pmmf_status pmmf_get_stage_info(const pmmf_handle *f, int p, pmmf_stage_info *info);
+
+/* Clustering of stage p (0-based): offsets[clusters + 1] into members[active];
+ * each cluster's members are global ids in ascending order. */
+pmmf_status pmmf_get_stage_clusters(const pmmf_handle *f, int p, int64_t *offsets,
+                                    int32_t *members);
+
+/* Rotations of stage p in (cluster, step) order, the order Algorithm 2 finds
+ * them: cluster[r], kk[r] (tuple size), idx[r*k + a] global ids of the tuple
+ * (i first, then partners by decreasing score; unused slots -1),
+ * O[r*k*k + a*kk + b] the kk x kk block acting as x_T' = O x_T (for kk = 2:
+ * [[c, -s], [s, c]]), elim[r] the eliminated global id. */
+pmmf_status pmmf_get_stage_rotations(const pmmf_handle *f, int p, int32_t *cluster, int32_t *kk,
+                                     int32_t *idx, double *O, int32_t *elim);
+
+/* H (core-diagonal, Sec. 2): hdiag[n] is the diagonal of H (core diagonal
+ * included), core_idx[core_size] the ascending global ids of S_L and
+ * core[core_size^2] the dense core block H[S_L, S_L] row-major. */
+pmmf_status pmmf_get_h(const pmmf_handle *f, double *hdiag, int32_t *core_idx, double *core);
+
+/* Recorded A_p[S_p, S_p] of stage p (params.record_stages != 0) as CSR over
+ * global ids: rowptr_n1[n + 1] (rows outside S_p empty), col[nnz], val[nnz].
+ * Pass NULL arrays to query nnz only. */
+pmmf_status pmmf_get_stage_matrix(const pmmf_handle *f, int p, int64_t *rowptr_n1, int32_t *col,
+                                  double *val, int64_t *nnz);
+
+/* Number of GPU kernel launches this process has issued through the library. */
+uint64_t pmmf_launch_count(void);
+
+/* ---- profiling (measurement aid; no counterpart in the paper) -------------
+ * Kernel families: 0 partition (k-means assignment), 1 Gram, 2 rotation
+ * search, 3 blocked-update row kernels, 4 matrix-free apply, 5 other.
+ * pmmf_profile_begin(mask) brackets every later launch of the families in mask
+ * with two CUDA events recorded on that launch's stream, together with the
+ * launch's algorithmic bytes and flops (compulsory traffic and arithmetic, as
+ * documented at each launch site).  pmmf_profile_end synchronizes the device
+ * and fills ms[6], launches[6], bytes[6], flops[6] (host arrays, one slot per
+ * family), then disables profiling. */
+pmmf_status pmmf_profile_begin(unsigned family_mask);
+pmmf_status pmmf_profile_end(double *ms, int64_t *launches, double *bytes, double *flops);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

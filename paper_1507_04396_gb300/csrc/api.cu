@@ -1,0 +1,644 @@
+// api.cu -- the C-ABI of include/pmmf.h: input staging and validation, the
+// stage loop of Algorithm 1, the factorization handle, matrix-free apply and
+// preconditioned CG.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <memory>
+#include <new>
+#include <vector>
+
+#include "apply.cuh"
+#include "common.cuh"
+#include "stage.cuh"
+
+namespace pmmf {
+const char *last_error_cstr();
+
+struct StageData {
+    int64_t s = 0, m = 0, nrot = 0, nnz_after = 0, cmax = 0;
+    int32_t max_levels = 0;
+    double contrib = 0.0;
+    StageClusters cls;
+    StageRotations rot;
+    Csr recorded;               // A_p[S_p, S_p] if params.record_stages
+    DBuf<int32_t> recorded_act; // its row -> global id map
+    bool has_record = false;
+};
+
+}  // namespace pmmf
+
+struct pmmf_handle {
+    int64_t n = 0, nnz_in = 0;
+    int k = 2;
+    double norm_a = 0.0, err = 0.0;
+    std::vector<pmmf::StageData> st;
+    pmmf::DBuf<double> hdiag;
+    int64_t ncore = 0;
+    pmmf::DBuf<int32_t> core_idx, core_pos;
+    pmmf::DBuf<double> core, core_inv;
+    int inv_state = 0;  // 0 not formed, 1 formed, 2 not SPD
+    pmmf::ApplyStages views;
+};
+
+namespace pmmf {
+namespace {
+
+pmmf_status fail(pmmf_status s, const char *msg) {
+    set_error(msg);
+    return s;
+}
+
+void set_pool_threshold() {
+    static bool done = false;
+    if (done) return;
+    done = true;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return;
+    cudaMemPool_t pool;
+    if (cudaDeviceGetDefaultMemPool(&pool, dev) != cudaSuccess) return;
+    uint64_t thr = UINT64_MAX;
+    cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+}
+
+template <class T>
+pmmf_status to_device(const T *src, int64_t count, int location, DBuf<T> &dst, const T *&out,
+                      cudaStream_t st) {
+    if (location == PMMF_DEVICE) {
+        out = src;
+        return PMMF_OK;
+    }
+    PMMF_TRY(dst.alloc(count, st));
+    if (count > 0)
+        PMMF_CUDA_TRY(cudaMemcpyAsync(dst.p, src, sizeof(T) * (size_t)count, cudaMemcpyHostToDevice, st));
+    out = dst.p;
+    return PMMF_OK;
+}
+
+// Device CSR of A with exact zeros dropped, validated (structure, finite,
+// exactly symmetric).
+pmmf_status stage_input(const pmmf_matrix *A, Csr &out, unsigned *status_d, cudaStream_t st) {
+    const int64_t n = A->n;
+    if (A->format == PMMF_DENSE) {
+        if (!A->val || A->ld < n) return fail(PMMF_ERR_INVALID_ARG, "dense A: val is NULL or ld < n");
+        DBuf<double> tmp;
+        const double *dv = nullptr;
+        int64_t cnt = (n - 1) * A->ld + n;
+        PMMF_TRY(to_device(A->val, cnt, A->location, tmp, dv, st));
+        PMMF_TRY(dense_to_csr(dv, n, A->ld, out.rowptr, out.col, out.val, st));
+    } else if (A->format == PMMF_CSR) {
+        if (!A->rowptr || !A->colidx || !A->val) return fail(PMMF_ERR_INVALID_ARG, "CSR A: NULL array");
+        int64_t nnz = 0;
+        if (A->location == PMMF_HOST) {
+            nnz = A->rowptr[n];
+            if (A->rowptr[0] != 0 || nnz < 0) return fail(PMMF_ERR_INVALID_ARG, "CSR A: bad rowptr");
+            for (int64_t i = 0; i < n; ++i)
+                if (A->rowptr[i + 1] < A->rowptr[i]) return fail(PMMF_ERR_INVALID_ARG, "CSR A: rowptr decreases");
+        } else {
+            int64_t ends[2];
+            PMMF_CUDA_TRY(cudaMemcpyAsync(&ends[0], A->rowptr, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+            PMMF_CUDA_TRY(cudaMemcpyAsync(&ends[1], A->rowptr + n, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+            PMMF_CUDA_TRY(cudaStreamSynchronize(st));
+            if (ends[0] != 0 || ends[1] < 0) return fail(PMMF_ERR_INVALID_ARG, "CSR A: bad rowptr");
+            nnz = ends[1];
+        }
+        DBuf<int64_t> trp;
+        DBuf<int32_t> tci;
+        DBuf<double> tv;
+        const int64_t *rp = nullptr;
+        const int32_t *ci = nullptr;
+        const double *v = nullptr;
+        PMMF_TRY(to_device(A->rowptr, n + 1, A->location, trp, rp, st));
+        PMMF_TRY(to_device(A->colidx, nnz, A->location, tci, ci, st));
+        PMMF_TRY(to_device(A->val, nnz, A->location, tv, v, st));
+        // structure first (monotone rows, columns in range and ascending), on
+        // the stored entries; then drop exact zeros and check symmetry
+        PMMF_CUDA_TRY(cudaMemsetAsync(status_d, 0, sizeof(unsigned), st));
+        PMMF_TRY(validate_csr(n, rp, ci, v, status_d, st));
+        unsigned hs = 0;
+        PMMF_CUDA_TRY(cudaMemcpyAsync(&hs, status_d, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
+        PMMF_CUDA_TRY(cudaStreamSynchronize(st));
+        if (hs & ST_BAD_CSR) return fail(PMMF_ERR_INVALID_ARG, "CSR A: columns out of range or not ascending");
+        PMMF_TRY(csr_drop_zeros(n, rp, ci, v, out.rowptr, out.col, out.val, st));
+    } else {
+        return fail(PMMF_ERR_INVALID_ARG, "unknown matrix format");
+    }
+    out.rows = n;
+    PMMF_CUDA_TRY(cudaMemcpyAsync(&out.nnz, out.rowptr.p + n, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+    PMMF_CUDA_TRY(cudaMemsetAsync(status_d, 0, sizeof(unsigned), st));
+    PMMF_TRY(validate_csr(n, out.rowptr.p, out.col.p, out.val.p, status_d, st));
+    unsigned hs = 0;
+    PMMF_CUDA_TRY(cudaMemcpyAsync(&hs, status_d, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
+    PMMF_CUDA_TRY(cudaStreamSynchronize(st));
+    if (hs & ST_BAD_CSR) return fail(PMMF_ERR_INVALID_ARG, "CSR A: columns out of range or not ascending");
+    if (hs & ST_NONFINITE) return fail(PMMF_ERR_NONFINITE, "A holds NaN or Inf");
+    if (hs & ST_NOT_SYMMETRIC) return fail(PMMF_ERR_NOT_SYMMETRIC, "A is not exactly symmetric");
+    return PMMF_OK;
+}
+
+pmmf_status check_params(const pmmf_matrix *A, const pmmf_params *p) {
+    if (!A || !p) return fail(PMMF_ERR_INVALID_ARG, "NULL matrix or params");
+    if (A->n < 1) return fail(PMMF_ERR_INVALID_ARG, "n must be >= 1");
+    if (A->n >= INT32_MAX) return fail(PMMF_ERR_UNSUPPORTED, "n must be < 2^31");
+    if (A->location != PMMF_HOST && A->location != PMMF_DEVICE)
+        return fail(PMMF_ERR_INVALID_ARG, "bad matrix location");
+    if (p->k < 2 || p->k > 8) return fail(PMMF_ERR_INVALID_ARG, "k must be in [2, 8]");
+    if (!(p->eta > 0.0 && p->eta < 1.0)) return fail(PMMF_ERR_INVALID_ARG, "eta must be in (0, 1)");
+    if (p->cluster_size < p->k) return fail(PMMF_ERR_INVALID_ARG, "cluster_size must be >= k");
+    if (p->core_size < 1 || p->core_size > A->n)
+        return fail(PMMF_ERR_INVALID_ARG, "core_size must be in [1, n]");
+    if (p->lloyd_iters < 0) return fail(PMMF_ERR_INVALID_ARG, "lloyd_iters must be >= 0");
+    if (p->coords && (p->coord_dim < 1 || p->coord_dim > 3))
+        return fail(PMMF_ERR_INVALID_ARG, "coord_dim must be 1, 2 or 3");
+    if (p->coords && p->coords_location != PMMF_HOST && p->coords_location != PMMF_DEVICE)
+        return fail(PMMF_ERR_INVALID_ARG, "bad coords location");
+    if (p->k != 2) return fail(PMMF_ERR_UNSUPPORTED, "this build factors with k = 2 (Givens) only");
+    return PMMF_OK;
+}
+
+pmmf_status factor_impl(const pmmf_matrix *A, const pmmf_params *prm, pmmf_handle *h,
+                        cudaStream_t st) {
+    const int64_t n = A->n;
+    h->n = n;
+    h->k = prm->k;
+    DBuf<unsigned> status;
+    PMMF_TRY(status.zeros(1, st));
+
+    Csr cur;
+    PMMF_TRY(stage_input(A, cur, status.p, st));
+    h->nnz_in = cur.nnz;
+    {
+        DBuf<double> ss;
+        PMMF_TRY(ss.alloc(1, st));
+        PMMF_TRY(sum_squares(cur.val.p, cur.nnz, ss.p, st));
+        double hs = 0.0;
+        PMMF_CUDA_TRY(cudaMemcpyAsync(&hs, ss.p, sizeof(double), cudaMemcpyDeviceToHost, st));
+        PMMF_CUDA_TRY(cudaStreamSynchronize(st));
+        h->norm_a = std::sqrt(hs);
+    }
+
+    // clustering geometry
+    const bool geo = prm->coords != nullptr;
+    const int dim = geo ? prm->coord_dim : 0;
+    DBuf<int32_t> q, morder;
+    if (geo) {
+        DBuf<double> tc;
+        const double *dc = nullptr;
+        PMMF_TRY(to_device(prm->coords, n * dim, prm->coords_location, tc, dc, st));
+        DBuf<uint64_t> code;
+        PMMF_TRY(q.alloc(n * dim, st));
+        PMMF_TRY(code.alloc(n, st));
+        PMMF_CUDA_TRY(cudaMemsetAsync(status.p, 0, sizeof(unsigned), st));
+        PMMF_TRY(quantize_points(dc, n, dim, q.p, code.p, status.p, st));
+        PMMF_TRY(morder.alloc(n, st));
+        PMMF_TRY(radix_sort_u64(code.p, n, 15 * dim, morder.p, st));
+        unsigned hs = 0;
+        PMMF_CUDA_TRY(cudaMemcpyAsync(&hs, status.p, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
+        PMMF_CUDA_TRY(cudaStreamSynchronize(st));
+        if (hs & ST_NONFINITE) return fail(PMMF_ERR_INVALID_ARG, "coords hold NaN or Inf");
+    }
+
+    DBuf<int32_t> act, pos, cl, loc, elimflag;
+    DBuf<double> contribs;
+    PMMF_TRY(act.alloc(n, st));
+    PMMF_TRY(iota_i32(act.p, n, st));
+    PMMF_TRY(pos.alloc(n, st));
+    PMMF_TRY(iota_i32(pos.p, n, st));
+    PMMF_TRY(cl.alloc(n, st));
+    PMMF_TRY(loc.alloc(n, st));
+    PMMF_TRY(elimflag.zeros(n, st));
+    PMMF_TRY(h->hdiag.zeros(n, st));
+    PMMF_TRY(contribs.zeros(n + 1, st));
+
+    const int iters = prm->lloyd_iters > 0 ? prm->lloyd_iters : 10;
+    int64_t s = n;
+    int64_t p = 0;
+    while (s > prm->core_size && (prm->max_stages <= 0 || p < prm->max_stages)) {
+        ++p;
+        h->st.emplace_back();
+        StageData &S = h->st.back();
+        S.s = s;
+        int64_t m = (s + prm->cluster_size / 2) / prm->cluster_size;
+        if (m < 1 || !geo) m = 1;
+        if (m > 1) {
+            PartitionIn in;
+            in.n = n;
+            in.s = s;
+            in.dim = dim;
+            in.q = q.p;
+            in.morder = morder.p;
+            in.pos = pos.p;
+            in.act = act.p;
+            in.cl = cl.p;
+            in.loc = loc.p;
+            PMMF_TRY(partition_stage(in, m, iters, S.cls, st));
+        } else {
+            PMMF_TRY(one_cluster(act.p, s, S.cls, cl.p, loc.p, st));
+        }
+        int64_t sched[2] = {0, 0};
+        DBuf<int64_t> e;
+        PMMF_TRY(schedule_stage(S.cls.coff.p, S.cls.m, s, prm->core_size, prm->eta, e,
+                                S.rot.roff, sched, st));
+        if (sched[1]) {
+            // every cluster too small to rotate: one cluster for this stage
+            PMMF_TRY(one_cluster(act.p, s, S.cls, cl.p, loc.p, st));
+        }
+        S.m = S.cls.m;
+        S.nrot = sched[0];
+        S.rot.nrot = sched[0];
+        {
+            std::vector<int64_t> hc((size_t)S.m + 1);
+            PMMF_CUDA_TRY(cudaMemcpyAsync(hc.data(), S.cls.coff.p, sizeof(int64_t) * hc.size(),
+                                          cudaMemcpyDeviceToHost, st));
+            PMMF_CUDA_TRY(cudaStreamSynchronize(st));
+            for (int64_t u = 0; u < S.m; ++u) S.cmax = std::max(S.cmax, hc[u + 1] - hc[u]);
+        }
+        PMMF_TRY(gram_and_select(cur, pos.p, cl.p, S.cls, S.cmax, prm->seed, p, S.rot,
+                                 elimflag.p, st));
+        UpdateOut up;
+        PMMF_CUDA_TRY(cudaMemsetAsync(status.p, 0, sizeof(unsigned), st));
+        PMMF_TRY(update_stage(cur, act.p, n, pos.p, cl.p, loc.p, S.cls, S.cmax, S.rot,
+                              elimflag.p, p, h->hdiag.p, contribs.p + (p - 1), up, status.p, st));
+        {
+            unsigned hs = 0;
+            int32_t ml = 0;
+            std::vector<int32_t> nl((size_t)S.m);
+            PMMF_CUDA_TRY(cudaMemcpyAsync(&hs, status.p, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
+            PMMF_CUDA_TRY(cudaMemcpyAsync(nl.data(), S.rot.nlev.p, sizeof(int32_t) * nl.size(),
+                                          cudaMemcpyDeviceToHost, st));
+            PMMF_CUDA_TRY(cudaStreamSynchronize(st));
+            if (hs & ST_ROW_TOO_LONG) return fail(PMMF_ERR_UNSUPPORTED, "update: output row too long");
+            for (int32_t v : nl) ml = std::max(ml, v);
+            S.max_levels = ml;
+        }
+        S.nnz_after = up.next.nnz;
+        // next stage's row positions
+        PMMF_CUDA_TRY(cudaMemsetAsync(pos.p, 0xFF, sizeof(int32_t) * (size_t)n, st));
+        PMMF_TRY(set_positions(up.act.p, up.next.rows, pos.p, st));
+        s = up.next.rows;
+        cur = std::move(up.next);
+        act = std::move(up.act);
+        if (prm->record_stages) {
+            S.recorded.rows = cur.rows;
+            S.recorded.nnz = cur.nnz;
+            PMMF_TRY(S.recorded.rowptr.alloc(cur.rows + 1, st));
+            PMMF_TRY(S.recorded.col.alloc(cur.nnz, st));
+            PMMF_TRY(S.recorded.val.alloc(cur.nnz, st));
+            PMMF_TRY(S.recorded_act.alloc(cur.rows, st));
+            PMMF_CUDA_TRY(cudaMemcpyAsync(S.recorded.rowptr.p, cur.rowptr.p, sizeof(int64_t) * (size_t)(cur.rows + 1), cudaMemcpyDeviceToDevice, st));
+            if (cur.nnz > 0) {
+                PMMF_CUDA_TRY(cudaMemcpyAsync(S.recorded.col.p, cur.col.p, sizeof(int32_t) * (size_t)cur.nnz, cudaMemcpyDeviceToDevice, st));
+                PMMF_CUDA_TRY(cudaMemcpyAsync(S.recorded.val.p, cur.val.p, sizeof(double) * (size_t)cur.nnz, cudaMemcpyDeviceToDevice, st));
+            }
+            if (cur.rows > 0)
+                PMMF_CUDA_TRY(cudaMemcpyAsync(S.recorded_act.p, act.p, sizeof(int32_t) * (size_t)cur.rows, cudaMemcpyDeviceToDevice, st));
+            S.has_record = true;
+        }
+    }
+
+    // H: core A_L[S_L, S_L] plus the diagonal
+    h->ncore = s;
+    PMMF_TRY(h->core_idx.alloc(s, st));
+    PMMF_CUDA_TRY(cudaMemcpyAsync(h->core_idx.p, act.p, sizeof(int32_t) * (size_t)s, cudaMemcpyDeviceToDevice, st));
+    PMMF_TRY(h->core.alloc(s * s, st));
+    PMMF_TRY(extract_core(cur, pos.p, s, h->core.p, h->hdiag.p, act.p, st));
+    PMMF_TRY(h->core_pos.alloc(n, st));
+    PMMF_CUDA_TRY(cudaMemsetAsync(h->core_pos.p, 0xFF, sizeof(int32_t) * (size_t)n, st));
+    PMMF_TRY(set_positions(act.p, s, h->core_pos.p, st));
+
+    std::vector<double> hc((size_t)p + 1, 0.0);
+    if (p > 0)
+        PMMF_CUDA_TRY(cudaMemcpyAsync(hc.data(), contribs.p, sizeof(double) * (size_t)p, cudaMemcpyDeviceToHost, st));
+    PMMF_CUDA_TRY(cudaStreamSynchronize(st));
+    double tot = 0.0;
+    for (int64_t i = 0; i < p; ++i) {
+        h->st[i].contrib = hc[i];
+        tot += hc[i];
+    }
+    h->err = h->norm_a > 0.0 ? std::sqrt(tot) / h->norm_a : 0.0;
+    for (auto &S : h->st) {
+        ApplyStage v;
+        v.m = S.m;
+        v.nrot = S.nrot;
+        v.cmax = S.cmax;
+        v.s = S.s;
+        v.coff = S.cls.coff.p;
+        v.members = S.cls.members.p;
+        v.roff = S.rot.roff.p;
+        v.lvl_off = S.rot.lvl_off.p;
+        v.nlev = S.rot.nlev.p;
+        v.lvlrot = S.rot.lvl.p;
+        h->views.push_back(v);
+    }
+    return PMMF_OK;
+}
+
+}  // namespace
+}  // namespace pmmf
+
+using namespace pmmf;
+
+extern "C" {
+
+const char *pmmf_last_error(void) { return last_error_cstr(); }
+
+uint64_t pmmf_launch_count(void) { return g_launches.load(); }
+
+pmmf_status pmmf_factor(const pmmf_matrix *A, const pmmf_params *p, pmmf_handle **out,
+                        void *stream) {
+    set_error("");
+    if (!out) return fail(PMMF_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    PMMF_TRY(check_params(A, p));
+    set_pool_threshold();
+    cudaStream_t st = (cudaStream_t)stream;
+    pmmf_handle *h = new (std::nothrow) pmmf_handle();
+    if (!h) return fail(PMMF_ERR_OOM, "host allocation failed");
+    pmmf_status s;
+    try {
+        s = factor_impl(A, p, h, st);
+    } catch (const std::bad_alloc &) {
+        s = fail(PMMF_ERR_OOM, "host allocation failed");
+    }
+    if (s != PMMF_OK) {
+        cudaStreamSynchronize(st);
+        delete h;
+        return s;
+    }
+    *out = h;
+    return PMMF_OK;
+}
+
+void pmmf_free(pmmf_handle *f) {
+    if (!f) return;
+    cudaDeviceSynchronize();
+    set_free_sync(true);
+    delete f;
+    set_free_sync(false);
+}
+
+pmmf_status pmmf_get_info(const pmmf_handle *f, pmmf_info *info) {
+    if (!f || !info) return fail(PMMF_ERR_INVALID_ARG, "NULL handle or info");
+    info->n = f->n;
+    info->stages = (int32_t)f->st.size();
+    info->core_size = f->ncore;
+    int64_t r = 0;
+    for (auto &s : f->st) r += s.nrot;
+    info->rotations = r;
+    info->nnz_input = f->nnz_in;
+    info->norm_a = f->norm_a;
+    info->error = f->err;
+    return PMMF_OK;
+}
+
+pmmf_status pmmf_get_stage_info(const pmmf_handle *f, int p, pmmf_stage_info *info) {
+    if (!f || !info || p < 0 || p >= (int)f->st.size()) return fail(PMMF_ERR_INVALID_ARG, "bad stage");
+    const StageData &s = f->st[p];
+    info->active = s.s;
+    info->clusters = s.m;
+    info->rotations = s.nrot;
+    info->nnz_after = s.nnz_after;
+    info->max_levels = s.max_levels;
+    info->contrib = s.contrib;
+    return PMMF_OK;
+}
+
+pmmf_status pmmf_get_stage_clusters(const pmmf_handle *f, int p, int64_t *offsets, int32_t *members) {
+    if (!f || p < 0 || p >= (int)f->st.size() || !offsets || !members)
+        return fail(PMMF_ERR_INVALID_ARG, "bad stage or NULL buffer");
+    const StageData &s = f->st[p];
+    PMMF_CUDA_TRY(cudaMemcpy(offsets, s.cls.coff.p, sizeof(int64_t) * (size_t)(s.m + 1), cudaMemcpyDeviceToHost));
+    PMMF_CUDA_TRY(cudaMemcpy(members, s.cls.members.p, sizeof(int32_t) * (size_t)s.s, cudaMemcpyDeviceToHost));
+    return PMMF_OK;
+}
+
+pmmf_status pmmf_get_stage_rotations(const pmmf_handle *f, int p, int32_t *cluster, int32_t *kk,
+                                     int32_t *idx, double *O, int32_t *elim) {
+    if (!f || p < 0 || p >= (int)f->st.size()) return fail(PMMF_ERR_INVALID_ARG, "bad stage");
+    const StageData &s = f->st[p];
+    const int K = f->k;
+    std::vector<int64_t> coff((size_t)s.m + 1), roff((size_t)s.m + 1);
+    std::vector<int32_t> mem((size_t)s.s);
+    std::vector<RotRec> rec((size_t)std::max<int64_t>(s.nrot, 1));
+    PMMF_CUDA_TRY(cudaMemcpy(coff.data(), s.cls.coff.p, sizeof(int64_t) * coff.size(), cudaMemcpyDeviceToHost));
+    PMMF_CUDA_TRY(cudaMemcpy(roff.data(), s.rot.roff.p, sizeof(int64_t) * roff.size(), cudaMemcpyDeviceToHost));
+    PMMF_CUDA_TRY(cudaMemcpy(mem.data(), s.cls.members.p, sizeof(int32_t) * mem.size(), cudaMemcpyDeviceToHost));
+    if (s.nrot > 0)
+        PMMF_CUDA_TRY(cudaMemcpy(rec.data(), s.rot.rec.p, sizeof(RotRec) * (size_t)s.nrot, cudaMemcpyDeviceToHost));
+    for (int64_t u = 0; u < s.m; ++u) {
+        for (int64_t r = roff[u]; r < roff[u + 1]; ++r) {
+            const RotRec &q = rec[r];
+            if (cluster) cluster[r] = (int32_t)u;
+            if (kk) kk[r] = 2;
+            if (idx) {
+                for (int a = 0; a < K; ++a) idx[r * K + a] = -1;
+                idx[r * K + 0] = mem[coff[u] + q.li];
+                idx[r * K + 1] = mem[coff[u] + q.lj];
+            }
+            if (O) {
+                for (int a = 0; a < K * K; ++a) O[r * K * K + a] = 0.0;
+                O[r * K * K + 0] = q.c;
+                O[r * K * K + 1] = -q.s;
+                O[r * K * K + 2] = q.s;
+                O[r * K * K + 3] = q.c;
+            }
+            if (elim) elim[r] = mem[coff[u] + q.le];
+        }
+    }
+    return PMMF_OK;
+}
+
+pmmf_status pmmf_get_h(const pmmf_handle *f, double *hdiag, int32_t *core_idx, double *core) {
+    if (!f) return fail(PMMF_ERR_INVALID_ARG, "NULL handle");
+    if (hdiag) PMMF_CUDA_TRY(cudaMemcpy(hdiag, f->hdiag.p, sizeof(double) * (size_t)f->n, cudaMemcpyDeviceToHost));
+    if (core_idx && f->ncore > 0)
+        PMMF_CUDA_TRY(cudaMemcpy(core_idx, f->core_idx.p, sizeof(int32_t) * (size_t)f->ncore, cudaMemcpyDeviceToHost));
+    if (core && f->ncore > 0)
+        PMMF_CUDA_TRY(cudaMemcpy(core, f->core.p, sizeof(double) * (size_t)(f->ncore * f->ncore), cudaMemcpyDeviceToHost));
+    return PMMF_OK;
+}
+
+}  // extern "C"
+
+namespace pmmf {
+namespace {
+
+pmmf_status ensure_inverse(pmmf_handle *f, cudaStream_t st) {
+    if (f->inv_state == 1) return PMMF_OK;
+    if (f->inv_state == 2) return fail(PMMF_ERR_NOT_SPD, "H is not positive definite");
+    DBuf<unsigned> status;
+    PMMF_TRY(status.zeros(1, st));
+    PMMF_TRY(f->core_inv.alloc(f->ncore * f->ncore, st));
+    PMMF_TRY(invert_core(f->core.p, f->ncore, f->hdiag.p, f->core_pos.p, f->n, f->core_inv.p,
+                         status.p, st));
+    unsigned hs = 0;
+    PMMF_CUDA_TRY(cudaMemcpyAsync(&hs, status.p, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
+    PMMF_CUDA_TRY(cudaStreamSynchronize(st));
+    if (hs & ST_NOT_SPD) {
+        f->inv_state = 2;
+        return fail(PMMF_ERR_NOT_SPD, "H is not positive definite");
+    }
+    f->inv_state = 1;
+    return PMMF_OK;
+}
+
+HData hdata(const pmmf_handle *f) {
+    HData H;
+    H.n = f->n;
+    H.m = f->ncore;
+    H.hdiag = f->hdiag.p;
+    H.core_pos = f->core_pos.p;
+    H.core_idx = f->core_idx.p;
+    H.core = f->core.p;
+    H.core_inv = f->core_inv.p;
+    return H;
+}
+
+// y <- op(x) with y already holding a copy of x.
+pmmf_status apply_inplace(pmmf_handle *f, int op, double *y, int64_t nrhs, int64_t ld,
+                          cudaStream_t st) {
+    const bool inv = op == PMMF_OP_A_INV || op == PMMF_OP_H_INV;
+    if (inv) PMMF_TRY(ensure_inverse(f, st));
+    switch (op) {
+    case PMMF_OP_U: return apply_rotations(f->views, false, y, ld, nrhs, st);
+    case PMMF_OP_UT: return apply_rotations(f->views, true, y, ld, nrhs, st);
+    case PMMF_OP_H:
+    case PMMF_OP_H_INV: return apply_h(hdata(f), inv, y, ld, nrhs, st);
+    case PMMF_OP_A:
+    case PMMF_OP_A_INV:
+        PMMF_TRY(apply_rotations(f->views, false, y, ld, nrhs, st));
+        PMMF_TRY(apply_h(hdata(f), inv, y, ld, nrhs, st));
+        return apply_rotations(f->views, true, y, ld, nrhs, st);
+    default: return fail(PMMF_ERR_INVALID_ARG, "unknown op");
+    }
+}
+
+}  // namespace
+}  // namespace pmmf
+
+extern "C" {
+
+pmmf_status pmmf_get_stage_matrix(const pmmf_handle *f, int p, int64_t *rowptr_n1, int32_t *col,
+                                  double *val, int64_t *nnz) {
+    if (!f || p < 0 || p >= (int)f->st.size()) return fail(PMMF_ERR_INVALID_ARG, "bad stage");
+    const StageData &s = f->st[p];
+    if (!s.has_record) return fail(PMMF_ERR_INVALID_ARG, "stage not recorded (set record_stages)");
+    if (nnz) *nnz = s.recorded.nnz;
+    if (!rowptr_n1 && !col && !val) return PMMF_OK;
+    if (!rowptr_n1 || !col || !val) return fail(PMMF_ERR_INVALID_ARG, "NULL buffer");
+    std::vector<int64_t> rp((size_t)s.recorded.rows + 1);
+    std::vector<int32_t> act((size_t)s.recorded.rows);
+    PMMF_CUDA_TRY(cudaMemcpy(rp.data(), s.recorded.rowptr.p, sizeof(int64_t) * rp.size(), cudaMemcpyDeviceToHost));
+    if (!act.empty())
+        PMMF_CUDA_TRY(cudaMemcpy(act.data(), s.recorded_act.p, sizeof(int32_t) * act.size(), cudaMemcpyDeviceToHost));
+    if (s.recorded.nnz > 0) {
+        PMMF_CUDA_TRY(cudaMemcpy(col, s.recorded.col.p, sizeof(int32_t) * (size_t)s.recorded.nnz, cudaMemcpyDeviceToHost));
+        PMMF_CUDA_TRY(cudaMemcpy(val, s.recorded.val.p, sizeof(double) * (size_t)s.recorded.nnz, cudaMemcpyDeviceToHost));
+    }
+    // rows by global id: rows outside S_p are empty
+    std::vector<int64_t> len((size_t)f->n, 0);
+    for (size_t r = 0; r < act.size(); ++r) len[act[r]] = rp[r + 1] - rp[r];
+    rowptr_n1[0] = 0;
+    for (int64_t i = 0; i < f->n; ++i) rowptr_n1[i + 1] = rowptr_n1[i] + len[i];
+    return PMMF_OK;
+}
+
+pmmf_status pmmf_apply(const pmmf_handle *fc, int op, const double *x, double *y, int64_t nrhs,
+                       int64_t ld, void *stream) {
+    set_error("");
+    pmmf_handle *f = const_cast<pmmf_handle *>(fc);
+    if (!f || !x || !y) return fail(PMMF_ERR_INVALID_ARG, "NULL handle or vector");
+    if (nrhs < 1 || ld < nrhs) return fail(PMMF_ERR_INVALID_ARG, "need nrhs >= 1 and ld >= nrhs");
+    if (op < PMMF_OP_A || op > PMMF_OP_H_INV) return fail(PMMF_ERR_INVALID_ARG, "unknown op");
+    cudaStream_t st = (cudaStream_t)stream;
+    if (x != y) PMMF_TRY(copy_block(x, ld, y, ld, f->n, nrhs, st));
+    return apply_inplace(f, op, y, nrhs, ld, st);
+}
+
+pmmf_status pmmf_solve_precond(const pmmf_handle *fc, const pmmf_matrix *A, const double *b,
+                               double *x, int64_t nrhs, double rtol, int maxit, int32_t *iters,
+                               double *relres, void *stream) {
+    set_error("");
+    pmmf_handle *f = const_cast<pmmf_handle *>(fc);
+    if (!f || !A || !b || !x || !iters || !relres) return fail(PMMF_ERR_INVALID_ARG, "NULL argument");
+    if (A->n != f->n) return fail(PMMF_ERR_INVALID_ARG, "A and the factorization differ in size");
+    if (nrhs < 1 || nrhs > 8) return fail(PMMF_ERR_UNSUPPORTED, "nrhs must be in [1, 8]");
+    if (!(rtol > 0.0) || maxit < 0) return fail(PMMF_ERR_INVALID_ARG, "need rtol > 0 and maxit >= 0");
+    cudaStream_t st = (cudaStream_t)stream;
+    const int64_t n = f->n;
+    const int nr = (int)nrhs;
+    DBuf<unsigned> status;
+    PMMF_TRY(status.zeros(1, st));
+    Csr M;
+    PMMF_TRY(stage_input(A, M, status.p, st));
+    DevCsr dA;
+    dA.n = n;
+    dA.rp = M.rowptr.p;
+    dA.ci = M.col.p;
+    dA.v = M.val.p;
+    PMMF_TRY(ensure_inverse(f, st));
+
+    DBuf<double> r, z, pv, qv, sc, part;
+    DBuf<int32_t> done;
+    PMMF_TRY(r.alloc(n * nr, st));
+    PMMF_TRY(z.alloc(n * nr, st));
+    PMMF_TRY(pv.alloc(n * nr, st));
+    PMMF_TRY(qv.alloc(n * nr, st));
+    PMMF_TRY(sc.zeros(5 * 8, st));          // rz, pq, rr, rznew, bb
+    PMMF_TRY(part.alloc(dot_partial_size(nr), st));
+    PMMF_TRY(done.zeros(8, st));
+    double *rz = sc.p, *pq = sc.p + 8, *rr = sc.p + 16, *rzn = sc.p + 24, *bb = sc.p + 32;
+    PMMF_CUDA_TRY(cudaMemsetAsync(x, 0, sizeof(double) * (size_t)(n * nr), st));
+    PMMF_CUDA_TRY(cudaMemcpyAsync(r.p, b, sizeof(double) * (size_t)(n * nr), cudaMemcpyDeviceToDevice, st));
+    PMMF_CUDA_TRY(cudaMemcpyAsync(z.p, b, sizeof(double) * (size_t)(n * nr), cudaMemcpyDeviceToDevice, st));
+    PMMF_TRY(apply_inplace(f, PMMF_OP_A_INV, z.p, nr, nr, st));
+    PMMF_CUDA_TRY(cudaMemcpyAsync(pv.p, z.p, sizeof(double) * (size_t)(n * nr), cudaMemcpyDeviceToDevice, st));
+    PMMF_TRY(dots(r.p, z.p, n, nr, rz, part.p, st));
+    PMMF_TRY(dots(b, b, n, nr, bb, part.p, st));
+    double hb[8], hr[8];
+    int32_t hdone[8];
+    PMMF_CUDA_TRY(cudaMemcpyAsync(hb, bb, sizeof(double) * nr, cudaMemcpyDeviceToHost, st));
+    PMMF_CUDA_TRY(cudaStreamSynchronize(st));
+    for (int c = 0; c < nr; ++c) {
+        hb[c] = std::sqrt(hb[c]);
+        hdone[c] = hb[c] == 0.0;
+        iters[c] = 0;
+    }
+    PMMF_CUDA_TRY(cudaMemcpyAsync(done.p, hdone, sizeof(int32_t) * nr, cudaMemcpyHostToDevice, st));
+    for (int it = 1; it <= maxit; ++it) {
+        bool all = true;
+        for (int c = 0; c < nr; ++c) all = all && hdone[c];
+        if (all) break;
+        PMMF_TRY(spmv(dA, pv.p, qv.p, nr, st));
+        PMMF_TRY(dots(pv.p, qv.p, n, nr, pq, part.p, st));
+        PMMF_TRY(cg_update_xr(x, r.p, pv.p, qv.p, n, nr, rz, pq, done.p, st));
+        PMMF_TRY(dots(r.p, r.p, n, nr, rr, part.p, st));
+        PMMF_CUDA_TRY(cudaMemcpyAsync(hr, rr, sizeof(double) * nr, cudaMemcpyDeviceToHost, st));
+        PMMF_CUDA_TRY(cudaStreamSynchronize(st));
+        for (int c = 0; c < nr; ++c) {
+            if (hdone[c]) continue;
+            iters[c] = it;
+            if (std::sqrt(hr[c]) / hb[c] <= rtol) hdone[c] = 1;
+        }
+        PMMF_CUDA_TRY(cudaMemcpyAsync(done.p, hdone, sizeof(int32_t) * nr, cudaMemcpyHostToDevice, st));
+        PMMF_CUDA_TRY(cudaMemcpyAsync(z.p, r.p, sizeof(double) * (size_t)(n * nr), cudaMemcpyDeviceToDevice, st));
+        PMMF_TRY(apply_inplace(f, PMMF_OP_A_INV, z.p, nr, nr, st));
+        PMMF_TRY(dots(r.p, z.p, n, nr, rzn, part.p, st));
+        PMMF_TRY(cg_update_p(pv.p, z.p, n, nr, rzn, rz, done.p, st));
+    }
+    // true residual at exit
+    PMMF_TRY(spmv(dA, x, qv.p, nr, st));
+    PMMF_TRY(vec_sub(b, qv.p, r.p, n * nr, st));
+    PMMF_TRY(dots(r.p, r.p, n, nr, rr, part.p, st));
+    PMMF_CUDA_TRY(cudaMemcpyAsync(hr, rr, sizeof(double) * nr, cudaMemcpyDeviceToHost, st));
+    PMMF_CUDA_TRY(cudaStreamSynchronize(st));
+    bool conv = true;
+    for (int c = 0; c < nr; ++c) {
+        relres[c] = hb[c] > 0.0 ? std::sqrt(hr[c]) / hb[c] : 0.0;
+        conv = conv && hdone[c];
+    }
+    if (!conv) return fail(PMMF_ERR_NOT_CONVERGED, "PCG did not converge within maxit");
+    return PMMF_OK;
+}
+
+}  // extern "C"

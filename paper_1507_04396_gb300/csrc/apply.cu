@@ -1,0 +1,345 @@
+// apply.cu -- matrix-free arithmetic with the factorization (Sec. 2.4) and the
+// preconditioned conjugate gradient solver of Sec. 4.
+//
+//   U x      stages 1..P in order; inside a stage every cluster's rotations
+//            level by level (one CTA per cluster, the cluster's slice of x
+//            staged in shared memory).
+//   U^T x    stages P..1, levels in reverse, transposed rotations.
+//   H x      diagonal on wavelet coordinates, dense core block on S_L.
+//   H^-1 x   reciprocal diagonal; the core's inverse, formed once by in-place
+//            Gauss-Jordan elimination (the core is symmetric positive
+//            definite, so no pivoting is needed and a non-positive pivot means
+//            "not SPD").
+#include "apply.cuh"
+
+namespace pmmf {
+
+namespace {
+
+constexpr int AP_THREADS = 256;
+
+// One CTA per cluster: gather x[members][0..nr), apply the levels, scatter.
+template <bool TRANSPOSE>
+__global__ void __launch_bounds__(AP_THREADS)
+k_apply_stage(const int64_t *coff, const int32_t *members, const int64_t *roff,
+              const int32_t *lvl_off, const int32_t *nlev, const Rot2 *lvlrot, double *x,
+              int64_t ld, int64_t r0, int nr) {
+    extern __shared__ double sx[];
+    const int64_t u = blockIdx.x;
+    const int64_t base = coff[u];
+    const int c = (int)(coff[u + 1] - base);
+    const int nl = nlev[u];
+    if (nl == 0) return;
+    for (int64_t q = threadIdx.x; q < (int64_t)c * nr; q += AP_THREADS) {
+        int64_t l = q / nr, r = q - l * nr;
+        sx[q] = x[(int64_t)members[base + l] * ld + r0 + r];
+    }
+    __syncthreads();
+    const int32_t *lo = lvl_off + roff[u] + u;
+    for (int Li = 0; Li < nl; ++Li) {
+        const int L = TRANSPOSE ? nl - 1 - Li : Li;
+        const int b0 = lo[L], cnt = lo[L + 1] - b0;
+        for (int q = threadIdx.x; q < cnt * nr; q += AP_THREADS) {
+            const int t = q / nr, r = q - t * nr;
+            const Rot2 rt = lvlrot[b0 + t];
+            double a = sx[rt.li * nr + r], b = sx[rt.lj * nr + r], na, nb;
+            if (TRANSPOSE) rot_pair_t(rt.c, rt.s, a, b, na, nb);
+            else rot_pair(rt.c, rt.s, a, b, na, nb);
+            sx[rt.li * nr + r] = na;
+            sx[rt.lj * nr + r] = nb;
+        }
+        __syncthreads();
+    }
+    for (int64_t q = threadIdx.x; q < (int64_t)c * nr; q += AP_THREADS) {
+        int64_t l = q / nr, r = q - l * nr;
+        x[(int64_t)members[base + l] * ld + r0 + r] = sx[q];
+    }
+}
+
+// y = x (strided copy of an n x nrhs block)
+__global__ void k_copy_block(const double *x, int64_t ldx, double *y, int64_t ldy, int64_t n,
+                             int64_t nrhs) {
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n * nrhs;
+         q += (int64_t)gridDim.x * blockDim.x) {
+        int64_t i = q / nrhs, r = q - i * nrhs;
+        y[i * ldy + r] = x[i * ldx + r];
+    }
+}
+
+// Wavelet part of H or H^-1 (core coordinates untouched here); gathers the
+// core slice into zc.
+template <bool INV>
+__global__ void k_h_diag(double *x, int64_t ld, int64_t n, int64_t nrhs, const double *hdiag,
+                         const int32_t *core_pos, double *zc) {
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n * nrhs;
+         q += (int64_t)gridDim.x * blockDim.x) {
+        int64_t i = q / nrhs, r = q - i * nrhs;
+        int32_t cp = core_pos[i];
+        double v = x[i * ld + r];
+        if (cp >= 0) zc[(int64_t)cp * nrhs + r] = v;
+        else x[i * ld + r] = INV ? __ddiv_rn(v, hdiag[i]) : __dmul_rn(hdiag[i], v);
+    }
+}
+
+// Core part: x[core_idx[a]] = sum_b C[a][b] zc[b], a sequential chain per output.
+__global__ void k_core_gemv(const double *C, int64_t m, const double *zc, int64_t nrhs,
+                            const int32_t *core_idx, double *x, int64_t ld) {
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < m * nrhs;
+         q += (int64_t)gridDim.x * blockDim.x) {
+        int64_t a = q / nrhs, r = q - a * nrhs;
+        const double *row = C + a * m;
+        double acc = 0.0;
+        for (int64_t b = 0; b < m; ++b) acc = __dadd_rn(acc, __dmul_rn(row[b], zc[b * nrhs + r]));
+        x[(int64_t)core_idx[a] * ld + r] = acc;
+    }
+}
+
+__global__ void k_wavelet_positive(const double *hdiag, const int32_t *core_pos, int64_t n,
+                                   unsigned *status) {
+    bool bad = false;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        if (core_pos[i] < 0 && !(hdiag[i] > 0.0)) bad = true;
+    if (bad) atomicOr(status, ST_NOT_SPD);
+}
+
+// Symmetric copy of the core from its lower triangle (the part a Cholesky
+// factorization would read).
+__global__ void k_sym_lower(const double *C, int64_t m, double *S) {
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < m * m;
+         q += (int64_t)gridDim.x * blockDim.x) {
+        int64_t i = q / m, j = q - i * m;
+        S[q] = i >= j ? C[i * m + j] : C[j * m + i];
+    }
+}
+
+__global__ void k_gj_save(const double *S, int64_t m, int64_t k, double *rowk, double *colk,
+                          unsigned *status) {
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < m;
+         q += (int64_t)gridDim.x * blockDim.x) {
+        rowk[q] = S[k * m + q];
+        colk[q] = S[q * m + k];
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0 && !(S[k * m + k] > 0.0)) atomicOr(status, ST_NOT_SPD);
+}
+
+// In-place Gauss-Jordan step on pivot k: a_kk <- 1/p, a_kj <- a_kj/p,
+// a_ik <- -a_ik/p, a_ij <- a_ij - a_ik a_kj / p.
+__global__ void k_gj_step(double *S, int64_t m, int64_t k, const double *rowk, const double *colk) {
+    const double p = rowk[k];
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < m * m;
+         q += (int64_t)gridDim.x * blockDim.x) {
+        int64_t i = q / m, j = q - i * m;
+        double v;
+        if (i == k && j == k) v = __ddiv_rn(1.0, p);
+        else if (i == k) v = __ddiv_rn(rowk[j], p);
+        else if (j == k) v = -__ddiv_rn(colk[i], p);
+        else v = __dsub_rn(S[q], __ddiv_rn(__dmul_rn(colk[i], rowk[j]), p));
+        S[q] = v;
+    }
+}
+
+// ---- PCG helpers (n x nrhs row-major, ld = nrhs) ----
+
+__global__ void k_spmv(int64_t n, const int64_t *rp, const int32_t *ci, const double *v,
+                       const double *x, double *y, int nrhs) {
+    int lane = threadIdx.x & 31;
+    int64_t w = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t i = w; i < n; i += nw) {
+        double acc[8];
+        for (int r = 0; r < 8; ++r) acc[r] = 0.0;
+        for (int64_t q = rp[i] + lane; q < rp[i + 1]; q += 32) {
+            double a = v[q];
+            int64_t c = ci[q];
+            for (int r = 0; r < nrhs; ++r) acc[r] = __fma_rn(a, x[c * nrhs + r], acc[r]);
+        }
+        for (int r = 0; r < nrhs; ++r) {
+            double s = warp_sum(acc[r]);
+            if (lane == 0) y[i * nrhs + r] = s;
+        }
+    }
+}
+
+constexpr int DOT_BLOCKS = 304;
+
+// partial[b * nrhs + r] = sum over this block's rows of x[:, r] * y[:, r]
+__global__ void k_dot_partial(const double *x, const double *y, int64_t n, int nrhs,
+                              double *partial) {
+    __shared__ double ws[8][8];
+    double acc[8];
+    for (int r = 0; r < 8; ++r) acc[r] = 0.0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        for (int r = 0; r < nrhs; ++r) acc[r] = __fma_rn(x[i * nrhs + r], y[i * nrhs + r], acc[r]);
+    int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    for (int r = 0; r < nrhs; ++r) {
+        double s = warp_sum(acc[r]);
+        if (lane == 0) ws[w][r] = s;
+    }
+    __syncthreads();
+    if (threadIdx.x < (unsigned)nrhs) {
+        double s = 0.0;
+        for (int q = 0; q < (int)(blockDim.x >> 5); ++q) s += ws[q][threadIdx.x];
+        partial[blockIdx.x * nrhs + threadIdx.x] = s;
+    }
+}
+
+__global__ void k_dot_final(const double *partial, int nb, int nrhs, double *out) {
+    int r = threadIdx.x;
+    if (r < nrhs) {
+        double s = 0.0;
+        for (int b = 0; b < nb; ++b) s += partial[b * nrhs + r];
+        out[r] = s;
+    }
+}
+
+// alpha = rz / pq on active columns; x += alpha p; r -= alpha q
+__global__ void k_cg_xr(double *x, double *r, const double *p, const double *q, int64_t n,
+                        int nrhs, const double *rz, const double *pq, const int32_t *done) {
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n * nrhs;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        int c = (int)(t % nrhs);
+        if (done[c]) continue;
+        double alpha = rz[c] / pq[c];
+        x[t] = __fma_rn(alpha, p[t], x[t]);
+        r[t] = __fma_rn(-alpha, q[t], r[t]);
+    }
+}
+
+// beta = rz_new / rz; p = z + beta p; rz <- rz_new  (active columns)
+__global__ void k_cg_p(double *p, const double *z, int64_t n, int nrhs, const double *rznew,
+                       const double *rz, const int32_t *done) {
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n * nrhs;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        int c = (int)(t % nrhs);
+        if (done[c]) continue;
+        double beta = rznew[c] / rz[c];
+        p[t] = __fma_rn(beta, p[t], z[t]);
+    }
+}
+
+__global__ void k_copy_scalars(const double *src, double *dst, const int32_t *done, int nrhs) {
+    int r = threadIdx.x;
+    if (r < nrhs && !done[r]) dst[r] = src[r];
+}
+
+__global__ void k_sub(const double *b, const double *q, double *r, int64_t cnt) {
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < cnt;
+         t += (int64_t)gridDim.x * blockDim.x)
+        r[t] = __dsub_rn(b[t], q[t]);
+}
+
+}  // namespace
+
+pmmf_status apply_rotations(const ApplyStages &S, bool transpose, double *x, int64_t ld,
+                            int64_t nrhs, cudaStream_t st) {
+    for (size_t pi = 0; pi < S.size(); ++pi) {
+        const ApplyStage &a = transpose ? S[S.size() - 1 - pi] : S[pi];
+        if (a.nrot == 0) continue;
+        int64_t chunk = (int64_t)(24 * 1024) / (a.cmax > 0 ? a.cmax : 1);
+        if (chunk < 1) {
+            set_error("apply: cluster too large for shared memory");
+            return PMMF_ERR_UNSUPPORTED;
+        }
+        if (chunk > nrhs) chunk = nrhs;
+        for (int64_t r0 = 0; r0 < nrhs; r0 += chunk) {
+            int nr = (int)(nrhs - r0 < chunk ? nrhs - r0 : chunk);
+            size_t sh = sizeof(double) * (size_t)a.cmax * (size_t)nr;
+            prof_begin(KF_APPLY, st);
+            if (transpose) {
+                if (sh > 48 * 1024)
+                    PMMF_CUDA_TRY(cudaFuncSetAttribute(k_apply_stage<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh));
+                k_apply_stage<true><<<(unsigned)a.m, AP_THREADS, sh, st>>>(
+                    a.coff, a.members, a.roff, a.lvl_off, a.nlev, a.lvlrot, x, ld, r0, nr);
+            } else {
+                if (sh > 48 * 1024)
+                    PMMF_CUDA_TRY(cudaFuncSetAttribute(k_apply_stage<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh));
+                k_apply_stage<false><<<(unsigned)a.m, AP_THREADS, sh, st>>>(
+                    a.coff, a.members, a.roff, a.lvl_off, a.nlev, a.lvlrot, x, ld, r0, nr);
+            }
+            // the stage's coordinates read and written once per right-hand side,
+            // their ids, and the rotations (24 B each) with their level offsets
+            prof_end(KF_APPLY, st,
+                     16.0 * (double)a.s * nr + 4.0 * (double)a.s + 24.0 * (double)a.nrot +
+                         4.0 * (double)(a.nrot + a.m), 0.0);
+            PMMF_TRY(launched("apply_stage"));
+        }
+    }
+    return PMMF_OK;
+}
+
+pmmf_status copy_block(const double *x, int64_t ldx, double *y, int64_t ldy, int64_t n,
+                       int64_t nrhs, cudaStream_t st) {
+    k_copy_block<<<grid_for(n * nrhs, 256), 256, 0, st>>>(x, ldx, y, ldy, n, nrhs);
+    return launched("copy_block");
+}
+
+pmmf_status apply_h(const HData &H, bool inverse, double *x, int64_t ld, int64_t nrhs,
+                    cudaStream_t st) {
+    DBuf<double> zc;
+    PMMF_TRY(zc.alloc(H.m * nrhs, st));
+    if (inverse)
+        k_h_diag<true><<<grid_for(H.n * nrhs, 256), 256, 0, st>>>(x, ld, H.n, nrhs, H.hdiag, H.core_pos, zc.p);
+    else
+        k_h_diag<false><<<grid_for(H.n * nrhs, 256), 256, 0, st>>>(x, ld, H.n, nrhs, H.hdiag, H.core_pos, zc.p);
+    PMMF_TRY(launched("h_diag"));
+    k_core_gemv<<<grid_for(H.m * nrhs, 64), 64, 0, st>>>(inverse ? H.core_inv : H.core, H.m, zc.p,
+                                                         nrhs, H.core_idx, x, ld);
+    return launched("core_gemv");
+}
+
+pmmf_status invert_core(const double *core, int64_t m, const double *hdiag, const int32_t *core_pos,
+                        int64_t n, double *inv, unsigned *status, cudaStream_t st) {
+    k_wavelet_positive<<<grid_for(n, 256), 256, 0, st>>>(hdiag, core_pos, n, status);
+    PMMF_TRY(launched("wavelet_positive"));
+    k_sym_lower<<<grid_for(m * m, 256), 256, 0, st>>>(core, m, inv);
+    PMMF_TRY(launched("sym_lower"));
+    DBuf<double> rowk, colk;
+    PMMF_TRY(rowk.alloc(m, st));
+    PMMF_TRY(colk.alloc(m, st));
+    for (int64_t k = 0; k < m; ++k) {
+        k_gj_save<<<grid_for(m, 256), 256, 0, st>>>(inv, m, k, rowk.p, colk.p, status);
+        PMMF_TRY(launched("gj_save"));
+        k_gj_step<<<grid_for(m * m, 256), 256, 0, st>>>(inv, m, k, rowk.p, colk.p);
+        PMMF_TRY(launched("gj_step"));
+    }
+    return PMMF_OK;
+}
+
+pmmf_status spmv(const DevCsr &A, const double *x, double *y, int nrhs, cudaStream_t st) {
+    k_spmv<<<grid_for(A.n * 32, 256), 256, 0, st>>>(A.n, A.rp, A.ci, A.v, x, y, nrhs);
+    return launched("spmv");
+}
+
+pmmf_status dots(const double *x, const double *y, int64_t n, int nrhs, double *out,
+                 double *partial, cudaStream_t st) {
+    k_dot_partial<<<DOT_BLOCKS, 256, 0, st>>>(x, y, n, nrhs, partial);
+    PMMF_TRY(launched("dot_partial"));
+    k_dot_final<<<1, 32, 0, st>>>(partial, DOT_BLOCKS, nrhs, out);
+    return launched("dot_final");
+}
+
+int64_t dot_partial_size(int nrhs) { return (int64_t)DOT_BLOCKS * nrhs; }
+
+pmmf_status cg_update_xr(double *x, double *r, const double *p, const double *q, int64_t n,
+                         int nrhs, const double *rz, const double *pq, const int32_t *done,
+                         cudaStream_t st) {
+    k_cg_xr<<<grid_for(n * nrhs, 256), 256, 0, st>>>(x, r, p, q, n, nrhs, rz, pq, done);
+    return launched("cg_xr");
+}
+
+pmmf_status cg_update_p(double *p, const double *z, int64_t n, int nrhs, const double *rznew,
+                        double *rz, const int32_t *done, cudaStream_t st) {
+    k_cg_p<<<grid_for(n * nrhs, 256), 256, 0, st>>>(p, z, n, nrhs, rznew, rz, done);
+    PMMF_TRY(launched("cg_p"));
+    k_copy_scalars<<<1, 32, 0, st>>>(rznew, rz, done, nrhs);
+    return launched("copy_scalars");
+}
+
+pmmf_status vec_sub(const double *b, const double *q, double *r, int64_t cnt, cudaStream_t st) {
+    k_sub<<<grid_for(cnt, 256), 256, 0, st>>>(b, q, r, cnt);
+    return launched("sub");
+}
+
+}  // namespace pmmf

@@ -1,0 +1,352 @@
+// partition.cu -- Algorithm 1, "cluster the active columns": k-means on the
+// coordinates' points, in exact integer arithmetic so that every assignment is
+// reproducible bit for bit, plus the per-stage elimination schedule.
+//
+// Points are quantized once to 15-bit integers per dimension over the bounding
+// box of all n points.  Each stage initialises m centroids as the rounded means
+// of m equal chunks of the active points in Morton order (ties by id), then
+// runs Lloyd iterations: squared integer distance (uint32 is exact: 3 * 32767^2
+// < 2^32), ties to the lower centroid, centroid = round(sum / count) with halves
+// up, an empty cluster keeps its centroid.  Sums are integers, so the atomics
+// that accumulate them are order independent.
+#include "common.cuh"
+#include "stage.cuh"
+
+namespace pmmf {
+
+namespace {
+
+constexpr uint32_t QMAX = 32767u;
+
+__global__ void k_bbox(const double *x, int64_t n, int dim, double *lohi, unsigned *status) {
+    __shared__ double slo[32], shi[32];
+    for (int d = 0; d < dim; ++d) {
+        double lo = x[d], hi = x[d];
+        bool bad = false;
+        for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
+            double v = x[i * dim + d];
+            bad |= !isfinite(v);
+            lo = fmin(lo, v);
+            hi = fmax(hi, v);
+        }
+        if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(status, ST_NONFINITE);
+        for (int o = 16; o > 0; o >>= 1) {
+            lo = fmin(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+            hi = fmax(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+        }
+        if ((threadIdx.x & 31) == 0) { slo[threadIdx.x >> 5] = lo; shi[threadIdx.x >> 5] = hi; }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            for (int w = 1; w < (int)(blockDim.x >> 5); ++w) { lo = fmin(lo, slo[w]); hi = fmax(hi, shi[w]); }
+            lo = fmin(lo, slo[0]);
+            hi = fmax(hi, shi[0]);
+            lohi[2 * d] = lo;
+            lohi[2 * d + 1] = hi;
+        }
+        __syncthreads();
+    }
+}
+
+__global__ void k_quantize(const double *x, int64_t n, int dim, const double *lohi, int32_t *q,
+                           uint64_t *code) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        uint32_t qq[3] = {0, 0, 0};
+        for (int d = 0; d < dim; ++d) {
+            double lo = lohi[2 * d], hi = lohi[2 * d + 1];
+            double span = __dsub_rn(hi, lo);
+            double scale = span > 0.0 ? __ddiv_rn((double)QMAX, span) : 0.0;
+            double f = floor(__dmul_rn(__dsub_rn(x[i * dim + d], lo), scale));
+            uint32_t v = f <= 0.0 ? 0u : (f >= (double)QMAX ? QMAX : (uint32_t)f);
+            qq[d] = v;
+            q[i * dim + d] = (int32_t)v;
+        }
+        uint64_t c = 0;
+        for (int b = 0; b < 15; ++b)
+            for (int d = 0; d < dim; ++d) c |= (uint64_t)((qq[d] >> b) & 1u) << (b * dim + d);
+        code[i] = c;
+    }
+}
+
+// flag[i] = 1 if the i-th point of the global Morton order is active
+__global__ void k_active_flags(const int32_t *morder, int64_t n, const int32_t *pos,
+                               int32_t *flag) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        flag[i] = pos[morder[i]] >= 0 ? 1 : 0;
+}
+
+__global__ void k_compact_order(const int32_t *morder, int64_t n, const int32_t *pos,
+                                const int64_t *ex, int32_t *out) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        if (pos[morder[i]] >= 0) out[ex[i]] = morder[i];
+}
+
+// Initial centroids: chunk t holds Morton-order positions [floor(t s/m), floor((t+1) s/m)).
+__global__ void k_chunk_sums(const int32_t *amorder, int64_t s, int64_t m, const int32_t *q,
+                             int dim, unsigned long long *sum, unsigned long long *cnt) {
+    for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < s;
+         r += (int64_t)gridDim.x * blockDim.x) {
+        int64_t t = ((r + 1) * m - 1) / s;
+        int32_t g = amorder[r];
+        for (int d = 0; d < dim; ++d) atomicAdd(&sum[t * dim + d], (unsigned long long)q[(int64_t)g * dim + d]);
+        atomicAdd(&cnt[t], 1ull);
+    }
+}
+
+__global__ void k_centroids(int64_t m, int dim, const unsigned long long *sum,
+                            const unsigned long long *cnt, int32_t *cen) {
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < m;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        unsigned long long c = cnt[t];
+        if (c == 0) continue;
+        for (int d = 0; d < dim; ++d) cen[t * dim + d] = (int32_t)((sum[t * dim + d] + c / 2) / c);
+    }
+}
+
+// Assignment step: nearest centroid in squared integer distance, ties to the
+// lower index; accumulate the new sums.
+template <int DIM>
+__global__ void k_assign(const int32_t *act, int64_t s, const int32_t *q, const int32_t *cen,
+                         int64_t m, int32_t *label, unsigned long long *sum,
+                         unsigned long long *cnt) {
+    extern __shared__ int32_t sc[];
+    for (int64_t t = threadIdx.x; t < m * DIM; t += blockDim.x) sc[t] = cen[t];
+    __syncthreads();
+    for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < s;
+         r += (int64_t)gridDim.x * blockDim.x) {
+        int32_t g = act[r];
+        int32_t p[DIM];
+        for (int d = 0; d < DIM; ++d) p[d] = q[(int64_t)g * DIM + d];
+        uint32_t best = 0xffffffffu;
+        int64_t bt = 0;
+        for (int64_t t = 0; t < m; ++t) {
+            uint32_t dd = 0;
+            for (int d = 0; d < DIM; ++d) {
+                int32_t z = p[d] - sc[t * DIM + d];
+                dd += (uint32_t)(z * z);
+            }
+            if (dd < best) { best = dd; bt = t; }
+        }
+        label[r] = (int32_t)bt;
+        for (int d = 0; d < DIM; ++d) atomicAdd(&sum[bt * DIM + d], (unsigned long long)p[d]);
+        atomicAdd(&cnt[bt], 1ull);
+    }
+}
+
+// Nonempty labels become cluster ordinals in ascending label order.
+__global__ void k_nonempty(const unsigned long long *cnt, int64_t m, int32_t *flag) {
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < m;
+         t += (int64_t)gridDim.x * blockDim.x)
+        flag[t] = cnt[t] > 0 ? 1 : 0;
+}
+
+__global__ void k_cluster_sizes(const unsigned long long *cnt, int64_t m, const int64_t *ord,
+                                int64_t *size) {
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < m;
+         t += (int64_t)gridDim.x * blockDim.x)
+        if (cnt[t] > 0) size[ord[t]] = (int64_t)cnt[t];
+}
+
+__global__ void k_members(const int32_t *act, const int32_t *label, const int32_t *perm, int64_t s,
+                          const int64_t *ord, const int64_t *coff, int32_t *members, int32_t *cl,
+                          int32_t *loc) {
+    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < s;
+         j += (int64_t)gridDim.x * blockDim.x) {
+        int32_t r = perm[j];
+        int32_t g = act[r];
+        int64_t u = ord[label[r]];
+        members[j] = g;
+        cl[g] = (int32_t)u;
+        loc[g] = (int32_t)(j - coff[u]);
+    }
+}
+
+__global__ void k_one_cluster(const int32_t *act, int64_t s, int32_t *members, int32_t *cl,
+                              int32_t *loc, int64_t *coff) {
+    for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < s;
+         r += (int64_t)gridDim.x * blockDim.x) {
+        int32_t g = act[r];
+        members[r] = g;
+        cl[g] = 0;
+        loc[g] = (int32_t)r;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) { coff[0] = 0; coff[1] = s; }
+}
+
+// Elimination schedule: e_u = floor(eta c_u); while the total exceeds
+// s - core_size, the largest e_u is decremented (ties to the lowest u).  That
+// greedy equals capping every e_u at the smallest level L with
+// sum_u min(e_u, L) >= target and then decrementing the first
+// (sum - target) clusters (ascending u) that sit at L.  out[0] = total,
+// out[1] = 1 if no cluster can rotate (the caller then uses one cluster).
+__global__ void k_schedule(const int64_t *coff, int64_t mm, int64_t s, int64_t core, double eta,
+                           int64_t *e, int64_t *roff, int64_t *out) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    int64_t total = 0, emax = 0;
+    for (int64_t u = 0; u < mm; ++u) {
+        int64_t c = coff[u + 1] - coff[u];
+        int64_t v = (int64_t)floor(__dmul_rn(eta, (double)c));
+        e[u] = v;
+        total += v;
+        emax = v > emax ? v : emax;
+    }
+    int64_t target = s - core;
+    if (total > target) {
+        int64_t lo = 0, hi = emax;  // smallest L with f(L) >= target
+        while (lo < hi) {
+            int64_t mid = (lo + hi) / 2, f = 0;
+            for (int64_t u = 0; u < mm; ++u) f += e[u] < mid ? e[u] : mid;
+            if (f >= target) hi = mid; else lo = mid + 1;
+        }
+        int64_t L = lo, f = 0;
+        for (int64_t u = 0; u < mm; ++u) {
+            if (e[u] > L) e[u] = L;
+            f += e[u];
+        }
+        for (int64_t u = 0; u < mm && f > target; ++u)
+            if (e[u] == L) { e[u] -= 1; --f; }
+        total = f;
+    }
+    out[1] = 0;
+    if (total == 0) {
+        int64_t ee = (int64_t)floor(__dmul_rn(eta, (double)s));
+        if (ee > target) ee = target;
+        if (ee < 1) ee = 1;
+        out[1] = 1;
+        total = ee;
+        e[0] = ee;
+    }
+    roff[0] = 0;
+    if (!out[1])
+        for (int64_t u = 0; u < mm; ++u) roff[u + 1] = roff[u] + e[u];
+    else
+        roff[1] = total;
+    out[0] = total;
+}
+
+}  // namespace
+
+pmmf_status quantize_points(const double *coords, int64_t n, int dim, int32_t *q, uint64_t *code,
+                            unsigned *status, cudaStream_t st) {
+    DBuf<double> lohi;
+    PMMF_TRY(lohi.alloc(2 * dim, st));
+    k_bbox<<<1, 1024, 0, st>>>(coords, n, dim, lohi.p, status);
+    PMMF_TRY(launched("bbox"));
+    k_quantize<<<grid_for(n, 256), 256, 0, st>>>(coords, n, dim, lohi.p, q, code);
+    return launched("quantize");
+}
+
+pmmf_status partition_stage(const PartitionIn &in, int64_t m, int iters, StageClusters &out,
+                            cudaStream_t st) {
+    const int64_t s = in.s;
+    const int dim = in.dim;
+    PMMF_TRY(out.members.alloc(s, st));
+    if (m <= 1 || !in.q) {
+        PMMF_TRY(out.coff.alloc(2, st));
+        k_one_cluster<<<grid_for(s, 256), 256, 0, st>>>(in.act, s, out.members.p, in.cl, in.loc,
+                                                         out.coff.p);
+        PMMF_TRY(launched("one_cluster"));
+        out.m = 1;
+        return PMMF_OK;
+    }
+    // active points in Morton order
+    DBuf<int32_t> flag, amorder, label, perm, cen, nflag;
+    DBuf<int64_t> ex, ord, size;
+    DBuf<unsigned long long> sum, cnt;
+    PMMF_TRY(flag.alloc(in.n, st));
+    PMMF_TRY(ex.alloc(in.n + 1, st));
+    PMMF_TRY(amorder.alloc(s, st));
+    k_active_flags<<<grid_for(in.n, 256), 256, 0, st>>>(in.morder, in.n, in.pos, flag.p);
+    PMMF_TRY(launched("active_flags"));
+    PMMF_TRY(scan_i32_to_i64(flag.p, ex.p, in.n, st));
+    k_compact_order<<<grid_for(in.n, 256), 256, 0, st>>>(in.morder, in.n, in.pos, ex.p, amorder.p);
+    PMMF_TRY(launched("compact_order"));
+    // initial centroids
+    PMMF_TRY(sum.zeros(m * dim, st));
+    PMMF_TRY(cnt.zeros(m, st));
+    PMMF_TRY(cen.alloc(m * dim, st));
+    k_chunk_sums<<<grid_for(s, 256), 256, 0, st>>>(amorder.p, s, m, in.q, dim, sum.p, cnt.p);
+    PMMF_TRY(launched("chunk_sums"));
+    k_centroids<<<grid_for(m, 256), 256, 0, st>>>(m, dim, sum.p, cnt.p, cen.p);
+    PMMF_TRY(launched("centroids"));
+    // Lloyd iterations
+    PMMF_TRY(label.alloc(s, st));
+    size_t sh = sizeof(int32_t) * (size_t)(m * dim);
+    if (sh > 200 * 1024) {
+        set_error("too many clusters for the assignment kernel");
+        return PMMF_ERR_UNSUPPORTED;
+    }
+    auto assign = dim == 1 ? (void *)k_assign<1> : dim == 2 ? (void *)k_assign<2> : (void *)k_assign<3>;
+    if (sh > 48 * 1024)
+        PMMF_CUDA_TRY(cudaFuncSetAttribute(assign, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh));
+    for (int it = 0; it < iters; ++it) {
+        PMMF_CUDA_TRY(cudaMemsetAsync(sum.p, 0, sizeof(unsigned long long) * (size_t)(m * dim), st));
+        PMMF_CUDA_TRY(cudaMemsetAsync(cnt.p, 0, sizeof(unsigned long long) * (size_t)m, st));
+        unsigned g = grid_for(s, 256, 152 * 8);
+        prof_begin(KF_PARTITION, st);
+        if (dim == 1) k_assign<1><<<g, 256, sh, st>>>(in.act, s, in.q, cen.p, m, label.p, sum.p, cnt.p);
+        else if (dim == 2) k_assign<2><<<g, 256, sh, st>>>(in.act, s, in.q, cen.p, m, label.p, sum.p, cnt.p);
+        else k_assign<3><<<g, 256, sh, st>>>(in.act, s, in.q, cen.p, m, label.p, sum.p, cnt.p);
+        // per point: its id, its quantized coordinates and its label; integer
+        // work of s * m distance evaluations (3 ops per dimension)
+        prof_end(KF_PARTITION, st, (double)s * (8.0 + 4.0 * dim), 3.0 * dim * (double)s * (double)m);
+        PMMF_TRY(launched("assign"));
+        if (it + 1 < iters) {
+            k_centroids<<<grid_for(m, 256), 256, 0, st>>>(m, dim, sum.p, cnt.p, cen.p);
+            PMMF_TRY(launched("centroids"));
+        }
+    }
+    if (iters <= 0) {
+        set_error("lloyd_iters must be positive");
+        return PMMF_ERR_INVALID_ARG;
+    }
+    // clusters: nonempty labels in order; members ascending by global id
+    PMMF_TRY(nflag.alloc(m, st));
+    PMMF_TRY(ord.alloc(m + 1, st));
+    k_nonempty<<<grid_for(m, 256), 256, 0, st>>>(cnt.p, m, nflag.p);
+    PMMF_TRY(launched("nonempty"));
+    PMMF_TRY(scan_i32_to_i64(nflag.p, ord.p, m, st));
+    int64_t mm = 0;
+    PMMF_CUDA_TRY(cudaMemcpyAsync(&mm, ord.p + m, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+    PMMF_CUDA_TRY(cudaStreamSynchronize(st));
+    PMMF_TRY(size.alloc(mm + 1, st));
+    k_cluster_sizes<<<grid_for(m, 256), 256, 0, st>>>(cnt.p, m, ord.p, size.p);
+    PMMF_TRY(launched("cluster_sizes"));
+    PMMF_TRY(out.coff.alloc(mm + 1, st));
+    PMMF_TRY(scan_i64(size.p, out.coff.p, mm, st));
+    PMMF_TRY(perm.alloc(s, st));
+    PMMF_TRY(stable_sort_by_key((const uint32_t *)label.p, s, m, perm.p, st));
+    k_members<<<grid_for(s, 256), 256, 0, st>>>(in.act, label.p, perm.p, s, ord.p, out.coff.p,
+                                                 out.members.p, in.cl, in.loc);
+    PMMF_TRY(launched("members"));
+    out.m = mm;
+    return PMMF_OK;
+}
+
+pmmf_status schedule_stage(const int64_t *coff, int64_t mm, int64_t s, int64_t core, double eta,
+                           DBuf<int64_t> &e, DBuf<int64_t> &roff, int64_t *host_out,
+                           cudaStream_t st) {
+    PMMF_TRY(e.alloc(mm > 1 ? mm : 1, st));
+    PMMF_TRY(roff.alloc(mm + 1 > 2 ? mm + 1 : 2, st));
+    DBuf<int64_t> out;
+    PMMF_TRY(out.alloc(2, st));
+    k_schedule<<<1, 32, 0, st>>>(coff, mm, s, core, eta, e.p, roff.p, out.p);
+    PMMF_TRY(launched("schedule"));
+    PMMF_CUDA_TRY(cudaMemcpyAsync(host_out, out.p, 2 * sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+    PMMF_CUDA_TRY(cudaStreamSynchronize(st));
+    return PMMF_OK;
+}
+
+pmmf_status one_cluster(const int32_t *act, int64_t s, StageClusters &out, int32_t *cl,
+                        int32_t *loc, cudaStream_t st) {
+    PMMF_TRY(out.members.alloc(s, st));
+    PMMF_TRY(out.coff.alloc(2, st));
+    k_one_cluster<<<grid_for(s, 256), 256, 0, st>>>(act, s, out.members.p, cl, loc, out.coff.p);
+    PMMF_TRY(launched("one_cluster"));
+    out.m = 1;
+    return PMMF_OK;
+}
+
+}  // namespace pmmf

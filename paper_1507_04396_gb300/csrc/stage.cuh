@@ -1,0 +1,78 @@
+// stage.cuh -- per-stage data passed between the kernels of one pMMF stage
+// (internal to the library).
+#pragma once
+
+#include "common.cuh"
+
+namespace pmmf {
+
+struct PartitionIn {
+    int64_t n = 0, s = 0;
+    int dim = 0;
+    const int32_t *q = nullptr;       // n x dim quantized points (null: one cluster)
+    const int32_t *morder = nullptr;  // n global ids in Morton order
+    const int32_t *pos = nullptr;     // n: row of a global id in the active list, -1 if inactive
+    const int32_t *act = nullptr;     // s active global ids, ascending
+    int32_t *cl = nullptr;            // n: cluster ordinal of a global id (output)
+    int32_t *loc = nullptr;           // n: index inside its cluster (output)
+};
+
+struct StageClusters {
+    int64_t m = 0;
+    DBuf<int64_t> coff;       // m + 1
+    DBuf<int32_t> members;    // s, cluster by cluster, ascending global id
+};
+
+// A CSR block over the active rows: row r is global id act[r].
+struct Csr {
+    int64_t rows = 0, nnz = 0;
+    DBuf<int64_t> rowptr;
+    DBuf<int32_t> col;        // global ids
+    DBuf<double> val;
+};
+
+// Rotations of one stage, in the two orders the kernels need.
+struct StageRotations {
+    int64_t nrot = 0;
+    int32_t max_levels = 0;
+    DBuf<int64_t> roff;       // m + 1: cluster u owns [roff[u], roff[u+1])
+    DBuf<RotRec> rec;         // step order (export)
+    DBuf<Rot2> lvl;           // grouped by dependency level inside each cluster
+    DBuf<int32_t> lvl_off;    // cluster u: entries [roff[u] + u, roff[u] + u + nlev_u + 1)
+    DBuf<int32_t> nlev;       // m
+};
+
+pmmf_status quantize_points(const double *coords, int64_t n, int dim, int32_t *q, uint64_t *code,
+                            unsigned *status, cudaStream_t st);
+pmmf_status partition_stage(const PartitionIn &in, int64_t m, int iters, StageClusters &out,
+                            cudaStream_t st);
+pmmf_status one_cluster(const int32_t *act, int64_t s, StageClusters &out, int32_t *cl,
+                        int32_t *loc, cudaStream_t st);
+pmmf_status schedule_stage(const int64_t *coff, int64_t mm, int64_t s, int64_t core, double eta,
+                           DBuf<int64_t> &e, DBuf<int64_t> &roff, int64_t *host_out,
+                           cudaStream_t st);
+
+// Gram G^u and symmetric local block M^u of every cluster (dense c_u x c_u,
+// row-major at goff[u]) and the rotation search of Algorithm 2.
+pmmf_status gram_and_select(const Csr &A, const int32_t *pos, const int32_t *cl,
+                            const StageClusters &cls, int64_t cmax, uint64_t seed, int64_t stage,
+                            StageRotations &rot, int32_t *elimflag, cudaStream_t st);
+
+// Blocked update A_p = (A Q^T)^T Q^T, residual accounting, H diagonal and
+// compaction to the surviving coordinates.
+struct UpdateOut {
+    Csr next;                 // A_p[S_p, S_p]
+    DBuf<int32_t> act;        // S_p ascending
+    double *contrib = nullptr;   // device accumulator (added to)
+};
+pmmf_status update_stage(const Csr &A, const int32_t *act, int64_t n, const int32_t *pos,
+                         const int32_t *cl, const int32_t *loc, const StageClusters &cls,
+                         int64_t cmax, const StageRotations &rot, const int32_t *elimflag,
+                         int64_t stage, double *hdiag, double *contrib, UpdateOut &out,
+                         unsigned *status, cudaStream_t st);
+
+pmmf_status set_positions(const int32_t *act, int64_t s, int32_t *pos, cudaStream_t st);
+pmmf_status extract_core(const Csr &A, const int32_t *pos, int64_t s, double *core, double *hdiag,
+                         const int32_t *act, cudaStream_t st);
+
+}  // namespace pmmf

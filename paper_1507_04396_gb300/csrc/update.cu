@@ -1,0 +1,355 @@
+// update.cu -- the blocked update of Algorithm 1,
+//     [A_p]_{u,v} <- Qbar_{p,u} [A_{p-1}]_{u,v} Qbar_{p,v}^T   for all u, v,
+// computed as A_p = (A_{p-1} Q^T)^T Q^T: the stage's rotations are applied to
+// every row (a row-local operation), the result is transposed, and the
+// rotations are applied to every row again.  Fused into the second pass: the
+// residual of the eliminated coordinates, the diagonal of H and the
+// compaction of A_p to the surviving coordinates S_p.
+//
+// Row kernel: one warp per row.  The row's entries are grouped by cluster;
+// each cluster's part is expanded into a dense vector in shared memory and the
+// cluster's rotations are applied level by level (rotations of one dependency
+// level touch disjoint coordinates, so lanes apply them concurrently and the
+// bits equal a sequential application in step order).  A rotation whose two
+// inputs are both zero leaves them zero and is skipped.  Exact zeros are
+// dropped from the output.
+#include <climits>
+
+#include "common.cuh"
+#include "stage.cuh"
+
+namespace pmmf {
+
+namespace {
+
+enum Mode { P1_COUNT = 0, P1_WRITE = 1, P2_COUNT = 2, P2_WRITE = 3 };
+
+struct RowArgs {
+    const int64_t *rp;
+    const int32_t *ci;
+    const double *v;
+    int64_t rows;
+    const int32_t *act;        // row -> global id
+    const int32_t *pos;        // global id -> row (stage start)
+    const int32_t *cl, *loc;
+    const int64_t *coff;
+    const int32_t *members;
+    const int64_t *roff;
+    const int32_t *lvl_off, *nlev;
+    const Rot2 *lvlrot;
+    int64_t cmax;
+    int outcap;
+    // pass 1
+    int64_t *wcnt;             // W row counts (COUNT)
+    int64_t *wcur;             // W write cursors (WRITE)
+    int32_t *wcol;
+    double *wval;
+    // pass 2
+    const int32_t *elimflag;
+    int32_t stage;
+    const int64_t *newrow;     // exclusive scan of surviving flags
+    int64_t *ocnt;             // COUNT: output row lengths (by new row)
+    const int64_t *orp;        // WRITE
+    int32_t *ocol;
+    double *oval;
+    double *hdiag;
+    double *contrib;
+    unsigned *status;
+    int64_t *maxlen;
+};
+
+template <int MODE>
+__global__ void k_rows(RowArgs a) {
+    extern __shared__ double smem[];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const int wpb = blockDim.x >> 5;
+    const int64_t per_warp = a.cmax + (MODE == P2_WRITE ? (int64_t)a.outcap * 3 / 2 + 1 : 0);
+    double *dense = smem + per_warp * wib;
+    int32_t *scol = (int32_t *)(dense + a.cmax);
+    double *sval = (double *)(scol + (a.outcap + (a.outcap & 1)));
+    double part = 0.0;
+    for (int64_t r = blockIdx.x * (int64_t)wpb + wib; r < a.rows; r += (int64_t)gridDim.x * wpb) {
+        const int64_t e0 = a.rp[r], e1 = a.rp[r + 1];
+        const int32_t y = a.act[r];
+        const bool yelim = (MODE >= P2_COUNT) && a.elimflag[y] == a.stage;
+        int64_t nout = 0;
+        int nseg = 0;
+        int prev = -1;
+        for (;;) {
+            int mu = INT_MAX;
+            for (int64_t q = e0 + lane; q < e1; q += 32) {
+                int uq = a.cl[a.ci[q]];
+                if (uq > prev && uq < mu) mu = uq;
+            }
+            for (int o = 16; o > 0; o >>= 1) mu = min(mu, __shfl_xor_sync(0xffffffffu, mu, o));
+            if (mu == INT_MAX) break;
+            ++nseg;
+            const int64_t cb = a.coff[mu];
+            const int c = (int)(a.coff[mu + 1] - cb);
+            for (int l = lane; l < c; l += 32) dense[l] = 0.0;
+            __syncwarp();
+            for (int64_t q = e0 + lane; q < e1; q += 32) {
+                int32_t g = a.ci[q];
+                if (a.cl[g] == mu) dense[a.loc[g]] = a.v[q];
+            }
+            __syncwarp();
+            const int32_t *lo = a.lvl_off + a.roff[mu] + mu;
+            const int nl = a.nlev[mu];
+            for (int L = 0; L < nl; ++L) {
+                for (int idx = lo[L] + lane; idx < lo[L + 1]; idx += 32) {
+                    Rot2 q = a.lvlrot[idx];
+                    double vi = dense[q.li], vj = dense[q.lj];
+                    if (vi != 0.0 || vj != 0.0) {
+                        double ni, nj;
+                        rot_pair(q.c, q.s, vi, vj, ni, nj);
+                        dense[q.li] = ni;
+                        dense[q.lj] = nj;
+                    }
+                }
+                __syncwarp();
+            }
+            for (int l0 = 0; l0 < c; l0 += 32) {
+                const int l = l0 + lane;
+                const double x = l < c ? dense[l] : 0.0;
+                const bool nz = x != 0.0;
+                const int32_t g = nz ? a.members[cb + l] : -1;
+                if (MODE == P1_COUNT) {
+                    if (nz) atomicAdd((unsigned long long *)&a.wcnt[a.pos[g]], 1ull);
+                } else if (MODE == P1_WRITE) {
+                    if (nz) {
+                        int64_t slot = (int64_t)atomicAdd((unsigned long long *)&a.wcur[a.pos[g]], 1ull);
+                        a.wcol[slot] = y;
+                        a.wval[slot] = x;
+                    }
+                } else {
+                    bool keep = false;
+                    if (nz) {
+                        if (yelim) {
+                            if (g == y) {
+                                if (MODE == P2_WRITE) a.hdiag[y] = x;
+                            } else {
+                                part = __fma_rn(x, x, part);
+                            }
+                        } else if (a.elimflag[g] == a.stage) {
+                            part = __fma_rn(x, x, part);
+                        } else {
+                            keep = true;
+                        }
+                    }
+                    unsigned km = __ballot_sync(0xffffffffu, keep);
+                    if (MODE == P2_WRITE && keep) {
+                        int64_t slot = nout + __popc(km & ((1u << lane) - 1u));
+                        if (slot < a.outcap) {
+                            scol[slot] = g;
+                            sval[slot] = x;
+                        }
+                    }
+                    nout += __popc(km);
+                }
+            }
+            __syncwarp();
+            prev = mu;
+        }
+        if (MODE == P2_COUNT && !yelim && lane == 0) {
+            a.ocnt[a.newrow[r]] = nout;
+            atomicMax((unsigned long long *)a.maxlen, (unsigned long long)nout);
+        }
+        if (MODE == P2_WRITE && !yelim) {
+            if (nout > a.outcap) {
+                if (lane == 0) atomicOr(a.status, ST_ROW_TOO_LONG);
+            } else {
+                __syncwarp();
+                const int64_t ob = a.orp[a.newrow[r]];
+                const int n = (int)nout;
+                // entries of one cluster segment are already ascending; a single
+                // segment needs no reordering, several are ranked by key
+                for (int q = lane; q < n; q += 32) {
+                    int32_t g = scol[q];
+                    int rank = q;
+                    if (nseg > 1) {
+                        rank = 0;
+                        for (int z = 0; z < n; ++z) rank += scol[z] < g;
+                    }
+                    a.ocol[ob + rank] = g;
+                    a.oval[ob + rank] = sval[q];
+                }
+                __syncwarp();
+            }
+        }
+    }
+    if (MODE == P2_WRITE) {
+        part = warp_sum(part);
+        if (lane == 0 && part != 0.0) atomicAdd(a.contrib, part);
+    }
+}
+
+__global__ void k_survivors(const int32_t *act, int64_t s, const int32_t *elimflag, int32_t stage,
+                            int32_t *flag) {
+    for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < s;
+         r += (int64_t)gridDim.x * blockDim.x)
+        flag[r] = elimflag[act[r]] == stage ? 0 : 1;
+}
+
+__global__ void k_compact_act(const int32_t *act, int64_t s, const int32_t *flag,
+                              const int64_t *newrow, int32_t *nact) {
+    for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < s;
+         r += (int64_t)gridDim.x * blockDim.x)
+        if (flag[r]) nact[newrow[r]] = act[r];
+}
+
+__global__ void k_set_pos(const int32_t *act, int64_t s, int32_t *pos) {
+    for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < s;
+         r += (int64_t)gridDim.x * blockDim.x)
+        pos[act[r]] = (int32_t)r;
+}
+
+__global__ void k_core(const int64_t *rp, const int32_t *ci, const double *v, int64_t s,
+                       const int32_t *pos, const int32_t *act, double *core, double *hdiag) {
+    int lane = threadIdx.x & 31;
+    int64_t w = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t r = w; r < s; r += nw) {
+        for (int64_t q = rp[r] + lane; q < rp[r + 1]; q += 32) {
+            int64_t b = pos[ci[q]];
+            core[r * s + b] = v[q];
+            if (b == r) hdiag[act[r]] = v[q];
+        }
+    }
+}
+
+template <int MODE>
+pmmf_status launch_rows(RowArgs &a, int64_t nnz_in, int64_t nnz_out, cudaStream_t st) {
+    const int64_t per_warp = a.cmax + (MODE == P2_WRITE ? (int64_t)a.outcap * 3 / 2 + 1 : 0);
+    size_t per = sizeof(double) * (size_t)per_warp;
+    int warps = 8;
+    while (warps > 1 && per * warps > 200 * 1024) warps >>= 1;
+    if (per * warps > 220 * 1024) {
+        set_error("row transform: cluster or output row too large for shared memory");
+        return PMMF_ERR_UNSUPPORTED;
+    }
+    size_t sh = per * warps;
+    if (sh > 48 * 1024)
+        PMMF_CUDA_TRY(cudaFuncSetAttribute(k_rows<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh));
+    unsigned grid = grid_for(a.rows, warps, 152 * 16);
+    prof_begin(KF_ROWS, st);
+    k_rows<MODE><<<grid, 32 * warps, sh, st>>>(a);
+    // input rows (12 B per entry, 8 B per row pointer) plus written entries
+    double bytes = 12.0 * (double)nnz_in + 8.0 * (double)(a.rows + 1);
+    if (MODE == P1_WRITE || MODE == P2_WRITE) bytes += 12.0 * (double)nnz_out;
+    prof_end(KF_ROWS, st, bytes, 0.0);
+    return launched("rows");
+}
+
+}  // namespace
+
+pmmf_status set_positions(const int32_t *act, int64_t s, int32_t *pos, cudaStream_t st) {
+    if (s <= 0) return PMMF_OK;
+    k_set_pos<<<grid_for(s, 256), 256, 0, st>>>(act, s, pos);
+    return launched("set_pos");
+}
+
+pmmf_status update_stage(const Csr &A, const int32_t *act, int64_t n, const int32_t *pos,
+                         const int32_t *cl, const int32_t *loc, const StageClusters &cls,
+                         int64_t cmax, const StageRotations &rot, const int32_t *elimflag,
+                         int64_t stage, double *hdiag, double *contrib, UpdateOut &out,
+                         unsigned *status, cudaStream_t st) {
+    (void)n;
+    const int64_t s = A.rows;
+    RowArgs a{};
+    a.act = act;
+    a.pos = pos;
+    a.cl = cl;
+    a.loc = loc;
+    a.coff = cls.coff.p;
+    a.members = cls.members.p;
+    a.roff = rot.roff.p;
+    a.lvl_off = rot.lvl_off.p;
+    a.nlev = rot.nlev.p;
+    a.lvlrot = rot.lvl.p;
+    a.cmax = cmax;
+    a.elimflag = elimflag;
+    a.stage = (int32_t)stage;
+    a.status = status;
+    a.contrib = contrib;
+    a.hdiag = hdiag;
+
+    // pass 1: V = A Q^T, scattered straight into the rows of W = V^T
+    DBuf<int64_t> wrp, wcur;
+    PMMF_TRY(wrp.zeros(s + 1, st));
+    a.rp = A.rowptr.p;
+    a.ci = A.col.p;
+    a.v = A.val.p;
+    a.rows = s;
+    a.wcnt = wrp.p;
+    PMMF_TRY(launch_rows<P1_COUNT>(a, A.nnz, 0, st));
+    PMMF_TRY(scan_i64(wrp.p, wrp.p, s, st));
+    int64_t wnnz = 0;
+    PMMF_CUDA_TRY(cudaMemcpyAsync(&wnnz, wrp.p + s, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+    PMMF_CUDA_TRY(cudaStreamSynchronize(st));
+    Csr W;
+    W.rows = s;
+    W.nnz = wnnz;
+    PMMF_TRY(W.col.alloc(wnnz, st));
+    PMMF_TRY(W.val.alloc(wnnz, st));
+    PMMF_TRY(wcur.alloc(s + 1, st));
+    PMMF_CUDA_TRY(cudaMemcpyAsync(wcur.p, wrp.p, sizeof(int64_t) * (size_t)(s + 1),
+                                  cudaMemcpyDeviceToDevice, st));
+    a.wcur = wcur.p;
+    a.wcol = W.col.p;
+    a.wval = W.val.p;
+    PMMF_TRY(launch_rows<P1_WRITE>(a, A.nnz, wnnz, st));
+    W.rowptr = std::move(wrp);
+
+    // survivors and their new rows
+    DBuf<int32_t> flag;
+    DBuf<int64_t> newrow;
+    PMMF_TRY(flag.alloc(s, st));
+    PMMF_TRY(newrow.alloc(s + 1, st));
+    k_survivors<<<grid_for(s, 256), 256, 0, st>>>(act, s, elimflag, (int32_t)stage, flag.p);
+    PMMF_TRY(launched("survivors"));
+    PMMF_TRY(scan_i32_to_i64(flag.p, newrow.p, s, st));
+    int64_t s2 = 0;
+    PMMF_CUDA_TRY(cudaMemcpyAsync(&s2, newrow.p + s, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+    PMMF_CUDA_TRY(cudaStreamSynchronize(st));
+
+    // pass 2: A_p = W Q^T with accounting and compaction
+    out.next.rows = s2;
+    PMMF_TRY(out.next.rowptr.zeros(s2 + 1, st));
+    DBuf<int64_t> maxlen;
+    PMMF_TRY(maxlen.zeros(1, st));
+    a.rp = W.rowptr.p;
+    a.ci = W.col.p;
+    a.v = W.val.p;
+    a.newrow = newrow.p;
+    a.ocnt = out.next.rowptr.p;
+    a.maxlen = maxlen.p;
+    PMMF_TRY(launch_rows<P2_COUNT>(a, wnnz, 0, st));
+    PMMF_TRY(scan_i64(out.next.rowptr.p, out.next.rowptr.p, s2, st));
+    int64_t hv[2] = {0, 0};
+    PMMF_CUDA_TRY(cudaMemcpyAsync(&hv[0], out.next.rowptr.p + s2, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+    PMMF_CUDA_TRY(cudaMemcpyAsync(&hv[1], maxlen.p, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+    PMMF_CUDA_TRY(cudaStreamSynchronize(st));
+    out.next.nnz = hv[0];
+    PMMF_TRY(out.next.col.alloc(hv[0], st));
+    PMMF_TRY(out.next.val.alloc(hv[0], st));
+    a.outcap = (int)(hv[1] > 0 ? hv[1] : 1);
+    a.orp = out.next.rowptr.p;
+    a.ocol = out.next.col.p;
+    a.oval = out.next.val.p;
+    PMMF_TRY(launch_rows<P2_WRITE>(a, wnnz, hv[0], st));
+
+    PMMF_TRY(out.act.alloc(s2, st));
+    k_compact_act<<<grid_for(s, 256), 256, 0, st>>>(act, s, flag.p, newrow.p, out.act.p);
+    return launched("compact_act");
+}
+
+pmmf_status extract_core(const Csr &A, const int32_t *pos, int64_t s, double *core, double *hdiag,
+                         const int32_t *act, cudaStream_t st) {
+    if (s <= 0) return PMMF_OK;
+    PMMF_CUDA_TRY(cudaMemsetAsync(core, 0, sizeof(double) * (size_t)(s * s), st));
+    k_core<<<grid_for(s * 32, 256), 256, 0, st>>>(A.rowptr.p, A.col.p, A.val.p, s, pos, act, core,
+                                                  hdiag);
+    return launched("core");
+}
+
+}  // namespace pmmf

@@ -1,0 +1,338 @@
+"""Thin Python binding of the pMMF C-ABI (``include/pmmf.h``).
+
+Argument marshalling only: every step of the factorization, the matrix-free
+apply and the preconditioned CG runs inside ``_lib/libpmmf.so``.  The functions
+``pmmf_factor``, ``pmmf_apply``, ``pmmf_solve_precond`` and ``pmmf_free`` keep
+the C names; ``Factorization`` wraps a handle for convenience.  Arrays are torch
+tensors (device data) or numpy arrays (host data).  Importing this module
+fails loudly when the compiled library is missing.
+"""
+
+from __future__ import annotations
+
+import ctypes as C
+import os
+from dataclasses import dataclass
+from typing import Optional
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_lib", "libpmmf.so")
+
+OK, ERR_INVALID_ARG, ERR_NOT_SYMMETRIC, ERR_NONFINITE, ERR_OOM, ERR_CUDA = 0, 1, 2, 3, 4, 5
+ERR_NOT_SPD, ERR_SINGULAR_CORE, ERR_NOT_CONVERGED, ERR_TIMEOUT, ERR_UNSUPPORTED = 6, 7, 8, 9, 10
+HOST, DEVICE = 0, 1
+CSR, DENSE = 0, 1
+OP_A, OP_A_INV, OP_U, OP_UT, OP_H, OP_H_INV = 0, 1, 2, 3, 4, 5
+
+STATUS_NAMES = {0: "OK", 1: "INVALID_ARG", 2: "NOT_SYMMETRIC", 3: "NONFINITE", 4: "OOM",
+                5: "CUDA", 6: "NOT_SPD", 7: "SINGULAR_CORE", 8: "NOT_CONVERGED", 9: "TIMEOUT",
+                10: "UNSUPPORTED"}
+
+
+class PmmfError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"pmmf status {status} ({STATUS_NAMES.get(status, '?')}): {message}")
+        self.status = status
+
+
+class Matrix(C.Structure):
+    _fields_ = [("n", C.c_int64), ("format", C.c_int), ("location", C.c_int),
+                ("rowptr", C.c_void_p), ("colidx", C.c_void_p), ("val", C.c_void_p),
+                ("ld", C.c_int64)]
+
+
+class Params(C.Structure):
+    _fields_ = [("k", C.c_int), ("eta", C.c_double), ("cluster_size", C.c_int),
+                ("core_size", C.c_int), ("seed", C.c_uint64), ("max_stages", C.c_int),
+                ("lloyd_iters", C.c_int), ("coords", C.c_void_p), ("coord_dim", C.c_int),
+                ("coords_location", C.c_int), ("record_stages", C.c_int)]
+
+
+class Info(C.Structure):
+    _fields_ = [("n", C.c_int64), ("stages", C.c_int32), ("core_size", C.c_int64),
+                ("rotations", C.c_int64), ("nnz_input", C.c_int64), ("norm_a", C.c_double),
+                ("error", C.c_double)]
+
+
+class StageInfo(C.Structure):
+    _fields_ = [("active", C.c_int64), ("clusters", C.c_int64), ("rotations", C.c_int64),
+                ("nnz_after", C.c_int64), ("max_levels", C.c_int32), ("contrib", C.c_double)]
+
+
+EXPORTS = ["pmmf_factor", "pmmf_apply", "pmmf_solve_precond", "pmmf_free", "pmmf_last_error",
+           "pmmf_profile_begin", "pmmf_profile_end",
+           "pmmf_get_info", "pmmf_get_stage_info", "pmmf_get_stage_clusters",
+           "pmmf_get_stage_rotations", "pmmf_get_h", "pmmf_get_stage_matrix",
+           "pmmf_launch_count"]
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load the compiled library (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise ImportError(f"pMMF CUDA library not built: {path} is missing "
+                          "(run paper_1507_04396_gb300.build.build())")
+    L = C.CDLL(path)
+    vp, i32, i64, f64 = C.c_void_p, C.c_int, C.c_int64, C.c_double
+    L.pmmf_factor.restype = i32
+    L.pmmf_factor.argtypes = [C.POINTER(Matrix), C.POINTER(Params), C.POINTER(vp), vp]
+    L.pmmf_apply.restype = i32
+    L.pmmf_apply.argtypes = [vp, i32, vp, vp, i64, i64, vp]
+    L.pmmf_solve_precond.restype = i32
+    L.pmmf_solve_precond.argtypes = [vp, C.POINTER(Matrix), vp, vp, i64, f64, i32, vp, vp, vp]
+    L.pmmf_free.restype = None
+    L.pmmf_free.argtypes = [vp]
+    L.pmmf_last_error.restype = C.c_char_p
+    L.pmmf_last_error.argtypes = []
+    L.pmmf_get_info.restype = i32
+    L.pmmf_get_info.argtypes = [vp, C.POINTER(Info)]
+    L.pmmf_get_stage_info.restype = i32
+    L.pmmf_get_stage_info.argtypes = [vp, i32, C.POINTER(StageInfo)]
+    L.pmmf_get_stage_clusters.restype = i32
+    L.pmmf_get_stage_clusters.argtypes = [vp, i32, vp, vp]
+    L.pmmf_get_stage_rotations.restype = i32
+    L.pmmf_get_stage_rotations.argtypes = [vp, i32, vp, vp, vp, vp, vp]
+    L.pmmf_get_h.restype = i32
+    L.pmmf_get_h.argtypes = [vp, vp, vp, vp]
+    L.pmmf_get_stage_matrix.restype = i32
+    L.pmmf_get_stage_matrix.argtypes = [vp, i32, vp, vp, vp, vp]
+    L.pmmf_launch_count.restype = C.c_uint64
+    L.pmmf_launch_count.argtypes = []
+    L.pmmf_profile_begin.restype = i32
+    L.pmmf_profile_begin.argtypes = [C.c_uint]
+    L.pmmf_profile_end.restype = i32
+    L.pmmf_profile_end.argtypes = [vp, vp, vp, vp]
+    _lib = L
+    return L
+
+
+FAMILIES = ["partition", "gram", "select", "rows", "apply", "other"]
+
+
+def pmmf_profile_begin(families) -> None:
+    """Start timing the named kernel families (see FAMILIES)."""
+    mask = 0
+    for f in families:
+        mask |= 1 << FAMILIES.index(f)
+    _check(load().pmmf_profile_begin(mask))
+
+
+def pmmf_profile_end() -> dict:
+    """Stop timing; per family: total ms, launches, algorithmic bytes and flops."""
+    ms = np.zeros(6)
+    la = np.zeros(6, dtype=np.int64)
+    by = np.zeros(6)
+    fl = np.zeros(6)
+    _check(load().pmmf_profile_end(ms.ctypes.data, la.ctypes.data, by.ctypes.data, fl.ctypes.data))
+    return {f: dict(ms=float(ms[i]), launches=int(la[i]), bytes=float(by[i]), flops=float(fl[i]))
+            for i, f in enumerate(FAMILIES)}
+
+
+def _check(st: int):
+    if st != OK:
+        raise PmmfError(st, load().pmmf_last_error().decode(errors="replace"))
+
+
+def _ptr(a) -> Optional[int]:
+    """Address of a torch tensor's or numpy array's data."""
+    if a is None:
+        return None
+    if hasattr(a, "data_ptr"):
+        return a.data_ptr()
+    return a.ctypes.data
+
+
+def _loc(a) -> int:
+    return DEVICE if hasattr(a, "is_cuda") and a.is_cuda else HOST
+
+
+def _stream(stream) -> Optional[int]:
+    if stream is None:
+        try:
+            import torch
+            if torch.cuda.is_available():
+                return torch.cuda.current_stream().cuda_stream
+        except Exception:
+            pass
+        return None
+    return stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+
+
+def make_matrix(a=None, *, n=None, rowptr=None, col=None, val=None, dense=None) -> tuple:
+    """Build a pmmf_matrix.  Returns (Matrix, keepalive)."""
+    keep = []
+    if a is not None and dense is None and hasattr(a, "rowptr"):
+        n, rowptr, col, val = a.n, a.rowptr, a.col, a.val
+    elif a is not None and dense is None:
+        dense = a
+    if dense is not None:
+        if not hasattr(dense, "data_ptr"):
+            dense = np.ascontiguousarray(dense, dtype=np.float64)
+        keep.append(dense)
+        m = Matrix(dense.shape[0], DENSE, _loc(dense), None, None, _ptr(dense), dense.shape[1])
+        return m, keep
+    if not hasattr(rowptr, "data_ptr"):
+        rowptr = np.ascontiguousarray(rowptr, dtype=np.int64)
+        col = np.ascontiguousarray(col, dtype=np.int32)
+        val = np.ascontiguousarray(val, dtype=np.float64)
+    keep += [rowptr, col, val]
+    m = Matrix(int(n), CSR, _loc(val), _ptr(rowptr), _ptr(col), _ptr(val), 0)
+    return m, keep
+
+
+# ---------------------------------------------------------------- C names
+
+def pmmf_factor(matrix: Matrix, params: Params, stream=None) -> int:
+    h = C.c_void_p()
+    _check(load().pmmf_factor(C.byref(matrix), C.byref(params), C.byref(h), _stream(stream)))
+    return h.value
+
+
+def pmmf_apply(handle: int, op: int, x, y, nrhs: int, ld: int, stream=None):
+    _check(load().pmmf_apply(handle, op, _ptr(x), _ptr(y), nrhs, ld, _stream(stream)))
+
+
+def pmmf_solve_precond(handle: int, matrix: Matrix, b, x, nrhs: int, rtol: float, maxit: int,
+                       stream=None):
+    iters = np.zeros(nrhs, dtype=np.int32)
+    relres = np.zeros(nrhs)
+    st = load().pmmf_solve_precond(handle, C.byref(matrix), _ptr(b), _ptr(x), nrhs, rtol, maxit,
+                                   iters.ctypes.data, relres.ctypes.data, _stream(stream))
+    return st, iters, relres
+
+
+def pmmf_free(handle: int):
+    if handle:
+        load().pmmf_free(handle)
+
+
+def pmmf_launch_count() -> int:
+    return int(load().pmmf_launch_count())
+
+
+# ---------------------------------------------------------------- convenience
+
+@dataclass
+class StageView:
+    active: int
+    clusters: int
+    rotations: int
+    nnz_after: int
+    max_levels: int
+    contrib: float
+
+
+class Factorization:
+    """Owns a pmmf_handle; frees it when garbage collected or on close()."""
+
+    def __init__(self, handle: int, k: int):
+        self.handle = handle
+        self.k = k
+
+    def close(self):
+        if self.handle:
+            pmmf_free(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def info(self) -> Info:
+        i = Info()
+        _check(load().pmmf_get_info(self.handle, C.byref(i)))
+        return i
+
+    @property
+    def error(self) -> float:
+        return self.info().error
+
+    def stage(self, p: int) -> StageView:
+        s = StageInfo()
+        _check(load().pmmf_get_stage_info(self.handle, p, C.byref(s)))
+        return StageView(s.active, s.clusters, s.rotations, s.nnz_after, s.max_levels, s.contrib)
+
+    def clusters(self, p: int):
+        s = self.stage(p)
+        off = np.zeros(s.clusters + 1, dtype=np.int64)
+        mem = np.zeros(s.active, dtype=np.int32)
+        _check(load().pmmf_get_stage_clusters(self.handle, p, off.ctypes.data, mem.ctypes.data))
+        return off, mem
+
+    def rotations(self, p: int):
+        s = self.stage(p)
+        nr, K = s.rotations, self.k
+        n1 = max(nr, 1)
+        cl = np.zeros(n1, dtype=np.int32)
+        kk = np.zeros(n1, dtype=np.int32)
+        idx = np.zeros((n1, K), dtype=np.int32)
+        O = np.zeros((n1, K * K))
+        el = np.zeros(n1, dtype=np.int32)
+        _check(load().pmmf_get_stage_rotations(self.handle, p, cl.ctypes.data, kk.ctypes.data,
+                                               idx.ctypes.data, O.ctypes.data, el.ctypes.data))
+        return cl[:nr], kk[:nr], idx[:nr], O[:nr], el[:nr]
+
+    def h(self):
+        i = self.info()
+        hd = np.zeros(i.n)
+        ci = np.zeros(i.core_size, dtype=np.int32)
+        core = np.zeros((i.core_size, i.core_size))
+        _check(load().pmmf_get_h(self.handle, hd.ctypes.data, ci.ctypes.data, core.ctypes.data))
+        return hd, ci, core
+
+    def stage_matrix(self, p: int):
+        nnz = C.c_int64()
+        _check(load().pmmf_get_stage_matrix(self.handle, p, None, None, None, C.byref(nnz)))
+        n = self.info().n
+        rp = np.zeros(n + 1, dtype=np.int64)
+        col = np.zeros(max(nnz.value, 1), dtype=np.int32)
+        val = np.zeros(max(nnz.value, 1))
+        _check(load().pmmf_get_stage_matrix(self.handle, p, rp.ctypes.data, col.ctypes.data,
+                                            val.ctypes.data, C.byref(nnz)))
+        return rp, col[:nnz.value], val[:nnz.value]
+
+    def apply(self, op: int, x, y=None, stream=None):
+        """y = op(x) for a CUDA float64 tensor x of shape (n,) or (n, nrhs)."""
+        import torch
+        assert x.is_cuda and x.dtype == torch.float64 and x.is_contiguous()
+        if y is None:
+            y = torch.empty_like(x)
+        nrhs = 1 if x.dim() == 1 else x.shape[1]
+        pmmf_apply(self.handle, op, x, y, nrhs, nrhs, stream)
+        return y
+
+    def solve(self, a, b, rtol=1e-8, maxit=1000, stream=None):
+        """Preconditioned CG for a x = b (b: CUDA float64 (n,) or (n, nrhs))."""
+        import torch
+        m, keep = make_matrix(a)
+        x = torch.empty_like(b)
+        nrhs = 1 if b.dim() == 1 else b.shape[1]
+        st, iters, relres = pmmf_solve_precond(self.handle, m, b, x, nrhs, rtol, maxit, stream)
+        return st, x, iters, relres
+
+
+def factor(a, *, k=2, eta=0.5, cluster_size=256, core_size=16, seed=0, max_stages=0,
+           lloyd_iters=10, coords="auto", record_stages=False, stream=None) -> Factorization:
+    """Factor a symmetric matrix (SymCSR-like object with numpy or torch arrays, or a
+    dense 2-D array/tensor).  coords='auto' uses ``a.coords`` when present."""
+    m, keep = make_matrix(a)
+    if isinstance(coords, str):
+        coords = getattr(a, "coords", None)
+    cp, cd, cl = None, 0, HOST
+    if coords is not None:
+        if not hasattr(coords, "data_ptr"):
+            coords = np.ascontiguousarray(coords, dtype=np.float64)
+        keep.append(coords)
+        cp, cd, cl = _ptr(coords), coords.shape[1], _loc(coords)
+    prm = Params(k, eta, cluster_size, core_size, seed, max_stages, lloyd_iters, cp, cd, cl,
+                 1 if record_stages else 0)
+    h = pmmf_factor(m, prm, stream)
+    return Factorization(h, k)

@@ -1,0 +1,64 @@
+"""The C-ABI library builds for sm_103a, loads, and exports every entry point
+that include/pmmf.h declares.  Runs without a GPU: only argument validation is
+exercised (it returns before any CUDA call)."""
+
+import ctypes as C
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    src = open(os.path.join(ROOT, "include", "pmmf.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(pmmf_[a-z_]+)\s*\(", src)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1507_04396_gb300 import build, pmmf
+    build.build()
+    return pmmf.load()
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for n in ("pmmf_factor", "pmmf_apply", "pmmf_solve_precond", "pmmf_free"):
+        assert n in names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    for name in declared_functions():
+        assert hasattr(lib, name), name
+
+
+def test_binding_lists_every_export():
+    from paper_1507_04396_gb300 import pmmf
+    assert sorted(pmmf.EXPORTS) == declared_functions()
+
+
+def test_invalid_parameters_rejected_without_gpu(lib):
+    from paper_1507_04396_gb300 import inputs as I
+    from paper_1507_04396_gb300 import pmmf
+    a = I.psd_dense(16, 4, seed=1)
+    m, keep = pmmf.make_matrix(a)
+    bad = [
+        pmmf.Params(1, 0.5, 16, 4, 0, 0, 10, None, 0, 0, 0),       # k < 2
+        pmmf.Params(2, 1.0, 16, 4, 0, 0, 10, None, 0, 0, 0),       # eta >= 1
+        pmmf.Params(2, 0.5, 1, 4, 0, 0, 10, None, 0, 0, 0),        # cluster < k
+        pmmf.Params(2, 0.5, 16, 0, 0, 0, 10, None, 0, 0, 0),       # core < 1
+        pmmf.Params(2, 0.5, 16, 17, 0, 0, 10, None, 0, 0, 0),      # core > n
+    ]
+    for prm in bad:
+        h = C.c_void_p()
+        st = lib.pmmf_factor(C.byref(m), C.byref(prm), C.byref(h), None)
+        assert st == pmmf.ERR_INVALID_ARG
+        assert h.value is None
+        assert lib.pmmf_last_error()
+    prm = pmmf.Params(3, 0.5, 16, 4, 0, 0, 10, None, 0, 0, 0)
+    h = C.c_void_p()
+    assert lib.pmmf_factor(C.byref(m), C.byref(prm), C.byref(h), None) == pmmf.ERR_UNSUPPORTED
+    lib.pmmf_free(None)   # NULL-safe

@@ -1,0 +1,182 @@
+"""CUDA path against the oracle, element by element, on identical seeded inputs.
+
+Bar (integer and index work bit-exact; floating point bit-exact wherever both
+sides run the same operation sequence):
+  - clusters, selected rotation tuples, eliminated coordinates: identical;
+  - rotation blocks (c, s), every stage's compacted A_p, H: identical bits;
+  - relative Frobenius error within 1e-10 (relative) of the oracle's (the
+    residual sums are accumulated in a different order);
+  - U x, U^T x, H x, A~ x: identical bits; A~^{-1} x within 1e-10 relative
+    (the core is inverted by Gauss-Jordan on the GPU, by Cholesky in the oracle).
+"""
+
+import numpy as np
+import pytest
+
+from helpers import assert_same_factorization, factor_both, gpu, gpu_lib
+from oracle import oracle as O
+from paper_1507_04396_gb300 import inputs as I
+
+pytestmark = gpu
+
+
+def test_dense_one_cluster_small_case():
+    """Dense PSD X X^T/64 + 0.1 I, n = 256, one cluster, core 16 (4 stages, 240 rotations)."""
+    a = I.psd_dense(256, 64, seed=0)
+    g, o = factor_both(a, k=2, eta=0.5, cluster_size=256, core_size=16, seed=0)
+    assert o.total_rotations() == 240 and len(o.stages) == 4
+    assert_same_factorization(g, o)
+
+
+@pytest.mark.parametrize("n,c,core", [(4096, 256, 64), (3000, 200, 100), (1500, 97, 31)])
+def test_knn_laplacian_clustered(n, c, core):
+    """kNN-graph Laplacian with k-means clusters, ragged cluster sizes."""
+    a = I.knn_laplacian(n, seed=1)
+    g, o = factor_both(a, k=2, eta=0.5, cluster_size=c, core_size=core, seed=3)
+    assert_same_factorization(g, o)
+
+
+@pytest.mark.parametrize("eta", [0.25, 0.7])
+def test_other_compression_ratios(eta):
+    a = I.knn_laplacian(2000, seed=2)
+    g, o = factor_both(a, k=2, eta=eta, cluster_size=128, core_size=40, seed=9)
+    assert_same_factorization(g, o)
+
+
+def test_poisson_3d_clusters():
+    a = I.poisson3d(12, seed=4)
+    g, o = factor_both(a, k=2, eta=0.5, cluster_size=64, core_size=50, seed=4)
+    assert_same_factorization(g, o)
+
+
+def test_ties_on_integer_grid_laplacian():
+    """Integer-valued grid Laplacian: many equal scores exercise the tie rules."""
+    a = I.poisson3d(8, sigma=0.0, seed=0)
+    g, o = factor_both(a, k=2, eta=0.5, cluster_size=64, core_size=16, seed=1)
+    assert_same_factorization(g, o)
+
+
+def test_edge_cases():
+    # n = 1: nothing to rotate, H = A
+    a = I.from_dense(np.array([[3.0]]))
+    g, o = factor_both(a, coords=None, k=2, eta=0.5, cluster_size=2, core_size=1, seed=0)
+    assert g.info().stages == 0
+    assert_same_factorization(g, o)
+    # n = 2, core 1: a single rotation
+    a = I.from_dense(np.array([[2.0, 0.7], [0.7, 1.0]]))
+    g, o = factor_both(a, coords=None, k=2, eta=0.5, cluster_size=2, core_size=1, seed=0)
+    assert_same_factorization(g, o)
+    # diagonal: every score 0, identity rotations, zero error
+    a = I.from_dense(np.diag(np.arange(1.0, 65.0)))
+    g, o = factor_both(a, coords=None, k=2, eta=0.5, cluster_size=64, core_size=4, seed=5)
+    assert_same_factorization(g, o)
+    assert g.info().error == 0.0
+    # stage limit and a core larger than half of n
+    a = I.knn_laplacian(800, seed=7)
+    g, o = factor_both(a, k=2, eta=0.5, cluster_size=100, core_size=10, seed=2, max_stages=2)
+    assert g.info().stages == 2
+    assert_same_factorization(g, o)
+    g, o = factor_both(a, k=2, eta=0.5, cluster_size=100, core_size=700, seed=2)
+    assert_same_factorization(g, o)
+    # clusters of one coordinate cannot rotate: falls back to one cluster
+    a = I.knn_laplacian(40, seed=8)
+    g, o = factor_both(a, k=2, eta=0.5, cluster_size=2, core_size=39, seed=2)
+    assert_same_factorization(g, o)
+
+
+def test_exact_block_sum():
+    a = I.block_pairs(128, k=2, seed=3)
+    g, o = factor_both(a, coords=None, k=2, eta=0.5, cluster_size=256, core_size=128, seed=1)
+    assert_same_factorization(g, o)
+    assert g.info().error <= 1e-14
+
+
+def test_input_forms_agree():
+    """Host CSR, device CSR and dense input give identical factorizations."""
+    import torch
+    pm = gpu_lib()
+    a = I.psd_dense(96, 20, seed=4)
+    kw = dict(k=2, eta=0.5, cluster_size=96, core_size=8, seed=2)
+    f1 = pm.factor(a, **kw)
+    dev = I.SymCSR(a.n, torch.from_numpy(a.rowptr).cuda(), torch.from_numpy(a.col).cuda(),
+                   torch.from_numpy(a.val).cuda())
+    f2 = pm.factor(dev, coords=None, **kw)
+    f3 = pm.factor(torch.from_numpy(a.to_dense()).cuda(), coords=None, **kw)
+    for f in (f2, f3):
+        for p in range(f1.info().stages):
+            assert np.array_equal(f1.rotations(p)[3], f.rotations(p)[3])
+        assert np.array_equal(f1.h()[0], f.h()[0])
+
+
+def test_apply_matches_oracle():
+    import torch
+    a = I.knn_laplacian(3000, seed=5)
+    g, o = factor_both(a, k=2, eta=0.5, cluster_size=150, core_size=60, seed=6)
+    x = np.random.default_rng(0).standard_normal((a.n, 3))
+    xd = torch.from_numpy(x).cuda()
+    for op in (O.OP_U, O.OP_UT, O.OP_H, O.OP_A):
+        y = g.apply(op, xd).cpu().numpy()
+        assert np.array_equal(y, o.apply(op, x)), op
+    for op in (O.OP_A_INV, O.OP_H_INV):
+        y = g.apply(op, xd).cpu().numpy()
+        want = o.apply(op, x)
+        assert np.abs(y - want).max() <= 1e-10 * np.abs(want).max(), op
+    # in place and a single vector
+    z = xd[:, 0].contiguous()
+    g.apply(O.OP_U, z, z)
+    assert np.array_equal(z.cpu().numpy(), o.apply(O.OP_U, x[:, :1])[:, 0])
+
+
+def test_pcg_matches_oracle():
+    import torch
+    a = I.poisson3d(14, seed=4)
+    g, o = factor_both(a, k=2, eta=0.5, cluster_size=64, core_size=64, seed=4)
+    b = np.random.default_rng(4).standard_normal((a.n, 4))
+    st, x, iters, rel = g.solve(a, torch.from_numpy(b).cuda(), rtol=1e-8, maxit=500)
+    ost, ox, oit, orel = o.pcg(a, b, 1e-8, 500)
+    assert st == 0 and ost == 0
+    assert (rel <= 1e-8 * 1.5).all()
+    assert (np.abs(iters - oit) <= 2).all(), (iters, oit)
+    np.testing.assert_allclose(x.cpu().numpy(), ox, rtol=0, atol=1e-6 * np.abs(ox).max())
+
+
+def test_rejects_bad_input():
+    pm = gpu_lib()
+    a = I.psd_dense(32, 8, seed=1)
+    val = a.val.copy()
+    val[3] += 1.0
+    with pytest.raises(pm.PmmfError) as e:
+        pm.factor(I.SymCSR(a.n, a.rowptr, a.col, val), k=2, eta=0.5, cluster_size=32, core_size=4)
+    assert e.value.status == pm.ERR_NOT_SYMMETRIC
+    val = a.val.copy()
+    val[0] = np.inf
+    with pytest.raises(pm.PmmfError) as e:
+        pm.factor(I.SymCSR(a.n, a.rowptr, a.col, val), k=2, eta=0.5, cluster_size=32, core_size=4)
+    assert e.value.status == pm.ERR_NONFINITE
+    with pytest.raises(pm.PmmfError) as e:
+        pm.factor(a, k=3, eta=0.5, cluster_size=32, core_size=4)
+    assert e.value.status == pm.ERR_UNSUPPORTED
+    with pytest.raises(pm.PmmfError) as e:
+        pm.factor(a, k=2, eta=1.5, cluster_size=32, core_size=4)
+    assert e.value.status == pm.ERR_INVALID_ARG
+
+
+def test_allocation_failure_is_clean():
+    """A failing device allocation returns OOM and leaves no handle behind."""
+    import subprocess
+    import sys
+    import os
+    code = (
+        "import sys; sys.path.insert(0, '.');"
+        "from paper_1507_04396_gb300 import inputs as I, pmmf as pm;"
+        "a = I.knn_laplacian(2000, seed=1);"
+        "import torch; torch.cuda.init();"
+        "\ntry:\n    pm.factor(a, k=2, eta=0.5, cluster_size=128, core_size=40)\n"
+        "    print('NOERR')\nexcept pm.PmmfError as e:\n    print('STATUS', e.status)\n")
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    gpu_lib()
+    for after in (0, 5, 40):
+        env = dict(os.environ, PMMF_FAIL_ALLOC_AFTER=str(after))
+        r = subprocess.run([sys.executable, "-c", code], cwd=root, env=env, capture_output=True,
+                           text=True, timeout=300)
+        assert "STATUS 4" in r.stdout, r.stdout + r.stderr
