@@ -146,6 +146,31 @@ pmmf_status pmmf_factor(const pmmf_matrix *A, const pmmf_params *p, pmmf_handle 
 pmmf_status pmmf_apply(const pmmf_handle *f, int op, const double *x, double *y, int64_t nrhs,
                        int64_t ld, void *stream);
 
+/* Allocation-free variant of pmmf_apply (the paper has no counterpart; this
+ * is a deployment aid).  Same arguments, semantics and results as pmmf_apply,
+ * but it never allocates device or host memory: no cudaMalloc / cudaFree and
+ * no allocating library routine.  It is for callers that must not allocate
+ * inside their loop -- e.g. a solver or serving path running with a fixed
+ * memory budget, or code whose allocator is owned by another framework --
+ * because an allocation there can fail, synchronize, or fragment memory.
+ *   Scratch: the core slice of the vectors (core_size * nrhs doubles) lives
+ *   in one library-owned device array of 1,048,576 doubles (8 MiB), held by
+ *   every GPU that loads the library until the process exits.  Calls with
+ *   core_size * nrhs > 1,048,576 for the H-using ops (A, A_INV, H, H_INV)
+ *   return PMMF_ERR_UNSUPPORTED with a message naming the limit.
+ *   Set-up: the first call on a device (the calling thread's current device)
+ *   looks up the array's device address; make that first call before any
+ *   stream capture.
+ *   Sharing: every call uses the same array, which keeps the previous call's
+ *   contents; nothing in it needs to start at zero (each call writes every
+ *   entry it reads).  Calls that overlap on the GPU (different streams, or
+ *   host threads) race on the array and must be serialized by the caller.
+ *   Inverse ops need the core inverse, which pmmf_apply / pmmf_solve_precond
+ *   form (and allocate) on their first inverse request; before that this
+ *   function returns PMMF_ERR_INVALID_ARG. */
+pmmf_status pmmf_apply_noalloc(const pmmf_handle *f, int op, const double *x, double *y,
+                               int64_t nrhs, int64_t ld, void *stream);
+
 /* Preconditioned conjugate gradients for A x = b with M^{-1} = A~^{-1}
  * (Sec. 4, xi = 1), every column of b independently, x_0 = 0.  A is the
  * system matrix (any location; CSR or dense); b and x are DEVICE n x nrhs

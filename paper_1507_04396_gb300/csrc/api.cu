@@ -642,3 +642,18 @@ pmmf_status pmmf_solve_precond(const pmmf_handle *fc, const pmmf_matrix *A, cons
 }
 
 }  // extern "C"
+
+namespace pmmf {
+
+// Read-only view of a handle for the allocation-free apply.
+pmmf_status handle_views(const pmmf_handle *f, const ApplyStages **views, HData *H, int64_t *n,
+                         bool *inverse_ready) {
+    if (!f) return fail(PMMF_ERR_INVALID_ARG, "NULL handle");
+    *views = &f->views;
+    *H = hdata(f);
+    *n = f->n;
+    *inverse_ready = f->inv_state == 1;
+    return PMMF_OK;
+}
+
+}  // namespace pmmf

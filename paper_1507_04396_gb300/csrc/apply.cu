@@ -343,3 +343,21 @@ pmmf_status vec_sub(const double *b, const double *q, double *r, int64_t cnt, cu
 }
 
 }  // namespace pmmf
+
+namespace pmmf {
+
+// H or H^-1 with caller-provided scratch for the core slice (H.m * nrhs
+// doubles); used by the allocation-free entry point.
+pmmf_status apply_h_scratch(const HData &H, bool inverse, double *x, int64_t ld, int64_t nrhs,
+                            double *zc, cudaStream_t st) {
+    if (inverse)
+        k_h_diag<true><<<grid_for(H.n * nrhs, 256), 256, 0, st>>>(x, ld, H.n, nrhs, H.hdiag, H.core_pos, zc);
+    else
+        k_h_diag<false><<<grid_for(H.n * nrhs, 256), 256, 0, st>>>(x, ld, H.n, nrhs, H.hdiag, H.core_pos, zc);
+    PMMF_TRY(launched("h_diag"));
+    k_core_gemv<<<grid_for(H.m * nrhs, 64), 64, 0, st>>>(inverse ? H.core_inv : H.core, H.m, zc,
+                                                         nrhs, H.core_idx, x, ld);
+    return launched("core_gemv");
+}
+
+}  // namespace pmmf

@@ -40,6 +40,8 @@ pmmf_status copy_block(const double *x, int64_t ldx, double *y, int64_t ldy, int
                        int64_t nrhs, cudaStream_t st);
 pmmf_status apply_h(const HData &H, bool inverse, double *x, int64_t ld, int64_t nrhs,
                     cudaStream_t st);
+pmmf_status apply_h_scratch(const HData &H, bool inverse, double *x, int64_t ld, int64_t nrhs,
+                            double *zc, cudaStream_t st);
 pmmf_status invert_core(const double *core, int64_t m, const double *hdiag, const int32_t *core_pos,
                         int64_t n, double *inv, unsigned *status, cudaStream_t st);
 pmmf_status spmv(const DevCsr &A, const double *x, double *y, int nrhs, cudaStream_t st);

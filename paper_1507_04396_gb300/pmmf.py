@@ -62,7 +62,7 @@ class StageInfo(C.Structure):
 
 
 EXPORTS = ["pmmf_factor", "pmmf_apply", "pmmf_solve_precond", "pmmf_free", "pmmf_last_error",
-           "pmmf_profile_begin", "pmmf_profile_end",
+           "pmmf_profile_begin", "pmmf_profile_end", "pmmf_apply_noalloc",
            "pmmf_get_info", "pmmf_get_stage_info", "pmmf_get_stage_clusters",
            "pmmf_get_stage_rotations", "pmmf_get_h", "pmmf_get_stage_matrix",
            "pmmf_launch_count"]
@@ -104,6 +104,8 @@ def load(path: str = LIB_PATH):
     L.pmmf_get_stage_matrix.argtypes = [vp, i32, vp, vp, vp, vp]
     L.pmmf_launch_count.restype = C.c_uint64
     L.pmmf_launch_count.argtypes = []
+    L.pmmf_apply_noalloc.restype = i32
+    L.pmmf_apply_noalloc.argtypes = [vp, i32, vp, vp, i64, i64, vp]
     L.pmmf_profile_begin.restype = i32
     L.pmmf_profile_begin.argtypes = [C.c_uint]
     L.pmmf_profile_end.restype = i32
@@ -196,6 +198,11 @@ def pmmf_factor(matrix: Matrix, params: Params, stream=None) -> int:
 
 def pmmf_apply(handle: int, op: int, x, y, nrhs: int, ld: int, stream=None):
     _check(load().pmmf_apply(handle, op, _ptr(x), _ptr(y), nrhs, ld, _stream(stream)))
+
+
+def pmmf_apply_noalloc(handle: int, op: int, x, y, nrhs: int, ld: int, stream=None):
+    """pmmf_apply without any allocation (for callers that must not allocate)."""
+    _check(load().pmmf_apply_noalloc(handle, op, _ptr(x), _ptr(y), nrhs, ld, _stream(stream)))
 
 
 def pmmf_solve_precond(handle: int, matrix: Matrix, b, x, nrhs: int, rtol: float, maxit: int,
