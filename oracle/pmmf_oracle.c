@@ -80,25 +80,33 @@ int64_t or_pick(uint64_t r, int64_t count) {
 
 /* R7, k = 2: the rotation (c, s) in the convention of R1 that zeroes the
  * off-diagonal of q [[a, b], [b, d]] q^T, with |theta| <= pi/4.  With
- * zeta = (d - a) / (2b), t = tan(theta) is the smaller root of
- * t^2 + 2 zeta t - 1 = 0. */
+ * h = d - a and g = 2b, t = tan(theta) is the smaller root of
+ * g t^2 + 2 h t - g = 0, t = sign(h) g / (|h| + sqrt(h^2 + g^2)) (sign(0) = +1).
+ * With q = |h| + sqrt(h^2 + g^2) and den = sqrt(q^2 + g^2):
+ *     c = q / den,   s = sign(h) g / den.
+ * h and g are first scaled by an exact power of two when they are huge or tiny,
+ * so that the squares neither overflow nor underflow (the angle is unchanged). */
 void or_jacobi2(double a, double b, double d, double *c, double *s) {
     if (b == 0.0) {
         *c = 1.0;
         *s = 0.0;
         return;
     }
-    double zeta = (d - a) / (2.0 * b);
-    double t;
-    if (fabs(zeta) > 1e150) {
-        t = 1.0 / (2.0 * zeta);
-    } else {
-        double r = sqrt(1.0 + zeta * zeta);
-        t = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + r);
+    double h = d - a;
+    double g = 2.0 * b;
+    double m = fabs(h) > fabs(g) ? fabs(h) : fabs(g);
+    if (m > 0x1p500) {
+        h = h * 0x1p-600;
+        g = g * 0x1p-600;
+    } else if (m < 0x1p-500) {
+        h = h * 0x1p600;
+        g = g * 0x1p600;
     }
-    double cc = 1.0 / sqrt(1.0 + t * t);
-    *c = cc;
-    *s = t * cc;
+    double r = sqrt(h * h + g * g);
+    double q = fabs(h) + r;
+    double den = sqrt(q * q + g * g);
+    *c = q / den;
+    *s = (h >= 0.0 ? g : -g) / den;
 }
 
 /* A k x k rotation block O (row-major, stride k) acting as x_T' = O x_T.

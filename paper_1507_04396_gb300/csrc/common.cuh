@@ -7,7 +7,7 @@
 #include <atomic>
 #include <string>
 
-#include "../../include/pmmf.h"
+#include "pmmf.h"
 
 namespace pmmf {
 
@@ -106,6 +106,11 @@ __device__ __forceinline__ void rot_pair_t(double c, double s, double a, double 
                                            double &nb) {
     na = __fma_rn(c, a, __dmul_rn(s, b));
     nb = __fma_rn(-s, a, __dmul_rn(c, b));
+}
+
+// x != 0.0 tested on the bits (integer pipe; FP64 compares are slow on GB300).
+__device__ __forceinline__ bool nonzero_bits(double x) {
+    return ((unsigned long long)__double_as_longlong(x) << 1) != 0ull;
 }
 
 __device__ __forceinline__ double warp_sum(double v) {

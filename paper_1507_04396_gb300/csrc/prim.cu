@@ -171,15 +171,14 @@ pmmf_status scan_i32_to_i64(const int32_t *in, int64_t *out, int64_t n, cudaStre
 
 namespace {
 
-constexpr int SORT_TILE = 8192;
 
 __global__ void k_sort_hist(const uint32_t *key, int64_t n, int64_t nbins, int64_t nblocks,
-                            int64_t *hist) {
+                            int64_t tile, int64_t *hist) {
     extern __shared__ int32_t sh[];
     for (int64_t b = threadIdx.x; b < nbins; b += blockDim.x) sh[b] = 0;
     __syncthreads();
-    int64_t base = (int64_t)blockIdx.x * SORT_TILE;
-    int64_t end = base + SORT_TILE < n ? base + SORT_TILE : n;
+    int64_t base = (int64_t)blockIdx.x * tile;
+    int64_t end = base + tile < n ? base + tile : n;
     for (int64_t i = base + threadIdx.x; i < end; i += blockDim.x) atomicAdd(&sh[key[i]], 1);
     __syncthreads();
     for (int64_t b = threadIdx.x; b < nbins; b += blockDim.x)
@@ -189,13 +188,13 @@ __global__ void k_sort_hist(const uint32_t *key, int64_t n, int64_t nbins, int64
 // One warp per tile walks the tile in order, 32 items at a time, so equal
 // keys keep their input order.
 __global__ void k_sort_scatter(const uint32_t *key, int64_t n, int64_t nbins, int64_t nblocks,
-                               const int64_t *offs, int32_t *perm) {
+                               int64_t tile, const int64_t *offs, int32_t *perm) {
     extern __shared__ int32_t cnt[];
     int lane = threadIdx.x;
     for (int64_t b = lane; b < nbins; b += 32) cnt[b] = 0;
     __syncwarp();
-    int64_t base = (int64_t)blockIdx.x * SORT_TILE;
-    int64_t end = base + SORT_TILE < n ? base + SORT_TILE : n;
+    int64_t base = (int64_t)blockIdx.x * tile;
+    int64_t end = base + tile < n ? base + tile : n;
     for (int64_t c = base; c < end; c += 32) {
         int64_t i = c + lane;
         bool ok = i < end;
@@ -248,7 +247,11 @@ pmmf_status stable_sort_by_key(const uint32_t *key, int64_t n, int64_t nbins, in
         set_error("stable_sort_by_key: too many bins");
         return PMMF_ERR_UNSUPPORTED;
     }
-    int64_t nblocks = (n + SORT_TILE - 1) / SORT_TILE;
+    // one warp walks each tile in order; tiles small enough to give the GPU
+    // many warps, large enough to keep the per-tile histograms under ~4M entries
+    int64_t tile = 512;
+    while (tile < n && nbins * ((n + tile - 1) / tile) > (int64_t(1) << 22)) tile *= 2;
+    int64_t nblocks = (n + tile - 1) / tile;
     DBuf<int64_t> hist;
     PMMF_TRY(hist.alloc(nbins * nblocks + 1, st));
     size_t sh = sizeof(int32_t) * (size_t)nbins;
@@ -256,10 +259,10 @@ pmmf_status stable_sort_by_key(const uint32_t *key, int64_t n, int64_t nbins, in
         PMMF_CUDA_TRY(cudaFuncSetAttribute(k_sort_hist, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh));
         PMMF_CUDA_TRY(cudaFuncSetAttribute(k_sort_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh));
     }
-    k_sort_hist<<<(unsigned)nblocks, 256, sh, st>>>(key, n, nbins, nblocks, hist.p);
+    k_sort_hist<<<(unsigned)nblocks, 256, sh, st>>>(key, n, nbins, nblocks, tile, hist.p);
     PMMF_TRY(launched("sort_hist"));
     PMMF_TRY(scan_i64(hist.p, hist.p, nbins * nblocks, st));
-    k_sort_scatter<<<(unsigned)nblocks, 32, sh, st>>>(key, n, nbins, nblocks, hist.p, perm);
+    k_sort_scatter<<<(unsigned)nblocks, 32, sh, st>>>(key, n, nbins, nblocks, tile, hist.p, perm);
     PMMF_TRY(launched("sort_scatter"));
     return PMMF_OK;
 }

@@ -13,6 +13,11 @@
 //   angle     smaller-angle Jacobi rotation of [[G_ii, G_ij], [G_ij, G_jj]].
 //   update    G <- q G q^T and M <- q M q^T, rows recomputed then mirrored.
 //   eliminate i if G_ii - M_ii^2 < G_jj - M_jj^2, else j (Alg. 2).
+//
+// On GB300 a dependent FP64 operation costs ~64 cycles and a divide or square
+// root ~600, so the per-step critical path is arranged around FP64 latency:
+// scores are compared through their (order-preserving) bit patterns, and the
+// angle takes two square roots and two independent divides.
 #include <vector>
 
 #include "common.cuh"
@@ -36,29 +41,44 @@ __device__ __forceinline__ uint64_t draw(uint64_t seed, uint64_t p, uint64_t u, 
     return mix1(h ^ t);
 }
 
-// Smaller-angle Jacobi rotation zeroing the off-diagonal of q [[a,b],[b,d]] q^T.
+// Smaller-angle Jacobi rotation zeroing the off-diagonal of q [[a,b],[b,d]] q^T:
+// h = d - a, g = 2b (scaled by an exact power of two when huge or tiny),
+// q = |h| + sqrt(h^2 + g^2), den = sqrt(q^2 + g^2), c = q/den, s = sign(h) g/den.
+// Comparisons, |.| and the sign test act on the bits (integer pipe): for finite
+// doubles the magnitude bits order like the magnitudes.
 __device__ void jacobi2(double a, double b, double d, double &c, double &s) {
-    if (b == 0.0) {
+    const unsigned long long ABS = 0x7fffffffffffffffull;
+    if ((__double_as_longlong(b) & ABS) == 0) {
         c = 1.0;
         s = 0.0;
         return;
     }
-    double zeta = __ddiv_rn(__dsub_rn(d, a), __dmul_rn(2.0, b));
-    double t;
-    if (fabs(zeta) > 1e150) {
-        t = __ddiv_rn(1.0, __dmul_rn(2.0, zeta));
-    } else {
-        double r = __dsqrt_rn(__dadd_rn(1.0, __dmul_rn(zeta, zeta)));
-        t = __ddiv_rn(zeta >= 0.0 ? 1.0 : -1.0, __dadd_rn(fabs(zeta), r));
+    double h = __dsub_rn(d, a);
+    double g = __dmul_rn(2.0, b);
+    const unsigned long long hm = __double_as_longlong(h) & ABS, gm = __double_as_longlong(g) & ABS;
+    const unsigned long long mm = hm > gm ? hm : gm;
+    if (mm > (unsigned long long)__double_as_longlong(0x1p500)) {
+        h = __dmul_rn(h, 0x1p-600);
+        g = __dmul_rn(g, 0x1p-600);
+    } else if (mm < (unsigned long long)__double_as_longlong(0x1p-500)) {
+        h = __dmul_rn(h, 0x1p600);
+        g = __dmul_rn(g, 0x1p600);
     }
-    c = __ddiv_rn(1.0, __dsqrt_rn(__dadd_rn(1.0, __dmul_rn(t, t))));
-    s = __dmul_rn(t, c);
+    const unsigned long long hb = __double_as_longlong(h);
+    const double habs = __longlong_as_double(hb & ABS);
+    const bool hnonneg = (hb >> 63) == 0 || (hb & ABS) == 0;   // h >= 0, -0 included
+    const double g2 = __dmul_rn(g, g);
+    const double r = __dsqrt_rn(__dadd_rn(__dmul_rn(h, h), g2));
+    const double q = __dadd_rn(habs, r);
+    const double den = __dsqrt_rn(__dadd_rn(__dmul_rn(q, q), g2));
+    c = __ddiv_rn(q, den);
+    s = __ddiv_rn(hnonneg ? g : -g, den);
 }
 
 // New 2x2 block of q X q^T for symmetric X with X_ii = a, X_ij = X_ji = b,
 // X_jj = d: row step R = q X_TT, then column step R q^T (upper half, mirrored).
-__device__ void rot_block(double c, double s, double a, double b, double d, double &na, double &nb,
-                          double &nd) {
+__device__ __forceinline__ void rot_block(double c, double s, double a, double b, double d,
+                                          double &na, double &nb, double &nd) {
     double rii, rij, rji, rjj;
     rot_pair(c, s, a, b, rii, rji);   // column i of X_TT
     rot_pair(c, s, b, d, rij, rjj);   // column j of X_TT
@@ -131,37 +151,140 @@ __global__ void k_gram(const int64_t *rp, const int32_t *ci, const double *v, co
 }
 
 constexpr int SEL_THREADS = 256;
+constexpr int SEL_WARPS = SEL_THREADS / 32;
 
-struct Best {
-    double sc;
+// Candidate of the partner search: the score's bit pattern (scores are
+// non-negative doubles, so their bits order like their values), the local
+// index, and the pivot row's G and M entries at that index.
+struct Cand {
+    unsigned long long key;
     int32_t idx;
+    double g, m;
 };
 
-__device__ __forceinline__ bool better(double s1, int32_t i1, double s2, int32_t i2) {
-    return s1 > s2 || (s1 == s2 && i1 < i2);
+__device__ __forceinline__ bool cand_better(unsigned long long k1, int32_t i1,
+                                            unsigned long long k2, int32_t i2) {
+    return k1 > k2 || (k1 == k2 && i1 < i2);
 }
 
-// i = position 'pos' among the set bits of mask[0..nw) (one thread).
-__device__ int select_bit(const uint32_t *mask, int nwords, int64_t pos) {
-    int64_t rem = pos;
+__device__ __forceinline__ void cand_merge(Cand &a, const Cand &b) {
+    if (cand_better(b.key, b.idx, a.key, a.idx)) a = b;
+}
+
+__device__ __forceinline__ Cand cand_make(double g, double m, double wy, int32_t y) {
+    const double ag = __longlong_as_double(__double_as_longlong(g) & 0x7fffffffffffffffll);   // |g|
+    return Cand{(unsigned long long)__double_as_longlong(__dmul_rn(ag, wy)), y, g, m};
+}
+
+// True when x is +0 or -0, tested on the bits (integer pipe, not FP64).
+__device__ __forceinline__ bool is_zero(double x) {
+    return ((unsigned long long)__double_as_longlong(x) << 1) == 0ull;
+}
+
+// Same candidate as cand_make; a zero entry scores +0 (key 0) without an FP64
+// multiply (|+-0| * w = +0 for the finite, non-negative w).
+__device__ __forceinline__ Cand cand_make_sparse(double g, double m, double wy, int32_t y) {
+    return is_zero(g) ? Cand{0ull, y, g, m} : cand_make(g, m, wy, y);
+}
+
+__device__ __forceinline__ Cand cand_none() { return Cand{0ull, 0x7fffffff, 0.0, 0.0}; }
+
+__device__ __forceinline__ Cand warp_argmax(Cand c) {
+    for (int o = 16; o > 0; o >>= 1) {
+        Cand x;
+        x.key = __shfl_xor_sync(0xffffffffu, c.key, o);
+        x.idx = __shfl_xor_sync(0xffffffffu, c.idx, o);
+        x.g = __shfl_xor_sync(0xffffffffu, c.g, o);
+        x.m = __shfl_xor_sync(0xffffffffu, c.m, o);
+        cand_merge(c, x);
+    }
+    return c;
+}
+
+// Warp argmax that moves only (key, index) between lanes; the lane that holds
+// the winner writes the full candidate to *out.
+__device__ __forceinline__ void warp_argmax_to(const Cand &mine, Cand *out) {
+    unsigned long long k = mine.key;
+    int32_t id = mine.idx;
+    for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long ok = __shfl_xor_sync(0xffffffffu, k, o);
+        const int32_t oi = __shfl_xor_sync(0xffffffffu, id, o);
+        if (cand_better(ok, oi, k, id)) {
+            k = ok;
+            id = oi;
+        }
+    }
+    const unsigned own = __ballot_sync(0xffffffffu, mine.idx == id && mine.key == k);
+    if (own == 0) {
+        if ((threadIdx.x & 31) == 0) *out = cand_none();
+    } else if ((threadIdx.x & 31) == __ffs(own) - 1) {
+        *out = mine;
+    }
+}
+
+__device__ __forceinline__ bool is_active(const uint32_t *mask, int y) {
+    return (mask[y >> 5] >> (y & 31)) & 1u;
+}
+
+// Position 'pos' among the set bits of mask, treating bit 'skip' as clear
+// (one thread): word scan, then a popcount bisection inside the word.
+__device__ int select_bit(const uint32_t *mask, int nwords, int64_t pos, int skip) {
+    int rem = (int)pos;
     for (int wi = 0; wi < nwords; ++wi) {
         uint32_t m = mask[wi];
-        int pc = __popc(m);
+        if (skip >= 0 && (skip >> 5) == wi) m &= ~(1u << (skip & 31));
+        const int pc = __popc(m);
         if (rem < pc) {
-            for (int b = 0; b < 32; ++b) {
-                if (m & (1u << b)) {
-                    if (rem == 0) return wi * 32 + b;
-                    --rem;
+            int base = 0;
+            for (int width = 16; width >= 1; width >>= 1) {
+                const int lc = __popc((m >> base) & ((1u << width) - 1u));
+                if (rem >= lc) {
+                    rem -= lc;
+                    base += width;
                 }
             }
+            return wi * 32 + base;
         }
         rem -= pc;
     }
     return -1;
 }
 
-// One CTA per cluster.  Shared memory: G and M diagonals, w, the active mask,
-// per-coordinate dependency levels and level counters.
+// Group a cluster's rotations by dependency level (rotations of one level
+// touch disjoint coordinates, so any order inside a level gives the same
+// bits) and flag the eliminated coordinates.
+__device__ void finish_cluster(int64_t u, int64_t r0, int e, int nl, const int32_t *members,
+                               int64_t base, const RotRec *rec, int32_t *lcnt, Rot2 *lvlrot,
+                               int32_t *lvl_off, int32_t *nlev, int32_t *elimflag, int64_t stage) {
+    const int tid = threadIdx.x;
+    for (int t = tid; t < e; t += blockDim.x) {
+        const RotRec rr = rec[r0 + t];
+        atomicAdd(&lcnt[rr.lvl], 1);
+        elimflag[members[base + rr.le]] = (int32_t)stage;
+    }
+    __syncthreads();
+    if (tid == 0) {
+        int acc = 0;
+        for (int L = 1; L <= nl; ++L) {
+            const int cnt = lcnt[L];
+            lcnt[L] = acc;
+            lvl_off[r0 + u + L - 1] = (int32_t)(r0 + acc);
+            acc += cnt;
+        }
+        lvl_off[r0 + u + nl] = (int32_t)(r0 + acc);
+        nlev[u] = nl;
+    }
+    __syncthreads();
+    for (int t = tid; t < e; t += blockDim.x) {
+        const RotRec rr = rec[r0 + t];
+        const int slot = atomicAdd(&lcnt[rr.lvl], 1);
+        lvlrot[r0 + slot] = Rot2{rr.li, rr.lj, rr.c, rr.s};
+    }
+}
+
+// Generic search (any cluster size; used above 8 * SEL_THREADS coordinates).
+// Shared memory: G and M diagonals, w, the active mask, per-coordinate
+// dependency levels and level counters.
 __global__ void __launch_bounds__(SEL_THREADS)
 k_select(const int64_t *coff, const int32_t *members, const int64_t *goff, double *Gall,
          double *Mall, const int64_t *roff, uint64_t seed, int64_t stage, RotRec *rec, Rot2 *lvlrot,
@@ -181,7 +304,7 @@ k_select(const int64_t *coff, const int32_t *members, const int64_t *goff, doubl
     uint32_t *mask = (uint32_t *)(w + c);
     int32_t *lvl = (int32_t *)(mask + nwords);
     int32_t *lcnt = lvl + c;          // e + 2 counters
-    __shared__ Best wbest[SEL_THREADS / 32];
+    __shared__ Cand wbest[SEL_WARPS];
     __shared__ int s_i, s_j, s_maxlev;
     __shared__ double s_c, s_s;
 
@@ -201,34 +324,26 @@ k_select(const int64_t *coff, const int32_t *members, const int64_t *goff, doubl
     __syncthreads();
     if (tid == 0) {
         s_maxlev = 0;
-        if (e > 0) s_i = select_bit(mask, nwords, (int64_t)__umul64hi(draw(seed, stage, u, 0), (uint64_t)c));
+        if (e > 0) s_i = select_bit(mask, nwords, (int64_t)__umul64hi(draw(seed, stage, u, 0), (uint64_t)c), -1);
     }
     __syncthreads();
 
     for (int t = 0; t < e; ++t) {
-        // partner search over the active coordinates
         const int i = s_i < 0 ? 0 : s_i;
         const double *Gi = G + (int64_t)i * c;
-        double bs = -1.0;
-        int32_t bi = 0x7fffffff;
+        Cand best = cand_none();
         for (int y = tid; y < c; y += SEL_THREADS) {
-            if (y == i || !(mask[y >> 5] & (1u << (y & 31)))) continue;
-            double sc = __dmul_rn(fabs(Gi[y]), w[y]);
-            if (better(sc, y, bs, bi)) { bs = sc; bi = y; }
+            if (y == i || !is_active(mask, y)) continue;
+            cand_merge(best, cand_make(Gi[y], 0.0, w[y], y));
         }
-        for (int o = 16; o > 0; o >>= 1) {
-            double os = __shfl_xor_sync(0xffffffffu, bs, o);
-            int32_t oi = __shfl_xor_sync(0xffffffffu, bi, o);
-            if (better(os, oi, bs, bi)) { bs = os; bi = oi; }
-        }
-        if (lane == 0) wbest[wid] = Best{bs, bi};
+        best = warp_argmax(best);
+        if (lane == 0) wbest[wid] = best;
         __syncthreads();
         if (tid == 0) {
-            for (int q = 1; q < SEL_THREADS / 32; ++q)
-                if (better(wbest[q].sc, wbest[q].idx, bs, bi)) { bs = wbest[q].sc; bi = wbest[q].idx; }
+            for (int q = 1; q < SEL_WARPS; ++q) cand_merge(best, wbest[q]);
             // at least two coordinates are active at every step (e_u <= c_u - 1);
             // the clamp only keeps a corrupted state from indexing out of bounds
-            const int j = (bi >= 0 && bi < c && bi != i) ? bi : (i == 0 ? 1 : 0);
+            const int j = (best.idx >= 0 && best.idx < c && best.idx != i) ? best.idx : (i == 0 ? 1 : 0);
             double cc, ss;
             const double gij = G[(int64_t)i * c + j];
             jacobi2(gd[i], gij, gd[j], cc, ss);
@@ -258,26 +373,25 @@ k_select(const int64_t *coff, const int32_t *members, const int64_t *goff, doubl
             lvl[j] = L;
             s_maxlev = max(s_maxlev, L);
             rec[r0 + t] = RotRec{i, j, le, L, cc, ss};
-            elimflag[members[base + le]] = (int32_t)stage;
             mask[le >> 5] &= ~(1u << (le & 31));
             s_j = j;
             s_c = cc;
             s_s = ss;
             if (t + 1 < e)
                 s_i = select_bit(mask, nwords,
-                                 (int64_t)__umul64hi(draw(seed, stage, u, t + 1), (uint64_t)(c - t - 1)));
+                                 (int64_t)__umul64hi(draw(seed, stage, u, t + 1), (uint64_t)(c - t - 1)), -1);
         }
         __syncthreads();
         // rows/columns i and j of G and M for every other active coordinate
         {
             const int j = s_j;
             const double cc = s_c, ss = s_s;
+            double *Gw = G + (int64_t)i * c;
             double *Gj = G + (int64_t)j * c;
             double *Mi = M + (int64_t)i * c;
             double *Mj = M + (int64_t)j * c;
-            double *Gw = G + (int64_t)i * c;
             for (int y = tid; y < c; y += SEL_THREADS) {
-                if (y == i || y == j || !(mask[y >> 5] & (1u << (y & 31)))) continue;
+                if (y == i || y == j || !is_active(mask, y)) continue;
                 double gi = Gw[y], gj = Gj[y];
                 if (gi != 0.0 || gj != 0.0) {
                     double ni, nj;
@@ -300,29 +414,378 @@ k_select(const int64_t *coff, const int32_t *members, const int64_t *goff, doubl
         }
         __syncthreads();
     }
+    finish_cluster(u, r0, e, s_maxlev, members, base, rec, lcnt, lvlrot, lvl_off, nlev, elimflag, stage);
+}
 
-    // group the rotations by dependency level (rotations of one level touch
-    // disjoint coordinates, so any order inside a level gives the same bits)
-    const int nl = s_maxlev;
-    for (int t = tid; t < e; t += SEL_THREADS) atomicAdd(&lcnt[rec[r0 + t].lvl], 1);
+// Restructured search for clusters of up to KPT * SEL_THREADS coordinates
+// (thread t owns columns t, t + SEL_THREADS, ...).  Per step t with pivot i
+// and partner j:
+//   P1  thread 0: angle, 2x2 blocks of G and M, elimination, level, record.
+//       Warp 1: the two rows that can be the pivot of step t + 2, for both
+//       possible eliminations.  Every thread: prefetch its columns of rows i
+//       and j and of the two rows a1, a2 that can be the pivot of step t + 1.
+//   P2  every thread rotates its columns of rows i and j (and the mirrored
+//       columns) and scores them for the next pivot; warp argmax.
+// Two barriers per step.  The arithmetic, and so every bit, is k_select's.
+// An entry of the per-step FP64 work list: a column y, what it needs, and the
+// values its owner thread prefetched.
+enum : int { W_G = 1, W_M = 2, W_SCORE = 4 };
+struct Work {
+    int32_t y, flags;
+    double gi, gj, mi, mj, g1, m1, g2, m2;
+};
+
+// Warps of the restructured search: warps 0..3 (one per SM sub-partition,
+// each with its own FP64 unit) share the step's serial FP64 work; warps
+// 4..SEL_WARPS-1 own the columns.
+constexpr int FP_WARPS = 4;
+constexpr int NCT = SEL_THREADS - 32 * FP_WARPS;
+
+// Barrier among the FP64 warps only (named barrier 1).
+__device__ __forceinline__ void fp_sync() { asm volatile("bar.sync 1, %0;" ::"n"(32 * FP_WARPS)); }
+
+// Best of the per-warp candidates, computed by every warp in parallel.
+__device__ __forceinline__ Cand block_best(const Cand *wb) {
+    const int lane = threadIdx.x & 31;
+    const Cand mine = lane < SEL_WARPS ? wb[lane] : cand_none();
+    unsigned long long k = mine.key;
+    int32_t id = mine.idx;
+    for (int o = 4; o > 0; o >>= 1) {
+        const unsigned long long ok = __shfl_xor_sync(0xffffffffu, k, o);
+        const int32_t oi = __shfl_xor_sync(0xffffffffu, id, o);
+        if (cand_better(ok, oi, k, id)) {
+            k = ok;
+            id = oi;
+        }
+    }
+    k = __shfl_sync(0xffffffffu, k, 0);
+    id = __shfl_sync(0xffffffffu, id, 0);
+    const unsigned own = __ballot_sync(0xffffffffu, lane < SEL_WARPS && mine.idx == id && mine.key == k);
+    const int src = own ? __ffs(own) - 1 : 0;
+    Cand r;
+    r.key = k;
+    r.idx = id;
+    r.g = __shfl_sync(0xffffffffu, mine.g, src);
+    r.m = __shfl_sync(0xffffffffu, mine.m, src);
+    return r;
+}
+
+// Restructured search for clusters of up to KPT * NCT coordinates (column
+// thread t owns columns t, t + NCT, ...).  Per step t with pivot i, partner j:
+//   P1   FP64 warps: the angle (prefix computed by all four, then c and s by
+//        two), the four new diagonal entries of the 2x2 blocks (one each), the
+//        new weights of i and j and the elimination; bookkeeping.  Column
+//        threads: load their columns of rows i, j and of the two rows a1, a2
+//        that can be the pivot of step t + 1, classify them and list those
+//        that may need FP64 work.
+//   P2   column threads: FP64 work on the listed columns (the survivor's row
+//        and column; the eliminated coordinate's are never read again), zero
+//        and nonzero candidates for the next pivot; warp argmax.
+// Two block barriers per step.  The arithmetic, and so every bit, is k_select's.
+template <int KPT>
+__global__ void __launch_bounds__(SEL_THREADS)
+k_select_fast(const int64_t *coff, const int32_t *members, const int64_t *goff, double *Gall,
+              double *Mall, const int64_t *roff, uint64_t seed, int64_t stage, RotRec *rec,
+              Rot2 *lvlrot, int32_t *lvl_off, int32_t *nlev, int32_t *elimflag) {
+    extern __shared__ double sh[];
+    const int64_t u = blockIdx.x;
+    const int64_t base = coff[u];
+    const int c = (int)(coff[u + 1] - base);
+    const int64_t r0 = roff[u];
+    const int e = (int)(roff[u + 1] - r0);
+    double *G = Gall + goff[u];
+    double *M = Mall + goff[u];
+    double *gd = sh;
+    double *md = gd + c;
+    double *w = md + c;
+    uint64_t *draws = (uint64_t *)(w + c);
+    const int nwords = (c + 31) / 32;
+    uint32_t *mask = (uint32_t *)(draws + e + 1);
+    int32_t *lvl = (int32_t *)(mask + nwords);
+    int32_t *lcnt = lvl + c;          // e + 2 counters
+    // c entries after the counters, 16-byte aligned (the launch adds the slack)
+    Work *work = (Work *)(((uintptr_t)(lcnt + e + 2) + 15) & ~(uintptr_t)15);
+    __shared__ Cand wbest[SEL_WARPS];
+    __shared__ int s_le, s_maxlev, s_a1, s_a2;
+    __shared__ int s_nwork[2];                  // by step parity
+    __shared__ int s_nb[2][4];                  // by step parity: [skip i: p, p+1, skip j: p, p+1]
+    __shared__ double s_c, s_s;
+    __shared__ double s_x[FP_WARPS];            // exchange among the FP64 warps
+    __shared__ double s_wn[2][2];               // new weights of i, j by step parity
+    __shared__ double s_survg[2], s_survm[2];   // by step parity
+
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    const int ct = tid - 32 * FP_WARPS;         // column thread index (>= 0 in column warps)
+    for (int a = tid; a < c; a += SEL_THREADS) {
+        const double g = G[(int64_t)a * c + a];
+        gd[a] = g;
+        md[a] = M[(int64_t)a * c + a];
+        w[a] = g > 0.0 ? __ddiv_rn(1.0, __dsqrt_rn(g)) : 0.0;
+        lvl[a] = 0;
+    }
+    for (int wi = tid; wi < nwords; wi += SEL_THREADS) {
+        const int rem = c - wi * 32;
+        mask[wi] = rem >= 32 ? 0xffffffffu : ((1u << rem) - 1u);
+    }
+    for (int t = tid; t < e; t += SEL_THREADS) draws[t] = draw(seed, stage, u, t);
+    for (int q = tid; q < e + 2; q += SEL_THREADS) lcnt[q] = 0;
     __syncthreads();
     if (tid == 0) {
-        int acc = 0;
-        for (int L = 1; L <= nl; ++L) {
-            int cnt = lcnt[L];
-            lcnt[L] = acc;
-            lvl_off[r0 + u + L - 1] = (int32_t)(r0 + acc);
-            acc += cnt;
+        s_maxlev = 0;
+        s_a1 = s_a2 = -1;
+        s_le = -1;
+        s_nwork[0] = s_nwork[1] = 0;
+        if (e > 1) {
+            const int64_t p1 = (int64_t)__umul64hi(draws[1], (uint64_t)(c - 1));
+            s_a1 = select_bit(mask, nwords, p1, -1);
+            s_a2 = select_bit(mask, nwords, p1 + 1, -1);
         }
-        lvl_off[r0 + u + nl] = (int32_t)(r0 + acc);
-        nlev[u] = nl;
     }
     __syncthreads();
-    for (int t = tid; t < e; t += SEL_THREADS) {
-        RotRec rr = rec[r0 + t];
-        int slot = atomicAdd(&lcnt[rr.lvl], 1);
-        lvlrot[r0 + slot] = Rot2{rr.li, rr.lj, rr.c, rr.s};
+    if (e > 0) {
+        int i = select_bit(mask, nwords, (int64_t)__umul64hi(draws[0], (uint64_t)c), -1);
+        // partner search for the first pivot
+        Cand best = cand_none();
+        if (ct >= 0)
+            for (int y = ct; y < c; y += NCT) {
+                if (y == i || !is_active(mask, y)) continue;
+                cand_merge(best, cand_make_sparse(G[(int64_t)i * c + y], M[(int64_t)i * c + y], w[y], y));
+            }
+        warp_argmax_to(best, &wbest[wid]);
+        __syncthreads();
+        best = block_best(wbest);
+        int j = best.idx;
+        double gij = best.g, mij = best.m;
+        int a1 = s_a1, a2 = s_a2;
+
+        for (int t = 0; t < e; ++t) {
+            const bool more = t + 1 < e;
+            const int par = t & 1;
+            if (i < 0 || i >= c) i = 0;                          // never taken; keeps
+            if (j < 0 || j >= c || j == i) j = i == 0 ? 1 : 0;   // indices in range
+            int zy[KPT];                                         // zero-score columns
+#pragma unroll
+            for (int k = 0; k < KPT; ++k) zy[k] = -1;
+            if (ct >= 0) {
+                // ---- P1, column threads: the loaded values are consumed here,
+                // so the loads complete under the FP64 warps' chain
+                double gi[KPT], gj[KPT], mi[KPT], mj[KPT], g1[KPT], m1[KPT], g2[KPT], m2[KPT];
+                unsigned bal[KPT];
+                int fl[KPT];
+                int total = 0;
+#pragma unroll
+                for (int k = 0; k < KPT; ++k) {
+                    const int y = ct + k * NCT;
+                    gi[k] = gj[k] = mi[k] = mj[k] = g1[k] = m1[k] = g2[k] = m2[k] = 0.0;
+                    const bool live = y < c && y != i && y != j && is_active(mask, y);
+                    if (live) {
+                        gi[k] = G[(int64_t)i * c + y];
+                        gj[k] = G[(int64_t)j * c + y];
+                        mi[k] = M[(int64_t)i * c + y];
+                        mj[k] = M[(int64_t)j * c + y];
+                        if (more && a1 >= 0 && a1 != i && a1 != j) {
+                            g1[k] = G[(int64_t)a1 * c + y];
+                            m1[k] = M[(int64_t)a1 * c + y];
+                        }
+                        if (more && a2 >= 0 && a2 != i && a2 != j) {
+                            g2[k] = G[(int64_t)a2 * c + y];
+                            m2[k] = M[(int64_t)a2 * c + y];
+                        }
+                    }
+                    int f = 0;
+                    if (live) {
+                        if (!(is_zero(gi[k]) && is_zero(gj[k]))) f |= W_G;
+                        if (!(is_zero(mi[k]) && is_zero(mj[k]))) f |= W_M;
+                        if (!is_zero(g1[k]) || !is_zero(g2[k])) f |= W_SCORE;
+                    }
+                    fl[k] = f;
+                    zy[k] = (live && f == 0) ? y : -1;
+                    bal[k] = __ballot_sync(0xffffffffu, f != 0);
+                    total += __popc(bal[k]);
+                }
+                int wbase = 0;
+                if (lane == 0 && total) wbase = atomicAdd(&s_nwork[par], total);
+                wbase = __shfl_sync(0xffffffffu, wbase, 0);
+#pragma unroll
+                for (int k = 0; k < KPT; ++k) {
+                    if (fl[k]) {
+                        Work &it = work[wbase + __popc(bal[k] & ((1u << lane) - 1u))];
+                        it.y = ct + k * NCT;
+                        it.flags = fl[k];
+                        it.gi = gi[k];
+                        it.gj = gj[k];
+                        it.mi = mi[k];
+                        it.mj = mj[k];
+                        it.g1 = g1[k];
+                        it.m1 = m1[k];
+                        it.g2 = g2[k];
+                        it.m2 = m2[k];
+                    }
+                    wbase += __popc(bal[k]);
+                }
+            } else {
+                // ---- P1, FP64 warps (all lanes of a warp compute the same
+                // values; an FP64 instruction costs the same for one lane or 32)
+                const double a = gd[i], d = gd[j], ma0 = md[i], md0 = md[j];
+                double cc, ss;
+                const unsigned long long ABS = 0x7fffffffffffffffull;
+                if ((__double_as_longlong(gij) & ABS) == 0) {
+                    cc = 1.0;
+                    ss = 0.0;
+                } else {
+                    // angle prefix (jacobi2), computed by every FP64 warp
+                    double h = __dsub_rn(d, a);
+                    double g = __dmul_rn(2.0, gij);
+                    const unsigned long long hm = __double_as_longlong(h) & ABS, gm = __double_as_longlong(g) & ABS;
+                    const unsigned long long mm = hm > gm ? hm : gm;
+                    if (mm > (unsigned long long)__double_as_longlong(0x1p500)) {
+                        h = __dmul_rn(h, 0x1p-600);
+                        g = __dmul_rn(g, 0x1p-600);
+                    } else if (mm < (unsigned long long)__double_as_longlong(0x1p-500)) {
+                        h = __dmul_rn(h, 0x1p600);
+                        g = __dmul_rn(g, 0x1p600);
+                    }
+                    const unsigned long long hb = __double_as_longlong(h);
+                    const double habs = __longlong_as_double(hb & ABS);
+                    const bool hnonneg = (hb >> 63) == 0 || (hb & ABS) == 0;
+                    const double g2v = __dmul_rn(g, g);
+                    const double r = __dsqrt_rn(__dadd_rn(__dmul_rn(h, h), g2v));
+                    const double q = __dadd_rn(habs, r);
+                    const double den = __dsqrt_rn(__dadd_rn(__dmul_rn(q, q), g2v));
+                    // c by warp 0, s by warp 1
+                    if (wid == 0) s_x[0] = __ddiv_rn(q, den);
+                    else if (wid == 1) s_x[1] = __ddiv_rn(hnonneg ? g : -g, den);
+                    fp_sync();
+                    cc = s_x[0];
+                    ss = s_x[1];
+                    fp_sync();
+                }
+                // new diagonal entries of the 2x2 blocks (rot_block's na, nd):
+                // G_ii by warp 0, G_jj by warp 1, M_ii by warp 2, M_jj by warp 3
+                {
+                    const double xa = wid < 2 ? a : ma0;
+                    const double xb = wid < 2 ? gij : mij;
+                    const double xd = wid < 2 ? d : md0;
+                    double v;
+                    if ((wid & 1) == 0) {
+                        const double rii = __fma_rn(cc, xa, -__dmul_rn(ss, xb));
+                        const double rij = __fma_rn(cc, xb, -__dmul_rn(ss, xd));
+                        v = __fma_rn(rii, cc, __dmul_rn(rij, -ss));
+                    } else {
+                        const double rji = __fma_rn(ss, xa, __dmul_rn(cc, xb));
+                        const double rjj = __fma_rn(ss, xb, __dmul_rn(cc, xd));
+                        v = __fma_rn(rji, ss, __dmul_rn(rjj, cc));
+                    }
+                    s_x[wid] = v;
+                }
+                fp_sync();
+                const double na = s_x[0], nd = s_x[1], ma = s_x[2], md2 = s_x[3];
+                if (wid == 2 && lane == 0) {
+                    const double di = __dsub_rn(na, __dmul_rn(ma, ma));
+                    const double dj = __dsub_rn(nd, __dmul_rn(md2, md2));
+                    const int le = di < dj ? i : j;
+                    gd[i] = na;
+                    gd[j] = nd;
+                    md[i] = ma;
+                    md[j] = md2;
+                    const int L = 1 + max(lvl[i], lvl[j]);
+                    lvl[i] = L;
+                    lvl[j] = L;
+                    s_maxlev = max(s_maxlev, L);
+                    mask[le >> 5] &= ~(1u << (le & 31));
+                    s_c = cc;
+                    s_s = ss;
+                    s_le = le;
+                    s_survg[par] = 0.0;
+                    s_survm[par] = 0.0;
+                    s_nwork[par ^ 1] = 0;                        // list count of step t + 1
+                    rec[r0 + t] = RotRec{i, j, le, L, cc, ss};
+                } else if (wid == 3 && lane < 4 && t + 2 < e) {
+                    // candidates for the pivot of step t + 2, for both possible
+                    // eliminations; the mask word may or may not show the update
+                    // yet, but the matching hypothesis reads the same bits
+                    const int64_t p2 = (int64_t)__umul64hi(draws[t + 2], (uint64_t)(c - t - 2));
+                    s_nb[par][lane] = select_bit(mask, nwords, p2 + (lane & 1), lane < 2 ? i : j);
+                }
+            }
+            __syncthreads();
+            // ---- P2
+            const double cc = s_c, ss = s_s;
+            const int le = s_le;
+            const int surv = le == i ? j : i;
+            // the pivot of step t + 1 is the p-th survivor: a1 unless the
+            // eliminated index sits at or before it
+            const int inext = more ? (le <= a1 ? a2 : a1) : -1;
+            Cand nbest = cand_none();
+            if (wid == 0) {
+                // the survivor's new weight (needed from the final reduce on),
+                // overlapping the column threads' work
+                const double x = gd[surv];
+                const double ws = x > 0.0 ? __ddiv_rn(1.0, __dsqrt_rn(x)) : 0.0;
+                if (lane == 0) {
+                    w[surv] = ws;
+                    s_wn[par][0] = ws;
+                }
+            } else if (ct >= 0) {
+                if (more) {
+#pragma unroll
+                    for (int k = 0; k < KPT; ++k)
+                        if (zy[k] >= 0 && zy[k] != inext) cand_merge(nbest, Cand{0ull, zy[k], 0.0, 0.0});
+                }
+                const int nwork = s_nwork[par];
+                for (int q = ct; q < nwork; q += NCT) {
+                    const Work it = work[q];
+                    const int y = it.y;
+                    double nig = it.gi, njg = it.gj, nim = it.mi, njm = it.mj;
+                    // only the survivor's row and column are read again
+                    if (it.flags & W_G) {
+                        rot_pair(cc, ss, it.gi, it.gj, nig, njg);
+                        const double v = surv == i ? nig : njg;
+                        G[(int64_t)surv * c + y] = v;
+                        G[(int64_t)y * c + surv] = v;
+                    }
+                    if (it.flags & W_M) {
+                        rot_pair(cc, ss, it.mi, it.mj, nim, njm);
+                        const double v = surv == i ? nim : njm;
+                        M[(int64_t)surv * c + y] = v;
+                        M[(int64_t)y * c + surv] = v;
+                    }
+                    if (!more) continue;
+                    if (y == inext) {
+                        // column inext of the survivor's new row
+                        s_survg[par] = surv == i ? nig : njg;
+                        s_survm[par] = surv == i ? nim : njm;
+                        continue;
+                    }
+                    double gv, mv;
+                    if (inext == i) { gv = nig; mv = nim; }
+                    else if (inext == j) { gv = njg; mv = njm; }
+                    else if (inext == a1) { gv = it.g1; mv = it.m1; }
+                    else { gv = it.g2; mv = it.m2; }
+                    cand_merge(nbest, cand_make_sparse(gv, mv, w[y], y));
+                }
+            }
+            if (more) warp_argmax_to(nbest, &wbest[wid]);
+            __syncthreads();
+            if (more) {
+                nbest = block_best(wbest);
+                if (inext != i && inext != j)
+                    cand_merge(nbest, cand_make_sparse(s_survg[par], s_survm[par], s_wn[par][0], surv));
+                if (t + 2 < e) {
+                    a1 = le == i ? s_nb[par][0] : s_nb[par][2];
+                    a2 = le == i ? s_nb[par][1] : s_nb[par][3];
+                } else {
+                    a1 = a2 = -1;
+                }
+                i = inext;
+                j = nbest.idx;
+                gij = nbest.g;
+                mij = nbest.m;
+            }
+        }
     }
+    __syncthreads();
+    finish_cluster(u, r0, e, s_maxlev, members, base, rec, lcnt, lvlrot, lvl_off, nlev, elimflag, stage);
 }
 
 }  // namespace
@@ -355,14 +818,13 @@ pmmf_status gram_and_select(const Csr &A, const int32_t *pos, const int32_t *cl,
     PMMF_TRY(rot.lvl.alloc(rot.nrot > 0 ? rot.nrot : 1, st));
     PMMF_TRY(rot.lvl_off.alloc(rot.nrot + m + 1, st));
     PMMF_TRY(rot.nlev.zeros(m, st));
-    size_t shb = sizeof(double) * 3 * (size_t)cmax + sizeof(uint32_t) * (size_t)((cmax + 31) / 32) +
-                 sizeof(int32_t) * (size_t)(2 * cmax + 4);
-    if (shb > 220 * 1024) {
+    const size_t shb = sizeof(double) * 3 * (size_t)cmax + sizeof(uint32_t) * (size_t)((cmax + 31) / 32) +
+                       sizeof(int32_t) * (size_t)(2 * cmax + 4);
+    const size_t shf = shb + sizeof(uint64_t) * (size_t)(cmax + 1) + sizeof(Work) * (size_t)cmax + 16;
+    if (shf > 220 * 1024) {
         set_error("cluster too large for the selection kernel");
         return PMMF_ERR_UNSUPPORTED;
     }
-    if (shb > 48 * 1024)
-        PMMF_CUDA_TRY(cudaFuncSetAttribute(k_select, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shb));
     double sel_flops = 0.0;
     if (prof_on(KF_SELECT)) {
         // per step with n_a active coordinates: n_a score products and 12 flops
@@ -377,9 +839,26 @@ pmmf_status gram_and_select(const Csr &A, const int32_t *pos, const int32_t *cl,
         }
     }
     prof_begin(KF_SELECT, st);
-    k_select<<<(unsigned)m, SEL_THREADS, shb, st>>>(cls.coff.p, cls.members.p, goff.p, G.p, M.p,
-                                                    rot.roff.p, seed, stage, rot.rec.p, rot.lvl.p,
-                                                    rot.lvl_off.p, rot.nlev.p, elimflag);
+    const int kpt = (int)((cmax + NCT - 1) / NCT);
+    if (kpt <= 4) {
+        auto launch = [&](auto kern) -> pmmf_status {
+            if (shf > 48 * 1024)
+                PMMF_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shf));
+            kern<<<(unsigned)m, SEL_THREADS, shf, st>>>(cls.coff.p, cls.members.p, goff.p, G.p, M.p,
+                                                        rot.roff.p, seed, stage, rot.rec.p, rot.lvl.p,
+                                                        rot.lvl_off.p, rot.nlev.p, elimflag);
+            return PMMF_OK;
+        };
+        if (kpt <= 1) PMMF_TRY(launch(k_select_fast<1>));
+        else if (kpt <= 2) PMMF_TRY(launch(k_select_fast<2>));
+        else PMMF_TRY(launch(k_select_fast<4>));
+    } else {
+        if (shb > 48 * 1024)
+            PMMF_CUDA_TRY(cudaFuncSetAttribute(k_select, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shb));
+        k_select<<<(unsigned)m, SEL_THREADS, shb, st>>>(cls.coff.p, cls.members.p, goff.p, G.p, M.p,
+                                                        rot.roff.p, seed, stage, rot.rec.p, rot.lvl.p,
+                                                        rot.lvl_off.p, rot.nlev.p, elimflag);
+    }
     prof_end(KF_SELECT, st, 0.0, sel_flops);
     PMMF_TRY(launched("select"));
     return PMMF_OK;

@@ -99,7 +99,7 @@ __global__ void k_rows(RowArgs a) {
                 for (int idx = lo[L] + lane; idx < lo[L + 1]; idx += 32) {
                     Rot2 q = a.lvlrot[idx];
                     double vi = dense[q.li], vj = dense[q.lj];
-                    if (vi != 0.0 || vj != 0.0) {
+                    if (nonzero_bits(vi) || nonzero_bits(vj)) {
                         double ni, nj;
                         rot_pair(q.c, q.s, vi, vj, ni, nj);
                         dense[q.li] = ni;
@@ -111,7 +111,7 @@ __global__ void k_rows(RowArgs a) {
             for (int l0 = 0; l0 < c; l0 += 32) {
                 const int l = l0 + lane;
                 const double x = l < c ? dense[l] : 0.0;
-                const bool nz = x != 0.0;
+                const bool nz = nonzero_bits(x);
                 const int32_t g = nz ? a.members[cb + l] : -1;
                 if (MODE == P1_COUNT) {
                     if (nz) atomicAdd((unsigned long long *)&a.wcnt[a.pos[g]], 1ull);

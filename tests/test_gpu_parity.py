@@ -36,6 +36,16 @@ def test_knn_laplacian_clustered(n, c, core):
     assert_same_factorization(g, o)
 
 
+def test_full_size_bench_workload():
+    """The benchmark's own configuration (n = 65,536 kNN Laplacian, clusters of
+    ~256, core 256), compared in full: every stage's clusters, rotations and
+    A_p, and H."""
+    a = I.knn_laplacian(65536, 10, seed=1)
+    g, o = factor_both(a, k=2, eta=0.5, cluster_size=256, core_size=256, seed=0)
+    assert len(o.stages) == 9 and o.total_rotations() == 65280
+    assert_same_factorization(g, o)
+
+
 @pytest.mark.parametrize("eta", [0.25, 0.7])
 def test_other_compression_ratios(eta):
     a = I.knn_laplacian(2000, seed=2)

@@ -32,9 +32,12 @@ MUTANTS = [
     ("inverse sweep uses untransposed blocks",
      "for (int b = 0; b < kk; ++b) Ot[a * kk + b] = O[b * kk + a];",
      "for (int b = 0; b < kk; ++b) Ot[a * kk + b] = O[a * kk + b];"),
-    ("Jacobi sign of zeta flipped",
-     "t = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + r);",
-     "t = (zeta >= 0.0 ? -1.0 : 1.0) / (fabs(zeta) + r);"),
+    ("Jacobi sign of the angle flipped",
+     "*s = (h >= 0.0 ? g : -g) / den;",
+     "*s = (h >= 0.0 ? -g : g) / den;"),
+    ("Jacobi drops the coupling from the root",
+     "double r = sqrt(h * h + g * g);",
+     "double r = sqrt(h * h);"),
     ("symmetric update forgets the column mirror",
      "            X[y * ld + T[a]] = out[a];\n",
      ""),
