@@ -85,6 +85,14 @@ def lib():
         L.or_partition.restype = i32
         L.or_partition.argtypes = [i64, vp, i32, i64, vp, i64, i32, vp]
         L.or_quantize.argtypes = [i64, vp, i32, vp]
+        L.or_total_rotations.restype = i64
+        L.or_total_rotations.argtypes = [vp]
+        L.or_apply_grad.restype = i32
+        L.or_apply_grad.argtypes = [vp, i32, vp, vp, i64, vp, vp, vp, vp, vp]
+        L.or_set_rotation.restype = i32
+        L.or_set_rotation.argtypes = [vp, i32, i64, vp]
+        L.or_set_h.restype = i32
+        L.or_set_h.argtypes = [vp, vp, vp]
         _lib = L
     return _lib
 
@@ -153,6 +161,38 @@ class Factorization:
 
     def total_rotations(self) -> int:
         return sum(len(s.rot_elim) for s in self.stages)
+
+    def apply_grad(self, op: int, x: np.ndarray, g: np.ndarray) -> dict:
+        """Gradient of sum(g * op(x)) for op A or A_INV, selections fixed:
+        dx, dO [T, K*K], dtheta [T] (k = 2 angles), dhdiag [n], dcore [m, m]."""
+        x = np.ascontiguousarray(x, dtype=np.float64)
+        g = np.ascontiguousarray(g, dtype=np.float64)
+        nrhs = 1 if x.ndim == 1 else x.shape[1]
+        T = int(lib().or_total_rotations(self._h))
+        m = len(self.core_idx)
+        out = dict(dx=np.empty_like(x), dhdiag=np.zeros(self.n), dcore=np.zeros((m, m)))
+        dO = np.zeros((max(T, 1), self.K * self.K))
+        dth = np.zeros(max(T, 1))
+        st = lib().or_apply_grad(self._h, op, _p(x), _p(g), nrhs, _p(out["dx"]), _p(dO), _p(dth),
+                                 _p(out["dhdiag"]), _p(out["dcore"]))
+        if st:
+            raise RuntimeError(f"oracle gradient failed with status {st}")
+        out["dO"], out["dtheta"] = dO[:T], dth[:T]
+        return out
+
+    def set_rotation(self, p: int, t: int, O: np.ndarray) -> None:
+        """Replace one rotation block inside the oracle (finite-difference pins);
+        the exported copy in self.stages is left as it was."""
+        O = np.ascontiguousarray(O, dtype=np.float64).ravel()
+        if lib().or_set_rotation(self._h, p, t, _p(O)):
+            raise ValueError("bad rotation index")
+
+    def set_h(self, hdiag: np.ndarray = None, core: np.ndarray = None) -> None:
+        """Replace H inside the oracle (finite-difference pins)."""
+        hd = None if hdiag is None else np.ascontiguousarray(hdiag, dtype=np.float64)
+        co = None if core is None else np.ascontiguousarray(core, dtype=np.float64)
+        if lib().or_set_h(self._h, None if hd is None else _p(hd), None if co is None else _p(co)):
+            raise ValueError("set_h failed")
 
 
 def factor(n, rowptr, col, val, coords=None, *, k=2, eta=0.5, cluster_size=256, core_size=16,

@@ -1135,3 +1135,206 @@ out:
     free(r); free(z); free(pv); free(qv); free(rz); free(bn); free(done);
     return st;
 }
+
+/* ------------------------------------------------------------------------ */
+/* Gradient of the factorized operator (Sec. 2.4's matrix-free product with
+ * the greedy selections held fixed; not in the paper).  For
+ * L = sum_r <g_r, y_r> with y = U^T M U x, M = H (OR_OP_A) or H^{-1}
+ * (OR_OP_A_INV), and U the product of every rotation x_T' = O x_T in stage and
+ * step order:
+ *   - each block O appears once in U (as x_T' = O x_T) and once in U^T (as
+ *     x_T' = O^T x_T); for an occurrence with input v and output gradient g',
+ *     dL/dO_ab gains sum_r g'_a v_b (in U) or sum_r g'_b v_a (in U^T);
+ *   - with z = U x and w = U g: dL/dx = U^T M^T w, dL/dM = w z^T on the
+ *     structure of H (diagonal on wavelet coordinates, dense core);
+ *   - for M = H^{-1}: dL/dH = -M^T (dL/dM) M^T (M is symmetric up to rounding
+ *     and is used as such).
+ * For k = 2 blocks O = [[c, -s], [s, c]] with (c, s) = (cos t, sin t):
+ *   dL/dt = -s (dO_00 + dO_11) + c (dO_10 - dO_01).
+ * Memory: two n x nrhs vectors plus the tuple entries of every occurrence. */
+
+static int64_t total_rotations(const or_fact *f) {
+    int64_t T = 0;
+    for (int p = 0; p < f->nst; ++p) T += f->st[p].nrot;
+    return T;
+}
+
+int64_t or_total_rotations(const or_fact *f) { return f ? total_rotations(f) : 0; }
+
+int or_apply_grad(const or_fact *fc, int op, const double *x, const double *g, int64_t nrhs,
+                  double *dx, double *dO, double *dtheta, double *dhdiag, double *dcore) {
+    or_fact *f = (or_fact *)fc;
+    if (!f || f->status || nrhs < 1 || (op != OR_OP_A && op != OR_OP_A_INV)) return OR_ERR_INVALID_ARG;
+    const int K = f->K;
+    const int64_t n = f->n, m = f->ncore, T = total_rotations(f);
+    const int inverse = op == OR_OP_A_INV;
+    const size_t nv = (size_t)(n * nrhs);
+    /* rotation occurrences in U order: (stage, step) */
+    int32_t *tp = (int32_t *)malloc(sizeof(int32_t) * (size_t)(T > 0 ? T : 1));
+    int64_t *tt = (int64_t *)malloc(sizeof(int64_t) * (size_t)(T > 0 ? T : 1));
+    double *vin = (double *)malloc(sizeof(double) * (size_t)(T > 0 ? T * K * nrhs : 1));
+    double *pin = (double *)malloc(sizeof(double) * (size_t)(T > 0 ? T * K * nrhs : 1));
+    double *z = (double *)malloc(sizeof(double) * nv);
+    double *u = (double *)malloc(sizeof(double) * nv);
+    double *a = (double *)malloc(sizeof(double) * nv);
+    double *b = (double *)malloc(sizeof(double) * nv);
+    double *G = (double *)calloc((size_t)(T > 0 ? T * K * K : 1), sizeof(double));
+    int8_t *isc = (int8_t *)calloc((size_t)(n > 0 ? n : 1), 1);
+    int rc = OR_OK;
+    if (!tp || !tt || !vin || !pin || !z || !u || !a || !b || !G || !isc) { rc = OR_ERR_OOM; goto done; }
+    {
+        int64_t q = 0;
+        for (int p = 0; p < f->nst; ++p)
+            for (int64_t t = 0; t < f->st[p].nrot; ++t) { tp[q] = p; tt[q] = t; ++q; }
+    }
+#define ROT_O(q) (f->st[tp[q]].rO + tt[q] * K * K)
+#define ROT_KK(q) (f->st[tp[q]].rk[tt[q]])
+#define ROT_IDX(q, c) ((int64_t)f->st[tp[q]].ridx[tt[q] * K + (c)])
+    /* forward through U, keeping each occurrence's input entries */
+    memcpy(z, x, sizeof(double) * nv);
+    for (int64_t q = 0; q < T; ++q) {
+        const int kk = ROT_KK(q);
+        const double *O = ROT_O(q);
+        for (int64_t r = 0; r < nrhs; ++r) {
+            double in[KMAX];
+            for (int c = 0; c < kk; ++c) {
+                in[c] = z[ROT_IDX(q, c) * nrhs + r];
+                vin[(q * K + c) * nrhs + r] = in[c];
+            }
+            for (int c = 0; c < kk; ++c) z[ROT_IDX(q, c) * nrhs + r] = rot_row(O, kk, c, in);
+        }
+    }
+    /* u = M z; then through U^T (occurrences in reverse), keeping inputs */
+    memcpy(u, z, sizeof(double) * nv);
+    rc = apply_h(f, u, nrhs, inverse);
+    if (rc) goto done;
+    memcpy(b, u, sizeof(double) * nv);
+    for (int64_t q = T - 1; q >= 0; --q) {
+        const int kk = ROT_KK(q);
+        const double *O = ROT_O(q);
+        for (int64_t r = 0; r < nrhs; ++r) {
+            double in[KMAX];
+            for (int c = 0; c < kk; ++c) {
+                in[c] = b[ROT_IDX(q, c) * nrhs + r];
+                pin[(q * K + c) * nrhs + r] = in[c];
+            }
+            for (int c = 0; c < kk; ++c) {
+                double acc = 0.0;
+                for (int e = 0; e < kk; ++e) acc = acc + O[e * kk + c] * in[e];
+                b[ROT_IDX(q, c) * nrhs + r] = acc;
+            }
+        }
+    }
+    /* backward through U^T: y = O_1^T ... O_T^T u; the gradient reaching the
+     * output of occurrence q's transposed block is a (U order), and then
+     * a <- O a carries it to the block's input */
+    memcpy(a, g, sizeof(double) * nv);
+    for (int64_t q = 0; q < T; ++q) {
+        const int kk = ROT_KK(q);
+        const double *O = ROT_O(q);
+        double *dq = G + q * K * K;
+        for (int64_t r = 0; r < nrhs; ++r) {
+            double ga[KMAX];
+            for (int c = 0; c < kk; ++c) ga[c] = a[ROT_IDX(q, c) * nrhs + r];
+            /* output x'_c = sum_e O_ec in_e: dL/dO_ec += ga_c in_e */
+            for (int c = 0; c < kk; ++c)
+                for (int e = 0; e < kk; ++e) dq[e * kk + c] = dq[e * kk + c] + ga[c] * pin[(q * K + e) * nrhs + r];
+            for (int c = 0; c < kk; ++c) a[ROT_IDX(q, c) * nrhs + r] = rot_row(O, kk, c, ga);
+        }
+    }
+    /* a = w = U g.  b = M w is the gradient at z; keep w for dH first */
+    for (int64_t e = 0; e < m; ++e) isc[f->core_idx[e]] = 1;
+    if (!inverse) {
+        if (dhdiag)
+            for (int64_t i = 0; i < n; ++i) {
+                double acc = 0.0;
+                if (!isc[i])
+                    for (int64_t r = 0; r < nrhs; ++r) acc = acc + a[i * nrhs + r] * z[i * nrhs + r];
+                dhdiag[i] = acc;
+            }
+        if (dcore)
+            for (int64_t e = 0; e < m; ++e)
+                for (int64_t c = 0; c < m; ++c) {
+                    double acc = 0.0;
+                    for (int64_t r = 0; r < nrhs; ++r)
+                        acc = acc + a[(int64_t)f->core_idx[e] * nrhs + r] * z[(int64_t)f->core_idx[c] * nrhs + r];
+                    dcore[e * m + c] = acc;
+                }
+    }
+    memcpy(b, a, sizeof(double) * nv);
+    rc = apply_h(f, b, nrhs, inverse);
+    if (rc) goto done;
+    if (inverse) {
+        /* dL/dH = -(M w)(M z)^T on H's structure; M z = u */
+        if (dhdiag)
+            for (int64_t i = 0; i < n; ++i) {
+                double acc = 0.0;
+                if (!isc[i])
+                    for (int64_t r = 0; r < nrhs; ++r) acc = acc + b[i * nrhs + r] * u[i * nrhs + r];
+                dhdiag[i] = -acc;
+            }
+        if (dcore)
+            for (int64_t e = 0; e < m; ++e)
+                for (int64_t c = 0; c < m; ++c) {
+                    double acc = 0.0;
+                    for (int64_t r = 0; r < nrhs; ++r)
+                        acc = acc + b[(int64_t)f->core_idx[e] * nrhs + r] * u[(int64_t)f->core_idx[c] * nrhs + r];
+                    dcore[e * m + c] = -acc;
+                }
+    }
+    /* backward through U (occurrences in reverse): b is the gradient at the
+     * block's output; dL/dO_ce += b_c in_e; then b <- O^T b */
+    for (int64_t q = T - 1; q >= 0; --q) {
+        const int kk = ROT_KK(q);
+        const double *O = ROT_O(q);
+        double *dq = G + q * K * K;
+        for (int64_t r = 0; r < nrhs; ++r) {
+            double gb[KMAX];
+            for (int c = 0; c < kk; ++c) gb[c] = b[ROT_IDX(q, c) * nrhs + r];
+            for (int c = 0; c < kk; ++c)
+                for (int e = 0; e < kk; ++e) dq[c * kk + e] = dq[c * kk + e] + gb[c] * vin[(q * K + e) * nrhs + r];
+            for (int c = 0; c < kk; ++c) {
+                double acc = 0.0;
+                for (int e = 0; e < kk; ++e) acc = acc + O[e * kk + c] * gb[e];
+                b[ROT_IDX(q, c) * nrhs + r] = acc;
+            }
+        }
+    }
+    if (dx) memcpy(dx, b, sizeof(double) * nv);
+    if (dO) memcpy(dO, G, sizeof(double) * (size_t)(T * K * K));
+    if (dtheta)
+        for (int64_t q = 0; q < T; ++q) {
+            const double *O = ROT_O(q);
+            const double *dq = G + q * K * K;
+            if (ROT_KK(q) != 2) { dtheta[q] = 0.0; continue; }
+            const double c = O[0], s = O[2];
+            dtheta[q] = -s * (dq[0] + dq[3]) + c * (dq[2] - dq[1]);
+        }
+#undef ROT_O
+#undef ROT_KK
+#undef ROT_IDX
+done:
+    free(tp); free(tt); free(vin); free(pin); free(z); free(u); free(a); free(b); free(G); free(isc);
+    return rc;
+}
+
+/* Replace rotation t of stage p (k x k block, stride kk) -- used by the
+ * finite-difference pins of the gradient. */
+int or_set_rotation(or_fact *f, int p, int64_t t, const double *O) {
+    if (!f || p < 0 || p >= f->nst || t < 0 || t >= f->st[p].nrot) return OR_ERR_INVALID_ARG;
+    const int kk = f->st[p].rk[t];
+    memcpy(f->st[p].rO + t * f->K * f->K, O, sizeof(double) * (size_t)(kk * kk));
+    return OR_OK;
+}
+
+/* Replace H (diagonal over all n coordinates, core block m x m); the cached
+ * Cholesky factor is dropped. */
+int or_set_h(or_fact *f, const double *hdiag, const double *core) {
+    if (!f || f->status) return OR_ERR_INVALID_ARG;
+    if (hdiag) memcpy(f->hdiag, hdiag, sizeof(double) * (size_t)f->n);
+    if (core) memcpy(f->core, core, sizeof(double) * (size_t)(f->ncore * f->ncore));
+    free(f->chol);
+    f->chol = NULL;
+    f->chol_status = OR_OK;
+    return OR_OK;
+}

@@ -83,6 +83,17 @@ int or_pcg(const or_fact *f, int64_t n, const int64_t *rowptr, const int32_t *co
            const double *val, const double *b, double *x, int64_t nrhs, double rtol,
            int maxit, int32_t *iters, double *relres);
 
+/* Gradient of L = sum <g, op(x)> for op = OR_OP_A or OR_OP_A_INV with the
+ * selections fixed: dx (n x nrhs), dO (K*K slots per rotation in stage, step
+ * order; stride kk inside), dtheta (per rotation; k = 2 angle with
+ * (c, s) = (cos, sin), 0 for larger blocks), dhdiag (n, 0 on core coordinates),
+ * dcore (core_size^2).  Any output may be NULL. */
+int64_t or_total_rotations(const or_fact *f);
+int or_apply_grad(const or_fact *f, int op, const double *x, const double *g, int64_t nrhs,
+                  double *dx, double *dO, double *dtheta, double *dhdiag, double *dcore);
+int or_set_rotation(or_fact *f, int p, int64_t t, const double *O);
+int or_set_h(or_fact *f, const double *hdiag, const double *core);
+
 /* building blocks, exposed for the pins */
 uint64_t or_splitmix64_next(uint64_t *state);
 uint64_t or_draw(uint64_t seed, int64_t p, int64_t u, int64_t t);

@@ -2,8 +2,8 @@
 
 Each case plants one mistake in a private copy of the oracle source (a
 flipped sign, a transposed operand, a dropped term, a wrong index or
-comparison), compiles it on the CPU and runs the pin suite against it in a
-child process: the suite must fail.  The real oracle is never modified.
+comparison), compiles it on the CPU and runs the pin suites (method and
+gradient) against it in a child process: the suites must fail.  The real oracle is never modified.
 """
 
 import os
@@ -50,6 +50,18 @@ MUTANTS = [
     ("H keeps the wrong diagonal",
      "if (w->col[e2] == x) f->hdiag[x] = w->val[e2];",
      "if (w->col[e2] == x) f->hdiag[x] = 0.0;"),
+    ("gradient drops the transposed occurrence of each block",
+     "dq[e * kk + c] = dq[e * kk + c] + ga[c] * pin[(q * K + e) * nrhs + r];",
+     "dq[e * kk + c] = dq[e * kk + c];"),
+    ("gradient of a block entry transposed",
+     "dq[c * kk + e] = dq[c * kk + e] + gb[c] * vin[(q * K + e) * nrhs + r];",
+     "dq[e * kk + c] = dq[e * kk + c] + gb[c] * vin[(q * K + e) * nrhs + r];"),
+    ("angle chain rule with a flipped sine term",
+     "dtheta[q] = -s * (dq[0] + dq[3]) + c * (dq[2] - dq[1]);",
+     "dtheta[q] = -s * (dq[0] + dq[3]) + c * (dq[1] - dq[2]);"),
+    ("inverse gradient of H without the minus sign",
+     "                dhdiag[i] = -acc;",
+     "                dhdiag[i] = acc;"),
 ]
 
 
@@ -66,6 +78,7 @@ def test_pins_catch_mutant(name, old, new, tmp_path):
                            "-w", "-o", so, str(mdir / "pmmf_oracle.c"), "-lm"])
     env = dict(os.environ, PMMF_ORACLE_SO=so)
     r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider",
-                        os.path.join(ROOT, "tests", "test_oracle_pins.py")],
+                        os.path.join(ROOT, "tests", "test_oracle_pins.py"),
+                        os.path.join(ROOT, "tests", "test_oracle_grad_pins.py")],
                        cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
     assert r.returncode != 0, f"mutant '{name}' survived the pins:\n{r.stdout[-2000:]}"
