@@ -182,6 +182,49 @@ pmmf_status pmmf_solve_precond(const pmmf_handle *f, const pmmf_matrix *A, const
                                double *x, int64_t nrhs, double rtol, int maxit, int32_t *iters,
                                double *relres, void *stream);
 
+/* ---- differentiation of the factorized operator ----------------------------
+ * With the greedy selections held fixed, A~ = U^T H U is a smooth function of
+ * x, of H (its wavelet diagonal and its dense core) and of every k = 2
+ * rotation's angle theta ((c, s) = (cos theta, sin theta); Sec. 2's Givens
+ * rotations).  The paper defines the product and inverse (Sec. 2.4) but no
+ * derivative; these calls add one.
+ *
+ * pmmf_apply_backward: for L = sum over entries of g * op(x), op = PMMF_OP_A
+ * (y = A~ x) or PMMF_OP_A_INV (y = A~^{-1} x), writes
+ *   dx[n x nrhs] (row-major, ld)   dL/dx
+ *   dtheta[rotations]              dL/dtheta, stages in order and (cluster,
+ *                                  step) order inside a stage (the order of
+ *                                  pmmf_get_stage_rotations)
+ *   dhdiag[n]                      dL/dH_xx on wavelet coordinates, 0 on core
+ *                                  coordinates
+ *   dcore[core_size^2]             dL/dcore (row-major; for A_INV the core
+ *                                  inverse is formed from the lower triangle,
+ *                                  so the gradient sits there: entries above
+ *                                  the diagonal are 0)
+ * All arrays are DEVICE memory; outputs are overwritten and any of them may be
+ * NULL.  The stage-start state of [x | g] is checkpointed per stage and each
+ * stage is replayed once, so the cost is about three applies.  Asynchronous on
+ * stream (except the first A_INV call, which forms the core inverse).  Errors:
+ * INVALID_ARG (op, sizes, NULL x or g), UNSUPPORTED (k > 2 or a cluster too
+ * large for one CTA's shared memory), NOT_SPD (A_INV with H not SPD), OOM. */
+pmmf_status pmmf_apply_backward(const pmmf_handle *f, int op, const double *x, const double *g,
+                                int64_t nrhs, int64_t ld, double *dx, double *dtheta,
+                                double *dhdiag, double *dcore, void *stream);
+
+/* Angles of every rotation, theta = atan2(s, c), into the DEVICE array
+ * theta[rotations] in the order above (k = 2 only; else UNSUPPORTED). */
+pmmf_status pmmf_get_angles(const pmmf_handle *f, double *theta, void *stream);
+
+/* Replace every rotation by (cos theta, sin theta) from the DEVICE array
+ * theta[rotations]; the selections (tuples, levels, eliminations) are kept.
+ * pmmf_get_info's error still describes the factorization as computed. */
+pmmf_status pmmf_set_angles(pmmf_handle *f, const double *theta, void *stream);
+
+/* Replace H: hdiag[n] (its core entries are not used) and/or
+ * core[core_size^2], DEVICE arrays, either may be NULL.  The cached core
+ * inverse is dropped and formed again on the next inverse request. */
+pmmf_status pmmf_set_h(pmmf_handle *f, const double *hdiag, const double *core, void *stream);
+
 /* Release a handle (NULL-safe). */
 void pmmf_free(pmmf_handle *f);
 

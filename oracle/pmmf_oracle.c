@@ -1148,7 +1148,8 @@ out:
  *   - with z = U x and w = U g: dL/dx = U^T M^T w, dL/dM = w z^T on the
  *     structure of H (diagonal on wavelet coordinates, dense core);
  *   - for M = H^{-1}: dL/dH = -M^T (dL/dM) M^T (M is symmetric up to rounding
- *     and is used as such).
+ *     and is used as such); the core enters through its lower triangle only
+ *     (the inverse is formed from it), so its gradient is folded onto it.
  * For k = 2 blocks O = [[c, -s], [s, c]] with (c, s) = (cos t, sin t):
  *   dL/dt = -s (dO_00 + dO_11) + c (dO_10 - dO_01).
  * Memory: two n x nrhs vectors plus the tuple entries of every occurrence. */
@@ -1273,7 +1274,7 @@ int or_apply_grad(const or_fact *fc, int op, const double *x, const double *g, i
                     for (int64_t r = 0; r < nrhs; ++r) acc = acc + b[i * nrhs + r] * u[i * nrhs + r];
                 dhdiag[i] = -acc;
             }
-        if (dcore)
+        if (dcore) {
             for (int64_t e = 0; e < m; ++e)
                 for (int64_t c = 0; c < m; ++c) {
                     double acc = 0.0;
@@ -1281,6 +1282,15 @@ int or_apply_grad(const or_fact *fc, int op, const double *x, const double *g, i
                         acc = acc + b[(int64_t)f->core_idx[e] * nrhs + r] * u[(int64_t)f->core_idx[c] * nrhs + r];
                     dcore[e * m + c] = -acc;
                 }
+            /* the inverse is formed from the core's lower triangle (R12): an
+             * entry below the diagonal stands for both (e, c) and (c, e), one
+             * above it is not read */
+            for (int64_t e = 0; e < m; ++e)
+                for (int64_t c = 0; c < e; ++c) {
+                    dcore[e * m + c] = dcore[e * m + c] + dcore[c * m + e];
+                    dcore[c * m + e] = 0.0;
+                }
+        }
     }
     /* backward through U (occurrences in reverse): b is the gradient at the
      * block's output; dL/dO_ce += b_c in_e; then b <- O^T b */

@@ -87,7 +87,8 @@ int or_pcg(const or_fact *f, int64_t n, const int64_t *rowptr, const int32_t *co
  * selections fixed: dx (n x nrhs), dO (K*K slots per rotation in stage, step
  * order; stride kk inside), dtheta (per rotation; k = 2 angle with
  * (c, s) = (cos, sin), 0 for larger blocks), dhdiag (n, 0 on core coordinates),
- * dcore (core_size^2).  Any output may be NULL. */
+ * dcore (core_size^2; for OR_OP_A_INV on the lower triangle, which is what the
+ * inverse reads).  Any output may be NULL. */
 int64_t or_total_rotations(const or_fact *f);
 int or_apply_grad(const or_fact *f, int op, const double *x, const double *g, int64_t nrhs,
                   double *dx, double *dO, double *dtheta, double *dhdiag, double *dcore);

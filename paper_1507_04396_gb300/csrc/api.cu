@@ -9,6 +9,7 @@
 #include <vector>
 
 #include "apply.cuh"
+#include "backward.cuh"
 #include "common.cuh"
 #include "stage.cuh"
 
@@ -638,6 +639,64 @@ pmmf_status pmmf_solve_precond(const pmmf_handle *fc, const pmmf_matrix *A, cons
         conv = conv && hdone[c];
     }
     if (!conv) return fail(PMMF_ERR_NOT_CONVERGED, "PCG did not converge within maxit");
+    return PMMF_OK;
+}
+
+pmmf_status pmmf_apply_backward(const pmmf_handle *fc, int op, const double *x, const double *g,
+                                int64_t nrhs, int64_t ld, double *dx, double *dtheta,
+                                double *dhdiag, double *dcore, void *stream) {
+    set_error("");
+    pmmf_handle *f = const_cast<pmmf_handle *>(fc);
+    if (!f || !x || !g) return fail(PMMF_ERR_INVALID_ARG, "NULL handle or vector");
+    if (nrhs < 1 || ld < nrhs) return fail(PMMF_ERR_INVALID_ARG, "need nrhs >= 1 and ld >= nrhs");
+    if (op != PMMF_OP_A && op != PMMF_OP_A_INV)
+        return fail(PMMF_ERR_INVALID_ARG, "backward is defined for PMMF_OP_A and PMMF_OP_A_INV");
+    if (f->k != 2) return fail(PMMF_ERR_UNSUPPORTED, "backward needs k = 2 rotations");
+    cudaStream_t st = (cudaStream_t)stream;
+    const bool inv = op == PMMF_OP_A_INV;
+    if (inv) PMMF_TRY(ensure_inverse(f, st));
+    std::vector<const RotRec *> recs;
+    for (auto &S : f->st) recs.push_back(S.rot.rec.p);
+    return apply_backward(f->views, recs, hdata(f), inv, x, g, nrhs, ld, dx, dtheta, dhdiag,
+                          dcore, st);
+}
+
+pmmf_status pmmf_get_angles(const pmmf_handle *f, double *theta, void *stream) {
+    set_error("");
+    if (!f || !theta) return fail(PMMF_ERR_INVALID_ARG, "NULL handle or output");
+    if (f->k != 2) return fail(PMMF_ERR_UNSUPPORTED, "angles exist for k = 2 rotations only");
+    int64_t off = 0;
+    for (auto &S : f->st) {
+        PMMF_TRY(get_angles(S.rot.rec.p, S.nrot, theta + off, (cudaStream_t)stream));
+        off += S.nrot;
+    }
+    return PMMF_OK;
+}
+
+pmmf_status pmmf_set_angles(pmmf_handle *f, const double *theta, void *stream) {
+    set_error("");
+    if (!f || !theta) return fail(PMMF_ERR_INVALID_ARG, "NULL handle or input");
+    if (f->k != 2) return fail(PMMF_ERR_UNSUPPORTED, "angles exist for k = 2 rotations only");
+    int64_t off = 0;
+    for (size_t p = 0; p < f->st.size(); ++p) {
+        StageData &S = f->st[p];
+        PMMF_TRY(set_angles(f->views[p], S.rot.rec.p, S.rot.lvl.p, theta + off, (cudaStream_t)stream));
+        off += S.nrot;
+    }
+    return PMMF_OK;
+}
+
+pmmf_status pmmf_set_h(pmmf_handle *f, const double *hdiag, const double *core, void *stream) {
+    set_error("");
+    if (!f) return fail(PMMF_ERR_INVALID_ARG, "NULL handle");
+    cudaStream_t st = (cudaStream_t)stream;
+    if (hdiag)
+        PMMF_CUDA_TRY(cudaMemcpyAsync(f->hdiag.p, hdiag, sizeof(double) * (size_t)f->n,
+                                      cudaMemcpyDeviceToDevice, st));
+    if (core && f->ncore > 0)
+        PMMF_CUDA_TRY(cudaMemcpyAsync(f->core.p, core, sizeof(double) * (size_t)(f->ncore * f->ncore),
+                                      cudaMemcpyDeviceToDevice, st));
+    if (hdiag || core) f->inv_state = 0;
     return PMMF_OK;
 }
 

@@ -65,7 +65,8 @@ EXPORTS = ["pmmf_factor", "pmmf_apply", "pmmf_solve_precond", "pmmf_free", "pmmf
            "pmmf_profile_begin", "pmmf_profile_end", "pmmf_apply_noalloc",
            "pmmf_get_info", "pmmf_get_stage_info", "pmmf_get_stage_clusters",
            "pmmf_get_stage_rotations", "pmmf_get_h", "pmmf_get_stage_matrix",
-           "pmmf_launch_count"]
+           "pmmf_launch_count", "pmmf_apply_backward", "pmmf_get_angles", "pmmf_set_angles",
+           "pmmf_set_h"]
 
 _lib = None
 
@@ -106,6 +107,14 @@ def load(path: str = LIB_PATH):
     L.pmmf_launch_count.argtypes = []
     L.pmmf_apply_noalloc.restype = i32
     L.pmmf_apply_noalloc.argtypes = [vp, i32, vp, vp, i64, i64, vp]
+    L.pmmf_apply_backward.restype = i32
+    L.pmmf_apply_backward.argtypes = [vp, i32, vp, vp, i64, i64, vp, vp, vp, vp, vp]
+    L.pmmf_get_angles.restype = i32
+    L.pmmf_get_angles.argtypes = [vp, vp, vp]
+    L.pmmf_set_angles.restype = i32
+    L.pmmf_set_angles.argtypes = [vp, vp, vp]
+    L.pmmf_set_h.restype = i32
+    L.pmmf_set_h.argtypes = [vp, vp, vp, vp]
     L.pmmf_profile_begin.restype = i32
     L.pmmf_profile_begin.argtypes = [C.c_uint]
     L.pmmf_profile_end.restype = i32
@@ -214,6 +223,24 @@ def pmmf_solve_precond(handle: int, matrix: Matrix, b, x, nrhs: int, rtol: float
     return st, iters, relres
 
 
+def pmmf_apply_backward(handle: int, op: int, x, g, nrhs: int, ld: int, dx, dtheta, dhdiag,
+                        dcore, stream=None):
+    _check(load().pmmf_apply_backward(handle, op, _ptr(x), _ptr(g), nrhs, ld, _ptr(dx),
+                                      _ptr(dtheta), _ptr(dhdiag), _ptr(dcore), _stream(stream)))
+
+
+def pmmf_get_angles(handle: int, theta, stream=None):
+    _check(load().pmmf_get_angles(handle, _ptr(theta), _stream(stream)))
+
+
+def pmmf_set_angles(handle: int, theta, stream=None):
+    _check(load().pmmf_set_angles(handle, _ptr(theta), _stream(stream)))
+
+
+def pmmf_set_h(handle: int, hdiag, core, stream=None):
+    _check(load().pmmf_set_h(handle, _ptr(hdiag), _ptr(core), _stream(stream)))
+
+
 def pmmf_free(handle: int):
     if handle:
         load().pmmf_free(handle)
@@ -316,6 +343,46 @@ class Factorization:
         pmmf_apply(self.handle, op, x, y, nrhs, nrhs, stream)
         return y
 
+    # ---- differentiation (selections fixed)
+
+    def angles(self):
+        """Every rotation's angle as a CUDA float64 tensor (stage, cluster, step order)."""
+        import torch
+        th = torch.empty(max(self.info().rotations, 1), dtype=torch.float64, device="cuda")
+        pmmf_get_angles(self.handle, th)
+        return th[:self.info().rotations]
+
+    def h_tensors(self):
+        """(hdiag, core) as CUDA float64 tensors."""
+        import torch
+        hd, _, core = self.h()
+        return torch.from_numpy(hd).cuda(), torch.from_numpy(core).cuda()
+
+    def set_parameters(self, theta=None, hdiag=None, core=None):
+        """Write angles and/or H (CUDA float64 tensors) into the factorization."""
+        if theta is not None:
+            pmmf_set_angles(self.handle, theta.contiguous())
+        if hdiag is not None or core is not None:
+            pmmf_set_h(self.handle, None if hdiag is None else hdiag.contiguous(),
+                       None if core is None else core.contiguous())
+
+    def backward(self, op: int, x, g):
+        """Gradients of sum(g * op(x)): dict with dx, dtheta, dhdiag, dcore."""
+        import torch
+        assert x.is_cuda and x.dtype == torch.float64 and x.shape == g.shape
+        x, g = x.contiguous(), g.contiguous()
+        i = self.info()
+        nrhs = 1 if x.dim() == 1 else x.shape[1]
+        out = dict(dx=torch.empty_like(x),
+                   dtheta=torch.empty(max(i.rotations, 1), dtype=torch.float64, device="cuda"),
+                   dhdiag=torch.empty(i.n, dtype=torch.float64, device="cuda"),
+                   dcore=torch.empty((i.core_size, i.core_size), dtype=torch.float64,
+                                     device="cuda"))
+        pmmf_apply_backward(self.handle, op, x, g, nrhs, nrhs, out["dx"], out["dtheta"],
+                            out["dhdiag"], out["dcore"])
+        out["dtheta"] = out["dtheta"][:i.rotations]
+        return out
+
     def solve(self, a, b, rtol=1e-8, maxit=1000, stream=None):
         """Preconditioned CG for a x = b (b: CUDA float64 (n,) or (n, nrhs))."""
         import torch
@@ -343,3 +410,46 @@ def factor(a, *, k=2, eta=0.5, cluster_size=256, core_size=16, seed=0, max_stage
                  1 if record_stages else 0)
     h = pmmf_factor(m, prm, stream)
     return Factorization(h, k)
+
+
+# ---------------------------------------------------------------- autograd
+
+def _operator_fn():
+    import torch
+
+    class PMMFOperator(torch.autograd.Function):
+        """y = U^T H U x (op A) or its inverse (op A_INV) as a function of x, the
+        rotation angles theta, the wavelet diagonal hdiag and the core of H, with
+        the factorization's greedy selections held fixed.  Forward and backward
+        run in the CUDA library (pmmf_set_angles / pmmf_set_h / pmmf_apply /
+        pmmf_apply_backward); this class only passes tensors through."""
+
+        @staticmethod
+        def forward(ctx, x, theta, hdiag, core, fac, op):
+            fac.set_parameters(theta.detach(), hdiag.detach(), core.detach())
+            y = fac.apply(op, x.detach().contiguous())
+            ctx.save_for_backward(x, theta, hdiag, core)
+            ctx.fac, ctx.op = fac, op
+            return y
+
+        @staticmethod
+        def backward(ctx, gy):
+            x, theta, hdiag, core = ctx.saved_tensors
+            fac = ctx.fac
+            # the handle may have been re-parameterised since the forward
+            fac.set_parameters(theta.detach(), hdiag.detach(), core.detach())
+            gr = fac.backward(ctx.op, x.detach().contiguous(), gy.contiguous())
+            return gr["dx"], gr["dtheta"], gr["dhdiag"], gr["dcore"], None, None
+
+    return PMMFOperator
+
+
+_PMMF_OPERATOR = None
+
+
+def pmmf_operator(fac: Factorization, x, theta, hdiag, core, op: int = OP_A):
+    """Differentiable y = op(x) with parameters (theta, hdiag, core)."""
+    global _PMMF_OPERATOR
+    if _PMMF_OPERATOR is None:
+        _PMMF_OPERATOR = _operator_fn()
+    return _PMMF_OPERATOR.apply(x, theta, hdiag, core, fac, op)
