@@ -182,6 +182,42 @@ pmmf_status pmmf_solve_precond(const pmmf_handle *f, const pmmf_matrix *A, const
                                double *x, int64_t nrhs, double rtol, int maxit, int32_t *iters,
                                double *relres, void *stream);
 
+/* ---- batches of independent matrices ---------------------------------------
+ * Many independent symmetric matrices factored together (the paper factors
+ * one matrix; a batch is many of its problems at once).  Matrix b is factored
+ * exactly as pmmf_factor would factor it alone with one cluster per stage
+ * (params.coords = NULL) and seed params.seed + b: per stage
+ * e = max(1, min(floor(eta c), c - core_size)) rotations for its c active
+ * coordinates, until at most core_size remain, which become its core block.
+ * All matrices advance through the stages together, so each stage is one
+ * launch per kernel kind over every matrix, the longest searches first.
+ *
+ * pmmf_factor_blockdiag: the batch as ONE block-diagonal matrix A (any format
+ * and location accepted by pmmf_factor) whose diagonal block b spans the
+ * coordinates block_off[b] .. block_off[b+1]-1 (block_off: HOST, nmat + 1
+ * entries, strictly increasing from 0 to n).  An entry outside its diagonal
+ * block gives INVALID_ARG.  params.coords must be NULL and max_stages 0.
+ * The handle acts on the whole block-diagonal operator: pmmf_apply and
+ * pmmf_solve_precond take n x nrhs vectors (the matrices' vectors stacked).
+ * pmmf_get_h then returns core_idx[nmat * core_stride] (unused slots -1) and
+ * core[nmat * core_stride^2]: block b's core at core + b * core_stride^2,
+ * row stride core_stride (see pmmf_get_batch).  pmmf_apply_backward is not
+ * available on a batch handle (UNSUPPORTED). */
+pmmf_status pmmf_factor_blockdiag(const pmmf_matrix *A, int64_t nmat, const int64_t *block_off,
+                                  const pmmf_params *p, pmmf_handle **out, void *stream);
+
+/* Convenience form: nmat separate HOST CSR matrices A[0..nmat-1], stacked
+ * into one block-diagonal matrix on the host and factored as above. */
+pmmf_status pmmf_factor_batched(int64_t nmat, const pmmf_matrix *A, const pmmf_params *p,
+                                pmmf_handle **out, void *stream);
+
+/* Batch layout (HOST outputs, any may be NULL): nmat, core_stride (slot
+ * stride of the core blocks), block_off[nmat + 1], errors[nmat] (each
+ * matrix's ||A_b - U_b^T H_b U_b||_F / ||A_b||_F) and core_dim[nmat] (each
+ * core block's size).  A single factorization reports nmat = 1. */
+pmmf_status pmmf_get_batch(const pmmf_handle *f, int64_t *nmat, int64_t *core_stride,
+                           int64_t *block_off, double *errors, int32_t *core_dim);
+
 /* ---- differentiation of the factorized operator ----------------------------
  * With the greedy selections held fixed, A~ = U^T H U is a smooth function of
  * x, of H (its wavelet diagonal and its dense core) and of every k = 2

@@ -10,6 +10,7 @@
 
 #include "apply.cuh"
 #include "backward.cuh"
+#include "batch.cuh"
 #include "common.cuh"
 #include "stage.cuh"
 
@@ -40,6 +41,13 @@ struct pmmf_handle {
     pmmf::DBuf<double> core, core_inv;
     int inv_state = 0;  // 0 not formed, 1 formed, 2 not SPD
     pmmf::ApplyStages views;
+    // core blocks (one for a single factorization, one per matrix of a batch)
+    int64_t nblk = 1, bs = 0;
+    pmmf::DBuf<int32_t> bdim;            // batch: per-block core size
+    // batch: matrix b owns coordinates moff[b] .. moff[b+1]-1
+    int64_t nmat = 1;
+    std::vector<int64_t> moff;
+    std::vector<double> mat_err;
 };
 
 namespace pmmf {
@@ -155,6 +163,24 @@ pmmf_status check_params(const pmmf_matrix *A, const pmmf_params *p) {
         return fail(PMMF_ERR_INVALID_ARG, "bad coords location");
     if (p->k != 2) return fail(PMMF_ERR_UNSUPPORTED, "this build factors with k = 2 (Givens) only");
     return PMMF_OK;
+}
+
+void build_views(pmmf_handle *h) {
+    h->views.clear();
+    for (auto &S : h->st) {
+        ApplyStage v;
+        v.m = S.m;
+        v.nrot = S.nrot;
+        v.cmax = S.cmax;
+        v.s = S.s;
+        v.coff = S.cls.coff.p;
+        v.members = S.cls.members.p;
+        v.roff = S.rot.roff.p;
+        v.lvl_off = S.rot.lvl_off.p;
+        v.nlev = S.rot.nlev.p;
+        v.lvlrot = S.rot.lvl.p;
+        h->views.push_back(v);
+    }
 }
 
 pmmf_status factor_impl(const pmmf_matrix *A, const pmmf_params *prm, pmmf_handle *h,
@@ -317,20 +343,198 @@ pmmf_status factor_impl(const pmmf_matrix *A, const pmmf_params *prm, pmmf_handl
         tot += hc[i];
     }
     h->err = h->norm_a > 0.0 ? std::sqrt(tot) / h->norm_a : 0.0;
-    for (auto &S : h->st) {
-        ApplyStage v;
-        v.m = S.m;
-        v.nrot = S.nrot;
-        v.cmax = S.cmax;
-        v.s = S.s;
-        v.coff = S.cls.coff.p;
-        v.members = S.cls.members.p;
-        v.roff = S.rot.roff.p;
-        v.lvl_off = S.rot.lvl_off.p;
-        v.nlev = S.rot.nlev.p;
-        v.lvlrot = S.rot.lvl.p;
-        h->views.push_back(v);
+    h->nblk = 1;
+    h->bs = h->ncore;
+    h->nmat = 1;
+    h->moff = {0, n};
+    h->mat_err = {h->err};
+    build_views(h);
+    return PMMF_OK;
+}
+
+template <class T>
+pmmf_status upload(const std::vector<T> &v, DBuf<T> &d, cudaStream_t st) {
+    PMMF_TRY(d.alloc((int64_t)std::max<size_t>(v.size(), 1), st));
+    if (!v.empty())
+        PMMF_CUDA_TRY(cudaMemcpyAsync(d.p, v.data(), sizeof(T) * v.size(), cudaMemcpyHostToDevice, st));
+    return PMMF_OK;
+}
+
+// Batched factorization of a block-diagonal matrix: block b (coordinates
+// moff[b] .. moff[b+1]-1) is factored exactly as pmmf_factor would factor it
+// alone with one cluster per stage and seed + b, i.e. Algorithm 1 per matrix;
+// all blocks advance through the stages together.  Per cluster (= matrix),
+// e = max(1, min(floor(eta c), c - core_size)) (the single-cluster case of the
+// stage schedule); a matrix retires, its active rows becoming its core block,
+// once at most core_size coordinates are active.
+pmmf_status factor_batch_impl(const pmmf_matrix *A, const std::vector<int64_t> &moff,
+                              const pmmf_params *prm, pmmf_handle *h, cudaStream_t st) {
+    const int64_t n = A->n, nmat = (int64_t)moff.size() - 1;
+    const int64_t delta = prm->core_size;
+    h->n = n;
+    h->k = prm->k;
+    h->nmat = nmat;
+    h->moff = moff;
+    DBuf<unsigned> status;
+    PMMF_TRY(status.zeros(1, st));
+    Csr cur;
+    PMMF_TRY(stage_input(A, cur, status.p, st));
+    h->nnz_in = cur.nnz;
+    DBuf<int64_t> moff_d;
+    PMMF_TRY(upload(moff, moff_d, st));
+    PMMF_CUDA_TRY(cudaMemsetAsync(status.p, 0, sizeof(unsigned), st));
+    PMMF_TRY(check_blocks(n, cur.rowptr.p, cur.col.p, moff_d.p, nmat, status.p, st));
+    std::vector<double> norm2((size_t)nmat);
+    {
+        DBuf<double> nd;
+        PMMF_TRY(nd.alloc(nmat, st));
+        PMMF_TRY(block_sumsq(cur.rowptr.p, cur.val.p, moff_d.p, nmat, nd.p, st));
+        unsigned hs = 0;
+        PMMF_CUDA_TRY(cudaMemcpyAsync(norm2.data(), nd.p, sizeof(double) * (size_t)nmat, cudaMemcpyDeviceToHost, st));
+        PMMF_CUDA_TRY(cudaMemcpyAsync(&hs, status.p, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
+        PMMF_CUDA_TRY(cudaStreamSynchronize(st));
+        if (hs & ST_BAD_CSR) return fail(PMMF_ERR_INVALID_ARG, "batch: an entry lies outside its diagonal block");
     }
+    double tot2 = 0.0;
+    for (double v : norm2) tot2 += v;
+    h->norm_a = std::sqrt(tot2);
+
+    int64_t nmax = 0;
+    for (int64_t b = 0; b < nmat; ++b) nmax = std::max(nmax, moff[b + 1] - moff[b]);
+    const int64_t bs = std::max<int64_t>(1, std::min(delta, nmax));
+    h->nblk = nmat;
+    h->bs = bs;
+    PMMF_TRY(h->core.zeros(nmat * bs * bs, st));
+    PMMF_TRY(h->core_idx.alloc(nmat * bs, st));
+    PMMF_CUDA_TRY(cudaMemsetAsync(h->core_idx.p, 0xFF, sizeof(int32_t) * (size_t)(nmat * bs), st));
+    PMMF_TRY(h->core_pos.alloc(n, st));
+    PMMF_CUDA_TRY(cudaMemsetAsync(h->core_pos.p, 0xFF, sizeof(int32_t) * (size_t)n, st));
+    PMMF_TRY(h->bdim.zeros(nmat, st));
+
+    DBuf<int32_t> act, pos, cl, loc, elimflag, retired_d;
+    DBuf<double> contrib1;
+    DBuf<int64_t> lo_d, cnt_d;
+    PMMF_TRY(act.alloc(n, st));
+    PMMF_TRY(iota_i32(act.p, n, st));
+    PMMF_TRY(pos.alloc(n, st));
+    PMMF_TRY(iota_i32(pos.p, n, st));
+    PMMF_TRY(cl.alloc(n, st));
+    PMMF_TRY(loc.alloc(n, st));
+    PMMF_TRY(elimflag.zeros(n, st));
+    PMMF_TRY(h->hdiag.zeros(n, st));
+    PMMF_TRY(contrib1.zeros(1, st));
+    PMMF_TRY(retired_d.zeros(nmat, st));
+    PMMF_TRY(lo_d.alloc(nmat, st));
+    PMMF_TRY(cnt_d.alloc(nmat, st));
+    std::vector<int32_t> retired((size_t)nmat, 0);
+    std::vector<int64_t> lo((size_t)nmat), cnt((size_t)nmat);
+    std::vector<double> mat_contrib((size_t)nmat, 0.0);
+    int64_t s = n, p = 0, ncore = 0;
+    for (;;) {
+        PMMF_TRY(batch_ranges(act.p, s, moff_d.p, nmat, lo_d.p, cnt_d.p, st));
+        PMMF_CUDA_TRY(cudaMemcpyAsync(lo.data(), lo_d.p, sizeof(int64_t) * (size_t)nmat, cudaMemcpyDeviceToHost, st));
+        PMMF_CUDA_TRY(cudaMemcpyAsync(cnt.data(), cnt_d.p, sizeof(int64_t) * (size_t)nmat, cudaMemcpyDeviceToHost, st));
+        PMMF_CUDA_TRY(cudaStreamSynchronize(st));
+        std::vector<int64_t> rmat, rlo, rcnt, amat;
+        for (int64_t b = 0; b < nmat; ++b) {
+            if (retired[b]) continue;
+            if (cnt[b] <= delta) {
+                rmat.push_back(b);
+                rlo.push_back(lo[b]);
+                rcnt.push_back(cnt[b]);
+                retired[b] = 1;
+                ncore += cnt[b];
+            } else {
+                amat.push_back(b);
+            }
+        }
+        if (!rmat.empty()) {
+            DBuf<int64_t> rm, rl, rc;
+            PMMF_TRY(upload(rmat, rm, st));
+            PMMF_TRY(upload(rlo, rl, st));
+            PMMF_TRY(upload(rcnt, rc, st));
+            PMMF_TRY(batch_core(cur, act.p, pos.p, (int64_t)rmat.size(), rm.p, rl.p, rc.p, bs,
+                                h->core.p, h->core_idx.p, h->core_pos.p, h->bdim.p, h->hdiag.p, st));
+            PMMF_TRY(upload(retired, retired_d, st));
+            PMMF_TRY(batch_drop_rows(cur, act, retired_d.p, moff_d.p, nmat, st));
+            s = cur.rows;
+            PMMF_CUDA_TRY(cudaMemsetAsync(pos.p, 0xFF, sizeof(int32_t) * (size_t)n, st));
+            PMMF_TRY(set_positions(act.p, s, pos.p, st));
+        }
+        if (amat.empty()) break;
+        ++p;
+        h->st.emplace_back();
+        StageData &S = h->st.back();
+        S.s = s;
+        const int64_t m = (int64_t)amat.size();
+        std::vector<int64_t> coff((size_t)m + 1, 0), roff((size_t)m + 1, 0);
+        std::vector<uint64_t> useed((size_t)m);
+        std::vector<int32_t> order((size_t)m);
+        for (int64_t u = 0; u < m; ++u) {
+            const int64_t c = cnt[amat[u]];
+            coff[u + 1] = coff[u] + c;
+            int64_t e = (int64_t)std::floor(prm->eta * (double)c);
+            e = std::max<int64_t>(1, std::min(e, c - delta));
+            roff[u + 1] = roff[u] + e;
+            S.cmax = std::max(S.cmax, c);
+            useed[u] = prm->seed + (uint64_t)amat[u];
+            order[u] = (int32_t)u;
+        }
+        // longest clusters first, so the longest searches start in the first wave
+        std::stable_sort(order.begin(), order.end(), [&](int32_t x, int32_t y) {
+            return roff[x + 1] - roff[x] > roff[y + 1] - roff[y];
+        });
+        PMMF_TRY(upload(coff, S.cls.coff, st));
+        PMMF_TRY(batch_clusters(act.p, s, S.cls.coff.p, m, S.cls, cl.p, loc.p, st));
+        PMMF_TRY(upload(roff, S.rot.roff, st));
+        DBuf<uint64_t> useed_d;
+        DBuf<int32_t> order_d;
+        PMMF_TRY(upload(useed, useed_d, st));
+        PMMF_TRY(upload(order, order_d, st));
+        S.m = m;
+        S.nrot = roff[m];
+        S.rot.nrot = roff[m];
+        PMMF_TRY(gram_and_select(cur, pos.p, cl.p, S.cls, S.cmax, prm->seed, p, S.rot,
+                                 elimflag.p, st, order_d.p, useed_d.p));
+        DBuf<double> ccl;
+        PMMF_TRY(ccl.zeros(m, st));
+        UpdateOut up;
+        PMMF_CUDA_TRY(cudaMemsetAsync(status.p, 0, sizeof(unsigned), st));
+        PMMF_TRY(update_stage(cur, act.p, n, pos.p, cl.p, loc.p, S.cls, S.cmax, S.rot, elimflag.p,
+                              p, h->hdiag.p, contrib1.p, up, status.p, st, ccl.p));
+        {
+            unsigned hs = 0;
+            std::vector<int32_t> nl((size_t)m);
+            std::vector<double> cc((size_t)m);
+            PMMF_CUDA_TRY(cudaMemcpyAsync(&hs, status.p, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
+            PMMF_CUDA_TRY(cudaMemcpyAsync(nl.data(), S.rot.nlev.p, sizeof(int32_t) * nl.size(), cudaMemcpyDeviceToHost, st));
+            PMMF_CUDA_TRY(cudaMemcpyAsync(cc.data(), ccl.p, sizeof(double) * cc.size(), cudaMemcpyDeviceToHost, st));
+            PMMF_CUDA_TRY(cudaStreamSynchronize(st));
+            if (hs & ST_ROW_TOO_LONG) return fail(PMMF_ERR_UNSUPPORTED, "update: output row too long");
+            int32_t ml = 0;
+            for (int32_t v : nl) ml = std::max(ml, v);
+            S.max_levels = ml;
+            for (int64_t u = 0; u < m; ++u) {
+                mat_contrib[amat[u]] += cc[u];
+                S.contrib += cc[u];
+            }
+        }
+        S.nnz_after = up.next.nnz;
+        PMMF_CUDA_TRY(cudaMemsetAsync(pos.p, 0xFF, sizeof(int32_t) * (size_t)n, st));
+        PMMF_TRY(set_positions(up.act.p, up.next.rows, pos.p, st));
+        s = up.next.rows;
+        cur = std::move(up.next);
+        act = std::move(up.act);
+    }
+    h->ncore = ncore;
+    double tot = 0.0;
+    h->mat_err.assign((size_t)nmat, 0.0);
+    for (int64_t b = 0; b < nmat; ++b) {
+        tot += mat_contrib[b];
+        h->mat_err[b] = norm2[b] > 0.0 ? std::sqrt(mat_contrib[b]) / std::sqrt(norm2[b]) : 0.0;
+    }
+    h->err = h->norm_a > 0.0 ? std::sqrt(tot) / h->norm_a : 0.0;
+    build_views(h);
     return PMMF_OK;
 }
 
@@ -367,6 +571,97 @@ pmmf_status pmmf_factor(const pmmf_matrix *A, const pmmf_params *p, pmmf_handle 
         return s;
     }
     *out = h;
+    return PMMF_OK;
+}
+
+pmmf_status pmmf_factor_blockdiag(const pmmf_matrix *A, int64_t nmat, const int64_t *block_off,
+                                  const pmmf_params *p, pmmf_handle **out, void *stream) {
+    set_error("");
+    if (!out) return fail(PMMF_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    PMMF_TRY(check_params(A, p));
+    if (nmat < 1 || !block_off) return fail(PMMF_ERR_INVALID_ARG, "need nmat >= 1 and block_off");
+    if (p->coords) return fail(PMMF_ERR_INVALID_ARG, "batch: one cluster per matrix, coords must be NULL");
+    if (p->max_stages > 0) return fail(PMMF_ERR_INVALID_ARG, "batch: max_stages must be 0");
+    std::vector<int64_t> moff(block_off, block_off + nmat + 1);
+    if (moff[0] != 0 || moff[nmat] != A->n) return fail(PMMF_ERR_INVALID_ARG, "block_off must run from 0 to n");
+    for (int64_t b = 0; b < nmat; ++b)
+        if (moff[b + 1] <= moff[b]) return fail(PMMF_ERR_INVALID_ARG, "block_off must increase strictly");
+    set_pool_threshold();
+    cudaStream_t st = (cudaStream_t)stream;
+    pmmf_handle *h = new (std::nothrow) pmmf_handle();
+    if (!h) return fail(PMMF_ERR_OOM, "host allocation failed");
+    pmmf_status s;
+    try {
+        s = factor_batch_impl(A, moff, p, h, st);
+    } catch (const std::bad_alloc &) {
+        s = fail(PMMF_ERR_OOM, "host allocation failed");
+    }
+    if (s != PMMF_OK) {
+        cudaStreamSynchronize(st);
+        delete h;
+        return s;
+    }
+    *out = h;
+    return PMMF_OK;
+}
+
+pmmf_status pmmf_factor_batched(int64_t nmat, const pmmf_matrix *A, const pmmf_params *p,
+                                pmmf_handle **out, void *stream) {
+    set_error("");
+    if (!out) return fail(PMMF_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (nmat < 1 || !A) return fail(PMMF_ERR_INVALID_ARG, "need nmat >= 1 matrices");
+    std::vector<int64_t> moff((size_t)nmat + 1, 0);
+    int64_t nnz = 0;
+    for (int64_t b = 0; b < nmat; ++b) {
+        if (A[b].format != PMMF_CSR || A[b].location != PMMF_HOST || !A[b].rowptr || A[b].n < 1)
+            return fail(PMMF_ERR_INVALID_ARG, "batch: every matrix must be a HOST CSR matrix with n >= 1");
+        moff[b + 1] = moff[b] + A[b].n;
+        nnz += A[b].rowptr[A[b].n] - A[b].rowptr[0];
+    }
+    if (moff[nmat] >= INT32_MAX) return fail(PMMF_ERR_UNSUPPORTED, "batch: total size must be < 2^31");
+    std::vector<int64_t> rp((size_t)moff[nmat] + 1, 0);
+    std::vector<int32_t> ci((size_t)std::max<int64_t>(nnz, 1));
+    std::vector<double> v((size_t)std::max<int64_t>(nnz, 1));
+    int64_t q = 0;
+    for (int64_t b = 0; b < nmat; ++b) {
+        const pmmf_matrix &M = A[b];
+        if (!M.colidx || !M.val) return fail(PMMF_ERR_INVALID_ARG, "batch: NULL CSR array");
+        for (int64_t i = 0; i < M.n; ++i) {
+            for (int64_t e = M.rowptr[i]; e < M.rowptr[i + 1]; ++e) {
+                if (M.colidx[e] < 0 || M.colidx[e] >= M.n)
+                    return fail(PMMF_ERR_INVALID_ARG, "batch: column index out of range");
+                ci[(size_t)q] = (int32_t)(M.colidx[e] + moff[b]);
+                v[(size_t)q] = M.val[e];
+                ++q;
+            }
+            rp[(size_t)(moff[b] + i + 1)] = q;
+        }
+    }
+    pmmf_matrix big{};
+    big.n = moff[nmat];
+    big.format = PMMF_CSR;
+    big.location = PMMF_HOST;
+    big.rowptr = rp.data();
+    big.colidx = ci.data();
+    big.val = v.data();
+    return pmmf_factor_blockdiag(&big, nmat, moff.data(), p, out, stream);
+}
+
+pmmf_status pmmf_get_batch(const pmmf_handle *f, int64_t *nmat, int64_t *core_stride,
+                           int64_t *block_off, double *errors, int32_t *core_dim) {
+    if (!f) return fail(PMMF_ERR_INVALID_ARG, "NULL handle");
+    if (nmat) *nmat = f->nmat;
+    if (core_stride) *core_stride = f->bs;
+    if (block_off) std::copy(f->moff.begin(), f->moff.end(), block_off);
+    if (errors) std::copy(f->mat_err.begin(), f->mat_err.end(), errors);
+    if (core_dim) {
+        if (f->nblk > 1)
+            PMMF_CUDA_TRY(cudaMemcpy(core_dim, f->bdim.p, sizeof(int32_t) * (size_t)f->nmat, cudaMemcpyDeviceToHost));
+        else
+            core_dim[0] = (int32_t)f->ncore;
+    }
     return PMMF_OK;
 }
 
@@ -452,10 +747,11 @@ pmmf_status pmmf_get_stage_rotations(const pmmf_handle *f, int p, int32_t *clust
 pmmf_status pmmf_get_h(const pmmf_handle *f, double *hdiag, int32_t *core_idx, double *core) {
     if (!f) return fail(PMMF_ERR_INVALID_ARG, "NULL handle");
     if (hdiag) PMMF_CUDA_TRY(cudaMemcpy(hdiag, f->hdiag.p, sizeof(double) * (size_t)f->n, cudaMemcpyDeviceToHost));
-    if (core_idx && f->ncore > 0)
-        PMMF_CUDA_TRY(cudaMemcpy(core_idx, f->core_idx.p, sizeof(int32_t) * (size_t)f->ncore, cudaMemcpyDeviceToHost));
-    if (core && f->ncore > 0)
-        PMMF_CUDA_TRY(cudaMemcpy(core, f->core.p, sizeof(double) * (size_t)(f->ncore * f->ncore), cudaMemcpyDeviceToHost));
+    const int64_t slots = f->nblk * f->bs;
+    if (core_idx && slots > 0)
+        PMMF_CUDA_TRY(cudaMemcpy(core_idx, f->core_idx.p, sizeof(int32_t) * (size_t)slots, cudaMemcpyDeviceToHost));
+    if (core && slots > 0)
+        PMMF_CUDA_TRY(cudaMemcpy(core, f->core.p, sizeof(double) * (size_t)(slots * f->bs), cudaMemcpyDeviceToHost));
     return PMMF_OK;
 }
 
@@ -469,9 +765,13 @@ pmmf_status ensure_inverse(pmmf_handle *f, cudaStream_t st) {
     if (f->inv_state == 2) return fail(PMMF_ERR_NOT_SPD, "H is not positive definite");
     DBuf<unsigned> status;
     PMMF_TRY(status.zeros(1, st));
-    PMMF_TRY(f->core_inv.alloc(f->ncore * f->ncore, st));
-    PMMF_TRY(invert_core(f->core.p, f->ncore, f->hdiag.p, f->core_pos.p, f->n, f->core_inv.p,
-                         status.p, st));
+    PMMF_TRY(f->core_inv.alloc(f->nblk * f->bs * f->bs, st));
+    if (f->nblk > 1)
+        PMMF_TRY(invert_core_blocks(f->core.p, f->nblk, f->bs, f->bdim.p, f->hdiag.p, f->core_pos.p,
+                                    f->n, f->core_inv.p, status.p, st));
+    else
+        PMMF_TRY(invert_core(f->core.p, f->ncore, f->hdiag.p, f->core_pos.p, f->n, f->core_inv.p,
+                             status.p, st));
     unsigned hs = 0;
     PMMF_CUDA_TRY(cudaMemcpyAsync(&hs, status.p, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
     PMMF_CUDA_TRY(cudaStreamSynchronize(st));
@@ -486,7 +786,10 @@ pmmf_status ensure_inverse(pmmf_handle *f, cudaStream_t st) {
 HData hdata(const pmmf_handle *f) {
     HData H;
     H.n = f->n;
-    H.m = f->ncore;
+    H.m = f->nblk * f->bs;
+    H.nblk = f->nblk;
+    H.bs = f->bs;
+    H.bdim = f->nblk > 1 ? f->bdim.p : nullptr;
     H.hdiag = f->hdiag.p;
     H.core_pos = f->core_pos.p;
     H.core_idx = f->core_idx.p;
@@ -652,6 +955,7 @@ pmmf_status pmmf_apply_backward(const pmmf_handle *fc, int op, const double *x, 
     if (op != PMMF_OP_A && op != PMMF_OP_A_INV)
         return fail(PMMF_ERR_INVALID_ARG, "backward is defined for PMMF_OP_A and PMMF_OP_A_INV");
     if (f->k != 2) return fail(PMMF_ERR_UNSUPPORTED, "backward needs k = 2 rotations");
+    if (f->nblk > 1) return fail(PMMF_ERR_UNSUPPORTED, "backward of a batch handle is not built");
     cudaStream_t st = (cudaStream_t)stream;
     const bool inv = op == PMMF_OP_A_INV;
     if (inv) PMMF_TRY(ensure_inverse(f, st));
@@ -693,8 +997,8 @@ pmmf_status pmmf_set_h(pmmf_handle *f, const double *hdiag, const double *core, 
     if (hdiag)
         PMMF_CUDA_TRY(cudaMemcpyAsync(f->hdiag.p, hdiag, sizeof(double) * (size_t)f->n,
                                       cudaMemcpyDeviceToDevice, st));
-    if (core && f->ncore > 0)
-        PMMF_CUDA_TRY(cudaMemcpyAsync(f->core.p, core, sizeof(double) * (size_t)(f->ncore * f->ncore),
+    if (core && f->nblk * f->bs > 0)
+        PMMF_CUDA_TRY(cudaMemcpyAsync(f->core.p, core, sizeof(double) * (size_t)(f->nblk * f->bs * f->bs),
                                       cudaMemcpyDeviceToDevice, st));
     if (hdiag || core) f->inv_state = 0;
     return PMMF_OK;

@@ -81,15 +81,21 @@ __global__ void k_h_diag(double *x, int64_t ld, int64_t n, int64_t nrhs, const d
     }
 }
 
-// Core part: x[core_idx[a]] = sum_b C[a][b] zc[b], a sequential chain per output.
-__global__ void k_core_gemv(const double *C, int64_t m, const double *zc, int64_t nrhs,
-                            const int32_t *core_idx, double *x, int64_t ld) {
-    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < m * nrhs;
+// Core part: x[core_idx[a]] = sum_b C[a][b] zc[b] over the slots b of a's
+// block, a sequential chain per output (a single core is one block).
+__global__ void k_core_gemv(const double *C, int64_t nblk, int64_t bs, const int32_t *bdim,
+                            const double *zc, int64_t nrhs, const int32_t *core_idx, double *x,
+                            int64_t ld) {
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < nblk * bs * nrhs;
          q += (int64_t)gridDim.x * blockDim.x) {
-        int64_t a = q / nrhs, r = q - a * nrhs;
-        const double *row = C + a * m;
+        const int64_t a = q / nrhs, r = q - a * nrhs;
+        const int64_t blk = a / bs, l = a - blk * bs;
+        const int64_t dim = bdim ? bdim[blk] : bs;
+        if (l >= dim) continue;
+        const double *row = C + blk * bs * bs + l * bs;
+        const double *zb = zc + blk * bs * nrhs;
         double acc = 0.0;
-        for (int64_t b = 0; b < m; ++b) acc = __dadd_rn(acc, __dmul_rn(row[b], zc[b * nrhs + r]));
+        for (int64_t b = 0; b < dim; ++b) acc = __dadd_rn(acc, __dmul_rn(row[b], zb[b * nrhs + r]));
         x[(int64_t)core_idx[a] * ld + r] = acc;
     }
 }
@@ -136,6 +142,47 @@ __global__ void k_gj_step(double *S, int64_t m, int64_t k, const double *rowk, c
         else if (j == k) v = -__ddiv_rn(colk[i], p);
         else v = __dsub_rn(S[q], __ddiv_rn(__dmul_rn(colk[i], rowk[j]), p));
         S[q] = v;
+    }
+}
+
+// One block per CTA: symmetric copy from the lower triangle, then the same
+// in-place Gauss-Jordan steps as k_gj_save / k_gj_step, in shared memory.
+__global__ void k_gj_blocks(const double *C, int64_t bs, const int32_t *bdim, double *inv,
+                            unsigned *status) {
+    extern __shared__ double S[];
+    const int64_t blk = blockIdx.x;
+    const int m = bdim ? bdim[blk] : (int)bs;
+    const double *Cb = C + blk * bs * bs;
+    double *Ib = inv + blk * bs * bs;
+    double *rowk = S + (int64_t)m * m;
+    double *colk = rowk + m;
+    for (int q = threadIdx.x; q < m * m; q += blockDim.x) {
+        const int i = q / m, j = q - i * m;
+        S[q] = i >= j ? Cb[i * bs + j] : Cb[j * bs + i];
+    }
+    __syncthreads();
+    for (int k = 0; k < m; ++k) {
+        for (int q = threadIdx.x; q < m; q += blockDim.x) {
+            rowk[q] = S[k * m + q];
+            colk[q] = S[q * m + k];
+        }
+        __syncthreads();
+        const double p = rowk[k];
+        if (threadIdx.x == 0 && !(p > 0.0)) atomicOr(status, ST_NOT_SPD);
+        for (int q = threadIdx.x; q < m * m; q += blockDim.x) {
+            const int i = q / m, j = q - i * m;
+            double v;
+            if (i == k && j == k) v = __ddiv_rn(1.0, p);
+            else if (i == k) v = __ddiv_rn(rowk[j], p);
+            else if (j == k) v = -__ddiv_rn(colk[i], p);
+            else v = __dsub_rn(S[q], __ddiv_rn(__dmul_rn(colk[i], rowk[j]), p));
+            S[q] = v;
+        }
+        __syncthreads();
+    }
+    for (int q = threadIdx.x; q < m * m; q += blockDim.x) {
+        const int i = q / m, j = q - i * m;
+        Ib[i * bs + j] = S[q];
     }
 }
 
@@ -284,9 +331,26 @@ pmmf_status apply_h(const HData &H, bool inverse, double *x, int64_t ld, int64_t
     else
         k_h_diag<false><<<grid_for(H.n * nrhs, 256), 256, 0, st>>>(x, ld, H.n, nrhs, H.hdiag, H.core_pos, zc.p);
     PMMF_TRY(launched("h_diag"));
-    k_core_gemv<<<grid_for(H.m * nrhs, 64), 64, 0, st>>>(inverse ? H.core_inv : H.core, H.m, zc.p,
-                                                         nrhs, H.core_idx, x, ld);
+    k_core_gemv<<<grid_for(H.m * nrhs, 64), 64, 0, st>>>(inverse ? H.core_inv : H.core, H.nblk,
+                                                         H.bs, H.bdim, zc.p, nrhs, H.core_idx, x, ld);
     return launched("core_gemv");
+}
+
+pmmf_status invert_core_blocks(const double *core, int64_t nblk, int64_t bs, const int32_t *bdim,
+                               const double *hdiag, const int32_t *core_pos, int64_t n,
+                               double *inv, unsigned *status, cudaStream_t st) {
+    k_wavelet_positive<<<grid_for(n, 256), 256, 0, st>>>(hdiag, core_pos, n, status);
+    PMMF_TRY(launched("wavelet_positive"));
+    if (nblk == 0 || bs == 0) return PMMF_OK;
+    const size_t sh = sizeof(double) * (size_t)(bs * bs + 2 * bs);
+    if (sh > 220 * 1024) {
+        set_error("core blocks too large to invert in shared memory");
+        return PMMF_ERR_UNSUPPORTED;
+    }
+    if (sh > 48 * 1024)
+        PMMF_CUDA_TRY(cudaFuncSetAttribute(k_gj_blocks, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh));
+    k_gj_blocks<<<(unsigned)nblk, 256, sh, st>>>(core, bs, bdim, inv, status);
+    return launched("gj_blocks");
 }
 
 pmmf_status invert_core(const double *core, int64_t m, const double *hdiag, const int32_t *core_pos,
@@ -355,8 +419,8 @@ pmmf_status apply_h_scratch(const HData &H, bool inverse, double *x, int64_t ld,
     else
         k_h_diag<false><<<grid_for(H.n * nrhs, 256), 256, 0, st>>>(x, ld, H.n, nrhs, H.hdiag, H.core_pos, zc);
     PMMF_TRY(launched("h_diag"));
-    k_core_gemv<<<grid_for(H.m * nrhs, 64), 64, 0, st>>>(inverse ? H.core_inv : H.core, H.m, zc,
-                                                         nrhs, H.core_idx, x, ld);
+    k_core_gemv<<<grid_for(H.m * nrhs, 64), 64, 0, st>>>(inverse ? H.core_inv : H.core, H.nblk,
+                                                         H.bs, H.bdim, zc, nrhs, H.core_idx, x, ld);
     return launched("core_gemv");
 }
 

@@ -18,13 +18,20 @@ struct ApplyStage {
 };
 using ApplyStages = std::vector<ApplyStage>;
 
+// H = diagonal on wavelet coordinates plus a block-diagonal core: nblk blocks
+// of slot stride bs (one dense block of size m for a single factorization,
+// one block per matrix for a batch).  Core slot a = blk * bs + l; block blk
+// holds bdim[blk] <= bs coordinates (all bs when bdim is null) and its values
+// at core[blk * bs * bs + l * bs + l'].
 struct HData {
-    int64_t n = 0, m = 0;
+    int64_t n = 0, m = 0;                // m = nblk * bs core slots
+    int64_t nblk = 1, bs = 0;
+    const int32_t *bdim = nullptr;       // nblk (null: every block full)
     const double *hdiag = nullptr;
-    const int32_t *core_pos = nullptr;   // n: position in the core or -1
-    const int32_t *core_idx = nullptr;   // m
-    const double *core = nullptr;        // m x m
-    const double *core_inv = nullptr;    // m x m
+    const int32_t *core_pos = nullptr;   // n: core slot or -1
+    const int32_t *core_idx = nullptr;   // m slots: global id (unused slots -1)
+    const double *core = nullptr;        // nblk * bs * bs
+    const double *core_inv = nullptr;    // nblk * bs * bs
 };
 
 struct DevCsr {
@@ -44,6 +51,11 @@ pmmf_status apply_h_scratch(const HData &H, bool inverse, double *x, int64_t ld,
                             double *zc, cudaStream_t st);
 pmmf_status invert_core(const double *core, int64_t m, const double *hdiag, const int32_t *core_pos,
                         int64_t n, double *inv, unsigned *status, cudaStream_t st);
+// Block cores (nblk > 1): every block inverted by the same Gauss-Jordan
+// sweep as invert_core, one CTA per block in shared memory.
+pmmf_status invert_core_blocks(const double *core, int64_t nblk, int64_t bs, const int32_t *bdim,
+                               const double *hdiag, const int32_t *core_pos, int64_t n,
+                               double *inv, unsigned *status, cudaStream_t st);
 pmmf_status spmv(const DevCsr &A, const double *x, double *y, int nrhs, cudaStream_t st);
 pmmf_status dots(const double *x, const double *y, int64_t n, int nrhs, double *out,
                  double *partial, cudaStream_t st);

@@ -288,9 +288,10 @@ __device__ void finish_cluster(int64_t u, int64_t r0, int e, int nl, const int32
 __global__ void __launch_bounds__(SEL_THREADS)
 k_select(const int64_t *coff, const int32_t *members, const int64_t *goff, double *Gall,
          double *Mall, const int64_t *roff, uint64_t seed, int64_t stage, RotRec *rec, Rot2 *lvlrot,
-         int32_t *lvl_off, int32_t *nlev, int32_t *elimflag) {
+         int32_t *lvl_off, int32_t *nlev, int32_t *elimflag, const int32_t *order,
+         const uint64_t *useed) {
     extern __shared__ double sh[];
-    const int64_t u = blockIdx.x;
+    const int64_t u = order ? order[blockIdx.x] : blockIdx.x;
     const int64_t base = coff[u];
     const int c = (int)(coff[u + 1] - base);
     const int64_t r0 = roff[u];
@@ -324,7 +325,7 @@ k_select(const int64_t *coff, const int32_t *members, const int64_t *goff, doubl
     __syncthreads();
     if (tid == 0) {
         s_maxlev = 0;
-        if (e > 0) s_i = select_bit(mask, nwords, (int64_t)__umul64hi(draw(seed, stage, u, 0), (uint64_t)c), -1);
+        if (e > 0) s_i = select_bit(mask, nwords, (int64_t)__umul64hi(draw(useed ? useed[u] : seed, stage, useed ? 0 : u, 0), (uint64_t)c), -1);
     }
     __syncthreads();
 
@@ -379,7 +380,7 @@ k_select(const int64_t *coff, const int32_t *members, const int64_t *goff, doubl
             s_s = ss;
             if (t + 1 < e)
                 s_i = select_bit(mask, nwords,
-                                 (int64_t)__umul64hi(draw(seed, stage, u, t + 1), (uint64_t)(c - t - 1)), -1);
+                                 (int64_t)__umul64hi(draw(useed ? useed[u] : seed, stage, useed ? 0 : u, t + 1), (uint64_t)(c - t - 1)), -1);
         }
         __syncthreads();
         // rows/columns i and j of G and M for every other active coordinate
@@ -445,12 +446,13 @@ constexpr int NCT = SEL_THREADS - 32 * FP_WARPS;
 __device__ __forceinline__ void fp_sync() { asm volatile("bar.sync 1, %0;" ::"n"(32 * FP_WARPS)); }
 
 // Best of the per-warp candidates, computed by every warp in parallel.
+template <int NWARPS>
 __device__ __forceinline__ Cand block_best(const Cand *wb) {
     const int lane = threadIdx.x & 31;
-    const Cand mine = lane < SEL_WARPS ? wb[lane] : cand_none();
+    const Cand mine = lane < NWARPS ? wb[lane] : cand_none();
     unsigned long long k = mine.key;
     int32_t id = mine.idx;
-    for (int o = 4; o > 0; o >>= 1) {
+    for (int o = NWARPS / 2; o > 0; o >>= 1) {
         const unsigned long long ok = __shfl_xor_sync(0xffffffffu, k, o);
         const int32_t oi = __shfl_xor_sync(0xffffffffu, id, o);
         if (cand_better(ok, oi, k, id)) {
@@ -460,7 +462,7 @@ __device__ __forceinline__ Cand block_best(const Cand *wb) {
     }
     k = __shfl_sync(0xffffffffu, k, 0);
     id = __shfl_sync(0xffffffffu, id, 0);
-    const unsigned own = __ballot_sync(0xffffffffu, lane < SEL_WARPS && mine.idx == id && mine.key == k);
+    const unsigned own = __ballot_sync(0xffffffffu, lane < NWARPS && mine.idx == id && mine.key == k);
     const int src = own ? __ffs(own) - 1 : 0;
     Cand r;
     r.key = k;
@@ -482,13 +484,16 @@ __device__ __forceinline__ Cand block_best(const Cand *wb) {
 //        and column; the eliminated coordinate's are never read again), zero
 //        and nonzero candidates for the next pivot; warp argmax.
 // Two block barriers per step.  The arithmetic, and so every bit, is k_select's.
-template <int KPT>
-__global__ void __launch_bounds__(SEL_THREADS)
+template <int KPT, int NT>
+__global__ void __launch_bounds__(NT)
 k_select_fast(const int64_t *coff, const int32_t *members, const int64_t *goff, double *Gall,
               double *Mall, const int64_t *roff, uint64_t seed, int64_t stage, RotRec *rec,
-              Rot2 *lvlrot, int32_t *lvl_off, int32_t *nlev, int32_t *elimflag) {
+              Rot2 *lvlrot, int32_t *lvl_off, int32_t *nlev, int32_t *elimflag,
+              const int32_t *order, const uint64_t *useed) {
+    constexpr int NW = NT / 32;                 // warps
+    constexpr int NCTT = NT - 32 * FP_WARPS;    // column threads
     extern __shared__ double sh[];
-    const int64_t u = blockIdx.x;
+    const int64_t u = order ? order[blockIdx.x] : blockIdx.x;
     const int64_t base = coff[u];
     const int c = (int)(coff[u + 1] - base);
     const int64_t r0 = roff[u];
@@ -505,7 +510,7 @@ k_select_fast(const int64_t *coff, const int32_t *members, const int64_t *goff, 
     int32_t *lcnt = lvl + c;          // e + 2 counters
     // c entries after the counters, 16-byte aligned (the launch adds the slack)
     Work *work = (Work *)(((uintptr_t)(lcnt + e + 2) + 15) & ~(uintptr_t)15);
-    __shared__ Cand wbest[SEL_WARPS];
+    __shared__ Cand wbest[NW];
     __shared__ int s_le, s_maxlev, s_a1, s_a2;
     __shared__ int s_nwork[2];                  // by step parity
     __shared__ int s_nb[2][4];                  // by step parity: [skip i: p, p+1, skip j: p, p+1]
@@ -516,19 +521,19 @@ k_select_fast(const int64_t *coff, const int32_t *members, const int64_t *goff, 
 
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     const int ct = tid - 32 * FP_WARPS;         // column thread index (>= 0 in column warps)
-    for (int a = tid; a < c; a += SEL_THREADS) {
+    for (int a = tid; a < c; a += NT) {
         const double g = G[(int64_t)a * c + a];
         gd[a] = g;
         md[a] = M[(int64_t)a * c + a];
         w[a] = g > 0.0 ? __ddiv_rn(1.0, __dsqrt_rn(g)) : 0.0;
         lvl[a] = 0;
     }
-    for (int wi = tid; wi < nwords; wi += SEL_THREADS) {
+    for (int wi = tid; wi < nwords; wi += NT) {
         const int rem = c - wi * 32;
         mask[wi] = rem >= 32 ? 0xffffffffu : ((1u << rem) - 1u);
     }
-    for (int t = tid; t < e; t += SEL_THREADS) draws[t] = draw(seed, stage, u, t);
-    for (int q = tid; q < e + 2; q += SEL_THREADS) lcnt[q] = 0;
+    for (int t = tid; t < e; t += NT) draws[t] = draw(useed ? useed[u] : seed, stage, useed ? 0 : u, t);
+    for (int q = tid; q < e + 2; q += NT) lcnt[q] = 0;
     __syncthreads();
     if (tid == 0) {
         s_maxlev = 0;
@@ -547,13 +552,13 @@ k_select_fast(const int64_t *coff, const int32_t *members, const int64_t *goff, 
         // partner search for the first pivot
         Cand best = cand_none();
         if (ct >= 0)
-            for (int y = ct; y < c; y += NCT) {
+            for (int y = ct; y < c; y += NCTT) {
                 if (y == i || !is_active(mask, y)) continue;
                 cand_merge(best, cand_make_sparse(G[(int64_t)i * c + y], M[(int64_t)i * c + y], w[y], y));
             }
         warp_argmax_to(best, &wbest[wid]);
         __syncthreads();
-        best = block_best(wbest);
+        best = block_best<NW>(wbest);
         int j = best.idx;
         double gij = best.g, mij = best.m;
         int a1 = s_a1, a2 = s_a2;
@@ -575,7 +580,7 @@ k_select_fast(const int64_t *coff, const int32_t *members, const int64_t *goff, 
                 int total = 0;
 #pragma unroll
                 for (int k = 0; k < KPT; ++k) {
-                    const int y = ct + k * NCT;
+                    const int y = ct + k * NCTT;
                     gi[k] = gj[k] = mi[k] = mj[k] = g1[k] = m1[k] = g2[k] = m2[k] = 0.0;
                     const bool live = y < c && y != i && y != j && is_active(mask, y);
                     if (live) {
@@ -610,7 +615,7 @@ k_select_fast(const int64_t *coff, const int32_t *members, const int64_t *goff, 
                 for (int k = 0; k < KPT; ++k) {
                     if (fl[k]) {
                         Work &it = work[wbase + __popc(bal[k] & ((1u << lane) - 1u))];
-                        it.y = ct + k * NCT;
+                        it.y = ct + k * NCTT;
                         it.flags = fl[k];
                         it.gi = gi[k];
                         it.gj = gj[k];
@@ -733,7 +738,7 @@ k_select_fast(const int64_t *coff, const int32_t *members, const int64_t *goff, 
                         if (zy[k] >= 0 && zy[k] != inext) cand_merge(nbest, Cand{0ull, zy[k], 0.0, 0.0});
                 }
                 const int nwork = s_nwork[par];
-                for (int q = ct; q < nwork; q += NCT) {
+                for (int q = ct; q < nwork; q += NCTT) {
                     const Work it = work[q];
                     const int y = it.y;
                     double nig = it.gi, njg = it.gj, nim = it.mi, njm = it.mj;
@@ -768,7 +773,7 @@ k_select_fast(const int64_t *coff, const int32_t *members, const int64_t *goff, 
             if (more) warp_argmax_to(nbest, &wbest[wid]);
             __syncthreads();
             if (more) {
-                nbest = block_best(wbest);
+                nbest = block_best<NW>(wbest);
                 if (inext != i && inext != j)
                     cand_merge(nbest, cand_make_sparse(s_survg[par], s_survm[par], s_wn[par][0], surv));
                 if (t + 2 < e) {
@@ -792,7 +797,8 @@ k_select_fast(const int64_t *coff, const int32_t *members, const int64_t *goff, 
 
 pmmf_status gram_and_select(const Csr &A, const int32_t *pos, const int32_t *cl,
                             const StageClusters &cls, int64_t cmax, uint64_t seed, int64_t stage,
-                            StageRotations &rot, int32_t *elimflag, cudaStream_t st) {
+                            StageRotations &rot, int32_t *elimflag, cudaStream_t st,
+                            const int32_t *order, const uint64_t *useed) {
     const int64_t m = cls.m;
     DBuf<int64_t> goff;
     PMMF_TRY(goff.alloc(m + 1, st));
@@ -839,25 +845,30 @@ pmmf_status gram_and_select(const Csr &A, const int32_t *pos, const int32_t *cl,
         }
     }
     prof_begin(KF_SELECT, st);
+    // 256 threads (128 column threads) up to 512 coordinates, 512 threads
+    // (384 column threads) up to 1,536, the generic kernel beyond
     const int kpt = (int)((cmax + NCT - 1) / NCT);
-    if (kpt <= 4) {
-        auto launch = [&](auto kern) -> pmmf_status {
-            if (shf > 48 * 1024)
-                PMMF_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shf));
-            kern<<<(unsigned)m, SEL_THREADS, shf, st>>>(cls.coff.p, cls.members.p, goff.p, G.p, M.p,
-                                                        rot.roff.p, seed, stage, rot.rec.p, rot.lvl.p,
-                                                        rot.lvl_off.p, rot.nlev.p, elimflag);
-            return PMMF_OK;
-        };
-        if (kpt <= 1) PMMF_TRY(launch(k_select_fast<1>));
-        else if (kpt <= 2) PMMF_TRY(launch(k_select_fast<2>));
-        else PMMF_TRY(launch(k_select_fast<4>));
-    } else {
+    const int kpt512 = (int)((cmax + 383) / 384);
+    auto launch = [&](auto kern, int nt) -> pmmf_status {
+        if (shf > 48 * 1024)
+            PMMF_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shf));
+        kern<<<(unsigned)m, nt, shf, st>>>(cls.coff.p, cls.members.p, goff.p, G.p, M.p, rot.roff.p,
+                                           seed, stage, rot.rec.p, rot.lvl.p, rot.lvl_off.p,
+                                           rot.nlev.p, elimflag, order, useed);
+        return PMMF_OK;
+    };
+    if (kpt <= 1) PMMF_TRY(launch(k_select_fast<1, 256>, 256));
+    else if (kpt <= 2) PMMF_TRY(launch(k_select_fast<2, 256>, 256));
+    else if (kpt <= 4) PMMF_TRY(launch(k_select_fast<4, 256>, 256));
+    else if (kpt512 <= 2) PMMF_TRY(launch(k_select_fast<2, 512>, 512));
+    else if (kpt512 <= 4) PMMF_TRY(launch(k_select_fast<4, 512>, 512));
+    else {
         if (shb > 48 * 1024)
             PMMF_CUDA_TRY(cudaFuncSetAttribute(k_select, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shb));
         k_select<<<(unsigned)m, SEL_THREADS, shb, st>>>(cls.coff.p, cls.members.p, goff.p, G.p, M.p,
                                                         rot.roff.p, seed, stage, rot.rec.p, rot.lvl.p,
-                                                        rot.lvl_off.p, rot.nlev.p, elimflag);
+                                                        rot.lvl_off.p, rot.nlev.p, elimflag, order,
+                                                        useed);
     }
     prof_end(KF_SELECT, st, 0.0, sel_flops);
     PMMF_TRY(launched("select"));

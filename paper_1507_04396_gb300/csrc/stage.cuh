@@ -54,9 +54,13 @@ pmmf_status schedule_stage(const int64_t *coff, int64_t mm, int64_t s, int64_t c
 
 // Gram G^u and symmetric local block M^u of every cluster (dense c_u x c_u,
 // row-major at goff[u]) and the rotation search of Algorithm 2.
+// order (optional): launch position -> cluster, e.g. longest first; useed
+// (optional): per-cluster seeds, the draws then use cluster ordinal 0 (each
+// cluster searched as if it were the only cluster of its own factorization).
 pmmf_status gram_and_select(const Csr &A, const int32_t *pos, const int32_t *cl,
                             const StageClusters &cls, int64_t cmax, uint64_t seed, int64_t stage,
-                            StageRotations &rot, int32_t *elimflag, cudaStream_t st);
+                            StageRotations &rot, int32_t *elimflag, cudaStream_t st,
+                            const int32_t *order = nullptr, const uint64_t *useed = nullptr);
 
 // Blocked update A_p = (A Q^T)^T Q^T, residual accounting, H diagonal and
 // compaction to the surviving coordinates.
@@ -69,7 +73,7 @@ pmmf_status update_stage(const Csr &A, const int32_t *act, int64_t n, const int3
                          const int32_t *cl, const int32_t *loc, const StageClusters &cls,
                          int64_t cmax, const StageRotations &rot, const int32_t *elimflag,
                          int64_t stage, double *hdiag, double *contrib, UpdateOut &out,
-                         unsigned *status, cudaStream_t st);
+                         unsigned *status, cudaStream_t st, double *contrib_cl = nullptr);
 
 pmmf_status set_positions(const int32_t *act, int64_t s, int32_t *pos, cudaStream_t st);
 pmmf_status extract_core(const Csr &A, const int32_t *pos, int64_t s, double *core, double *hdiag,

@@ -54,6 +54,7 @@ struct RowArgs {
     double *oval;
     double *hdiag;
     double *contrib;
+    double *contrib_cl;        // optional: per-cluster residual (indexed by cl of the row)
     unsigned *status;
     int64_t *maxlen;
 };
@@ -75,6 +76,7 @@ __global__ void k_rows(RowArgs a) {
         int64_t nout = 0;
         int nseg = 0;
         int prev = -1;
+        double prow = 0.0;   // this row's residual terms (per-cluster accounting)
         for (;;) {
             int mu = INT_MAX;
             for (int64_t q = e0 + lane; q < e1; q += 32) {
@@ -124,16 +126,21 @@ __global__ void k_rows(RowArgs a) {
                 } else {
                     bool keep = false;
                     if (nz) {
+                        bool term = false;
                         if (yelim) {
                             if (g == y) {
                                 if (MODE == P2_WRITE) a.hdiag[y] = x;
                             } else {
-                                part = __fma_rn(x, x, part);
+                                term = true;
                             }
                         } else if (a.elimflag[g] == a.stage) {
-                            part = __fma_rn(x, x, part);
+                            term = true;
                         } else {
                             keep = true;
+                        }
+                        if (term) {
+                            if (a.contrib_cl) prow = __fma_rn(x, x, prow);
+                            else part = __fma_rn(x, x, part);
                         }
                     }
                     unsigned km = __ballot_sync(0xffffffffu, keep);
@@ -149,6 +156,10 @@ __global__ void k_rows(RowArgs a) {
             }
             __syncwarp();
             prev = mu;
+        }
+        if (MODE == P2_WRITE && a.contrib_cl) {
+            prow = warp_sum(prow);
+            if (lane == 0 && prow != 0.0) atomicAdd(a.contrib_cl + a.cl[y], prow);
         }
         if (MODE == P2_COUNT && !yelim && lane == 0) {
             a.ocnt[a.newrow[r]] = nout;
@@ -252,7 +263,7 @@ pmmf_status update_stage(const Csr &A, const int32_t *act, int64_t n, const int3
                          const int32_t *cl, const int32_t *loc, const StageClusters &cls,
                          int64_t cmax, const StageRotations &rot, const int32_t *elimflag,
                          int64_t stage, double *hdiag, double *contrib, UpdateOut &out,
-                         unsigned *status, cudaStream_t st) {
+                         unsigned *status, cudaStream_t st, double *contrib_cl) {
     (void)n;
     const int64_t s = A.rows;
     RowArgs a{};
@@ -271,6 +282,7 @@ pmmf_status update_stage(const Csr &A, const int32_t *act, int64_t n, const int3
     a.stage = (int32_t)stage;
     a.status = status;
     a.contrib = contrib;
+    a.contrib_cl = contrib_cl;
     a.hdiag = hdiag;
 
     // pass 1: V = A Q^T, scattered straight into the rows of W = V^T

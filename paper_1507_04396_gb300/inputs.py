@@ -198,6 +198,24 @@ def er_laplacian_batch(count: int = 4096, lo: int = 64, hi: int = 1024, seed: in
     return [er_laplacian(int(s), rng) for s in sizes]
 
 
+def blockdiag(mats):
+    """Stack independent matrices into one block-diagonal SymCSR; returns it and
+    the block offsets (block b spans coordinates off[b] .. off[b+1]-1)."""
+    off = np.zeros(len(mats) + 1, dtype=np.int64)
+    for b, m in enumerate(mats):
+        off[b + 1] = off[b] + m.n
+    nnz = np.array([len(m.val) for m in mats], dtype=np.int64)
+    eoff = np.concatenate([[0], np.cumsum(nnz)])
+    rowptr = np.zeros(off[-1] + 1, dtype=np.int64)
+    col = np.empty(eoff[-1], dtype=np.int32)
+    val = np.empty(eoff[-1])
+    for b, m in enumerate(mats):
+        rowptr[off[b] + 1:off[b + 1] + 1] = m.rowptr[1:] + eoff[b]
+        col[eoff[b]:eoff[b + 1]] = m.col + off[b]
+        val[eoff[b]:eoff[b + 1]] = m.val
+    return SymCSR(int(off[-1]), rowptr, col, val, None, f"blockdiag({len(mats)})"), off
+
+
 def block_pairs(nblocks: int, k: int = 2, seed: int = 5) -> SymCSR:
     """Direct sum of random SPD k x k blocks, symmetrically permuted.
 

@@ -66,7 +66,7 @@ EXPORTS = ["pmmf_factor", "pmmf_apply", "pmmf_solve_precond", "pmmf_free", "pmmf
            "pmmf_get_info", "pmmf_get_stage_info", "pmmf_get_stage_clusters",
            "pmmf_get_stage_rotations", "pmmf_get_h", "pmmf_get_stage_matrix",
            "pmmf_launch_count", "pmmf_apply_backward", "pmmf_get_angles", "pmmf_set_angles",
-           "pmmf_set_h"]
+           "pmmf_set_h", "pmmf_factor_blockdiag", "pmmf_factor_batched", "pmmf_get_batch"]
 
 _lib = None
 
@@ -115,6 +115,13 @@ def load(path: str = LIB_PATH):
     L.pmmf_set_angles.argtypes = [vp, vp, vp]
     L.pmmf_set_h.restype = i32
     L.pmmf_set_h.argtypes = [vp, vp, vp, vp]
+    L.pmmf_factor_blockdiag.restype = i32
+    L.pmmf_factor_blockdiag.argtypes = [C.POINTER(Matrix), i64, vp, C.POINTER(Params),
+                                        C.POINTER(vp), vp]
+    L.pmmf_factor_batched.restype = i32
+    L.pmmf_factor_batched.argtypes = [i64, vp, C.POINTER(Params), C.POINTER(vp), vp]
+    L.pmmf_get_batch.restype = i32
+    L.pmmf_get_batch.argtypes = [vp, vp, vp, vp, vp, vp]
     L.pmmf_profile_begin.restype = i32
     L.pmmf_profile_begin.argtypes = [C.c_uint]
     L.pmmf_profile_end.restype = i32
@@ -315,6 +322,8 @@ class Factorization:
         return cl[:nr], kk[:nr], idx[:nr], O[:nr], el[:nr]
 
     def h(self):
+        if self.batch()["nmat"] > 1:
+            raise ValueError("a batch handle's H comes in blocks: use h_blocks()")
         i = self.info()
         hd = np.zeros(i.n)
         ci = np.zeros(i.core_size, dtype=np.int32)
@@ -342,6 +351,29 @@ class Factorization:
         nrhs = 1 if x.dim() == 1 else x.shape[1]
         pmmf_apply(self.handle, op, x, y, nrhs, nrhs, stream)
         return y
+
+    def batch(self) -> dict:
+        """nmat, core_stride, block_off, errors, core_dim of a batch handle."""
+        nm, cs = C.c_int64(), C.c_int64()
+        _check(load().pmmf_get_batch(self.handle, C.byref(nm), C.byref(cs), None, None, None))
+        bo = np.zeros(nm.value + 1, dtype=np.int64)
+        err = np.zeros(nm.value)
+        cd = np.zeros(nm.value, dtype=np.int32)
+        _check(load().pmmf_get_batch(self.handle, None, None, bo.ctypes.data, err.ctypes.data,
+                                     cd.ctypes.data))
+        return dict(nmat=nm.value, core_stride=cs.value, block_off=bo, errors=err, core_dim=cd)
+
+    def h_blocks(self):
+        """(hdiag, core_idx [nmat, stride], core [nmat, stride, stride]) of any handle."""
+        b = self.batch()
+        i = self.info()
+        ns = b["nmat"] * b["core_stride"]
+        hd = np.zeros(i.n)
+        ci = np.zeros(max(ns, 1), dtype=np.int32)
+        core = np.zeros(max(ns * b["core_stride"], 1))
+        _check(load().pmmf_get_h(self.handle, hd.ctypes.data, ci.ctypes.data, core.ctypes.data))
+        st = b["core_stride"]
+        return hd, ci[:ns].reshape(b["nmat"], st), core[:ns * st].reshape(b["nmat"], st, st)
 
     # ---- differentiation (selections fixed)
 
@@ -410,6 +442,33 @@ def factor(a, *, k=2, eta=0.5, cluster_size=256, core_size=16, seed=0, max_stage
                  1 if record_stages else 0)
     h = pmmf_factor(m, prm, stream)
     return Factorization(h, k)
+
+
+def factor_blockdiag(a, block_off, *, k=2, eta=0.5, core_size=16, seed=0, stream=None
+                     ) -> Factorization:
+    """Batched factorization of a block-diagonal matrix (block b spans
+    coordinates block_off[b] .. block_off[b+1]-1), each block on its own."""
+    m, keep = make_matrix(a)
+    bo = np.ascontiguousarray(block_off, dtype=np.int64)
+    prm = Params(k, eta, 2, core_size, seed, 0, 10, None, 0, HOST, 0)
+    h = C.c_void_p()
+    _check(load().pmmf_factor_blockdiag(C.byref(m), len(bo) - 1, bo.ctypes.data, C.byref(prm),
+                                        C.byref(h), _stream(stream)))
+    return Factorization(h.value, k)
+
+
+def factor_batched(mats, *, k=2, eta=0.5, core_size=16, seed=0, stream=None) -> Factorization:
+    """Batched factorization of separate host CSR matrices (pmmf_factor_batched)."""
+    ms, keep = [], []
+    for a in mats:
+        m, kp = make_matrix(a)
+        ms.append(m)
+        keep += kp
+    arr = (Matrix * len(ms))(*ms)
+    prm = Params(k, eta, 2, core_size, seed, 0, 10, None, 0, HOST, 0)
+    h = C.c_void_p()
+    _check(load().pmmf_factor_batched(len(ms), arr, C.byref(prm), C.byref(h), _stream(stream)))
+    return Factorization(h.value, k)
 
 
 # ---------------------------------------------------------------- autograd
