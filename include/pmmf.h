@@ -196,7 +196,9 @@ pmmf_status pmmf_solve_precond(const pmmf_handle *f, const pmmf_matrix *A, const
  * and location accepted by pmmf_factor) whose diagonal block b spans the
  * coordinates block_off[b] .. block_off[b+1]-1 (block_off: HOST, nmat + 1
  * entries, strictly increasing from 0 to n).  An entry outside its diagonal
- * block gives INVALID_ARG.  params.coords must be NULL and max_stages 0.
+ * block gives INVALID_ARG.  params.coords must be NULL and max_stages 0;
+ * params.cluster_size is not used (each matrix is one cluster) but must still
+ * be >= k.
  * The handle acts on the whole block-diagonal operator: pmmf_apply and
  * pmmf_solve_precond take n x nrhs vectors (the matrices' vectors stacked).
  * pmmf_get_h then returns core_idx[nmat * core_stride] (unused slots -1) and

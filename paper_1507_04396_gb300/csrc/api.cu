@@ -161,7 +161,6 @@ pmmf_status check_params(const pmmf_matrix *A, const pmmf_params *p) {
         return fail(PMMF_ERR_INVALID_ARG, "coord_dim must be 1, 2 or 3");
     if (p->coords && p->coords_location != PMMF_HOST && p->coords_location != PMMF_DEVICE)
         return fail(PMMF_ERR_INVALID_ARG, "bad coords location");
-    if (p->k != 2) return fail(PMMF_ERR_UNSUPPORTED, "this build factors with k = 2 (Givens) only");
     return PMMF_OK;
 }
 
@@ -179,6 +178,11 @@ void build_views(pmmf_handle *h) {
         v.lvl_off = S.rot.lvl_off.p;
         v.nlev = S.rot.nlev.p;
         v.lvlrot = S.rot.lvl.p;
+        v.K = S.rot.K;
+        v.kidx = S.rot.kidx.p;
+        v.kkv = S.rot.kk.p;
+        v.lvlidx = S.rot.lvlidx.p;
+        v.kO = S.rot.kO.p;
         h->views.push_back(v);
     }
 }
@@ -280,10 +284,11 @@ pmmf_status factor_impl(const pmmf_matrix *A, const pmmf_params *prm, pmmf_handl
             PMMF_CUDA_TRY(cudaStreamSynchronize(st));
             for (int64_t u = 0; u < S.m; ++u) S.cmax = std::max(S.cmax, hc[u + 1] - hc[u]);
         }
-        PMMF_TRY(gram_and_select(cur, pos.p, cl.p, S.cls, S.cmax, prm->seed, p, S.rot,
-                                 elimflag.p, st));
-        UpdateOut up;
+        S.rot.K = prm->k;
         PMMF_CUDA_TRY(cudaMemsetAsync(status.p, 0, sizeof(unsigned), st));
+        PMMF_TRY(gram_and_select(cur, pos.p, cl.p, S.cls, S.cmax, prm->seed, p, S.rot,
+                                 elimflag.p, st, nullptr, nullptr, status.p));
+        UpdateOut up;
         PMMF_TRY(update_stage(cur, act.p, n, pos.p, cl.p, loc.p, S.cls, S.cmax, S.rot,
                               elimflag.p, p, h->hdiag.p, contribs.p + (p - 1), up, status.p, st));
         {
@@ -295,6 +300,8 @@ pmmf_status factor_impl(const pmmf_matrix *A, const pmmf_params *prm, pmmf_handl
                                           cudaMemcpyDeviceToHost, st));
             PMMF_CUDA_TRY(cudaStreamSynchronize(st));
             if (hs & ST_ROW_TOO_LONG) return fail(PMMF_ERR_UNSUPPORTED, "update: output row too long");
+            if (hs & ST_NOT_CONVERGED)
+                return fail(PMMF_ERR_NOT_CONVERGED, "k x k Jacobi did not converge in 32 sweeps");
             for (int32_t v : nl) ml = std::max(ml, v);
             S.max_levels = ml;
         }
@@ -494,12 +501,13 @@ pmmf_status factor_batch_impl(const pmmf_matrix *A, const std::vector<int64_t> &
         S.m = m;
         S.nrot = roff[m];
         S.rot.nrot = roff[m];
+        S.rot.K = prm->k;
+        PMMF_CUDA_TRY(cudaMemsetAsync(status.p, 0, sizeof(unsigned), st));
         PMMF_TRY(gram_and_select(cur, pos.p, cl.p, S.cls, S.cmax, prm->seed, p, S.rot,
-                                 elimflag.p, st, order_d.p, useed_d.p));
+                                 elimflag.p, st, order_d.p, useed_d.p, status.p));
         DBuf<double> ccl;
         PMMF_TRY(ccl.zeros(m, st));
         UpdateOut up;
-        PMMF_CUDA_TRY(cudaMemsetAsync(status.p, 0, sizeof(unsigned), st));
         PMMF_TRY(update_stage(cur, act.p, n, pos.p, cl.p, loc.p, S.cls, S.cmax, S.rot, elimflag.p,
                               p, h->hdiag.p, contrib1.p, up, status.p, st, ccl.p));
         {
@@ -511,6 +519,8 @@ pmmf_status factor_batch_impl(const pmmf_matrix *A, const std::vector<int64_t> &
             PMMF_CUDA_TRY(cudaMemcpyAsync(cc.data(), ccl.p, sizeof(double) * cc.size(), cudaMemcpyDeviceToHost, st));
             PMMF_CUDA_TRY(cudaStreamSynchronize(st));
             if (hs & ST_ROW_TOO_LONG) return fail(PMMF_ERR_UNSUPPORTED, "update: output row too long");
+            if (hs & ST_NOT_CONVERGED)
+                return fail(PMMF_ERR_NOT_CONVERGED, "k x k Jacobi did not converge in 32 sweeps");
             int32_t ml = 0;
             for (int32_t v : nl) ml = std::max(ml, v);
             S.max_levels = ml;
@@ -715,10 +725,33 @@ pmmf_status pmmf_get_stage_rotations(const pmmf_handle *f, int p, int32_t *clust
     const int K = f->k;
     std::vector<int64_t> coff((size_t)s.m + 1), roff((size_t)s.m + 1);
     std::vector<int32_t> mem((size_t)s.s);
-    std::vector<RotRec> rec((size_t)std::max<int64_t>(s.nrot, 1));
     PMMF_CUDA_TRY(cudaMemcpy(coff.data(), s.cls.coff.p, sizeof(int64_t) * coff.size(), cudaMemcpyDeviceToHost));
     PMMF_CUDA_TRY(cudaMemcpy(roff.data(), s.rot.roff.p, sizeof(int64_t) * roff.size(), cudaMemcpyDeviceToHost));
     PMMF_CUDA_TRY(cudaMemcpy(mem.data(), s.cls.members.p, sizeof(int32_t) * mem.size(), cudaMemcpyDeviceToHost));
+    if (K > 2) {
+        const size_t nr = (size_t)std::max<int64_t>(s.nrot, 1);
+        std::vector<int32_t> ki(nr * K), kv(nr), ke(nr);
+        std::vector<double> ko(nr * K * K);
+        if (s.nrot > 0) {
+            PMMF_CUDA_TRY(cudaMemcpy(ki.data(), s.rot.kidx.p, sizeof(int32_t) * (size_t)(s.nrot * K), cudaMemcpyDeviceToHost));
+            PMMF_CUDA_TRY(cudaMemcpy(kv.data(), s.rot.kk.p, sizeof(int32_t) * (size_t)s.nrot, cudaMemcpyDeviceToHost));
+            PMMF_CUDA_TRY(cudaMemcpy(ke.data(), s.rot.kel.p, sizeof(int32_t) * (size_t)s.nrot, cudaMemcpyDeviceToHost));
+            PMMF_CUDA_TRY(cudaMemcpy(ko.data(), s.rot.kO.p, sizeof(double) * (size_t)(s.nrot * K * K), cudaMemcpyDeviceToHost));
+        }
+        for (int64_t u = 0; u < s.m; ++u)
+            for (int64_t r = roff[u]; r < roff[u + 1]; ++r) {
+                if (cluster) cluster[r] = (int32_t)u;
+                if (kk) kk[r] = kv[r];
+                if (idx)
+                    for (int a = 0; a < K; ++a)
+                        idx[r * K + a] = ki[r * K + a] >= 0 ? mem[coff[u] + ki[r * K + a]] : -1;
+                if (O)
+                    for (int a = 0; a < K * K; ++a) O[r * K * K + a] = ko[r * K * K + a];
+                if (elim) elim[r] = mem[coff[u] + ke[r]];
+            }
+        return PMMF_OK;
+    }
+    std::vector<RotRec> rec((size_t)std::max<int64_t>(s.nrot, 1));
     if (s.nrot > 0)
         PMMF_CUDA_TRY(cudaMemcpy(rec.data(), s.rot.rec.p, sizeof(RotRec) * (size_t)s.nrot, cudaMemcpyDeviceToHost));
     for (int64_t u = 0; u < s.m; ++u) {

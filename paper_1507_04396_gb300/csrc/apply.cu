@@ -11,6 +11,7 @@
 //            definite, so no pivoting is needed and a non-positive pivot means
 //            "not SPD").
 #include "apply.cuh"
+#include "rotmath.cuh"
 
 namespace pmmf {
 
@@ -23,7 +24,8 @@ template <bool TRANSPOSE>
 __global__ void __launch_bounds__(AP_THREADS)
 k_apply_stage(const int64_t *coff, const int32_t *members, const int64_t *roff,
               const int32_t *lvl_off, const int32_t *nlev, const Rot2 *lvlrot, double *x,
-              int64_t ld, int64_t r0, int nr) {
+              int64_t ld, int64_t r0, int nr, int K, const int32_t *kidx, const int32_t *kkv,
+              const int32_t *lvlidx, const double *kO) {
     extern __shared__ double sx[];
     const int64_t u = blockIdx.x;
     const int64_t base = coff[u];
@@ -41,12 +43,31 @@ k_apply_stage(const int64_t *coff, const int32_t *members, const int64_t *roff,
         const int b0 = lo[L], cnt = lo[L + 1] - b0;
         for (int q = threadIdx.x; q < cnt * nr; q += AP_THREADS) {
             const int t = q / nr, r = q - t * nr;
-            const Rot2 rt = lvlrot[b0 + t];
-            double a = sx[rt.li * nr + r], b = sx[rt.lj * nr + r], na, nb;
-            if (TRANSPOSE) rot_pair_t(rt.c, rt.s, a, b, na, nb);
-            else rot_pair(rt.c, rt.s, a, b, na, nb);
-            sx[rt.li * nr + r] = na;
-            sx[rt.lj * nr + r] = nb;
+            if (K == 2) {
+                const Rot2 rt = lvlrot[b0 + t];
+                double a = sx[rt.li * nr + r], b = sx[rt.lj * nr + r], na, nb;
+                if (TRANSPOSE) rot_pair_t(rt.c, rt.s, a, b, na, nb);
+                else rot_pair(rt.c, rt.s, a, b, na, nb);
+                sx[rt.li * nr + r] = na;
+                sx[rt.lj * nr + r] = nb;
+            } else {
+                // x_T' = O x_T, or x_T = O^T x_T' for the transpose (chains
+                // over the block's rows of O^T, i.e. its columns)
+                const int64_t tt = lvlidx[b0 + t];
+                const int kk = kkv[tt];
+                const int32_t *T = kidx + tt * K;
+                const double *O = kO + tt * K * K;
+                double in[8], out[8], Ot[64];
+                for (int a = 0; a < kk; ++a) in[a] = sx[T[a] * nr + r];
+                if (TRANSPOSE) {
+                    for (int a = 0; a < kk; ++a)
+                        for (int b = 0; b < kk; ++b) Ot[a * kk + b] = O[b * kk + a];
+                    for (int a = 0; a < kk; ++a) out[a] = rot_row(Ot, kk, a, in);
+                } else {
+                    for (int a = 0; a < kk; ++a) out[a] = rot_row(O, kk, a, in);
+                }
+                for (int a = 0; a < kk; ++a) sx[T[a] * nr + r] = out[a];
+            }
         }
         __syncthreads();
     }
@@ -298,12 +319,14 @@ pmmf_status apply_rotations(const ApplyStages &S, bool transpose, double *x, int
                 if (sh > 48 * 1024)
                     PMMF_CUDA_TRY(cudaFuncSetAttribute(k_apply_stage<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh));
                 k_apply_stage<true><<<(unsigned)a.m, AP_THREADS, sh, st>>>(
-                    a.coff, a.members, a.roff, a.lvl_off, a.nlev, a.lvlrot, x, ld, r0, nr);
+                    a.coff, a.members, a.roff, a.lvl_off, a.nlev, a.lvlrot, x, ld, r0, nr, a.K,
+                    a.kidx, a.kkv, a.lvlidx, a.kO);
             } else {
                 if (sh > 48 * 1024)
                     PMMF_CUDA_TRY(cudaFuncSetAttribute(k_apply_stage<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh));
                 k_apply_stage<false><<<(unsigned)a.m, AP_THREADS, sh, st>>>(
-                    a.coff, a.members, a.roff, a.lvl_off, a.nlev, a.lvlrot, x, ld, r0, nr);
+                    a.coff, a.members, a.roff, a.lvl_off, a.nlev, a.lvlrot, x, ld, r0, nr, a.K,
+                    a.kidx, a.kkv, a.lvlidx, a.kO);
             }
             // the stage's coordinates read and written once per right-hand side,
             // their ids, and the rotations (24 B each) with their level offsets

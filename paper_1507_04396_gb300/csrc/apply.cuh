@@ -15,6 +15,10 @@ struct ApplyStage {
     const int32_t *lvl_off = nullptr;
     const int32_t *nlev = nullptr;
     const Rot2 *lvlrot = nullptr;
+    // k >= 3 (see StageRotations)
+    int K = 2;
+    const int32_t *kidx = nullptr, *kkv = nullptr, *lvlidx = nullptr;
+    const double *kO = nullptr;
 };
 using ApplyStages = std::vector<ApplyStage>;
 

@@ -74,6 +74,7 @@ enum : unsigned {
     ST_ROW_TOO_LONG = 8u,
     ST_NOT_SPD = 16u,
     ST_CLUSTER_TOO_BIG = 32u,
+    ST_NOT_CONVERGED = 64u,
 };
 
 // ---------------------------------------------------------------- rotations

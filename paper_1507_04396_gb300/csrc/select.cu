@@ -21,6 +21,7 @@
 #include <vector>
 
 #include "common.cuh"
+#include "rotmath.cuh"
 #include "stage.cuh"
 
 namespace pmmf {
@@ -39,40 +40,6 @@ __device__ __forceinline__ uint64_t draw(uint64_t seed, uint64_t p, uint64_t u, 
     h = mix1(h ^ p);
     h = mix1(h ^ u);
     return mix1(h ^ t);
-}
-
-// Smaller-angle Jacobi rotation zeroing the off-diagonal of q [[a,b],[b,d]] q^T:
-// h = d - a, g = 2b (scaled by an exact power of two when huge or tiny),
-// q = |h| + sqrt(h^2 + g^2), den = sqrt(q^2 + g^2), c = q/den, s = sign(h) g/den.
-// Comparisons, |.| and the sign test act on the bits (integer pipe): for finite
-// doubles the magnitude bits order like the magnitudes.
-__device__ void jacobi2(double a, double b, double d, double &c, double &s) {
-    const unsigned long long ABS = 0x7fffffffffffffffull;
-    if ((__double_as_longlong(b) & ABS) == 0) {
-        c = 1.0;
-        s = 0.0;
-        return;
-    }
-    double h = __dsub_rn(d, a);
-    double g = __dmul_rn(2.0, b);
-    const unsigned long long hm = __double_as_longlong(h) & ABS, gm = __double_as_longlong(g) & ABS;
-    const unsigned long long mm = hm > gm ? hm : gm;
-    if (mm > (unsigned long long)__double_as_longlong(0x1p500)) {
-        h = __dmul_rn(h, 0x1p-600);
-        g = __dmul_rn(g, 0x1p-600);
-    } else if (mm < (unsigned long long)__double_as_longlong(0x1p-500)) {
-        h = __dmul_rn(h, 0x1p600);
-        g = __dmul_rn(g, 0x1p600);
-    }
-    const unsigned long long hb = __double_as_longlong(h);
-    const double habs = __longlong_as_double(hb & ABS);
-    const bool hnonneg = (hb >> 63) == 0 || (hb & ABS) == 0;   // h >= 0, -0 included
-    const double g2 = __dmul_rn(g, g);
-    const double r = __dsqrt_rn(__dadd_rn(__dmul_rn(h, h), g2));
-    const double q = __dadd_rn(habs, r);
-    const double den = __dsqrt_rn(__dadd_rn(__dmul_rn(q, q), g2));
-    c = __ddiv_rn(q, den);
-    s = __ddiv_rn(hnonneg ? g : -g, den);
 }
 
 // New 2x2 block of q X q^T for symmetric X with X_ii = a, X_ij = X_ji = b,
@@ -798,7 +765,7 @@ k_select_fast(const int64_t *coff, const int32_t *members, const int64_t *goff, 
 pmmf_status gram_and_select(const Csr &A, const int32_t *pos, const int32_t *cl,
                             const StageClusters &cls, int64_t cmax, uint64_t seed, int64_t stage,
                             StageRotations &rot, int32_t *elimflag, cudaStream_t st,
-                            const int32_t *order, const uint64_t *useed) {
+                            const int32_t *order, const uint64_t *useed, unsigned *status) {
     const int64_t m = cls.m;
     DBuf<int64_t> goff;
     PMMF_TRY(goff.alloc(m + 1, st));
@@ -820,6 +787,14 @@ pmmf_status gram_and_select(const Csr &A, const int32_t *pos, const int32_t *cl,
     prof_end(KF_GRAM, st, 12.0 * (double)A.nnz + 8.0 * (double)s + 16.0 * (double)gtot, 0.0);
     PMMF_TRY(launched("gram"));
 
+    if (rot.K > 2) {
+        if (!status) {
+            set_error("k-point search needs a status word");
+            return PMMF_ERR_INVALID_ARG;
+        }
+        return select_kpoint(cls, cmax, goff.p, G.p, M.p, seed, stage, rot, elimflag, st, order,
+                             useed, status);
+    }
     PMMF_TRY(rot.rec.alloc(rot.nrot > 0 ? rot.nrot : 1, st));
     PMMF_TRY(rot.lvl.alloc(rot.nrot > 0 ? rot.nrot : 1, st));
     PMMF_TRY(rot.lvl_off.alloc(rot.nrot + m + 1, st));

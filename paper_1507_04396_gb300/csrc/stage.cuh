@@ -35,11 +35,18 @@ struct Csr {
 struct StageRotations {
     int64_t nrot = 0;
     int32_t max_levels = 0;
+    int K = 2;                // rotation order k
     DBuf<int64_t> roff;       // m + 1: cluster u owns [roff[u], roff[u+1])
-    DBuf<RotRec> rec;         // step order (export)
-    DBuf<Rot2> lvl;           // grouped by dependency level inside each cluster
     DBuf<int32_t> lvl_off;    // cluster u: entries [roff[u] + u, roff[u] + u + nlev_u + 1)
     DBuf<int32_t> nlev;       // m
+    // k = 2
+    DBuf<RotRec> rec;         // step order (export)
+    DBuf<Rot2> lvl;           // grouped by dependency level inside each cluster
+    // k >= 3, step order: tuple (local indices, K slots, -1 unused), kk x kk
+    // block (K*K slots, stride kk inside), tuple size, eliminated local index,
+    // level; lvlidx = the step-order rotation at each level-grouped slot
+    DBuf<int32_t> kidx, kk, kel, klvl, lvlidx;
+    DBuf<double> kO;
 };
 
 pmmf_status quantize_points(const double *coords, int64_t n, int dim, int32_t *q, uint64_t *code,
@@ -57,10 +64,18 @@ pmmf_status schedule_stage(const int64_t *coff, int64_t mm, int64_t s, int64_t c
 // order (optional): launch position -> cluster, e.g. longest first; useed
 // (optional): per-cluster seeds, the draws then use cluster ordinal 0 (each
 // cluster searched as if it were the only cluster of its own factorization).
+// rot.K selects Givens (2) or k-point (>= 3) rotations; status receives
+// ST_NOT_CONVERGED when a k x k Jacobi did not converge.
 pmmf_status gram_and_select(const Csr &A, const int32_t *pos, const int32_t *cl,
                             const StageClusters &cls, int64_t cmax, uint64_t seed, int64_t stage,
                             StageRotations &rot, int32_t *elimflag, cudaStream_t st,
-                            const int32_t *order = nullptr, const uint64_t *useed = nullptr);
+                            const int32_t *order = nullptr, const uint64_t *useed = nullptr,
+                            unsigned *status = nullptr);
+// The k >= 3 search on Gram blocks already formed (selectk.cu).
+pmmf_status select_kpoint(const StageClusters &cls, int64_t cmax, const int64_t *goff, double *G,
+                          double *M, uint64_t seed, int64_t stage, StageRotations &rot,
+                          int32_t *elimflag, cudaStream_t st, const int32_t *order,
+                          const uint64_t *useed, unsigned *status);
 
 // Blocked update A_p = (A Q^T)^T Q^T, residual accounting, H diagonal and
 // compaction to the surviving coordinates.

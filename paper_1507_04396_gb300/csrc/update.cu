@@ -16,6 +16,7 @@
 #include <climits>
 
 #include "common.cuh"
+#include "rotmath.cuh"
 #include "stage.cuh"
 
 namespace pmmf {
@@ -37,6 +38,9 @@ struct RowArgs {
     const int64_t *roff;
     const int32_t *lvl_off, *nlev;
     const Rot2 *lvlrot;
+    int K;                     // k >= 3: tuples, blocks and level slots below
+    const int32_t *kidx, *kkv, *lvlidx;
+    const double *kO;
     int64_t cmax;
     int outcap;
     // pass 1
@@ -98,14 +102,34 @@ __global__ void k_rows(RowArgs a) {
             const int32_t *lo = a.lvl_off + a.roff[mu] + mu;
             const int nl = a.nlev[mu];
             for (int L = 0; L < nl; ++L) {
-                for (int idx = lo[L] + lane; idx < lo[L + 1]; idx += 32) {
-                    Rot2 q = a.lvlrot[idx];
-                    double vi = dense[q.li], vj = dense[q.lj];
-                    if (nonzero_bits(vi) || nonzero_bits(vj)) {
-                        double ni, nj;
-                        rot_pair(q.c, q.s, vi, vj, ni, nj);
-                        dense[q.li] = ni;
-                        dense[q.lj] = nj;
+                if (a.K == 2) {
+                    for (int idx = lo[L] + lane; idx < lo[L + 1]; idx += 32) {
+                        Rot2 q = a.lvlrot[idx];
+                        double vi = dense[q.li], vj = dense[q.lj];
+                        if (nonzero_bits(vi) || nonzero_bits(vj)) {
+                            double ni, nj;
+                            rot_pair(q.c, q.s, vi, vj, ni, nj);
+                            dense[q.li] = ni;
+                            dense[q.lj] = nj;
+                        }
+                    }
+                } else {
+                    for (int idx = lo[L] + lane; idx < lo[L + 1]; idx += 32) {
+                        const int64_t t = a.lvlidx[idx];
+                        const int kk = a.kkv[t];
+                        const int32_t *T = a.kidx + t * a.K;
+                        double in[8];
+                        bool nz = false;
+                        for (int q = 0; q < kk; ++q) {
+                            in[q] = dense[T[q]];
+                            nz |= nonzero_bits(in[q]);
+                        }
+                        if (nz) {
+                            const double *O = a.kO + t * a.K * a.K;
+                            double out[8];
+                            for (int q = 0; q < kk; ++q) out[q] = rot_row(O, kk, q, in);
+                            for (int q = 0; q < kk; ++q) dense[T[q]] = out[q];
+                        }
                     }
                 }
                 __syncwarp();
@@ -277,6 +301,11 @@ pmmf_status update_stage(const Csr &A, const int32_t *act, int64_t n, const int3
     a.lvl_off = rot.lvl_off.p;
     a.nlev = rot.nlev.p;
     a.lvlrot = rot.lvl.p;
+    a.K = rot.K;
+    a.kidx = rot.kidx.p;
+    a.kkv = rot.kk.p;
+    a.lvlidx = rot.lvlidx.p;
+    a.kO = rot.kO.p;
     a.cmax = cmax;
     a.elimflag = elimflag;
     a.stage = (int32_t)stage;

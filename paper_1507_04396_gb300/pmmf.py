@@ -363,6 +363,13 @@ class Factorization:
                                      cd.ctypes.data))
         return dict(nmat=nm.value, core_stride=cs.value, block_off=bo, errors=err, core_dim=cd)
 
+    def hdiag(self, out=None):
+        """The diagonal of H (host float64 array of n)."""
+        n = self.info().n
+        hd = np.empty(n) if out is None else out
+        _check(load().pmmf_get_h(self.handle, hd.ctypes.data, None, None))
+        return hd
+
     def h_blocks(self):
         """(hdiag, core_idx [nmat, stride], core [nmat, stride, stride]) of any handle."""
         b = self.batch()
@@ -450,7 +457,7 @@ def factor_blockdiag(a, block_off, *, k=2, eta=0.5, core_size=16, seed=0, stream
     coordinates block_off[b] .. block_off[b+1]-1), each block on its own."""
     m, keep = make_matrix(a)
     bo = np.ascontiguousarray(block_off, dtype=np.int64)
-    prm = Params(k, eta, 2, core_size, seed, 0, 10, None, 0, HOST, 0)
+    prm = Params(k, eta, k, core_size, seed, 0, 10, None, 0, HOST, 0)
     h = C.c_void_p()
     _check(load().pmmf_factor_blockdiag(C.byref(m), len(bo) - 1, bo.ctypes.data, C.byref(prm),
                                         C.byref(h), _stream(stream)))
@@ -465,7 +472,7 @@ def factor_batched(mats, *, k=2, eta=0.5, core_size=16, seed=0, stream=None) -> 
         ms.append(m)
         keep += kp
     arr = (Matrix * len(ms))(*ms)
-    prm = Params(k, eta, 2, core_size, seed, 0, 10, None, 0, HOST, 0)
+    prm = Params(k, eta, k, core_size, seed, 0, 10, None, 0, HOST, 0)
     h = C.c_void_p()
     _check(load().pmmf_factor_batched(len(ms), arr, C.byref(prm), C.byref(h), _stream(stream)))
     return Factorization(h.value, k)

@@ -58,7 +58,7 @@ def test_invalid_parameters_rejected_without_gpu(lib):
         assert st == pmmf.ERR_INVALID_ARG
         assert h.value is None
         assert lib.pmmf_last_error()
-    prm = pmmf.Params(3, 0.5, 16, 4, 0, 0, 10, None, 0, 0, 0)
+    prm = pmmf.Params(9, 0.5, 16, 4, 0, 0, 10, None, 0, 0, 0)    # k > 8
     h = C.c_void_p()
-    assert lib.pmmf_factor(C.byref(m), C.byref(prm), C.byref(h), None) == pmmf.ERR_UNSUPPORTED
+    assert lib.pmmf_factor(C.byref(m), C.byref(prm), C.byref(h), None) == pmmf.ERR_INVALID_ARG
     lib.pmmf_free(None)   # NULL-safe

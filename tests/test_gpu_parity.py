@@ -164,8 +164,8 @@ def test_rejects_bad_input():
         pm.factor(I.SymCSR(a.n, a.rowptr, a.col, val), k=2, eta=0.5, cluster_size=32, core_size=4)
     assert e.value.status == pm.ERR_NONFINITE
     with pytest.raises(pm.PmmfError) as e:
-        pm.factor(a, k=3, eta=0.5, cluster_size=32, core_size=4)
-    assert e.value.status == pm.ERR_UNSUPPORTED
+        pm.factor(a, k=9, eta=0.5, cluster_size=32, core_size=4)
+    assert e.value.status == pm.ERR_INVALID_ARG
     with pytest.raises(pm.PmmfError) as e:
         pm.factor(a, k=2, eta=1.5, cluster_size=32, core_size=4)
     assert e.value.status == pm.ERR_INVALID_ARG
