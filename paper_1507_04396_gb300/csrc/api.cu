@@ -915,16 +915,34 @@ pmmf_status pmmf_solve_precond(const pmmf_handle *fc, const pmmf_matrix *A, cons
     dA.v = M.val.p;
     PMMF_TRY(ensure_inverse(f, st));
 
-    DBuf<double> r, z, pv, qv, sc, part;
-    DBuf<int32_t> done;
+    DBuf<double> r, z, pv, qv, sc, part, zc;
+    DBuf<int32_t> done, itd;
     PMMF_TRY(r.alloc(n * nr, st));
     PMMF_TRY(z.alloc(n * nr, st));
     PMMF_TRY(pv.alloc(n * nr, st));
     PMMF_TRY(qv.alloc(n * nr, st));
-    PMMF_TRY(sc.zeros(5 * 8, st));          // rz, pq, rr, rznew, bb
+    PMMF_TRY(sc.zeros(8 * 8, st));          // rz, pq, rr, rznew, bb, bnorm, alpha, beta
     PMMF_TRY(part.alloc(dot_partial_size(nr), st));
     PMMF_TRY(done.zeros(8, st));
+    PMMF_TRY(itd.zeros(9, st));             // iterations per column, then the counter
+    PMMF_TRY(zc.alloc(std::max<int64_t>(f->nblk * f->bs * nr, 1), st));
     double *rz = sc.p, *pq = sc.p + 8, *rr = sc.p + 16, *rzn = sc.p + 24, *bb = sc.p + 32;
+    double *bnorm = sc.p + 40, *alpha = sc.p + 48, *beta = sc.p + 56;
+    const HData H = hdata(f);
+    // one PCG iteration (Sec. 4 with M^{-1} = U^T H^{-1} U applied matrix-free)
+    auto body = [&](cudaStream_t s) -> pmmf_status {
+        PMMF_TRY(spmv(dA, pv.p, qv.p, nr, s));
+        PMMF_TRY(dots(pv.p, qv.p, n, nr, pq, part.p, s));
+        PMMF_TRY(cg_update_xr(x, r.p, pv.p, qv.p, n, nr, rz, pq, done.p, alpha, s));
+        PMMF_TRY(dots(r.p, r.p, n, nr, rr, part.p, s));
+        PMMF_TRY(cg_check(rr, bnorm, rtol, nr, done.p, itd.p, itd.p + 8, s));
+        PMMF_CUDA_TRY(cudaMemcpyAsync(z.p, r.p, sizeof(double) * (size_t)(n * nr), cudaMemcpyDeviceToDevice, s));
+        PMMF_TRY(apply_rotations(f->views, false, z.p, nr, nr, s));
+        PMMF_TRY(apply_h_scratch(H, true, z.p, nr, nr, zc.p, s));
+        PMMF_TRY(apply_rotations(f->views, true, z.p, nr, nr, s));
+        PMMF_TRY(dots(r.p, z.p, n, nr, rzn, part.p, s));
+        return cg_update_p(pv.p, z.p, n, nr, rzn, rz, done.p, beta, s);
+    };
     PMMF_CUDA_TRY(cudaMemsetAsync(x, 0, sizeof(double) * (size_t)(n * nr), st));
     PMMF_CUDA_TRY(cudaMemcpyAsync(r.p, b, sizeof(double) * (size_t)(n * nr), cudaMemcpyDeviceToDevice, st));
     PMMF_CUDA_TRY(cudaMemcpyAsync(z.p, b, sizeof(double) * (size_t)(n * nr), cudaMemcpyDeviceToDevice, st));
@@ -942,27 +960,62 @@ pmmf_status pmmf_solve_precond(const pmmf_handle *fc, const pmmf_matrix *A, cons
         iters[c] = 0;
     }
     PMMF_CUDA_TRY(cudaMemcpyAsync(done.p, hdone, sizeof(int32_t) * nr, cudaMemcpyHostToDevice, st));
-    for (int it = 1; it <= maxit; ++it) {
-        bool all = true;
-        for (int c = 0; c < nr; ++c) all = all && hdone[c];
-        if (all) break;
-        PMMF_TRY(spmv(dA, pv.p, qv.p, nr, st));
-        PMMF_TRY(dots(pv.p, qv.p, n, nr, pq, part.p, st));
-        PMMF_TRY(cg_update_xr(x, r.p, pv.p, qv.p, n, nr, rz, pq, done.p, st));
-        PMMF_TRY(dots(r.p, r.p, n, nr, rr, part.p, st));
-        PMMF_CUDA_TRY(cudaMemcpyAsync(hr, rr, sizeof(double) * nr, cudaMemcpyDeviceToHost, st));
+    PMMF_CUDA_TRY(cudaMemcpyAsync(bnorm, hb, sizeof(double) * nr, cudaMemcpyHostToDevice, st));
+    // Iteration 1 runs directly (it also sets the kernels' shared-memory
+    // attributes); the iteration is then captured once as a CUDA graph and
+    // replayed in batches, the convergence flags read back after each batch.
+    // Iterations after a column has converged leave that column unchanged.
+    auto all_done = [&]() -> pmmf_status {
+        PMMF_CUDA_TRY(cudaMemcpyAsync(hdone, done.p, sizeof(int32_t) * nr, cudaMemcpyDeviceToHost, st));
         PMMF_CUDA_TRY(cudaStreamSynchronize(st));
-        for (int c = 0; c < nr; ++c) {
-            if (hdone[c]) continue;
-            iters[c] = it;
-            if (std::sqrt(hr[c]) / hb[c] <= rtol) hdone[c] = 1;
-        }
-        PMMF_CUDA_TRY(cudaMemcpyAsync(done.p, hdone, sizeof(int32_t) * nr, cudaMemcpyHostToDevice, st));
-        PMMF_CUDA_TRY(cudaMemcpyAsync(z.p, r.p, sizeof(double) * (size_t)(n * nr), cudaMemcpyDeviceToDevice, st));
-        PMMF_TRY(apply_inplace(f, PMMF_OP_A_INV, z.p, nr, nr, st));
-        PMMF_TRY(dots(r.p, z.p, n, nr, rzn, part.p, st));
-        PMMF_TRY(cg_update_p(pv.p, z.p, n, nr, rzn, rz, done.p, st));
+        return PMMF_OK;
+    };
+    auto finished = [&]() {
+        for (int c = 0; c < nr; ++c)
+            if (!hdone[c]) return false;
+        return true;
+    };
+    int it = 0;
+    if (maxit > 0 && !finished()) {
+        PMMF_TRY(body(st));
+        it = 1;
+        PMMF_TRY(all_done());
     }
+    if (it < maxit && !finished()) {
+        cudaStream_t cs = nullptr;
+        PMMF_CUDA_TRY(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+        cudaGraph_t graph = nullptr;
+        cudaGraphExec_t exec = nullptr;
+        pmmf_status bs = PMMF_OK;
+        cudaError_t ce = cudaStreamBeginCapture(cs, cudaStreamCaptureModeRelaxed);
+        if (ce == cudaSuccess) {
+            bs = body(cs);
+            ce = cudaStreamEndCapture(cs, &graph);
+        }
+        if (ce == cudaSuccess && bs == PMMF_OK) ce = cudaGraphInstantiate(&exec, graph, 0);
+        if (graph) cudaGraphDestroy(graph);
+        cudaStreamDestroy(cs);
+        if (bs != PMMF_OK) return bs;
+        if (ce != cudaSuccess) {
+            if (exec) cudaGraphExecDestroy(exec);
+            return fail(PMMF_ERR_CUDA, (std::string("PCG graph capture: ") + cudaGetErrorString(ce)).c_str());
+        }
+        pmmf_status ls = PMMF_OK;
+        while (it < maxit && !finished()) {
+            const int batch = std::min(8, maxit - it);
+            for (int q = 0; q < batch && ls == PMMF_OK; ++q) {
+                const cudaError_t le = cudaGraphLaunch(exec, st);
+                if (le != cudaSuccess) ls = fail(PMMF_ERR_CUDA, (std::string("PCG graph launch: ") + cudaGetErrorString(le)).c_str());
+                g_launches.fetch_add(1, std::memory_order_relaxed);
+            }
+            it += batch;
+            if (ls == PMMF_OK) ls = all_done();
+            if (ls != PMMF_OK) break;
+        }
+        cudaGraphExecDestroy(exec);
+        PMMF_TRY(ls);
+    }
+    PMMF_CUDA_TRY(cudaMemcpyAsync(iters, itd.p, sizeof(int32_t) * nr, cudaMemcpyDeviceToHost, st));
     // true residual at exit
     PMMF_TRY(spmv(dA, x, qv.p, nr, st));
     PMMF_TRY(vec_sub(b, qv.p, r.p, n * nr, st));

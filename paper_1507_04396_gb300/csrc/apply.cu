@@ -209,23 +209,20 @@ __global__ void k_gj_blocks(const double *C, int64_t bs, const int32_t *bdim, do
 
 // ---- PCG helpers (n x nrhs row-major, ld = nrhs) ----
 
+// y = A x for n x nrhs blocks (nrhs <= 8): a group of 8 lanes per row, lane
+// r < nrhs owns right-hand side r and walks the row in order (the row's
+// entries are read once per group; x rows are 8 contiguous doubles).
 __global__ void k_spmv(int64_t n, const int64_t *rp, const int32_t *ci, const double *v,
                        const double *x, double *y, int nrhs) {
-    int lane = threadIdx.x & 31;
-    int64_t w = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-    int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t i = w; i < n; i += nw) {
-        double acc[8];
-        for (int r = 0; r < 8; ++r) acc[r] = 0.0;
-        for (int64_t q = rp[i] + lane; q < rp[i + 1]; q += 32) {
-            double a = v[q];
-            int64_t c = ci[q];
-            for (int r = 0; r < nrhs; ++r) acc[r] = __fma_rn(a, x[c * nrhs + r], acc[r]);
-        }
-        for (int r = 0; r < nrhs; ++r) {
-            double s = warp_sum(acc[r]);
-            if (lane == 0) y[i * nrhs + r] = s;
-        }
+    const int r = threadIdx.x & 7;
+    const int64_t g = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 3;
+    const int64_t ng = ((int64_t)gridDim.x * blockDim.x) >> 3;
+    for (int64_t i = g; i < n; i += ng) {
+        if (r >= nrhs) continue;
+        double acc = 0.0;
+        for (int64_t q = rp[i]; q < rp[i + 1]; ++q)
+            acc = __fma_rn(v[q], x[(int64_t)ci[q] * nrhs + r], acc);
+        y[i * nrhs + r] = acc;
     }
 }
 
@@ -262,28 +259,46 @@ __global__ void k_dot_final(const double *partial, int nb, int nrhs, double *out
     }
 }
 
+// ratio[c] = num[c] / den[c] (one divide per column, not per entry)
+__global__ void k_ratio(const double *num, const double *den, int nrhs, double *ratio) {
+    const int r = threadIdx.x;
+    if (r < nrhs) ratio[r] = __ddiv_rn(num[r], den[r]);
+}
+
 // alpha = rz / pq on active columns; x += alpha p; r -= alpha q
 __global__ void k_cg_xr(double *x, double *r, const double *p, const double *q, int64_t n,
-                        int nrhs, const double *rz, const double *pq, const int32_t *done) {
+                        int nrhs, const double *alpha, const int32_t *done) {
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n * nrhs;
          t += (int64_t)gridDim.x * blockDim.x) {
         int c = (int)(t % nrhs);
         if (done[c]) continue;
-        double alpha = rz[c] / pq[c];
-        x[t] = __fma_rn(alpha, p[t], x[t]);
-        r[t] = __fma_rn(-alpha, q[t], r[t]);
+        const double a = alpha[c];
+        x[t] = __fma_rn(a, p[t], x[t]);
+        r[t] = __fma_rn(-a, q[t], r[t]);
     }
 }
 
 // beta = rz_new / rz; p = z + beta p; rz <- rz_new  (active columns)
-__global__ void k_cg_p(double *p, const double *z, int64_t n, int nrhs, const double *rznew,
-                       const double *rz, const int32_t *done) {
+__global__ void k_cg_p(double *p, const double *z, int64_t n, int nrhs, const double *beta,
+                       const int32_t *done) {
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n * nrhs;
          t += (int64_t)gridDim.x * blockDim.x) {
         int c = (int)(t % nrhs);
         if (done[c]) continue;
-        double beta = rznew[c] / rz[c];
-        p[t] = __fma_rn(beta, p[t], z[t]);
+        p[t] = __fma_rn(beta[c], p[t], z[t]);
+    }
+}
+
+// Convergence of every column after iteration ++*itc: ||r|| / ||b|| <= rtol
+// (same arithmetic as the host test: sqrt, then divide).
+__global__ void k_cg_check(const double *rr, const double *bnorm, double rtol, int nrhs,
+                           int32_t *done, int32_t *iters, int32_t *itc) {
+    if (threadIdx.x != 0) return;
+    const int it = ++*itc;
+    for (int c = 0; c < nrhs; ++c) {
+        if (done[c]) continue;
+        iters[c] = it;
+        if (__ddiv_rn(__dsqrt_rn(rr[c]), bnorm[c]) <= rtol) done[c] = 1;
     }
 }
 
@@ -395,7 +410,7 @@ pmmf_status invert_core(const double *core, int64_t m, const double *hdiag, cons
 }
 
 pmmf_status spmv(const DevCsr &A, const double *x, double *y, int nrhs, cudaStream_t st) {
-    k_spmv<<<grid_for(A.n * 32, 256), 256, 0, st>>>(A.n, A.rp, A.ci, A.v, x, y, nrhs);
+    k_spmv<<<grid_for(A.n * 8, 256), 256, 0, st>>>(A.n, A.rp, A.ci, A.v, x, y, nrhs);
     return launched("spmv");
 }
 
@@ -411,17 +426,27 @@ int64_t dot_partial_size(int nrhs) { return (int64_t)DOT_BLOCKS * nrhs; }
 
 pmmf_status cg_update_xr(double *x, double *r, const double *p, const double *q, int64_t n,
                          int nrhs, const double *rz, const double *pq, const int32_t *done,
-                         cudaStream_t st) {
-    k_cg_xr<<<grid_for(n * nrhs, 256), 256, 0, st>>>(x, r, p, q, n, nrhs, rz, pq, done);
+                         double *alpha, cudaStream_t st) {
+    k_ratio<<<1, 32, 0, st>>>(rz, pq, nrhs, alpha);
+    PMMF_TRY(launched("ratio"));
+    k_cg_xr<<<grid_for(n * nrhs, 256), 256, 0, st>>>(x, r, p, q, n, nrhs, alpha, done);
     return launched("cg_xr");
 }
 
 pmmf_status cg_update_p(double *p, const double *z, int64_t n, int nrhs, const double *rznew,
-                        double *rz, const int32_t *done, cudaStream_t st) {
-    k_cg_p<<<grid_for(n * nrhs, 256), 256, 0, st>>>(p, z, n, nrhs, rznew, rz, done);
+                        double *rz, const int32_t *done, double *beta, cudaStream_t st) {
+    k_ratio<<<1, 32, 0, st>>>(rznew, rz, nrhs, beta);
+    PMMF_TRY(launched("ratio"));
+    k_cg_p<<<grid_for(n * nrhs, 256), 256, 0, st>>>(p, z, n, nrhs, beta, done);
     PMMF_TRY(launched("cg_p"));
     k_copy_scalars<<<1, 32, 0, st>>>(rznew, rz, done, nrhs);
     return launched("copy_scalars");
+}
+
+pmmf_status cg_check(const double *rr, const double *bnorm, double rtol, int nrhs, int32_t *done,
+                     int32_t *iters, int32_t *itc, cudaStream_t st) {
+    k_cg_check<<<1, 32, 0, st>>>(rr, bnorm, rtol, nrhs, done, iters, itc);
+    return launched("cg_check");
 }
 
 pmmf_status vec_sub(const double *b, const double *q, double *r, int64_t cnt, cudaStream_t st) {

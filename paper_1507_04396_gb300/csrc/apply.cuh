@@ -66,9 +66,12 @@ pmmf_status dots(const double *x, const double *y, int64_t n, int nrhs, double *
 int64_t dot_partial_size(int nrhs);
 pmmf_status cg_update_xr(double *x, double *r, const double *p, const double *q, int64_t n,
                          int nrhs, const double *rz, const double *pq, const int32_t *done,
-                         cudaStream_t st);
+                         double *alpha, cudaStream_t st);
 pmmf_status cg_update_p(double *p, const double *z, int64_t n, int nrhs, const double *rznew,
-                        double *rz, const int32_t *done, cudaStream_t st);
+                        double *rz, const int32_t *done, double *beta, cudaStream_t st);
+// done/iters per column after the iteration counter *itc is advanced.
+pmmf_status cg_check(const double *rr, const double *bnorm, double rtol, int nrhs, int32_t *done,
+                     int32_t *iters, int32_t *itc, cudaStream_t st);
 pmmf_status vec_sub(const double *b, const double *q, double *r, int64_t cnt, cudaStream_t st);
 
 }  // namespace pmmf
