@@ -11,6 +11,7 @@
 #include "apply.cuh"
 #include "backward.cuh"
 #include "batch.cuh"
+#include "dense.cuh"
 #include "common.cuh"
 #include "stage.cuh"
 
@@ -52,6 +53,8 @@ struct pmmf_handle {
 
 namespace pmmf {
 namespace {
+
+constexpr int64_t DENSE_MAX_N = 24576;   // rows of 8 * n bytes in shared memory
 
 pmmf_status fail(pmmf_status s, const char *msg) {
     set_error(msg);
@@ -359,6 +362,178 @@ pmmf_status factor_impl(const pmmf_matrix *A, const pmmf_params *prm, pmmf_handl
     return PMMF_OK;
 }
 
+// Algorithm 1 on a dense input kept dense (n x n in HBM): the same stage as
+// the sparse path (partition, schedule, rotation search) with the dense Gram
+// and dense blocked update; the same readings, so the same bits.
+pmmf_status factor_dense_impl(const pmmf_matrix *A, const pmmf_params *prm, pmmf_handle *h,
+                              cudaStream_t st) {
+    const int64_t n = A->n;
+    h->n = n;
+    h->k = prm->k;
+    DBuf<unsigned> status;
+    PMMF_TRY(status.zeros(1, st));
+    DBuf<double> D;
+    {
+        DBuf<double> tmp;
+        const double *dv = nullptr;
+        if (!A->val || A->ld < n) return fail(PMMF_ERR_INVALID_ARG, "dense A: val is NULL or ld < n");
+        PMMF_TRY(to_device(A->val, (n - 1) * A->ld + n, A->location, tmp, dv, st));
+        PMMF_TRY(dense_load(dv, n, A->ld, D, status.p, st));
+        unsigned hs = 0;
+        PMMF_CUDA_TRY(cudaMemcpyAsync(&hs, status.p, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
+        PMMF_CUDA_TRY(cudaStreamSynchronize(st));
+        if (hs & ST_NONFINITE) return fail(PMMF_ERR_NONFINITE, "A holds NaN or Inf");
+        if (hs & ST_NOT_SYMMETRIC) return fail(PMMF_ERR_NOT_SYMMETRIC, "A is not exactly symmetric");
+    }
+    {
+        DBuf<double> ss;
+        PMMF_TRY(ss.alloc(1, st));
+        PMMF_TRY(sum_squares(D.p, n * n, ss.p, st));
+        double hs = 0.0;
+        PMMF_CUDA_TRY(cudaMemcpyAsync(&hs, ss.p, sizeof(double), cudaMemcpyDeviceToHost, st));
+        PMMF_CUDA_TRY(cudaStreamSynchronize(st));
+        h->norm_a = std::sqrt(hs);
+        // stored entries of the input, as the sparse path counts them
+        PMMF_TRY(dense_nonzeros(D.p, n * n, &h->nnz_in, st));
+    }
+    const bool geo = prm->coords != nullptr;
+    const int dim = geo ? prm->coord_dim : 0;
+    DBuf<int32_t> q, morder;
+    if (geo) {
+        DBuf<double> tc;
+        const double *dc = nullptr;
+        PMMF_TRY(to_device(prm->coords, n * dim, prm->coords_location, tc, dc, st));
+        DBuf<uint64_t> code;
+        PMMF_TRY(q.alloc(n * dim, st));
+        PMMF_TRY(code.alloc(n, st));
+        PMMF_CUDA_TRY(cudaMemsetAsync(status.p, 0, sizeof(unsigned), st));
+        PMMF_TRY(quantize_points(dc, n, dim, q.p, code.p, status.p, st));
+        PMMF_TRY(morder.alloc(n, st));
+        PMMF_TRY(radix_sort_u64(code.p, n, 15 * dim, morder.p, st));
+        unsigned hs = 0;
+        PMMF_CUDA_TRY(cudaMemcpyAsync(&hs, status.p, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
+        PMMF_CUDA_TRY(cudaStreamSynchronize(st));
+        if (hs & ST_NONFINITE) return fail(PMMF_ERR_INVALID_ARG, "coords hold NaN or Inf");
+    }
+    DBuf<int32_t> act, pos, cl, loc, elimflag;
+    DBuf<double> contribs;
+    PMMF_TRY(act.alloc(n, st));
+    PMMF_TRY(iota_i32(act.p, n, st));
+    PMMF_TRY(pos.alloc(n, st));
+    PMMF_TRY(iota_i32(pos.p, n, st));
+    PMMF_TRY(cl.alloc(n, st));
+    PMMF_TRY(loc.alloc(n, st));
+    PMMF_TRY(elimflag.zeros(n, st));
+    PMMF_TRY(h->hdiag.zeros(n, st));
+    PMMF_TRY(contribs.zeros(n + 1, st));
+    const int iters = prm->lloyd_iters > 0 ? prm->lloyd_iters : 10;
+    int64_t s = n, p = 0;
+    while (s > prm->core_size && (prm->max_stages <= 0 || p < prm->max_stages)) {
+        ++p;
+        h->st.emplace_back();
+        StageData &S = h->st.back();
+        S.s = s;
+        int64_t m = (s + prm->cluster_size / 2) / prm->cluster_size;
+        if (m < 1 || !geo) m = 1;
+        if (m > 1) {
+            PartitionIn in;
+            in.n = n;
+            in.s = s;
+            in.dim = dim;
+            in.q = q.p;
+            in.morder = morder.p;
+            in.pos = pos.p;
+            in.act = act.p;
+            in.cl = cl.p;
+            in.loc = loc.p;
+            PMMF_TRY(partition_stage(in, m, iters, S.cls, st));
+        } else {
+            PMMF_TRY(one_cluster(act.p, s, S.cls, cl.p, loc.p, st));
+        }
+        int64_t sched[2] = {0, 0};
+        DBuf<int64_t> e;
+        PMMF_TRY(schedule_stage(S.cls.coff.p, S.cls.m, s, prm->core_size, prm->eta, e, S.rot.roff,
+                                sched, st));
+        if (sched[1]) PMMF_TRY(one_cluster(act.p, s, S.cls, cl.p, loc.p, st));
+        S.m = S.cls.m;
+        S.nrot = sched[0];
+        S.rot.nrot = sched[0];
+        S.rot.K = prm->k;
+        std::vector<int64_t> hc((size_t)S.m + 1);
+        PMMF_CUDA_TRY(cudaMemcpyAsync(hc.data(), S.cls.coff.p, sizeof(int64_t) * hc.size(), cudaMemcpyDeviceToHost, st));
+        PMMF_CUDA_TRY(cudaStreamSynchronize(st));
+        for (int64_t u = 0; u < S.m; ++u) S.cmax = std::max(S.cmax, hc[u + 1] - hc[u]);
+        PMMF_CUDA_TRY(cudaMemsetAsync(status.p, 0, sizeof(unsigned), st));
+        {
+            GramBlocks gb;
+            PMMF_TRY(gram_blocks(S.cls, gb, st));
+            PMMF_TRY(dense_gram(D, s, pos.p, S.cls, hc, gb, st));
+            PMMF_TRY(select_stage(S.cls, S.cmax, gb, prm->seed, p, S.rot, elimflag.p, st, nullptr,
+                                  nullptr, status.p));
+        }
+        int32_t nlv = 0;
+        {
+            unsigned hs = 0;
+            std::vector<int32_t> nl((size_t)S.m);
+            PMMF_CUDA_TRY(cudaMemcpyAsync(&hs, status.p, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
+            PMMF_CUDA_TRY(cudaMemcpyAsync(nl.data(), S.rot.nlev.p, sizeof(int32_t) * nl.size(), cudaMemcpyDeviceToHost, st));
+            PMMF_CUDA_TRY(cudaStreamSynchronize(st));
+            if (hs & ST_NOT_CONVERGED)
+                return fail(PMMF_ERR_NOT_CONVERGED, "k x k Jacobi did not converge in 32 sweeps");
+            for (int32_t v : nl) nlv = std::max(nlv, v);
+            S.max_levels = nlv;
+        }
+        DenseLevels lv;
+        PMMF_TRY(dense_levels(S.cls, S.rot, pos.p, nlv, lv, st));
+        DBuf<double> Dn;
+        DBuf<int32_t> nact;
+        int64_t s2 = 0;
+        PMMF_TRY(dense_update(D, s, lv, act.p, elimflag.p, p, h->hdiag.p, contribs.p + (p - 1), Dn,
+                              nact, s2, st));
+        PMMF_CUDA_TRY(cudaMemsetAsync(pos.p, 0xFF, sizeof(int32_t) * (size_t)n, st));
+        PMMF_TRY(set_positions(nact.p, s2, pos.p, st));
+        s = s2;
+        D = std::move(Dn);
+        act = std::move(nact);
+        if (prm->record_stages) {
+            PMMF_TRY(dense_record(D.p, s, act.p, S.recorded, st));
+            PMMF_TRY(S.recorded_act.alloc(s, st));
+            if (s > 0)
+                PMMF_CUDA_TRY(cudaMemcpyAsync(S.recorded_act.p, act.p, sizeof(int32_t) * (size_t)s, cudaMemcpyDeviceToDevice, st));
+            S.has_record = true;
+            S.nnz_after = S.recorded.nnz;
+        } else {
+            S.nnz_after = s * s;
+        }
+    }
+    h->ncore = s;
+    PMMF_TRY(h->core_idx.alloc(s, st));
+    if (s > 0)
+        PMMF_CUDA_TRY(cudaMemcpyAsync(h->core_idx.p, act.p, sizeof(int32_t) * (size_t)s, cudaMemcpyDeviceToDevice, st));
+    PMMF_TRY(h->core.alloc(s * s, st));
+    PMMF_TRY(dense_core(D.p, s, act.p, h->core.p, h->hdiag.p, st));
+    PMMF_TRY(h->core_pos.alloc(n, st));
+    PMMF_CUDA_TRY(cudaMemsetAsync(h->core_pos.p, 0xFF, sizeof(int32_t) * (size_t)n, st));
+    PMMF_TRY(set_positions(act.p, s, h->core_pos.p, st));
+    std::vector<double> hcb((size_t)p + 1, 0.0);
+    if (p > 0)
+        PMMF_CUDA_TRY(cudaMemcpyAsync(hcb.data(), contribs.p, sizeof(double) * (size_t)p, cudaMemcpyDeviceToHost, st));
+    PMMF_CUDA_TRY(cudaStreamSynchronize(st));
+    double tot = 0.0;
+    for (int64_t i = 0; i < p; ++i) {
+        h->st[i].contrib = hcb[i];
+        tot += hcb[i];
+    }
+    h->err = h->norm_a > 0.0 ? std::sqrt(tot) / h->norm_a : 0.0;
+    h->nblk = 1;
+    h->bs = h->ncore;
+    h->nmat = 1;
+    h->moff = {0, n};
+    h->mat_err = {h->err};
+    build_views(h);
+    return PMMF_OK;
+}
+
 template <class T>
 pmmf_status upload(const std::vector<T> &v, DBuf<T> &d, cudaStream_t st) {
     PMMF_TRY(d.alloc((int64_t)std::max<size_t>(v.size(), 1), st));
@@ -571,7 +746,11 @@ pmmf_status pmmf_factor(const pmmf_matrix *A, const pmmf_params *p, pmmf_handle 
     if (!h) return fail(PMMF_ERR_OOM, "host allocation failed");
     pmmf_status s;
     try {
-        s = factor_impl(A, p, h, st);
+        // a dense input stays dense when its rows fit one CTA's shared memory
+        if (A->format == PMMF_DENSE && A->n <= DENSE_MAX_N)
+            s = factor_dense_impl(A, p, h, st);
+        else
+            s = factor_impl(A, p, h, st);
     } catch (const std::bad_alloc &) {
         s = fail(PMMF_ERR_OOM, "host allocation failed");
     }

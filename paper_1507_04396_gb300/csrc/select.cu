@@ -762,31 +762,43 @@ k_select_fast(const int64_t *coff, const int32_t *members, const int64_t *goff, 
 
 }  // namespace
 
+pmmf_status gram_blocks(const StageClusters &cls, GramBlocks &gb, cudaStream_t st) {
+    const int64_t m = cls.m;
+    PMMF_TRY(gb.goff.alloc(m + 1, st));
+    k_square_sizes<<<grid_for(m, 256), 256, 0, st>>>(cls.coff.p, m, gb.goff.p);
+    PMMF_TRY(launched("square_sizes"));
+    PMMF_TRY(scan_i64(gb.goff.p, gb.goff.p, m, st));
+    PMMF_CUDA_TRY(cudaMemcpyAsync(&gb.total, gb.goff.p + m, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+    PMMF_CUDA_TRY(cudaStreamSynchronize(st));
+    PMMF_TRY(gb.G.alloc(gb.total, st));   // the Gram kernels write every entry of every block
+    PMMF_TRY(gb.M.alloc(gb.total, st));
+    return PMMF_OK;
+}
+
 pmmf_status gram_and_select(const Csr &A, const int32_t *pos, const int32_t *cl,
                             const StageClusters &cls, int64_t cmax, uint64_t seed, int64_t stage,
                             StageRotations &rot, int32_t *elimflag, cudaStream_t st,
                             const int32_t *order, const uint64_t *useed, unsigned *status) {
-    const int64_t m = cls.m;
-    DBuf<int64_t> goff;
-    PMMF_TRY(goff.alloc(m + 1, st));
-    k_square_sizes<<<grid_for(m, 256), 256, 0, st>>>(cls.coff.p, m, goff.p);
-    PMMF_TRY(launched("square_sizes"));
-    PMMF_TRY(scan_i64(goff.p, goff.p, m, st));
-    int64_t gtot = 0;
-    PMMF_CUDA_TRY(cudaMemcpyAsync(&gtot, goff.p + m, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
-    PMMF_CUDA_TRY(cudaStreamSynchronize(st));
-    DBuf<double> G, M;
-    PMMF_TRY(G.alloc(gtot, st));   // k_gram writes every entry of every cluster block
-    PMMF_TRY(M.alloc(gtot, st));
-    int64_t s = A.rows;
+    GramBlocks gb;
+    PMMF_TRY(gram_blocks(cls, gb, st));
+    const int64_t s = A.rows;
     prof_begin(KF_GRAM, st);
     k_gram<<<grid_for(s * 32, 256), 256, 0, st>>>(A.rowptr.p, A.col.p, A.val.p, pos, cl,
-                                                   cls.coff.p, cls.members.p, s, goff.p, G.p, M.p);
+                                                   cls.coff.p, cls.members.p, s, gb.goff.p, gb.G.p,
+                                                   gb.M.p);
     // compulsory traffic: the cluster rows once (12 B per entry, 8 B per row
     // pointer) and both c_u x c_u outputs
-    prof_end(KF_GRAM, st, 12.0 * (double)A.nnz + 8.0 * (double)s + 16.0 * (double)gtot, 0.0);
+    prof_end(KF_GRAM, st, 12.0 * (double)A.nnz + 8.0 * (double)s + 16.0 * (double)gb.total, 0.0);
     PMMF_TRY(launched("gram"));
+    return select_stage(cls, cmax, gb, seed, stage, rot, elimflag, st, order, useed, status);
+}
 
+pmmf_status select_stage(const StageClusters &cls, int64_t cmax, GramBlocks &gb, uint64_t seed,
+                         int64_t stage, StageRotations &rot, int32_t *elimflag, cudaStream_t st,
+                         const int32_t *order, const uint64_t *useed, unsigned *status) {
+    const int64_t m = cls.m;
+    DBuf<int64_t> &goff = gb.goff;
+    DBuf<double> &G = gb.G, &M = gb.M;
     if (rot.K > 2) {
         if (!status) {
             set_error("k-point search needs a status word");

@@ -64,6 +64,20 @@ pmmf_status schedule_stage(const int64_t *coff, int64_t mm, int64_t s, int64_t c
 // order (optional): launch position -> cluster, e.g. longest first; useed
 // (optional): per-cluster seeds, the draws then use cluster ordinal 0 (each
 // cluster searched as if it were the only cluster of its own factorization).
+// Dense per-cluster Gram and local blocks: block u (c_u x c_u, row-major) at
+// goff[u] of G and M.
+struct GramBlocks {
+    int64_t total = 0;
+    DBuf<int64_t> goff;       // m + 1
+    DBuf<double> G, M;
+};
+pmmf_status gram_blocks(const StageClusters &cls, GramBlocks &gb, cudaStream_t st);
+// Rotation search of every cluster on formed Gram blocks.
+pmmf_status select_stage(const StageClusters &cls, int64_t cmax, GramBlocks &gb, uint64_t seed,
+                         int64_t stage, StageRotations &rot, int32_t *elimflag, cudaStream_t st,
+                         const int32_t *order = nullptr, const uint64_t *useed = nullptr,
+                         unsigned *status = nullptr);
+
 // rot.K selects Givens (2) or k-point (>= 3) rotations; status receives
 // ST_NOT_CONVERGED when a k x k Jacobi did not converge.
 pmmf_status gram_and_select(const Csr &A, const int32_t *pos, const int32_t *cl,

@@ -1,0 +1,54 @@
+"""Dense inputs kept dense on the GPU (dense Gram and dense blocked update)
+against the oracle: the same bar as the sparse path (bit-identical
+selections, rotations, stage matrices, H and products)."""
+
+import numpy as np
+import pytest
+
+from helpers import assert_same_factorization, gpu, gpu_lib
+from oracle import oracle as O
+from paper_1507_04396_gb300 import inputs as I
+
+pytestmark = gpu
+
+
+def _both(a, coords, **kw):
+    import torch
+    pm = gpu_lib()
+    dense = torch.from_numpy(a.to_dense()).cuda()
+    g = pm.factor(dense, coords=coords, record_stages=True, **kw)
+    o = O.factor(a.n, a.rowptr, a.col, a.val, coords, record=True, **kw)
+    assert o.status == 0
+    return g, o
+
+
+def test_dense_psd_one_cluster():
+    """X X^T/64 + 0.1 I, n = 256, one cluster, core 16."""
+    a = I.psd_dense(256, 64, seed=0)
+    g, o = _both(a, None, k=2, eta=0.5, cluster_size=256, core_size=16, seed=0)
+    assert_same_factorization(g, o)
+
+
+@pytest.mark.parametrize("k", [2, 3])
+def test_dense_rbf_clustered(k):
+    """Gaussian RBF kernel of a 3-D mixture, k-means clusters of 128."""
+    a = I.rbf_mixture(1024, components=8, seed=5)
+    g, o = _both(a, a.coords, k=k, eta=0.5, cluster_size=128, core_size=64, seed=3)
+    assert_same_factorization(g, o)
+
+
+def test_sparse_matrix_given_dense():
+    """A sparse Laplacian passed as a dense array: zeros must not change a bit."""
+    a = I.knn_laplacian(1200, seed=4)
+    g, o = _both(a, a.coords, k=2, eta=0.5, cluster_size=100, core_size=50, seed=2)
+    assert_same_factorization(g, o)
+
+
+def test_dense_apply_matches_oracle():
+    import torch
+    a = I.rbf_mixture(768, components=6, seed=1)
+    g, o = _both(a, a.coords, k=3, eta=0.5, cluster_size=96, core_size=48, seed=1)
+    x = np.random.default_rng(0).standard_normal((a.n, 2))
+    xd = torch.from_numpy(x).cuda()
+    for op in (O.OP_U, O.OP_UT, O.OP_H, O.OP_A):
+        assert np.array_equal(g.apply(op, xd).cpu().numpy(), o.apply(op, x)), op
