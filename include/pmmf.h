@@ -78,9 +78,9 @@ typedef struct {
 } pmmf_matrix;
 
 /* Parameters, named as in the paper.
- *   k             rotation order (Sec. 2, k-point rotations), 2 <= k <= 8.
- *                 This build runs k = 2 (Givens, Algorithm 2) on the GPU;
- *                 k > 2 returns PMMF_ERR_UNSUPPORTED.
+ *   k             rotation order (Sec. 2, k-point rotations), 2 <= k <= 8:
+ *                 k = 2 Givens rotations (Algorithm 2), k >= 3 k-point
+ *                 rotations diagonalizing the k x k Gram sub-block.
  *   eta           compression ratio of Algorithm 2: floor(eta c_u) rotations
  *                 (one elimination each) per cluster per stage, 0 < eta < 1.
  *   cluster_size  typical cluster size c (Sec. 2.1), >= k; a stage with s
@@ -95,7 +95,19 @@ typedef struct {
  *                 k-means; NULL -> one cluster per stage.
  *   coords_location  PMMF_HOST or PMMF_DEVICE for coords.
  *   record_stages nonzero keeps a device copy of every stage's compacted
- *                 A_p (for inspection with pmmf_stage_matrix). */
+ *                 A_p (for inspection with pmmf_stage_matrix).
+ *   precision     PMMF_PREC_FP64 (0): every Gram entry in FP64 (the oracle's
+ *                 arithmetic, bit for bit).  PMMF_PREC_TF32 / PMMF_PREC_BF16:
+ *                 dense inputs only (PMMF_DENSE with n <= 24576; anything
+ *                 else returns UNSUPPORTED): the Gram matrices are formed on
+ *                 the tensor cores from TF32 / BF16 copies with FP32
+ *                 accumulation and serve only to shortlist partners; every
+ *                 shortlisted partner is re-scored, and every angle, Gram
+ *                 diagonal and rotation computed, in FP64 from the FP64 rows
+ *                 (the shortlist keeps every candidate that a certified error
+ *                 bound cannot rule out, so the choice is the FP64 choice up to
+ *                 rounding of the FP64 scores).  Not bit-identical to FP64
+ *                 mode; pmmf_get_precision_stats reports the shortlists. */
 typedef struct {
     int k;
     double eta;
@@ -108,7 +120,10 @@ typedef struct {
     int coord_dim;
     int coords_location;
     int record_stages;
+    int precision;
 } pmmf_params;
+
+enum { PMMF_PREC_FP64 = 0, PMMF_PREC_TF32 = 1, PMMF_PREC_BF16 = 2 };
 
 typedef struct pmmf_handle pmmf_handle;
 
@@ -212,6 +227,13 @@ pmmf_status pmmf_factor_blockdiag(const pmmf_matrix *A, int64_t nmat, const int6
  * into one block-diagonal matrix on the host and factored as above. */
 pmmf_status pmmf_factor_batched(int64_t nmat, const pmmf_matrix *A, const pmmf_params *p,
                                 pmmf_handle **out, void *stream);
+
+/* Shortlist counters of a reduced-precision factorization (HOST outputs, any
+ * may be NULL): candidates re-scored in FP64 over all steps, steps whose
+ * shortlist held more than 64 candidates, rotation search steps, and the
+ * largest shortlist.  All zero in FP64 mode. */
+pmmf_status pmmf_get_precision_stats(const pmmf_handle *f, int64_t *rescored, int64_t *fallbacks,
+                                     int64_t *steps, int64_t *max_shortlist);
 
 /* Batch layout (HOST outputs, any may be NULL): nmat, core_stride (slot
  * stride of the core blocks), block_off[nmat + 1], errors[nmat] (each

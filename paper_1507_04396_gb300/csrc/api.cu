@@ -12,6 +12,7 @@
 #include "backward.cuh"
 #include "batch.cuh"
 #include "dense.cuh"
+#include "mixed.cuh"
 #include "common.cuh"
 #include "stage.cuh"
 
@@ -49,6 +50,8 @@ struct pmmf_handle {
     int64_t nmat = 1;
     std::vector<int64_t> moff;
     std::vector<double> mat_err;
+    // reduced-precision shortlist counters: re-scored, fallbacks, steps, max
+    unsigned long long prec_stats[4] = {0, 0, 0, 0};
 };
 
 namespace pmmf {
@@ -160,6 +163,8 @@ pmmf_status check_params(const pmmf_matrix *A, const pmmf_params *p) {
     if (p->core_size < 1 || p->core_size > A->n)
         return fail(PMMF_ERR_INVALID_ARG, "core_size must be in [1, n]");
     if (p->lloyd_iters < 0) return fail(PMMF_ERR_INVALID_ARG, "lloyd_iters must be >= 0");
+    if (p->precision < PMMF_PREC_FP64 || p->precision > PMMF_PREC_BF16)
+        return fail(PMMF_ERR_INVALID_ARG, "unknown precision mode");
     if (p->coords && (p->coord_dim < 1 || p->coord_dim > 3))
         return fail(PMMF_ERR_INVALID_ARG, "coord_dim must be 1, 2 or 3");
     if (p->coords && p->coords_location != PMMF_HOST && p->coords_location != PMMF_DEVICE)
@@ -427,6 +432,8 @@ pmmf_status factor_dense_impl(const pmmf_matrix *A, const pmmf_params *prm, pmmf
     PMMF_TRY(h->hdiag.zeros(n, st));
     PMMF_TRY(contribs.zeros(n + 1, st));
     const int iters = prm->lloyd_iters > 0 ? prm->lloyd_iters : 10;
+    DBuf<unsigned long long> pstats;
+    PMMF_TRY(pstats.zeros(4, st));
     int64_t s = n, p = 0;
     while (s > prm->core_size && (prm->max_stages <= 0 || p < prm->max_stages)) {
         ++p;
@@ -464,7 +471,10 @@ pmmf_status factor_dense_impl(const pmmf_matrix *A, const pmmf_params *prm, pmmf
         PMMF_CUDA_TRY(cudaStreamSynchronize(st));
         for (int64_t u = 0; u < S.m; ++u) S.cmax = std::max(S.cmax, hc[u + 1] - hc[u]);
         PMMF_CUDA_TRY(cudaMemsetAsync(status.p, 0, sizeof(unsigned), st));
-        {
+        if (prm->precision != PMMF_PREC_FP64) {
+            PMMF_TRY(mixed_stage_select(D, s, pos.p, S.cls, hc, S.cmax, prm->precision, prm->seed,
+                                        p, S.rot, elimflag.p, pstats.p, status.p, st));
+        } else {
             GramBlocks gb;
             PMMF_TRY(gram_blocks(S.cls, gb, st));
             PMMF_TRY(dense_gram(D, s, pos.p, S.cls, hc, gb, st));
@@ -530,6 +540,7 @@ pmmf_status factor_dense_impl(const pmmf_matrix *A, const pmmf_params *prm, pmmf
     h->nmat = 1;
     h->moff = {0, n};
     h->mat_err = {h->err};
+    PMMF_CUDA_TRY(cudaMemcpy(h->prec_stats, pstats.p, sizeof(h->prec_stats), cudaMemcpyDeviceToHost));
     build_views(h);
     return PMMF_OK;
 }
@@ -747,7 +758,10 @@ pmmf_status pmmf_factor(const pmmf_matrix *A, const pmmf_params *p, pmmf_handle 
     pmmf_status s;
     try {
         // a dense input stays dense when its rows fit one CTA's shared memory
-        if (A->format == PMMF_DENSE && A->n <= DENSE_MAX_N)
+        const bool dense = A->format == PMMF_DENSE && A->n <= DENSE_MAX_N;
+        if (p->precision != PMMF_PREC_FP64 && !dense)
+            s = fail(PMMF_ERR_UNSUPPORTED, "reduced-precision Gram needs a dense input with n <= 24576");
+        else if (dense)
             s = factor_dense_impl(A, p, h, st);
         else
             s = factor_impl(A, p, h, st);
@@ -836,6 +850,16 @@ pmmf_status pmmf_factor_batched(int64_t nmat, const pmmf_matrix *A, const pmmf_p
     big.colidx = ci.data();
     big.val = v.data();
     return pmmf_factor_blockdiag(&big, nmat, moff.data(), p, out, stream);
+}
+
+pmmf_status pmmf_get_precision_stats(const pmmf_handle *f, int64_t *rescored, int64_t *fallbacks,
+                                     int64_t *steps, int64_t *max_shortlist) {
+    if (!f) return fail(PMMF_ERR_INVALID_ARG, "NULL handle");
+    if (rescored) *rescored = (int64_t)f->prec_stats[0];
+    if (fallbacks) *fallbacks = (int64_t)f->prec_stats[1];
+    if (steps) *steps = (int64_t)f->prec_stats[2];
+    if (max_shortlist) *max_shortlist = (int64_t)f->prec_stats[3];
+    return PMMF_OK;
 }
 
 pmmf_status pmmf_get_batch(const pmmf_handle *f, int64_t *nmat, int64_t *core_stride,

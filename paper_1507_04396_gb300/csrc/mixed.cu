@@ -1,0 +1,769 @@
+// mixed.cu -- the rotation search with a low-precision Gram shortlist.
+//
+// The cluster's Gram matrix is formed on the tensor cores from a TF32 or BF16
+// split of its rows, x = hi + lo with hi = round(x), lo = round(x - hi), as
+// hi hi^T + hi lo^T + lo hi^T with FP32 accumulation over chunks of 128 terms
+// and FP64 accumulation of the chunks.  That matrix only screens partners:
+// for the pivot row i every candidate j gets a score interval
+//   |G~_ij| w_j -/+ B_ij w_j,
+// where B bounds |G~ - G| entry by entry (initially eps sqrt(G_ii G_jj) with
+// eps from the input rounding and the FP32 accumulation over s terms, then
+// carried through every rotation of G~ with the rotation's own rounding
+// added), and w_j = 1/sqrt(G_jj) with G_jj kept in FP64.  Every candidate
+// whose interval reaches the (k-1)-th largest lower end is re-scored in FP64
+// from the FP64 rows, and the partners are the best FP64 scores (ties to the
+// smaller index), as in FP64 mode.  The angle uses FP64 Gram entries (dot
+// products of the current rows), the rows themselves are rotated in FP64, and
+// the FP64 diagonal follows the FP64 k x k block.  Only the Gram matrix, its
+// error bound and their rotation are in reduced precision.
+#include <cuda_bf16.h>
+
+#include <vector>
+
+#include "dense.cuh"
+#include "mixed.cuh"
+
+namespace pmmf {
+namespace {
+
+constexpr int MX_THREADS = 512;
+constexpr int MX_WARPS = MX_THREADS / 32;
+constexpr int SL_MAX = 64;           // shortlists above this are counted as long
+constexpr int DOT_BATCH = 8;
+
+__device__ __forceinline__ uint64_t mixm(uint64_t x) {
+    uint64_t z = x + 0x9E3779B97F4A7C15ULL;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+    return z ^ (z >> 31);
+}
+
+__device__ __forceinline__ uint64_t drawm(uint64_t seed, uint64_t p, uint64_t u, uint64_t t) {
+    uint64_t h = mixm(seed);
+    h = mixm(h ^ p);
+    h = mixm(h ^ u);
+    return mixm(h ^ t);
+}
+
+__device__ int nth_set(const uint32_t *mask, int nwords, int64_t pos) {
+    int rem = (int)pos;
+    for (int wi = 0; wi < nwords; ++wi) {
+        const uint32_t m = mask[wi];
+        const int pc = __popc(m);
+        if (rem < pc) {
+            for (int b = 0; b < 32; ++b)
+                if ((m >> b) & 1u) {
+                    if (rem == 0) return wi * 32 + b;
+                    --rem;
+                }
+        }
+        rem -= pc;
+    }
+    return -1;
+}
+
+__device__ __forceinline__ bool on(const uint32_t *mask, int y) { return (mask[y >> 5] >> (y & 31)) & 1u; }
+
+// ---------------------------------------------------------------- slab
+
+// Row q of the slab = row pos[members[q]] of D (cluster order), in FP64 and in
+// the reduced precision (TF32: round to nearest, ties away, kept in a float;
+// BF16: round to nearest even).
+// The reduced-precision rows have stride sp (s rounded up to even for BF16,
+// the padding zero): XH = round(x), XL = round(x - XH) (TF32: round to nearest,
+// ties away, kept in a float; BF16: round to nearest even).
+template <int PREC>
+__global__ void k_build_slab(const double *D, int64_t s, int64_t sp, const int32_t *pos,
+                             const int32_t *members, double *X, void *XH, void *XL) {
+    const int64_t q = blockIdx.x;
+    const double *src = D + (int64_t)pos[members[q]] * s;
+    for (int64_t r = threadIdx.x; r < sp; r += blockDim.x) {
+        const double v = r < s ? src[r] : 0.0;
+        if (r < s) X[q * s + r] = v;
+        if (PREC == PMMF_PREC_TF32) {
+            const float f = __double2float_rn(v);
+            uint32_t h, l;
+            asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(h) : "f"(f));
+            const float rest = __double2float_rn(v - (double)__uint_as_float(h));
+            asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(l) : "f"(rest));
+            ((uint32_t *)XH)[q * sp + r] = h;
+            ((uint32_t *)XL)[q * sp + r] = l;
+        } else {
+            const __nv_bfloat16 h = __float2bfloat16_rn(__double2float_rn(v));
+            const __nv_bfloat16 l = __float2bfloat16_rn(__double2float_rn(v - (double)__bfloat162float(h)));
+            ((__nv_bfloat16 *)XH)[q * sp + r] = h;
+            ((__nv_bfloat16 *)XL)[q * sp + r] = l;
+        }
+    }
+}
+
+// FP64 squared norms of the slab rows (warp per row, fixed order).
+__global__ void k_row_norms(const double *X, int64_t rows, int64_t s, double *out) {
+    const int lane = threadIdx.x & 31;
+    const int64_t w = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t q = w; q < rows; q += nw) {
+        double acc = 0.0;
+        for (int64_t r = lane; r < s; r += 32) acc = __fma_rn(X[q * s + r], X[q * s + r], acc);
+        acc = warp_sum(acc);
+        if (lane == 0) out[q] = acc;
+    }
+}
+
+// Local symmetric blocks M^u_ab = D[x_min][x_max] (one CTA per cluster).
+__global__ void k_local_block(const double *D, int64_t s, const int32_t *pos, const int64_t *coff,
+                              const int32_t *members, const int64_t *goff, double *M) {
+    const int64_t u = blockIdx.x;
+    const int64_t base = coff[u];
+    const int64_t c = coff[u + 1] - base;
+    double *Mu = M + goff[u];
+    for (int64_t q = threadIdx.x; q < c * c; q += blockDim.x) {
+        const int64_t a = q / c, b = q - a * c;
+        const int64_t pa = pos[members[base + (a < b ? a : b)]];
+        const int64_t pb = pos[members[base + (a < b ? b : a)]];
+        Mu[q] = D[pa * s + pb];
+    }
+}
+
+// ---------------------------------------------------------------- tensor-core Gram
+
+// mma.sync fragments (PTX ISA, warp-level MMA):
+//   m16n8k16 BF16: A a0..a3 = rows (g, g+8), k pairs (2t, 2t+1) and (2t+8, 2t+9);
+//                  B b0, b1 = k pairs (2t, 2t+1), (2t+8, 2t+9) of column g;
+//   m16n8k8 TF32:  A a0..a3 = (g, t), (g+8, t), (g, t+4), (g+8, t+4);
+//                  B b0, b1 = (t, g), (t+4, g);
+//   C c0..c3 = (g, 2t), (g, 2t+1), (g+8, 2t), (g+8, 2t+1);  g = lane / 4, t = lane % 4.
+constexpr int TG = 64;      // output tile
+constexpr int TKB = 32;     // k chunk staged in shared memory (elements)
+constexpr int KFLUSH = 128; // FP32 accumulation length before the FP64 sum
+
+__device__ __forceinline__ void mma_bf16(float *d, const uint32_t *a, const uint32_t *b) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 "
+        "{%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+
+__device__ __forceinline__ void mma_tf32(float *d, const uint32_t *a, const uint32_t *b) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 "
+        "{%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+
+// One CTA (4 warps, each a 32 x 32 patch) per 64 x 64 tile (ta <= tb) of one
+// cluster's Gram block: hi hi^T + hi lo^T + lo hi^T on the tensor cores.
+template <int PREC>
+__global__ void __launch_bounds__(128)
+k_tc_gram(const void *XH, const void *XL, int64_t sp /* padded row length */,
+          const int64_t *coff, const int64_t *goff, const int32_t *tu, const int32_t *ta,
+          const int32_t *tb, float *G) {
+    // operand tiles as 32-bit words: BF16 pairs or TF32 values
+    constexpr int WPR = PREC == PMMF_PREC_BF16 ? TKB / 2 : TKB;   // words per row per chunk
+    __shared__ uint32_t Ah[TG][WPR + 4], Al[TG][WPR + 4], Bh[TG][WPR + 4], Bl[TG][WPR + 4];
+    const int64_t u = tu[blockIdx.x];
+    const int64_t base = coff[u];
+    const int c = (int)(coff[u + 1] - base);
+    const int a0 = ta[blockIdx.x] * TG, b0 = tb[blockIdx.x] * TG;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int g = lane >> 2, t = lane & 3;
+    const int wm = (warp >> 1) * 32, wn = (warp & 1) * 32;
+    float acc[2][4][4];
+    double dacc[2][4][4];
+    for (int i = 0; i < 2; ++i)
+        for (int j = 0; j < 4; ++j)
+            for (int q = 0; q < 4; ++q) {
+                acc[i][j][q] = 0.0f;
+                dacc[i][j][q] = 0.0;
+            }
+    const uint32_t *WH = (const uint32_t *)XH, *WL = (const uint32_t *)XL;
+    const int64_t wrow = PREC == PMMF_PREC_BF16 ? sp / 2 : sp;   // words per row
+    for (int64_t k0 = 0; k0 < sp; k0 += TKB) {
+        const int64_t kw0 = PREC == PMMF_PREC_BF16 ? k0 / 2 : k0;
+        const int64_t kwl = wrow - kw0;                            // words left in the row
+        for (int q = tid; q < TG * WPR; q += 128) {
+            const int r = q / WPR, kw = q - r * WPR;
+            const bool okk = kw < kwl;
+            const bool oa = a0 + r < c && okk, ob = b0 + r < c && okk;
+            const int64_t ia = (base + a0 + r) * wrow + kw0 + kw, ib = (base + b0 + r) * wrow + kw0 + kw;
+            Ah[r][kw] = oa ? WH[ia] : 0u;
+            Al[r][kw] = oa ? WL[ia] : 0u;
+            Bh[r][kw] = ob ? WH[ib] : 0u;
+            Bl[r][kw] = ob ? WL[ib] : 0u;
+        }
+        __syncthreads();
+        constexpr int KSTEP = PREC == PMMF_PREC_BF16 ? 16 : 8;
+        for (int kk = 0; kk < TKB / KSTEP; ++kk) {
+            const int kb = kk * 8;   // word offset of this k step (8 words either way)
+            uint32_t ah[2][4], al[2][4], bh[4][2], bl[4][2];
+            for (int i = 0; i < 2; ++i) {
+                const int r = wm + i * 16;
+                ah[i][0] = Ah[r + g][kb + t];
+                ah[i][1] = Ah[r + g + 8][kb + t];
+                ah[i][2] = Ah[r + g][kb + t + 4];
+                ah[i][3] = Ah[r + g + 8][kb + t + 4];
+                al[i][0] = Al[r + g][kb + t];
+                al[i][1] = Al[r + g + 8][kb + t];
+                al[i][2] = Al[r + g][kb + t + 4];
+                al[i][3] = Al[r + g + 8][kb + t + 4];
+            }
+            for (int j = 0; j < 4; ++j) {
+                const int n = wn + j * 8 + g;
+                bh[j][0] = Bh[n][kb + t];
+                bh[j][1] = Bh[n][kb + t + 4];
+                bl[j][0] = Bl[n][kb + t];
+                bl[j][1] = Bl[n][kb + t + 4];
+            }
+            for (int i = 0; i < 2; ++i)
+                for (int j = 0; j < 4; ++j) {
+                    if (PREC == PMMF_PREC_BF16) {
+                        mma_bf16(acc[i][j], al[i], bh[j]);
+                        mma_bf16(acc[i][j], ah[i], bl[j]);
+                        mma_bf16(acc[i][j], ah[i], bh[j]);
+                    } else {
+                        mma_tf32(acc[i][j], al[i], bh[j]);
+                        mma_tf32(acc[i][j], ah[i], bl[j]);
+                        mma_tf32(acc[i][j], ah[i], bh[j]);
+                    }
+                }
+        }
+        __syncthreads();
+        if ((k0 + TKB) % KFLUSH == 0 || k0 + TKB >= sp) {
+            for (int i = 0; i < 2; ++i)
+                for (int j = 0; j < 4; ++j)
+                    for (int q = 0; q < 4; ++q) {
+                        dacc[i][j][q] = __dadd_rn(dacc[i][j][q], (double)acc[i][j][q]);
+                        acc[i][j][q] = 0.0f;
+                    }
+        }
+    }
+    float *Gu = G + goff[u];
+    for (int i = 0; i < 2; ++i)
+        for (int j = 0; j < 4; ++j)
+            for (int q = 0; q < 4; ++q) {
+                const int a = a0 + wm + i * 16 + g + (q >= 2 ? 8 : 0);
+                const int b = b0 + wn + j * 8 + 2 * t + (q & 1);
+                if (a < c && b < c) {
+                    const float f = __double2float_rn(dacc[i][j][q]);
+                    Gu[(int64_t)a * c + b] = f;
+                    Gu[(int64_t)b * c + a] = f;
+                }
+            }
+}
+
+// ---------------------------------------------------------------- search
+
+__device__ __forceinline__ double block_max(double v, double *red) {
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    __syncthreads();
+    if (lane == 0) red[w] = v;
+    __syncthreads();
+    double r = red[0];
+    for (int q = 1; q < MX_WARPS; ++q) r = fmax(r, red[q]);
+    return r;
+}
+
+// Sums of DOT_BATCH dot products of row xi with the rows xs[0..nb) (length s),
+// a fixed reduction order; result in out[0..nb) (all threads see it after the
+// trailing barrier).
+__device__ void block_dots(const double *xi, const double *const *xs, int nb, int64_t s,
+                           double *red, double *out) {
+    double acc[DOT_BATCH];
+    for (int b = 0; b < DOT_BATCH; ++b) acc[b] = 0.0;
+    for (int64_t r = threadIdx.x; r < s; r += MX_THREADS) {
+        const double a = xi[r];
+        for (int b = 0; b < nb; ++b) acc[b] = __fma_rn(a, xs[b][r], acc[b]);
+    }
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    for (int b = 0; b < nb; ++b) {
+        const double v = warp_sum(acc[b]);
+        if (lane == 0) red[b * MX_WARPS + w] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < (unsigned)nb) {
+        double v = 0.0;
+        for (int q = 0; q < MX_WARPS; ++q) v = __dadd_rn(v, red[threadIdx.x * MX_WARPS + q]);
+        out[threadIdx.x] = v;
+    }
+    __syncthreads();
+}
+
+__global__ void __launch_bounds__(MX_THREADS)
+k_select_mixed(int64_t s, const int64_t *coff, const int32_t *members, const int64_t *goff,
+               double *Xs, float *Gt, float *Bd, double *Mall, const double *gdiag0,
+               const int64_t *roff, uint64_t seed, int64_t stage, int K, double eps, int32_t *kidx,
+               int32_t *kkv, int32_t *kel, int32_t *klvl, double *kO, int32_t *lvlidx,
+               int32_t *lvl_off, int32_t *nlev, int32_t *elimflag, unsigned long long *stats,
+               unsigned *status) {
+    extern __shared__ double sh[];
+    const int64_t u = blockIdx.x;
+    const int64_t base = coff[u];
+    const int c = (int)(coff[u + 1] - base);
+    const int64_t r0 = roff[u];
+    const int e = (int)(roff[u + 1] - r0);
+    double *X = Xs + base * s;
+    float *G = Gt + goff[u];
+    float *B = Bd + goff[u];
+    double *M = Mall + goff[u];
+    double *gd = sh;
+    double *md = gd + c;
+    double *w = md + c;
+    double *hi = w + c;
+    double *lo = hi + c;
+    double *red = lo + c;                       // MX_WARPS * DOT_BATCH
+    const int nwords = (c + 31) / 32;
+    uint32_t *mask = (uint32_t *)(red + MX_WARPS * DOT_BATCH);
+    int32_t *lvl = (int32_t *)(mask + nwords);
+    int32_t *lcnt = lvl + c;                    // e + 2
+    int32_t *sl = lcnt + e + 2;                 // shortlist, c
+    __shared__ int s_T[8], s_kk, s_maxlev, s_nsl, s_fall;
+    __shared__ double s_O[64], s_GT[64], s_dots[DOT_BATCH], s_es[SL_MAX + 8];
+    __shared__ int s_wcnt[MX_WARPS];
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+
+    for (int a = tid; a < c; a += MX_THREADS) {
+        gd[a] = gdiag0[base + a];
+        md[a] = M[(int64_t)a * c + a];
+        w[a] = gd[a] > 0.0 ? __ddiv_rn(1.0, __dsqrt_rn(gd[a])) : 0.0;
+        lvl[a] = 0;
+    }
+    for (int wi = tid; wi < nwords; wi += MX_THREADS) {
+        const int rem = c - wi * 32;
+        mask[wi] = rem >= 32 ? 0xffffffffu : ((1u << rem) - 1u);
+    }
+    for (int q = tid; q < e + 2; q += MX_THREADS) lcnt[q] = 0;
+    if (tid == 0) s_maxlev = 0;
+    __syncthreads();
+    // initial bound eps sqrt(G_aa G_bb), rounded up
+    for (int64_t q = tid; q < (int64_t)c * c; q += MX_THREADS) {
+        const int a = (int)(q / c), b = (int)(q - (int64_t)a * c);
+        const double v = __dmul_ru(__dmul_ru(eps, __dsqrt_ru(gd[a])), __dsqrt_ru(gd[b]));
+        B[q] = __double2float_ru(v);
+    }
+    __syncthreads();
+
+    int na = c;
+    unsigned long long n_rescored = 0, n_fall = 0, sl_max = 0;
+    for (int t = 0; t < e; ++t, --na) {
+        if (tid == 0) {
+            const uint64_t r = drawm(seed, (uint64_t)stage, (uint64_t)u, (uint64_t)t);
+            s_T[0] = nth_set(mask, nwords, (int64_t)__umul64hi(r, (uint64_t)na));
+            s_kk = K < na ? K : na;
+        }
+        __syncthreads();
+        const int i = s_T[0], kk = s_kk;
+        // score intervals from the reduced-precision row
+        for (int y = tid; y < c; y += MX_THREADS) {
+            double h = -1.0, l = -1.0;
+            if (y != i && on(mask, y)) {
+                const double sc = __dmul_rn(fabs((double)G[(int64_t)i * c + y]), w[y]);
+                const double d = __dmul_ru((double)B[(int64_t)i * c + y], __dmul_ru(w[y], 1.0 + 0x1p-40));
+                h = __dadd_ru(sc, __dadd_ru(d, __dmul_ru(sc, 0x1p-50)));
+                l = __dsub_rd(sc, __dadd_ru(d, __dmul_ru(sc, 0x1p-50)));
+            }
+            hi[y] = h;
+            lo[y] = l;
+        }
+        __syncthreads();
+        // threshold: the (kk-1)-th largest lower end (one occurrence of the
+        // maximum is removed between rounds)
+        double tau = -1.0;
+        for (int a = 1; a < kk; ++a) {
+            double mv = -1.0;
+            for (int y = tid; y < c; y += MX_THREADS) mv = fmax(mv, lo[y]);
+            mv = block_max(mv, red);
+            tau = mv;
+            if (a + 1 < kk) {
+                __syncthreads();
+                if (tid == 0)
+                    for (int y = 0; y < c; ++y)
+                        if (lo[y] == mv) {
+                            lo[y] = -1.0;
+                            break;
+                        }
+                __syncthreads();
+            }
+        }
+        // shortlist: candidates whose upper end reaches tau (ascending index)
+        {
+            int cnt = 0;
+            for (int y0 = 0; y0 < c; y0 += MX_THREADS) {
+                const int y = y0 + tid;
+                const bool in = y < c && hi[y] >= tau && hi[y] >= 0.0;
+                const unsigned bal = __ballot_sync(0xffffffffu, in);
+                if (lane == 0) s_wcnt[wid] = __popc(bal);
+                __syncthreads();
+                int off = cnt;
+                for (int q = 0; q < wid; ++q) off += s_wcnt[q];
+                int tot = 0;
+                for (int q = 0; q < MX_WARPS; ++q) tot += s_wcnt[q];
+                if (in) sl[off + __popc(bal & ((1u << lane) - 1u))] = y;
+                cnt += tot;
+                __syncthreads();
+            }
+            if (tid == 0) {
+                s_nsl = cnt;
+                s_fall = cnt > SL_MAX;
+            }
+            __syncthreads();
+        }
+        const int nsl = s_nsl;
+        if (s_fall) ++n_fall;
+        n_rescored += (unsigned long long)nsl;
+        sl_max = max(sl_max, (unsigned long long)nsl);
+        // FP64 re-score: G_iy = <X_i, X_y>; partners by FP64 score
+        double best_s[8];
+        int best_y[8];
+        double best_g[8];
+        for (int a = 0; a < 8; ++a) {
+            best_s[a] = -1.0;
+            best_y[a] = 0x7fffffff;
+            best_g[a] = 0.0;
+        }
+        for (int q0 = 0; q0 < nsl; q0 += DOT_BATCH) {
+            const int nb = min(DOT_BATCH, nsl - q0);
+            const double *xs[DOT_BATCH];
+            for (int b = 0; b < DOT_BATCH; ++b) xs[b] = X + (int64_t)sl[q0 + (b < nb ? b : 0)] * s;
+            block_dots(X + (int64_t)i * s, xs, nb, s, red, s_dots);
+            // every thread keeps the same running top list
+            for (int b = 0; b < nb; ++b) {
+                const int y = sl[q0 + b];
+                const double gv = s_dots[b];
+                const double sc = __dmul_rn(fabs(gv), w[y]);
+                // insert into the top kk-1 (ties to the smaller index)
+                int pos2 = kk - 1;
+                while (pos2 > 0 && (sc > best_s[pos2 - 1] || (sc == best_s[pos2 - 1] && y < best_y[pos2 - 1])))
+                    --pos2;
+                if (pos2 < kk - 1) {
+                    for (int a = kk - 2; a > pos2; --a) {
+                        best_s[a] = best_s[a - 1];
+                        best_y[a] = best_y[a - 1];
+                        best_g[a] = best_g[a - 1];
+                    }
+                    best_s[pos2] = sc;
+                    best_y[pos2] = y;
+                    best_g[pos2] = gv;
+                }
+            }
+            __syncthreads();
+        }
+        int T[8];
+        T[0] = i;
+        for (int a = 1; a < kk; ++a) {
+            int y = best_y[a - 1];
+            if (y < 0 || y >= c) {
+                // never taken (the shortlist holds at least kk - 1 candidates);
+                // keeps every index in range: the first active index not used
+                if (tid == 0) atomicOr(status, ST_NOT_CONVERGED);
+                for (y = 0; y < c; ++y) {
+                    bool used = !on(mask, y);
+                    for (int b = 0; b < a; ++b) used |= T[b] == y;
+                    if (!used) break;
+                }
+            }
+            T[a] = y;
+        }
+        // FP64 k x k block: diagonal kept, (i, partner) from the re-score, the
+        // partner pairs by further dot products
+        if (tid == 0) {
+            for (int a = 0; a < kk; ++a) s_GT[a * kk + a] = gd[T[a]];
+            for (int a = 1; a < kk; ++a) {
+                s_GT[a] = best_g[a - 1];
+                s_GT[a * kk] = best_g[a - 1];
+            }
+        }
+        for (int a = 1; a < kk; ++a) {
+            const int nb = kk - 1 - a;
+            if (nb <= 0) continue;
+            const double *xs[DOT_BATCH];
+            for (int b = 0; b < DOT_BATCH; ++b) xs[b] = X + (int64_t)T[a + 1 + (b < nb ? b : 0)] * s;
+            block_dots(X + (int64_t)T[a] * s, xs, nb, s, red, s_dots);
+            if (tid == 0)
+                for (int b = 0; b < nb; ++b) {
+                    s_GT[a * kk + a + 1 + b] = s_dots[b];
+                    s_GT[(a + 1 + b) * kk + a] = s_dots[b];
+                }
+        }
+        if (tid == 0) {
+            double O[64];
+            if (kk == 2) {
+                double cc, ss;
+                jacobi2(s_GT[0], s_GT[1], s_GT[3], cc, ss);
+                O[0] = cc;
+                O[1] = -ss;
+                O[2] = ss;
+                O[3] = cc;
+            } else if (!jacobi_k(kk, s_GT, O)) {
+                atomicOr(status, ST_NOT_CONVERGED);
+            }
+            for (int a = 0; a < kk * kk; ++a) s_O[a] = O[a];
+        }
+        __syncthreads();
+        // FP64 rows X_T <- O X_T
+        for (int64_t r = tid; r < s; r += MX_THREADS) {
+            double in[8], out[8];
+            for (int a = 0; a < kk; ++a) in[a] = X[(int64_t)T[a] * s + r];
+            for (int a = 0; a < kk; ++a) out[a] = rot_row(s_O, kk, a, in);
+            for (int a = 0; a < kk; ++a) X[(int64_t)T[a] * s + r] = out[a];
+        }
+        // reduced-precision Gram rows and their bound; FP64 local block M
+        {
+            float Of[64], Oa[64];
+            for (int a = 0; a < kk * kk; ++a) {
+                Of[a] = __double2float_rn(s_O[a]);
+                Oa[a] = fabsf(Of[a]);
+            }
+            // rounding of one rotated entry: kk products and sums in FP32 plus
+            // the FP32 rounding of O itself
+            const float gam = (float)(kk + 3) * 0x1p-24f;
+            for (int y = tid; y < c; y += MX_THREADS) {
+                bool inT = false;
+                for (int a = 0; a < kk; ++a) inT |= T[a] == y;
+                if (inT || !on(mask, y)) continue;
+                float gin[8], bin[8];
+                double min_[8];
+                for (int a = 0; a < kk; ++a) {
+                    gin[a] = G[(int64_t)T[a] * c + y];
+                    bin[a] = B[(int64_t)T[a] * c + y];
+                    min_[a] = M[(int64_t)T[a] * c + y];
+                }
+                for (int a = 0; a < kk; ++a) {
+                    float gv = 0.0f, bv = 0.0f, mag = 0.0f;
+                    for (int b = 0; b < kk; ++b) {
+                        gv = __fmaf_rn(Of[a * kk + b], gin[b], gv);
+                        bv = __fmaf_ru(Oa[a * kk + b], bin[b], bv);
+                        mag = __fmaf_ru(Oa[a * kk + b], fabsf(gin[b]), mag);
+                    }
+                    bv = __fmaf_ru(gam, mag, bv);
+                    G[(int64_t)T[a] * c + y] = gv;
+                    G[(int64_t)y * c + T[a]] = gv;
+                    B[(int64_t)T[a] * c + y] = bv;
+                    B[(int64_t)y * c + T[a]] = bv;
+                    const double mv = rot_row(s_O, kk, a, min_);
+                    M[(int64_t)T[a] * c + y] = mv;
+                    M[(int64_t)y * c + T[a]] = mv;
+                }
+            }
+        }
+        // tuple blocks: G_TT' = O G_TT O^T in FP64 (diagonal kept), M_TT' likewise
+        if (tid == 0 || tid == 32) {
+            const bool isg = tid == 0;
+            double X2[64], R[64];
+            for (int a = 0; a < kk; ++a)
+                for (int b = 0; b < kk; ++b)
+                    X2[a * kk + b] = isg ? s_GT[a * kk + b] : M[(int64_t)T[a] * c + T[b]];
+            for (int cc = 0; cc < kk; ++cc) {
+                double in[8];
+                for (int b = 0; b < kk; ++b) in[b] = X2[b * kk + cc];
+                for (int a = 0; a < kk; ++a) R[a * kk + cc] = rot_row(s_O, kk, a, in);
+            }
+            for (int a = 0; a < kk; ++a)
+                for (int b = a; b < kk; ++b) {
+                    double acc = __dmul_rn(R[a * kk + kk - 1], s_O[b * kk + kk - 1]);
+                    for (int cc = kk - 2; cc >= 0; --cc) acc = __fma_rn(R[a * kk + cc], s_O[b * kk + cc], acc);
+                    if (isg) {
+                        const float f = __double2float_rn(acc);
+                        const float bf = __fadd_ru(__fmul_ru(fabsf(f), 0x1p-22f), 1e-30f);
+                        G[(int64_t)T[a] * c + T[b]] = f;
+                        G[(int64_t)T[b] * c + T[a]] = f;
+                        B[(int64_t)T[a] * c + T[b]] = bf;
+                        B[(int64_t)T[b] * c + T[a]] = bf;
+                        if (a == b) gd[T[a]] = acc;
+                    } else {
+                        M[(int64_t)T[a] * c + T[b]] = acc;
+                        M[(int64_t)T[b] * c + T[a]] = acc;
+                        if (a == b) md[T[a]] = acc;
+                    }
+                }
+        }
+        __syncthreads();
+        if (tid < kk) {
+            const double gv = gd[T[tid]];
+            w[T[tid]] = gv > 0.0 ? __ddiv_rn(1.0, __dsqrt_rn(gv)) : 0.0;
+        }
+        if (tid == 0) {
+            int bi = 0;
+            double dbest = __dsub_rn(gd[T[0]], __dmul_rn(md[T[0]], md[T[0]]));
+            for (int a = 1; a < kk; ++a) {
+                const double d = __dsub_rn(gd[T[a]], __dmul_rn(md[T[a]], md[T[a]]));
+                if (d <= dbest) {
+                    dbest = d;
+                    bi = a;
+                }
+            }
+            const int le = T[bi];
+            int L = 0;
+            for (int a = 0; a < kk; ++a) L = max(L, lvl[T[a]]);
+            ++L;
+            for (int a = 0; a < kk; ++a) lvl[T[a]] = L;
+            s_maxlev = max(s_maxlev, L);
+            mask[le >> 5] &= ~(1u << (le & 31));
+            const int64_t rr = r0 + t;
+            for (int a = 0; a < K; ++a) kidx[rr * K + a] = a < kk ? T[a] : -1;
+            for (int a = 0; a < K * K; ++a) kO[rr * K * K + a] = a < kk * kk ? s_O[a] : 0.0;
+            kkv[rr] = kk;
+            kel[rr] = le;
+            klvl[rr] = L;
+        }
+        __syncthreads();
+    }
+    if (tid == 0) {
+        atomicAdd(&stats[0], n_rescored);
+        atomicAdd(&stats[1], n_fall);
+        atomicAdd(&stats[2], (unsigned long long)e);
+        atomicMax(&stats[3], sl_max);
+    }
+    const int nl = s_maxlev;
+    for (int t = tid; t < e; t += MX_THREADS) {
+        atomicAdd(&lcnt[klvl[r0 + t]], 1);
+        elimflag[members[base + kel[r0 + t]]] = (int32_t)stage;
+    }
+    __syncthreads();
+    if (tid == 0) {
+        int acc = 0;
+        for (int L = 1; L <= nl; ++L) {
+            const int cnt = lcnt[L];
+            lcnt[L] = acc;
+            lvl_off[r0 + u + L - 1] = (int32_t)(r0 + acc);
+            acc += cnt;
+        }
+        lvl_off[r0 + u + nl] = (int32_t)(r0 + acc);
+        nlev[u] = nl;
+    }
+    __syncthreads();
+    for (int t = tid; t < e; t += MX_THREADS) {
+        const int slot = atomicAdd(&lcnt[klvl[r0 + t]], 1);
+        lvlidx[r0 + slot] = (int32_t)(r0 + t);
+    }
+}
+
+// k = 2 rotations found by the k-point search, in the Givens records the
+// update and apply kernels use for k = 2.
+__global__ void k_to_givens(const int32_t *kidx, const int32_t *kel, const int32_t *klvl,
+                            const double *kO, const int32_t *lvlidx, int64_t nrot, RotRec *rec,
+                            Rot2 *lvlrot) {
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < nrot;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        rec[t] = RotRec{kidx[2 * t], kidx[2 * t + 1], kel[t], klvl[t], kO[4 * t], kO[4 * t + 2]};
+        const int64_t q = lvlidx[t];
+        lvlrot[t] = Rot2{kidx[2 * q], kidx[2 * q + 1], kO[4 * q], kO[4 * q + 2]};
+    }
+}
+
+}  // namespace
+
+pmmf_status mixed_stage_select(const DBuf<double> &D, int64_t s, const int32_t *pos,
+                               const StageClusters &cls, const std::vector<int64_t> &hcoff,
+                               int64_t cmax, int precision, uint64_t seed, int64_t stage,
+                               StageRotations &rot, int32_t *elimflag, unsigned long long *stats,
+                               unsigned *status, cudaStream_t st) {
+    const int64_t m = cls.m;
+    GramBlocks gb;   // goff and the FP64 local blocks M (G is not used here)
+    PMMF_TRY(gram_blocks(cls, gb, st));
+    DBuf<double> X;
+    DBuf<uint32_t> XH, XL;
+    DBuf<double> gd0;
+    DBuf<float> Gt, Bd;
+    PMMF_TRY(X.alloc(s * s, st));
+    const int64_t sp = precision == PMMF_PREC_BF16 ? s + (s & 1) : s;   // padded row length
+    PMMF_TRY(XH.alloc(precision == PMMF_PREC_BF16 ? s * sp / 2 : s * s, st));
+    PMMF_TRY(XL.alloc(precision == PMMF_PREC_BF16 ? s * sp / 2 : s * s, st));
+    PMMF_TRY(gd0.alloc(s, st));
+    PMMF_TRY(Gt.alloc(gb.total, st));
+    PMMF_TRY(Bd.alloc(gb.total, st));
+    if (precision == PMMF_PREC_BF16)
+        k_build_slab<PMMF_PREC_BF16><<<(unsigned)s, 256, 0, st>>>(D.p, s, sp, pos, cls.members.p, X.p,
+                                                                  XH.p, XL.p);
+    else
+        k_build_slab<PMMF_PREC_TF32><<<(unsigned)s, 256, 0, st>>>(D.p, s, sp, pos, cls.members.p, X.p,
+                                                                  XH.p, XL.p);
+    PMMF_TRY(launched("build_slab"));
+    k_row_norms<<<grid_for(s * 32, 256), 256, 0, st>>>(X.p, s, s, gd0.p);
+    PMMF_TRY(launched("row_norms"));
+    k_local_block<<<(unsigned)m, 256, 0, st>>>(D.p, s, pos, cls.coff.p, cls.members.p, gb.goff.p, gb.M.p);
+    PMMF_TRY(launched("local_block"));
+    std::vector<int32_t> tu, ta, tb;
+    for (int64_t u = 0; u < m; ++u) {
+        const int64_t c = hcoff[u + 1] - hcoff[u];
+        const int T = (int)((c + TG - 1) / TG);
+        for (int a = 0; a < T; ++a)
+            for (int b = a; b < T; ++b) {
+                tu.push_back((int32_t)u);
+                ta.push_back(a);
+                tb.push_back(b);
+            }
+    }
+    DBuf<int32_t> dtu, dta, dtb;
+    PMMF_TRY(dtu.alloc((int64_t)tu.size(), st));
+    PMMF_TRY(dta.alloc((int64_t)tu.size(), st));
+    PMMF_TRY(dtb.alloc((int64_t)tu.size(), st));
+    PMMF_CUDA_TRY(cudaMemcpyAsync(dtu.p, tu.data(), sizeof(int32_t) * tu.size(), cudaMemcpyHostToDevice, st));
+    PMMF_CUDA_TRY(cudaMemcpyAsync(dta.p, ta.data(), sizeof(int32_t) * ta.size(), cudaMemcpyHostToDevice, st));
+    PMMF_CUDA_TRY(cudaMemcpyAsync(dtb.p, tb.data(), sizeof(int32_t) * tb.size(), cudaMemcpyHostToDevice, st));
+    double flops = 0.0;
+    for (int64_t u = 0; u < m; ++u) {
+        const double c = (double)(hcoff[u + 1] - hcoff[u]);
+        flops += c * (c + 1.0) * (double)s;
+    }
+    prof_begin(KF_GRAM, st);
+    if (precision == PMMF_PREC_BF16)
+        k_tc_gram<PMMF_PREC_BF16><<<(unsigned)tu.size(), 128, 0, st>>>(XH.p, XL.p, sp, cls.coff.p, gb.goff.p,
+                                                                      dtu.p, dta.p, dtb.p, Gt.p);
+    else
+        k_tc_gram<PMMF_PREC_TF32><<<(unsigned)tu.size(), 128, 0, st>>>(XH.p, XL.p, sp, cls.coff.p, gb.goff.p,
+                                                                      dtu.p, dta.p, dtb.p, Gt.p);
+    prof_end(KF_GRAM, st, (precision == PMMF_PREC_BF16 ? 4.0 : 8.0) * (double)s * (double)s +
+                              4.0 * (double)gb.total, 3.0 * flops);
+    PMMF_TRY(launched("tc_gram"));
+
+    // eps, relative to |x||y| per term: the split leaves |x - hi - lo| <= u^2 |x|
+    // (u = 2^-11 TF32, 2^-8 BF16), the dropped lo lo^T term is <= u^2 |x||y|,
+    // so the three products miss x y by <= 3 u^2 (1 + u) |x||y|; FP32
+    // accumulation of 3 KFLUSH products per chunk (taken at twice the
+    // round-to-nearest bound) and the FP64 sum of the chunks and the final
+    // FP32 rounding add the rest; Cauchy-Schwarz turns sum |x||y| into
+    // sqrt(G_ii G_jj).  10% margin.
+    const double uin = precision == PMMF_PREC_BF16 ? 0x1p-8 : 0x1p-11;
+    const double eps = 1.1 * (3.0 * uin * uin * (1.0 + uin) + 6.0 * (double)KFLUSH * 0x1p-24 +
+                              ((double)s / KFLUSH + 2.0) * 0x1p-52 + 0x1p-24);
+    const int K = rot.K;
+    const int64_t nr = std::max<int64_t>(rot.nrot, 1);
+    PMMF_TRY(rot.kidx.alloc(nr * K, st));
+    PMMF_TRY(rot.kO.alloc(nr * K * K, st));
+    PMMF_TRY(rot.kk.alloc(nr, st));
+    PMMF_TRY(rot.kel.alloc(nr, st));
+    PMMF_TRY(rot.klvl.alloc(nr, st));
+    PMMF_TRY(rot.lvlidx.alloc(nr, st));
+    PMMF_TRY(rot.lvl_off.alloc(rot.nrot + m + 1, st));
+    PMMF_TRY(rot.nlev.zeros(m, st));
+    const size_t sh = sizeof(double) * (5 * (size_t)cmax + MX_WARPS * DOT_BATCH) +
+                      sizeof(uint32_t) * (size_t)((cmax + 31) / 32) +
+                      sizeof(int32_t) * (size_t)(3 * cmax + 4);
+    if (sh > 200 * 1024) {
+        set_error("cluster too large for the shortlist search");
+        return PMMF_ERR_UNSUPPORTED;
+    }
+    if (sh > 48 * 1024)
+        PMMF_CUDA_TRY(cudaFuncSetAttribute(k_select_mixed, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh));
+    prof_begin(KF_SELECT, st);
+    k_select_mixed<<<(unsigned)m, MX_THREADS, sh, st>>>(
+        s, cls.coff.p, cls.members.p, gb.goff.p, X.p, Gt.p, Bd.p, gb.M.p, gd0.p, rot.roff.p, seed,
+        stage, K, eps, rot.kidx.p, rot.kk.p, rot.kel.p, rot.klvl.p, rot.kO.p, rot.lvlidx.p,
+        rot.lvl_off.p, rot.nlev.p, elimflag, stats, status);
+    prof_end(KF_SELECT, st, 0.0, 0.0);
+    PMMF_TRY(launched("select_mixed"));
+    if (K == 2) {
+        PMMF_TRY(rot.rec.alloc(nr, st));
+        PMMF_TRY(rot.lvl.alloc(nr, st));
+        k_to_givens<<<grid_for(rot.nrot, 256), 256, 0, st>>>(rot.kidx.p, rot.kel.p, rot.klvl.p,
+                                                             rot.kO.p, rot.lvlidx.p, rot.nrot,
+                                                             rot.rec.p, rot.lvl.p);
+        PMMF_TRY(launched("to_givens"));
+    }
+    return PMMF_OK;
+}
+
+}  // namespace pmmf

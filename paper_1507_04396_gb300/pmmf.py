@@ -25,6 +25,7 @@ ERR_NOT_SPD, ERR_SINGULAR_CORE, ERR_NOT_CONVERGED, ERR_TIMEOUT, ERR_UNSUPPORTED 
 HOST, DEVICE = 0, 1
 CSR, DENSE = 0, 1
 OP_A, OP_A_INV, OP_U, OP_UT, OP_H, OP_H_INV = 0, 1, 2, 3, 4, 5
+PREC_FP64, PREC_TF32, PREC_BF16 = 0, 1, 2
 
 STATUS_NAMES = {0: "OK", 1: "INVALID_ARG", 2: "NOT_SYMMETRIC", 3: "NONFINITE", 4: "OOM",
                 5: "CUDA", 6: "NOT_SPD", 7: "SINGULAR_CORE", 8: "NOT_CONVERGED", 9: "TIMEOUT",
@@ -47,7 +48,8 @@ class Params(C.Structure):
     _fields_ = [("k", C.c_int), ("eta", C.c_double), ("cluster_size", C.c_int),
                 ("core_size", C.c_int), ("seed", C.c_uint64), ("max_stages", C.c_int),
                 ("lloyd_iters", C.c_int), ("coords", C.c_void_p), ("coord_dim", C.c_int),
-                ("coords_location", C.c_int), ("record_stages", C.c_int)]
+                ("coords_location", C.c_int), ("record_stages", C.c_int),
+                ("precision", C.c_int)]
 
 
 class Info(C.Structure):
@@ -66,7 +68,8 @@ EXPORTS = ["pmmf_factor", "pmmf_apply", "pmmf_solve_precond", "pmmf_free", "pmmf
            "pmmf_get_info", "pmmf_get_stage_info", "pmmf_get_stage_clusters",
            "pmmf_get_stage_rotations", "pmmf_get_h", "pmmf_get_stage_matrix",
            "pmmf_launch_count", "pmmf_apply_backward", "pmmf_get_angles", "pmmf_set_angles",
-           "pmmf_set_h", "pmmf_factor_blockdiag", "pmmf_factor_batched", "pmmf_get_batch"]
+           "pmmf_set_h", "pmmf_factor_blockdiag", "pmmf_factor_batched", "pmmf_get_batch",
+           "pmmf_get_precision_stats"]
 
 _lib = None
 
@@ -121,6 +124,8 @@ def load(path: str = LIB_PATH):
     L.pmmf_factor_batched.restype = i32
     L.pmmf_factor_batched.argtypes = [i64, vp, C.POINTER(Params), C.POINTER(vp), vp]
     L.pmmf_get_batch.restype = i32
+    L.pmmf_get_precision_stats.restype = i32
+    L.pmmf_get_precision_stats.argtypes = [vp, vp, vp, vp, vp]
     L.pmmf_get_batch.argtypes = [vp, vp, vp, vp, vp, vp]
     L.pmmf_profile_begin.restype = i32
     L.pmmf_profile_begin.argtypes = [C.c_uint]
@@ -352,6 +357,12 @@ class Factorization:
         pmmf_apply(self.handle, op, x, y, nrhs, nrhs, stream)
         return y
 
+    def precision_stats(self) -> dict:
+        v = [C.c_int64() for _ in range(4)]
+        _check(load().pmmf_get_precision_stats(self.handle, *[C.byref(x) for x in v]))
+        return dict(rescored=v[0].value, fallbacks=v[1].value, steps=v[2].value,
+                    max_shortlist=v[3].value)
+
     def batch(self) -> dict:
         """nmat, core_stride, block_off, errors, core_dim of a batch handle."""
         nm, cs = C.c_int64(), C.c_int64()
@@ -433,7 +444,8 @@ class Factorization:
 
 
 def factor(a, *, k=2, eta=0.5, cluster_size=256, core_size=16, seed=0, max_stages=0,
-           lloyd_iters=10, coords="auto", record_stages=False, stream=None) -> Factorization:
+           lloyd_iters=10, coords="auto", record_stages=False, precision=PREC_FP64,
+           stream=None) -> Factorization:
     """Factor a symmetric matrix (SymCSR-like object with numpy or torch arrays, or a
     dense 2-D array/tensor).  coords='auto' uses ``a.coords`` when present."""
     m, keep = make_matrix(a)
@@ -446,7 +458,7 @@ def factor(a, *, k=2, eta=0.5, cluster_size=256, core_size=16, seed=0, max_stage
         keep.append(coords)
         cp, cd, cl = _ptr(coords), coords.shape[1], _loc(coords)
     prm = Params(k, eta, cluster_size, core_size, seed, max_stages, lloyd_iters, cp, cd, cl,
-                 1 if record_stages else 0)
+                 1 if record_stages else 0, precision)
     h = pmmf_factor(m, prm, stream)
     return Factorization(h, k)
 
