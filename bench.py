@@ -523,6 +523,185 @@ def run_gpu_batch(args):
     return 0
 
 
+RBF = dict(n=16384, components=20, gen_seed=2, k=3, eta=0.5, cluster_size=512, core_size=512, seed=0)
+POISSON = dict(nx=128, gen_seed=4, k=2, eta=0.5, cluster_size=256, core_size=1024, seed=0, nrhs=8,
+               rtol=1e-8)
+PREC = {"fp64": 0, "tf32": 1, "bf16": 2}
+
+
+def _timed(stream, fn, steps, flush):
+    """Run fn() steps times with an L2 flush before each, CUDA events on stream."""
+    import torch
+    total, out = 0.0, None
+    for _ in range(steps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        out = fn()
+        e1.record(stream)
+        e1.synchronize()
+        total += e0.elapsed_time(e1)
+        if hasattr(out, "close") and _ < steps - 1:
+            out.close()
+    return total, out
+
+
+def run_gpu_rbf(args):
+    """Dense Gaussian RBF kernel (3-D mixture), k = 3, clusters of 512: the
+    dense path in FP64 and, with --precision, the tensor-core Gram shortlist."""
+    import numpy as np
+    import torch
+    from paper_1507_04396_gb300 import build, inputs as I, pmmf
+    build.build()
+    pmmf.load()
+    dev = torch.device("cuda", 0)
+    n = args.n if args.n != WORK["n"] else RBF["n"]
+    a = I.rbf_mixture(n, RBF["components"], seed=RBF["gen_seed"])
+    D = torch.from_numpy(a.to_dense()).to(dev)
+    co = torch.from_numpy(a.coords).to(dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+    kw = dict(k=RBF["k"], eta=RBF["eta"], cluster_size=RBF["cluster_size"],
+              core_size=RBF["core_size"], seed=RBF["seed"])
+    prec = PREC[args.precision]
+
+    def run(p):
+        return lambda: pmmf.factor(D, coords=co, precision=p, stream=stream, **kw)
+
+    for _ in range(max(args.warmup, 0)):
+        run(prec)().close()
+    pmmf.pmmf_profile_begin(pmmf.FAMILIES)
+    run(prec)().close()
+    breakdown = pmmf.pmmf_profile_end()
+    clocks = Clocks(0)
+    torch.cuda.synchronize()
+    clocks.start()
+    pmmf.pmmf_profile_begin(["gram"])
+    l0 = pmmf.pmmf_launch_count()
+    ms, f = _timed(stream, run(prec), args.steps, flush)
+    launches = pmmf.pmmf_launch_count() - l0
+    gram = pmmf.pmmf_profile_end()["gram"]
+    clk = clocks.stop()
+    info, st = f.info(), f.precision_stats()
+    rots = [f.rotations(p) for p in range(info.stages)]
+    f.close()
+    ref = None
+    if prec != 0:
+        # the FP64 mode on the same input: time and identical selections
+        run(0)().close()
+        ms64, g = _timed(stream, run(0), 1, flush)
+        same = sum(int((r[2] == q[2]).all(axis=1).sum()) for r, q in
+                   zip(rots, [g.rotations(p) for p in range(g.info().stages)]))
+        ref = {"fp64_ms_per_step": ms64, "fp64_frobenius_error": g.info().error,
+               "identical_tuples": same, "rotations": info.rotations}
+        g.close()
+    value = n * n * args.steps / (ms / 1e3)
+    if prec != 0:
+        peak = float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["bf16_tflops"]) \
+            if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")) else 1933.5
+        # tf32 runs at half the bf16 rate; the split does three products per term
+        pk = peak / 2 if prec == 1 else peak
+        ach = gram["flops"] / (gram["ms"] / 1e3) / 1e12
+        roof = {"bound": "tensor", "achieved": ach, "peak": pk, "unit": "TFLOP/s", "frac": ach / pk,
+                "traffic": None, "kernel_family": "gram (tensor-core split product)",
+                "peak_kind": "measured bf16" + (" x 1/2 (tf32)" if prec == 1 else "")}
+    else:
+        ach = gram["flops"] / (gram["ms"] / 1e3) / 1e12
+        roof = {"bound": "alu", "achieved": ach, "peak": FP64_NOMINAL_TFLOPS, "unit": "TFLOP/s",
+                "frac": ach / FP64_NOMINAL_TFLOPS, "traffic": None, "kernel_family": "gram (FP64)",
+                "peak_kind": "nominal FP64"}
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64" if prec == 0 else f"f64 + {args.precision} Gram",
+        "data": "synthetic",
+        "config": {"workload": f"rbf_mixture n={n} (20-component 3-D Gaussian mixture, seed 2), dense "
+                               f"FP64 Gaussian kernel, sigma = median distance; k-means clusters of 512, "
+                               f"k=3, eta=0.5, core 512", "n": n, "nnz": n * n,
+                   "stages": info.stages, "rotations": info.rotations, "frobenius_error": info.error,
+                   "precision": args.precision, "l2": "256 MiB buffer written between timed steps"},
+        "roofline": roof, "shortlist": st, "fp64_mode": ref,
+        "kernel_breakdown_ms": {k: round(v["ms"], 3) for k, v in breakdown.items() if v["launches"]},
+        "cpu_baseline": None, "e2e": None, "gpu_launches": int(launches), "clocks": clk,
+    }
+    print(json.dumps(line))
+    return 0
+
+
+def run_gpu_poisson(args):
+    """3-D variable-coefficient Poisson (log-normal, 128^3), pMMF as the PCG
+    preconditioner for 8 right-hand sides to 1e-8."""
+    import numpy as np
+    import torch
+    from paper_1507_04396_gb300 import build, inputs as I, pmmf
+    build.build()
+    pmmf.load()
+    dev = torch.device("cuda", 0)
+    a = I.poisson3d(POISSON["nx"], seed=POISSON["gen_seed"])
+    A = I.SymCSR(a.n, torch.from_numpy(a.rowptr).to(dev), torch.from_numpy(a.col).to(dev),
+                 torch.from_numpy(a.val).to(dev))
+    co = torch.from_numpy(a.coords).to(dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+    kw = dict(k=POISSON["k"], eta=POISSON["eta"], cluster_size=POISSON["cluster_size"],
+              core_size=POISSON["core_size"], seed=POISSON["seed"])
+    fac = lambda: pmmf.factor(A, coords=co, stream=stream, **kw)
+    for _ in range(max(args.warmup, 0)):
+        fac().close()
+    clocks = Clocks(0)
+    torch.cuda.synchronize()
+    clocks.start()
+    l0 = pmmf.pmmf_launch_count()
+    ms, f = _timed(stream, fac, args.steps, flush)
+    rng = np.random.default_rng(POISSON["gen_seed"])
+    rng.standard_normal(a.n)
+    b = torch.from_numpy(rng.standard_normal((a.n, POISSON["nrhs"]))).to(dev)
+    f.solve(A, b, rtol=POISSON["rtol"], maxit=3000)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    st, x, iters, relres = f.solve(A, b, rtol=POISSON["rtol"], maxit=3000)
+    torch.cuda.synchronize()
+    pcg_s = time.perf_counter() - t0
+    launches = pmmf.pmmf_launch_count() - l0
+    xx = torch.randn(a.n, POISSON["nrhs"], dtype=torch.float64, device=dev)
+    yy = torch.empty_like(xx)
+    for _ in range(3):
+        f.apply(pmmf.OP_A_INV, xx, yy)
+    pmmf.pmmf_profile_begin(["apply"])
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(10):
+        f.apply(pmmf.OP_A_INV, xx, yy)
+    e1.record(stream)
+    e1.synchronize()
+    ap = pmmf.pmmf_profile_end()["apply"]
+    clk = clocks.stop()
+    info = f.info()
+    hbm, hbm_kind = peaks()
+    ach = ap["bytes"] / (ap["ms"] / 1e3) / 1e9
+    line = {
+        "metric": METRIC, "value": a.nnz * args.steps / (ms / 1e3), "unit": UNIT, "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": "poisson3d 128^3 (7-point FV, log-normal sigma=1, seed 4), FP64 CSR; "
+                               "k-means clusters of 256 on cell centres, k=2, eta=0.5, core 1024",
+                   "n": a.n, "nnz": a.nnz, "stages": info.stages, "frobenius_error": info.error,
+                   "l2": "256 MiB buffer written between timed steps"},
+        "pcg": {"nrhs": POISSON["nrhs"], "rtol": POISSON["rtol"], "status": st, "seconds": pcg_s,
+                "iterations": [int(v) for v in iters], "max_relres": float(np.max(relres))},
+        "roofline": {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
+                     "traffic": None, "kernel_family": "apply (rotation passes of A~^-1 x, 8 RHS)",
+                     "peak_kind": hbm_kind},
+        "cpu_baseline": None, "e2e": None, "gpu_launches": int(launches), "clocks": clk,
+    }
+    print(json.dumps(line))
+    f.close()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -531,10 +710,18 @@ def main():
     ap.add_argument("--impl", choices=["gpu", "reference"], default="gpu")
     ap.add_argument("--n", type=int, default=WORK["n"])
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
-    ap.add_argument("--workload", choices=["knn", "er_batch"], default="knn",
+    ap.add_argument("--workload", choices=["knn", "er_batch", "rbf_dense", "poisson"],
+                    default="knn",
                     help="knn: the kNN Laplacian (default); er_batch: 4,096 independent ER "
-                         "Laplacians factored as one batch")
+                         "Laplacians factored as one batch; rbf_dense: dense RBF kernel, k = 3; "
+                         "poisson: 128^3 Poisson factorization and PCG")
+    ap.add_argument("--precision", choices=list(PREC), default="fp64",
+                    help="Gram precision of the rbf_dense workload")
     args = ap.parse_args()
+    if args.workload == "rbf_dense":
+        return run_gpu_rbf(args)
+    if args.workload == "poisson":
+        return run_gpu_poisson(args)
     if args.workload == "er_batch":
         return run_reference_batch(args) if args.impl == "reference" else run_gpu_batch(args)
     if args.impl == "reference":
