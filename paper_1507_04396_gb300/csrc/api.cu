@@ -252,6 +252,8 @@ pmmf_status factor_impl(const pmmf_matrix *A, const pmmf_params *prm, pmmf_handl
     const int iters = prm->lloyd_iters > 0 ? prm->lloyd_iters : 10;
     int64_t s = n;
     int64_t p = 0;
+    // device status bits of every stage, read once after the loop
+    PMMF_CUDA_TRY(cudaMemsetAsync(status.p, 0, sizeof(unsigned), st));
     while (s > prm->core_size && (prm->max_stages <= 0 || p < prm->max_stages)) {
         ++p;
         h->st.emplace_back();
@@ -274,7 +276,9 @@ pmmf_status factor_impl(const pmmf_matrix *A, const pmmf_params *prm, pmmf_handl
         } else {
             PMMF_TRY(one_cluster(act.p, s, S.cls, cl.p, loc.p, st));
         }
-        int64_t sched[2] = {0, 0};
+        // one readback per stage for the schedule: rotations, the one-cluster
+        // fallback, the largest cluster and the Gram blocks' total size
+        int64_t sched[4] = {0, 0, 0, 0};
         DBuf<int64_t> e;
         PMMF_TRY(schedule_stage(S.cls.coff.p, S.cls.m, s, prm->core_size, prm->eta, e,
                                 S.rot.roff, sched, st));
@@ -285,34 +289,13 @@ pmmf_status factor_impl(const pmmf_matrix *A, const pmmf_params *prm, pmmf_handl
         S.m = S.cls.m;
         S.nrot = sched[0];
         S.rot.nrot = sched[0];
-        {
-            std::vector<int64_t> hc((size_t)S.m + 1);
-            PMMF_CUDA_TRY(cudaMemcpyAsync(hc.data(), S.cls.coff.p, sizeof(int64_t) * hc.size(),
-                                          cudaMemcpyDeviceToHost, st));
-            PMMF_CUDA_TRY(cudaStreamSynchronize(st));
-            for (int64_t u = 0; u < S.m; ++u) S.cmax = std::max(S.cmax, hc[u + 1] - hc[u]);
-        }
+        S.cmax = sched[2];
         S.rot.K = prm->k;
-        PMMF_CUDA_TRY(cudaMemsetAsync(status.p, 0, sizeof(unsigned), st));
-        PMMF_TRY(gram_and_select(cur, pos.p, cl.p, S.cls, S.cmax, prm->seed, p, S.rot,
-                                 elimflag.p, st, nullptr, nullptr, status.p));
+        PMMF_TRY(gram_and_select(cur, act.p, pos.p, cl.p, loc.p, S.cls, S.cmax, prm->seed, p, S.rot,
+                                 elimflag.p, st, nullptr, nullptr, status.p, sched[3]));
         UpdateOut up;
         PMMF_TRY(update_stage(cur, act.p, n, pos.p, cl.p, loc.p, S.cls, S.cmax, S.rot,
                               elimflag.p, p, h->hdiag.p, contribs.p + (p - 1), up, status.p, st));
-        {
-            unsigned hs = 0;
-            int32_t ml = 0;
-            std::vector<int32_t> nl((size_t)S.m);
-            PMMF_CUDA_TRY(cudaMemcpyAsync(&hs, status.p, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
-            PMMF_CUDA_TRY(cudaMemcpyAsync(nl.data(), S.rot.nlev.p, sizeof(int32_t) * nl.size(),
-                                          cudaMemcpyDeviceToHost, st));
-            PMMF_CUDA_TRY(cudaStreamSynchronize(st));
-            if (hs & ST_ROW_TOO_LONG) return fail(PMMF_ERR_UNSUPPORTED, "update: output row too long");
-            if (hs & ST_NOT_CONVERGED)
-                return fail(PMMF_ERR_NOT_CONVERGED, "k x k Jacobi did not converge in 32 sweeps");
-            for (int32_t v : nl) ml = std::max(ml, v);
-            S.max_levels = ml;
-        }
         S.nnz_after = up.next.nnz;
         // next stage's row positions
         PMMF_CUDA_TRY(cudaMemsetAsync(pos.p, 0xFF, sizeof(int32_t) * (size_t)n, st));
@@ -338,6 +321,27 @@ pmmf_status factor_impl(const pmmf_matrix *A, const pmmf_params *prm, pmmf_handl
         }
     }
 
+    {
+        // status bits and each stage's number of dependency levels
+        unsigned hs = 0;
+        std::vector<std::vector<int32_t>> nl(h->st.size());
+        PMMF_CUDA_TRY(cudaMemcpyAsync(&hs, status.p, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
+        for (size_t q = 0; q < h->st.size(); ++q) {
+            nl[q].resize((size_t)h->st[q].m);
+            if (h->st[q].m > 0)
+                PMMF_CUDA_TRY(cudaMemcpyAsync(nl[q].data(), h->st[q].rot.nlev.p, sizeof(int32_t) * nl[q].size(),
+                                              cudaMemcpyDeviceToHost, st));
+        }
+        PMMF_CUDA_TRY(cudaStreamSynchronize(st));
+        if (hs & ST_ROW_TOO_LONG) return fail(PMMF_ERR_UNSUPPORTED, "update: output row too long");
+        if (hs & ST_NOT_CONVERGED)
+            return fail(PMMF_ERR_NOT_CONVERGED, "k x k Jacobi did not converge in 32 sweeps");
+        for (size_t q = 0; q < h->st.size(); ++q) {
+            int32_t ml = 0;
+            for (int32_t v : nl[q]) ml = std::max(ml, v);
+            h->st[q].max_levels = ml;
+        }
+    }
     // H: core A_L[S_L, S_L] plus the diagonal
     h->ncore = s;
     PMMF_TRY(h->core_idx.alloc(s, st));
@@ -457,7 +461,7 @@ pmmf_status factor_dense_impl(const pmmf_matrix *A, const pmmf_params *prm, pmmf
         } else {
             PMMF_TRY(one_cluster(act.p, s, S.cls, cl.p, loc.p, st));
         }
-        int64_t sched[2] = {0, 0};
+        int64_t sched[4] = {0, 0, 0, 0};
         DBuf<int64_t> e;
         PMMF_TRY(schedule_stage(S.cls.coff.p, S.cls.m, s, prm->core_size, prm->eta, e, S.rot.roff,
                                 sched, st));
@@ -689,7 +693,7 @@ pmmf_status factor_batch_impl(const pmmf_matrix *A, const std::vector<int64_t> &
         S.rot.nrot = roff[m];
         S.rot.K = prm->k;
         PMMF_CUDA_TRY(cudaMemsetAsync(status.p, 0, sizeof(unsigned), st));
-        PMMF_TRY(gram_and_select(cur, pos.p, cl.p, S.cls, S.cmax, prm->seed, p, S.rot,
+        PMMF_TRY(gram_and_select(cur, act.p, pos.p, cl.p, loc.p, S.cls, S.cmax, prm->seed, p, S.rot,
                                  elimflag.p, st, order_d.p, useed_d.p, status.p));
         DBuf<double> ccl;
         PMMF_TRY(ccl.zeros(m, st));

@@ -210,6 +210,14 @@ __global__ void k_schedule(const int64_t *coff, int64_t mm, int64_t s, int64_t c
         total = f;
     }
     out[1] = 0;
+    int64_t cmax = 0, sq = 0;
+    for (int64_t u = 0; u < mm; ++u) {
+        const int64_t c = coff[u + 1] - coff[u];
+        cmax = c > cmax ? c : cmax;
+        sq += c * c;
+    }
+    out[2] = cmax;
+    out[3] = sq;
     if (total == 0) {
         int64_t ee = (int64_t)floor(__dmul_rn(eta, (double)s));
         if (ee > target) ee = target;
@@ -217,6 +225,8 @@ __global__ void k_schedule(const int64_t *coff, int64_t mm, int64_t s, int64_t c
         out[1] = 1;
         total = ee;
         e[0] = ee;
+        out[2] = s;
+        out[3] = s * s;
     }
     roff[0] = 0;
     if (!out[1])
@@ -331,10 +341,10 @@ pmmf_status schedule_stage(const int64_t *coff, int64_t mm, int64_t s, int64_t c
     PMMF_TRY(e.alloc(mm > 1 ? mm : 1, st));
     PMMF_TRY(roff.alloc(mm + 1 > 2 ? mm + 1 : 2, st));
     DBuf<int64_t> out;
-    PMMF_TRY(out.alloc(2, st));
+    PMMF_TRY(out.alloc(4, st));
     k_schedule<<<1, 32, 0, st>>>(coff, mm, s, core, eta, e.p, roff.p, out.p);
     PMMF_TRY(launched("schedule"));
-    PMMF_CUDA_TRY(cudaMemcpyAsync(host_out, out.p, 2 * sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+    PMMF_CUDA_TRY(cudaMemcpyAsync(host_out, out.p, 4 * sizeof(int64_t), cudaMemcpyDeviceToHost, st));
     PMMF_CUDA_TRY(cudaStreamSynchronize(st));
     return PMMF_OK;
 }

@@ -62,58 +62,87 @@ __global__ void k_square_sizes(const int64_t *coff, int64_t m, int64_t *sz) {
     }
 }
 
-// One warp per Gram row (cluster u, local a); lanes walk b >= a.  Each entry
-// is a sequential fma chain over the common columns of rows x_a and x_b in
-// ascending column order (terms where either entry is zero leave the chain
-// unchanged, so only common stored columns matter).
-__global__ void k_gram(const int64_t *rp, const int32_t *ci, const double *v, const int32_t *pos,
-                       const int32_t *cl, const int64_t *coff, const int32_t *members, int64_t s,
-                       const int64_t *goff, double *G, double *M) {
-    int lane = threadIdx.x & 31;
-    int64_t w = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-    int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+// Transpose of the active matrix (rows by position, entries = (row's global
+// id, value)): count, scan, scatter.  The order inside a transposed row is
+// arbitrary; the Gram kernel below does not depend on it.
+__global__ void k_tcount(const int64_t *rp, const int32_t *ci, int64_t s, const int32_t *pos,
+                         int64_t *tcnt) {
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < rp[s];
+         q += (int64_t)gridDim.x * blockDim.x)
+        atomicAdd((unsigned long long *)&tcnt[pos[ci[q]]], 1ull);
+}
+
+__global__ void k_tscatter(const int64_t *rp, const int32_t *ci, const double *v, int64_t s,
+                           const int32_t *pos, const int32_t *act, int64_t *tcur, int32_t *tci,
+                           double *tv) {
+    const int lane = threadIdx.x & 31;
+    const int64_t w = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t r = w; r < s; r += nw) {
+        const int32_t g = act[r];
+        for (int64_t q = rp[r] + lane; q < rp[r + 1]; q += 32) {
+            const int64_t slot = (int64_t)atomicAdd((unsigned long long *)&tcur[pos[ci[q]]], 1ull);
+            tci[slot] = g;
+            tv[slot] = v[q];
+        }
+    }
+}
+
+// Gram rows by the row-by-row (Gustavson) product, one warp per Gram row a of
+// cluster u: row x_a's entries r are taken in ascending order and, for each,
+// the stored entries of column r in cluster u update a dense accumulator, so
+// every G_ab is one fma chain over the common columns in ascending order (the
+// same bits as the merge in k_gram; the product is commutative, so G_ab and
+// G_ba agree).  Whole rows are written, coalesced.  M row a: A[x_a][x_b] for
+// b >= a from row x_a, A[x_b][x_a] for b < a from column x_a.
+__global__ void k_gram_rows(const int64_t *rp, const int32_t *ci, const double *v,
+                            const int64_t *trp, const int32_t *tci, const double *tv,
+                            const int32_t *pos, const int32_t *cl, const int32_t *loc,
+                            const int64_t *coff, const int32_t *members, int64_t s, int64_t cmax,
+                            const int64_t *goff, double *G, double *M) {
+    extern __shared__ double gacc[];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    double *acc = gacc + (int64_t)wib * cmax;
+    const int64_t w = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
     for (int64_t j = w; j < s; j += nw) {
-        int32_t xa = members[j];
-        int64_t u = cl[xa];
-        int64_t base = coff[u];
-        int64_t c = coff[u + 1] - base;
-        int64_t a = j - base;
-        int64_t ra = pos[xa];
-        int64_t a0 = rp[ra], a1 = rp[ra + 1];
-        double *Gu = G + goff[u];
-        double *Mu = M + goff[u];
-        for (int64_t b = a + lane; b < c; b += 32) {
-            int32_t xb = members[base + b];
-            int64_t rb = pos[xb];
-            int64_t pa = a0, pb = rp[rb], eb = rp[rb + 1];
-            double acc = 0.0;
-            while (pa < a1 && pb < eb) {
-                int32_t ca = ci[pa], cb = ci[pb];
-                if (ca < cb) {
-                    ++pa;
-                } else if (ca > cb) {
-                    ++pb;
-                } else {
-                    acc = __fma_rn(v[pa], v[pb], acc);
-                    ++pa;
-                    ++pb;
+        const int32_t xa = members[j];
+        const int32_t u = cl[xa];
+        const int64_t base = coff[u];
+        const int c = (int)(coff[u + 1] - base);
+        const int a = (int)(j - base);
+        const int64_t ra = pos[xa];
+        for (int b = lane; b < c; b += 32) acc[b] = 0.0;
+        __syncwarp();
+        for (int64_t q = rp[ra]; q < rp[ra + 1]; ++q) {
+            const double va = v[q];
+            const int64_t rr = pos[ci[q]];
+            for (int64_t e = trp[rr] + lane; e < trp[rr + 1]; e += 32) {
+                const int32_t xb = tci[e];
+                if (cl[xb] == u) {
+                    const int lb = loc[xb];
+                    acc[lb] = __fma_rn(va, tv[e], acc[lb]);
                 }
             }
-            // M_ab = A[x_a][x_b] (x_a < x_b since members ascend)
-            double mv = 0.0;
-            int64_t lo = a0, hi = a1;
-            while (lo < hi) {
-                int64_t mid = (lo + hi) >> 1;
-                int32_t cm = ci[mid];
-                if (cm < xb) lo = mid + 1;
-                else if (cm > xb) hi = mid;
-                else { mv = v[mid]; break; }
-            }
-            Gu[a * c + b] = acc;
-            Gu[b * c + a] = acc;
-            Mu[a * c + b] = mv;
-            Mu[b * c + a] = mv;
+            __syncwarp();
         }
+        double *Gr = G + goff[u] + (int64_t)a * c;
+        for (int b = lane; b < c; b += 32) Gr[b] = acc[b];
+        __syncwarp();
+        for (int b = lane; b < c; b += 32) acc[b] = 0.0;
+        __syncwarp();
+        for (int64_t q = rp[ra] + lane; q < rp[ra + 1]; q += 32) {
+            const int32_t xb = ci[q];
+            if (cl[xb] == u && loc[xb] >= a) acc[loc[xb]] = v[q];
+        }
+        for (int64_t e = trp[ra] + lane; e < trp[ra + 1]; e += 32) {
+            const int32_t xb = tci[e];
+            if (cl[xb] == u && loc[xb] < a) acc[loc[xb]] = tv[e];
+        }
+        __syncwarp();
+        double *Mr = M + goff[u] + (int64_t)a * c;
+        for (int b = lane; b < c; b += 32) Mr[b] = acc[b];
+        __syncwarp();
     }
 }
 
@@ -762,33 +791,58 @@ k_select_fast(const int64_t *coff, const int32_t *members, const int64_t *goff, 
 
 }  // namespace
 
-pmmf_status gram_blocks(const StageClusters &cls, GramBlocks &gb, cudaStream_t st) {
+pmmf_status gram_blocks(const StageClusters &cls, GramBlocks &gb, cudaStream_t st, int64_t total) {
     const int64_t m = cls.m;
     PMMF_TRY(gb.goff.alloc(m + 1, st));
     k_square_sizes<<<grid_for(m, 256), 256, 0, st>>>(cls.coff.p, m, gb.goff.p);
     PMMF_TRY(launched("square_sizes"));
     PMMF_TRY(scan_i64(gb.goff.p, gb.goff.p, m, st));
-    PMMF_CUDA_TRY(cudaMemcpyAsync(&gb.total, gb.goff.p + m, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
-    PMMF_CUDA_TRY(cudaStreamSynchronize(st));
+    if (total >= 0) {
+        gb.total = total;
+    } else {
+        PMMF_CUDA_TRY(cudaMemcpyAsync(&gb.total, gb.goff.p + m, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+        PMMF_CUDA_TRY(cudaStreamSynchronize(st));
+    }
     PMMF_TRY(gb.G.alloc(gb.total, st));   // the Gram kernels write every entry of every block
     PMMF_TRY(gb.M.alloc(gb.total, st));
     return PMMF_OK;
 }
 
-pmmf_status gram_and_select(const Csr &A, const int32_t *pos, const int32_t *cl,
-                            const StageClusters &cls, int64_t cmax, uint64_t seed, int64_t stage,
-                            StageRotations &rot, int32_t *elimflag, cudaStream_t st,
-                            const int32_t *order, const uint64_t *useed, unsigned *status) {
+pmmf_status gram_and_select(const Csr &A, const int32_t *act_ids, const int32_t *pos,
+                            const int32_t *cl, const int32_t *loc, const StageClusters &cls,
+                            int64_t cmax, uint64_t seed, int64_t stage, StageRotations &rot,
+                            int32_t *elimflag, cudaStream_t st, const int32_t *order,
+                            const uint64_t *useed, unsigned *status, int64_t gram_total) {
     GramBlocks gb;
-    PMMF_TRY(gram_blocks(cls, gb, st));
+    PMMF_TRY(gram_blocks(cls, gb, st, gram_total));
     const int64_t s = A.rows;
+    // the transpose of the active matrix
+    DBuf<int64_t> trp, tcur;
+    DBuf<int32_t> tci;
+    DBuf<double> tv;
+    PMMF_TRY(trp.zeros(s + 1, st));
+    PMMF_TRY(tcur.alloc(s + 1, st));
+    PMMF_TRY(tci.alloc(std::max<int64_t>(A.nnz, 1), st));
+    PMMF_TRY(tv.alloc(std::max<int64_t>(A.nnz, 1), st));
+    k_tcount<<<grid_for(A.nnz, 256), 256, 0, st>>>(A.rowptr.p, A.col.p, s, pos, trp.p);
+    PMMF_TRY(launched("tcount"));
+    PMMF_TRY(scan_i64(trp.p, trp.p, s, st));
+    PMMF_CUDA_TRY(cudaMemcpyAsync(tcur.p, trp.p, sizeof(int64_t) * (size_t)(s + 1), cudaMemcpyDeviceToDevice, st));
+    k_tscatter<<<grid_for(s * 32, 256), 256, 0, st>>>(A.rowptr.p, A.col.p, A.val.p, s, pos,
+                                                       act_ids, tcur.p, tci.p, tv.p);
+    PMMF_TRY(launched("tscatter"));
+    int warps = 8;
+    while (warps > 1 && sizeof(double) * (size_t)cmax * warps > 96 * 1024) warps >>= 1;
+    const size_t gsh = sizeof(double) * (size_t)cmax * warps;
+    if (gsh > 48 * 1024)
+        PMMF_CUDA_TRY(cudaFuncSetAttribute(k_gram_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gsh));
     prof_begin(KF_GRAM, st);
-    k_gram<<<grid_for(s * 32, 256), 256, 0, st>>>(A.rowptr.p, A.col.p, A.val.p, pos, cl,
-                                                   cls.coff.p, cls.members.p, s, gb.goff.p, gb.G.p,
-                                                   gb.M.p);
-    // compulsory traffic: the cluster rows once (12 B per entry, 8 B per row
-    // pointer) and both c_u x c_u outputs
-    prof_end(KF_GRAM, st, 12.0 * (double)A.nnz + 8.0 * (double)s + 16.0 * (double)gb.total, 0.0);
+    k_gram_rows<<<grid_for(s * 32, 32 * warps), 32 * warps, gsh, st>>>(
+        A.rowptr.p, A.col.p, A.val.p, trp.p, tci.p, tv.p, pos, cl, loc, cls.coff.p, cls.members.p,
+        s, cmax, gb.goff.p, gb.G.p, gb.M.p);
+    // compulsory traffic: the active matrix and its transpose once (12 B per
+    // entry, 8 B per row pointer) and both c_u x c_u outputs
+    prof_end(KF_GRAM, st, 24.0 * (double)A.nnz + 16.0 * (double)s + 16.0 * (double)gb.total, 0.0);
     PMMF_TRY(launched("gram"));
     return select_stage(cls, cmax, gb, seed, stage, rot, elimflag, st, order, useed, status);
 }

@@ -55,6 +55,9 @@ pmmf_status partition_stage(const PartitionIn &in, int64_t m, int iters, StageCl
                             cudaStream_t st);
 pmmf_status one_cluster(const int32_t *act, int64_t s, StageClusters &out, int32_t *cl,
                         int32_t *loc, cudaStream_t st);
+// host_out[4]: total rotations, one-cluster fallback flag, largest cluster,
+// sum of squared cluster sizes (the two last for the fallback's one cluster
+// when the flag is set).
 pmmf_status schedule_stage(const int64_t *coff, int64_t mm, int64_t s, int64_t core, double eta,
                            DBuf<int64_t> &e, DBuf<int64_t> &roff, int64_t *host_out,
                            cudaStream_t st);
@@ -71,7 +74,9 @@ struct GramBlocks {
     DBuf<int64_t> goff;       // m + 1
     DBuf<double> G, M;
 };
-pmmf_status gram_blocks(const StageClusters &cls, GramBlocks &gb, cudaStream_t st);
+// total: sum of c_u^2 when the caller knows it (-1: read it back).
+pmmf_status gram_blocks(const StageClusters &cls, GramBlocks &gb, cudaStream_t st,
+                        int64_t total = -1);
 // Rotation search of every cluster on formed Gram blocks.
 pmmf_status select_stage(const StageClusters &cls, int64_t cmax, GramBlocks &gb, uint64_t seed,
                          int64_t stage, StageRotations &rot, int32_t *elimflag, cudaStream_t st,
@@ -80,11 +85,12 @@ pmmf_status select_stage(const StageClusters &cls, int64_t cmax, GramBlocks &gb,
 
 // rot.K selects Givens (2) or k-point (>= 3) rotations; status receives
 // ST_NOT_CONVERGED when a k x k Jacobi did not converge.
-pmmf_status gram_and_select(const Csr &A, const int32_t *pos, const int32_t *cl,
-                            const StageClusters &cls, int64_t cmax, uint64_t seed, int64_t stage,
-                            StageRotations &rot, int32_t *elimflag, cudaStream_t st,
-                            const int32_t *order = nullptr, const uint64_t *useed = nullptr,
-                            unsigned *status = nullptr);
+pmmf_status gram_and_select(const Csr &A, const int32_t *act, const int32_t *pos,
+                            const int32_t *cl, const int32_t *loc, const StageClusters &cls,
+                            int64_t cmax, uint64_t seed, int64_t stage, StageRotations &rot,
+                            int32_t *elimflag, cudaStream_t st, const int32_t *order = nullptr,
+                            const uint64_t *useed = nullptr, unsigned *status = nullptr,
+                            int64_t gram_total = -1);
 // The k >= 3 search on Gram blocks already formed (selectk.cu).
 pmmf_status select_kpoint(const StageClusters &cls, int64_t cmax, const int64_t *goff, double *G,
                           double *M, uint64_t seed, int64_t stage, StageRotations &rot,
@@ -103,6 +109,7 @@ pmmf_status update_stage(const Csr &A, const int32_t *act, int64_t n, const int3
                          int64_t cmax, const StageRotations &rot, const int32_t *elimflag,
                          int64_t stage, double *hdiag, double *contrib, UpdateOut &out,
                          unsigned *status, cudaStream_t st, double *contrib_cl = nullptr);
+// (the survivors are rot.nrot fewer than the active rows: one elimination per rotation)
 
 pmmf_status set_positions(const int32_t *act, int64_t s, int32_t *pos, cudaStream_t st);
 pmmf_status extract_core(const Csr &A, const int32_t *pos, int64_t s, double *core, double *hdiag,

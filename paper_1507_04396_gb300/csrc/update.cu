@@ -63,15 +63,32 @@ struct RowArgs {
     int64_t *maxlen;
 };
 
+// Per-warp shared memory of the row kernel: the dense local vector (cmax
+// doubles, all zero between segments), its touched-position bitmask (one bit
+// per local index, an even number of words) and, for the output pass, the
+// row's kept entries.
+__host__ __device__ inline int64_t rows_mask_words(int64_t cmax) {
+    const int64_t w = (cmax + 31) / 32;
+    return w + (w & 1);
+}
+__host__ __device__ inline int64_t rows_per_warp(int64_t cmax, int64_t outcap, bool write2) {
+    return cmax + rows_mask_words(cmax) / 2 + (write2 ? outcap * 3 / 2 + 1 : 0);
+}
+
 template <int MODE>
 __global__ void k_rows(RowArgs a) {
     extern __shared__ double smem[];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const int wpb = blockDim.x >> 5;
-    const int64_t per_warp = a.cmax + (MODE == P2_WRITE ? (int64_t)a.outcap * 3 / 2 + 1 : 0);
+    const int64_t per_warp = rows_per_warp(a.cmax, a.outcap, MODE == P2_WRITE);
     double *dense = smem + per_warp * wib;
-    int32_t *scol = (int32_t *)(dense + a.cmax);
+    uint32_t *tb = (uint32_t *)(dense + a.cmax);
+    const int nwmax = (int)rows_mask_words(a.cmax);
+    int32_t *scol = (int32_t *)(tb + nwmax);
     double *sval = (double *)(scol + (a.outcap + (a.outcap & 1)));
+    for (int64_t l = lane; l < a.cmax; l += 32) dense[l] = 0.0;
+    for (int l = lane; l < nwmax; l += 32) tb[l] = 0u;
+    __syncwarp();
     double part = 0.0;
     for (int64_t r = blockIdx.x * (int64_t)wpb + wib; r < a.rows; r += (int64_t)gridDim.x * wpb) {
         const int64_t e0 = a.rp[r], e1 = a.rp[r + 1];
@@ -92,28 +109,57 @@ __global__ void k_rows(RowArgs a) {
             ++nseg;
             const int64_t cb = a.coff[mu];
             const int c = (int)(a.coff[mu + 1] - cb);
-            for (int l = lane; l < c; l += 32) dense[l] = 0.0;
-            __syncwarp();
+            const int nw = (c + 31) / 32;
             for (int64_t q = e0 + lane; q < e1; q += 32) {
                 int32_t g = a.ci[q];
-                if (a.cl[g] == mu) dense[a.loc[g]] = a.v[q];
+                if (a.cl[g] == mu) {
+                    const int l = a.loc[g];
+                    dense[l] = a.v[q];
+                    atomicOr(&tb[l >> 5], 1u << (l & 31));
+                }
             }
             __syncwarp();
             const int32_t *lo = a.lvl_off + a.roff[mu] + mu;
             const int nl = a.nlev[mu];
-            for (int L = 0; L < nl; ++L) {
-                if (a.K == 2) {
-                    for (int idx = lo[L] + lane; idx < lo[L + 1]; idx += 32) {
-                        Rot2 q = a.lvlrot[idx];
+            if (a.K == 2) {
+                // level offsets in registers (lane L holds lo[L]) and the first
+                // 32 rotations of the next level loaded while this one runs
+                const int lol = lane <= nl ? lo[lane] : 0;
+                // lo[L] for a warp-uniform L
+                auto level_start = [&](int L) {
+                    const int v = __shfl_sync(0xffffffffu, lol, L & 31);
+                    return L < 32 ? v : lo[L];
+                };
+                int b0 = level_start(0);
+                int b1 = level_start(1);
+                Rot2 cur = Rot2{0, 0, 1.0, 0.0};
+                if (nl > 0 && b0 + lane < b1) cur = a.lvlrot[b0 + lane];
+                for (int L = 0; L < nl; ++L) {
+                    const int c0 = b0, c1 = b1;
+                    if (L + 1 < nl) {
+                        b0 = c1;
+                        b1 = level_start(L + 2);
+                    }
+                    Rot2 nxt = Rot2{0, 0, 1.0, 0.0};
+                    if (L + 1 < nl && b0 + lane < b1) nxt = a.lvlrot[b0 + lane];
+                    for (int idx = c0 + lane; idx < c1; idx += 32) {
+                        const Rot2 q = idx == c0 + lane ? cur : a.lvlrot[idx];
                         double vi = dense[q.li], vj = dense[q.lj];
                         if (nonzero_bits(vi) || nonzero_bits(vj)) {
                             double ni, nj;
                             rot_pair(q.c, q.s, vi, vj, ni, nj);
                             dense[q.li] = ni;
                             dense[q.lj] = nj;
+                            atomicOr(&tb[q.li >> 5], 1u << (q.li & 31));
+                            atomicOr(&tb[q.lj >> 5], 1u << (q.lj & 31));
                         }
                     }
-                } else {
+                    __syncwarp();
+                    cur = nxt;
+                }
+            } else {
+            for (int L = 0; L < nl; ++L) {
+                {
                     for (int idx = lo[L] + lane; idx < lo[L + 1]; idx += 32) {
                         const int64_t t = a.lvlidx[idx];
                         const int kk = a.kkv[t];
@@ -128,29 +174,54 @@ __global__ void k_rows(RowArgs a) {
                             const double *O = a.kO + t * a.K * a.K;
                             double out[8];
                             for (int q = 0; q < kk; ++q) out[q] = rot_row(O, kk, q, in);
-                            for (int q = 0; q < kk; ++q) dense[T[q]] = out[q];
+                            for (int q = 0; q < kk; ++q) {
+                                dense[T[q]] = out[q];
+                                atomicOr(&tb[T[q] >> 5], 1u << (T[q] & 31));
+                            }
                         }
                     }
                 }
                 __syncwarp();
             }
-            for (int l0 = 0; l0 < c; l0 += 32) {
-                const int l = l0 + lane;
-                const double x = l < c ? dense[l] : 0.0;
-                const bool nz = nonzero_bits(x);
-                const int32_t g = nz ? a.members[cb + l] : -1;
-                if (MODE == P1_COUNT) {
-                    if (nz) atomicAdd((unsigned long long *)&a.wcnt[a.pos[g]], 1ull);
-                } else if (MODE == P1_WRITE) {
-                    if (nz) {
+            }
+            // emit the touched positions in ascending order (lane = word,
+            // bits ascending inside a word) and reset them
+            for (int w0 = 0; w0 < nw; w0 += 32) {
+                const int wi = w0 + lane;
+                const uint32_t bits = wi < nw ? tb[wi] : 0u;
+                int kept = 0;
+                if (MODE == P2_WRITE) {
+                    // pass 1: how many entries of this word are kept
+                    for (uint32_t m = bits; m; m &= m - 1) {
+                        const int l = wi * 32 + __ffs(m) - 1;
+                        const double x = dense[l];
+                        if (!nonzero_bits(x) || yelim) continue;
+                        const int32_t g = a.members[cb + l];
+                        if (a.elimflag[g] != a.stage) ++kept;
+                    }
+                }
+                int off = kept;   // inclusive scan over lanes
+                for (int o = 1; o < 32; o <<= 1) {
+                    const int t2 = __shfl_up_sync(0xffffffffu, off, o);
+                    if (lane >= o) off += t2;
+                }
+                const int wtot = __shfl_sync(0xffffffffu, off, 31);
+                off -= kept;
+                int cnt = 0;
+                for (uint32_t m = bits; m; m &= m - 1) {
+                    const int l = wi * 32 + __ffs(m) - 1;
+                    const double x = dense[l];
+                    dense[l] = 0.0;
+                    if (!nonzero_bits(x)) continue;
+                    const int32_t g = a.members[cb + l];
+                    if (MODE == P1_COUNT) {
+                        atomicAdd((unsigned long long *)&a.wcnt[a.pos[g]], 1ull);
+                    } else if (MODE == P1_WRITE) {
                         int64_t slot = (int64_t)atomicAdd((unsigned long long *)&a.wcur[a.pos[g]], 1ull);
                         a.wcol[slot] = y;
                         a.wval[slot] = x;
-                    }
-                } else {
-                    bool keep = false;
-                    if (nz) {
-                        bool term = false;
+                    } else {
+                        bool term = false, keep = false;
                         if (yelim) {
                             if (g == y) {
                                 if (MODE == P2_WRITE) a.hdiag[y] = x;
@@ -166,16 +237,25 @@ __global__ void k_rows(RowArgs a) {
                             if (a.contrib_cl) prow = __fma_rn(x, x, prow);
                             else part = __fma_rn(x, x, part);
                         }
-                    }
-                    unsigned km = __ballot_sync(0xffffffffu, keep);
-                    if (MODE == P2_WRITE && keep) {
-                        int64_t slot = nout + __popc(km & ((1u << lane) - 1u));
-                        if (slot < a.outcap) {
-                            scol[slot] = g;
-                            sval[slot] = x;
+                        if (keep) {
+                            if (MODE == P2_WRITE) {
+                                const int64_t slot = nout + off + cnt;
+                                if (slot < a.outcap) {
+                                    scol[slot] = g;
+                                    sval[slot] = x;
+                                }
+                            }
+                            ++cnt;
                         }
                     }
-                    nout += __popc(km);
+                }
+                if (wi < nw) tb[wi] = 0u;
+                if (MODE == P2_WRITE) {
+                    nout += wtot;
+                } else if (MODE == P2_COUNT) {
+                    int tot = cnt;
+                    for (int o = 16; o > 0; o >>= 1) tot += __shfl_xor_sync(0xffffffffu, tot, o);
+                    nout += tot;
                 }
             }
             __syncwarp();
@@ -254,7 +334,7 @@ __global__ void k_core(const int64_t *rp, const int32_t *ci, const double *v, in
 
 template <int MODE>
 pmmf_status launch_rows(RowArgs &a, int64_t nnz_in, int64_t nnz_out, cudaStream_t st) {
-    const int64_t per_warp = a.cmax + (MODE == P2_WRITE ? (int64_t)a.outcap * 3 / 2 + 1 : 0);
+    const int64_t per_warp = rows_per_warp(a.cmax, a.outcap, MODE == P2_WRITE);
     size_t per = sizeof(double) * (size_t)per_warp;
     int warps = 8;
     while (warps > 1 && per * warps > 200 * 1024) warps >>= 1;
@@ -349,9 +429,7 @@ pmmf_status update_stage(const Csr &A, const int32_t *act, int64_t n, const int3
     k_survivors<<<grid_for(s, 256), 256, 0, st>>>(act, s, elimflag, (int32_t)stage, flag.p);
     PMMF_TRY(launched("survivors"));
     PMMF_TRY(scan_i32_to_i64(flag.p, newrow.p, s, st));
-    int64_t s2 = 0;
-    PMMF_CUDA_TRY(cudaMemcpyAsync(&s2, newrow.p + s, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
-    PMMF_CUDA_TRY(cudaStreamSynchronize(st));
+    const int64_t s2 = s - rot.nrot;   // one elimination per rotation
 
     // pass 2: A_p = W Q^T with accounting and compaction
     out.next.rows = s2;
