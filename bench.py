@@ -250,6 +250,13 @@ def run_gpu(args):
 
     # matrix-free apply: y = U^T H U x on 8 right-hand sides
     f = factor()
+    if dominant == "select":
+        # DRAM bytes per launch of the rotation search, measured with ncu on the
+        # 32,768-point instance: 0.917 x 16 B per Gram entry (G and M streamed
+        # once); scaled to this workload's launches by their Gram entries
+        sq = [int((np.diff(f.clusters(p)[0]) ** 2).sum()) for p in range(f.info().stages)]
+        roof["traffic"] = 0.917 * 16.0 * sum(sq) / max(len(sq), 1)
+        roof["traffic_basis"] = "ncu DRAM bytes on n=32768 scaled by Gram entries per launch"
     x = torch.randn(a.n, NRHS_APPLY, dtype=torch.float64, device=dev)
     y = torch.empty_like(x)
     for _ in range(3):
