@@ -9,6 +9,10 @@
 // < 2^32), ties to the lower centroid, centroid = round(sum / count) with halves
 // up, an empty cluster keeps its centroid.  Sums are integers, so the atomics
 // that accumulate them are order independent.
+#include <cooperative_groups.h>
+
+#include <algorithm>
+
 #include "common.cuh"
 #include "stage.cuh"
 
@@ -132,6 +136,56 @@ __global__ void k_assign(const int32_t *act, int64_t s, const int32_t *q, const 
         label[r] = (int32_t)bt;
         for (int d = 0; d < DIM; ++d) atomicAdd(&sum[bt * DIM + d], (unsigned long long)p[d]);
         atomicAdd(&cnt[bt], 1ull);
+    }
+}
+
+// All Lloyd iterations in one cooperative launch (every block resident):
+// per iteration the accumulators are cleared, every point is assigned to its
+// nearest centroid (as k_assign) and, except after the last iteration, the
+// centroids are recomputed (as k_centroids), with a grid-wide barrier between
+// the phases.  Integer sums, so the result is independent of the order of the
+// atomics.
+template <int DIM>
+__global__ void k_lloyd(const int32_t *act, int64_t s, const int32_t *q, int32_t *cen, int64_t m,
+                        int iters, int32_t *label, unsigned long long *sum,
+                        unsigned long long *cnt) {
+    namespace cg = cooperative_groups;
+    cg::grid_group grid = cg::this_grid();
+    extern __shared__ int32_t sc[];
+    const int64_t gt = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t gs = (int64_t)gridDim.x * blockDim.x;
+    for (int it = 0; it < iters; ++it) {
+        for (int64_t t = gt; t < m * DIM; t += gs) sum[t] = 0ull;
+        for (int64_t t = gt; t < m; t += gs) cnt[t] = 0ull;
+        for (int64_t t = threadIdx.x; t < m * DIM; t += blockDim.x) sc[t] = cen[t];
+        grid.sync();
+        for (int64_t r = gt; r < s; r += gs) {
+            const int32_t g = act[r];
+            int32_t p[DIM];
+            for (int d = 0; d < DIM; ++d) p[d] = q[(int64_t)g * DIM + d];
+            uint32_t best = 0xffffffffu;
+            int64_t bt = 0;
+            for (int64_t t = 0; t < m; ++t) {
+                uint32_t dd = 0;
+                for (int d = 0; d < DIM; ++d) {
+                    const int32_t z = p[d] - sc[t * DIM + d];
+                    dd += (uint32_t)(z * z);
+                }
+                if (dd < best) { best = dd; bt = t; }
+            }
+            label[r] = (int32_t)bt;
+            for (int d = 0; d < DIM; ++d) atomicAdd(&sum[bt * DIM + d], (unsigned long long)p[d]);
+            atomicAdd(&cnt[bt], 1ull);
+        }
+        grid.sync();
+        if (it + 1 < iters) {
+            for (int64_t t = gt; t < m; t += gs) {
+                const unsigned long long c = cnt[t];
+                if (c == 0) continue;
+                for (int d = 0; d < DIM; ++d) cen[t * DIM + d] = (int32_t)((sum[t * DIM + d] + c / 2) / c);
+            }
+            grid.sync();
+        }
     }
 }
 
@@ -288,6 +342,36 @@ pmmf_status partition_stage(const PartitionIn &in, int64_t m, int iters, StageCl
         set_error("too many clusters for the assignment kernel");
         return PMMF_ERR_UNSUPPORTED;
     }
+    if (iters <= 0) {
+        set_error("lloyd_iters must be positive");
+        return PMMF_ERR_INVALID_ARG;
+    }
+    // one cooperative launch for all iterations when every block fits at once
+    const void *lloyd = dim == 1 ? (const void *)k_lloyd<1> : dim == 2 ? (const void *)k_lloyd<2>
+                                                                   : (const void *)k_lloyd<3>;
+    if (sh > 48 * 1024)
+        PMMF_CUDA_TRY(cudaFuncSetAttribute(lloyd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh));
+    int dev = 0, nsm = 0, per_sm = 0, coop = 0;
+    PMMF_CUDA_TRY(cudaGetDevice(&dev));
+    PMMF_CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    PMMF_CUDA_TRY(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev));
+    PMMF_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, lloyd, 256, sh));
+    if (coop && per_sm > 0) {
+        const int64_t want = (s + 255) / 256;
+        const unsigned g = (unsigned)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)nsm * per_sm));
+        const int32_t *a_act = in.act;
+        const int32_t *a_q = in.q;
+        int32_t *a_cen = cen.p, *a_label = label.p;
+        int64_t a_s = s, a_m = m;
+        int a_it = iters;
+        unsigned long long *a_sum = sum.p, *a_cnt = cnt.p;
+        void *args[] = {&a_act, &a_s, &a_q, &a_cen, &a_m, &a_it, &a_label, &a_sum, &a_cnt};
+        prof_begin(KF_PARTITION, st);
+        PMMF_CUDA_TRY(cudaLaunchCooperativeKernel(lloyd, dim3(g), dim3(256), args, sh, st));
+        prof_end(KF_PARTITION, st, (double)iters * (double)s * (8.0 + 4.0 * dim),
+                 3.0 * dim * (double)iters * (double)s * (double)m);
+        PMMF_TRY(launched("lloyd"));
+    } else {
     auto assign = dim == 1 ? (void *)k_assign<1> : dim == 2 ? (void *)k_assign<2> : (void *)k_assign<3>;
     if (sh > 48 * 1024)
         PMMF_CUDA_TRY(cudaFuncSetAttribute(assign, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh));
@@ -308,9 +392,6 @@ pmmf_status partition_stage(const PartitionIn &in, int64_t m, int iters, StageCl
             PMMF_TRY(launched("centroids"));
         }
     }
-    if (iters <= 0) {
-        set_error("lloyd_iters must be positive");
-        return PMMF_ERR_INVALID_ARG;
     }
     // clusters: nonempty labels in order; members ascending by global id
     PMMF_TRY(nflag.alloc(m, st));
