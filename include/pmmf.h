@@ -320,6 +320,19 @@ pmmf_status pmmf_get_h(const pmmf_handle *f, double *hdiag, int32_t *core_idx, d
 pmmf_status pmmf_get_stage_matrix(const pmmf_handle *f, int p, int64_t *rowptr_n1, int32_t *col,
                                   double *val, int64_t *nnz);
 
+/* ---- launch tuning (no counterpart in the paper) ---------------------------
+ * Launch shapes an offline sweep may choose per cluster-size bucket
+ * (paper_1507_04396_gb300/autotune.py writes them to a JSON file that the
+ * Python binding applies at load time).  param: PMMF_TUNE_ROWS_WARPS (warps
+ * per block of the blocked-update row kernel, 1..8), PMMF_TUNE_GRAM_WARPS
+ * (warps per block of the Gram kernel, 1..8).  A value applies to launches
+ * whose largest cluster has at most max_size coordinates and no smaller
+ * bucket matches; shared-memory limits still halve it when needed.  Process
+ * wide; INVALID_ARG for an unknown param or a value outside 1..32. */
+enum { PMMF_TUNE_ROWS_WARPS = 0, PMMF_TUNE_GRAM_WARPS = 1 };
+pmmf_status pmmf_set_tuning(int param, int64_t max_size, int value);
+void pmmf_clear_tuning(void);
+
 /* Number of GPU kernel launches this process has issued through the library. */
 uint64_t pmmf_launch_count(void);
 

@@ -54,6 +54,14 @@ inline unsigned grid_for(int64_t items, int per_block, int64_t cap = 152 * 64) {
     return (unsigned)g;
 }
 
+// ---------------------------------------------------------------- launch tuning
+
+// Launch parameters that an offline sweep may set per cluster-size bucket
+// (pmmf_set_tuning); tuned(param, size, fallback) returns the value of the
+// smallest bucket whose bound is >= size, else fallback.
+enum TuneParam : int { TUNE_ROWS_WARPS = 0, TUNE_GRAM_WARPS = 1, TUNE_COUNT = 2 };
+int tuned(int param, int64_t size, int fallback);
+
 // ---------------------------------------------------------------- profiling
 
 // Kernel families that can be timed with CUDA events on their launch stream.

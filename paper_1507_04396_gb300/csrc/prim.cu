@@ -1,6 +1,7 @@
 // prim.cu -- data-movement primitives of the pMMF library: scans, stable
 // counting sort / radix sort, CSR construction and validation, reductions.
 #include <cstdlib>
+#include <algorithm>
 #include <mutex>
 #include <vector>
 #include <string>
@@ -517,6 +518,26 @@ void prof_end(int family, cudaStream_t st, double bytes, double flops) {
     t_open = nullptr;
 }
 
+namespace {
+struct TuneTable {
+    std::mutex mu;
+    std::vector<std::pair<int64_t, int>> b[TUNE_COUNT];   // (bucket bound, value), ascending
+};
+TuneTable &tune_table() {
+    static TuneTable t;
+    return t;
+}
+}  // namespace
+
+int tuned(int param, int64_t size, int fallback) {
+    if (param < 0 || param >= TUNE_COUNT) return fallback;
+    TuneTable &t = tune_table();
+    std::lock_guard<std::mutex> g(t.mu);
+    for (const auto &e : t.b[param])
+        if (size <= e.first) return e.second;
+    return fallback;
+}
+
 }  // namespace pmmf
 
 extern "C" {
@@ -555,6 +576,36 @@ pmmf_status pmmf_profile_end(double *ms, int64_t *launches, double *bytes, doubl
     pmmf::g_prof.clear();
     pmmf::g_prof_mask = 0;
     return PMMF_OK;
+}
+
+}  // extern "C"
+
+extern "C" {
+
+pmmf_status pmmf_set_tuning(int param, int64_t max_size, int value) {
+    using namespace pmmf;
+    if (param < 0 || param >= TUNE_COUNT || max_size < 1 || value < 1 || value > 32) {
+        set_error("pmmf_set_tuning: unknown parameter or value out of range");
+        return PMMF_ERR_INVALID_ARG;
+    }
+    TuneTable &t = tune_table();
+    std::lock_guard<std::mutex> g(t.mu);
+    auto &v = t.b[param];
+    for (auto &e : v)
+        if (e.first == max_size) {
+            e.second = value;
+            return PMMF_OK;
+        }
+    v.emplace_back(max_size, value);
+    std::sort(v.begin(), v.end());
+    return PMMF_OK;
+}
+
+void pmmf_clear_tuning(void) {
+    using namespace pmmf;
+    TuneTable &t = tune_table();
+    std::lock_guard<std::mutex> g(t.mu);
+    for (auto &v : t.b) v.clear();
 }
 
 }  // extern "C"

@@ -831,7 +831,7 @@ pmmf_status gram_and_select(const Csr &A, const int32_t *act_ids, const int32_t 
     k_tscatter<<<grid_for(s * 32, 256), 256, 0, st>>>(A.rowptr.p, A.col.p, A.val.p, s, pos,
                                                        act_ids, tcur.p, tci.p, tv.p);
     PMMF_TRY(launched("tscatter"));
-    int warps = 8;
+    int warps = tuned(TUNE_GRAM_WARPS, cmax, 8);
     while (warps > 1 && sizeof(double) * (size_t)cmax * warps > 96 * 1024) warps >>= 1;
     const size_t gsh = sizeof(double) * (size_t)cmax * warps;
     if (gsh > 48 * 1024)

@@ -336,7 +336,7 @@ template <int MODE>
 pmmf_status launch_rows(RowArgs &a, int64_t nnz_in, int64_t nnz_out, cudaStream_t st) {
     const int64_t per_warp = rows_per_warp(a.cmax, a.outcap, MODE == P2_WRITE);
     size_t per = sizeof(double) * (size_t)per_warp;
-    int warps = 8;
+    int warps = tuned(TUNE_ROWS_WARPS, a.cmax, 8);
     while (warps > 1 && per * warps > 200 * 1024) warps >>= 1;
     if (per * warps > 220 * 1024) {
         set_error("row transform: cluster or output row too large for shared memory");

@@ -69,7 +69,7 @@ EXPORTS = ["pmmf_factor", "pmmf_apply", "pmmf_solve_precond", "pmmf_free", "pmmf
            "pmmf_get_stage_rotations", "pmmf_get_h", "pmmf_get_stage_matrix",
            "pmmf_launch_count", "pmmf_apply_backward", "pmmf_get_angles", "pmmf_set_angles",
            "pmmf_set_h", "pmmf_factor_blockdiag", "pmmf_factor_batched", "pmmf_get_batch",
-           "pmmf_get_precision_stats"]
+           "pmmf_get_precision_stats", "pmmf_set_tuning", "pmmf_clear_tuning"]
 
 _lib = None
 
@@ -127,12 +127,36 @@ def load(path: str = LIB_PATH):
     L.pmmf_get_precision_stats.restype = i32
     L.pmmf_get_precision_stats.argtypes = [vp, vp, vp, vp, vp]
     L.pmmf_get_batch.argtypes = [vp, vp, vp, vp, vp, vp]
+    L.pmmf_set_tuning.restype = i32
+    L.pmmf_set_tuning.argtypes = [i32, i64, i32]
+    L.pmmf_clear_tuning.restype = None
+    L.pmmf_clear_tuning.argtypes = []
     L.pmmf_profile_begin.restype = i32
     L.pmmf_profile_begin.argtypes = [C.c_uint]
     L.pmmf_profile_end.restype = i32
     L.pmmf_profile_end.argtypes = [vp, vp, vp, vp]
     _lib = L
+    apply_tuning(os.environ.get("PMMF_TUNING", TUNING_PATH))
     return L
+
+
+TUNING_PATH = os.path.join(_HERE, "tuning.json")
+TUNE_PARAMS = {"rows_warps": 0, "gram_warps": 1}
+
+
+def apply_tuning(path: str) -> bool:
+    """Load launch shapes chosen by autotune.py ({"buckets": {param: [[max_size,
+    value], ...]}}) into the library; False when the file is absent."""
+    import json
+    if not path or not os.path.exists(path):
+        return False
+    with open(path) as fh:
+        cfg = json.load(fh)
+    _lib.pmmf_clear_tuning()
+    for name, table in cfg.get("buckets", {}).items():
+        for max_size, value in table:
+            _check(_lib.pmmf_set_tuning(TUNE_PARAMS[name], int(max_size), int(value)))
+    return True
 
 
 FAMILIES = ["partition", "gram", "select", "rows", "apply", "other"]

@@ -62,3 +62,20 @@ def test_invalid_parameters_rejected_without_gpu(lib):
     h = C.c_void_p()
     assert lib.pmmf_factor(C.byref(m), C.byref(prm), C.byref(h), None) == pmmf.ERR_INVALID_ARG
     lib.pmmf_free(None)   # NULL-safe
+
+
+def test_tuning_table_validation_and_json(tmp_path):
+    """Launch-shape tuning: argument checks and the JSON the autotuner writes."""
+    import json
+    from paper_1507_04396_gb300 import pmmf
+    lib = pmmf.load()
+    assert lib.pmmf_set_tuning(0, 256, 4) == pmmf.OK
+    assert lib.pmmf_set_tuning(7, 256, 4) == pmmf.ERR_INVALID_ARG     # unknown parameter
+    assert lib.pmmf_set_tuning(0, 0, 4) == pmmf.ERR_INVALID_ARG       # empty bucket
+    assert lib.pmmf_set_tuning(1, 512, 0) == pmmf.ERR_INVALID_ARG     # value out of range
+    path = tmp_path / "tuning.json"
+    path.write_text(json.dumps({"buckets": {"rows_warps": [[256, 4], [1024, 2]],
+                                            "gram_warps": [[512, 8]]}}))
+    assert pmmf.apply_tuning(str(path))
+    assert not pmmf.apply_tuning(str(tmp_path / "missing.json"))
+    lib.pmmf_clear_tuning()
