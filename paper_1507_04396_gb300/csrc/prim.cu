@@ -141,11 +141,41 @@ __global__ void k_scan_final(const T *in, int64_t *out, int64_t n, const int64_t
     if (blockIdx.x == gridDim.x - 1 && threadIdx.x == 0) out[n] = partial[gridDim.x];
 }
 
+// Short inputs: one CTA walks the tiles in order with a running carry (one
+// launch instead of three).
+template <class T>
+__global__ void k_scan_one(const T *in, int64_t *out, int64_t n) {
+    __shared__ int64_t tot;
+    int64_t carry = 0;
+    for (int64_t t0 = 0; t0 < n; t0 += SCAN_TILE) {
+        const int64_t base = t0 + (int64_t)threadIdx.x * SCAN_ITEMS;
+        int64_t v[SCAN_ITEMS];
+        int64_t sum = 0;
+        for (int q = 0; q < SCAN_ITEMS; ++q) {
+            v[q] = base + q < n ? (int64_t)in[base + q] : 0;
+            sum += v[q];
+        }
+        int64_t ex = block_exclusive_scan<int64_t>(sum, &tot) + carry;
+        __syncthreads();  // reads of this tile precede its writes (aliasing)
+        for (int q = 0; q < SCAN_ITEMS; ++q) {
+            if (base + q < n) out[base + q] = ex;
+            ex += v[q];
+        }
+        carry += tot;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) out[n] = carry;
+}
+
 template <class T>
 pmmf_status scan_impl(const T *in, int64_t *out, int64_t n, cudaStream_t st) {
     if (n <= 0) {
         PMMF_CUDA_TRY(cudaMemsetAsync(out, 0, sizeof(int64_t), st));
         return PMMF_OK;
+    }
+    if (n <= 4 * SCAN_TILE) {
+        k_scan_one<T><<<1, SCAN_THREADS, 0, st>>>(in, out, n);
+        return launched("scan_one");
     }
     int64_t nb = (n + SCAN_TILE - 1) / SCAN_TILE;
     DBuf<int64_t> part;
