@@ -709,6 +709,90 @@ def run_gpu_poisson(args):
     return 0
 
 
+def run_gpu_scaling(args):
+    """Factor time against input size (the linear-scaling claim): kNN Laplacians
+    of 2^14 .. 2^20 points, clusters of 256, core 256, median of 3 runs each."""
+    import numpy as np
+    import torch
+    from paper_1507_04396_gb300 import build, inputs as I, pmmf
+    build.build()
+    pmmf.load()
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    rows = []
+    for lg in range(14, 21):
+        n = 1 << lg
+        a = I.knn_laplacian(n, WORK["knn"], seed=WORK["gen_seed"])
+        A = I.SymCSR(a.n, torch.from_numpy(a.rowptr).to(dev), torch.from_numpy(a.col).to(dev),
+                     torch.from_numpy(a.val).to(dev))
+        co = torch.from_numpy(a.coords).to(dev)
+        kw = dict(k=2, eta=0.5, cluster_size=256, core_size=256, seed=0)
+        fac = lambda: pmmf.factor(A, coords=co, stream=stream, **kw)
+        fac().close()
+        ts = []
+        for _ in range(3):
+            ms, f = _timed(stream, fac, 1, flush)
+            ts.append(ms)
+            err = f.info().error
+            f.close()
+        ms = sorted(ts)[1]
+        rows.append({"n": n, "nnz": a.nnz, "ms": round(ms, 3), "nnz_per_s": a.nnz / (ms / 1e3),
+                     "error": err})
+        print(json.dumps(rows[-1]), file=sys.stderr, flush=True)
+    # least-squares slope of log(time) against log(nnz) over the four largest sizes
+    x = np.log([r["nnz"] for r in rows[-4:]])
+    y = np.log([r["ms"] for r in rows[-4:]])
+    slope = float(np.polyfit(x, y, 1)[0])
+    big = rows[-1]
+    line = {"metric": METRIC, "value": big["nnz_per_s"], "unit": UNIT, "n_gpus": 1, "steps": 3,
+            "warmup": 1, "ms_per_step": big["ms"], "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "knn_laplacian n = 2^14 .. 2^20 (10-NN, 2-D uniform points, seed 1), "
+                                   "clusters ~256, k=2, eta=0.5, core 256; median of 3 per size",
+                       "log_log_slope_time_vs_nnz": slope},
+            "sizes": rows}
+    print(json.dumps(line))
+    return 0
+
+
+def run_gpu_quality(args):
+    """Compression quality against core size: ||A - A~||_F / ||A - A_r||_F with
+    A_r the best rank-r approximation (r = core size), on a kNN Laplacian and a
+    dense RBF kernel matrix (eigenvalues by numpy on the host)."""
+    import numpy as np
+    import torch
+    from paper_1507_04396_gb300 import build, inputs as I, pmmf
+    build.build()
+    pmmf.load()
+    dev = torch.device("cuda", 0)
+    cases = [("knn_laplacian n=4096 (10-NN), clusters 256, k=2",
+              I.knn_laplacian(4096, 10, seed=1), dict(k=2, cluster_size=256)),
+             ("rbf_mixture n=2048 (dense), clusters 256, k=3",
+              I.rbf_mixture(2048, 20, seed=2), dict(k=3, cluster_size=256))]
+    out = []
+    for name, a, kw in cases:
+        dense = a.to_dense()
+        ev = np.linalg.eigvalsh(dense)
+        order = np.sort(np.abs(ev))[::-1]
+        nrm = float(np.sqrt(np.sum(ev ** 2)))
+        for core in (64, 128, 256, 512):
+            f = pmmf.factor(torch.from_numpy(dense).to(dev) if kw["k"] == 3 else a, coords=a.coords,
+                            eta=0.5, core_size=core, seed=0, **kw)
+            e = f.info().error
+            f.close()
+            best = float(np.sqrt(np.sum(order[core:] ** 2))) / nrm
+            out.append({"matrix": name, "core": core, "pmmf_rel_error": e,
+                        "best_rank_r_rel_error": best, "ratio": e / best if best > 0 else None})
+            print(json.dumps(out[-1]), file=sys.stderr, flush=True)
+    line = {"metric": "||A - A~||_F / ||A - A_r||_F against core size", "value": out[-1]["ratio"],
+            "unit": "ratio", "n_gpus": 1, "steps": 1, "warmup": 0, "higher_is_better": False,
+            "dtype": "f64", "data": "synthetic", "config": {"workload": "compression quality"},
+            "results": out}
+    print(json.dumps(line))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -717,7 +801,8 @@ def main():
     ap.add_argument("--impl", choices=["gpu", "reference"], default="gpu")
     ap.add_argument("--n", type=int, default=WORK["n"])
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
-    ap.add_argument("--workload", choices=["knn", "er_batch", "rbf_dense", "poisson"],
+    ap.add_argument("--workload", choices=["knn", "er_batch", "rbf_dense", "poisson", "scaling",
+                                           "quality"],
                     default="knn",
                     help="knn: the kNN Laplacian (default); er_batch: 4,096 independent ER "
                          "Laplacians factored as one batch; rbf_dense: dense RBF kernel, k = 3; "
@@ -727,6 +812,10 @@ def main():
     args = ap.parse_args()
     if args.workload == "rbf_dense":
         return run_gpu_rbf(args)
+    if args.workload == "scaling":
+        return run_gpu_scaling(args)
+    if args.workload == "quality":
+        return run_gpu_quality(args)
     if args.workload == "poisson":
         return run_gpu_poisson(args)
     if args.workload == "er_batch":
