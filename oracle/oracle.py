@@ -23,6 +23,7 @@ _SRC = os.path.join(_HERE, "pmmf_oracle.c")
 OK, ERR_INVALID_ARG, ERR_NOT_SYMMETRIC, ERR_NONFINITE, ERR_OOM = 0, 1, 2, 3, 4
 ERR_NOT_SPD, ERR_NOT_CONVERGED = 6, 8
 OP_A, OP_A_INV, OP_U, OP_UT, OP_H, OP_H_INV = 0, 1, 2, 3, 4, 5
+OP_A_INV_SQRT, OP_H_INV_SQRT = 6, 7
 
 
 def build(force: bool = False) -> str:

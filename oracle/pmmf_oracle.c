@@ -378,6 +378,8 @@ struct or_fact {
     double *core;
     double *chol;         /* lower Cholesky factor of the core, lazily */
     int chol_status;
+    double *isqrt;        /* core^{-1/2}, lazily (xi = 1/2 preconditioner) */
+    int isqrt_status;
     double err, norm_a;
 };
 
@@ -391,6 +393,7 @@ void or_free(or_fact *f) {
     if (!f) return;
     for (int p = 0; p < f->nst; ++p) stage_free(&f->st[p]);
     free(f->st); free(f->hdiag); free(f->core_idx); free(f->core); free(f->chol);
+    free(f->isqrt);
     free(f);
 }
 
@@ -978,6 +981,85 @@ static int core_cholesky(or_fact *f) {
     return OR_OK;
 }
 
+/* Symmetric eigendecomposition S = V diag(w) V^T of an m x m matrix by
+ * classical cyclic Jacobi (rows of V are eigenvectors): sweeps over all pairs
+ * (p, q), each rotation zeroing S_pq with the smaller-angle rotation of R7,
+ * until the off-diagonal sum of squares is at most 1e-30 times the total. */
+static int sym_eig(int64_t m, double *S, double *w, double *V) {
+    for (int64_t a = 0; a < m * m; ++a) V[a] = 0.0;
+    for (int64_t a = 0; a < m; ++a) V[a * m + a] = 1.0;
+    for (int sweep = 0; sweep < 64; ++sweep) {
+        double off = 0.0, tot = 0.0;
+        for (int64_t p = 0; p < m; ++p)
+            for (int64_t q = 0; q < m; ++q) {
+                tot = tot + S[p * m + q] * S[p * m + q];
+                if (p != q) off = off + S[p * m + q] * S[p * m + q];
+            }
+        if (off <= 1e-30 * tot) {
+            for (int64_t a = 0; a < m; ++a) w[a] = S[a * m + a];
+            return OR_OK;
+        }
+        for (int64_t p = 0; p < m - 1; ++p)
+            for (int64_t q = p + 1; q < m; ++q) {
+                if (S[p * m + q] == 0.0) continue;
+                double c, sn;
+                or_jacobi2(S[p * m + p], S[p * m + q], S[q * m + q], &c, &sn);
+                /* rows p, q then columns p, q of S; rows p, q of V */
+                for (int64_t y = 0; y < m; ++y) {
+                    double sp = S[p * m + y], sq = S[q * m + y];
+                    S[p * m + y] = c * sp - sn * sq;
+                    S[q * m + y] = sn * sp + c * sq;
+                }
+                for (int64_t y = 0; y < m; ++y) {
+                    double sp = S[y * m + p], sq = S[y * m + q];
+                    S[y * m + p] = c * sp - sn * sq;
+                    S[y * m + q] = sn * sp + c * sq;
+                }
+                for (int64_t y = 0; y < m; ++y) {
+                    double vp = V[p * m + y], vq = V[q * m + y];
+                    V[p * m + y] = c * vp - sn * vq;
+                    V[q * m + y] = sn * vp + c * vq;
+                }
+            }
+    }
+    return OR_ERR_NOT_CONVERGED;
+}
+
+/* core^{-1/2} = V^T diag(w^{-1/2}) V of the core's lower triangle mirrored
+ * (the symmetric matrix the inverse also uses, R12); NOT_SPD if an
+ * eigenvalue is not positive. */
+static int core_isqrt(or_fact *f) {
+    if (f->isqrt) return f->isqrt_status;
+    const int64_t m = f->ncore;
+    const size_t mm = (size_t)(m > 0 ? m * m : 1);
+    f->isqrt = (double *)calloc(mm, sizeof(double));
+    double *S = (double *)malloc(sizeof(double) * mm);
+    double *V = (double *)malloc(sizeof(double) * mm);
+    double *w = (double *)malloc(sizeof(double) * (size_t)(m > 0 ? m : 1));
+    if (!f->isqrt || !S || !V || !w) {
+        free(S); free(V); free(w);
+        return OR_ERR_OOM;
+    }
+    for (int64_t i = 0; i < m; ++i)
+        for (int64_t j = 0; j < m; ++j) S[i * m + j] = i >= j ? f->core[i * m + j] : f->core[j * m + i];
+    f->isqrt_status = sym_eig(m, S, w, V);
+    if (f->isqrt_status == OR_OK) {
+        for (int64_t a = 0; a < m; ++a)
+            if (!(w[a] > 0.0)) f->isqrt_status = OR_ERR_NOT_SPD;
+    }
+    if (f->isqrt_status == OR_OK)
+        for (int64_t i = 0; i < m; ++i)
+            for (int64_t j = 0; j < m; ++j) {
+                double acc = 0.0;
+                for (int64_t a = 0; a < m; ++a) acc = acc + V[a * m + i] * V[a * m + j] / sqrt(w[a]);
+                f->isqrt[i * m + j] = acc;
+            }
+    free(S); free(V); free(w);
+    return f->isqrt_status;
+}
+
+/* mode 0: H; 1: H^{-1}; 2: H^{-1/2} (wavelets 1/sqrt(H_xx), the core's
+ * inverse square root). */
 static int apply_h(or_fact *f, double *z, int64_t nrhs, int inverse) {
     int64_t n = f->n, m = f->ncore;
     int8_t *isc = (int8_t *)calloc((size_t)n, 1);
@@ -988,7 +1070,7 @@ static int apply_h(or_fact *f, double *z, int64_t nrhs, int inverse) {
     if (inverse) {
         for (int64_t x = 0; x < n; ++x)
             if (!isc[x] && !(f->hdiag[x] > 0.0)) { free(isc); free(zc); free(wc); return OR_ERR_NOT_SPD; }
-        int cs = core_cholesky(f);
+        int cs = inverse == 2 ? core_isqrt(f) : core_cholesky(f);
         if (cs) { free(isc); free(zc); free(wc); return cs; }
     }
     for (int64_t a = 0; a < m; ++a)
@@ -996,13 +1078,15 @@ static int apply_h(or_fact *f, double *z, int64_t nrhs, int inverse) {
     for (int64_t x = 0; x < n; ++x) {
         if (isc[x]) continue;
         for (int64_t r = 0; r < nrhs; ++r)
-            z[x * nrhs + r] = inverse ? z[x * nrhs + r] / f->hdiag[x] : f->hdiag[x] * z[x * nrhs + r];
+            z[x * nrhs + r] = inverse == 2 ? z[x * nrhs + r] / sqrt(f->hdiag[x])
+                            : inverse ? z[x * nrhs + r] / f->hdiag[x] : f->hdiag[x] * z[x * nrhs + r];
     }
     for (int64_t r = 0; r < nrhs; ++r) {
-        if (!inverse) {
+        if (inverse != 1) {
+            const double *C = inverse == 2 ? f->isqrt : f->core;
             for (int64_t a = 0; a < m; ++a) {
                 double acc = 0.0;
-                for (int64_t b = 0; b < m; ++b) acc = acc + f->core[a * m + b] * zc[b * nrhs + r];
+                for (int64_t b = 0; b < m; ++b) acc = acc + C[a * m + b] * zc[b * nrhs + r];
                 wc[a * nrhs + r] = acc;
             }
         } else {
@@ -1035,10 +1119,12 @@ int or_apply(const or_fact *fc, int op, const double *x, double *y, int64_t nrhs
     case OR_OP_UT: apply_u(f, y, nrhs, 1); break;
     case OR_OP_H: st = apply_h(f, y, nrhs, 0); break;
     case OR_OP_H_INV: st = apply_h(f, y, nrhs, 1); break;
+    case OR_OP_H_INV_SQRT: st = apply_h(f, y, nrhs, 2); break;
     case OR_OP_A:
     case OR_OP_A_INV:
+    case OR_OP_A_INV_SQRT:
         apply_u(f, y, nrhs, 0);
-        st = apply_h(f, y, nrhs, op == OR_OP_A_INV);
+        st = apply_h(f, y, nrhs, op == OR_OP_A ? 0 : op == OR_OP_A_INV ? 1 : 2);
         if (st == OR_OK) apply_u(f, y, nrhs, 1);
         break;
     default: return OR_ERR_INVALID_ARG;
@@ -1346,5 +1432,8 @@ int or_set_h(or_fact *f, const double *hdiag, const double *core) {
     free(f->chol);
     f->chol = NULL;
     f->chol_status = OR_OK;
+    free(f->isqrt);
+    f->isqrt = NULL;
+    f->isqrt_status = OR_OK;
     return OR_OK;
 }

@@ -33,7 +33,8 @@ enum {
     OR_ERR_NOT_CONVERGED = 8
 };
 
-enum { OR_OP_A = 0, OR_OP_A_INV = 1, OR_OP_U = 2, OR_OP_UT = 3, OR_OP_H = 4, OR_OP_H_INV = 5 };
+enum { OR_OP_A = 0, OR_OP_A_INV = 1, OR_OP_U = 2, OR_OP_UT = 3, OR_OP_H = 4, OR_OP_H_INV = 5,
+       OR_OP_A_INV_SQRT = 6, OR_OP_H_INV_SQRT = 7 };
 
 typedef struct {
     int k;              /* rotation order, 2..8 (Sec. 2, k-point rotations) */

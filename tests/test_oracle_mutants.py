@@ -59,6 +59,12 @@ MUTANTS = [
     ("angle chain rule with a flipped sine term",
      "dtheta[q] = -s * (dq[0] + dq[3]) + c * (dq[2] - dq[1]);",
      "dtheta[q] = -s * (dq[0] + dq[3]) + c * (dq[1] - dq[2]);"),
+    ("inverse square root divides the wavelets by H_xx",
+     "z[x * nrhs + r] = inverse == 2 ? z[x * nrhs + r] / sqrt(f->hdiag[x])",
+     "z[x * nrhs + r] = inverse == 2 ? z[x * nrhs + r] / f->hdiag[x]"),
+    ("core inverse square root without the square root",
+     "acc = acc + V[a * m + i] * V[a * m + j] / sqrt(w[a]);",
+     "acc = acc + V[a * m + i] * V[a * m + j] / w[a];"),
     ("inverse gradient of H without the minus sign",
      "                dhdiag[i] = -acc;",
      "                dhdiag[i] = acc;"),

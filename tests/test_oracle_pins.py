@@ -347,3 +347,37 @@ def test_rejects_bad_inputs():
     assert O.factor(a.n, a.rowptr, a.col, val, k=2, core_size=4).status == O.ERR_NONFINITE
     assert O.factor(a.n, a.rowptr, a.col, a.val, k=1, core_size=4).status == O.ERR_INVALID_ARG
     assert O.factor(a.n, a.rowptr, a.col, a.val, k=2, eta=1.0, core_size=4).status == O.ERR_INVALID_ARG
+
+
+# ---------------------------------------------------------------- xi = 1/2 preconditioner
+
+def test_inverse_square_root_operator():
+    """Sec. 4 (xi = 1/2): A~^{-1/2} = U^T H^{-1/2} U squares to A~^{-1}, is
+    symmetric, and H^{-1/2} equals the dense inverse square root of H."""
+    a = I.poisson3d(6, seed=2)
+    f = O.factor_csr(a, k=2, eta=0.5, cluster_size=27, core_size=20, seed=1)
+    rng = np.random.default_rng(3)
+    x = rng.standard_normal((a.n, 2))
+    y = f.apply(O.OP_A_INV_SQRT, f.apply(O.OP_A_INV_SQRT, x))
+    want = f.apply(O.OP_A_INV, x)
+    np.testing.assert_allclose(y, want, rtol=0, atol=1e-10 * np.abs(want).max())
+    z = rng.standard_normal((a.n, 2))
+    lhs = np.sum(z * f.apply(O.OP_A_INV_SQRT, x))
+    rhs = np.sum(f.apply(O.OP_A_INV_SQRT, z) * x)
+    assert abs(lhs - rhs) <= 1e-12 * abs(lhs)
+    # H^{-1/2} against numpy on the dense H (wavelet diagonal plus symmetric core)
+    h = np.diag(f.hdiag.copy())
+    ci = np.asarray(f.core_idx)
+    c = np.tril(f.core) + np.tril(f.core, -1).T
+    h[np.ix_(ci, ci)] = c
+    ev, vec = np.linalg.eigh(h)
+    hs = vec @ np.diag(ev ** -0.5) @ vec.T
+    np.testing.assert_allclose(f.apply(O.OP_H_INV_SQRT, x), hs @ x, rtol=0, atol=1e-10 * np.abs(hs @ x).max())
+
+
+def test_inverse_square_root_of_diagonal_is_exact():
+    a = I.from_dense(np.diag(np.arange(1.0, 33.0)))
+    f = O.factor_csr(a, k=2, eta=0.5, cluster_size=32, core_size=4, seed=3)
+    x = np.ones((32, 1))
+    got = f.apply(O.OP_A_INV_SQRT, x)[:, 0]
+    np.testing.assert_allclose(got, 1.0 / np.sqrt(np.arange(1.0, 33.0)), rtol=1e-15)
