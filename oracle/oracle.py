@@ -72,6 +72,8 @@ def lib():
         L.or_apply.argtypes = [vp, i32, vp, vp, i64]
         L.or_pcg.restype = i32
         L.or_pcg.argtypes = [vp, i64, vp, vp, vp, vp, vp, i64, f64, i32, vp, vp]
+        L.or_pcg_sym.restype = i32
+        L.or_pcg_sym.argtypes = [vp, i64, vp, vp, vp, vp, vp, i64, f64, i32, vp, vp]
         L.or_splitmix64_next.restype = u64
         L.or_splitmix64_next.argtypes = [vp]
         L.or_draw.restype = u64
@@ -158,6 +160,17 @@ class Factorization:
         relres = np.zeros(nrhs)
         st = lib().or_pcg(self._h, a.n, _p(a.rowptr), _p(a.col), _p(a.val), _p(b), _p(x), nrhs,
                           rtol, maxit, _p(iters), _p(relres))
+        return st, x, iters, relres
+
+    def pcg_sym(self, a, b: np.ndarray, rtol: float, maxit: int):
+        """xi = 1/2: CG on the split system W A W y = W b, x = W y."""
+        b = np.ascontiguousarray(b, dtype=np.float64)
+        nrhs = 1 if b.ndim == 1 else b.shape[1]
+        x = np.zeros_like(b)
+        iters = np.zeros(nrhs, dtype=np.int32)
+        relres = np.zeros(nrhs)
+        st = lib().or_pcg_sym(self._h, a.n, _p(a.rowptr), _p(a.col), _p(a.val), _p(b), _p(x), nrhs,
+                              rtol, maxit, _p(iters), _p(relres))
         return st, x, iters, relres
 
     def total_rotations(self) -> int:

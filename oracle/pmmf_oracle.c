@@ -1222,6 +1222,86 @@ out:
     return st;
 }
 
+/* Symmetrically preconditioned conjugate gradients (Sec. 4, xi = 1/2): plain
+ * CG on the split system W A W y = W b with W = (U^T H U)^{-1/2}
+ * = U^T H^{-1/2} U, each right-hand side independently, y_0 = 0, stopping when
+ * the split system's recurrence residual satisfies ||r|| / ||W b|| <= rtol;
+ * the solution is x = W y.  relres reports the true residual
+ * ||b - A x|| / ||b|| at exit. */
+int or_pcg_sym(const or_fact *fc, int64_t n, const int64_t *rowptr, const int32_t *col,
+               const double *val, const double *b, double *x, int64_t nrhs, double rtol,
+               int maxit, int32_t *iters, double *relres) {
+    or_fact *f = (or_fact *)fc;
+    if (!f || f->status || n != f->n) return OR_ERR_INVALID_ARG;
+    size_t sz = sizeof(double) * (size_t)(n * nrhs);
+    double *y = (double *)malloc(sz), *r = (double *)malloc(sz), *pv = (double *)malloc(sz),
+           *w = (double *)malloc(sz), *qv = (double *)malloc(sz);
+    double *rr = (double *)malloc(sizeof(double) * (size_t)nrhs);
+    double *bn = (double *)malloc(sizeof(double) * (size_t)nrhs);
+    int8_t *done = (int8_t *)calloc((size_t)nrhs, 1);
+    if (!y || !r || !pv || !w || !qv || !rr || !bn || !done) {
+        free(y); free(r); free(pv); free(w); free(qv); free(rr); free(bn); free(done);
+        return OR_ERR_OOM;
+    }
+    memset(y, 0, sz);
+    int st = or_apply(f, OR_OP_A_INV_SQRT, b, r, nrhs);     /* r = W b */
+    if (st) goto out;
+    memcpy(pv, r, sz);
+    for (int64_t c = 0; c < nrhs; ++c) {
+        double a = 0.0;
+        for (int64_t i = 0; i < n; ++i) a = a + r[i * nrhs + c] * r[i * nrhs + c];
+        rr[c] = a;
+        bn[c] = sqrt(a);
+        iters[c] = 0;
+        if (bn[c] == 0.0) done[c] = 1;
+    }
+    for (int it = 1; it <= maxit; ++it) {
+        int all = 1;
+        for (int64_t c = 0; c < nrhs; ++c) all &= done[c];
+        if (all) break;
+        st = or_apply(f, OR_OP_A_INV_SQRT, pv, w, nrhs);    /* q = W A W p */
+        if (st) goto out;
+        spmv(n, rowptr, col, val, w, qv, nrhs);
+        st = or_apply(f, OR_OP_A_INV_SQRT, qv, qv, nrhs);
+        if (st) goto out;
+        for (int64_t c = 0; c < nrhs; ++c) {
+            if (done[c]) continue;
+            double pq = 0.0;
+            for (int64_t i = 0; i < n; ++i) pq = pq + pv[i * nrhs + c] * qv[i * nrhs + c];
+            double alpha = rr[c] / pq;
+            double a = 0.0;
+            for (int64_t i = 0; i < n; ++i) {
+                y[i * nrhs + c] = y[i * nrhs + c] + alpha * pv[i * nrhs + c];
+                r[i * nrhs + c] = r[i * nrhs + c] - alpha * qv[i * nrhs + c];
+                a = a + r[i * nrhs + c] * r[i * nrhs + c];
+            }
+            iters[c] = it;
+            if (sqrt(a) / bn[c] <= rtol) done[c] = 1;
+            else {
+                double beta = a / rr[c];
+                rr[c] = a;
+                for (int64_t i = 0; i < n; ++i) pv[i * nrhs + c] = r[i * nrhs + c] + beta * pv[i * nrhs + c];
+            }
+        }
+    }
+    st = or_apply(f, OR_OP_A_INV_SQRT, y, x, nrhs);         /* x = W y */
+    if (st) goto out;
+    spmv(n, rowptr, col, val, x, qv, nrhs);
+    for (int64_t c = 0; c < nrhs; ++c) {
+        double a = 0.0, bb = 0.0;
+        for (int64_t i = 0; i < n; ++i) {
+            double d = b[i * nrhs + c] - qv[i * nrhs + c];
+            a = a + d * d;
+            bb = bb + b[i * nrhs + c] * b[i * nrhs + c];
+        }
+        relres[c] = bb > 0.0 ? sqrt(a / bb) : 0.0;
+        if (!done[c]) st = OR_ERR_NOT_CONVERGED;
+    }
+out:
+    free(y); free(r); free(pv); free(w); free(qv); free(rr); free(bn); free(done);
+    return st;
+}
+
 /* ------------------------------------------------------------------------ */
 /* Gradient of the factorized operator (Sec. 2.4's matrix-free product with
  * the greedy selections held fixed; not in the paper).  For

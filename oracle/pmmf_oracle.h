@@ -83,6 +83,10 @@ int or_apply(const or_fact *f, int op, const double *x, double *y, int64_t nrhs)
 int or_pcg(const or_fact *f, int64_t n, const int64_t *rowptr, const int32_t *col,
            const double *val, const double *b, double *x, int64_t nrhs, double rtol,
            int maxit, int32_t *iters, double *relres);
+/* xi = 1/2: CG on W A W y = W b, W = (U^T H U)^{-1/2}, x = W y. */
+int or_pcg_sym(const or_fact *f, int64_t n, const int64_t *rowptr, const int32_t *col,
+               const double *val, const double *b, double *x, int64_t nrhs, double rtol,
+               int maxit, int32_t *iters, double *relres);
 
 /* Gradient of L = sum <g, op(x)> for op = OR_OP_A or OR_OP_A_INV with the
  * selections fixed: dx (n x nrhs), dO (K*K slots per rotation in stage, step

@@ -65,6 +65,12 @@ MUTANTS = [
     ("core inverse square root without the square root",
      "acc = acc + V[a * m + i] * V[a * m + j] / sqrt(w[a]);",
      "acc = acc + V[a * m + i] * V[a * m + j] / w[a];"),
+    ("split CG returns y instead of W y",
+     "    st = or_apply(f, OR_OP_A_INV_SQRT, y, x, nrhs);         /* x = W y */",
+     "    memcpy(x, y, sz);"),
+    ("split CG applies W on one side only",
+     "        st = or_apply(f, OR_OP_A_INV_SQRT, qv, qv, nrhs);\n",
+     ""),
     ("inverse gradient of H without the minus sign",
      "                dhdiag[i] = -acc;",
      "                dhdiag[i] = acc;"),

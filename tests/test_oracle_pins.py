@@ -381,3 +381,23 @@ def test_inverse_square_root_of_diagonal_is_exact():
     x = np.ones((32, 1))
     got = f.apply(O.OP_A_INV_SQRT, x)[:, 0]
     np.testing.assert_allclose(got, 1.0 / np.sqrt(np.arange(1.0, 33.0)), rtol=1e-15)
+
+
+def test_split_cg_matches_pcg_iterates_and_exact_split_takes_one_step():
+    """Sec. 4 (xi = 1/2): CG on W A W y = W b with x = W y, W^2 = M^{-1}, runs
+    the same iterates as PCG with M^{-1} in exact arithmetic; with no stages
+    (H = A) the split system is the identity and CG stops after one step."""
+    a = I.poisson3d(6, seed=2)
+    b = np.random.default_rng(5).standard_normal((a.n, 3))
+    f = O.factor_csr(a, k=2, eta=0.5, cluster_size=27, core_size=20, seed=1)
+    for it in (1, 3, 6):
+        st1, x1, i1, _ = f.pcg(a, b, 1e-300, it)
+        st2, x2, i2, _ = f.pcg_sym(a, b, 1e-300, it)
+        assert st1 == st2 == O.ERR_NOT_CONVERGED and (i1 == it).all() and (i2 == it).all()
+        np.testing.assert_allclose(x2, x1, rtol=0, atol=1e-9 * np.abs(x1).max())
+    st, x, iters, rel = f.pcg_sym(a, b, 1e-10, 500)
+    assert st == 0 and (rel <= 1e-8).all()
+    np.testing.assert_allclose(a.to_dense() @ x, b, atol=1e-8 * np.abs(b).max())
+    f0 = O.factor_csr(a, k=2, eta=0.5, cluster_size=27, core_size=a.n, seed=1)
+    st, x, iters, rel = f0.pcg_sym(a, b, 1e-10, 10)
+    assert st == 0 and (iters == 1).all() and (rel <= 1e-10).all()
