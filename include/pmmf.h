@@ -56,9 +56,15 @@ enum { PMMF_CSR = 0, PMMF_DENSE = 1 };
  *   PMMF_OP_U      y = U x,   U = Qbar_P ... Qbar_1
  *   PMMF_OP_UT     y = U^T x
  *   PMMF_OP_H      y = H x
- *   PMMF_OP_H_INV  y = H^{-1} x */
+ *   PMMF_OP_H_INV  y = H^{-1} x
+ *   PMMF_OP_A_INV_SQRT  y = U^T H^{-1/2} U x   (A~^{-1/2}, the symmetric
+ *                                          preconditioner of Sec. 4 with
+ *                                          xi = 1/2; wavelet entries
+ *                                          1/sqrt(H_ii), core^{-1/2})
+ *   PMMF_OP_H_INV_SQRT  y = H^{-1/2} x
+ * The core enters the inverse ops through its lower triangle (mirrored). */
 enum { PMMF_OP_A = 0, PMMF_OP_A_INV = 1, PMMF_OP_U = 2, PMMF_OP_UT = 3, PMMF_OP_H = 4,
-       PMMF_OP_H_INV = 5 };
+       PMMF_OP_H_INV = 5, PMMF_OP_A_INV_SQRT = 6, PMMF_OP_H_INV_SQRT = 7 };
 
 /* A symmetric n x n matrix (Sec. 2: "a symmetric matrix A").
  *   PMMF_CSR:   rowptr[n+1] (int64), colidx[nnz] (int32, strictly ascending
@@ -157,7 +163,11 @@ pmmf_status pmmf_factor(const pmmf_matrix *A, const pmmf_params *p, pmmf_handle 
  * dimension ld >= nrhs; x == y (in place) is allowed.  Asynchronous.
  * PMMF_OP_A_INV / PMMF_OP_H_INV return PMMF_ERR_NOT_SPD when a wavelet
  * diagonal entry of H is <= 0 or the core is not positive definite; that check
- * runs on the first inverse request and synchronizes the stream once. */
+ * runs on the first inverse request and synchronizes the stream once.  The
+ * inverse square root ops form core^{-1/2} on their first request by the
+ * coupled Newton-Schulz iteration (dense products, at most 100 steps,
+ * synchronizing once per step); PMMF_ERR_NOT_SPD when it diverges or stalls
+ * (an eigenvalue <= 0, or numerically so). */
 pmmf_status pmmf_apply(const pmmf_handle *f, int op, const double *x, double *y, int64_t nrhs,
                        int64_t ld, void *stream);
 
@@ -171,7 +181,7 @@ pmmf_status pmmf_apply(const pmmf_handle *f, int op, const double *x, double *y,
  *   Scratch: the core slice of the vectors (core_size * nrhs doubles) lives
  *   in one library-owned device array of 1,048,576 doubles (8 MiB), held by
  *   every GPU that loads the library until the process exits.  Calls with
- *   core_size * nrhs > 1,048,576 for the H-using ops (A, A_INV, H, H_INV)
+ *   core_size * nrhs > 1,048,576 for the H-using ops (all but U and UT)
  *   return PMMF_ERR_UNSUPPORTED with a message naming the limit.
  *   Set-up: the first call on a device (the calling thread's current device)
  *   looks up the array's device address; make that first call before any
@@ -180,9 +190,10 @@ pmmf_status pmmf_apply(const pmmf_handle *f, int op, const double *x, double *y,
  *   contents; nothing in it needs to start at zero (each call writes every
  *   entry it reads).  Calls that overlap on the GPU (different streams, or
  *   host threads) race on the array and must be serialized by the caller.
- *   Inverse ops need the core inverse, which pmmf_apply / pmmf_solve_precond
- *   form (and allocate) on their first inverse request; before that this
- *   function returns PMMF_ERR_INVALID_ARG. */
+ *   Inverse ops need the core inverse (inverse square root ops: the core's
+ *   inverse square root), which pmmf_apply / pmmf_solve_precond /
+ *   pmmf_solve_precond_sym form (and allocate) on their first request;
+ *   before that this function returns PMMF_ERR_INVALID_ARG. */
 pmmf_status pmmf_apply_noalloc(const pmmf_handle *f, int op, const double *x, double *y,
                                int64_t nrhs, int64_t ld, void *stream);
 
@@ -196,6 +207,18 @@ pmmf_status pmmf_apply_noalloc(const pmmf_handle *f, int op, const double *x, do
 pmmf_status pmmf_solve_precond(const pmmf_handle *f, const pmmf_matrix *A, const double *b,
                                double *x, int64_t nrhs, double rtol, int maxit, int32_t *iters,
                                double *relres, void *stream);
+
+/* Symmetrically preconditioned conjugate gradients (Sec. 4, xi = 1/2): plain
+ * CG on W A W y = W b with W = A~^{-1/2} = U^T H^{-1/2} U applied matrix-free,
+ * then x = W y; every column independently, y_0 = 0.  Same arguments as
+ * pmmf_solve_precond; a column stops when the split system's recurrence
+ * residual satisfies ||r|| / ||W b|| <= rtol.  relres is the true residual
+ * ||b - A x|| / ||b|| at exit.  In exact arithmetic the iterates equal those
+ * of pmmf_solve_precond.  PMMF_ERR_NOT_SPD when H has no real inverse square
+ * root; PMMF_ERR_NOT_CONVERGED as for pmmf_solve_precond. */
+pmmf_status pmmf_solve_precond_sym(const pmmf_handle *f, const pmmf_matrix *A, const double *b,
+                                   double *x, int64_t nrhs, double rtol, int maxit,
+                                   int32_t *iters, double *relres, void *stream);
 
 /* ---- batches of independent matrices ---------------------------------------
  * Many independent symmetric matrices factored together (the paper factors

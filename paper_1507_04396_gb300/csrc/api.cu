@@ -42,6 +42,9 @@ struct pmmf_handle {
     pmmf::DBuf<int32_t> core_idx, core_pos;
     pmmf::DBuf<double> core, core_inv;
     int inv_state = 0;  // 0 not formed, 1 formed, 2 not SPD
+    pmmf::DBuf<double> core_isqrt;       // core^{-1/2} per block (xi = 1/2)
+    int isqrt_state = 0;                 // as inv_state
+    int isqrt_iters = 0;                 // Newton-Schulz steps it took
     pmmf::ApplyStages views;
     // core blocks (one for a single factorization, one per matrix of a batch)
     int64_t nblk = 1, bs = 0;
@@ -1023,6 +1026,31 @@ pmmf_status ensure_inverse(pmmf_handle *f, cudaStream_t st) {
     return PMMF_OK;
 }
 
+pmmf_status ensure_isqrt(pmmf_handle *f, cudaStream_t st) {
+    if (f->isqrt_state == 1) return PMMF_OK;
+    if (f->isqrt_state == 2) return fail(PMMF_ERR_NOT_SPD, "H is not positive definite");
+    DBuf<unsigned> status;
+    PMMF_TRY(status.zeros(1, st));
+    PMMF_TRY(f->core_isqrt.alloc(f->nblk * f->bs * f->bs, st));
+    const pmmf_status cs = core_inverse_sqrt(f->core.p, f->nblk, f->bs, f->nblk > 1 ? f->bdim.p : nullptr,
+                                             f->hdiag.p, f->core_pos.p, f->n, f->core_isqrt.p,
+                                             status.p, &f->isqrt_iters, st);
+    if (cs == PMMF_ERR_NOT_SPD) {
+        f->isqrt_state = 2;
+        return cs;
+    }
+    PMMF_TRY(cs);
+    unsigned hs = 0;
+    PMMF_CUDA_TRY(cudaMemcpyAsync(&hs, status.p, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
+    PMMF_CUDA_TRY(cudaStreamSynchronize(st));
+    if (hs & ST_NOT_SPD) {
+        f->isqrt_state = 2;
+        return fail(PMMF_ERR_NOT_SPD, "H is not positive definite");
+    }
+    f->isqrt_state = 1;
+    return PMMF_OK;
+}
+
 HData hdata(const pmmf_handle *f) {
     HData H;
     H.n = f->n;
@@ -1035,23 +1063,28 @@ HData hdata(const pmmf_handle *f) {
     H.core_idx = f->core_idx.p;
     H.core = f->core.p;
     H.core_inv = f->core_inv.p;
+    H.core_isqrt = f->core_isqrt.p;
     return H;
 }
 
 // y <- op(x) with y already holding a copy of x.
 pmmf_status apply_inplace(pmmf_handle *f, int op, double *y, int64_t nrhs, int64_t ld,
                           cudaStream_t st) {
-    const bool inv = op == PMMF_OP_A_INV || op == PMMF_OP_H_INV;
-    if (inv) PMMF_TRY(ensure_inverse(f, st));
+    const int mode = op == PMMF_OP_A_INV || op == PMMF_OP_H_INV ? 1
+                   : op == PMMF_OP_A_INV_SQRT || op == PMMF_OP_H_INV_SQRT ? 2 : 0;
+    if (mode == 1) PMMF_TRY(ensure_inverse(f, st));
+    if (mode == 2) PMMF_TRY(ensure_isqrt(f, st));
     switch (op) {
     case PMMF_OP_U: return apply_rotations(f->views, false, y, ld, nrhs, st);
     case PMMF_OP_UT: return apply_rotations(f->views, true, y, ld, nrhs, st);
     case PMMF_OP_H:
-    case PMMF_OP_H_INV: return apply_h(hdata(f), inv, y, ld, nrhs, st);
+    case PMMF_OP_H_INV:
+    case PMMF_OP_H_INV_SQRT: return apply_h(hdata(f), mode, y, ld, nrhs, st);
     case PMMF_OP_A:
     case PMMF_OP_A_INV:
+    case PMMF_OP_A_INV_SQRT:
         PMMF_TRY(apply_rotations(f->views, false, y, ld, nrhs, st));
-        PMMF_TRY(apply_h(hdata(f), inv, y, ld, nrhs, st));
+        PMMF_TRY(apply_h(hdata(f), mode, y, ld, nrhs, st));
         return apply_rotations(f->views, true, y, ld, nrhs, st);
     default: return fail(PMMF_ERR_INVALID_ARG, "unknown op");
     }
@@ -1093,15 +1126,23 @@ pmmf_status pmmf_apply(const pmmf_handle *fc, int op, const double *x, double *y
     pmmf_handle *f = const_cast<pmmf_handle *>(fc);
     if (!f || !x || !y) return fail(PMMF_ERR_INVALID_ARG, "NULL handle or vector");
     if (nrhs < 1 || ld < nrhs) return fail(PMMF_ERR_INVALID_ARG, "need nrhs >= 1 and ld >= nrhs");
-    if (op < PMMF_OP_A || op > PMMF_OP_H_INV) return fail(PMMF_ERR_INVALID_ARG, "unknown op");
+    if (op < PMMF_OP_A || op > PMMF_OP_H_INV_SQRT) return fail(PMMF_ERR_INVALID_ARG, "unknown op");
     cudaStream_t st = (cudaStream_t)stream;
     if (x != y) PMMF_TRY(copy_block(x, ld, y, ld, f->n, nrhs, st));
     return apply_inplace(f, op, y, nrhs, ld, st);
 }
 
-pmmf_status pmmf_solve_precond(const pmmf_handle *fc, const pmmf_matrix *A, const double *b,
-                               double *x, int64_t nrhs, double rtol, int maxit, int32_t *iters,
-                               double *relres, void *stream) {
+}  // extern "C"
+
+namespace pmmf {
+namespace {
+
+// Conjugate gradients with the factorization as preconditioner (Sec. 4):
+// sym = false: PCG with M^{-1} = A~^{-1} (xi = 1); sym = true: plain CG on the
+// split system W A W y = W b, W = A~^{-1/2}, x = W y (xi = 1/2).
+pmmf_status solve_impl(const pmmf_handle *fc, const pmmf_matrix *A, const double *b, double *x,
+                       int64_t nrhs, double rtol, int maxit, int32_t *iters, double *relres,
+                       void *stream, bool sym) {
     set_error("");
     pmmf_handle *f = const_cast<pmmf_handle *>(fc);
     if (!f || !A || !b || !x || !iters || !relres) return fail(PMMF_ERR_INVALID_ARG, "NULL argument");
@@ -1120,7 +1161,7 @@ pmmf_status pmmf_solve_precond(const pmmf_handle *fc, const pmmf_matrix *A, cons
     dA.rp = M.rowptr.p;
     dA.ci = M.col.p;
     dA.v = M.val.p;
-    PMMF_TRY(ensure_inverse(f, st));
+    PMMF_TRY(sym ? ensure_isqrt(f, st) : ensure_inverse(f, st));
 
     DBuf<double> r, z, pv, qv, sc, part, zc;
     DBuf<int32_t> done, itd;
@@ -1136,8 +1177,27 @@ pmmf_status pmmf_solve_precond(const pmmf_handle *fc, const pmmf_matrix *A, cons
     double *rz = sc.p, *pq = sc.p + 8, *rr = sc.p + 16, *rzn = sc.p + 24, *bb = sc.p + 32;
     double *bnorm = sc.p + 40, *alpha = sc.p + 48, *beta = sc.p + 56;
     const HData H = hdata(f);
+    // W v in place (W = U^T H^{-1/2} U)
+    auto apply_w = [&](double *v, cudaStream_t s) -> pmmf_status {
+        PMMF_TRY(apply_rotations(f->views, false, v, nr, nr, s));
+        PMMF_TRY(apply_h_scratch(H, 2, v, nr, nr, zc.p, s));
+        return apply_rotations(f->views, true, v, nr, nr, s);
+    };
+    // one CG iteration on the split system: q = W A W p, x holds y; the
+    // residual is the split one, and p <- r + beta p
+    auto body_sym = [&](cudaStream_t s) -> pmmf_status {
+        PMMF_CUDA_TRY(cudaMemcpyAsync(z.p, pv.p, sizeof(double) * (size_t)(n * nr), cudaMemcpyDeviceToDevice, s));
+        PMMF_TRY(apply_w(z.p, s));
+        PMMF_TRY(spmv(dA, z.p, qv.p, nr, s));
+        PMMF_TRY(apply_w(qv.p, s));
+        PMMF_TRY(dots(pv.p, qv.p, n, nr, pq, part.p, s));
+        PMMF_TRY(cg_update_xr(x, r.p, pv.p, qv.p, n, nr, rz, pq, done.p, alpha, s));
+        PMMF_TRY(dots(r.p, r.p, n, nr, rr, part.p, s));
+        PMMF_TRY(cg_check(rr, bnorm, rtol, nr, done.p, itd.p, itd.p + 8, s));
+        return cg_update_p(pv.p, r.p, n, nr, rr, rz, done.p, beta, s);
+    };
     // one PCG iteration (Sec. 4 with M^{-1} = U^T H^{-1} U applied matrix-free)
-    auto body = [&](cudaStream_t s) -> pmmf_status {
+    auto body_pcg = [&](cudaStream_t s) -> pmmf_status {
         PMMF_TRY(spmv(dA, pv.p, qv.p, nr, s));
         PMMF_TRY(dots(pv.p, qv.p, n, nr, pq, part.p, s));
         PMMF_TRY(cg_update_xr(x, r.p, pv.p, qv.p, n, nr, rz, pq, done.p, alpha, s));
@@ -1150,13 +1210,22 @@ pmmf_status pmmf_solve_precond(const pmmf_handle *fc, const pmmf_matrix *A, cons
         PMMF_TRY(dots(r.p, z.p, n, nr, rzn, part.p, s));
         return cg_update_p(pv.p, z.p, n, nr, rzn, rz, done.p, beta, s);
     };
+    auto body = [&](cudaStream_t s) -> pmmf_status { return sym ? body_sym(s) : body_pcg(s); };
     PMMF_CUDA_TRY(cudaMemsetAsync(x, 0, sizeof(double) * (size_t)(n * nr), st));
     PMMF_CUDA_TRY(cudaMemcpyAsync(r.p, b, sizeof(double) * (size_t)(n * nr), cudaMemcpyDeviceToDevice, st));
-    PMMF_CUDA_TRY(cudaMemcpyAsync(z.p, b, sizeof(double) * (size_t)(n * nr), cudaMemcpyDeviceToDevice, st));
-    PMMF_TRY(apply_inplace(f, PMMF_OP_A_INV, z.p, nr, nr, st));
-    PMMF_CUDA_TRY(cudaMemcpyAsync(pv.p, z.p, sizeof(double) * (size_t)(n * nr), cudaMemcpyDeviceToDevice, st));
-    PMMF_TRY(dots(r.p, z.p, n, nr, rz, part.p, st));
-    PMMF_TRY(dots(b, b, n, nr, bb, part.p, st));
+    if (sym) {
+        // r = W b, p = r, rz = r.r, and the split right-hand side's norm
+        PMMF_TRY(apply_w(r.p, st));
+        PMMF_CUDA_TRY(cudaMemcpyAsync(pv.p, r.p, sizeof(double) * (size_t)(n * nr), cudaMemcpyDeviceToDevice, st));
+        PMMF_TRY(dots(r.p, r.p, n, nr, rz, part.p, st));
+        PMMF_TRY(dots(r.p, r.p, n, nr, bb, part.p, st));
+    } else {
+        PMMF_CUDA_TRY(cudaMemcpyAsync(z.p, b, sizeof(double) * (size_t)(n * nr), cudaMemcpyDeviceToDevice, st));
+        PMMF_TRY(apply_inplace(f, PMMF_OP_A_INV, z.p, nr, nr, st));
+        PMMF_CUDA_TRY(cudaMemcpyAsync(pv.p, z.p, sizeof(double) * (size_t)(n * nr), cudaMemcpyDeviceToDevice, st));
+        PMMF_TRY(dots(r.p, z.p, n, nr, rz, part.p, st));
+        PMMF_TRY(dots(b, b, n, nr, bb, part.p, st));
+    }
     double hb[8], hr[8];
     int32_t hdone[8];
     PMMF_CUDA_TRY(cudaMemcpyAsync(hb, bb, sizeof(double) * nr, cudaMemcpyDeviceToHost, st));
@@ -1223,19 +1292,42 @@ pmmf_status pmmf_solve_precond(const pmmf_handle *fc, const pmmf_matrix *A, cons
         PMMF_TRY(ls);
     }
     PMMF_CUDA_TRY(cudaMemcpyAsync(iters, itd.p, sizeof(int32_t) * nr, cudaMemcpyDeviceToHost, st));
+    if (sym) {
+        PMMF_TRY(apply_w(x, st));                       // x = W y
+        PMMF_TRY(dots(b, b, n, nr, bb, part.p, st));    // ||b|| for relres
+    }
     // true residual at exit
     PMMF_TRY(spmv(dA, x, qv.p, nr, st));
     PMMF_TRY(vec_sub(b, qv.p, r.p, n * nr, st));
     PMMF_TRY(dots(r.p, r.p, n, nr, rr, part.p, st));
+    double hbb[8];
     PMMF_CUDA_TRY(cudaMemcpyAsync(hr, rr, sizeof(double) * nr, cudaMemcpyDeviceToHost, st));
+    PMMF_CUDA_TRY(cudaMemcpyAsync(hbb, bb, sizeof(double) * nr, cudaMemcpyDeviceToHost, st));
     PMMF_CUDA_TRY(cudaStreamSynchronize(st));
     bool conv = true;
     for (int c = 0; c < nr; ++c) {
-        relres[c] = hb[c] > 0.0 ? std::sqrt(hr[c]) / hb[c] : 0.0;
+        relres[c] = hbb[c] > 0.0 ? std::sqrt(hr[c] / hbb[c]) : 0.0;
         conv = conv && hdone[c];
     }
     if (!conv) return fail(PMMF_ERR_NOT_CONVERGED, "PCG did not converge within maxit");
     return PMMF_OK;
+}
+
+}  // namespace
+}  // namespace pmmf
+
+extern "C" {
+
+pmmf_status pmmf_solve_precond(const pmmf_handle *f, const pmmf_matrix *A, const double *b,
+                               double *x, int64_t nrhs, double rtol, int maxit, int32_t *iters,
+                               double *relres, void *stream) {
+    return pmmf::solve_impl(f, A, b, x, nrhs, rtol, maxit, iters, relres, stream, false);
+}
+
+pmmf_status pmmf_solve_precond_sym(const pmmf_handle *f, const pmmf_matrix *A, const double *b,
+                                   double *x, int64_t nrhs, double rtol, int maxit,
+                                   int32_t *iters, double *relres, void *stream) {
+    return pmmf::solve_impl(f, A, b, x, nrhs, rtol, maxit, iters, relres, stream, true);
 }
 
 pmmf_status pmmf_apply_backward(const pmmf_handle *fc, int op, const double *x, const double *g,
@@ -1293,7 +1385,7 @@ pmmf_status pmmf_set_h(pmmf_handle *f, const double *hdiag, const double *core, 
     if (core && f->nblk * f->bs > 0)
         PMMF_CUDA_TRY(cudaMemcpyAsync(f->core.p, core, sizeof(double) * (size_t)(f->nblk * f->bs * f->bs),
                                       cudaMemcpyDeviceToDevice, st));
-    if (hdiag || core) f->inv_state = 0;
+    if (hdiag || core) f->inv_state = f->isqrt_state = 0;
     return PMMF_OK;
 }
 
@@ -1303,12 +1395,13 @@ namespace pmmf {
 
 // Read-only view of a handle for the allocation-free apply.
 pmmf_status handle_views(const pmmf_handle *f, const ApplyStages **views, HData *H, int64_t *n,
-                         bool *inverse_ready) {
+                         bool *inverse_ready, bool *isqrt_ready) {
     if (!f) return fail(PMMF_ERR_INVALID_ARG, "NULL handle");
     *views = &f->views;
     *H = hdata(f);
     *n = f->n;
     *inverse_ready = f->inv_state == 1;
+    *isqrt_ready = f->isqrt_state == 1;
     return PMMF_OK;
 }
 

@@ -11,6 +11,9 @@
 //            definite, so no pivoting is needed and a non-positive pivot means
 //            "not SPD").
 #include "apply.cuh"
+
+#include <cmath>
+#include <utility>
 #include "rotmath.cuh"
 
 namespace pmmf {
@@ -87,9 +90,9 @@ __global__ void k_copy_block(const double *x, int64_t ldx, double *y, int64_t ld
     }
 }
 
-// Wavelet part of H or H^-1 (core coordinates untouched here); gathers the
-// core slice into zc.
-template <bool INV>
+// Wavelet part of H (MODE 0), H^-1 (1) or H^-1/2 (2) (core coordinates
+// untouched here); gathers the core slice into zc.
+template <int MODE>
 __global__ void k_h_diag(double *x, int64_t ld, int64_t n, int64_t nrhs, const double *hdiag,
                          const int32_t *core_pos, double *zc) {
     for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n * nrhs;
@@ -98,7 +101,8 @@ __global__ void k_h_diag(double *x, int64_t ld, int64_t n, int64_t nrhs, const d
         int32_t cp = core_pos[i];
         double v = x[i * ld + r];
         if (cp >= 0) zc[(int64_t)cp * nrhs + r] = v;
-        else x[i * ld + r] = INV ? __ddiv_rn(v, hdiag[i]) : __dmul_rn(hdiag[i], v);
+        else x[i * ld + r] = MODE == 2 ? __ddiv_rn(v, __dsqrt_rn(hdiag[i]))
+                           : MODE == 1 ? __ddiv_rn(v, hdiag[i]) : __dmul_rn(hdiag[i], v);
     }
 }
 
@@ -360,18 +364,34 @@ pmmf_status copy_block(const double *x, int64_t ldx, double *y, int64_t ldy, int
     return launched("copy_block");
 }
 
-pmmf_status apply_h(const HData &H, bool inverse, double *x, int64_t ld, int64_t nrhs,
+pmmf_status apply_h_scratch(const HData &H, int mode, double *x, int64_t ld, int64_t nrhs,
+                            double *zc, cudaStream_t st) {
+    const unsigned g = grid_for(H.n * nrhs, 256);
+    if (mode == 2) k_h_diag<2><<<g, 256, 0, st>>>(x, ld, H.n, nrhs, H.hdiag, H.core_pos, zc);
+    else if (mode == 1) k_h_diag<1><<<g, 256, 0, st>>>(x, ld, H.n, nrhs, H.hdiag, H.core_pos, zc);
+    else k_h_diag<0><<<g, 256, 0, st>>>(x, ld, H.n, nrhs, H.hdiag, H.core_pos, zc);
+    PMMF_TRY(launched("h_diag"));
+    const double *C = mode == 2 ? H.core_isqrt : mode == 1 ? H.core_inv : H.core;
+    k_core_gemv<<<grid_for(H.m * nrhs, 64), 64, 0, st>>>(C, H.nblk, H.bs, H.bdim, zc, nrhs,
+                                                         H.core_idx, x, ld);
+    return launched("core_gemv");
+}
+
+pmmf_status apply_h_scratch(const HData &H, bool inverse, double *x, int64_t ld, int64_t nrhs,
+                            double *zc, cudaStream_t st) {
+    return apply_h_scratch(H, inverse ? 1 : 0, x, ld, nrhs, zc, st);
+}
+
+pmmf_status apply_h(const HData &H, int mode, double *x, int64_t ld, int64_t nrhs,
                     cudaStream_t st) {
     DBuf<double> zc;
     PMMF_TRY(zc.alloc(H.m * nrhs, st));
-    if (inverse)
-        k_h_diag<true><<<grid_for(H.n * nrhs, 256), 256, 0, st>>>(x, ld, H.n, nrhs, H.hdiag, H.core_pos, zc.p);
-    else
-        k_h_diag<false><<<grid_for(H.n * nrhs, 256), 256, 0, st>>>(x, ld, H.n, nrhs, H.hdiag, H.core_pos, zc.p);
-    PMMF_TRY(launched("h_diag"));
-    k_core_gemv<<<grid_for(H.m * nrhs, 64), 64, 0, st>>>(inverse ? H.core_inv : H.core, H.nblk,
-                                                         H.bs, H.bdim, zc.p, nrhs, H.core_idx, x, ld);
-    return launched("core_gemv");
+    return apply_h_scratch(H, mode, x, ld, nrhs, zc.p, st);
+}
+
+pmmf_status apply_h(const HData &H, bool inverse, double *x, int64_t ld, int64_t nrhs,
+                    cudaStream_t st) {
+    return apply_h(H, inverse ? 1 : 0, x, ld, nrhs, st);
 }
 
 pmmf_status invert_core_blocks(const double *core, int64_t nblk, int64_t bs, const int32_t *bdim,
@@ -407,6 +427,222 @@ pmmf_status invert_core(const double *core, int64_t m, const double *hdiag, cons
         PMMF_TRY(launched("gj_step"));
     }
     return PMMF_OK;
+}
+
+// ---- core inverse square root (Sec. 4, xi = 1/2) --------------------------
+// The coupled Newton-Schulz iteration for S^{1/2} and S^{-1/2} of a symmetric
+// positive definite S scaled into the unit ball (Higham, Functions of
+// Matrices, Sec. 6.3): Y_0 = S / alpha, Z_0 = I,
+//   T = (3 I - Z Y) / 2,  Y <- Y T,  Z <- T Z,
+// with Z -> (S / alpha)^{-1/2} quadratically once Z Y is near I.  Every step
+// is a dense product, which is what a GPU does well; the eigendecomposition
+// the definition suggests is a long chain of dependent rotations.
+constexpr int NS_TILE = 64, NS_KT = 16, NS_THREADS = 256, NS_MAXIT = 100;
+
+// Per core block: alpha = ||S||_F of the block's d x d symmetric core (lower
+// triangle mirrored); Y = S / alpha with the identity on the padding, Z = I.
+__global__ void __launch_bounds__(NS_THREADS) k_ns_init(const double *C, int64_t bs,
+                                                        const int32_t *bdim, double *Y, double *Z,
+                                                        double *alpha, unsigned *status) {
+    __shared__ double red[NS_THREADS];
+    const int64_t blk = blockIdx.x;
+    const int64_t d = bdim ? bdim[blk] : bs;
+    const double *Cb = C + blk * bs * bs;
+    double acc = 0.0;
+    for (int64_t q = threadIdx.x; q < d * d; q += NS_THREADS) {
+        const int64_t i = q / d, j = q - i * d;
+        const double v = i >= j ? Cb[i * bs + j] : Cb[j * bs + i];
+        acc = __fma_rn(v, v, acc);
+    }
+    red[threadIdx.x] = acc;
+    __syncthreads();
+    for (int w = NS_THREADS / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < w) red[threadIdx.x] = __dadd_rn(red[threadIdx.x], red[threadIdx.x + w]);
+        __syncthreads();
+    }
+    double a = d > 0 ? __dsqrt_rn(red[0]) : 1.0;
+    if (!(a > 0.0 && a < INFINITY)) {
+        if (threadIdx.x == 0) atomicOr(status, ST_NOT_SPD);
+        a = 1.0;
+    }
+    if (threadIdx.x == 0) alpha[blk] = a;
+    double *Yb = Y + blk * bs * bs, *Zb = Z + blk * bs * bs;
+    for (int64_t q = threadIdx.x; q < bs * bs; q += NS_THREADS) {
+        const int64_t i = q / bs, j = q - i * bs;
+        Yb[q] = i < d && j < d ? __ddiv_rn(i >= j ? Cb[i * bs + j] : Cb[j * bs + i], a)
+                               : (i == j ? 1.0 : 0.0);
+        Zb[q] = i == j ? 1.0 : 0.0;
+    }
+}
+
+// C_b = A_b B_b for every bs x bs block b = blockIdx.z; 64 x 64 output tile
+// per CTA, 4 x 4 outputs per thread, k staged 16 at a time in shared memory.
+// EPI: C <- (3 I - A B) / 2, and the tile's sum of (A B - I)^2 over the
+// block's d x d part goes to part[b * tiles + tile].
+template <bool EPI>
+__global__ void __launch_bounds__(NS_THREADS) k_ns_gemm(const double *A, const double *B,
+                                                        double *C, int64_t bs,
+                                                        const int32_t *bdim, double *part) {
+    __shared__ double As[NS_KT][NS_TILE + 1];
+    __shared__ double Bs[NS_KT][NS_TILE];
+    __shared__ double red[NS_THREADS];
+    const int64_t blk = blockIdx.z;
+    const double *Ab = A + blk * bs * bs, *Bb = B + blk * bs * bs;
+    double *Cb = C + blk * bs * bs;
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    const int64_t r0 = (int64_t)blockIdx.y * NS_TILE, c0 = (int64_t)blockIdx.x * NS_TILE;
+    double acc[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = 0.0;
+    for (int64_t k0 = 0; k0 < bs; k0 += NS_KT) {
+        for (int e = threadIdx.x; e < NS_TILE * NS_KT; e += NS_THREADS) {
+            const int ra = e / NS_KT, ka = e - ra * NS_KT;
+            const int64_t gr = r0 + ra, gk = k0 + ka;
+            As[ka][ra] = gr < bs && gk < bs ? Ab[gr * bs + gk] : 0.0;
+            const int kb = e / NS_TILE, cb = e - kb * NS_TILE;
+            const int64_t gk2 = k0 + kb, gc = c0 + cb;
+            Bs[kb][cb] = gk2 < bs && gc < bs ? Bb[gk2 * bs + gc] : 0.0;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < NS_KT; ++kk) {
+            double a[4], b[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) a[i] = As[kk][ty + 16 * i];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) b[j] = Bs[kk][tx + 16 * j];
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) acc[i][j] = __fma_rn(a[i], b[j], acc[i][j]);
+        }
+        __syncthreads();
+    }
+    const int64_t d = bdim ? bdim[blk] : bs;
+    double ssq = 0.0;
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int64_t gr = r0 + ty + 16 * i, gc = c0 + tx + 16 * j;
+            if (gr >= bs || gc >= bs) continue;
+            double v = acc[i][j];
+            if (EPI) {
+                const double e = gr == gc ? __dsub_rn(v, 1.0) : v;
+                if (gr < d && gc < d) ssq = __fma_rn(e, e, ssq);
+                v = __dsub_rn(gr == gc ? 1.5 : 0.0, __dmul_rn(0.5, v));
+            }
+            Cb[gr * bs + gc] = v;
+        }
+    if (EPI) {
+        red[threadIdx.x] = ssq;
+        __syncthreads();
+        for (int w = NS_THREADS / 2; w > 0; w >>= 1) {
+            if (threadIdx.x < w) red[threadIdx.x] = __dadd_rn(red[threadIdx.x], red[threadIdx.x + w]);
+            __syncthreads();
+        }
+        if (threadIdx.x == 0)
+            part[blk * (int64_t)(gridDim.x * gridDim.y) + blockIdx.y * gridDim.x + blockIdx.x] = red[0];
+    }
+}
+
+// out[0] = max over blocks of ||Z Y - I||_F (tile partials summed in a fixed
+// order); a NaN anywhere gives NaN.
+__global__ void __launch_bounds__(NS_THREADS) k_ns_resid(const double *part, int64_t nblk,
+                                                         int tiles, double *out) {
+    __shared__ double red[NS_THREADS];
+    double mx = 0.0;
+    for (int64_t b = threadIdx.x; b < nblk; b += NS_THREADS) {
+        double sum = 0.0;
+        for (int t = 0; t < tiles; ++t) sum = __dadd_rn(sum, part[b * tiles + t]);
+        if (!(sum <= mx)) mx = sum;
+    }
+    red[threadIdx.x] = mx;
+    __syncthreads();
+    for (int w = NS_THREADS / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < w && !(red[threadIdx.x + w] <= red[threadIdx.x]))
+            red[threadIdx.x] = red[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) out[0] = __dsqrt_rn(red[0]);
+}
+
+// out = (Z + Z^T) / (2 sqrt(alpha)) on each block's d x d part, 0 on the padding.
+__global__ void k_ns_finish(const double *Z, int64_t nblk, int64_t bs, const int32_t *bdim,
+                            const double *alpha, double *out) {
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < nblk * bs * bs;
+         q += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t blk = q / (bs * bs), l = q - blk * bs * bs;
+        const int64_t i = l / bs, j = l - i * bs;
+        const int64_t d = bdim ? bdim[blk] : bs;
+        const double *Zb = Z + blk * bs * bs;
+        out[q] = i < d && j < d
+                     ? __ddiv_rn(__dmul_rn(0.5, __dadd_rn(Zb[i * bs + j], Zb[j * bs + i])),
+                                 __dsqrt_rn(alpha[blk]))
+                     : 0.0;
+    }
+}
+
+pmmf_status core_inverse_sqrt(const double *core, int64_t nblk, int64_t bs, const int32_t *bdim,
+                              const double *hdiag, const int32_t *core_pos, int64_t n,
+                              double *out, unsigned *status, int *iterations, cudaStream_t st) {
+    k_wavelet_positive<<<grid_for(n, 256), 256, 0, st>>>(hdiag, core_pos, n, status);
+    PMMF_TRY(launched("wavelet_positive"));
+    if (iterations) *iterations = 0;
+    if (nblk == 0 || bs == 0) return PMMF_OK;
+    const int64_t bb = nblk * bs * bs;
+    const int tx = (int)((bs + NS_TILE - 1) / NS_TILE);
+    if (nblk > 65535) {
+        set_error("too many core blocks for the inverse square root");
+        return PMMF_ERR_UNSUPPORTED;
+    }
+    DBuf<double> Y, Z, Y2, Z2, T, alpha, part, res;
+    PMMF_TRY(Y.alloc(bb, st));
+    PMMF_TRY(Z.alloc(bb, st));
+    PMMF_TRY(Y2.alloc(bb, st));
+    PMMF_TRY(Z2.alloc(bb, st));
+    PMMF_TRY(T.alloc(bb, st));
+    PMMF_TRY(alpha.alloc(nblk, st));
+    PMMF_TRY(part.alloc(nblk * tx * tx, st));
+    PMMF_TRY(res.alloc(1, st));
+    k_ns_init<<<(unsigned)nblk, NS_THREADS, 0, st>>>(core, bs, bdim, Y.p, Z.p, alpha.p, status);
+    PMMF_TRY(launched("ns_init"));
+    const dim3 grid((unsigned)tx, (unsigned)tx, (unsigned)nblk);
+    double *y = Y.p, *z = Z.p, *y2 = Y2.p, *z2 = Z2.p;
+    double prev = INFINITY, r = INFINITY;
+    bool conv = false;
+    int it = 0;
+    for (; it < NS_MAXIT; ++it) {
+        k_ns_gemm<true><<<grid, NS_THREADS, 0, st>>>(z, y, T.p, bs, bdim, part.p);
+        PMMF_TRY(launched("ns_gemm"));
+        k_ns_resid<<<1, NS_THREADS, 0, st>>>(part.p, nblk, tx * tx, res.p);
+        PMMF_TRY(launched("ns_resid"));
+        PMMF_CUDA_TRY(cudaMemcpyAsync(&r, res.p, sizeof(double), cudaMemcpyDeviceToHost, st));
+        PMMF_CUDA_TRY(cudaStreamSynchronize(st));
+        // converged: at the rounding floor, or no longer contracting once
+        // quadratic convergence has brought the residual near it
+        if (r <= 1e-15 * (double)bs || (r <= 1e-6 && r > 0.25 * prev)) {
+            conv = true;
+            break;
+        }
+        if (!(r < 1e12)) break;     // diverging (an eigenvalue <= 0) or NaN
+        k_ns_gemm<false><<<grid, NS_THREADS, 0, st>>>(y, T.p, y2, bs, bdim, nullptr);
+        PMMF_TRY(launched("ns_gemm"));
+        k_ns_gemm<false><<<grid, NS_THREADS, 0, st>>>(T.p, z, z2, bs, bdim, nullptr);
+        PMMF_TRY(launched("ns_gemm"));
+        std::swap(y, y2);
+        std::swap(z, z2);
+        prev = r;
+    }
+    if (iterations) *iterations = it;
+    if (!conv && !(r <= 1e-6)) {
+        set_error("core is not positive definite (its inverse square root did not converge)");
+        return PMMF_ERR_NOT_SPD;
+    }
+    k_ns_finish<<<grid_for(bb, 256), 256, 0, st>>>(z, nblk, bs, bdim, alpha.p, out);
+    return launched("ns_finish");
 }
 
 pmmf_status spmv(const DevCsr &A, const double *x, double *y, int nrhs, cudaStream_t st) {
@@ -460,16 +696,5 @@ namespace pmmf {
 
 // H or H^-1 with caller-provided scratch for the core slice (H.m * nrhs
 // doubles); used by the allocation-free entry point.
-pmmf_status apply_h_scratch(const HData &H, bool inverse, double *x, int64_t ld, int64_t nrhs,
-                            double *zc, cudaStream_t st) {
-    if (inverse)
-        k_h_diag<true><<<grid_for(H.n * nrhs, 256), 256, 0, st>>>(x, ld, H.n, nrhs, H.hdiag, H.core_pos, zc);
-    else
-        k_h_diag<false><<<grid_for(H.n * nrhs, 256), 256, 0, st>>>(x, ld, H.n, nrhs, H.hdiag, H.core_pos, zc);
-    PMMF_TRY(launched("h_diag"));
-    k_core_gemv<<<grid_for(H.m * nrhs, 64), 64, 0, st>>>(inverse ? H.core_inv : H.core, H.nblk,
-                                                         H.bs, H.bdim, zc, nrhs, H.core_idx, x, ld);
-    return launched("core_gemv");
-}
 
 }  // namespace pmmf

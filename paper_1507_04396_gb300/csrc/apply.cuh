@@ -36,6 +36,7 @@ struct HData {
     const int32_t *core_idx = nullptr;   // m slots: global id (unused slots -1)
     const double *core = nullptr;        // nblk * bs * bs
     const double *core_inv = nullptr;    // nblk * bs * bs
+    const double *core_isqrt = nullptr;  // bs * bs (single core): core^{-1/2}
 };
 
 struct DevCsr {
@@ -53,6 +54,21 @@ pmmf_status apply_h(const HData &H, bool inverse, double *x, int64_t ld, int64_t
                     cudaStream_t st);
 pmmf_status apply_h_scratch(const HData &H, bool inverse, double *x, int64_t ld, int64_t nrhs,
                             double *zc, cudaStream_t st);
+// mode 0: H, 1: H^{-1}, 2: H^{-1/2} (the core's inverse square root formed
+// by core_inverse_sqrt).
+pmmf_status apply_h(const HData &H, int mode, double *x, int64_t ld, int64_t nrhs,
+                    cudaStream_t st);
+pmmf_status apply_h_scratch(const HData &H, int mode, double *x, int64_t ld, int64_t nrhs,
+                            double *zc, cudaStream_t st);
+// out = S^{-1/2} for each core block's symmetric S (lower triangle mirrored,
+// the block's bdim x bdim part; bdim NULL: all bs), by the coupled
+// Newton-Schulz iteration, 0 on the padding; status gets ST_NOT_SPD for a
+// wavelet entry that is not positive; PMMF_ERR_NOT_SPD when the iteration
+// diverges or stalls (an eigenvalue <= 0, or numerically so).  iterations
+// (may be NULL) gets the number of Newton-Schulz steps taken.
+pmmf_status core_inverse_sqrt(const double *core, int64_t nblk, int64_t bs, const int32_t *bdim,
+                              const double *hdiag, const int32_t *core_pos, int64_t n,
+                              double *out, unsigned *status, int *iterations, cudaStream_t st);
 pmmf_status invert_core(const double *core, int64_t m, const double *hdiag, const int32_t *core_pos,
                         int64_t n, double *inv, unsigned *status, cudaStream_t st);
 // Block cores (nblk > 1): every block inverted by the same Gauss-Jordan

@@ -15,7 +15,7 @@
 
 namespace pmmf {
 pmmf_status handle_views(const pmmf_handle *f, const ApplyStages **views, HData *H, int64_t *n,
-                         bool *inverse_ready);
+                         bool *inverse_ready, bool *isqrt_ready);
 }
 
 namespace {
@@ -67,26 +67,31 @@ extern "C" pmmf_status pmmf_apply_noalloc(const pmmf_handle *f, int op, const do
         set_error("need nrhs >= 1 and ld >= nrhs");
         return PMMF_ERR_INVALID_ARG;
     }
-    if (op < PMMF_OP_A || op > PMMF_OP_H_INV) {
+    if (op < PMMF_OP_A || op > PMMF_OP_H_INV_SQRT) {
         set_error("unknown op");
         return PMMF_ERR_INVALID_ARG;
     }
     const ApplyStages *views = nullptr;
     HData H;
     int64_t n = 0;
-    bool inv_ready = false;
-    PMMF_TRY(handle_views(f, &views, &H, &n, &inv_ready));
-    const bool uses_h = op == PMMF_OP_A || op == PMMF_OP_A_INV || op == PMMF_OP_H ||
-                        op == PMMF_OP_H_INV;
-    const bool inverse = op == PMMF_OP_A_INV || op == PMMF_OP_H_INV;
+    bool inv_ready = false, isqrt_ready = false;
+    PMMF_TRY(handle_views(f, &views, &H, &n, &inv_ready, &isqrt_ready));
+    const bool uses_h = op != PMMF_OP_U && op != PMMF_OP_UT;
+    const int mode = op == PMMF_OP_A_INV || op == PMMF_OP_H_INV ? 1
+                   : op == PMMF_OP_A_INV_SQRT || op == PMMF_OP_H_INV_SQRT ? 2 : 0;
     if (uses_h && H.m * nrhs > NOALLOC_SCRATCH) {
         set_error("pmmf_apply_noalloc: core_size * nrhs = " + std::to_string(H.m * nrhs) +
                   " exceeds the scratch limit of " + std::to_string(NOALLOC_SCRATCH) + " doubles");
         return PMMF_ERR_UNSUPPORTED;
     }
-    if (inverse && !inv_ready) {
+    if (mode == 1 && !inv_ready) {
         set_error("pmmf_apply_noalloc: the core inverse is not formed yet; call pmmf_apply once "
                   "with PMMF_OP_A_INV or PMMF_OP_H_INV first");
+        return PMMF_ERR_INVALID_ARG;
+    }
+    if (mode == 2 && !isqrt_ready) {
+        set_error("pmmf_apply_noalloc: the core inverse square root is not formed yet; call "
+                  "pmmf_apply once with PMMF_OP_A_INV_SQRT or PMMF_OP_H_INV_SQRT first");
         return PMMF_ERR_INVALID_ARG;
     }
     double *scratch = nullptr;
@@ -97,10 +102,11 @@ extern "C" pmmf_status pmmf_apply_noalloc(const pmmf_handle *f, int op, const do
     case PMMF_OP_U: return apply_rotations(*views, false, y, ld, nrhs, st);
     case PMMF_OP_UT: return apply_rotations(*views, true, y, ld, nrhs, st);
     case PMMF_OP_H:
-    case PMMF_OP_H_INV: return apply_h_scratch(H, inverse, y, ld, nrhs, scratch, st);
+    case PMMF_OP_H_INV:
+    case PMMF_OP_H_INV_SQRT: return apply_h_scratch(H, mode, y, ld, nrhs, scratch, st);
     default:
         PMMF_TRY(apply_rotations(*views, false, y, ld, nrhs, st));
-        PMMF_TRY(apply_h_scratch(H, inverse, y, ld, nrhs, scratch, st));
+        PMMF_TRY(apply_h_scratch(H, mode, y, ld, nrhs, scratch, st));
         return apply_rotations(*views, true, y, ld, nrhs, st);
     }
 }

@@ -25,6 +25,7 @@ ERR_NOT_SPD, ERR_SINGULAR_CORE, ERR_NOT_CONVERGED, ERR_TIMEOUT, ERR_UNSUPPORTED 
 HOST, DEVICE = 0, 1
 CSR, DENSE = 0, 1
 OP_A, OP_A_INV, OP_U, OP_UT, OP_H, OP_H_INV = 0, 1, 2, 3, 4, 5
+OP_A_INV_SQRT, OP_H_INV_SQRT = 6, 7
 PREC_FP64, PREC_TF32, PREC_BF16 = 0, 1, 2
 
 STATUS_NAMES = {0: "OK", 1: "INVALID_ARG", 2: "NOT_SYMMETRIC", 3: "NONFINITE", 4: "OOM",
@@ -69,7 +70,8 @@ EXPORTS = ["pmmf_factor", "pmmf_apply", "pmmf_solve_precond", "pmmf_free", "pmmf
            "pmmf_get_stage_rotations", "pmmf_get_h", "pmmf_get_stage_matrix",
            "pmmf_launch_count", "pmmf_apply_backward", "pmmf_get_angles", "pmmf_set_angles",
            "pmmf_set_h", "pmmf_factor_blockdiag", "pmmf_factor_batched", "pmmf_get_batch",
-           "pmmf_get_precision_stats", "pmmf_set_tuning", "pmmf_clear_tuning"]
+           "pmmf_get_precision_stats", "pmmf_set_tuning", "pmmf_clear_tuning",
+           "pmmf_solve_precond_sym"]
 
 _lib = None
 
@@ -90,6 +92,8 @@ def load(path: str = LIB_PATH):
     L.pmmf_apply.argtypes = [vp, i32, vp, vp, i64, i64, vp]
     L.pmmf_solve_precond.restype = i32
     L.pmmf_solve_precond.argtypes = [vp, C.POINTER(Matrix), vp, vp, i64, f64, i32, vp, vp, vp]
+    L.pmmf_solve_precond_sym.restype = i32
+    L.pmmf_solve_precond_sym.argtypes = [vp, C.POINTER(Matrix), vp, vp, i64, f64, i32, vp, vp, vp]
     L.pmmf_free.restype = None
     L.pmmf_free.argtypes = [vp]
     L.pmmf_last_error.restype = C.c_char_p
@@ -256,6 +260,16 @@ def pmmf_solve_precond(handle: int, matrix: Matrix, b, x, nrhs: int, rtol: float
     relres = np.zeros(nrhs)
     st = load().pmmf_solve_precond(handle, C.byref(matrix), _ptr(b), _ptr(x), nrhs, rtol, maxit,
                                    iters.ctypes.data, relres.ctypes.data, _stream(stream))
+    return st, iters, relres
+
+
+def pmmf_solve_precond_sym(handle: int, matrix: Matrix, b, x, nrhs: int, rtol: float,
+                           maxit: int, stream=None):
+    iters = np.zeros(nrhs, dtype=np.int32)
+    relres = np.zeros(nrhs)
+    st = load().pmmf_solve_precond_sym(handle, C.byref(matrix), _ptr(b), _ptr(x), nrhs, rtol,
+                                       maxit, iters.ctypes.data, relres.ctypes.data,
+                                       _stream(stream))
     return st, iters, relres
 
 
@@ -457,13 +471,18 @@ class Factorization:
         out["dtheta"] = out["dtheta"][:i.rotations]
         return out
 
-    def solve(self, a, b, rtol=1e-8, maxit=1000, stream=None):
-        """Preconditioned CG for a x = b (b: CUDA float64 (n,) or (n, nrhs))."""
+    def solve(self, a, b, rtol=1e-8, maxit=1000, xi=1.0, stream=None):
+        """Preconditioned CG for a x = b (b: CUDA float64 (n,) or (n, nrhs)).
+        xi = 1: PCG with M^{-1} = A~^{-1}; xi = 0.5: CG on the split system
+        A~^{-1/2} a A~^{-1/2} (Sec. 4)."""
         import torch
+        if xi not in (1, 1.0, 0.5):
+            raise ValueError("xi must be 1 or 0.5")
         m, keep = make_matrix(a)
         x = torch.empty_like(b)
         nrhs = 1 if b.dim() == 1 else b.shape[1]
-        st, iters, relres = pmmf_solve_precond(self.handle, m, b, x, nrhs, rtol, maxit, stream)
+        fn = pmmf_solve_precond_sym if xi == 0.5 else pmmf_solve_precond
+        st, iters, relres = fn(self.handle, m, b, x, nrhs, rtol, maxit, stream)
         return st, x, iters, relres
 
 

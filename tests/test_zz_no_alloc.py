@@ -49,8 +49,9 @@ def test_noalloc_apply_matches_apply_twice_without_allocating():
     f = pm.factor(a, k=2, eta=0.5, cluster_size=150, core_size=60, seed=6)
     nrhs = 4
     x = torch.from_numpy(np.random.default_rng(1).standard_normal((a.n, nrhs))).cuda()
-    ops = [pm.OP_U, pm.OP_UT, pm.OP_H, pm.OP_A, pm.OP_H_INV, pm.OP_A_INV]
-    ref = {op: f.apply(op, x) for op in ops}          # allocating path; forms the inverse
+    ops = [pm.OP_U, pm.OP_UT, pm.OP_H, pm.OP_A, pm.OP_H_INV, pm.OP_A_INV, pm.OP_H_INV_SQRT,
+           pm.OP_A_INV_SQRT]
+    ref = {op: f.apply(op, x) for op in ops}   # allocating path; forms inverse, inverse sqrt
     outs = {op: [torch.empty_like(x), torch.empty_like(x)] for op in ops}
     torch.cuda.synchronize()
 
@@ -93,5 +94,8 @@ def test_noalloc_rejects_oversize_and_unformed_inverse():
     pm.pmmf_apply_noalloc(f.handle, pm.OP_U, x, y, nrhs, nrhs)
     with pytest.raises(pm.PmmfError) as e:
         pm.pmmf_apply_noalloc(f.handle, pm.OP_A_INV, x[:, :2].contiguous(), y[:, :2].contiguous(), 2, 2)
+    assert e.value.status == pm.ERR_INVALID_ARG
+    with pytest.raises(pm.PmmfError) as e:
+        pm.pmmf_apply_noalloc(f.handle, pm.OP_A_INV_SQRT, x[:, :2].contiguous(), y[:, :2].contiguous(), 2, 2)
     assert e.value.status == pm.ERR_INVALID_ARG
     f.close()
