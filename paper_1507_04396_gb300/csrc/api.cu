@@ -28,6 +28,7 @@ struct StageData {
     Csr recorded;               // A_p[S_p, S_p] if params.record_stages
     DBuf<int32_t> recorded_act; // its row -> global id map
     bool has_record = false;
+    DBuf<int64_t> nnz_d;        // A_p's exact entry count, read after the loop
 };
 
 }  // namespace pmmf
@@ -65,6 +66,17 @@ constexpr int64_t DENSE_MAX_N = 24576;   // rows of 8 * n bytes in shared memory
 pmmf_status fail(pmmf_status s, const char *msg) {
     set_error(msg);
     return s;
+}
+
+// Reads the exact entry count of a matrix whose nnz is only a capacity.
+pmmf_status exact_nnz(Csr &A, cudaStream_t st) {
+    if (A.nnz_exact) return PMMF_OK;
+    int64_t v = 0;
+    PMMF_CUDA_TRY(cudaMemcpyAsync(&v, A.rowptr.p + A.rows, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+    PMMF_CUDA_TRY(cudaStreamSynchronize(st));
+    A.nnz = v;
+    A.nnz_exact = true;
+    return PMMF_OK;
 }
 
 void set_pool_threshold() {
@@ -299,7 +311,9 @@ pmmf_status factor_impl(const pmmf_matrix *A, const pmmf_params *prm, pmmf_handl
         UpdateOut up;
         PMMF_TRY(update_stage(cur, act.p, n, pos.p, cl.p, loc.p, S.cls, S.cmax, S.rot,
                               elimflag.p, p, h->hdiag.p, contribs.p + (p - 1), up, status.p, st));
-        S.nnz_after = up.next.nnz;
+        PMMF_TRY(S.nnz_d.alloc(1, st));
+        PMMF_CUDA_TRY(cudaMemcpyAsync(S.nnz_d.p, up.next.rowptr.p + up.next.rows, sizeof(int64_t),
+                                      cudaMemcpyDeviceToDevice, st));
         // next stage's row positions
         PMMF_CUDA_TRY(cudaMemsetAsync(pos.p, 0xFF, sizeof(int32_t) * (size_t)n, st));
         PMMF_TRY(set_positions(up.act.p, up.next.rows, pos.p, st));
@@ -307,6 +321,7 @@ pmmf_status factor_impl(const pmmf_matrix *A, const pmmf_params *prm, pmmf_handl
         cur = std::move(up.next);
         act = std::move(up.act);
         if (prm->record_stages) {
+            PMMF_TRY(exact_nnz(cur, st));
             S.recorded.rows = cur.rows;
             S.recorded.nnz = cur.nnz;
             PMMF_TRY(S.recorded.rowptr.alloc(cur.rows + 1, st));
@@ -334,6 +349,8 @@ pmmf_status factor_impl(const pmmf_matrix *A, const pmmf_params *prm, pmmf_handl
             if (h->st[q].m > 0)
                 PMMF_CUDA_TRY(cudaMemcpyAsync(nl[q].data(), h->st[q].rot.nlev.p, sizeof(int32_t) * nl[q].size(),
                                               cudaMemcpyDeviceToHost, st));
+            PMMF_CUDA_TRY(cudaMemcpyAsync(&h->st[q].nnz_after, h->st[q].nnz_d.p, sizeof(int64_t),
+                                          cudaMemcpyDeviceToHost, st));
         }
         PMMF_CUDA_TRY(cudaStreamSynchronize(st));
         if (hs & ST_ROW_TOO_LONG) return fail(PMMF_ERR_UNSUPPORTED, "update: output row too long");
@@ -710,7 +727,10 @@ pmmf_status factor_batch_impl(const pmmf_matrix *A, const std::vector<int64_t> &
             PMMF_CUDA_TRY(cudaMemcpyAsync(&hs, status.p, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
             PMMF_CUDA_TRY(cudaMemcpyAsync(nl.data(), S.rot.nlev.p, sizeof(int32_t) * nl.size(), cudaMemcpyDeviceToHost, st));
             PMMF_CUDA_TRY(cudaMemcpyAsync(cc.data(), ccl.p, sizeof(double) * cc.size(), cudaMemcpyDeviceToHost, st));
+            PMMF_CUDA_TRY(cudaMemcpyAsync(&up.next.nnz, up.next.rowptr.p + up.next.rows, sizeof(int64_t),
+                                          cudaMemcpyDeviceToHost, st));
             PMMF_CUDA_TRY(cudaStreamSynchronize(st));
+            up.next.nnz_exact = true;
             if (hs & ST_ROW_TOO_LONG) return fail(PMMF_ERR_UNSUPPORTED, "update: output row too long");
             if (hs & ST_NOT_CONVERGED)
                 return fail(PMMF_ERR_NOT_CONVERGED, "k x k Jacobi did not converge in 32 sweeps");

@@ -117,10 +117,25 @@ __device__ __forceinline__ void rot_pair_t(double c, double s, double a, double 
     nb = __fma_rn(-s, a, __dmul_rn(c, b));
 }
 
-// x != 0.0 tested on the bits (integer pipe; FP64 compares are slow on GB300).
-__device__ __forceinline__ bool nonzero_bits(double x) {
-    return ((unsigned long long)__double_as_longlong(x) << 1) != 0ull;
+// The bits of a double and back, moved by inline PTX.  The move is opaque to
+// the compiler, so integer tests on the bits stay integer instructions; an
+// equivalent bit test written in C++ may be turned back into an FP64 compare
+// or absolute value, and on GB300 every FP64 instruction takes a share of the
+// SM's small FP64 pipe (one warp instruction per ~19 cycles per SM).
+__device__ __forceinline__ unsigned long long f64_bits(double x) {
+    unsigned long long u;
+    asm("mov.b64 %0, %1;" : "=l"(u) : "d"(x));
+    return u;
 }
+__device__ __forceinline__ double f64_from_bits(unsigned long long u) {
+    double x;
+    asm("mov.b64 %0, %1;" : "=d"(x) : "l"(u));
+    return x;
+}
+constexpr unsigned long long F64_ABS = 0x7fffffffffffffffull;
+
+// x != 0.0 tested on the bits (integer pipe).
+__device__ __forceinline__ bool nonzero_bits(double x) { return (f64_bits(x) << 1) != 0ull; }
 
 __device__ __forceinline__ double warp_sum(double v) {
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);

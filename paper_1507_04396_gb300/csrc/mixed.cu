@@ -359,7 +359,7 @@ k_select_mixed(int64_t s, const int64_t *coff, const int32_t *members, const int
         for (int y = tid; y < c; y += MX_THREADS) {
             double h = -1.0, l = -1.0;
             if (y != i && on(mask, y)) {
-                const double sc = __dmul_rn(fabs((double)G[(int64_t)i * c + y]), w[y]);
+                const double sc = f64_from_bits(f64_bits(__dmul_rn((double)G[(int64_t)i * c + y], w[y])) & F64_ABS);
                 const double d = __dmul_ru((double)B[(int64_t)i * c + y], __dmul_ru(w[y], 1.0 + 0x1p-40));
                 h = __dadd_ru(sc, __dadd_ru(d, __dmul_ru(sc, 0x1p-50)));
                 l = __dsub_rd(sc, __dadd_ru(d, __dmul_ru(sc, 0x1p-50)));
@@ -432,7 +432,7 @@ k_select_mixed(int64_t s, const int64_t *coff, const int32_t *members, const int
             for (int b = 0; b < nb; ++b) {
                 const int y = sl[q0 + b];
                 const double gv = s_dots[b];
-                const double sc = __dmul_rn(fabs(gv), w[y]);
+                const double sc = f64_from_bits(f64_bits(__dmul_rn(gv, w[y])) & F64_ABS);
                 // insert into the top kk-1 (ties to the smaller index)
                 int pos2 = kk - 1;
                 while (pos2 > 0 && (sc > best_s[pos2 - 1] || (sc == best_s[pos2 - 1] && y < best_y[pos2 - 1])))

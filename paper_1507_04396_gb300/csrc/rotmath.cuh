@@ -14,14 +14,14 @@ namespace pmmf {
 // doubles the magnitude bits order like the magnitudes.
 __device__ __forceinline__ void jacobi2(double a, double b, double d, double &c, double &s) {
     const unsigned long long ABS = 0x7fffffffffffffffull;
-    if ((__double_as_longlong(b) & ABS) == 0) {
+    if ((f64_bits(b) & ABS) == 0) {
         c = 1.0;
         s = 0.0;
         return;
     }
     double h = __dsub_rn(d, a);
     double g = __dmul_rn(2.0, b);
-    const unsigned long long hm = __double_as_longlong(h) & ABS, gm = __double_as_longlong(g) & ABS;
+    const unsigned long long hm = f64_bits(h) & ABS, gm = f64_bits(g) & ABS;
     const unsigned long long mm = hm > gm ? hm : gm;
     if (mm > (unsigned long long)__double_as_longlong(0x1p500)) {
         h = __dmul_rn(h, 0x1p-600);
@@ -30,15 +30,15 @@ __device__ __forceinline__ void jacobi2(double a, double b, double d, double &c,
         h = __dmul_rn(h, 0x1p600);
         g = __dmul_rn(g, 0x1p600);
     }
-    const unsigned long long hb = __double_as_longlong(h);
-    const double habs = __longlong_as_double(hb & ABS);
+    const unsigned long long hb = f64_bits(h);
+    const double habs = f64_from_bits(hb & ABS);
     const bool hnonneg = (hb >> 63) == 0 || (hb & ABS) == 0;   // h >= 0, -0 included
     const double g2 = __dmul_rn(g, g);
     const double r = __dsqrt_rn(__dadd_rn(__dmul_rn(h, h), g2));
     const double q = __dadd_rn(habs, r);
     const double den = __dsqrt_rn(__dadd_rn(__dmul_rn(q, q), g2));
     c = __ddiv_rn(q, den);
-    s = __ddiv_rn(hnonneg ? g : -g, den);
+    s = __ddiv_rn(hnonneg ? g : f64_from_bits(f64_bits(g) ^ ~ABS), den);
 }
 
 // Row a of x_T' = O x_T for a k x k block O (row-major, stride kk): an fma

@@ -168,13 +168,13 @@ __device__ __forceinline__ void cand_merge(Cand &a, const Cand &b) {
 }
 
 __device__ __forceinline__ Cand cand_make(double g, double m, double wy, int32_t y) {
-    const double ag = __longlong_as_double(__double_as_longlong(g) & 0x7fffffffffffffffll);   // |g|
-    return Cand{(unsigned long long)__double_as_longlong(__dmul_rn(ag, wy)), y, g, m};
+    // |g| * w = |g * w| bit for bit (round to nearest is symmetric, w >= 0)
+    return Cand{f64_bits(__dmul_rn(g, wy)) & F64_ABS, y, g, m};
 }
 
 // True when x is +0 or -0, tested on the bits (integer pipe, not FP64).
 __device__ __forceinline__ bool is_zero(double x) {
-    return ((unsigned long long)__double_as_longlong(x) << 1) == 0ull;
+    return (f64_bits(x) << 1) == 0ull;
 }
 
 // Same candidate as cand_make; a zero entry scores +0 (key 0) without an FP64
@@ -630,14 +630,14 @@ k_select_fast(const int64_t *coff, const int32_t *members, const int64_t *goff, 
                 const double a = gd[i], d = gd[j], ma0 = md[i], md0 = md[j];
                 double cc, ss;
                 const unsigned long long ABS = 0x7fffffffffffffffull;
-                if ((__double_as_longlong(gij) & ABS) == 0) {
+                if ((f64_bits(gij) & ABS) == 0) {
                     cc = 1.0;
                     ss = 0.0;
                 } else {
                     // angle prefix (jacobi2), computed by every FP64 warp
                     double h = __dsub_rn(d, a);
                     double g = __dmul_rn(2.0, gij);
-                    const unsigned long long hm = __double_as_longlong(h) & ABS, gm = __double_as_longlong(g) & ABS;
+                    const unsigned long long hm = f64_bits(h) & ABS, gm = f64_bits(g) & ABS;
                     const unsigned long long mm = hm > gm ? hm : gm;
                     if (mm > (unsigned long long)__double_as_longlong(0x1p500)) {
                         h = __dmul_rn(h, 0x1p-600);
@@ -646,8 +646,8 @@ k_select_fast(const int64_t *coff, const int32_t *members, const int64_t *goff, 
                         h = __dmul_rn(h, 0x1p600);
                         g = __dmul_rn(g, 0x1p600);
                     }
-                    const unsigned long long hb = __double_as_longlong(h);
-                    const double habs = __longlong_as_double(hb & ABS);
+                    const unsigned long long hb = f64_bits(h);
+                    const double habs = f64_from_bits(hb & ABS);
                     const bool hnonneg = (hb >> 63) == 0 || (hb & ABS) == 0;
                     const double g2v = __dmul_rn(g, g);
                     const double r = __dsqrt_rn(__dadd_rn(__dmul_rn(h, h), g2v));
@@ -655,7 +655,7 @@ k_select_fast(const int64_t *coff, const int32_t *members, const int64_t *goff, 
                     const double den = __dsqrt_rn(__dadd_rn(__dmul_rn(q, q), g2v));
                     // c by warp 0, s by warp 1
                     if (wid == 0) s_x[0] = __ddiv_rn(q, den);
-                    else if (wid == 1) s_x[1] = __ddiv_rn(hnonneg ? g : -g, den);
+                    else if (wid == 1) s_x[1] = __ddiv_rn(hnonneg ? g : f64_from_bits(f64_bits(g) ^ ~ABS), den);
                     fp_sync();
                     cc = s_x[0];
                     ss = s_x[1];

@@ -121,8 +121,8 @@ k_select_k(const int64_t *coff, const int32_t *members, const int64_t *goff, dou
             unsigned long long kv = EXCL;
             if (y != i && active_bit(mask, y)) {
                 const double g = G[(int64_t)i * c + y];
-                const double ag = __longlong_as_double(__double_as_longlong(g) & 0x7fffffffffffffffll);
-                kv = (unsigned long long)__double_as_longlong(__dmul_rn(ag, w[y]));
+                // |g| * w = |g * w| bit for bit (round to nearest is symmetric)
+                kv = f64_bits(__dmul_rn(g, w[y])) & F64_ABS;
             }
             key[y] = kv;
         }

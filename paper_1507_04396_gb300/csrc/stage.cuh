@@ -25,7 +25,8 @@ struct StageClusters {
 
 // A CSR block over the active rows: row r is global id act[r].
 struct Csr {
-    int64_t rows = 0, nnz = 0;
+    int64_t rows = 0, nnz = 0;    // nnz: entries allocated (>= rowptr[rows])
+    bool nnz_exact = true;        // false: the count is rowptr[rows] on the device
     DBuf<int64_t> rowptr;
     DBuf<int32_t> col;        // global ids
     DBuf<double> val;

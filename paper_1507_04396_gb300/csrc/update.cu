@@ -13,6 +13,13 @@
 // bits equal a sequential application in step order).  A rotation whose two
 // inputs are both zero leaves them zero and is skipped.  Exact zeros are
 // dropped from the output.
+//
+// The counting passes that size the outputs run on the sparsity pattern only
+// (a rotation makes both of its coordinates nonzero when either is): integer
+// work, no FP64, and an upper bound of the numeric counts, which differ only
+// where a value cancels to exactly zero.  Pass 1 writes W into rows of that
+// capacity (each row's end is its write cursor); pass 2 writes A_p into rows
+// of that capacity and a compaction copies them to their exact positions.
 #include <climits>
 
 #include "common.cuh"
@@ -27,6 +34,7 @@ enum Mode { P1_COUNT = 0, P1_WRITE = 1, P2_COUNT = 2, P2_WRITE = 3 };
 
 struct RowArgs {
     const int64_t *rp;
+    const int64_t *rend;       // row ends (NULL: rp[r + 1])
     const int32_t *ci;
     const double *v;
     int64_t rows;
@@ -52,8 +60,9 @@ struct RowArgs {
     const int32_t *elimflag;
     int32_t stage;
     const int64_t *newrow;     // exclusive scan of surviving flags
-    int64_t *ocnt;             // COUNT: output row lengths (by new row)
-    const int64_t *orp;        // WRITE
+    int64_t *ocnt;             // COUNT: output row capacities (by new row)
+    const int64_t *orp;        // WRITE: row starts of capacity rowptr
+    int64_t *acnt;             // WRITE: exact output row lengths (by new row)
     int32_t *ocol;
     double *oval;
     double *hdiag;
@@ -77,6 +86,7 @@ __host__ __device__ inline int64_t rows_per_warp(int64_t cmax, int64_t outcap, b
 
 template <int MODE>
 __global__ void k_rows(RowArgs a) {
+    constexpr bool COUNT = MODE == P1_COUNT || MODE == P2_COUNT;
     extern __shared__ double smem[];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const int wpb = blockDim.x >> 5;
@@ -91,7 +101,7 @@ __global__ void k_rows(RowArgs a) {
     __syncwarp();
     double part = 0.0;
     for (int64_t r = blockIdx.x * (int64_t)wpb + wib; r < a.rows; r += (int64_t)gridDim.x * wpb) {
-        const int64_t e0 = a.rp[r], e1 = a.rp[r + 1];
+        const int64_t e0 = a.rp[r], e1 = a.rend ? a.rend[r] : a.rp[r + 1];
         const int32_t y = a.act[r];
         const bool yelim = (MODE >= P2_COUNT) && a.elimflag[y] == a.stage;
         int64_t nout = 0;
@@ -114,7 +124,7 @@ __global__ void k_rows(RowArgs a) {
                 int32_t g = a.ci[q];
                 if (a.cl[g] == mu) {
                     const int l = a.loc[g];
-                    dense[l] = a.v[q];
+                    if (!COUNT) dense[l] = a.v[q];
                     atomicOr(&tb[l >> 5], 1u << (l & 31));
                 }
             }
@@ -144,6 +154,16 @@ __global__ void k_rows(RowArgs a) {
                     if (L + 1 < nl && b0 + lane < b1) nxt = a.lvlrot[b0 + lane];
                     for (int idx = c0 + lane; idx < c1; idx += 32) {
                         const Rot2 q = idx == c0 + lane ? cur : a.lvlrot[idx];
+                        if (COUNT) {
+                            // pattern only: both coordinates nonzero if either is
+                            const bool bi = (tb[q.li >> 5] >> (q.li & 31)) & 1u;
+                            const bool bj = (tb[q.lj >> 5] >> (q.lj & 31)) & 1u;
+                            if (bi != bj) {
+                                atomicOr(&tb[q.li >> 5], 1u << (q.li & 31));
+                                atomicOr(&tb[q.lj >> 5], 1u << (q.lj & 31));
+                            }
+                            continue;
+                        }
                         double vi = dense[q.li], vj = dense[q.lj];
                         if (nonzero_bits(vi) || nonzero_bits(vj)) {
                             double ni, nj;
@@ -164,6 +184,13 @@ __global__ void k_rows(RowArgs a) {
                         const int64_t t = a.lvlidx[idx];
                         const int kk = a.kkv[t];
                         const int32_t *T = a.kidx + t * a.K;
+                        if (COUNT) {
+                            bool any = false;
+                            for (int q = 0; q < kk; ++q) any |= (tb[T[q] >> 5] >> (T[q] & 31)) & 1u;
+                            if (any)
+                                for (int q = 0; q < kk; ++q) atomicOr(&tb[T[q] >> 5], 1u << (T[q] & 31));
+                            continue;
+                        }
                         double in[8];
                         bool nz = false;
                         for (int q = 0; q < kk; ++q) {
@@ -210,9 +237,12 @@ __global__ void k_rows(RowArgs a) {
                 int cnt = 0;
                 for (uint32_t m = bits; m; m &= m - 1) {
                     const int l = wi * 32 + __ffs(m) - 1;
-                    const double x = dense[l];
-                    dense[l] = 0.0;
-                    if (!nonzero_bits(x)) continue;
+                    double x = 0.0;
+                    if (!COUNT) {
+                        x = dense[l];
+                        dense[l] = 0.0;
+                        if (!nonzero_bits(x)) continue;
+                    }
                     const int32_t g = a.members[cb + l];
                     if (MODE == P1_COUNT) {
                         atomicAdd((unsigned long long *)&a.wcnt[a.pos[g]], 1ull);
@@ -270,6 +300,7 @@ __global__ void k_rows(RowArgs a) {
             atomicMax((unsigned long long *)a.maxlen, (unsigned long long)nout);
         }
         if (MODE == P2_WRITE && !yelim) {
+            if (lane == 0) a.acnt[a.newrow[r]] = nout;
             if (nout > a.outcap) {
                 if (lane == 0) atomicOr(a.status, ST_ROW_TOO_LONG);
             } else {
@@ -303,6 +334,22 @@ __global__ void k_survivors(const int32_t *act, int64_t s, const int32_t *elimfl
     for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < s;
          r += (int64_t)gridDim.x * blockDim.x)
         flag[r] = elimflag[act[r]] == stage ? 0 : 1;
+}
+
+// A_p's rows from their capacity slots to their exact positions (warp per row).
+__global__ void k_compact_rows(const int64_t *caprp, const int64_t *rp, int64_t rows,
+                               const int32_t *icol, const double *ival, int32_t *ocol,
+                               double *oval) {
+    const int lane = threadIdx.x & 31;
+    const int64_t w = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t r = w; r < rows; r += nw) {
+        const int64_t src = caprp[r], dst = rp[r], cnt = rp[r + 1] - dst;
+        for (int64_t q = lane; q < cnt; q += 32) {
+            ocol[dst + q] = icol[src + q];
+            oval[dst + q] = ival[src + q];
+        }
+    }
 }
 
 __global__ void k_compact_act(const int32_t *act, int64_t s, const int32_t *flag,
@@ -420,6 +467,7 @@ pmmf_status update_stage(const Csr &A, const int32_t *act, int64_t n, const int3
     a.wval = W.val.p;
     PMMF_TRY(launch_rows<P1_WRITE>(a, A.nnz, wnnz, st));
     W.rowptr = std::move(wrp);
+    // W's row r holds wrp[r] .. wcur[r] - 1 (the written part of its capacity)
 
     // survivors and their new rows
     DBuf<int32_t> flag;
@@ -433,29 +481,46 @@ pmmf_status update_stage(const Csr &A, const int32_t *act, int64_t n, const int3
 
     // pass 2: A_p = W Q^T with accounting and compaction
     out.next.rows = s2;
-    PMMF_TRY(out.next.rowptr.zeros(s2 + 1, st));
-    DBuf<int64_t> maxlen;
+    DBuf<int64_t> caprp, acnt, maxlen;
+    PMMF_TRY(caprp.zeros(s2 + 1, st));
+    PMMF_TRY(acnt.zeros(s2 + 1, st));
     PMMF_TRY(maxlen.zeros(1, st));
     a.rp = W.rowptr.p;
+    a.rend = wcur.p;
     a.ci = W.col.p;
     a.v = W.val.p;
     a.newrow = newrow.p;
-    a.ocnt = out.next.rowptr.p;
+    a.ocnt = caprp.p;
     a.maxlen = maxlen.p;
     PMMF_TRY(launch_rows<P2_COUNT>(a, wnnz, 0, st));
-    PMMF_TRY(scan_i64(out.next.rowptr.p, out.next.rowptr.p, s2, st));
+    PMMF_TRY(scan_i64(caprp.p, caprp.p, s2, st));
     int64_t hv[2] = {0, 0};
-    PMMF_CUDA_TRY(cudaMemcpyAsync(&hv[0], out.next.rowptr.p + s2, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+    PMMF_CUDA_TRY(cudaMemcpyAsync(&hv[0], caprp.p + s2, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
     PMMF_CUDA_TRY(cudaMemcpyAsync(&hv[1], maxlen.p, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
     PMMF_CUDA_TRY(cudaStreamSynchronize(st));
+    DBuf<int32_t> tcol;
+    DBuf<double> tval;
+    PMMF_TRY(tcol.alloc(hv[0], st));
+    PMMF_TRY(tval.alloc(hv[0], st));
+    a.outcap = (int)(hv[1] > 0 ? hv[1] : 1);
+    a.orp = caprp.p;
+    a.ocol = tcol.p;
+    a.oval = tval.p;
+    a.acnt = acnt.p;
+    PMMF_TRY(launch_rows<P2_WRITE>(a, wnnz, hv[0], st));
+    // exact row pointers, and the rows moved there; nnz is the capacity (an
+    // upper bound), the exact count is rowptr[s2] on the device
+    PMMF_TRY(out.next.rowptr.alloc(s2 + 1, st));
+    PMMF_TRY(scan_i64(acnt.p, out.next.rowptr.p, s2, st));
     out.next.nnz = hv[0];
+    out.next.nnz_exact = false;
     PMMF_TRY(out.next.col.alloc(hv[0], st));
     PMMF_TRY(out.next.val.alloc(hv[0], st));
-    a.outcap = (int)(hv[1] > 0 ? hv[1] : 1);
-    a.orp = out.next.rowptr.p;
-    a.ocol = out.next.col.p;
-    a.oval = out.next.val.p;
-    PMMF_TRY(launch_rows<P2_WRITE>(a, wnnz, hv[0], st));
+    if (s2 > 0) {
+        k_compact_rows<<<grid_for(s2 * 32, 256), 256, 0, st>>>(caprp.p, out.next.rowptr.p, s2, tcol.p,
+                                                                tval.p, out.next.col.p, out.next.val.p);
+        PMMF_TRY(launched("compact_rows"));
+    }
 
     PMMF_TRY(out.act.alloc(s2, st));
     k_compact_act<<<grid_for(s, 256), 256, 0, st>>>(act, s, flag.p, newrow.p, out.act.p);
