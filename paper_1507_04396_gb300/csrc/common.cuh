@@ -59,7 +59,7 @@ inline unsigned grid_for(int64_t items, int per_block, int64_t cap = 152 * 64) {
 // Launch parameters that an offline sweep may set per cluster-size bucket
 // (pmmf_set_tuning); tuned(param, size, fallback) returns the value of the
 // smallest bucket whose bound is >= size, else fallback.
-enum TuneParam : int { TUNE_ROWS_WARPS = 0, TUNE_GRAM_WARPS = 1, TUNE_COUNT = 2 };
+enum TuneParam : int { TUNE_ROWS_WARPS = 0, TUNE_GRAM_WARPS = 1, TUNE_SELECT_WARPS = 2, TUNE_COUNT = 3 };
 int tuned(int param, int64_t size, int fallback);
 
 // ---------------------------------------------------------------- profiling
@@ -110,6 +110,11 @@ __device__ __forceinline__ void rot_pair(double c, double s, double a, double b,
     nb = __fma_rn(s, a, __dmul_rn(c, b));
 }
 
+// One output of rot_pair, the same bits: a' when first, else b'.
+__device__ __forceinline__ double rot_pair_one(double c, double s, double a, double b, bool first) {
+    return first ? __fma_rn(c, a, -__dmul_rn(s, b)) : __fma_rn(s, a, __dmul_rn(c, b));
+}
+
 // Transposed rotation: a' = fma(c, a, s b),  b' = fma(-s, a, c b)
 __device__ __forceinline__ void rot_pair_t(double c, double s, double a, double b, double &na,
                                            double &nb) {
@@ -136,6 +141,22 @@ constexpr unsigned long long F64_ABS = 0x7fffffffffffffffull;
 
 // x != 0.0 tested on the bits (integer pipe).
 __device__ __forceinline__ bool nonzero_bits(double x) { return (f64_bits(x) << 1) != 0ull; }
+
+// x > 0.0 on the bits, for x not NaN.
+__device__ __forceinline__ bool pos_bits(double x) {
+    const unsigned long long u = f64_bits(x);
+    return (u >> 63) == 0 && u != 0ull;
+}
+
+// x < y on the bits, for x, y not NaN: magnitudes order like their bits, so
+// map the sign-magnitude pattern to an unsigned order; +0 and -0 are equal.
+__device__ __forceinline__ bool lt_bits(double x, double y) {
+    const unsigned long long a = f64_bits(x), b = f64_bits(y);
+    if (((a | b) << 1) == 0ull) return false;
+    const unsigned long long ka = (a >> 63) ? ~a : (a | 0x8000000000000000ull);
+    const unsigned long long kb = (b >> 63) ? ~b : (b | 0x8000000000000000ull);
+    return ka < kb;
+}
 
 __device__ __forceinline__ double warp_sum(double v) {
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);

@@ -634,28 +634,32 @@ k_select_fast(const int64_t *coff, const int32_t *members, const int64_t *goff, 
                     cc = 1.0;
                     ss = 0.0;
                 } else {
-                    // angle prefix (jacobi2), computed by every FP64 warp
-                    double h = __dsub_rn(d, a);
-                    double g = __dmul_rn(2.0, gij);
-                    const unsigned long long hm = f64_bits(h) & ABS, gm = f64_bits(g) & ABS;
-                    const unsigned long long mm = hm > gm ? hm : gm;
-                    if (mm > (unsigned long long)__double_as_longlong(0x1p500)) {
-                        h = __dmul_rn(h, 0x1p-600);
-                        g = __dmul_rn(g, 0x1p-600);
-                    } else if (mm < (unsigned long long)__double_as_longlong(0x1p-500)) {
-                        h = __dmul_rn(h, 0x1p600);
-                        g = __dmul_rn(g, 0x1p600);
+                    // angle prefix (jacobi2), computed by warps 0 and 1 (each
+                    // needs it for its divide); warps 2 and 3 stay off the
+                    // SM's FP64 pipe meanwhile
+                    if (wid < 2) {
+                        double h = __dsub_rn(d, a);
+                        double g = __dmul_rn(2.0, gij);
+                        const unsigned long long hm = f64_bits(h) & ABS, gm = f64_bits(g) & ABS;
+                        const unsigned long long mm = hm > gm ? hm : gm;
+                        if (mm > (unsigned long long)__double_as_longlong(0x1p500)) {
+                            h = __dmul_rn(h, 0x1p-600);
+                            g = __dmul_rn(g, 0x1p-600);
+                        } else if (mm < (unsigned long long)__double_as_longlong(0x1p-500)) {
+                            h = __dmul_rn(h, 0x1p600);
+                            g = __dmul_rn(g, 0x1p600);
+                        }
+                        const unsigned long long hb = f64_bits(h);
+                        const double habs = f64_from_bits(hb & ABS);
+                        const bool hnonneg = (hb >> 63) == 0 || (hb & ABS) == 0;
+                        const double g2v = __dmul_rn(g, g);
+                        const double r = __dsqrt_rn(__dadd_rn(__dmul_rn(h, h), g2v));
+                        const double q = __dadd_rn(habs, r);
+                        const double den = __dsqrt_rn(__dadd_rn(__dmul_rn(q, q), g2v));
+                        // c by warp 0, s by warp 1
+                        if (wid == 0) s_x[0] = __ddiv_rn(q, den);
+                        else s_x[1] = __ddiv_rn(hnonneg ? g : f64_from_bits(f64_bits(g) ^ ~ABS), den);
                     }
-                    const unsigned long long hb = f64_bits(h);
-                    const double habs = f64_from_bits(hb & ABS);
-                    const bool hnonneg = (hb >> 63) == 0 || (hb & ABS) == 0;
-                    const double g2v = __dmul_rn(g, g);
-                    const double r = __dsqrt_rn(__dadd_rn(__dmul_rn(h, h), g2v));
-                    const double q = __dadd_rn(habs, r);
-                    const double den = __dsqrt_rn(__dadd_rn(__dmul_rn(q, q), g2v));
-                    // c by warp 0, s by warp 1
-                    if (wid == 0) s_x[0] = __ddiv_rn(q, den);
-                    else if (wid == 1) s_x[1] = __ddiv_rn(hnonneg ? g : f64_from_bits(f64_bits(g) ^ ~ABS), den);
                     fp_sync();
                     cc = s_x[0];
                     ss = s_x[1];
@@ -684,7 +688,7 @@ k_select_fast(const int64_t *coff, const int32_t *members, const int64_t *goff, 
                 if (wid == 2 && lane == 0) {
                     const double di = __dsub_rn(na, __dmul_rn(ma, ma));
                     const double dj = __dsub_rn(nd, __dmul_rn(md2, md2));
-                    const int le = di < dj ? i : j;
+                    const int le = lt_bits(di, dj) ? i : j;
                     gd[i] = na;
                     gd[j] = nd;
                     md[i] = ma;
@@ -722,7 +726,7 @@ k_select_fast(const int64_t *coff, const int32_t *members, const int64_t *goff, 
                 // the survivor's new weight (needed from the final reduce on),
                 // overlapping the column threads' work
                 const double x = gd[surv];
-                const double ws = x > 0.0 ? __ddiv_rn(1.0, __dsqrt_rn(x)) : 0.0;
+                const double ws = pos_bits(x) ? __ddiv_rn(1.0, __dsqrt_rn(x)) : 0.0;
                 if (lane == 0) {
                     w[surv] = ws;
                     s_wn[par][0] = ws;
@@ -737,30 +741,31 @@ k_select_fast(const int64_t *coff, const int32_t *members, const int64_t *goff, 
                 for (int q = ct; q < nwork; q += NCTT) {
                     const Work it = work[q];
                     const int y = it.y;
-                    double nig = it.gi, njg = it.gj, nim = it.mi, njm = it.mj;
-                    // only the survivor's row and column are read again
+                    // only the survivor's row and column are read again, so
+                    // only its output of each rotated pair is formed
+                    const bool si = surv == i;
+                    double sg = si ? it.gi : it.gj, sm = si ? it.mi : it.mj;
                     if (it.flags & W_G) {
-                        rot_pair(cc, ss, it.gi, it.gj, nig, njg);
-                        const double v = surv == i ? nig : njg;
-                        G[(int64_t)surv * c + y] = v;
-                        G[(int64_t)y * c + surv] = v;
+                        sg = rot_pair_one(cc, ss, it.gi, it.gj, si);
+                        G[(int64_t)surv * c + y] = sg;
+                        G[(int64_t)y * c + surv] = sg;
                     }
                     if (it.flags & W_M) {
-                        rot_pair(cc, ss, it.mi, it.mj, nim, njm);
-                        const double v = surv == i ? nim : njm;
-                        M[(int64_t)surv * c + y] = v;
-                        M[(int64_t)y * c + surv] = v;
+                        sm = rot_pair_one(cc, ss, it.mi, it.mj, si);
+                        M[(int64_t)surv * c + y] = sm;
+                        M[(int64_t)y * c + surv] = sm;
                     }
                     if (!more) continue;
                     if (y == inext) {
                         // column inext of the survivor's new row
-                        s_survg[par] = surv == i ? nig : njg;
-                        s_survm[par] = surv == i ? nim : njm;
+                        s_survg[par] = sg;
+                        s_survm[par] = sm;
                         continue;
                     }
+                    // the next pivot is the survivor, a1 or a2 (never the
+                    // eliminated coordinate)
                     double gv, mv;
-                    if (inext == i) { gv = nig; mv = nim; }
-                    else if (inext == j) { gv = njg; mv = njm; }
+                    if (inext == surv) { gv = sg; mv = sm; }
                     else if (inext == a1) { gv = it.g1; mv = it.m1; }
                     else { gv = it.g2; mv = it.m2; }
                     cand_merge(nbest, cand_make_sparse(gv, mv, w[y], y));
@@ -887,9 +892,16 @@ pmmf_status select_stage(const StageClusters &cls, int64_t cmax, GramBlocks &gb,
     }
     prof_begin(KF_SELECT, st);
     // 256 threads (128 column threads) up to 512 coordinates, 512 threads
-    // (384 column threads) up to 1,536, the generic kernel beyond
+    // (384 column threads) up to 1,536, the generic kernel beyond.  The wide
+    // CTA spreads a step's loads and FP64 work over 12 column warps; measured
+    // on GB300 it is slower for clusters the narrow one covers (kNN
+    // Laplacians, clusters ~256: 5.1 vs 4.7 ms of search per factorization),
+    // so it is used only beyond 512 coordinates unless tuned otherwise.
     const int kpt = (int)((cmax + NCT - 1) / NCT);
     const int kpt512 = (int)((cmax + 383) / 384);
+    int sw = tuned(TUNE_SELECT_WARPS, cmax, 0);
+    if (sw == 0) sw = 8;
+    if (kpt > 4) sw = 16;
     auto launch = [&](auto kern, int nt) -> pmmf_status {
         if (shf > 48 * 1024)
             PMMF_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shf));
@@ -898,9 +910,10 @@ pmmf_status select_stage(const StageClusters &cls, int64_t cmax, GramBlocks &gb,
                                            rot.nlev.p, elimflag, order, useed);
         return PMMF_OK;
     };
-    if (kpt <= 1) PMMF_TRY(launch(k_select_fast<1, 256>, 256));
-    else if (kpt <= 2) PMMF_TRY(launch(k_select_fast<2, 256>, 256));
-    else if (kpt <= 4) PMMF_TRY(launch(k_select_fast<4, 256>, 256));
+    if (sw == 8 && kpt <= 1) PMMF_TRY(launch(k_select_fast<1, 256>, 256));
+    else if (sw == 8 && kpt <= 2) PMMF_TRY(launch(k_select_fast<2, 256>, 256));
+    else if (sw == 8 && kpt <= 4) PMMF_TRY(launch(k_select_fast<4, 256>, 256));
+    else if (kpt512 <= 1) PMMF_TRY(launch(k_select_fast<1, 512>, 512));
     else if (kpt512 <= 2) PMMF_TRY(launch(k_select_fast<2, 512>, 512));
     else if (kpt512 <= 4) PMMF_TRY(launch(k_select_fast<4, 512>, 512));
     else {
