@@ -293,13 +293,15 @@ pmmf_status factor_impl(const pmmf_matrix *A, const pmmf_params *prm, pmmf_handl
         }
         // one readback per stage for the schedule: rotations, the one-cluster
         // fallback, the largest cluster and the Gram blocks' total size
-        int64_t sched[4] = {0, 0, 0, 0};
+        int64_t sched[5] = {0, 0, 0, 0, 0};
         DBuf<int64_t> e;
-        PMMF_TRY(schedule_stage(S.cls.coff.p, S.cls.m, s, prm->core_size, prm->eta, e,
-                                S.rot.roff, sched, st));
+        PMMF_TRY(schedule_stage(S.cls.coff.p, S.cls.m, S.cls.count_d.p, s, prm->core_size, prm->eta,
+                                e, S.rot.roff, sched, st));
         if (sched[1]) {
             // every cluster too small to rotate: one cluster for this stage
             PMMF_TRY(one_cluster(act.p, s, S.cls, cl.p, loc.p, st));
+        } else {
+            S.cls.m = sched[4];
         }
         S.m = S.cls.m;
         S.nrot = sched[0];
@@ -481,11 +483,12 @@ pmmf_status factor_dense_impl(const pmmf_matrix *A, const pmmf_params *prm, pmmf
         } else {
             PMMF_TRY(one_cluster(act.p, s, S.cls, cl.p, loc.p, st));
         }
-        int64_t sched[4] = {0, 0, 0, 0};
+        int64_t sched[5] = {0, 0, 0, 0, 0};
         DBuf<int64_t> e;
-        PMMF_TRY(schedule_stage(S.cls.coff.p, S.cls.m, s, prm->core_size, prm->eta, e, S.rot.roff,
-                                sched, st));
+        PMMF_TRY(schedule_stage(S.cls.coff.p, S.cls.m, S.cls.count_d.p, s, prm->core_size, prm->eta,
+                                e, S.rot.roff, sched, st));
         if (sched[1]) PMMF_TRY(one_cluster(act.p, s, S.cls, cl.p, loc.p, st));
+        else S.cls.m = sched[4];
         S.m = S.cls.m;
         S.nrot = sched[0];
         S.rot.nrot = sched[0];

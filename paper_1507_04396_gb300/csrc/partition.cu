@@ -22,42 +22,53 @@ namespace {
 
 constexpr uint32_t QMAX = 32767u;
 
-__global__ void k_bbox(const double *x, int64_t n, int dim, double *lohi, unsigned *status) {
-    __shared__ double slo[32], shi[32];
-    for (int d = 0; d < dim; ++d) {
-        double lo = x[d], hi = x[d];
-        bool bad = false;
-        for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
-            double v = x[i * dim + d];
-            bad |= !isfinite(v);
-            lo = fmin(lo, v);
-            hi = fmax(hi, v);
-        }
-        if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(status, ST_NONFINITE);
-        for (int o = 16; o > 0; o >>= 1) {
-            lo = fmin(lo, __shfl_xor_sync(0xffffffffu, lo, o));
-            hi = fmax(hi, __shfl_xor_sync(0xffffffffu, hi, o));
-        }
-        if ((threadIdx.x & 31) == 0) { slo[threadIdx.x >> 5] = lo; shi[threadIdx.x >> 5] = hi; }
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            for (int w = 1; w < (int)(blockDim.x >> 5); ++w) { lo = fmin(lo, slo[w]); hi = fmax(hi, shi[w]); }
-            lo = fmin(lo, slo[0]);
-            hi = fmax(hi, shi[0]);
-            lohi[2 * d] = lo;
-            lohi[2 * d + 1] = hi;
-        }
-        __syncthreads();
-    }
+// Order-preserving map of a (not NaN) double to an unsigned key and back:
+// min and max of the keys are the min and max of the values, in integer
+// instructions (the FP64 pipe is narrow on GB300).
+__device__ __forceinline__ unsigned long long ord_key(double x) {
+    const unsigned long long u = f64_bits(x);
+    return (u >> 63) ? ~u : (u | 0x8000000000000000ull);
+}
+__device__ __forceinline__ double ord_val(unsigned long long k) {
+    return f64_from_bits((k >> 63) ? (k & 0x7fffffffffffffffull) : ~k);
 }
 
-__global__ void k_quantize(const double *x, int64_t n, int dim, const double *lohi, int32_t *q,
-                           uint64_t *code) {
+// Bounding box of the points: keys[d] = min key, keys[dim + d] = max key of
+// coordinate d (keys preset to all ones / zero); flags non-finite values.
+__global__ void k_bbox(const double *x, int64_t n, int dim, unsigned long long *keys,
+                       unsigned *status) {
+    bool bad = false;
+    for (int d = 0; d < dim; ++d) {
+        unsigned long long lo = ~0ull, hi = 0ull;
+        for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+             i += (int64_t)gridDim.x * blockDim.x) {
+            const double v = x[i * dim + d];
+            bad |= ((f64_bits(v) >> 52) & 0x7ffull) == 0x7ffull;   // inf or NaN
+            const unsigned long long k = ord_key(v);
+            lo = k < lo ? k : lo;
+            hi = k > hi ? k : hi;
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            const unsigned long long a = __shfl_xor_sync(0xffffffffu, lo, o);
+            const unsigned long long b = __shfl_xor_sync(0xffffffffu, hi, o);
+            lo = a < lo ? a : lo;
+            hi = b > hi ? b : hi;
+        }
+        if ((threadIdx.x & 31) == 0) {
+            atomicMin(&keys[d], lo);
+            atomicMax(&keys[dim + d], hi);
+        }
+    }
+    if (bad) atomicOr(status, ST_NONFINITE);
+}
+
+__global__ void k_quantize(const double *x, int64_t n, int dim, const unsigned long long *keys,
+                           int32_t *q, uint64_t *code) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x) {
         uint32_t qq[3] = {0, 0, 0};
         for (int d = 0; d < dim; ++d) {
-            double lo = lohi[2 * d], hi = lohi[2 * d + 1];
+            const double lo = ord_val(keys[d]), hi = ord_val(keys[dim + d]);
             double span = __dsub_rn(hi, lo);
             double scale = span > 0.0 ? __ddiv_rn((double)QMAX, span) : 0.0;
             double f = floor(__dmul_rn(__dsub_rn(x[i * dim + d], lo), scale));
@@ -235,70 +246,157 @@ __global__ void k_one_cluster(const int32_t *act, int64_t s, int32_t *members, i
 // sum_u min(e_u, L) >= target and then decrementing the first
 // (sum - target) clusters (ascending u) that sit at L.  out[0] = total,
 // out[1] = 1 if no cluster can rotate (the caller then uses one cluster).
-__global__ void k_schedule(const int64_t *coff, int64_t mm, int64_t s, int64_t core, double eta,
-                           int64_t *e, int64_t *roff, int64_t *out) {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
-    int64_t total = 0, emax = 0;
-    for (int64_t u = 0; u < mm; ++u) {
-        int64_t c = coff[u + 1] - coff[u];
-        int64_t v = (int64_t)floor(__dmul_rn(eta, (double)c));
-        e[u] = v;
-        total += v;
-        emax = v > emax ? v : emax;
+// Block-wide reductions and exclusive scan of int64 (every thread gets the
+// result); red holds one slot per warp plus one.
+template <bool MAX>
+__device__ int64_t block_reduce_i64(int64_t v, int64_t *red) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+    for (int o = 16; o > 0; o >>= 1) {
+        const int64_t x = __shfl_xor_sync(0xffffffffu, v, o);
+        v = MAX ? (x > v ? x : v) : v + x;
     }
-    int64_t target = s - core;
-    if (total > target) {
-        int64_t lo = 0, hi = emax;  // smallest L with f(L) >= target
-        while (lo < hi) {
-            int64_t mid = (lo + hi) / 2, f = 0;
-            for (int64_t u = 0; u < mm; ++u) f += e[u] < mid ? e[u] : mid;
-            if (f >= target) hi = mid; else lo = mid + 1;
+    if (lane == 0) red[w] = v;
+    __syncthreads();
+    if (w == 0) {
+        v = lane < nw ? red[lane] : 0;
+        for (int o = 16; o > 0; o >>= 1) {
+            const int64_t x = __shfl_xor_sync(0xffffffffu, v, o);
+            v = MAX ? (x > v ? x : v) : v + x;
         }
-        int64_t L = lo, f = 0;
-        for (int64_t u = 0; u < mm; ++u) {
-            if (e[u] > L) e[u] = L;
-            f += e[u];
-        }
-        for (int64_t u = 0; u < mm && f > target; ++u)
-            if (e[u] == L) { e[u] -= 1; --f; }
-        total = f;
+        if (lane == 0) red[32] = v;
     }
-    out[1] = 0;
-    int64_t cmax = 0, sq = 0;
-    for (int64_t u = 0; u < mm; ++u) {
+    __syncthreads();
+    v = red[32];
+    __syncthreads();
+    return v;
+}
+
+__device__ int64_t block_exscan_i64(int64_t v, int64_t *red) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+    int64_t inc = v;
+    for (int o = 1; o < 32; o <<= 1) {
+        const int64_t x = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += x;
+    }
+    if (lane == 31) red[w] = inc;
+    __syncthreads();
+    if (w == 0) {
+        int64_t t = lane < nw ? red[lane] : 0, ti = t;
+        for (int o = 1; o < 32; o <<= 1) {
+            const int64_t x = __shfl_up_sync(0xffffffffu, ti, o);
+            if (lane >= o) ti += x;
+        }
+        if (lane < nw) red[lane] = ti - t;     // exclusive warp offsets
+    }
+    __syncthreads();
+    const int64_t r = red[w] + inc - v;
+    __syncthreads();
+    return r;
+}
+
+constexpr int SCHED_THREADS = 1024;
+
+// Rotations per cluster for one stage (one block; thread t owns the
+// contiguous clusters [t * chunk, (t + 1) * chunk)): e_u = floor(eta c_u),
+// capped when the total would take the active set below the core size (the
+// largest cap L keeping the total >= s - core, then the surplus taken one by
+// one from the first clusters at the cap, in cluster order); a single
+// cluster of the whole stage when no cluster can rotate.  Writes e, roff
+// (exclusive scan of e) and out = [total, one-cluster fallback, largest
+// cluster, sum of squared cluster sizes].
+__global__ void __launch_bounds__(SCHED_THREADS)
+k_schedule(const int64_t *coff, int64_t mm_host, const int64_t *mm_dev, int64_t s, int64_t core,
+           double eta, int64_t *e, int64_t *roff, int64_t *out) {
+    __shared__ int64_t red[33];
+    const int64_t mm = mm_dev ? *mm_dev : mm_host;
+    if (threadIdx.x == 0) out[4] = mm;
+    const int64_t chunk = (mm + SCHED_THREADS - 1) / SCHED_THREADS;
+    const int64_t u0 = threadIdx.x * chunk, u1 = u0 + chunk < mm ? u0 + chunk : mm;
+    int64_t tot = 0, emx = 0, cmx = 0, sq = 0;
+    for (int64_t u = u0; u < u1; ++u) {
         const int64_t c = coff[u + 1] - coff[u];
-        cmax = c > cmax ? c : cmax;
+        const int64_t v = (int64_t)floor(__dmul_rn(eta, (double)c));
+        e[u] = v;
+        tot += v;
+        emx = v > emx ? v : emx;
+        cmx = c > cmx ? c : cmx;
         sq += c * c;
     }
-    out[2] = cmax;
-    out[3] = sq;
-    if (total == 0) {
-        int64_t ee = (int64_t)floor(__dmul_rn(eta, (double)s));
-        if (ee > target) ee = target;
-        if (ee < 1) ee = 1;
-        out[1] = 1;
-        total = ee;
-        e[0] = ee;
-        out[2] = s;
-        out[3] = s * s;
+    int64_t total = block_reduce_i64<false>(tot, red);
+    const int64_t emax = block_reduce_i64<true>(emx, red);
+    const int64_t cmax = block_reduce_i64<true>(cmx, red);
+    const int64_t sqs = block_reduce_i64<false>(sq, red);
+    const int64_t target = s - core;
+    if (total > target) {
+        int64_t lo = 0, hi = emax;   // smallest L with sum_u min(e_u, L) >= target
+        while (lo < hi) {
+            const int64_t mid = (lo + hi) / 2;
+            int64_t f = 0;
+            for (int64_t u = u0; u < u1; ++u) f += e[u] < mid ? e[u] : mid;
+            f = block_reduce_i64<false>(f, red);
+            if (f >= target) hi = mid; else lo = mid + 1;
+        }
+        const int64_t L = lo;
+        int64_t f = 0, atL = 0;
+        for (int64_t u = u0; u < u1; ++u) {
+            if (e[u] > L) e[u] = L;
+            f += e[u];
+            atL += e[u] == L;
+        }
+        f = block_reduce_i64<false>(f, red);
+        const int64_t before = block_exscan_i64(atL, red);   // clusters at L before mine
+        const int64_t excess = f - target;
+        int64_t rank = before;
+        for (int64_t u = u0; u < u1; ++u)
+            if (e[u] == L) {
+                if (rank < excess) e[u] -= 1;
+                ++rank;
+            }
+        total = f - (excess > 0 ? excess : 0);
     }
-    roff[0] = 0;
-    if (!out[1])
-        for (int64_t u = 0; u < mm; ++u) roff[u + 1] = roff[u] + e[u];
-    else
-        roff[1] = total;
-    out[0] = total;
+    if (total == 0) {
+        // every cluster too small to rotate: one cluster for the stage
+        if (threadIdx.x == 0) {
+            int64_t ee = (int64_t)floor(__dmul_rn(eta, (double)s));
+            if (ee > target) ee = target;
+            if (ee < 1) ee = 1;
+            e[0] = ee;
+            roff[0] = 0;
+            roff[1] = ee;
+            out[0] = ee;
+            out[1] = 1;
+            out[2] = s;
+            out[3] = s * s;
+        }
+        return;
+    }
+    int64_t mine = 0;
+    for (int64_t u = u0; u < u1; ++u) mine += e[u];
+    int64_t acc = block_exscan_i64(mine, red);
+    if (threadIdx.x == 0) roff[0] = 0;
+    for (int64_t u = u0; u < u1; ++u) {
+        acc += e[u];
+        roff[u + 1] = acc;
+    }
+    if (threadIdx.x == 0) {
+        out[0] = total;
+        out[1] = 0;
+        out[2] = cmax;
+        out[3] = sqs;
+    }
 }
 
 }  // namespace
 
 pmmf_status quantize_points(const double *coords, int64_t n, int dim, int32_t *q, uint64_t *code,
                             unsigned *status, cudaStream_t st) {
-    DBuf<double> lohi;
-    PMMF_TRY(lohi.alloc(2 * dim, st));
-    k_bbox<<<1, 1024, 0, st>>>(coords, n, dim, lohi.p, status);
+    DBuf<unsigned long long> keys;
+    PMMF_TRY(keys.alloc(2 * dim, st));
+    PMMF_CUDA_TRY(cudaMemsetAsync(keys.p, 0xFF, sizeof(unsigned long long) * (size_t)dim, st));
+    PMMF_CUDA_TRY(cudaMemsetAsync(keys.p + dim, 0, sizeof(unsigned long long) * (size_t)dim, st));
+    k_bbox<<<grid_for(n, 256), 256, 0, st>>>(coords, n, dim, keys.p, status);
     PMMF_TRY(launched("bbox"));
-    k_quantize<<<grid_for(n, 256), 256, 0, st>>>(coords, n, dim, lohi.p, q, code);
+    k_quantize<<<grid_for(n, 256), 256, 0, st>>>(coords, n, dim, keys.p, q, code);
     return launched("quantize");
 }
 
@@ -399,33 +497,34 @@ pmmf_status partition_stage(const PartitionIn &in, int64_t m, int iters, StageCl
     k_nonempty<<<grid_for(m, 256), 256, 0, st>>>(cnt.p, m, nflag.p);
     PMMF_TRY(launched("nonempty"));
     PMMF_TRY(scan_i32_to_i64(nflag.p, ord.p, m, st));
-    int64_t mm = 0;
-    PMMF_CUDA_TRY(cudaMemcpyAsync(&mm, ord.p + m, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
-    PMMF_CUDA_TRY(cudaStreamSynchronize(st));
-    PMMF_TRY(size.alloc(mm + 1, st));
+    // the nonempty count stays on the device (read with the schedule); the
+    // arrays are sized for all m labels, the empty ones last with size 0
+    PMMF_TRY(out.count_d.alloc(1, st));
+    PMMF_CUDA_TRY(cudaMemcpyAsync(out.count_d.p, ord.p + m, sizeof(int64_t), cudaMemcpyDeviceToDevice, st));
+    PMMF_TRY(size.zeros(m + 1, st));
     k_cluster_sizes<<<grid_for(m, 256), 256, 0, st>>>(cnt.p, m, ord.p, size.p);
     PMMF_TRY(launched("cluster_sizes"));
-    PMMF_TRY(out.coff.alloc(mm + 1, st));
-    PMMF_TRY(scan_i64(size.p, out.coff.p, mm, st));
+    PMMF_TRY(out.coff.alloc(m + 1, st));
+    PMMF_TRY(scan_i64(size.p, out.coff.p, m, st));
     PMMF_TRY(perm.alloc(s, st));
     PMMF_TRY(stable_sort_by_key((const uint32_t *)label.p, s, m, perm.p, st));
     k_members<<<grid_for(s, 256), 256, 0, st>>>(in.act, label.p, perm.p, s, ord.p, out.coff.p,
                                                  out.members.p, in.cl, in.loc);
     PMMF_TRY(launched("members"));
-    out.m = mm;
+    out.m = m;
     return PMMF_OK;
 }
 
-pmmf_status schedule_stage(const int64_t *coff, int64_t mm, int64_t s, int64_t core, double eta,
-                           DBuf<int64_t> &e, DBuf<int64_t> &roff, int64_t *host_out,
-                           cudaStream_t st) {
+pmmf_status schedule_stage(const int64_t *coff, int64_t mm, const int64_t *mm_dev, int64_t s,
+                           int64_t core, double eta, DBuf<int64_t> &e, DBuf<int64_t> &roff,
+                           int64_t *host_out, cudaStream_t st) {
     PMMF_TRY(e.alloc(mm > 1 ? mm : 1, st));
     PMMF_TRY(roff.alloc(mm + 1 > 2 ? mm + 1 : 2, st));
     DBuf<int64_t> out;
-    PMMF_TRY(out.alloc(4, st));
-    k_schedule<<<1, 32, 0, st>>>(coff, mm, s, core, eta, e.p, roff.p, out.p);
+    PMMF_TRY(out.alloc(5, st));
+    k_schedule<<<1, SCHED_THREADS, 0, st>>>(coff, mm, mm_dev, s, core, eta, e.p, roff.p, out.p);
     PMMF_TRY(launched("schedule"));
-    PMMF_CUDA_TRY(cudaMemcpyAsync(host_out, out.p, 4 * sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+    PMMF_CUDA_TRY(cudaMemcpyAsync(host_out, out.p, 5 * sizeof(int64_t), cudaMemcpyDeviceToHost, st));
     PMMF_CUDA_TRY(cudaStreamSynchronize(st));
     return PMMF_OK;
 }

@@ -18,9 +18,11 @@ struct PartitionIn {
 };
 
 struct StageClusters {
-    int64_t m = 0;
+    int64_t m = 0;            // clusters (an upper bound while count_d is set)
     DBuf<int64_t> coff;       // m + 1
     DBuf<int32_t> members;    // s, cluster by cluster, ascending global id
+    DBuf<int64_t> count_d;    // exact cluster count on the device (k-means),
+                              // read with the stage schedule
 };
 
 // A CSR block over the active rows: row r is global id act[r].
@@ -56,12 +58,13 @@ pmmf_status partition_stage(const PartitionIn &in, int64_t m, int iters, StageCl
                             cudaStream_t st);
 pmmf_status one_cluster(const int32_t *act, int64_t s, StageClusters &out, int32_t *cl,
                         int32_t *loc, cudaStream_t st);
-// host_out[4]: total rotations, one-cluster fallback flag, largest cluster,
+// host_out[5]: total rotations, one-cluster fallback flag, largest cluster,
 // sum of squared cluster sizes (the two last for the fallback's one cluster
-// when the flag is set).
-pmmf_status schedule_stage(const int64_t *coff, int64_t mm, int64_t s, int64_t core, double eta,
-                           DBuf<int64_t> &e, DBuf<int64_t> &roff, int64_t *host_out,
-                           cudaStream_t st);
+// when the flag is set), number of clusters.  mm_dev (may be NULL): the exact
+// cluster count on the device, mm then an upper bound.
+pmmf_status schedule_stage(const int64_t *coff, int64_t mm, const int64_t *mm_dev, int64_t s,
+                           int64_t core, double eta, DBuf<int64_t> &e, DBuf<int64_t> &roff,
+                           int64_t *host_out, cudaStream_t st);
 
 // Gram G^u and symmetric local block M^u of every cluster (dense c_u x c_u,
 // row-major at goff[u]) and the rotation search of Algorithm 2.
