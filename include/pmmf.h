@@ -100,6 +100,14 @@ typedef struct {
  *                 that the clustering step (Algorithm 1, "cluster") groups by
  *                 k-means; NULL -> one cluster per stage.
  *   coords_location  PMMF_HOST or PMMF_DEVICE for coords.
+ *   labels        optional given clusters for stage 1: labels[x] in
+ *                 [0, num_labels) for every coordinate x (e.g. the bricks of
+ *                 a structured grid); clusters are the nonempty labels in
+ *                 ascending order, members ascending.  Later stages use the
+ *                 clustering rule.  NULL -> the clustering rule at stage 1
+ *                 too.  A label outside [0, num_labels) -> INVALID_ARG.
+ *   labels_location  PMMF_HOST or PMMF_DEVICE for labels.
+ *   num_labels    number of label values (>= 1 when labels is set).
  *   record_stages nonzero keeps a device copy of every stage's compacted
  *                 A_p (for inspection with pmmf_stage_matrix).
  *   precision     PMMF_PREC_FP64 (0): every Gram entry in FP64 (the oracle's
@@ -127,6 +135,9 @@ typedef struct {
     int coords_location;
     int record_stages;
     int precision;
+    const int32_t *labels;
+    int labels_location;
+    int64_t num_labels;
 } pmmf_params;
 
 enum { PMMF_PREC_FP64 = 0, PMMF_PREC_TF32 = 1, PMMF_PREC_BF16 = 2 };

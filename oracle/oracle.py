@@ -107,7 +107,7 @@ def _p(a: np.ndarray):
 class _Params(C.Structure):
     _fields_ = [("k", C.c_int), ("eta", C.c_double), ("cluster_size", C.c_int),
                 ("core_size", C.c_int), ("seed", C.c_uint64), ("max_stages", C.c_int),
-                ("lloyd_iters", C.c_int)]
+                ("lloyd_iters", C.c_int), ("labels", C.c_void_p), ("num_labels", C.c_int64)]
 
 
 @dataclass
@@ -210,8 +210,9 @@ class Factorization:
 
 
 def factor(n, rowptr, col, val, coords=None, *, k=2, eta=0.5, cluster_size=256, core_size=16,
-           seed=0, max_stages=0, lloyd_iters=10, record=False) -> Factorization:
-    """Run the oracle's pMMF (Algorithm 1) and copy every result out."""
+           seed=0, max_stages=0, lloyd_iters=10, record=False, labels=None) -> Factorization:
+    """Run the oracle's pMMF (Algorithm 1) and copy every result out.  labels:
+    optional stage-1 cluster label per coordinate (0 .. max), e.g. grid bricks."""
     L = lib()
     rowptr = np.ascontiguousarray(rowptr, dtype=np.int64)
     col = np.ascontiguousarray(col, dtype=np.int32)
@@ -222,7 +223,12 @@ def factor(n, rowptr, col, val, coords=None, *, k=2, eta=0.5, cluster_size=256, 
         coords = np.ascontiguousarray(coords, dtype=np.float64)
         dim = coords.shape[1]
         cp = _p(coords)
-    prm = _Params(k, eta, cluster_size, core_size, seed, max_stages, lloyd_iters)
+    lab = None
+    if labels is not None:
+        lab = np.ascontiguousarray(labels, dtype=np.int32)
+        assert lab.shape == (n,)
+    prm = _Params(k, eta, cluster_size, core_size, seed, max_stages, lloyd_iters,
+                  None if lab is None else _p(lab), 0 if lab is None else int(lab.max()) + 1)
     h = L.or_factor(n, _p(rowptr), _p(col), _p(val), cp, dim, C.byref(prm), 1 if record else 0)
     if not h:
         raise MemoryError("oracle allocation failed")

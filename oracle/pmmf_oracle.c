@@ -618,7 +618,7 @@ or_fact *or_factor(int64_t n, const int64_t *rowptr, const int32_t *col, const d
     f->K = prm->k;
     if (n < 1 || prm->k < 2 || prm->k > KMAX || !(prm->eta > 0.0 && prm->eta < 1.0) ||
         prm->cluster_size < prm->k || prm->core_size < 1 || prm->core_size > n ||
-        (coords && (dim < 1 || dim > 3))) {
+        (coords && (dim < 1 || dim > 3)) || (prm->labels && prm->num_labels < 1)) {
         f->status = OR_ERR_INVALID_ARG;
         return f;
     }
@@ -670,10 +670,18 @@ or_fact *or_factor(int64_t n, const int64_t *rowptr, const int32_t *col, const d
         int64_t m = (s + prm->cluster_size / 2) / prm->cluster_size;
         if (m < 1) m = 1;
         if (!coords) m = 1;
+        if (p == 1 && prm->labels) m = prm->num_labels;
         int32_t *label = (int32_t *)calloc((size_t)s, sizeof(int32_t));
         int64_t *e = NULL;
         if (!label) goto oom;
-        if (m > 1) {
+        if (p == 1 && prm->labels) {
+            /* given stage-1 clusters (R10: grid bricks for structured grids) */
+            for (int64_t r = 0; r < s; ++r) {
+                int32_t l = prm->labels[act[r]];
+                if (l < 0 || l >= m) { free(label); f->status = OR_ERR_INVALID_ARG; goto done; }
+                label[r] = l;
+            }
+        } else if (m > 1) {
             int ps = partition_q(q, dim, s, act, m, prm->lloyd_iters, label);
             if (ps) { free(label); goto oom; }
         }

@@ -44,6 +44,9 @@ typedef struct {
     uint64_t seed;      /* seed of the counter-based random pick of Alg. 2 */
     int max_stages;     /* <= 0: no limit */
     int lloyd_iters;    /* Lloyd iterations of the clustering step */
+    const int32_t *labels;   /* optional stage-1 clusters: label per coordinate in
+                                [0, num_labels) (e.g. grid bricks), or NULL */
+    int64_t num_labels;
 } or_params;
 
 typedef struct or_fact or_fact;

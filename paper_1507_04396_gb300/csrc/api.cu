@@ -105,6 +105,21 @@ pmmf_status to_device(const T *src, int64_t count, int location, DBuf<T> &dst, c
     return PMMF_OK;
 }
 
+// Given stage-1 clusters on the device, checked (one synchronization).
+pmmf_status stage1_labels(const pmmf_params *prm, int64_t n, DBuf<int32_t> &tmp,
+                          const int32_t *&dl, unsigned *status, cudaStream_t st) {
+    dl = nullptr;
+    if (!prm->labels) return PMMF_OK;
+    PMMF_TRY(to_device(prm->labels, n, prm->labels_location, tmp, dl, st));
+    PMMF_CUDA_TRY(cudaMemsetAsync(status, 0, sizeof(unsigned), st));
+    PMMF_TRY(check_labels(dl, n, prm->num_labels, status, st));
+    unsigned hs = 0;
+    PMMF_CUDA_TRY(cudaMemcpyAsync(&hs, status, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
+    PMMF_CUDA_TRY(cudaStreamSynchronize(st));
+    if (hs & ST_BAD_LABEL) return fail(PMMF_ERR_INVALID_ARG, "a stage-1 label is outside [0, num_labels)");
+    return PMMF_OK;
+}
+
 // Device CSR of A with exact zeros dropped, validated (structure, finite,
 // exactly symmetric).
 pmmf_status stage_input(const pmmf_matrix *A, Csr &out, unsigned *status_d, cudaStream_t st) {
@@ -184,6 +199,10 @@ pmmf_status check_params(const pmmf_matrix *A, const pmmf_params *p) {
         return fail(PMMF_ERR_INVALID_ARG, "coord_dim must be 1, 2 or 3");
     if (p->coords && p->coords_location != PMMF_HOST && p->coords_location != PMMF_DEVICE)
         return fail(PMMF_ERR_INVALID_ARG, "bad coords location");
+    if (p->labels && (p->num_labels < 1 || p->num_labels > INT32_MAX))
+        return fail(PMMF_ERR_INVALID_ARG, "num_labels must be in [1, 2^31)");
+    if (p->labels && p->labels_location != PMMF_HOST && p->labels_location != PMMF_DEVICE)
+        return fail(PMMF_ERR_INVALID_ARG, "bad labels location");
     return PMMF_OK;
 }
 
@@ -251,6 +270,9 @@ pmmf_status factor_impl(const pmmf_matrix *A, const pmmf_params *prm, pmmf_handl
         PMMF_CUDA_TRY(cudaStreamSynchronize(st));
         if (hs & ST_NONFINITE) return fail(PMMF_ERR_INVALID_ARG, "coords hold NaN or Inf");
     }
+    DBuf<int32_t> tlab;
+    const int32_t *dlab = nullptr;
+    PMMF_TRY(stage1_labels(prm, n, tlab, dlab, status.p, st));
 
     DBuf<int32_t> act, pos, cl, loc, elimflag;
     DBuf<double> contribs;
@@ -276,7 +298,7 @@ pmmf_status factor_impl(const pmmf_matrix *A, const pmmf_params *prm, pmmf_handl
         S.s = s;
         int64_t m = (s + prm->cluster_size / 2) / prm->cluster_size;
         if (m < 1 || !geo) m = 1;
-        if (m > 1) {
+        if (m > 1 || (p == 1 && dlab)) {
             PartitionIn in;
             in.n = n;
             in.s = s;
@@ -287,7 +309,8 @@ pmmf_status factor_impl(const pmmf_matrix *A, const pmmf_params *prm, pmmf_handl
             in.act = act.p;
             in.cl = cl.p;
             in.loc = loc.p;
-            PMMF_TRY(partition_stage(in, m, iters, S.cls, st));
+            if (p == 1 && dlab) PMMF_TRY(partition_from_labels(in, dlab, prm->num_labels, S.cls, st));
+            else PMMF_TRY(partition_stage(in, m, iters, S.cls, st));
         } else {
             PMMF_TRY(one_cluster(act.p, s, S.cls, cl.p, loc.p, st));
         }
@@ -446,6 +469,9 @@ pmmf_status factor_dense_impl(const pmmf_matrix *A, const pmmf_params *prm, pmmf
         PMMF_CUDA_TRY(cudaStreamSynchronize(st));
         if (hs & ST_NONFINITE) return fail(PMMF_ERR_INVALID_ARG, "coords hold NaN or Inf");
     }
+    DBuf<int32_t> tlab;
+    const int32_t *dlab = nullptr;
+    PMMF_TRY(stage1_labels(prm, n, tlab, dlab, status.p, st));
     DBuf<int32_t> act, pos, cl, loc, elimflag;
     DBuf<double> contribs;
     PMMF_TRY(act.alloc(n, st));
@@ -468,7 +494,7 @@ pmmf_status factor_dense_impl(const pmmf_matrix *A, const pmmf_params *prm, pmmf
         S.s = s;
         int64_t m = (s + prm->cluster_size / 2) / prm->cluster_size;
         if (m < 1 || !geo) m = 1;
-        if (m > 1) {
+        if (m > 1 || (p == 1 && dlab)) {
             PartitionIn in;
             in.n = n;
             in.s = s;
@@ -479,7 +505,8 @@ pmmf_status factor_dense_impl(const pmmf_matrix *A, const pmmf_params *prm, pmmf
             in.act = act.p;
             in.cl = cl.p;
             in.loc = loc.p;
-            PMMF_TRY(partition_stage(in, m, iters, S.cls, st));
+            if (p == 1 && dlab) PMMF_TRY(partition_from_labels(in, dlab, prm->num_labels, S.cls, st));
+            else PMMF_TRY(partition_stage(in, m, iters, S.cls, st));
         } else {
             PMMF_TRY(one_cluster(act.p, s, S.cls, cl.p, loc.p, st));
         }

@@ -83,6 +83,7 @@ enum : unsigned {
     ST_NOT_SPD = 16u,
     ST_CLUSTER_TOO_BIG = 32u,
     ST_NOT_CONVERGED = 64u,
+    ST_BAD_LABEL = 128u,
 };
 
 // ---------------------------------------------------------------- rotations

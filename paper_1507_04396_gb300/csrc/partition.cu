@@ -400,6 +400,74 @@ pmmf_status quantize_points(const double *coords, int64_t n, int dim, int32_t *q
     return launched("quantize");
 }
 
+// Clusters from labels in [0, m) with their counts: the nonempty labels in
+// ascending order, members ascending by global id (R10's order).
+static pmmf_status clusters_from_labels(const PartitionIn &in, DBuf<int32_t> &label,
+                                        const unsigned long long *cnt, int64_t m,
+                                        StageClusters &out, cudaStream_t st) {
+    const int64_t s = in.s;
+    DBuf<int32_t> perm, nflag;
+    DBuf<int64_t> ord, size;
+    PMMF_TRY(nflag.alloc(m, st));
+    PMMF_TRY(ord.alloc(m + 1, st));
+    k_nonempty<<<grid_for(m, 256), 256, 0, st>>>(cnt, m, nflag.p);
+    PMMF_TRY(launched("nonempty"));
+    PMMF_TRY(scan_i32_to_i64(nflag.p, ord.p, m, st));
+    // the nonempty count stays on the device (read with the schedule); the
+    // arrays are sized for all m labels, the empty ones last with size 0
+    PMMF_TRY(out.count_d.alloc(1, st));
+    PMMF_CUDA_TRY(cudaMemcpyAsync(out.count_d.p, ord.p + m, sizeof(int64_t), cudaMemcpyDeviceToDevice, st));
+    PMMF_TRY(size.zeros(m + 1, st));
+    k_cluster_sizes<<<grid_for(m, 256), 256, 0, st>>>(cnt, m, ord.p, size.p);
+    PMMF_TRY(launched("cluster_sizes"));
+    PMMF_TRY(out.coff.alloc(m + 1, st));
+    PMMF_TRY(scan_i64(size.p, out.coff.p, m, st));
+    PMMF_TRY(perm.alloc(s, st));
+    PMMF_TRY(stable_sort_by_key((const uint32_t *)label.p, s, m, perm.p, st));
+    k_members<<<grid_for(s, 256), 256, 0, st>>>(in.act, label.p, perm.p, s, ord.p, out.coff.p,
+                                                 out.members.p, in.cl, in.loc);
+    PMMF_TRY(launched("members"));
+    out.m = m;
+    return PMMF_OK;
+}
+
+__global__ void k_check_labels(const int32_t *lab, int64_t n, int64_t m, unsigned *status) {
+    bool bad = false;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        bad |= lab[i] < 0 || lab[i] >= m;
+    if (bad) atomicOr(status, ST_BAD_LABEL);
+}
+
+__global__ void k_gather_labels(const int32_t *act, int64_t s, const int32_t *labels, int32_t *label,
+                                unsigned long long *cnt) {
+    for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < s;
+         r += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t l = labels[act[r]];
+        label[r] = l;
+        atomicAdd(&cnt[l], 1ull);
+    }
+}
+
+pmmf_status check_labels(const int32_t *labels, int64_t n, int64_t m, unsigned *status,
+                         cudaStream_t st) {
+    k_check_labels<<<grid_for(n, 256), 256, 0, st>>>(labels, n, m, status);
+    return launched("check_labels");
+}
+
+pmmf_status partition_from_labels(const PartitionIn &in, const int32_t *labels, int64_t m,
+                                  StageClusters &out, cudaStream_t st) {
+    const int64_t s = in.s;
+    PMMF_TRY(out.members.alloc(s, st));
+    DBuf<int32_t> label;
+    DBuf<unsigned long long> cnt;
+    PMMF_TRY(label.alloc(s, st));
+    PMMF_TRY(cnt.zeros(m, st));
+    k_gather_labels<<<grid_for(s, 256), 256, 0, st>>>(in.act, s, labels, label.p, cnt.p);
+    PMMF_TRY(launched("gather_labels"));
+    return clusters_from_labels(in, label, cnt.p, m, out, st);
+}
+
 pmmf_status partition_stage(const PartitionIn &in, int64_t m, int iters, StageClusters &out,
                             cudaStream_t st) {
     const int64_t s = in.s;
@@ -414,8 +482,8 @@ pmmf_status partition_stage(const PartitionIn &in, int64_t m, int iters, StageCl
         return PMMF_OK;
     }
     // active points in Morton order
-    DBuf<int32_t> flag, amorder, label, perm, cen, nflag;
-    DBuf<int64_t> ex, ord, size;
+    DBuf<int32_t> flag, amorder, label, cen;
+    DBuf<int64_t> ex;
     DBuf<unsigned long long> sum, cnt;
     PMMF_TRY(flag.alloc(in.n, st));
     PMMF_TRY(ex.alloc(in.n + 1, st));
@@ -491,28 +559,7 @@ pmmf_status partition_stage(const PartitionIn &in, int64_t m, int iters, StageCl
         }
     }
     }
-    // clusters: nonempty labels in order; members ascending by global id
-    PMMF_TRY(nflag.alloc(m, st));
-    PMMF_TRY(ord.alloc(m + 1, st));
-    k_nonempty<<<grid_for(m, 256), 256, 0, st>>>(cnt.p, m, nflag.p);
-    PMMF_TRY(launched("nonempty"));
-    PMMF_TRY(scan_i32_to_i64(nflag.p, ord.p, m, st));
-    // the nonempty count stays on the device (read with the schedule); the
-    // arrays are sized for all m labels, the empty ones last with size 0
-    PMMF_TRY(out.count_d.alloc(1, st));
-    PMMF_CUDA_TRY(cudaMemcpyAsync(out.count_d.p, ord.p + m, sizeof(int64_t), cudaMemcpyDeviceToDevice, st));
-    PMMF_TRY(size.zeros(m + 1, st));
-    k_cluster_sizes<<<grid_for(m, 256), 256, 0, st>>>(cnt.p, m, ord.p, size.p);
-    PMMF_TRY(launched("cluster_sizes"));
-    PMMF_TRY(out.coff.alloc(m + 1, st));
-    PMMF_TRY(scan_i64(size.p, out.coff.p, m, st));
-    PMMF_TRY(perm.alloc(s, st));
-    PMMF_TRY(stable_sort_by_key((const uint32_t *)label.p, s, m, perm.p, st));
-    k_members<<<grid_for(s, 256), 256, 0, st>>>(in.act, label.p, perm.p, s, ord.p, out.coff.p,
-                                                 out.members.p, in.cl, in.loc);
-    PMMF_TRY(launched("members"));
-    out.m = m;
-    return PMMF_OK;
+    return clusters_from_labels(in, label, cnt.p, m, out, st);
 }
 
 pmmf_status schedule_stage(const int64_t *coff, int64_t mm, const int64_t *mm_dev, int64_t s,

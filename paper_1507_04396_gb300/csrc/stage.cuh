@@ -58,6 +58,13 @@ pmmf_status partition_stage(const PartitionIn &in, int64_t m, int iters, StageCl
                             cudaStream_t st);
 pmmf_status one_cluster(const int32_t *act, int64_t s, StageClusters &out, int32_t *cl,
                         int32_t *loc, cudaStream_t st);
+// Given clusters (labels[x] in [0, m) for every coordinate x): the nonempty
+// labels in ascending order, members ascending.  check_labels sets
+// ST_BAD_LABEL for a label outside [0, m).
+pmmf_status check_labels(const int32_t *labels, int64_t n, int64_t m, unsigned *status,
+                         cudaStream_t st);
+pmmf_status partition_from_labels(const PartitionIn &in, const int32_t *labels, int64_t m,
+                                  StageClusters &out, cudaStream_t st);
 // host_out[5]: total rotations, one-cluster fallback flag, largest cluster,
 // sum of squared cluster sizes (the two last for the fallback's one cluster
 // when the flag is set), number of clusters.  mm_dev (may be NULL): the exact

@@ -18,6 +18,7 @@ Workloads (the paper measures on graph Laplacians and kernel matrices, §3,
 * ``knn_laplacian``      Laplacian + 1e-3 I of a symmetrised k-nearest-
                          neighbour graph on uniform points in the unit square
 * ``poisson3d``          7-point finite-volume variable-coefficient Poisson
+* ``grid_bricks``        stage-1 cluster labels of a structured grid by bricks
 * ``rbf_mixture``        dense Gaussian RBF kernel on a 3-D Gaussian mixture
 * ``er_laplacian``       Laplacian + 1e-3 I of an Erdos-Renyi graph
 * ``block_pairs``        direct sum of random SPD k x k blocks under a random
@@ -151,6 +152,16 @@ def poisson3d(nx: int = 128, sigma: float = 1.0, seed: int = 4) -> SymCSR:
     g = (np.stack(np.meshgrid(np.arange(nx), np.arange(nx), np.arange(nx), indexing="ij"),
                   axis=-1).reshape(n, 3) + 0.5)
     return _from_scipy(m, coords=g.astype(np.float64), name=f"poisson3d(nx={nx},seed={seed})")
+
+
+def grid_bricks(nx: int, ny: int, nz: int, bx: int, by: int, bz: int) -> np.ndarray:
+    """Label of each cell of an nx x ny x nz grid (cell id (x * ny + y) * nz + z,
+    the poisson3d order) by its bx x by x bz brick, bricks numbered in
+    lexicographic (x, y, z) brick order."""
+    x, y, z = np.meshgrid(np.arange(nx), np.arange(ny), np.arange(nz), indexing="ij")
+    nby, nbz = -(-ny // by), -(-nz // bz)
+    lab = ((x // bx) * nby + (y // by)) * nbz + (z // bz)
+    return lab.reshape(-1).astype(np.int32)
 
 
 def rbf_mixture(n: int = 16384, components: int = 20, seed: int = 2) -> SymCSR:

@@ -50,7 +50,8 @@ class Params(C.Structure):
                 ("core_size", C.c_int), ("seed", C.c_uint64), ("max_stages", C.c_int),
                 ("lloyd_iters", C.c_int), ("coords", C.c_void_p), ("coord_dim", C.c_int),
                 ("coords_location", C.c_int), ("record_stages", C.c_int),
-                ("precision", C.c_int)]
+                ("precision", C.c_int), ("labels", C.c_void_p), ("labels_location", C.c_int),
+                ("num_labels", C.c_int64)]
 
 
 class Info(C.Structure):
@@ -488,9 +489,11 @@ class Factorization:
 
 def factor(a, *, k=2, eta=0.5, cluster_size=256, core_size=16, seed=0, max_stages=0,
            lloyd_iters=10, coords="auto", record_stages=False, precision=PREC_FP64,
-           stream=None) -> Factorization:
+           labels=None, stream=None) -> Factorization:
     """Factor a symmetric matrix (SymCSR-like object with numpy or torch arrays, or a
-    dense 2-D array/tensor).  coords='auto' uses ``a.coords`` when present."""
+    dense 2-D array/tensor).  coords='auto' uses ``a.coords`` when present.
+    labels: optional stage-1 cluster label per coordinate (int32, numpy or
+    torch), e.g. grid bricks; num_labels is taken as labels.max() + 1."""
     m, keep = make_matrix(a)
     if isinstance(coords, str):
         coords = getattr(a, "coords", None)
@@ -500,8 +503,20 @@ def factor(a, *, k=2, eta=0.5, cluster_size=256, core_size=16, seed=0, max_stage
             coords = np.ascontiguousarray(coords, dtype=np.float64)
         keep.append(coords)
         cp, cd, cl = _ptr(coords), coords.shape[1], _loc(coords)
+    lp, ll, nl = None, HOST, 0
+    if labels is not None:
+        if not hasattr(labels, "data_ptr"):
+            labels = np.ascontiguousarray(labels, dtype=np.int32)
+            nl = int(labels.max()) + 1 if labels.size else 0
+        else:
+            import torch
+            if labels.dtype != torch.int32 or not labels.is_contiguous():
+                raise TypeError("labels must be a contiguous int32 tensor")
+            nl = int(labels.max().item()) + 1 if labels.numel() else 0
+        keep.append(labels)
+        lp, ll = _ptr(labels), _loc(labels)
     prm = Params(k, eta, cluster_size, core_size, seed, max_stages, lloyd_iters, cp, cd, cl,
-                 1 if record_stages else 0, precision)
+                 1 if record_stages else 0, precision, lp, ll, nl)
     h = pmmf_factor(m, prm, stream)
     return Factorization(h, k)
 

@@ -190,3 +190,38 @@ def test_allocation_failure_is_clean():
         r = subprocess.run([sys.executable, "-c", code], cwd=root, env=env, capture_output=True,
                            text=True, timeout=300)
         assert "STATUS 4" in r.stdout, r.stdout + r.stderr
+
+
+@gpu
+def test_given_stage1_bricks():
+    """Stage 1 from given clusters (8 x 8 x 4 grid bricks, the structured-grid
+    rule), k-means afterwards: bit-identical to the oracle with the same
+    labels, from host or device labels; a label out of range is rejected."""
+    import torch
+    a = I.poisson3d(16, seed=4)
+    lab = I.grid_bricks(16, 16, 16, 8, 8, 4)
+    kw = dict(k=2, eta=0.5, cluster_size=256, core_size=64, seed=4)
+    g, o = factor_both(a, labels=lab, **kw)
+    assert_same_factorization(g, o)
+    off, mem = g.clusters(0)
+    assert len(off) - 1 == 16
+    assert np.array_equal(mem[off[3]:off[4]], np.nonzero(lab == 3)[0])
+    pm = gpu_lib()
+    g2 = pm.factor(a, labels=torch.from_numpy(lab).cuda(), **kw)
+    for p in range(g.info().stages):
+        assert np.array_equal(g.rotations(p)[3], g2.rotations(p)[3])
+    bad = lab.copy()
+    bad[100] = 99
+    with pytest.raises(pm.PmmfError) as ei:
+        pm.pmmf_factor(*_params_with_labels(pm, a, bad, 16, kw))
+    assert ei.value.status == pm.ERR_INVALID_ARG
+
+
+def _params_with_labels(pm, a, lab, num, kw):
+    """Raw C-ABI arguments with num_labels fixed (the binding derives it)."""
+    m, keep = pm.make_matrix(a)
+    co = np.ascontiguousarray(a.coords)
+    prm = pm.Params(kw["k"], kw["eta"], kw["cluster_size"], kw["core_size"], kw["seed"], 0, 10,
+                    co.ctypes.data, 3, pm.HOST, 0, 0, lab.ctypes.data, pm.HOST, num)
+    _params_with_labels.keep = (keep, co, lab)
+    return m, prm

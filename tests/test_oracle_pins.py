@@ -401,3 +401,35 @@ def test_split_cg_matches_pcg_iterates_and_exact_split_takes_one_step():
     f0 = O.factor_csr(a, k=2, eta=0.5, cluster_size=27, core_size=a.n, seed=1)
     st, x, iters, rel = f0.pcg_sym(a, b, 1e-10, 10)
     assert st == 0 and (iters == 1).all() and (rel <= 1e-10).all()
+
+
+# ---------------------------------------------------------------- given stage-1 clusters
+
+def test_stage1_labels_reproduce_kmeans_and_bricks():
+    """R10: stage 1 may take given clusters (grid bricks for structured grids).
+    Labels equal to the k-means labels give the k-means factorization; brick
+    labels give stage-1 clusters that are exactly the bricks, in brick order,
+    members ascending."""
+    a = I.poisson3d(8, seed=3)
+    kw = dict(k=2, eta=0.5, cluster_size=32, core_size=24, seed=2)
+    f0 = O.factor_csr(a, **kw)
+    km = O.partition(a.coords, np.arange(a.n, dtype=np.int32), (a.n + 16) // 32)
+    f1 = O.factor_csr(a, labels=km, **kw)
+    assert f0.status == f1.status == 0
+    for s0, s1 in zip(f0.stages, f1.stages):
+        assert np.array_equal(s0.members, s1.members) and np.array_equal(s0.rot_idx, s1.rot_idx)
+    assert f0.error == f1.error
+    lab = I.grid_bricks(8, 8, 8, 4, 4, 2)
+    assert lab.max() == 2 * 2 * 4 - 1
+    fb = O.factor_csr(a, labels=lab, **kw)
+    assert fb.status == 0
+    st = fb.stages[0]
+    assert len(st.offsets) - 1 == 16
+    for u in range(16):
+        want = np.nonzero(lab == u)[0]
+        assert np.array_equal(st.members[st.offsets[u]:st.offsets[u + 1]], want)
+    x, y, z = np.unravel_index(st.members[st.offsets[5]:st.offsets[6]], (8, 8, 8))
+    assert (x // 4 == 0).all() and (y // 4 == 1).all() and (z // 2 == 1).all()   # brick (0, 1, 1)
+    bad = lab.copy()
+    bad[7] = -1
+    assert O.factor_csr(a, labels=bad, **kw).status == O.ERR_INVALID_ARG
