@@ -74,15 +74,20 @@ struct RowArgs {
 
 // Per-warp shared memory of the row kernel: the dense local vector (cmax
 // doubles, all zero between segments), its touched-position bitmask (one bit
-// per local index, an even number of words) and, for the output pass, the
-// row's kept entries.
+// per local index, an even number of words), the touched positions listed in
+// ascending order (cmax int32, even) and, for the output pass, the row's kept
+// entries.
 __host__ __device__ inline int64_t rows_mask_words(int64_t cmax) {
     const int64_t w = (cmax + 31) / 32;
     return w + (w & 1);
 }
 __host__ __device__ inline int64_t rows_per_warp(int64_t cmax, int64_t outcap, bool write2) {
-    return cmax + rows_mask_words(cmax) / 2 + (write2 ? outcap * 3 / 2 + 1 : 0);
+    return cmax + rows_mask_words(cmax) / 2 + (cmax + 1) / 2 + (write2 ? outcap * 3 / 2 + 1 : 0);
 }
+
+// Row entries a lane keeps in registers (rows up to 32 * ROW_CACHE entries
+// are read from global memory once; longer rows are re-read per segment).
+constexpr int ROW_CACHE = 2;
 
 template <int MODE>
 __global__ void k_rows(RowArgs a) {
@@ -94,7 +99,8 @@ __global__ void k_rows(RowArgs a) {
     double *dense = smem + per_warp * wib;
     uint32_t *tb = (uint32_t *)(dense + a.cmax);
     const int nwmax = (int)rows_mask_words(a.cmax);
-    int32_t *scol = (int32_t *)(tb + nwmax);
+    int32_t *plist = (int32_t *)(tb + nwmax);
+    int32_t *scol = plist + (a.cmax + (a.cmax & 1));
     double *sval = (double *)(scol + (a.outcap + (a.outcap & 1)));
     for (int64_t l = lane; l < a.cmax; l += 32) dense[l] = 0.0;
     for (int l = lane; l < nwmax; l += 32) tb[l] = 0u;
@@ -108,11 +114,34 @@ __global__ void k_rows(RowArgs a) {
         int nseg = 0;
         int prev = -1;
         double prow = 0.0;   // this row's residual terms (per-cluster accounting)
+        // the row's entries (cluster, local index, value) in registers
+        const bool cached = e1 - e0 <= 32 * ROW_CACHE;
+        int cu[ROW_CACHE], cloc[ROW_CACHE];
+        double cv[ROW_CACHE];
+#pragma unroll
+        for (int k = 0; k < ROW_CACHE; ++k) {
+            const int64_t q = e0 + lane + 32 * k;
+            cu[k] = INT_MAX;
+            cloc[k] = 0;
+            cv[k] = 0.0;
+            if (cached && q < e1) {
+                const int32_t g = a.ci[q];
+                cu[k] = a.cl[g];
+                cloc[k] = a.loc[g];
+                if (!COUNT) cv[k] = a.v[q];
+            }
+        }
         for (;;) {
             int mu = INT_MAX;
-            for (int64_t q = e0 + lane; q < e1; q += 32) {
-                int uq = a.cl[a.ci[q]];
-                if (uq > prev && uq < mu) mu = uq;
+            if (cached) {
+#pragma unroll
+                for (int k = 0; k < ROW_CACHE; ++k)
+                    if (cu[k] > prev && cu[k] < mu) mu = cu[k];
+            } else {
+                for (int64_t q = e0 + lane; q < e1; q += 32) {
+                    int uq = a.cl[a.ci[q]];
+                    if (uq > prev && uq < mu) mu = uq;
+                }
             }
             for (int o = 16; o > 0; o >>= 1) mu = min(mu, __shfl_xor_sync(0xffffffffu, mu, o));
             if (mu == INT_MAX) break;
@@ -120,12 +149,22 @@ __global__ void k_rows(RowArgs a) {
             const int64_t cb = a.coff[mu];
             const int c = (int)(a.coff[mu + 1] - cb);
             const int nw = (c + 31) / 32;
-            for (int64_t q = e0 + lane; q < e1; q += 32) {
-                int32_t g = a.ci[q];
-                if (a.cl[g] == mu) {
-                    const int l = a.loc[g];
-                    if (!COUNT) dense[l] = a.v[q];
-                    atomicOr(&tb[l >> 5], 1u << (l & 31));
+            if (cached) {
+#pragma unroll
+                for (int k = 0; k < ROW_CACHE; ++k)
+                    if (cu[k] == mu) {
+                        const int l = cloc[k];
+                        if (!COUNT) dense[l] = cv[k];
+                        atomicOr(&tb[l >> 5], 1u << (l & 31));
+                    }
+            } else {
+                for (int64_t q = e0 + lane; q < e1; q += 32) {
+                    int32_t g = a.ci[q];
+                    if (a.cl[g] == mu) {
+                        const int l = a.loc[g];
+                        if (!COUNT) dense[l] = a.v[q];
+                        atomicOr(&tb[l >> 5], 1u << (l & 31));
+                    }
                 }
             }
             __syncwarp();
@@ -211,47 +250,48 @@ __global__ void k_rows(RowArgs a) {
                 __syncwarp();
             }
             }
-            // emit the touched positions in ascending order (lane = word,
-            // bits ascending inside a word) and reset them
+            // emit: list the touched positions in ascending order (lane =
+            // word) and reset the mask, then one lane per position, so the
+            // dependent loads and atomics of 32 positions overlap
+            int ntouch = 0;
             for (int w0 = 0; w0 < nw; w0 += 32) {
                 const int wi = w0 + lane;
                 const uint32_t bits = wi < nw ? tb[wi] : 0u;
-                int kept = 0;
-                if (MODE == P2_WRITE) {
-                    // pass 1: how many entries of this word are kept
-                    for (uint32_t m = bits; m; m &= m - 1) {
-                        const int l = wi * 32 + __ffs(m) - 1;
-                        const double x = dense[l];
-                        if (!nonzero_bits(x) || yelim) continue;
-                        const int32_t g = a.members[cb + l];
-                        if (a.elimflag[g] != a.stage) ++kept;
-                    }
-                }
-                int off = kept;   // inclusive scan over lanes
+                if (wi < nw) tb[wi] = 0u;
+                const int cntw = __popc(bits);
+                int inc = cntw;   // inclusive scan over lanes
                 for (int o = 1; o < 32; o <<= 1) {
-                    const int t2 = __shfl_up_sync(0xffffffffu, off, o);
-                    if (lane >= o) off += t2;
+                    const int t2 = __shfl_up_sync(0xffffffffu, inc, o);
+                    if (lane >= o) inc += t2;
                 }
-                const int wtot = __shfl_sync(0xffffffffu, off, 31);
-                off -= kept;
-                int cnt = 0;
-                for (uint32_t m = bits; m; m &= m - 1) {
-                    const int l = wi * 32 + __ffs(m) - 1;
-                    double x = 0.0;
-                    if (!COUNT) {
-                        x = dense[l];
-                        dense[l] = 0.0;
-                        if (!nonzero_bits(x)) continue;
-                    }
-                    const int32_t g = a.members[cb + l];
-                    if (MODE == P1_COUNT) {
-                        atomicAdd((unsigned long long *)&a.wcnt[a.pos[g]], 1ull);
-                    } else if (MODE == P1_WRITE) {
-                        int64_t slot = (int64_t)atomicAdd((unsigned long long *)&a.wcur[a.pos[g]], 1ull);
+                int off = ntouch + inc - cntw;
+                for (uint32_t m = bits; m; m &= m - 1) plist[off++] = wi * 32 + __ffs(m) - 1;
+                ntouch += __shfl_sync(0xffffffffu, inc, 31);
+            }
+            __syncwarp();
+            for (int k0 = 0; k0 < ntouch; k0 += 32) {
+                const int k = k0 + lane;
+                const int l = k < ntouch ? plist[k] : 0;
+                double x = 0.0;
+                bool nz = k < ntouch;
+                if (!COUNT && nz) {
+                    x = dense[l];
+                    dense[l] = 0.0;
+                    nz = nonzero_bits(x);
+                }
+                const int32_t g = nz ? a.members[cb + l] : 0;
+                if (MODE == P1_COUNT) {
+                    if (nz) atomicAdd((unsigned long long *)&a.wcnt[a.pos[g]], 1ull);
+                } else if (MODE == P1_WRITE) {
+                    if (nz) {
+                        const int64_t slot = (int64_t)atomicAdd((unsigned long long *)&a.wcur[a.pos[g]], 1ull);
                         a.wcol[slot] = y;
                         a.wval[slot] = x;
-                    } else {
-                        bool term = false, keep = false;
+                    }
+                } else {
+                    bool keep = false;
+                    if (nz) {
+                        bool term = false;
                         if (yelim) {
                             if (g == y) {
                                 if (MODE == P2_WRITE) a.hdiag[y] = x;
@@ -263,29 +303,21 @@ __global__ void k_rows(RowArgs a) {
                         } else {
                             keep = true;
                         }
-                        if (term) {
+                        if (MODE == P2_WRITE && term) {
                             if (a.contrib_cl) prow = __fma_rn(x, x, prow);
                             else part = __fma_rn(x, x, part);
                         }
-                        if (keep) {
-                            if (MODE == P2_WRITE) {
-                                const int64_t slot = nout + off + cnt;
-                                if (slot < a.outcap) {
-                                    scol[slot] = g;
-                                    sval[slot] = x;
-                                }
-                            }
-                            ++cnt;
+                    }
+                    // kept entries in ascending position order
+                    const unsigned kb = __ballot_sync(0xffffffffu, keep);
+                    if (MODE == P2_WRITE && keep) {
+                        const int64_t slot = nout + __popc(kb & ((1u << lane) - 1u));
+                        if (slot < a.outcap) {
+                            scol[slot] = g;
+                            sval[slot] = x;
                         }
                     }
-                }
-                if (wi < nw) tb[wi] = 0u;
-                if (MODE == P2_WRITE) {
-                    nout += wtot;
-                } else if (MODE == P2_COUNT) {
-                    int tot = cnt;
-                    for (int o = 16; o > 0; o >>= 1) tot += __shfl_xor_sync(0xffffffffu, tot, o);
-                    nout += tot;
+                    nout += __popc(kb);
                 }
             }
             __syncwarp();
