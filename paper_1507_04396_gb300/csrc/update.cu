@@ -89,8 +89,10 @@ __host__ __device__ inline int64_t rows_per_warp(int64_t cmax, int64_t outcap, b
 // are read from global memory once; longer rows are re-read per segment).
 constexpr int ROW_CACHE = 2;
 
-template <int MODE>
-__global__ void k_rows(RowArgs a) {
+// KP: the stage's rotations are k-point (k >= 3) blocks; the k = 2
+// instantiation carries no k-point code (fewer registers, more warps).
+template <int MODE, bool KP>
+__global__ void __launch_bounds__(256, 4) k_rows(RowArgs a) {
     constexpr bool COUNT = MODE == P1_COUNT || MODE == P2_COUNT;
     extern __shared__ double smem[];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
@@ -170,7 +172,7 @@ __global__ void k_rows(RowArgs a) {
             __syncwarp();
             const int32_t *lo = a.lvl_off + a.roff[mu] + mu;
             const int nl = a.nlev[mu];
-            if (a.K == 2) {
+            if (!KP) {
                 // level offsets in registers (lane L holds lo[L]) and the first
                 // 32 rotations of the next level loaded while this one runs
                 const int lol = lane <= nl ? lo[lane] : 0;
@@ -422,11 +424,12 @@ pmmf_status launch_rows(RowArgs &a, int64_t nnz_in, int64_t nnz_out, cudaStream_
         return PMMF_ERR_UNSUPPORTED;
     }
     size_t sh = per * warps;
+    auto kern = a.K > 2 ? k_rows<MODE, true> : k_rows<MODE, false>;
     if (sh > 48 * 1024)
-        PMMF_CUDA_TRY(cudaFuncSetAttribute(k_rows<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh));
+        PMMF_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh));
     unsigned grid = grid_for(a.rows, warps, 152 * 16);
     prof_begin(KF_ROWS, st);
-    k_rows<MODE><<<grid, 32 * warps, sh, st>>>(a);
+    kern<<<grid, 32 * warps, sh, st>>>(a);
     // input rows (12 B per entry, 8 B per row pointer) plus written entries
     double bytes = 12.0 * (double)nnz_in + 8.0 * (double)(a.rows + 1);
     if (MODE == P1_WRITE || MODE == P2_WRITE) bytes += 12.0 * (double)nnz_out;
