@@ -288,7 +288,12 @@ pmmf_status pmmf_get_batch(const pmmf_handle *f, int64_t *nmat, int64_t *core_st
  *   dx[n x nrhs] (row-major, ld)   dL/dx
  *   dtheta[rotations]              dL/dtheta, stages in order and (cluster,
  *                                  step) order inside a stage (the order of
- *                                  pmmf_get_stage_rotations)
+ *                                  pmmf_get_stage_rotations); for k >= 3 the
+ *                                  rotations are parameterised by their block
+ *                                  O (x_T' = O x_T) and dtheta[rotations *
+ *                                  k * k] receives dL/dO, k * k slots per
+ *                                  rotation, entry (a, b) of a kk x kk block
+ *                                  at slot a * kk + b, the others 0
  *   dhdiag[n]                      dL/dH_xx on wavelet coordinates, 0 on core
  *                                  coordinates
  *   dcore[core_size^2]             dL/dcore (row-major; for A_INV the core
@@ -299,8 +304,9 @@ pmmf_status pmmf_get_batch(const pmmf_handle *f, int64_t *nmat, int64_t *core_st
  * NULL.  The stage-start state of [x | g] is checkpointed per stage and each
  * stage is replayed once, so the cost is about three applies.  Asynchronous on
  * stream (except the first A_INV call, which forms the core inverse).  Errors:
- * INVALID_ARG (op, sizes, NULL x or g), UNSUPPORTED (k > 2 or a cluster too
- * large for one CTA's shared memory), NOT_SPD (A_INV with H not SPD), OOM. */
+ * INVALID_ARG (op, sizes, NULL x or g), UNSUPPORTED (a batch handle, or a
+ * cluster too large for one CTA's shared memory), NOT_SPD (A_INV with H not
+ * SPD), OOM. */
 pmmf_status pmmf_apply_backward(const pmmf_handle *f, int op, const double *x, const double *g,
                                 int64_t nrhs, int64_t ld, double *dx, double *dtheta,
                                 double *dhdiag, double *dcore, void *stream);

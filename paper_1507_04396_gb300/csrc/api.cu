@@ -1389,14 +1389,17 @@ pmmf_status pmmf_apply_backward(const pmmf_handle *fc, int op, const double *x, 
     if (nrhs < 1 || ld < nrhs) return fail(PMMF_ERR_INVALID_ARG, "need nrhs >= 1 and ld >= nrhs");
     if (op != PMMF_OP_A && op != PMMF_OP_A_INV)
         return fail(PMMF_ERR_INVALID_ARG, "backward is defined for PMMF_OP_A and PMMF_OP_A_INV");
-    if (f->k != 2) return fail(PMMF_ERR_UNSUPPORTED, "backward needs k = 2 rotations");
     if (f->nblk > 1) return fail(PMMF_ERR_UNSUPPORTED, "backward of a batch handle is not built");
     cudaStream_t st = (cudaStream_t)stream;
     const bool inv = op == PMMF_OP_A_INV;
     if (inv) PMMF_TRY(ensure_inverse(f, st));
     std::vector<const RotRec *> recs;
-    for (auto &S : f->st) recs.push_back(S.rot.rec.p);
-    return apply_backward(f->views, recs, hdata(f), inv, x, g, nrhs, ld, dx, dtheta, dhdiag,
+    std::vector<const int32_t *> klvls;
+    for (auto &S : f->st) {
+        recs.push_back(S.rot.rec.p);
+        klvls.push_back(S.rot.klvl.p);
+    }
+    return apply_backward(f->views, recs, klvls, hdata(f), inv, x, g, nrhs, ld, dx, dtheta, dhdiag,
                           dcore, st);
 }
 

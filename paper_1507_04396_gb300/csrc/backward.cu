@@ -18,10 +18,15 @@
 //   the U^T occurrence q_i p_j - q_j p_i (a 2-D cross product, invariant under
 //   the rotation itself, so both are taken at the same point), summed over the
 //   right-hand sides.  What remains in r after the last stage is dL/dx.
+// k-point rotations are parameterised by their block O (x_T' = O x_T): the U
+// occurrence adds r_a v_b and the U^T occurrence p_a q_b to dL/dO_ab, with
+// r, p at the rotation's output and v, q at its input, over the right-hand
+// sides.
 #include <cmath>
 
 #include "apply.cuh"
 #include "backward.cuh"
+#include "rotmath.cuh"
 
 namespace pmmf {
 namespace {
@@ -201,6 +206,113 @@ size_t backward_smem(int64_t c, int64_t e, int nr) {
     return sizeof(double) * (size_t)(4 * c * nr + 5 * e * nr) + sizeof(RotRec) * (size_t)e;
 }
 
+// One stage of the backward sweep for k-point rotations (one CTA per
+// cluster).  The replay keeps each rotation's inputs of v and q (SIN: per
+// rotation and right-hand side, K entries of each); the undo runs one thread
+// per rotation of a level, which forms the rotation's dL/dO block over all
+// right-hand sides and then applies O^T to its coordinates of p and r.  dO
+// gets K*K slots per rotation (stride kk inside, unused slots 0) in step
+// order.
+__global__ void __launch_bounds__(BW_THREADS)
+k_backward_stage_k(const int64_t *coff, const int32_t *members, const int64_t *roff, int K,
+                   const int32_t *kidx, const int32_t *kkv, const int32_t *klvl, const double *kO,
+                   const int32_t *nlev, const double *ck, double *pr, int nr, int accumulate,
+                   double *dO) {
+    extern __shared__ double sm[];
+    const int64_t u = blockIdx.x;
+    const int64_t base = coff[u];
+    const int c = (int)(coff[u + 1] - base);
+    const int64_t r0 = roff[u];
+    const int e = (int)(roff[u + 1] - r0);
+    if (e == 0) return;
+    const int nl = nlev[u];
+    const int w2 = 2 * nr;
+    const int tid = threadIdx.x;
+    double *V = sm;
+    double *Q = V + (int64_t)c * nr;
+    double *P = Q + (int64_t)c * nr;
+    double *R = P + (int64_t)c * nr;
+    double *SIN = R + (int64_t)c * nr;
+    for (int64_t q = tid; q < (int64_t)c * nr; q += BW_THREADS) {
+        const int64_t l = q / nr, r = q - l * nr;
+        const double *cq = ck + (base + l) * w2;
+        const double *pq = pr + (int64_t)members[base + l] * w2;
+        V[q] = cq[r];
+        Q[q] = cq[nr + r];
+        P[q] = pq[r];
+        R[q] = pq[nr + r];
+    }
+    __syncthreads();
+    const int en = e * nr;
+    for (int L = 1; L <= nl; ++L) {
+        for (int q = tid; q < en; q += BW_THREADS) {
+            const int t = q / nr, r = q - t * nr;
+            const int64_t tt = r0 + t;
+            if (klvl[tt] != L) continue;
+            const int kk = kkv[tt];
+            const int32_t *T = kidx + tt * K;
+            const double *O = kO + tt * K * K;
+            double *sin = SIN + (int64_t)q * 2 * K;
+            double vin[8], qin[8];
+            for (int a = 0; a < kk; ++a) {
+                vin[a] = V[T[a] * nr + r];
+                qin[a] = Q[T[a] * nr + r];
+                sin[a] = vin[a];
+                sin[K + a] = qin[a];
+            }
+            for (int a = 0; a < kk; ++a) {
+                V[T[a] * nr + r] = rot_row(O, kk, a, vin);
+                Q[T[a] * nr + r] = rot_row(O, kk, a, qin);
+            }
+        }
+        __syncthreads();
+    }
+    for (int L = nl; L >= 1; --L) {
+        for (int t = tid; t < e; t += BW_THREADS) {
+            const int64_t tt = r0 + t;
+            if (klvl[tt] != L) continue;
+            const int kk = kkv[tt];
+            const int32_t *T = kidx + tt * K;
+            const double *O = kO + tt * K * K;
+            double *d = dO + tt * K * K;
+            for (int a = 0; a < kk; ++a)
+                for (int b = 0; b < kk; ++b) {
+                    double acc = accumulate ? d[a * kk + b] : 0.0;
+                    for (int r = 0; r < nr; ++r) {
+                        const double *sin = SIN + ((int64_t)t * nr + r) * 2 * K;
+                        acc = __fma_rn(R[T[a] * nr + r], sin[b], acc);
+                        acc = __fma_rn(P[T[a] * nr + r], sin[K + b], acc);
+                    }
+                    d[a * kk + b] = acc;
+                }
+            if (!accumulate)
+                for (int z = kk * kk; z < K * K; ++z) d[z] = 0.0;
+            for (int r = 0; r < nr; ++r) {
+                double pin[8], rin[8];
+                for (int a = 0; a < kk; ++a) {
+                    pin[a] = P[T[a] * nr + r];
+                    rin[a] = R[T[a] * nr + r];
+                }
+                for (int a = 0; a < kk; ++a) {
+                    P[T[a] * nr + r] = rot_row_t(O, kk, a, pin);
+                    R[T[a] * nr + r] = rot_row_t(O, kk, a, rin);
+                }
+            }
+        }
+        __syncthreads();
+    }
+    for (int64_t q = tid; q < (int64_t)c * nr; q += BW_THREADS) {
+        const int64_t l = q / nr, r = q - l * nr;
+        double *pq = pr + (int64_t)members[base + l] * w2;
+        pq[r] = P[q];
+        pq[nr + r] = R[q];
+    }
+}
+
+size_t backward_smem_k(int64_t c, int64_t e, int K, int nr) {
+    return sizeof(double) * (size_t)(4 * c * nr + 2 * e * nr * K);
+}
+
 __global__ void k_get_angles(const RotRec *rec, int64_t nrot, double *theta) {
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < nrot;
          t += (int64_t)gridDim.x * blockDim.x)
@@ -240,24 +352,30 @@ __global__ void k_regroup_levels(const int64_t *roff, const RotRec *rec, const i
 }  // namespace
 
 pmmf_status apply_backward(const ApplyStages &S, const std::vector<const RotRec *> &recs,
-                           const HData &H, bool inverse, const double *x, const double *g,
-                           int64_t nrhs, int64_t ld, double *dx, double *dtheta, double *dhdiag,
-                           double *dcore, cudaStream_t st) {
+                           const std::vector<const int32_t *> &klvls, const HData &H,
+                           bool inverse, const double *x, const double *g, int64_t nrhs,
+                           int64_t ld, double *dx, double *dtheta, double *dhdiag, double *dcore,
+                           cudaStream_t st) {
     const int64_t n = H.n;
     const int nst = (int)S.size();
     int64_t totrot = 0;
     std::vector<int64_t> toff((size_t)nst + 1, 0);
     int nr = 8;
+    const int K = nst > 0 ? S[0].K : 2;
+    auto smem = [&](int64_t c, int w) {
+        return K > 2 ? backward_smem_k(c, c, K, w) : backward_smem(c, c, w);
+    };
     for (int p = 0; p < nst; ++p) {
         toff[p + 1] = toff[p] + S[p].nrot;
         // a cluster never rotates more coordinates than it holds
-        while (nr > 1 && backward_smem(S[p].cmax, S[p].cmax, nr) > 220 * 1024) --nr;
-        if (backward_smem(S[p].cmax, S[p].cmax, nr) > 220 * 1024) {
+        while (nr > 1 && smem(S[p].cmax, nr) > 220 * 1024) --nr;
+        if (smem(S[p].cmax, nr) > 220 * 1024) {
             set_error("backward: cluster too large for shared memory");
             return PMMF_ERR_UNSUPPORTED;
         }
     }
     totrot = toff[nst];
+    const int64_t per_rot = K > 2 ? (int64_t)K * K : 1;   // dtheta slots per rotation
     nr = (int)std::min<int64_t>(nr, nrhs);
     const int w2 = 2 * nr;
     // checkpoint offsets: stage p's slice holds its active coordinates x 2nr
@@ -269,7 +387,7 @@ pmmf_status apply_backward(const ApplyStages &S, const std::vector<const RotRec 
     PMMF_TRY(ck.alloc(std::max<int64_t>(coff_ck[nst], 1), st));
     double *dt = dtheta;
     if (!dt && totrot > 0) {
-        PMMF_TRY(dth.alloc(totrot, st));
+        PMMF_TRY(dth.alloc(totrot * per_rot, st));
         dt = dth.p;
     }
 
@@ -314,6 +432,16 @@ pmmf_status apply_backward(const ApplyStages &S, const std::vector<const RotRec 
         for (int p = nst - 1; p >= 0; --p) {
             const ApplyStage &a = S[p];
             if (a.nrot == 0) continue;
+            if (K > 2) {
+                const size_t shk = backward_smem_k(a.cmax, a.cmax, K, cur);
+                if (shk > 48 * 1024)
+                    PMMF_CUDA_TRY(cudaFuncSetAttribute(k_backward_stage_k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shk));
+                k_backward_stage_k<<<(unsigned)a.m, BW_THREADS, shk, st>>>(
+                    a.coff, a.members, a.roff, K, a.kidx, a.kkv, klvls[p], a.kO, a.nlev,
+                    ck.p + coff_ck[p], prb.p, cur, acc, dt + toff[p] * per_rot);
+                PMMF_TRY(launched("bw_stage_k"));
+                continue;
+            }
             const size_t sh = backward_smem(a.cmax, a.cmax, cur);
             if (sh > 48 * 1024)
                 PMMF_CUDA_TRY(cudaFuncSetAttribute(k_backward_stage, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh));

@@ -8,13 +8,16 @@
 namespace pmmf {
 
 // dL/dx, dL/dtheta (per rotation, stages in order, (cluster, step) order
-// inside), dL/d(diagonal of H) (0 on core coordinates) and dL/dcore for
-// L = sum(g * U^T M U x), M = H or H^{-1}.  Outputs are overwritten; any may
-// be NULL.  recs[p] = stage p's step-order rotation records.
+// inside; for k-point rotations dL/dO, K*K slots per rotation), dL/d(diagonal
+// of H) (0 on core coordinates) and dL/dcore for L = sum(g * U^T M U x),
+// M = H or H^{-1}.  Outputs are overwritten; any may be NULL.  recs[p] =
+// stage p's step-order rotation records (k = 2), klvls[p] = its rotations'
+// levels (k >= 3).
 pmmf_status apply_backward(const ApplyStages &S, const std::vector<const RotRec *> &recs,
-                           const HData &H, bool inverse, const double *x, const double *g,
-                           int64_t nrhs, int64_t ld, double *dx, double *dtheta, double *dhdiag,
-                           double *dcore, cudaStream_t st);
+                           const std::vector<const int32_t *> &klvls, const HData &H,
+                           bool inverse, const double *x, const double *g, int64_t nrhs,
+                           int64_t ld, double *dx, double *dtheta, double *dhdiag, double *dcore,
+                           cudaStream_t st);
 
 // theta[t] = atan2(s_t, c_t) for one stage's records.
 pmmf_status get_angles(const RotRec *rec, int64_t nrot, double *theta, cudaStream_t st);

@@ -50,6 +50,13 @@ __device__ __forceinline__ double rot_row(const double *O, int kk, int a, const 
     return acc;
 }
 
+// Row a of x_T' = O^T x_T (the same chain on the transposed block).
+__device__ __forceinline__ double rot_row_t(const double *O, int kk, int a, const double *in) {
+    double acc = __dmul_rn(O[(kk - 1) * kk + a], in[kk - 1]);
+    for (int b = kk - 2; b >= 0; --b) acc = __fma_rn(O[b * kk + a], in[b], acc);
+    return acc;
+}
+
 // X <- J X J^T on the pair (p, q) of a small symmetric k x k matrix X
 // (row-major): rows p, q recomputed for every other column and mirrored; the
 // 2 x 2 block as R = J X_TT, then R J^T for a <= b, mirrored.

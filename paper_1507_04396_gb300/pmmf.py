@@ -456,20 +456,27 @@ class Factorization:
                        None if core is None else core.contiguous())
 
     def backward(self, op: int, x, g):
-        """Gradients of sum(g * op(x)): dict with dx, dtheta, dhdiag, dcore."""
+        """Gradients of sum(g * op(x)): dict with dx, dtheta (k = 2) or dO
+        (k >= 3: [rotations, k * k], block entry (a, b) at a * kk + b), dhdiag,
+        dcore."""
         import torch
         assert x.is_cuda and x.dtype == torch.float64 and x.shape == g.shape
         x, g = x.contiguous(), g.contiguous()
         i = self.info()
         nrhs = 1 if x.dim() == 1 else x.shape[1]
+        per = self.k * self.k if self.k > 2 else 1
         out = dict(dx=torch.empty_like(x),
-                   dtheta=torch.empty(max(i.rotations, 1), dtype=torch.float64, device="cuda"),
+                   dtheta=torch.empty(max(i.rotations * per, 1), dtype=torch.float64,
+                                      device="cuda"),
                    dhdiag=torch.empty(i.n, dtype=torch.float64, device="cuda"),
                    dcore=torch.empty((i.core_size, i.core_size), dtype=torch.float64,
                                      device="cuda"))
         pmmf_apply_backward(self.handle, op, x, g, nrhs, nrhs, out["dx"], out["dtheta"],
                             out["dhdiag"], out["dcore"])
-        out["dtheta"] = out["dtheta"][:i.rotations]
+        if self.k > 2:
+            out["dO"] = out.pop("dtheta")[:i.rotations * per].reshape(i.rotations, per)
+        else:
+            out["dtheta"] = out["dtheta"][:i.rotations]
         return out
 
     def solve(self, a, b, rtol=1e-8, maxit=1000, xi=1.0, stream=None):

@@ -60,6 +60,29 @@ def test_backward_matches_oracle_dense_one_cluster():
 
 
 @gpu
+@pytest.mark.parametrize("k", [3, 4])
+def test_backward_kpoint_block_gradient(k):
+    """k-point rotations parameterised by their blocks: dL/dO per rotation
+    (k * k slots), dx, dH against the oracle; two stages of several clusters,
+    nrhs = 10 runs two column chunks."""
+    import torch
+    a = I.knn_laplacian(1500, seed=8)
+    g, o = factor_both(a, k=k, eta=0.5, cluster_size=80, core_size=60, seed=2)
+    assert_same_factorization(g, o)
+    assert g.info().stages >= 2
+    rng = np.random.default_rng(k)
+    for op, nrhs in ((OP_A, 10), (OP_A_INV, 3)):
+        x = rng.standard_normal((a.n, nrhs))
+        gy = rng.standard_normal((a.n, nrhs))
+        want = o.apply_grad(op, x, gy)
+        got = g.backward(op, torch.from_numpy(x).cuda(), torch.from_numpy(gy).cuda())
+        _close(got["dx"].cpu().numpy(), want["dx"], "dx")
+        _close(got["dO"].cpu().numpy(), want["dO"].reshape(got["dO"].shape), "dO")
+        _close(got["dhdiag"].cpu().numpy(), want["dhdiag"], "dhdiag")
+        _close(got["dcore"].cpu().numpy(), want["dcore"], "dcore")
+
+
+@gpu
 def test_backward_full_size_workload():
     """The bench workload (65,536 coordinates, 9 stages), 8 right-hand sides."""
     a = I.knn_laplacian(65536, seed=1)

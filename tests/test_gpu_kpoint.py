@@ -67,12 +67,12 @@ def test_batch_k3_matches_oracle():
         assert np.array_equal(core[b, :d, :d], o.core)
 
 
-def test_backward_rejects_kpoint():
-    import torch
+def test_angles_reject_kpoint():
+    """k-point blocks have no single angle: get_angles is UNSUPPORTED (their
+    gradient is taken with respect to the block entries)."""
     pm = gpu_lib()
     a = I.knn_laplacian(300, seed=1)
     g = pm.factor(a, k=3, eta=0.5, cluster_size=64, core_size=20, seed=0)
-    x = torch.zeros(a.n, 1, dtype=torch.float64, device="cuda")
     with pytest.raises(pm.PmmfError) as e:
-        g.backward(0, x, x)
+        g.angles()
     assert e.value.status == pm.ERR_UNSUPPORTED
