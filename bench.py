@@ -251,12 +251,14 @@ def run_gpu(args):
     # matrix-free apply: y = U^T H U x on 8 right-hand sides
     f = factor()
     if dominant == "select":
-        # DRAM bytes per launch of the rotation search, measured with ncu on the
-        # 32,768-point instance: 0.917 x 16 B per Gram entry (G and M streamed
-        # once); scaled to this workload's launches by their Gram entries
+        # DRAM bytes per launch of the rotation search, measured with ncu on
+        # this workload's stage-2 launch: 132.3 MB = 0.973 x 16 B per Gram
+        # entry (G and M streamed once); scaled to every launch by its Gram
+        # entries
         sq = [int((np.diff(f.clusters(p)[0]) ** 2).sum()) for p in range(f.info().stages)]
-        roof["traffic"] = 0.917 * 16.0 * sum(sq) / max(len(sq), 1)
-        roof["traffic_basis"] = "ncu DRAM bytes on n=32768 scaled by Gram entries per launch"
+        roof["traffic"] = 0.973 * 16.0 * sum(sq) / max(len(sq), 1)
+        roof["traffic_basis"] = ("ncu DRAM bytes of the stage-2 launch at n=65536 scaled by "
+                                 "Gram entries per launch")
     x = torch.randn(a.n, NRHS_APPLY, dtype=torch.float64, device=dev)
     y = torch.empty_like(x)
     for _ in range(3):
