@@ -83,6 +83,12 @@ def lib():
         L.or_jacobi2.argtypes = [f64, f64, f64, vp, vp]
         L.or_jacobik.restype = i32
         L.or_jacobik.argtypes = [i32, vp, vp]
+        L.or_block_angles.restype = i32
+        L.or_block_angles.argtypes = [i32, vp, vp, vp]
+        L.or_block_from_angles.restype = None
+        L.or_block_from_angles.argtypes = [i32, vp, vp, vp]
+        L.or_block_angle_grad.restype = None
+        L.or_block_angle_grad.argtypes = [i32, vp, vp, vp, vp]
         L.or_sym_rotate.argtypes = [vp, i64, i64, i32, vp, vp]
         L.or_gram.argtypes = [i64, vp, vp, vp, i64, vp, vp, vp]
         L.or_partition.restype = i32
@@ -341,3 +347,33 @@ def quantize(coords: np.ndarray) -> np.ndarray:
     q = np.zeros(coords.shape, dtype=np.uint32)
     lib().or_quantize(coords.shape[0], _p(coords), coords.shape[1], _p(q))
     return q
+
+
+def block_angles(O: np.ndarray):
+    """Givens angles theta [kk(kk-1)/2] and signs D [kk] of an orthogonal block."""
+    O = np.ascontiguousarray(O, dtype=np.float64)
+    kk = O.shape[0]
+    th = np.zeros(kk * (kk - 1) // 2)
+    D = np.zeros(kk)
+    if lib().or_block_angles(kk, _p(O), _p(th), _p(D)):
+        raise ValueError("bad block size")
+    return th, D
+
+
+def block_from_angles(theta: np.ndarray, D: np.ndarray) -> np.ndarray:
+    theta = np.ascontiguousarray(theta, dtype=np.float64)
+    D = np.ascontiguousarray(D, dtype=np.float64)
+    kk = len(D)
+    O = np.zeros((kk, kk))
+    lib().or_block_from_angles(kk, _p(theta), _p(D), _p(O))
+    return O
+
+
+def block_angle_grad(theta: np.ndarray, D: np.ndarray, dO: np.ndarray) -> np.ndarray:
+    theta = np.ascontiguousarray(theta, dtype=np.float64)
+    D = np.ascontiguousarray(D, dtype=np.float64)
+    dO = np.ascontiguousarray(dO, dtype=np.float64)
+    kk = len(D)
+    dth = np.zeros(kk * (kk - 1) // 2)
+    lib().or_block_angle_grad(kk, _p(theta), _p(D), _p(dO), _p(dth))
+    return dth

@@ -1525,3 +1525,98 @@ int or_set_h(or_fact *f, const double *hdiag, const double *core) {
     f->isqrt_status = OR_OK;
     return OR_OK;
 }
+
+/* ------------------------------------------------------------------------ */
+/* Angle parameterisation of a k-point block (the derivative's angles for
+ * k >= 3; not in the paper).  Givens elimination of O column by column: for
+ * j = 0 .. kk-2 and l = j+1 .. kk-1 in that order, G_i acts on rows (j, l)
+ * with theta_i = atan2(A_lj, A_jj), c = cos, s = sin:
+ *   row j <- c row j + s row l,   row l <- -s row j + c row l,
+ * which zeroes A_lj.  What remains, G_P .. G_1 O, is orthogonal and upper
+ * triangular: D = diag(+-1) (its diagonal, rounded to the sign).  Hence
+ *   O = G_1^T G_2^T ... G_P^T D,   P = kk (kk - 1) / 2.                      */
+
+static void givens_rows(double *A, int kk, int j, int l, double c, double s) {
+    for (int b = 0; b < kk; ++b) {
+        const double aj = A[j * kk + b], al = A[l * kk + b];
+        A[j * kk + b] = c * aj + s * al;
+        A[l * kk + b] = -s * aj + c * al;
+    }
+}
+
+/* rows (j, l) <- G^T rows (j, l):  row j <- c row j - s row l,
+ * row l <- s row j + c row l (dc, ds: the derivative's (dc/dt, ds/dt)). */
+static void givens_rows_t(double *A, int kk, int j, int l, double c, double s) {
+    for (int b = 0; b < kk; ++b) {
+        const double aj = A[j * kk + b], al = A[l * kk + b];
+        A[j * kk + b] = c * aj - s * al;
+        A[l * kk + b] = s * aj + c * al;
+    }
+}
+
+int or_block_angles(int kk, const double *O, double *theta, double *D) {
+    if (kk < 2 || kk > KMAX) return OR_ERR_INVALID_ARG;
+    double A[KMAX * KMAX];
+    memcpy(A, O, sizeof(double) * (size_t)(kk * kk));
+    int i = 0;
+    for (int j = 0; j + 1 < kk; ++j)
+        for (int l = j + 1; l < kk; ++l) {
+            const double t = atan2(A[l * kk + j], A[j * kk + j]);
+            theta[i++] = t;
+            givens_rows(A, kk, j, l, cos(t), sin(t));
+        }
+    for (int a = 0; a < kk; ++a) D[a] = A[a * kk + a] < 0.0 ? -1.0 : 1.0;
+    return OR_OK;
+}
+
+void or_block_from_angles(int kk, const double *theta, const double *D, double *O) {
+    const int P = kk * (kk - 1) / 2;
+    for (int a = 0; a < kk; ++a)
+        for (int b = 0; b < kk; ++b) O[a * kk + b] = a == b ? D[a] : 0.0;
+    /* O = G_1^T (G_2^T ( ... (G_P^T D))) */
+    int i = P;
+    for (int j = kk - 2; j >= 0; --j)
+        for (int l = kk - 1; l > j; --l) {
+            --i;
+            givens_rows_t(O, kk, j, l, cos(theta[i]), sin(theta[i]));
+        }
+}
+
+/* dL/dtheta_i = < dO, G_1^T .. G_{i-1}^T (dG_i^T/dtheta) G_{i+1}^T .. G_P^T D >
+ * = < Lam_i, (dG_i^T/dtheta) B_i > with Lam_i = G_{i-1} .. G_1 dO and
+ * B_i = G_{i+1}^T .. G_P^T D; dG^T/dtheta on rows (j, l) is
+ * [[-s, -c], [c, -s]]. */
+void or_block_angle_grad(int kk, const double *theta, const double *D, const double *dO,
+                         double *dtheta) {
+    const int P = kk * (kk - 1) / 2;
+    int pj[KMAX * KMAX], pl[KMAX * KMAX];
+    {
+        int i = 0;
+        for (int j = 0; j + 1 < kk; ++j)
+            for (int l = j + 1; l < kk; ++l) { pj[i] = j; pl[i] = l; ++i; }
+    }
+    double B[KMAX * KMAX * KMAX * KMAX / 2 + KMAX * KMAX];   /* P + 1 blocks of kk x kk */
+    double *Bi = B + (size_t)P * kk * kk;                      /* B_P = D */
+    for (int a = 0; a < kk; ++a)
+        for (int b = 0; b < kk; ++b) Bi[a * kk + b] = a == b ? D[a] : 0.0;
+    for (int i = P - 1; i >= 1; --i) {     /* B_i = G_{i+1}^T B_{i+1}, stored at slot i */
+        double *dst = B + (size_t)i * kk * kk;
+        memcpy(dst, B + (size_t)(i + 1) * kk * kk, sizeof(double) * (size_t)(kk * kk));
+        givens_rows_t(dst, kk, pj[i], pl[i], cos(theta[i]), sin(theta[i]));
+    }
+    /* slot i (1-based in the comment) holds B_i for i = 1..P at index i - 1 */
+    double Lam[KMAX * KMAX];
+    memcpy(Lam, dO, sizeof(double) * (size_t)(kk * kk));
+    for (int i = 0; i < P; ++i) {
+        const double *Bcur = B + (size_t)(i + 1) * kk * kk;
+        const double c = cos(theta[i]), s = sin(theta[i]);
+        const int j = pj[i], l = pl[i];
+        double acc = 0.0;
+        for (int b = 0; b < kk; ++b) {
+            const double bj = Bcur[j * kk + b], bl = Bcur[l * kk + b];
+            acc = acc + Lam[j * kk + b] * (-s * bj - c * bl) + Lam[l * kk + b] * (c * bj - s * bl);
+        }
+        dtheta[i] = acc;
+        givens_rows(Lam, kk, j, l, c, s);   /* Lam_{i+1} = G_i Lam_i */
+    }
+}

@@ -109,6 +109,16 @@ uint64_t or_draw(uint64_t seed, int64_t p, int64_t u, int64_t t);
 int64_t or_pick(uint64_t r, int64_t count);
 void or_jacobi2(double a, double b, double d, double *c, double *s);
 int or_jacobik(int k, const double *g, double *O);
+
+/* Angle parameterisation of a kk x kk orthogonal block (k-point rotations'
+ * derivative): Givens elimination column by column (j = 0..kk-2, l > j) gives
+ * theta[kk(kk-1)/2] and D[kk] (+-1) with O = G_1^T .. G_P^T D;
+ * or_block_from_angles rebuilds O; or_block_angle_grad maps dL/dO to
+ * dL/dtheta at theta (D fixed). */
+int or_block_angles(int kk, const double *O, double *theta, double *D);
+void or_block_from_angles(int kk, const double *theta, const double *D, double *O);
+void or_block_angle_grad(int kk, const double *theta, const double *D, const double *dO,
+                         double *dtheta);
 void or_sym_rotate(double *X, int64_t ld, int64_t nn, int kk, const int64_t *T, const double *O);
 void or_gram(int64_t n, const int64_t *rowptr, const int32_t *col, const double *val,
              int64_t cu, const int32_t *members, double *G, double *M);

@@ -167,3 +167,73 @@ def test_h_gradient_against_dense_u():
     np.testing.assert_allclose(grad["dcore"], outer[np.ix_(ci, ci)], rtol=1e-12, atol=1e-12)
     want = np.where(core, 0.0, np.diag(outer))
     np.testing.assert_allclose(grad["dhdiag"], want, rtol=1e-12, atol=1e-12)
+
+
+# ---------------------------------------------------------------- k-point angles
+
+@pytest.mark.parametrize("kk", [2, 3, 4, 6, 8])
+def test_block_angles_round_trip(kk):
+    """Givens elimination of an orthogonal block and its rebuild: O is
+    recovered to rounding, the signs are +-1 with det(D) = det(O), the
+    identity has zero angles, and a 2 x 2 rotation R(t) = [[c, -s], [s, c]]
+    has the single angle t (the k = 2 parameterisation)."""
+    rng = np.random.default_rng(kk)
+    for _ in range(5):
+        q, _r = np.linalg.qr(rng.standard_normal((kk, kk)))
+        th, D = O.block_angles(q)
+        assert th.shape == (kk * (kk - 1) // 2,) and set(np.abs(D)) == {1.0}
+        assert np.prod(D) == np.sign(np.linalg.det(q))
+        np.testing.assert_allclose(O.block_from_angles(th, D), q, rtol=0, atol=1e-14)
+    th, D = O.block_angles(np.eye(kk))
+    assert np.all(th == 0.0) and np.all(D == 1.0)
+    if kk == 2:
+        for t in (0.3, -2.1, 3.0):
+            R = np.array([[np.cos(t), -np.sin(t)], [np.sin(t), np.cos(t)]])
+            th, D = O.block_angles(R)
+            assert abs(th[0] - t) <= 1e-15 and np.all(D == 1.0)
+
+
+@pytest.mark.parametrize("kk", [3, 5])
+def test_block_angle_gradient_finite_differences(kk):
+    """d<W, O(theta)>/dtheta against central differences in every angle."""
+    rng = np.random.default_rng(10 + kk)
+    q, _r = np.linalg.qr(rng.standard_normal((kk, kk)))
+    th, D = O.block_angles(q)
+    W = rng.standard_normal((kk, kk))
+    grad = O.block_angle_grad(th, D, W)
+    eps = 1e-6
+    for i in range(len(th)):
+        tp, tm = th.copy(), th.copy()
+        tp[i] += eps
+        tm[i] -= eps
+        fd = (np.sum(W * O.block_from_angles(tp, D)) - np.sum(W * O.block_from_angles(tm, D))) / (2 * eps)
+        assert abs(fd - grad[i]) <= 1e-8 * max(1.0, abs(fd)), (i, fd, grad[i])
+
+
+def test_operator_angle_gradient_kpoint():
+    """dL/dtheta of the operator for k = 3 (block gradient, then the angle
+    chain rule) against central differences of the forward apply with the
+    block rebuilt from perturbed angles."""
+    a = I.psd_dense(18, 6, seed=8)
+    f = O.factor_csr(a, k=3, eta=0.5, cluster_size=18, core_size=4, seed=3)
+    rng = np.random.default_rng(2)
+    x = rng.standard_normal((a.n, 2))
+    g = rng.standard_normal((a.n, 2))
+    grad = f.apply_grad(OP_A, x, g)
+    s0 = f.stages[0]
+    for t in (0, 1):
+        kk = int(s0.rot_k[t])
+        o = s0.rot_O[t, :kk * kk].copy()
+        th, D = O.block_angles(o.reshape(kk, kk))
+        dth = O.block_angle_grad(th, D, grad["dO"][t, :kk * kk].reshape(kk, kk))
+        eps = 1e-6
+        for i in range(len(th)):
+            vals = []
+            for sgn in (1.0, -1.0):
+                tt = th.copy()
+                tt[i] += sgn * eps
+                f.set_rotation(0, t, O.block_from_angles(tt, D).ravel())
+                vals.append(_loss(f, OP_A, x, g))
+            f.set_rotation(0, t, o)
+            fd = (vals[0] - vals[1]) / (2 * eps)
+            assert abs(fd - dth[i]) <= 1e-7 * max(1.0, abs(fd)), (t, i, fd, dth[i])

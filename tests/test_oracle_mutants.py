@@ -71,6 +71,12 @@ MUTANTS = [
     ("split CG applies W on one side only",
      "        st = or_apply(f, OR_OP_A_INV_SQRT, qv, qv, nrhs);\n",
      ""),
+    ("block angles taken from the transposed entries",
+     "            const double t = atan2(A[l * kk + j], A[j * kk + j]);",
+     "            const double t = atan2(A[j * kk + l], A[j * kk + j]);"),
+    ("angle chain rule with the derivative's sine sign flipped",
+     "acc = acc + Lam[j * kk + b] * (-s * bj - c * bl) + Lam[l * kk + b] * (c * bj - s * bl);",
+     "acc = acc + Lam[j * kk + b] * (s * bj - c * bl) + Lam[l * kk + b] * (c * bj - s * bl);"),
     ("inverse gradient of H without the minus sign",
      "                dhdiag[i] = -acc;",
      "                dhdiag[i] = acc;"),
