@@ -311,14 +311,30 @@ pmmf_status pmmf_apply_backward(const pmmf_handle *f, int op, const double *x, c
                                 int64_t nrhs, int64_t ld, double *dx, double *dtheta,
                                 double *dhdiag, double *dcore, void *stream);
 
-/* Angles of every rotation, theta = atan2(s, c), into the DEVICE array
- * theta[rotations] in the order above (k = 2 only; else UNSUPPORTED). */
+/* Angles of every rotation into the DEVICE array theta, rotations in the
+ * order above.  k = 2: theta[rotations], theta = atan2(s, c).  k >= 3 (the
+ * angle parameterisation of a k-point block, not in the paper): P = k(k-1)/2
+ * slots per rotation, the Givens elimination of the kk x kk block column by
+ * column (j = 0..kk-2, l = j+1..kk-1; theta = atan2(A_lj, A_jj), rows (j, l)
+ * <- (c row j + s row l, -s row j + c row l)), which leaves signs D =
+ * diag(+-1) with O = G_1^T .. G_P^T D; slots beyond kk(kk-1)/2 are 0.  The
+ * signs are formed on the first call (of this function, pmmf_set_angles or
+ * pmmf_block_angle_grad) and kept in the handle.  UNSUPPORTED for a batch. */
 pmmf_status pmmf_get_angles(const pmmf_handle *f, double *theta, void *stream);
 
-/* Replace every rotation by (cos theta, sin theta) from the DEVICE array
- * theta[rotations]; the selections (tuples, levels, eliminations) are kept.
- * pmmf_get_info's error still describes the factorization as computed. */
+/* Replace every rotation from the DEVICE array theta (layout above): k = 2
+ * (cos theta, sin theta); k >= 3 O = G_1^T .. G_P^T D with the kept signs.
+ * The selections (tuples, levels, eliminations) are kept; pmmf_get_info's
+ * error still describes the factorization as computed. */
 pmmf_status pmmf_set_angles(pmmf_handle *f, const double *theta, void *stream);
+
+/* k >= 3: dL/dtheta[rotations * k(k-1)/2] (layout of pmmf_get_angles) from
+ * dL/dO[rotations * k * k] (the output of pmmf_apply_backward) at the
+ * handle's current blocks, by the chain rule through O = G_1^T .. G_P^T D
+ * (D fixed).  DEVICE arrays.  UNSUPPORTED for k = 2 (the backward returns
+ * angle gradients directly) and for a batch. */
+pmmf_status pmmf_block_angle_grad(const pmmf_handle *f, const double *dO, double *dtheta,
+                                  void *stream);
 
 /* Replace H: hdiag[n] (its core entries are not used) and/or
  * core[core_size^2], DEVICE arrays, either may be NULL.  The cached core

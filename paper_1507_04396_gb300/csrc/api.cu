@@ -1403,13 +1403,39 @@ pmmf_status pmmf_apply_backward(const pmmf_handle *fc, int op, const double *x, 
                           dcore, st);
 }
 
-pmmf_status pmmf_get_angles(const pmmf_handle *f, double *theta, void *stream) {
+}  // extern "C"
+
+namespace pmmf {
+namespace {
+
+// The Givens signs of every k-point block, formed once from the blocks as
+// they are (theta_scratch receives their angles).
+pmmf_status ensure_block_signs(pmmf_handle *f, StageData &S, double *theta_scratch,
+                               cudaStream_t st) {
+    if (S.rot.kD_ready) return block_angles(S.nrot, f->k, S.rot.kk.p, S.rot.kO.p, theta_scratch,
+                                            nullptr, st);
+    PMMF_TRY(S.rot.kD.alloc(std::max<int64_t>(S.nrot * f->k, 1), st));
+    PMMF_TRY(block_angles(S.nrot, f->k, S.rot.kk.p, S.rot.kO.p, theta_scratch, S.rot.kD.p, st));
+    S.rot.kD_ready = true;
+    return PMMF_OK;
+}
+
+}  // namespace
+}  // namespace pmmf
+
+extern "C" {
+
+pmmf_status pmmf_get_angles(const pmmf_handle *fc, double *theta, void *stream) {
     set_error("");
+    pmmf_handle *f = const_cast<pmmf_handle *>(fc);
     if (!f || !theta) return fail(PMMF_ERR_INVALID_ARG, "NULL handle or output");
-    if (f->k != 2) return fail(PMMF_ERR_UNSUPPORTED, "angles exist for k = 2 rotations only");
+    if (f->nblk > 1) return fail(PMMF_ERR_UNSUPPORTED, "angles of a batch handle are not built");
+    cudaStream_t st = (cudaStream_t)stream;
     int64_t off = 0;
+    const int64_t per = f->k > 2 ? (int64_t)f->k * (f->k - 1) / 2 : 1;
     for (auto &S : f->st) {
-        PMMF_TRY(get_angles(S.rot.rec.p, S.nrot, theta + off, (cudaStream_t)stream));
+        if (f->k > 2) PMMF_TRY(ensure_block_signs(f, S, theta + off * per, st));
+        else PMMF_TRY(get_angles(S.rot.rec.p, S.nrot, theta + off, st));
         off += S.nrot;
     }
     return PMMF_OK;
@@ -1418,11 +1444,44 @@ pmmf_status pmmf_get_angles(const pmmf_handle *f, double *theta, void *stream) {
 pmmf_status pmmf_set_angles(pmmf_handle *f, const double *theta, void *stream) {
     set_error("");
     if (!f || !theta) return fail(PMMF_ERR_INVALID_ARG, "NULL handle or input");
-    if (f->k != 2) return fail(PMMF_ERR_UNSUPPORTED, "angles exist for k = 2 rotations only");
+    if (f->nblk > 1) return fail(PMMF_ERR_UNSUPPORTED, "angles of a batch handle are not built");
+    cudaStream_t st = (cudaStream_t)stream;
     int64_t off = 0;
+    const int64_t per = f->k > 2 ? (int64_t)f->k * (f->k - 1) / 2 : 1;
     for (size_t p = 0; p < f->st.size(); ++p) {
         StageData &S = f->st[p];
-        PMMF_TRY(set_angles(f->views[p], S.rot.rec.p, S.rot.lvl.p, theta + off, (cudaStream_t)stream));
+        if (f->k > 2) {
+            if (!S.rot.kD_ready) {
+                DBuf<double> scratch;
+                PMMF_TRY(scratch.alloc(std::max<int64_t>(S.nrot * per, 1), st));
+                PMMF_TRY(ensure_block_signs(f, S, scratch.p, st));
+            }
+            PMMF_TRY(block_from_angles(S.nrot, f->k, S.rot.kk.p, theta + off * per, S.rot.kD.p,
+                                       S.rot.kO.p, st));
+        } else {
+            PMMF_TRY(set_angles(f->views[p], S.rot.rec.p, S.rot.lvl.p, theta + off, st));
+        }
+        off += S.nrot;
+    }
+    return PMMF_OK;
+}
+
+pmmf_status pmmf_block_angle_grad(const pmmf_handle *fc, const double *dO, double *dtheta,
+                                  void *stream) {
+    set_error("");
+    pmmf_handle *f = const_cast<pmmf_handle *>(fc);
+    if (!f || !dO || !dtheta) return fail(PMMF_ERR_INVALID_ARG, "NULL handle or array");
+    if (f->k < 3) return fail(PMMF_ERR_UNSUPPORTED, "k = 2 rotations are angles already");
+    if (f->nblk > 1) return fail(PMMF_ERR_UNSUPPORTED, "angles of a batch handle are not built");
+    cudaStream_t st = (cudaStream_t)stream;
+    const int64_t per = (int64_t)f->k * (f->k - 1) / 2, kk2 = (int64_t)f->k * f->k;
+    int64_t off = 0;
+    for (auto &S : f->st) {
+        DBuf<double> th;
+        PMMF_TRY(th.alloc(std::max<int64_t>(S.nrot * per, 1), st));
+        PMMF_TRY(ensure_block_signs(f, S, th.p, st));
+        PMMF_TRY(block_angle_grad(S.nrot, f->k, S.rot.kk.p, th.p, S.rot.kD.p, dO + off * kk2,
+                                  dtheta + off * per, st));
         off += S.nrot;
     }
     return PMMF_OK;

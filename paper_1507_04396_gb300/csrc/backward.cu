@@ -329,6 +329,120 @@ __global__ void k_set_angles(RotRec *rec, int64_t nrot, const double *theta) {
     }
 }
 
+// ---- angle parameterisation of k-point blocks --------------------------------
+// Givens elimination of the kk x kk block column by column (j = 0..kk-2,
+// l = j+1..kk-1): theta_i = atan2(A_lj, A_jj), rows (j, l) <- G (c row j + s
+// row l, -s row j + c row l), leaving D = diag(+-1); O = G_1^T .. G_P^T D.
+// One thread per rotation; P = K (K - 1) / 2 angle slots and K sign slots per
+// rotation (unused slots 0).
+__device__ __forceinline__ void bl_rows(double *A, int kk, int j, int l, double c, double s) {
+    for (int b = 0; b < kk; ++b) {
+        const double aj = A[j * kk + b], al = A[l * kk + b];
+        A[j * kk + b] = __dadd_rn(__dmul_rn(c, aj), __dmul_rn(s, al));
+        A[l * kk + b] = __dadd_rn(__dmul_rn(-s, aj), __dmul_rn(c, al));
+    }
+}
+__device__ __forceinline__ void bl_rows_t(double *A, int kk, int j, int l, double c, double s) {
+    for (int b = 0; b < kk; ++b) {
+        const double aj = A[j * kk + b], al = A[l * kk + b];
+        A[j * kk + b] = __dsub_rn(__dmul_rn(c, aj), __dmul_rn(s, al));
+        A[l * kk + b] = __dadd_rn(__dmul_rn(s, aj), __dmul_rn(c, al));
+    }
+}
+
+__global__ void k_block_angles(int64_t nrot, int K, const int32_t *kkv, const double *kO,
+                               double *theta, double *D) {
+    const int P = K * (K - 1) / 2;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < nrot;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const int kk = kkv[t];
+        double A[64];
+        for (int q = 0; q < kk * kk; ++q) A[q] = kO[t * K * K + q];
+        double *th = theta + t * P;
+        int i = 0;
+        for (int j = 0; j + 1 < kk; ++j)
+            for (int l = j + 1; l < kk; ++l) {
+                const double a = atan2(A[l * kk + j], A[j * kk + j]);
+                double s, c;
+                sincos(a, &s, &c);
+                th[i++] = a;
+                bl_rows(A, kk, j, l, c, s);
+            }
+        for (; i < P; ++i) th[i] = 0.0;
+        if (D)
+            for (int a = 0; a < K; ++a)
+                D[t * K + a] = a < kk ? ((f64_bits(A[a * kk + a]) >> 63) && (f64_bits(A[a * kk + a]) << 1) ? -1.0 : 1.0) : 0.0;
+    }
+}
+
+__global__ void k_block_from_angles(int64_t nrot, int K, const int32_t *kkv, const double *theta,
+                                    const double *D, double *kO) {
+    const int P = K * (K - 1) / 2;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < nrot;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const int kk = kkv[t];
+        double O[64];
+        for (int a = 0; a < kk; ++a)
+            for (int b = 0; b < kk; ++b) O[a * kk + b] = a == b ? D[t * K + a] : 0.0;
+        const double *th = theta + t * P;
+        int i = kk * (kk - 1) / 2;
+        for (int j = kk - 2; j >= 0; --j)
+            for (int l = kk - 1; l > j; --l) {
+                --i;
+                double s, c;
+                sincos(th[i], &s, &c);
+                bl_rows_t(O, kk, j, l, c, s);
+            }
+        for (int q = 0; q < K * K; ++q) kO[t * K * K + q] = q < kk * kk ? O[q] : 0.0;
+    }
+}
+
+// dL/dtheta_i = < Lam_i, dG_i^T/dtheta B_i > with Lam_i = G_{i-1} .. G_1 dO and
+// B_i = G_{i+1}^T .. G_P^T D; dG^T/dtheta on rows (j, l) = [[-s, -c], [c, -s]].
+// Lam is carried to the last rotation and walked back with G_i^T (G is
+// orthogonal) while B grows from D, so each thread holds two kk x kk blocks.
+__global__ void k_block_angle_grad(int64_t nrot, int K, const int32_t *kkv, const double *theta,
+                                   const double *D, const double *dO, double *dtheta) {
+    const int P = K * (K - 1) / 2;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < nrot;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const int kk = kkv[t];
+        const int pk = kk * (kk - 1) / 2;
+        const double *th = theta + t * P;
+        double Lam[64], B[64];
+        for (int q = 0; q < kk * kk; ++q) Lam[q] = dO[t * K * K + q];
+        {
+            int i = 0;
+            for (int j = 0; j + 1 < kk; ++j)
+                for (int l = j + 1; l < kk; ++l) {
+                    double s, c;
+                    sincos(th[i++], &s, &c);
+                    bl_rows(Lam, kk, j, l, c, s);
+                }
+        }
+        for (int a = 0; a < kk; ++a)
+            for (int b = 0; b < kk; ++b) B[a * kk + b] = a == b ? D[t * K + a] : 0.0;
+        double *out = dtheta + t * P;
+        int i = pk;
+        for (int j = kk - 2; j >= 0; --j)
+            for (int l = kk - 1; l > j; --l) {
+                --i;
+                double s, c;
+                sincos(th[i], &s, &c);
+                bl_rows_t(Lam, kk, j, l, c, s);        // Lam_i = G_i^T Lam_{i+1}
+                double acc = 0.0;
+                for (int b = 0; b < kk; ++b) {
+                    const double bj = B[j * kk + b], bl = B[l * kk + b];
+                    acc = __dadd_rn(acc, __dmul_rn(Lam[j * kk + b], __dsub_rn(__dmul_rn(-s, bj), __dmul_rn(c, bl))));
+                    acc = __dadd_rn(acc, __dmul_rn(Lam[l * kk + b], __dsub_rn(__dmul_rn(c, bj), __dmul_rn(s, bl))));
+                }
+                out[i] = acc;
+                bl_rows_t(B, kk, j, l, c, s);          // B_{i-1} = G_i^T B_i
+            }
+        for (int q = pk; q < P; ++q) out[q] = 0.0;
+    }
+}
+
 // Rebuild the level-grouped copies from the step-order records (one CTA per
 // cluster; the level offsets are unchanged).  Thread 0 walks the cluster's
 // rotations in step order, so the order inside a level is deterministic.
@@ -456,6 +570,27 @@ pmmf_status apply_backward(const ApplyStages &S, const std::vector<const RotRec 
         }
     }
     return PMMF_OK;
+}
+
+pmmf_status block_angles(int64_t nrot, int K, const int32_t *kkv, const double *kO,
+                         double *theta, double *D, cudaStream_t st) {
+    if (nrot == 0) return PMMF_OK;
+    k_block_angles<<<grid_for(nrot, 128), 128, 0, st>>>(nrot, K, kkv, kO, theta, D);
+    return launched("block_angles");
+}
+
+pmmf_status block_from_angles(int64_t nrot, int K, const int32_t *kkv, const double *theta,
+                              const double *D, double *kO, cudaStream_t st) {
+    if (nrot == 0) return PMMF_OK;
+    k_block_from_angles<<<grid_for(nrot, 128), 128, 0, st>>>(nrot, K, kkv, theta, D, kO);
+    return launched("block_from_angles");
+}
+
+pmmf_status block_angle_grad(int64_t nrot, int K, const int32_t *kkv, const double *theta,
+                             const double *D, const double *dO, double *dtheta, cudaStream_t st) {
+    if (nrot == 0) return PMMF_OK;
+    k_block_angle_grad<<<grid_for(nrot, 64), 64, 0, st>>>(nrot, K, kkv, theta, D, dO, dtheta);
+    return launched("block_angle_grad");
 }
 
 pmmf_status get_angles(const RotRec *rec, int64_t nrot, double *theta, cudaStream_t st) {

@@ -19,6 +19,16 @@ pmmf_status apply_backward(const ApplyStages &S, const std::vector<const RotRec 
                            int64_t ld, double *dx, double *dtheta, double *dhdiag, double *dcore,
                            cudaStream_t st);
 
+// k-point blocks (K*K slots each, kk x kk used) <-> Givens angles (P = K(K-1)/2
+// slots per rotation) and signs D (K slots), and dL/dO -> dL/dtheta at theta.
+// D may be NULL in block_angles.
+pmmf_status block_angles(int64_t nrot, int K, const int32_t *kkv, const double *kO,
+                         double *theta, double *D, cudaStream_t st);
+pmmf_status block_from_angles(int64_t nrot, int K, const int32_t *kkv, const double *theta,
+                              const double *D, double *kO, cudaStream_t st);
+pmmf_status block_angle_grad(int64_t nrot, int K, const int32_t *kkv, const double *theta,
+                             const double *D, const double *dO, double *dtheta, cudaStream_t st);
+
 // theta[t] = atan2(s_t, c_t) for one stage's records.
 pmmf_status get_angles(const RotRec *rec, int64_t nrot, double *theta, cudaStream_t st);
 

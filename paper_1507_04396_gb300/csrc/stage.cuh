@@ -50,6 +50,8 @@ struct StageRotations {
     // level; lvlidx = the step-order rotation at each level-grouped slot
     DBuf<int32_t> kidx, kk, kel, klvl, lvlidx;
     DBuf<double> kO;
+    DBuf<double> kD;          // k >= 3: the blocks' Givens signs (K per rotation), once formed
+    bool kD_ready = false;
 };
 
 pmmf_status quantize_points(const double *coords, int64_t n, int dim, int32_t *q, uint64_t *code,

@@ -72,7 +72,7 @@ EXPORTS = ["pmmf_factor", "pmmf_apply", "pmmf_solve_precond", "pmmf_free", "pmmf
            "pmmf_launch_count", "pmmf_apply_backward", "pmmf_get_angles", "pmmf_set_angles",
            "pmmf_set_h", "pmmf_factor_blockdiag", "pmmf_factor_batched", "pmmf_get_batch",
            "pmmf_get_precision_stats", "pmmf_set_tuning", "pmmf_clear_tuning",
-           "pmmf_solve_precond_sym"]
+           "pmmf_solve_precond_sym", "pmmf_block_angle_grad"]
 
 _lib = None
 
@@ -121,6 +121,8 @@ def load(path: str = LIB_PATH):
     L.pmmf_get_angles.argtypes = [vp, vp, vp]
     L.pmmf_set_angles.restype = i32
     L.pmmf_set_angles.argtypes = [vp, vp, vp]
+    L.pmmf_block_angle_grad.restype = i32
+    L.pmmf_block_angle_grad.argtypes = [vp, vp, vp, vp]
     L.pmmf_set_h.restype = i32
     L.pmmf_set_h.argtypes = [vp, vp, vp, vp]
     L.pmmf_factor_blockdiag.restype = i32
@@ -288,6 +290,10 @@ def pmmf_set_angles(handle: int, theta, stream=None):
     _check(load().pmmf_set_angles(handle, _ptr(theta), _stream(stream)))
 
 
+def pmmf_block_angle_grad(handle: int, dO, dtheta, stream=None):
+    _check(load().pmmf_block_angle_grad(handle, _ptr(dO), _ptr(dtheta), _stream(stream)))
+
+
 def pmmf_set_h(handle: int, hdiag, core, stream=None):
     _check(load().pmmf_set_h(handle, _ptr(hdiag), _ptr(core), _stream(stream)))
 
@@ -435,11 +441,16 @@ class Factorization:
     # ---- differentiation (selections fixed)
 
     def angles(self):
-        """Every rotation's angle as a CUDA float64 tensor (stage, cluster, step order)."""
+        """Every rotation's angle as a CUDA float64 tensor (stage, cluster, step
+        order): [rotations] for k = 2, [rotations, k(k-1)/2] Givens angles of
+        each block for k >= 3."""
         import torch
-        th = torch.empty(max(self.info().rotations, 1), dtype=torch.float64, device="cuda")
+        nr = self.info().rotations
+        per = self.k * (self.k - 1) // 2 if self.k > 2 else 1
+        th = torch.empty(max(nr * per, 1), dtype=torch.float64, device="cuda")
         pmmf_get_angles(self.handle, th)
-        return th[:self.info().rotations]
+        th = th[:nr * per]
+        return th.reshape(nr, per) if self.k > 2 else th
 
     def h_tensors(self):
         """(hdiag, core) as CUDA float64 tensors."""
@@ -456,9 +467,10 @@ class Factorization:
                        None if core is None else core.contiguous())
 
     def backward(self, op: int, x, g):
-        """Gradients of sum(g * op(x)): dict with dx, dtheta (k = 2) or dO
-        (k >= 3: [rotations, k * k], block entry (a, b) at a * kk + b), dhdiag,
-        dcore."""
+        """Gradients of sum(g * op(x)): dict with dx, dtheta, dhdiag, dcore; for
+        k >= 3 also dO ([rotations, k * k], block entry (a, b) at a * kk + b),
+        and dtheta is then [rotations, k(k-1)/2] for the Givens angles of
+        angles()."""
         import torch
         assert x.is_cuda and x.dtype == torch.float64 and x.shape == g.shape
         x, g = x.contiguous(), g.contiguous()
@@ -475,6 +487,10 @@ class Factorization:
                             out["dhdiag"], out["dcore"])
         if self.k > 2:
             out["dO"] = out.pop("dtheta")[:i.rotations * per].reshape(i.rotations, per)
+            pa = self.k * (self.k - 1) // 2
+            dth = torch.empty(max(i.rotations * pa, 1), dtype=torch.float64, device="cuda")
+            pmmf_block_angle_grad(self.handle, out["dO"].contiguous(), dth)
+            out["dtheta"] = dth[:i.rotations * pa].reshape(i.rotations, pa)
         else:
             out["dtheta"] = out["dtheta"][:i.rotations]
         return out

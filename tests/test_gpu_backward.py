@@ -131,3 +131,43 @@ def test_autograd_gradcheck(op):
     x = torch.from_numpy(np.random.default_rng(1).standard_normal((a.n, 2))).cuda().requires_grad_(True)
     fn = lambda x_, t_, h_, c_: P.pmmf_operator(g, x_, t_, h_, c_, op)
     assert torch.autograd.gradcheck(fn, (x, th, hd, core), eps=1e-6, atol=1e-7, rtol=1e-5)
+
+
+@gpu
+def test_kpoint_angles_against_oracle():
+    """k >= 3 angle parameterisation on the GPU: every block's Givens angles
+    equal the oracle's decomposition of the same block, set(get()) leaves the
+    operator unchanged, and dL/dtheta equals the oracle's chain rule applied
+    to the oracle's dL/dO."""
+    import torch
+    from oracle import oracle as O
+    a = I.knn_laplacian(1200, seed=9)
+    g, o = factor_both(a, k=3, eta=0.5, cluster_size=80, core_size=50, seed=5)
+    assert_same_factorization(g, o)
+    th = g.angles().cpu().numpy()
+    blocks = np.concatenate([s.rot_O for s in o.stages])
+    kks = np.concatenate([s.rot_k for s in o.stages])
+    want_th, want_D = [], []
+    for t in range(len(kks)):
+        kk = int(kks[t])
+        w, d = O.block_angles(blocks[t, :kk * kk].reshape(kk, kk))
+        want_th.append(np.pad(w, (0, 3 - len(w))))
+        want_D.append(d)
+    np.testing.assert_allclose(th, np.array(want_th), rtol=0, atol=1e-13)
+    x = np.random.default_rng(0).standard_normal((a.n, 2))
+    xd = torch.from_numpy(x).cuda()
+    y0 = g.apply(0, xd).cpu().numpy()
+    g.set_parameters(theta=torch.from_numpy(th.ravel()).cuda())
+    y1 = g.apply(0, xd).cpu().numpy()
+    np.testing.assert_allclose(y1, y0, rtol=0, atol=1e-13 * np.abs(y0).max())
+    gy = np.random.default_rng(1).standard_normal((a.n, 2))
+    got = g.backward(0, xd, torch.from_numpy(gy).cuda())
+    want = o.apply_grad(0, x, gy)
+    dth = got["dtheta"].cpu().numpy()
+    ref = []
+    for t in range(len(kks)):
+        kk = int(kks[t])
+        r = O.block_angle_grad(want_th[t][:kk * (kk - 1) // 2], want_D[t],
+                               want["dO"][t, :kk * kk].reshape(kk, kk))
+        ref.append(np.pad(r, (0, 3 - len(r))))
+    _close(dth, np.array(ref), "dtheta (k = 3)")

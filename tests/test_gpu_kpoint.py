@@ -67,12 +67,19 @@ def test_batch_k3_matches_oracle():
         assert np.array_equal(core[b, :d, :d], o.core)
 
 
-def test_angles_reject_kpoint():
-    """k-point blocks have no single angle: get_angles is UNSUPPORTED (their
-    gradient is taken with respect to the block entries)."""
+def test_angle_entry_points_reject_what_they_do_not_cover():
+    """The block-angle chain rule is for k >= 3 (k = 2 rotations are angles
+    already); a batch handle has no angle parameterisation."""
+    import torch
     pm = gpu_lib()
     a = I.knn_laplacian(300, seed=1)
-    g = pm.factor(a, k=3, eta=0.5, cluster_size=64, core_size=20, seed=0)
+    g2 = pm.factor(a, k=2, eta=0.5, cluster_size=64, core_size=20, seed=0)
+    z = torch.zeros(16, dtype=torch.float64, device="cuda")
     with pytest.raises(pm.PmmfError) as e:
-        g.angles()
+        pm.pmmf_block_angle_grad(g2.handle, z, z)
+    assert e.value.status == pm.ERR_UNSUPPORTED
+    mats = I.er_laplacian_batch(3, lo=20, hi=40, seed=1)
+    gb = pm.factor_batched(mats, k=3, eta=0.5, core_size=8, seed=0)
+    with pytest.raises(pm.PmmfError) as e:
+        gb.angles()
     assert e.value.status == pm.ERR_UNSUPPORTED
