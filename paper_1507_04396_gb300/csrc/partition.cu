@@ -99,14 +99,35 @@ __global__ void k_compact_order(const int32_t *morder, int64_t n, const int32_t 
 }
 
 // Initial centroids: chunk t holds Morton-order positions [floor(t s/m), floor((t+1) s/m)).
+// Chunk t holds Morton positions r with t = ((r + 1) m - 1) / s (contiguous
+// and nondecreasing in r): each warp sums its lanes' points per chunk first
+// (segments are runs of lanes) and one lane per segment adds the total.
 __global__ void k_chunk_sums(const int32_t *amorder, int64_t s, int64_t m, const int32_t *q,
                              int dim, unsigned long long *sum, unsigned long long *cnt) {
-    for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < s;
-         r += (int64_t)gridDim.x * blockDim.x) {
-        int64_t t = ((r + 1) * m - 1) / s;
-        int32_t g = amorder[r];
-        for (int d = 0; d < dim; ++d) atomicAdd(&sum[t * dim + d], (unsigned long long)q[(int64_t)g * dim + d]);
-        atomicAdd(&cnt[t], 1ull);
+    const int lane = threadIdx.x & 31;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t r0 = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); r0 < s; r0 += stride) {
+        const int64_t r = r0 + lane;
+        const bool in = r < s;
+        const int64_t t = in ? ((r + 1) * m - 1) / s : -1 - lane;
+        const int32_t g = in ? amorder[r] : 0;
+        unsigned long long v[3], c = in ? 1ull : 0ull;
+        for (int d = 0; d < dim; ++d) v[d] = in ? (unsigned long long)q[(int64_t)g * dim + d] : 0ull;
+        for (int o = 1; o < 32; o <<= 1) {
+            const int64_t to = __shfl_down_sync(0xffffffffu, t, o);
+            const unsigned long long co = __shfl_down_sync(0xffffffffu, c, o);
+            unsigned long long vo[3];
+            for (int d = 0; d < dim; ++d) vo[d] = __shfl_down_sync(0xffffffffu, v[d], o);
+            if (lane + o < 32 && to == t) {
+                c += co;
+                for (int d = 0; d < dim; ++d) v[d] += vo[d];
+            }
+        }
+        const int64_t tp = __shfl_up_sync(0xffffffffu, t, 1);
+        if (in && (lane == 0 || tp != t)) {
+            for (int d = 0; d < dim; ++d) atomicAdd(&sum[t * dim + d], v[d]);
+            atomicAdd(&cnt[t], c);
+        }
     }
 }
 
@@ -156,20 +177,39 @@ __global__ void k_assign(const int32_t *act, int64_t s, const int32_t *q, const 
 // centroids are recomputed (as k_centroids), with a grid-wide barrier between
 // the phases.  Integer sums, so the result is independent of the order of the
 // atomics.
+// One grid barrier per iteration: the sums rotate through three buffers (the
+// one being accumulated, the previous iteration's, which every block turns
+// into the centroids in its own shared memory, and the next one, zeroed
+// meanwhile; sum and cnt hold 3 m DIM and 3 m entries, buffer 0 zero on
+// entry).  The last iteration's counts are in buffer (iters - 1) % 3.
 template <int DIM>
-__global__ void k_lloyd(const int32_t *act, int64_t s, const int32_t *q, int32_t *cen, int64_t m,
-                        int iters, int32_t *label, unsigned long long *sum,
+__global__ void k_lloyd(const int32_t *act, int64_t s, const int32_t *q, const int32_t *cen,
+                        int64_t m, int iters, int32_t *label, unsigned long long *sum,
                         unsigned long long *cnt) {
     namespace cg = cooperative_groups;
     cg::grid_group grid = cg::this_grid();
     extern __shared__ int32_t sc[];
     const int64_t gt = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t gs = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t t = threadIdx.x; t < m * DIM; t += blockDim.x) sc[t] = cen[t];
     for (int it = 0; it < iters; ++it) {
-        for (int64_t t = gt; t < m * DIM; t += gs) sum[t] = 0ull;
-        for (int64_t t = gt; t < m; t += gs) cnt[t] = 0ull;
-        for (int64_t t = threadIdx.x; t < m * DIM; t += blockDim.x) sc[t] = cen[t];
-        grid.sync();
+        unsigned long long *sacc = sum + (int64_t)(it % 3) * m * DIM, *cacc = cnt + (int64_t)(it % 3) * m;
+        unsigned long long *snext = sum + (int64_t)((it + 1) % 3) * m * DIM, *cnext = cnt + (int64_t)((it + 1) % 3) * m;
+        if (it + 1 < iters) {
+            for (int64_t t = gt; t < m * DIM; t += gs) snext[t] = 0ull;
+            for (int64_t t = gt; t < m; t += gs) cnext[t] = 0ull;
+        }
+        if (it > 0) {
+            // the previous iteration's centroids (an empty cluster keeps its own)
+            const unsigned long long *sp = sum + (int64_t)((it + 2) % 3) * m * DIM;
+            const unsigned long long *cp = cnt + (int64_t)((it + 2) % 3) * m;
+            for (int64_t t = threadIdx.x; t < m; t += blockDim.x) {
+                const unsigned long long c = cp[t];
+                if (c == 0) continue;
+                for (int d = 0; d < DIM; ++d) sc[t * DIM + d] = (int32_t)((sp[t * DIM + d] + c / 2) / c);
+            }
+        }
+        __syncthreads();
         for (int64_t r = gt; r < s; r += gs) {
             const int32_t g = act[r];
             int32_t p[DIM];
@@ -185,18 +225,10 @@ __global__ void k_lloyd(const int32_t *act, int64_t s, const int32_t *q, int32_t
                 if (dd < best) { best = dd; bt = t; }
             }
             label[r] = (int32_t)bt;
-            for (int d = 0; d < DIM; ++d) atomicAdd(&sum[bt * DIM + d], (unsigned long long)p[d]);
-            atomicAdd(&cnt[bt], 1ull);
+            for (int d = 0; d < DIM; ++d) atomicAdd(&sacc[bt * DIM + d], (unsigned long long)p[d]);
+            atomicAdd(&cacc[bt], 1ull);
         }
         grid.sync();
-        if (it + 1 < iters) {
-            for (int64_t t = gt; t < m; t += gs) {
-                const unsigned long long c = cnt[t];
-                if (c == 0) continue;
-                for (int d = 0; d < DIM; ++d) cen[t * DIM + d] = (int32_t)((sum[t * DIM + d] + c / 2) / c);
-            }
-            grid.sync();
-        }
     }
 }
 
@@ -522,21 +554,27 @@ pmmf_status partition_stage(const PartitionIn &in, int64_t m, int iters, StageCl
     PMMF_CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
     PMMF_CUDA_TRY(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev));
     PMMF_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, lloyd, 256, sh));
+    DBuf<unsigned long long> lsum, lcnt;
+    const unsigned long long *fcnt = cnt.p;   // the last assignment's counts
     if (coop && per_sm > 0) {
         const int64_t want = (s + 255) / 256;
         const unsigned g = (unsigned)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)nsm * per_sm));
+        PMMF_TRY(lsum.zeros(3 * m * dim, st));
+        PMMF_TRY(lcnt.zeros(3 * m, st));
         const int32_t *a_act = in.act;
         const int32_t *a_q = in.q;
-        int32_t *a_cen = cen.p, *a_label = label.p;
+        const int32_t *a_cen = cen.p;
+        int32_t *a_label = label.p;
         int64_t a_s = s, a_m = m;
         int a_it = iters;
-        unsigned long long *a_sum = sum.p, *a_cnt = cnt.p;
+        unsigned long long *a_sum = lsum.p, *a_cnt = lcnt.p;
         void *args[] = {&a_act, &a_s, &a_q, &a_cen, &a_m, &a_it, &a_label, &a_sum, &a_cnt};
         prof_begin(KF_PARTITION, st);
         PMMF_CUDA_TRY(cudaLaunchCooperativeKernel(lloyd, dim3(g), dim3(256), args, sh, st));
         prof_end(KF_PARTITION, st, (double)iters * (double)s * (8.0 + 4.0 * dim),
                  3.0 * dim * (double)iters * (double)s * (double)m);
         PMMF_TRY(launched("lloyd"));
+        fcnt = lcnt.p + (int64_t)((iters - 1) % 3) * m;
     } else {
     auto assign = dim == 1 ? (void *)k_assign<1> : dim == 2 ? (void *)k_assign<2> : (void *)k_assign<3>;
     if (sh > 48 * 1024)
@@ -559,7 +597,7 @@ pmmf_status partition_stage(const PartitionIn &in, int64_t m, int iters, StageCl
         }
     }
     }
-    return clusters_from_labels(in, label, cnt.p, m, out, st);
+    return clusters_from_labels(in, label, fcnt, m, out, st);
 }
 
 pmmf_status schedule_stage(const int64_t *coff, int64_t mm, const int64_t *mm_dev, int64_t s,
