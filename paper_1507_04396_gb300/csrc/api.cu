@@ -79,6 +79,32 @@ pmmf_status exact_nnz(Csr &A, cudaStream_t st) {
     return PMMF_OK;
 }
 
+// A second stream on which the next stage's clustering runs while the current
+// stage's update runs on the caller's stream.  Its destructor waits for the
+// stream, so declare it after the buffers the stream writes: it is then
+// destroyed (and synchronized) before they are freed.
+struct SideStream {
+    cudaStream_t s = nullptr;
+    cudaEvent_t fork = nullptr, join = nullptr;
+    SideStream() = default;
+    SideStream(const SideStream &) = delete;
+    SideStream &operator=(const SideStream &) = delete;
+    ~SideStream() {
+        if (s) {
+            cudaStreamSynchronize(s);
+            cudaStreamDestroy(s);
+        }
+        if (fork) cudaEventDestroy(fork);
+        if (join) cudaEventDestroy(join);
+    }
+    pmmf_status init() {
+        PMMF_CUDA_TRY(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+        PMMF_CUDA_TRY(cudaEventCreateWithFlags(&fork, cudaEventDisableTiming));
+        PMMF_CUDA_TRY(cudaEventCreateWithFlags(&join, cudaEventDisableTiming));
+        return PMMF_OK;
+    }
+};
+
 void set_pool_threshold() {
     static bool done = false;
     if (done) return;
@@ -291,29 +317,47 @@ pmmf_status factor_impl(const pmmf_matrix *A, const pmmf_params *prm, pmmf_handl
     int64_t p = 0;
     // device status bits of every stage, read once after the loop
     PMMF_CUDA_TRY(cudaMemsetAsync(status.p, 0, sizeof(unsigned), st));
-    while (s > prm->core_size && (prm->max_stages <= 0 || p < prm->max_stages)) {
+    // clusters of stage pp (active set actp, positions posp) into cls; cl/loc
+    // receive each active coordinate's cluster and local index
+    auto cluster_stage = [&](int64_t pp, int64_t ss, const int32_t *actp, const int32_t *posp,
+                             int32_t *clp, int32_t *locp, StageClusters &cls,
+                             cudaStream_t sx) -> pmmf_status {
+        int64_t m = (ss + prm->cluster_size / 2) / prm->cluster_size;
+        if (m < 1 || !geo) m = 1;
+        if (m > 1 || (pp == 1 && dlab)) {
+            PartitionIn in;
+            in.n = n;
+            in.s = ss;
+            in.dim = dim;
+            in.q = q.p;
+            in.morder = morder.p;
+            in.pos = posp;
+            in.act = actp;
+            in.cl = clp;
+            in.loc = locp;
+            if (pp == 1 && dlab) return partition_from_labels(in, dlab, prm->num_labels, cls, sx);
+            return partition_stage(in, m, iters, cls, sx);
+        }
+        return one_cluster(actp, ss, cls, clp, locp, sx);
+    };
+    auto more_stages = [&](int64_t ss, int64_t pp) {
+        return ss > prm->core_size && (prm->max_stages <= 0 || pp < prm->max_stages);
+    };
+    // the next stage's positions and cluster maps (swapped in after each stage)
+    DBuf<int32_t> posN, clN, locN;
+    PMMF_TRY(posN.alloc(n, st));
+    PMMF_TRY(clN.alloc(n, st));
+    PMMF_TRY(locN.alloc(n, st));
+    StageClusters next_cls;
+    SideStream side;
+    PMMF_TRY(side.init());
+    if (more_stages(s, p)) PMMF_TRY(cluster_stage(1, s, act.p, pos.p, cl.p, loc.p, next_cls, st));
+    while (more_stages(s, p)) {
         ++p;
         h->st.emplace_back();
         StageData &S = h->st.back();
         S.s = s;
-        int64_t m = (s + prm->cluster_size / 2) / prm->cluster_size;
-        if (m < 1 || !geo) m = 1;
-        if (m > 1 || (p == 1 && dlab)) {
-            PartitionIn in;
-            in.n = n;
-            in.s = s;
-            in.dim = dim;
-            in.q = q.p;
-            in.morder = morder.p;
-            in.pos = pos.p;
-            in.act = act.p;
-            in.cl = cl.p;
-            in.loc = loc.p;
-            if (p == 1 && dlab) PMMF_TRY(partition_from_labels(in, dlab, prm->num_labels, S.cls, st));
-            else PMMF_TRY(partition_stage(in, m, iters, S.cls, st));
-        } else {
-            PMMF_TRY(one_cluster(act.p, s, S.cls, cl.p, loc.p, st));
-        }
+        S.cls = std::move(next_cls);
         // one readback per stage for the schedule: rotations, the one-cluster
         // fallback, the largest cluster and the Gram blocks' total size
         int64_t sched[5] = {0, 0, 0, 0, 0};
@@ -333,18 +377,60 @@ pmmf_status factor_impl(const pmmf_matrix *A, const pmmf_params *prm, pmmf_handl
         S.rot.K = prm->k;
         PMMF_TRY(gram_and_select(cur, act.p, pos.p, cl.p, loc.p, S.cls, S.cmax, prm->seed, p, S.rot,
                                  elimflag.p, st, nullptr, nullptr, status.p, sched[3]));
+        Survivors sv;
+        PMMF_TRY(survivors_stage(act.p, s, S.nrot, elimflag.p, p, sv, st));
+        const int64_t s2 = sv.count;
+        // the next stage's positions and clusters depend only on the
+        // survivors: they run on the side stream while the update runs here
+        const bool next = more_stages(s2, p);
+        cudaStream_t ns = st;
+        if (next) {
+            ns = side.s;
+            PMMF_CUDA_TRY(cudaEventRecord(side.fork, st));
+            PMMF_CUDA_TRY(cudaStreamWaitEvent(ns, side.fork, 0));
+        }
+        {
+            // (on failure, wait for the side stream: it may still read sv)
+            pmmf_status ps = cudaMemsetAsync(posN.p, 0xFF, sizeof(int32_t) * (size_t)n, ns) == cudaSuccess
+                                 ? PMMF_OK
+                                 : fail(PMMF_ERR_CUDA, "position reset failed");
+            if (ps == PMMF_OK) ps = set_positions(sv.act.p, s2, posN.p, ns);
+            if (ps == PMMF_OK && next)
+                ps = cluster_stage(p + 1, s2, sv.act.p, posN.p, clN.p, locN.p, next_cls, ns);
+            if (ps == PMMF_OK && next && cudaEventRecord(side.join, ns) != cudaSuccess)
+                ps = fail(PMMF_ERR_CUDA, "event record failed");
+            if (ps != PMMF_OK) {
+                cudaStreamSynchronize(side.s);
+                return ps;
+            }
+        }
         UpdateOut up;
-        PMMF_TRY(update_stage(cur, act.p, n, pos.p, cl.p, loc.p, S.cls, S.cmax, S.rot,
-                              elimflag.p, p, h->hdiag.p, contribs.p + (p - 1), up, status.p, st));
-        PMMF_TRY(S.nnz_d.alloc(1, st));
-        PMMF_CUDA_TRY(cudaMemcpyAsync(S.nnz_d.p, up.next.rowptr.p + up.next.rows, sizeof(int64_t),
-                                      cudaMemcpyDeviceToDevice, st));
-        // next stage's row positions
-        PMMF_CUDA_TRY(cudaMemsetAsync(pos.p, 0xFF, sizeof(int32_t) * (size_t)n, st));
-        PMMF_TRY(set_positions(up.act.p, up.next.rows, pos.p, st));
-        s = up.next.rows;
+        pmmf_status us = update_stage(cur, act.p, n, pos.p, cl.p, loc.p, S.cls, S.cmax, S.rot,
+                                      elimflag.p, p, sv, h->hdiag.p, contribs.p + (p - 1), up,
+                                      status.p, st);
+        if (us == PMMF_OK) us = S.nnz_d.alloc(1, st);
+        if (us == PMMF_OK &&
+            cudaMemcpyAsync(S.nnz_d.p, up.next.rowptr.p + up.next.rows, sizeof(int64_t),
+                            cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+            us = fail(PMMF_ERR_CUDA, "stage nnz copy failed");
+        if (us != PMMF_OK) {
+            // the side stream still reads this stage's survivors
+            cudaStreamSynchronize(side.s);
+            return us;
+        }
+        if (next) {
+            PMMF_CUDA_TRY(cudaStreamWaitEvent(st, side.join, 0));
+            // made on the side stream, used and freed on this one from here
+            next_cls.coff.st = st;
+            next_cls.members.st = st;
+            next_cls.count_d.st = st;
+        }
+        std::swap(pos, posN);
+        std::swap(cl, clN);
+        std::swap(loc, locN);
+        s = s2;
         cur = std::move(up.next);
-        act = std::move(up.act);
+        act = std::move(sv.act);
         if (prm->record_stages) {
             PMMF_TRY(exact_nnz(cur, st));
             S.recorded.rows = cur.rows;
@@ -747,9 +833,11 @@ pmmf_status factor_batch_impl(const pmmf_matrix *A, const std::vector<int64_t> &
                                  elimflag.p, st, order_d.p, useed_d.p, status.p));
         DBuf<double> ccl;
         PMMF_TRY(ccl.zeros(m, st));
+        Survivors sv;
+        PMMF_TRY(survivors_stage(act.p, s, S.nrot, elimflag.p, p, sv, st));
         UpdateOut up;
         PMMF_TRY(update_stage(cur, act.p, n, pos.p, cl.p, loc.p, S.cls, S.cmax, S.rot, elimflag.p,
-                              p, h->hdiag.p, contrib1.p, up, status.p, st, ccl.p));
+                              p, sv, h->hdiag.p, contrib1.p, up, status.p, st, ccl.p));
         {
             unsigned hs = 0;
             std::vector<int32_t> nl((size_t)m);
@@ -774,10 +862,10 @@ pmmf_status factor_batch_impl(const pmmf_matrix *A, const std::vector<int64_t> &
         }
         S.nnz_after = up.next.nnz;
         PMMF_CUDA_TRY(cudaMemsetAsync(pos.p, 0xFF, sizeof(int32_t) * (size_t)n, st));
-        PMMF_TRY(set_positions(up.act.p, up.next.rows, pos.p, st));
+        PMMF_TRY(set_positions(sv.act.p, up.next.rows, pos.p, st));
         s = up.next.rows;
         cur = std::move(up.next);
-        act = std::move(up.act);
+        act = std::move(sv.act);
     }
     h->ncore = ncore;
     double tot = 0.0;

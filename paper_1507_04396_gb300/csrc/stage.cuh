@@ -114,15 +114,24 @@ pmmf_status select_kpoint(const StageClusters &cls, int64_t cmax, const int64_t 
 // compaction to the surviving coordinates.
 struct UpdateOut {
     Csr next;                 // A_p[S_p, S_p]
-    DBuf<int32_t> act;        // S_p ascending
     double *contrib = nullptr;   // device accumulator (added to)
 };
+// The survivors S_p of a stage (one elimination per rotation, so nrot fewer
+// than the active rows): flag per active row, their new row numbers (an
+// exclusive scan of the flags) and S_p ascending.
+struct Survivors {
+    DBuf<int32_t> flag, act;
+    DBuf<int64_t> newrow;
+    int64_t count = 0;
+};
+pmmf_status survivors_stage(const int32_t *act, int64_t s, int64_t nrot, const int32_t *elimflag,
+                            int64_t stage, Survivors &sv, cudaStream_t st);
 pmmf_status update_stage(const Csr &A, const int32_t *act, int64_t n, const int32_t *pos,
                          const int32_t *cl, const int32_t *loc, const StageClusters &cls,
                          int64_t cmax, const StageRotations &rot, const int32_t *elimflag,
-                         int64_t stage, double *hdiag, double *contrib, UpdateOut &out,
-                         unsigned *status, cudaStream_t st, double *contrib_cl = nullptr);
-// (the survivors are rot.nrot fewer than the active rows: one elimination per rotation)
+                         int64_t stage, const Survivors &sv, double *hdiag, double *contrib,
+                         UpdateOut &out, unsigned *status, cudaStream_t st,
+                         double *contrib_cl = nullptr);
 
 pmmf_status set_positions(const int32_t *act, int64_t s, int32_t *pos, cudaStream_t st);
 pmmf_status extract_core(const Csr &A, const int32_t *pos, int64_t s, double *core, double *hdiag,

@@ -445,11 +445,25 @@ pmmf_status set_positions(const int32_t *act, int64_t s, int32_t *pos, cudaStrea
     return launched("set_pos");
 }
 
+pmmf_status survivors_stage(const int32_t *act, int64_t s, int64_t nrot, const int32_t *elimflag,
+                            int64_t stage, Survivors &sv, cudaStream_t st) {
+    PMMF_TRY(sv.flag.alloc(s, st));
+    PMMF_TRY(sv.newrow.alloc(s + 1, st));
+    sv.count = s - nrot;
+    PMMF_TRY(sv.act.alloc(sv.count, st));
+    if (s <= 0) return PMMF_OK;
+    k_survivors<<<grid_for(s, 256), 256, 0, st>>>(act, s, elimflag, (int32_t)stage, sv.flag.p);
+    PMMF_TRY(launched("survivors"));
+    PMMF_TRY(scan_i32_to_i64(sv.flag.p, sv.newrow.p, s, st));
+    k_compact_act<<<grid_for(s, 256), 256, 0, st>>>(act, s, sv.flag.p, sv.newrow.p, sv.act.p);
+    return launched("compact_act");
+}
+
 pmmf_status update_stage(const Csr &A, const int32_t *act, int64_t n, const int32_t *pos,
                          const int32_t *cl, const int32_t *loc, const StageClusters &cls,
                          int64_t cmax, const StageRotations &rot, const int32_t *elimflag,
-                         int64_t stage, double *hdiag, double *contrib, UpdateOut &out,
-                         unsigned *status, cudaStream_t st, double *contrib_cl) {
+                         int64_t stage, const Survivors &sv, double *hdiag, double *contrib,
+                         UpdateOut &out, unsigned *status, cudaStream_t st, double *contrib_cl) {
     (void)n;
     const int64_t s = A.rows;
     RowArgs a{};
@@ -504,15 +518,7 @@ pmmf_status update_stage(const Csr &A, const int32_t *act, int64_t n, const int3
     W.rowptr = std::move(wrp);
     // W's row r holds wrp[r] .. wcur[r] - 1 (the written part of its capacity)
 
-    // survivors and their new rows
-    DBuf<int32_t> flag;
-    DBuf<int64_t> newrow;
-    PMMF_TRY(flag.alloc(s, st));
-    PMMF_TRY(newrow.alloc(s + 1, st));
-    k_survivors<<<grid_for(s, 256), 256, 0, st>>>(act, s, elimflag, (int32_t)stage, flag.p);
-    PMMF_TRY(launched("survivors"));
-    PMMF_TRY(scan_i32_to_i64(flag.p, newrow.p, s, st));
-    const int64_t s2 = s - rot.nrot;   // one elimination per rotation
+    const int64_t s2 = sv.count;       // one elimination per rotation
 
     // pass 2: A_p = W Q^T with accounting and compaction
     out.next.rows = s2;
@@ -524,7 +530,7 @@ pmmf_status update_stage(const Csr &A, const int32_t *act, int64_t n, const int3
     a.rend = wcur.p;
     a.ci = W.col.p;
     a.v = W.val.p;
-    a.newrow = newrow.p;
+    a.newrow = sv.newrow.p;
     a.ocnt = caprp.p;
     a.maxlen = maxlen.p;
     PMMF_TRY(launch_rows<P2_COUNT>(a, wnnz, 0, st));
@@ -556,10 +562,7 @@ pmmf_status update_stage(const Csr &A, const int32_t *act, int64_t n, const int3
                                                                 tval.p, out.next.col.p, out.next.val.p);
         PMMF_TRY(launched("compact_rows"));
     }
-
-    PMMF_TRY(out.act.alloc(s2, st));
-    k_compact_act<<<grid_for(s, 256), 256, 0, st>>>(act, s, flag.p, newrow.p, out.act.p);
-    return launched("compact_act");
+    return PMMF_OK;
 }
 
 pmmf_status extract_core(const Csr &A, const int32_t *pos, int64_t s, double *core, double *hdiag,
