@@ -383,12 +383,17 @@ pmmf_status pmmf_get_stage_matrix(const pmmf_handle *f, int p, int64_t *rowptr_n
  * per block of the blocked-update row kernel, 1..8), PMMF_TUNE_GRAM_WARPS
  * (warps per block of the Gram kernel, 1..8), PMMF_TUNE_SELECT_WARPS (warps
  * per cluster of the k = 2 rotation search, 8 or 16; without a setting the
- * search uses 8; clusters above 512 coordinates always use 16).  A value
+ * search uses 8; clusters above 512 coordinates always use 16),
+ * PMMF_TUNE_PASS1_ESTIMATE (the first stage allocates the blocked update's
+ * intermediate for this many times the input's entries, 1..32, default 8;
+ * later stages scale the previous stage's size; a short estimate costs a
+ * second pass, never a wrong result; use max_size 1).  A value
  * applies to launches whose largest cluster has at most max_size coordinates
  * and no smaller bucket matches; shared-memory limits still halve the row and
  * Gram warps when needed.  Process wide; INVALID_ARG for an unknown param or
  * a value outside 1..32 (outside {8, 16} for the search). */
-enum { PMMF_TUNE_ROWS_WARPS = 0, PMMF_TUNE_GRAM_WARPS = 1, PMMF_TUNE_SELECT_WARPS = 2 };
+enum { PMMF_TUNE_ROWS_WARPS = 0, PMMF_TUNE_GRAM_WARPS = 1, PMMF_TUNE_SELECT_WARPS = 2,
+       PMMF_TUNE_PASS1_ESTIMATE = 3 };
 pmmf_status pmmf_set_tuning(int param, int64_t max_size, int value);
 void pmmf_clear_tuning(void);
 

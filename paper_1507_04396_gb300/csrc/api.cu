@@ -349,6 +349,7 @@ pmmf_status factor_impl(const pmmf_matrix *A, const pmmf_params *prm, pmmf_handl
     PMMF_TRY(clN.alloc(n, st));
     PMMF_TRY(locN.alloc(n, st));
     StageClusters next_cls;
+    int64_t w_hint = 0;
     SideStream side;
     PMMF_TRY(side.init());
     if (more_stages(s, p)) PMMF_TRY(cluster_stage(1, s, act.p, pos.p, cl.p, loc.p, next_cls, st));
@@ -405,6 +406,7 @@ pmmf_status factor_impl(const pmmf_matrix *A, const pmmf_params *prm, pmmf_handl
             }
         }
         UpdateOut up;
+        up.w_hint = w_hint;
         pmmf_status us = update_stage(cur, act.p, n, pos.p, cl.p, loc.p, S.cls, S.cmax, S.rot,
                                       elimflag.p, p, sv, h->hdiag.p, contribs.p + (p - 1), up,
                                       status.p, st);
@@ -425,6 +427,9 @@ pmmf_status factor_impl(const pmmf_matrix *A, const pmmf_params *prm, pmmf_handl
             next_cls.members.st = st;
             next_cls.count_d.st = st;
         }
+        // pass 1's output for the next stage, scaled from this one with a 2x margin
+        w_hint = (int64_t)(2.0 * (double)up.w_nnz * (double)up.next.nnz /
+                           (double)std::max<int64_t>(cur.nnz, 1)) + 1024;
         std::swap(pos, posN);
         std::swap(cl, clN);
         std::swap(loc, locN);

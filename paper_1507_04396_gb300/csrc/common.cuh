@@ -59,7 +59,10 @@ inline unsigned grid_for(int64_t items, int per_block, int64_t cap = 152 * 64) {
 // Launch parameters that an offline sweep may set per cluster-size bucket
 // (pmmf_set_tuning); tuned(param, size, fallback) returns the value of the
 // smallest bucket whose bound is >= size, else fallback.
-enum TuneParam : int { TUNE_ROWS_WARPS = 0, TUNE_GRAM_WARPS = 1, TUNE_SELECT_WARPS = 2, TUNE_COUNT = 3 };
+enum TuneParam : int {
+    TUNE_ROWS_WARPS = 0, TUNE_GRAM_WARPS = 1, TUNE_SELECT_WARPS = 2, TUNE_PASS1_ESTIMATE = 3,
+    TUNE_COUNT = 4
+};
 int tuned(int param, int64_t size, int fallback);
 
 // ---------------------------------------------------------------- profiling

@@ -115,6 +115,8 @@ pmmf_status select_kpoint(const StageClusters &cls, int64_t cmax, const int64_t 
 struct UpdateOut {
     Csr next;                 // A_p[S_p, S_p]
     double *contrib = nullptr;   // device accumulator (added to)
+    int64_t w_hint = 0;       // in: estimate of pass 1's output (0: 8 nnz(A))
+    int64_t w_nnz = 0;        // out: pass 1's output size (upper bound of V's entries)
 };
 // The survivors S_p of a stage (one elimination per rotation, so nrot fewer
 // than the active rows): flag per active row, their new row numbers (an

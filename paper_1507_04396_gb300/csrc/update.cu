@@ -56,6 +56,9 @@ struct RowArgs {
     int64_t *wcur;             // W write cursors (WRITE)
     int32_t *wcol;
     double *wval;
+    const int64_t *wtotal;     // WRITE: W's entries (the scan's total) ...
+    int64_t wcap;              // ... must fit the allocation, else nothing is written
+    unsigned *wover;           // and this flag is set
     // pass 2
     const int32_t *elimflag;
     int32_t stage;
@@ -97,6 +100,10 @@ __global__ void __launch_bounds__(256, 4) k_rows(RowArgs a) {
     extern __shared__ double smem[];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const int wpb = blockDim.x >> 5;
+    if (MODE == P1_WRITE && *a.wtotal > a.wcap) {
+        if (threadIdx.x == 0 && blockIdx.x == 0) *a.wover = 1u;
+        return;
+    }
     const int64_t per_warp = rows_per_warp(a.cmax, a.outcap, MODE == P2_WRITE);
     double *dense = smem + per_warp * wib;
     uint32_t *tb = (uint32_t *)(dense + a.cmax);
@@ -500,22 +507,34 @@ pmmf_status update_stage(const Csr &A, const int32_t *act, int64_t n, const int3
     a.wcnt = wrp.p;
     PMMF_TRY(launch_rows<P1_COUNT>(a, A.nnz, 0, st));
     PMMF_TRY(scan_i64(wrp.p, wrp.p, s, st));
-    int64_t wnnz = 0;
-    PMMF_CUDA_TRY(cudaMemcpyAsync(&wnnz, wrp.p + s, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
-    PMMF_CUDA_TRY(cudaStreamSynchronize(st));
+    // W is allocated from an estimate, without waiting for the count: when the
+    // count exceeds it, pass 1 writes nothing, W's rows stay empty, and the
+    // size read with pass 2's below triggers a second, exact round
     Csr W;
     W.rows = s;
-    W.nnz = wnnz;
-    PMMF_TRY(W.col.alloc(wnnz, st));
-    PMMF_TRY(W.val.alloc(wnnz, st));
+    int64_t wcap = out.w_hint > 0 ? out.w_hint
+                                  : (int64_t)tuned(TUNE_PASS1_ESTIMATE, 0, 8) * A.nnz + 1024;
+    DBuf<unsigned> wover;
+    PMMF_TRY(wover.zeros(1, st));
+    PMMF_TRY(W.col.alloc(wcap, st));
+    PMMF_TRY(W.val.alloc(wcap, st));
     PMMF_TRY(wcur.alloc(s + 1, st));
-    PMMF_CUDA_TRY(cudaMemcpyAsync(wcur.p, wrp.p, sizeof(int64_t) * (size_t)(s + 1),
-                                  cudaMemcpyDeviceToDevice, st));
-    a.wcur = wcur.p;
-    a.wcol = W.col.p;
-    a.wval = W.val.p;
-    PMMF_TRY(launch_rows<P1_WRITE>(a, A.nnz, wnnz, st));
-    W.rowptr = std::move(wrp);
+    auto pass1_write = [&]() -> pmmf_status {
+        PMMF_CUDA_TRY(cudaMemcpyAsync(wcur.p, wrp.p, sizeof(int64_t) * (size_t)(s + 1),
+                                      cudaMemcpyDeviceToDevice, st));
+        a.rp = A.rowptr.p;
+        a.rend = nullptr;
+        a.ci = A.col.p;
+        a.v = A.val.p;
+        a.wcur = wcur.p;
+        a.wcol = W.col.p;
+        a.wval = W.val.p;
+        a.wtotal = wrp.p + s;
+        a.wcap = wcap;
+        a.wover = wover.p;
+        return launch_rows<P1_WRITE>(a, A.nnz, wcap, st);
+    };
+    PMMF_TRY(pass1_write());
     // W's row r holds wrp[r] .. wcur[r] - 1 (the written part of its capacity)
 
     const int64_t s2 = sv.count;       // one elimination per rotation
@@ -523,22 +542,44 @@ pmmf_status update_stage(const Csr &A, const int32_t *act, int64_t n, const int3
     // pass 2: A_p = W Q^T with accounting and compaction
     out.next.rows = s2;
     DBuf<int64_t> caprp, acnt, maxlen;
-    PMMF_TRY(caprp.zeros(s2 + 1, st));
+    PMMF_TRY(caprp.alloc(s2 + 1, st));
     PMMF_TRY(acnt.zeros(s2 + 1, st));
-    PMMF_TRY(maxlen.zeros(1, st));
-    a.rp = W.rowptr.p;
-    a.rend = wcur.p;
-    a.ci = W.col.p;
-    a.v = W.val.p;
-    a.newrow = sv.newrow.p;
-    a.ocnt = caprp.p;
-    a.maxlen = maxlen.p;
-    PMMF_TRY(launch_rows<P2_COUNT>(a, wnnz, 0, st));
-    PMMF_TRY(scan_i64(caprp.p, caprp.p, s2, st));
-    int64_t hv[2] = {0, 0};
-    PMMF_CUDA_TRY(cudaMemcpyAsync(&hv[0], caprp.p + s2, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
-    PMMF_CUDA_TRY(cudaMemcpyAsync(&hv[1], maxlen.p, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
-    PMMF_CUDA_TRY(cudaStreamSynchronize(st));
+    PMMF_TRY(maxlen.alloc(1, st));
+    // hv: pass 2's capacity and longest row, W's exact size, pass 1's overflow
+    int64_t hv[4] = {0, 0, 0, 0};
+    auto pass2_count = [&]() -> pmmf_status {
+        PMMF_CUDA_TRY(cudaMemsetAsync(caprp.p, 0, sizeof(int64_t) * (size_t)(s2 + 1), st));
+        PMMF_CUDA_TRY(cudaMemsetAsync(maxlen.p, 0, sizeof(int64_t), st));
+        a.rp = wrp.p;
+        a.rend = wcur.p;
+        a.ci = W.col.p;
+        a.v = W.val.p;
+        a.newrow = sv.newrow.p;
+        a.ocnt = caprp.p;
+        a.maxlen = maxlen.p;
+        PMMF_TRY(launch_rows<P2_COUNT>(a, wcap, 0, st));
+        PMMF_TRY(scan_i64(caprp.p, caprp.p, s2, st));
+        unsigned ov = 0;
+        PMMF_CUDA_TRY(cudaMemcpyAsync(&hv[0], caprp.p + s2, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+        PMMF_CUDA_TRY(cudaMemcpyAsync(&hv[1], maxlen.p, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+        PMMF_CUDA_TRY(cudaMemcpyAsync(&hv[2], wrp.p + s, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+        PMMF_CUDA_TRY(cudaMemcpyAsync(&ov, wover.p, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
+        PMMF_CUDA_TRY(cudaStreamSynchronize(st));
+        hv[3] = ov;
+        return PMMF_OK;
+    };
+    PMMF_TRY(pass2_count());
+    if (hv[3]) {
+        // the estimate was short: W at its exact size, and pass 1's writes and
+        // pass 2's count again
+        wcap = hv[2];
+        PMMF_TRY(W.col.alloc(wcap, st));
+        PMMF_TRY(W.val.alloc(wcap, st));
+        PMMF_CUDA_TRY(cudaMemsetAsync(wover.p, 0, sizeof(unsigned), st));
+        PMMF_TRY(pass1_write());
+        PMMF_TRY(pass2_count());
+    }
+    out.w_nnz = hv[2];
     DBuf<int32_t> tcol;
     DBuf<double> tval;
     PMMF_TRY(tcol.alloc(hv[0], st));
@@ -548,7 +589,7 @@ pmmf_status update_stage(const Csr &A, const int32_t *act, int64_t n, const int3
     a.ocol = tcol.p;
     a.oval = tval.p;
     a.acnt = acnt.p;
-    PMMF_TRY(launch_rows<P2_WRITE>(a, wnnz, hv[0], st));
+    PMMF_TRY(launch_rows<P2_WRITE>(a, hv[2], hv[0], st));
     // exact row pointers, and the rows moved there; nnz is the capacity (an
     // upper bound), the exact count is rowptr[s2] on the device
     PMMF_TRY(out.next.rowptr.alloc(s2 + 1, st));

@@ -148,7 +148,7 @@ def load(path: str = LIB_PATH):
 
 
 TUNING_PATH = os.path.join(_HERE, "tuning.json")
-TUNE_PARAMS = {"rows_warps": 0, "gram_warps": 1, "select_warps": 2}
+TUNE_PARAMS = {"rows_warps": 0, "gram_warps": 1, "select_warps": 2, "pass1_estimate": 3}
 
 
 def apply_tuning(path: str) -> bool:

@@ -225,3 +225,20 @@ def _params_with_labels(pm, a, lab, num, kw):
                     co.ctypes.data, 3, pm.HOST, 0, 0, lab.ctypes.data, pm.HOST, num)
     _params_with_labels.keep = (keep, co, lab)
     return m, prm
+
+
+@gpu
+def test_short_pass1_estimate_retries_exactly():
+    """The blocked update allocates its intermediate from an estimate and
+    redoes the pass at the exact size when the estimate is short: with the
+    first-stage estimate forced to 1x the input the result is still the
+    oracle's, bit for bit."""
+    pm = gpu_lib()
+    L = pm.load()
+    a = I.knn_laplacian(3000, seed=5)
+    try:
+        assert L.pmmf_set_tuning(pm.TUNE_PARAMS["pass1_estimate"], 1, 1) == 0
+        g, o = factor_both(a, k=2, eta=0.5, cluster_size=150, core_size=60, seed=6)
+        assert_same_factorization(g, o)
+    finally:
+        pm.apply_tuning(pm.TUNING_PATH)
