@@ -439,7 +439,9 @@ constexpr int FP_WARPS = 4;
 constexpr int NCT = SEL_THREADS - 32 * FP_WARPS;
 
 // Barrier among the FP64 warps only (named barrier 1).
-__device__ __forceinline__ void fp_sync() { asm volatile("bar.sync 1, %0;" ::"n"(32 * FP_WARPS)); }
+__device__ __forceinline__ void fp_sync() {
+    asm volatile("bar.sync 1, %0;" ::"n"(32 * FP_WARPS) : "memory");
+}
 
 // Best of the per-warp candidates, computed by every warp in parallel.
 template <int NWARPS>
@@ -514,6 +516,8 @@ k_select_fast(const int64_t *coff, const int32_t *members, const int64_t *goff, 
     __shared__ double s_x[FP_WARPS];            // exchange among the FP64 warps
     __shared__ double s_wn[2][2];               // new weights of i, j by step parity
     __shared__ double s_survg[2], s_survm[2];   // by step parity
+    __shared__ int s_nx[4];                      // next step's i, j, a1, a2 (FP64 -> column warps)
+    __shared__ double s_nxg, s_nxm;              // and its G_ij, M_ij
 
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     const int ct = tid - 32 * FP_WARPS;         // column thread index (>= 0 in column warps)
@@ -714,79 +718,113 @@ k_select_fast(const int64_t *coff, const int32_t *members, const int64_t *goff, 
                 }
             }
             __syncthreads();
-            // ---- P2
+            // ---- P2.  Column warps: (A) score the candidates of the next
+            // pivot and publish each warp's best (barrier 2, arrive), (B) write
+            // the survivor's rotated row and column into G and M, then take the
+            // next step's (i, j) (barrier 3, wait).  FP64 warps: the survivor's
+            // new weight, then (barrier 2, wait) the block's best partner,
+            // published with barrier 3 (arrive), and on to the next step's
+            // chain while the column warps are still writing.  Both roles pass
+            // each barrier exactly once per step with a next step; the column
+            // warps' writes are visible to their next loads through barrier 3.
             const double cc = s_c, ss = s_s;
             const int le = s_le;
             const int surv = le == i ? j : i;
             // the pivot of step t + 1 is the p-th survivor: a1 unless the
             // eliminated index sits at or before it
             const int inext = more ? (le <= a1 ? a2 : a1) : -1;
-            Cand nbest = cand_none();
-            if (wid == 0) {
-                // the survivor's new weight (needed from the final reduce on),
-                // overlapping the column threads' work
-                const double x = gd[surv];
-                const double ws = pos_bits(x) ? __ddiv_rn(1.0, __dsqrt_rn(x)) : 0.0;
-                if (lane == 0) {
-                    w[surv] = ws;
-                    s_wn[par][0] = ws;
-                }
-            } else if (ct >= 0) {
+            if (ct >= 0) {
                 if (more) {
+                    const int nwork = s_nwork[par];
+                    const bool si = surv == i;
+                    Cand nbest = cand_none();
 #pragma unroll
                     for (int k = 0; k < KPT; ++k)
                         if (zy[k] >= 0 && zy[k] != inext) cand_merge(nbest, Cand{0ull, zy[k], 0.0, 0.0});
-                }
-                const int nwork = s_nwork[par];
-                for (int q = ct; q < nwork; q += NCTT) {
-                    const Work it = work[q];
-                    const int y = it.y;
-                    // only the survivor's row and column are read again, so
+                    // (A) the next pivot is the survivor, a1 or a2 (never the
+                    // eliminated coordinate); only the survivor's row changed
+                    for (int q = ct; q < nwork; q += NCTT) {
+                        const Work it = work[q];
+                        const int y = it.y;
+                        if (y == inext || inext == surv) {
+                            double sg = si ? it.gi : it.gj, sm = si ? it.mi : it.mj;
+                            if (it.flags & W_G) sg = rot_pair_one(cc, ss, it.gi, it.gj, si);
+                            if (it.flags & W_M) sm = rot_pair_one(cc, ss, it.mi, it.mj, si);
+                            if (y == inext) {
+                                // column inext of the survivor's new row
+                                s_survg[par] = sg;
+                                s_survm[par] = sm;
+                                continue;
+                            }
+                            cand_merge(nbest, cand_make_sparse(sg, sm, w[y], y));
+                        } else {
+                            const bool o1 = inext == a1;
+                            cand_merge(nbest, cand_make_sparse(o1 ? it.g1 : it.g2, o1 ? it.m1 : it.m2,
+                                                               w[y], y));
+                        }
+                    }
+                    warp_argmax_to(nbest, &wbest[wid]);
+                    asm volatile("bar.arrive 2, %0;" ::"n"(NT) : "memory");
+                    // (B) only the survivor's row and column are read again, so
                     // only its output of each rotated pair is formed
-                    const bool si = surv == i;
-                    double sg = si ? it.gi : it.gj, sm = si ? it.mi : it.mj;
-                    if (it.flags & W_G) {
-                        sg = rot_pair_one(cc, ss, it.gi, it.gj, si);
-                        G[(int64_t)surv * c + y] = sg;
-                        G[(int64_t)y * c + surv] = sg;
+                    for (int q = ct; q < nwork; q += NCTT) {
+                        const Work it = work[q];
+                        const int y = it.y;
+                        if (it.flags & W_G) {
+                            const double sg = rot_pair_one(cc, ss, it.gi, it.gj, si);
+                            G[(int64_t)surv * c + y] = sg;
+                            G[(int64_t)y * c + surv] = sg;
+                        }
+                        if (it.flags & W_M) {
+                            const double sm = rot_pair_one(cc, ss, it.mi, it.mj, si);
+                            M[(int64_t)surv * c + y] = sm;
+                            M[(int64_t)y * c + surv] = sm;
+                        }
                     }
-                    if (it.flags & W_M) {
-                        sm = rot_pair_one(cc, ss, it.mi, it.mj, si);
-                        M[(int64_t)surv * c + y] = sm;
-                        M[(int64_t)y * c + surv] = sm;
-                    }
-                    if (!more) continue;
-                    if (y == inext) {
-                        // column inext of the survivor's new row
-                        s_survg[par] = sg;
-                        s_survm[par] = sm;
-                        continue;
-                    }
-                    // the next pivot is the survivor, a1 or a2 (never the
-                    // eliminated coordinate)
-                    double gv, mv;
-                    if (inext == surv) { gv = sg; mv = sm; }
-                    else if (inext == a1) { gv = it.g1; mv = it.m1; }
-                    else { gv = it.g2; mv = it.m2; }
-                    cand_merge(nbest, cand_make_sparse(gv, mv, w[y], y));
+                    asm volatile("bar.sync 3, %0;" ::"n"(NT) : "memory");
+                    i = s_nx[0];
+                    j = s_nx[1];
+                    a1 = s_nx[2];
+                    a2 = s_nx[3];
+                    gij = s_nxg;
+                    mij = s_nxm;
                 }
-            }
-            if (more) warp_argmax_to(nbest, &wbest[wid]);
-            __syncthreads();
-            if (more) {
-                nbest = block_best<NW>(wbest);
-                if (inext != i && inext != j)
-                    cand_merge(nbest, cand_make_sparse(s_survg[par], s_survm[par], s_wn[par][0], surv));
-                if (t + 2 < e) {
-                    a1 = le == i ? s_nb[par][0] : s_nb[par][2];
-                    a2 = le == i ? s_nb[par][1] : s_nb[par][3];
-                } else {
-                    a1 = a2 = -1;
+            } else {
+                if (wid == 0) {
+                    // the survivor's new weight (for the merge below)
+                    const double x = gd[surv];
+                    const double ws = pos_bits(x) ? __ddiv_rn(1.0, __dsqrt_rn(x)) : 0.0;
+                    if (lane == 0) {
+                        w[surv] = ws;
+                        s_wn[par][0] = ws;
+                    }
                 }
-                i = inext;
-                j = nbest.idx;
-                gij = nbest.g;
-                mij = nbest.m;
+                if (more) {
+                    if (lane == 0) wbest[wid] = cand_none();
+                    asm volatile("bar.sync 2, %0;" ::"n"(NT) : "memory");
+                    Cand nbest = block_best<NW>(wbest);
+                    if (inext != i && inext != j)
+                        cand_merge(nbest, cand_make_sparse(s_survg[par], s_survm[par], s_wn[par][0], surv));
+                    if (t + 2 < e) {
+                        a1 = le == i ? s_nb[par][0] : s_nb[par][2];
+                        a2 = le == i ? s_nb[par][1] : s_nb[par][3];
+                    } else {
+                        a1 = a2 = -1;
+                    }
+                    i = inext;
+                    j = nbest.idx;
+                    gij = nbest.g;
+                    mij = nbest.m;
+                    if (wid == 0 && lane == 0) {
+                        s_nx[0] = i;
+                        s_nx[1] = j;
+                        s_nx[2] = a1;
+                        s_nx[3] = a2;
+                        s_nxg = gij;
+                        s_nxm = mij;
+                    }
+                    asm volatile("bar.arrive 3, %0;" ::"n"(NT) : "memory");
+                }
             }
         }
     }
