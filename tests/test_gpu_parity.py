@@ -242,3 +242,25 @@ def test_short_pass1_estimate_retries_exactly():
         assert_same_factorization(g, o)
     finally:
         pm.apply_tuning(pm.TUNING_PATH)
+
+
+@gpu
+@pytest.mark.parametrize("case", ["gaps", "one-label", "two-stages"])
+def test_stage_pipeline_edge_cases(case):
+    """Stage-1 labels with unused label values or a single label, and a run
+    stopped after two stages (the next stage's clustering is then never
+    started): bit-identical to the oracle."""
+    a = I.poisson3d(12, seed=3)
+    kw = dict(k=2, eta=0.5, cluster_size=96, core_size=40, seed=2)
+    if case == "gaps":
+        lab = I.grid_bricks(12, 12, 12, 6, 6, 4) * 3 + 1       # values 1, 4, 7, ...
+        g, o = factor_both(a, labels=lab, **kw)
+        assert len(g.clusters(0)[0]) - 1 == int(lab.max() // 3) + 1
+    elif case == "one-label":
+        lab = np.zeros(a.n, dtype=np.int32)
+        g, o = factor_both(a, labels=lab, **kw)
+        assert len(g.clusters(0)[0]) == 2
+    else:
+        g, o = factor_both(a, max_stages=2, **kw)
+        assert g.info().stages == 2
+    assert_same_factorization(g, o)
