@@ -68,6 +68,42 @@ pmmf_status fail(pmmf_status s, const char *msg) {
     return s;
 }
 
+// The loop's results gathered for one readback: out[0] = status bits,
+// out[1 + q] = stage q's dependency levels (max over its clusters),
+// out[1 + P + q] = its matrix's entry count, out[1 + 2P + q] = the bits of its
+// residual contribution.  One block per stage of a chunk of up to 32.
+constexpr int SUMMARY_CHUNK = 32;
+struct SummaryChunk {
+    const int32_t *nlev[SUMMARY_CHUNK];
+    const int64_t *nnz[SUMMARY_CHUNK];
+    int64_t m[SUMMARY_CHUNK];
+};
+
+__global__ void __launch_bounds__(256) k_stage_summary(SummaryChunk c, int64_t q0, int64_t P,
+                                                       const unsigned *status,
+                                                       const double *contrib, int64_t *out) {
+    __shared__ int32_t red[8];
+    const int b = blockIdx.x;
+    const int64_t q = q0 + b;
+    if (q0 == 0 && b == 0) {
+        if (threadIdx.x == 0) out[0] = (int64_t)*status;
+        for (int64_t i = threadIdx.x; i < P; i += blockDim.x) {
+            out[1 + 2 * P + i] = (int64_t)__double_as_longlong(contrib[i]);
+        }
+    }
+    if (q >= P) return;
+    int32_t mx = 0;
+    for (int64_t u = threadIdx.x; u < c.m[b]; u += blockDim.x) mx = max(mx, c.nlev[b][u]);
+    for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mx;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < (int)(blockDim.x >> 5); ++w) mx = max(mx, red[w]);
+        out[1 + q] = mx;
+        out[1 + P + q] = *c.nnz[b];
+    }
+}
+
 // Reads the exact entry count of a matrix whose nnz is only a capacity.
 pmmf_status exact_nnz(Csr &A, cudaStream_t st) {
     if (A.nnz_exact) return PMMF_OK;
@@ -79,10 +115,18 @@ pmmf_status exact_nnz(Csr &A, cudaStream_t st) {
     return PMMF_OK;
 }
 
-// A second stream on which the next stage's clustering runs while the current
-// stage's update runs on the caller's stream.  Its destructor waits for the
-// stream, so declare it after the buffers the stream writes: it is then
-// destroyed (and synchronized) before they are freed.
+// A second stream on which the next stage's clustering and schedule run while
+// the current stage's update runs on the caller's stream.  Declare it before
+// the buffers allocated on it (they are freed on it, so it must outlive them)
+// and a SideDrain after every buffer it touches: the drain waits for the
+// stream before those are freed.
+struct SideDrain {
+    cudaStream_t s = nullptr;
+    ~SideDrain() {
+        if (s) cudaStreamSynchronize(s);
+    }
+};
+
 struct SideStream {
     cudaStream_t s = nullptr;
     cudaEvent_t fork = nullptr, join = nullptr;
@@ -343,28 +387,38 @@ pmmf_status factor_impl(const pmmf_matrix *A, const pmmf_params *prm, pmmf_handl
     auto more_stages = [&](int64_t ss, int64_t pp) {
         return ss > prm->core_size && (prm->max_stages <= 0 || pp < prm->max_stages);
     };
+    SideStream side;
+    PMMF_TRY(side.init());
     // the next stage's positions and cluster maps (swapped in after each stage)
     DBuf<int32_t> posN, clN, locN;
     PMMF_TRY(posN.alloc(n, st));
     PMMF_TRY(clN.alloc(n, st));
     PMMF_TRY(locN.alloc(n, st));
     StageClusters next_cls;
+    DBuf<int64_t> next_e, next_roff;
+    SideDrain drain{side.s};
     int64_t w_hint = 0;
-    SideStream side;
-    PMMF_TRY(side.init());
-    if (more_stages(s, p)) PMMF_TRY(cluster_stage(1, s, act.p, pos.p, cl.p, loc.p, next_cls, st));
+    if (more_stages(s, p)) {
+        PMMF_TRY(cluster_stage(1, s, act.p, pos.p, cl.p, loc.p, next_cls, st));
+        PMMF_TRY(schedule_launch(next_cls.coff.p, next_cls.m, next_cls.count_d.p, s, prm->core_size,
+                                 prm->eta, next_e, next_roff, st));
+    }
     while (more_stages(s, p)) {
         ++p;
         h->st.emplace_back();
         StageData &S = h->st.back();
         S.s = s;
         S.cls = std::move(next_cls);
-        // one readback per stage for the schedule: rotations, the one-cluster
-        // fallback, the largest cluster and the Gram blocks' total size
+        // one readback per stage for the schedule (rotations, the one-cluster
+        // fallback, the largest cluster and the Gram blocks' total size); from
+        // stage 2 on it was computed on the side stream during the previous
+        // stage's update, so the wait normally finds it done
         int64_t sched[5] = {0, 0, 0, 0, 0};
-        DBuf<int64_t> e;
-        PMMF_TRY(schedule_stage(S.cls.coff.p, S.cls.m, S.cls.count_d.p, s, prm->core_size, prm->eta,
-                                e, S.rot.roff, sched, st));
+        if (p == 1) PMMF_CUDA_TRY(cudaStreamSynchronize(st));
+        else PMMF_CUDA_TRY(cudaEventSynchronize(side.join));
+        schedule_read(sched);
+        DBuf<int64_t> e = std::move(next_e);
+        S.rot.roff = std::move(next_roff);
         if (sched[1]) {
             // every cluster too small to rotate: one cluster for this stage
             PMMF_TRY(one_cluster(act.p, s, S.cls, cl.p, loc.p, st));
@@ -398,6 +452,9 @@ pmmf_status factor_impl(const pmmf_matrix *A, const pmmf_params *prm, pmmf_handl
             if (ps == PMMF_OK) ps = set_positions(sv.act.p, s2, posN.p, ns);
             if (ps == PMMF_OK && next)
                 ps = cluster_stage(p + 1, s2, sv.act.p, posN.p, clN.p, locN.p, next_cls, ns);
+            if (ps == PMMF_OK && next)
+                ps = schedule_launch(next_cls.coff.p, next_cls.m, next_cls.count_d.p, s2,
+                                     prm->core_size, prm->eta, next_e, next_roff, ns);
             if (ps == PMMF_OK && next && cudaEventRecord(side.join, ns) != cudaSuccess)
                 ps = fail(PMMF_ERR_CUDA, "event record failed");
             if (ps != PMMF_OK) {
@@ -421,11 +478,16 @@ pmmf_status factor_impl(const pmmf_matrix *A, const pmmf_params *prm, pmmf_handl
             return us;
         }
         if (next) {
-            PMMF_CUDA_TRY(cudaStreamWaitEvent(st, side.join, 0));
+            if (cudaStreamWaitEvent(st, side.join, 0) != cudaSuccess) {
+                cudaStreamSynchronize(side.s);
+                return fail(PMMF_ERR_CUDA, "stream wait failed");
+            }
             // made on the side stream, used and freed on this one from here
             next_cls.coff.st = st;
             next_cls.members.st = st;
             next_cls.count_d.st = st;
+            next_e.st = st;
+            next_roff.st = st;
         }
         // pass 1's output for the next stage, scaled from this one with a 2x margin
         w_hint = (int64_t)(2.0 * (double)up.w_nnz * (double)up.next.nnz /
@@ -455,28 +517,27 @@ pmmf_status factor_impl(const pmmf_matrix *A, const pmmf_params *prm, pmmf_handl
         }
     }
 
+    // status bits, each stage's dependency levels, entry count and residual
+    // contribution: gathered on the device, read with one copy
+    const int64_t P = (int64_t)h->st.size();
+    std::vector<int64_t> summ((size_t)(1 + 3 * P));
     {
-        // status bits and each stage's number of dependency levels
-        unsigned hs = 0;
-        std::vector<std::vector<int32_t>> nl(h->st.size());
-        PMMF_CUDA_TRY(cudaMemcpyAsync(&hs, status.p, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
-        for (size_t q = 0; q < h->st.size(); ++q) {
-            nl[q].resize((size_t)h->st[q].m);
-            if (h->st[q].m > 0)
-                PMMF_CUDA_TRY(cudaMemcpyAsync(nl[q].data(), h->st[q].rot.nlev.p, sizeof(int32_t) * nl[q].size(),
-                                              cudaMemcpyDeviceToHost, st));
-            PMMF_CUDA_TRY(cudaMemcpyAsync(&h->st[q].nnz_after, h->st[q].nnz_d.p, sizeof(int64_t),
-                                          cudaMemcpyDeviceToHost, st));
+        DBuf<int64_t> summ_d;
+        PMMF_TRY(summ_d.alloc(1 + 3 * P, st));
+        for (int64_t q0 = 0; q0 == 0 || q0 < P; q0 += SUMMARY_CHUNK) {
+            SummaryChunk c{};
+            const int64_t nb = std::max<int64_t>(1, std::min<int64_t>(SUMMARY_CHUNK, P - q0));
+            for (int64_t b = 0; b < nb && q0 + b < P; ++b) {
+                const StageData &S = h->st[(size_t)(q0 + b)];
+                c.nlev[b] = S.rot.nlev.p;
+                c.nnz[b] = S.nnz_d.p;
+                c.m[b] = S.rot.nlev.p ? S.m : 0;
+            }
+            k_stage_summary<<<(unsigned)nb, 256, 0, st>>>(c, q0, P, status.p, contribs.p, summ_d.p);
+            PMMF_TRY(launched("stage_summary"));
         }
-        PMMF_CUDA_TRY(cudaStreamSynchronize(st));
-        if (hs & ST_ROW_TOO_LONG) return fail(PMMF_ERR_UNSUPPORTED, "update: output row too long");
-        if (hs & ST_NOT_CONVERGED)
-            return fail(PMMF_ERR_NOT_CONVERGED, "k x k Jacobi did not converge in 32 sweeps");
-        for (size_t q = 0; q < h->st.size(); ++q) {
-            int32_t ml = 0;
-            for (int32_t v : nl[q]) ml = std::max(ml, v);
-            h->st[q].max_levels = ml;
-        }
+        PMMF_CUDA_TRY(cudaMemcpyAsync(summ.data(), summ_d.p, sizeof(int64_t) * summ.size(),
+                                      cudaMemcpyDeviceToHost, st));
     }
     // H: core A_L[S_L, S_L] plus the diagonal
     h->ncore = s;
@@ -487,15 +548,20 @@ pmmf_status factor_impl(const pmmf_matrix *A, const pmmf_params *prm, pmmf_handl
     PMMF_TRY(h->core_pos.alloc(n, st));
     PMMF_CUDA_TRY(cudaMemsetAsync(h->core_pos.p, 0xFF, sizeof(int32_t) * (size_t)n, st));
     PMMF_TRY(set_positions(act.p, s, h->core_pos.p, st));
-
-    std::vector<double> hc((size_t)p + 1, 0.0);
-    if (p > 0)
-        PMMF_CUDA_TRY(cudaMemcpyAsync(hc.data(), contribs.p, sizeof(double) * (size_t)p, cudaMemcpyDeviceToHost, st));
     PMMF_CUDA_TRY(cudaStreamSynchronize(st));
+    const unsigned hs = (unsigned)summ[0];
+    if (hs & ST_ROW_TOO_LONG) return fail(PMMF_ERR_UNSUPPORTED, "update: output row too long");
+    if (hs & ST_NOT_CONVERGED)
+        return fail(PMMF_ERR_NOT_CONVERGED, "k x k Jacobi did not converge in 32 sweeps");
     double tot = 0.0;
-    for (int64_t i = 0; i < p; ++i) {
-        h->st[i].contrib = hc[i];
-        tot += hc[i];
+    for (int64_t i = 0; i < P; ++i) {
+        StageData &S = h->st[(size_t)i];
+        S.max_levels = (int32_t)summ[(size_t)(1 + i)];
+        S.nnz_after = summ[(size_t)(1 + P + i)];
+        double c;
+        std::memcpy(&c, &summ[(size_t)(1 + 2 * P + i)], sizeof(c));
+        S.contrib = c;
+        tot += c;
     }
     h->err = h->norm_a > 0.0 ? std::sqrt(tot) / h->norm_a : 0.0;
     h->nblk = 1;

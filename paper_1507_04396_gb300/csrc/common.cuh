@@ -172,6 +172,16 @@ __device__ __forceinline__ int64_t warp_sum_i64(int64_t v) {
     return v;
 }
 
+// ---------------------------------------------------------------- readbacks
+
+// Page-locked host words mapped into the device's address space (per host
+// thread); returns the host view, *dev the device view, NULL on failure.
+// Slot ranges: MB_SCHED for the stage schedule, MB_PASS2 for the blocked
+// update's sizes.  A kernel writes a range; the host reads it after waiting
+// for that kernel's stream or event.
+enum : int { MB_SCHED = 0, MB_PASS2 = 8, MAILBOX_SLOTS = 16 };
+int64_t *host_mailbox(int64_t **dev);
+
 // ---------------------------------------------------------------- device buffers
 
 struct Arena;  // tracks allocations so an error path frees everything

@@ -600,17 +600,30 @@ pmmf_status partition_stage(const PartitionIn &in, int64_t m, int iters, StageCl
     return clusters_from_labels(in, label, fcnt, m, out, st);
 }
 
+pmmf_status schedule_launch(const int64_t *coff, int64_t mm, const int64_t *mm_dev, int64_t s,
+                            int64_t core, double eta, DBuf<int64_t> &e, DBuf<int64_t> &roff,
+                            cudaStream_t st) {
+    int64_t *mb_d = nullptr;
+    if (!host_mailbox(&mb_d)) return PMMF_ERR_CUDA;
+    PMMF_TRY(e.alloc(mm > 1 ? mm : 1, st));
+    PMMF_TRY(roff.alloc(mm + 1 > 2 ? mm + 1 : 2, st));
+    k_schedule<<<1, SCHED_THREADS, 0, st>>>(coff, mm, mm_dev, s, core, eta, e.p, roff.p,
+                                            mb_d + MB_SCHED);
+    return launched("schedule");
+}
+
+void schedule_read(int64_t *host_out) {
+    int64_t *mb_d = nullptr;
+    const volatile int64_t *mb = host_mailbox(&mb_d);
+    for (int i = 0; i < 5; ++i) host_out[i] = mb[MB_SCHED + i];
+}
+
 pmmf_status schedule_stage(const int64_t *coff, int64_t mm, const int64_t *mm_dev, int64_t s,
                            int64_t core, double eta, DBuf<int64_t> &e, DBuf<int64_t> &roff,
                            int64_t *host_out, cudaStream_t st) {
-    PMMF_TRY(e.alloc(mm > 1 ? mm : 1, st));
-    PMMF_TRY(roff.alloc(mm + 1 > 2 ? mm + 1 : 2, st));
-    DBuf<int64_t> out;
-    PMMF_TRY(out.alloc(5, st));
-    k_schedule<<<1, SCHED_THREADS, 0, st>>>(coff, mm, mm_dev, s, core, eta, e.p, roff.p, out.p);
-    PMMF_TRY(launched("schedule"));
-    PMMF_CUDA_TRY(cudaMemcpyAsync(host_out, out.p, 5 * sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+    PMMF_TRY(schedule_launch(coff, mm, mm_dev, s, core, eta, e, roff, st));
     PMMF_CUDA_TRY(cudaStreamSynchronize(st));
+    schedule_read(host_out);
     return PMMF_OK;
 }
 

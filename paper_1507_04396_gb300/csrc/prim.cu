@@ -19,6 +19,35 @@ std::once_flag g_alloc_env_once;
 }  // namespace
 
 void set_error(const std::string &msg) { t_last_error = msg; }
+
+// Page-locked, device-mapped host words (one set per host thread): kernels
+// write small results straight into them, so a readback is a wait on the
+// stream or an event instead of a copy.  Allocated once per thread and kept
+// for the life of the process.
+int64_t *host_mailbox(int64_t **dev) {
+    thread_local int64_t *h = nullptr;
+    thread_local int64_t *d = nullptr;
+    if (!h) {
+        void *p = nullptr;
+        if (cudaHostAlloc(&p, sizeof(int64_t) * MAILBOX_SLOTS,
+                          cudaHostAllocMapped | cudaHostAllocPortable) != cudaSuccess) {
+            cudaGetLastError();
+            set_error("page-locked host allocation failed");
+            return nullptr;
+        }
+        void *dp = nullptr;
+        if (cudaHostGetDevicePointer(&dp, p, 0) != cudaSuccess) {
+            cudaGetLastError();
+            cudaFreeHost(p);
+            set_error("mapping page-locked host memory failed");
+            return nullptr;
+        }
+        h = (int64_t *)p;
+        d = (int64_t *)dp;
+    }
+    *dev = d;
+    return h;
+}
 const char *last_error_cstr() { return t_last_error.c_str(); }
 
 // Test hook: PMMF_FAIL_ALLOC_AFTER=N makes the (N+1)-th device allocation of

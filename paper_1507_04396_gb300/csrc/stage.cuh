@@ -74,6 +74,13 @@ pmmf_status partition_from_labels(const PartitionIn &in, const int32_t *labels, 
 pmmf_status schedule_stage(const int64_t *coff, int64_t mm, const int64_t *mm_dev, int64_t s,
                            int64_t core, double eta, DBuf<int64_t> &e, DBuf<int64_t> &roff,
                            int64_t *host_out, cudaStream_t st);
+// The same in two halves: schedule_launch enqueues the kernel on st (its
+// results go to the host mailbox's MB_SCHED slots); schedule_read copies them
+// out once the host has waited for st (or an event recorded after the launch).
+pmmf_status schedule_launch(const int64_t *coff, int64_t mm, const int64_t *mm_dev, int64_t s,
+                            int64_t core, double eta, DBuf<int64_t> &e, DBuf<int64_t> &roff,
+                            cudaStream_t st);
+void schedule_read(int64_t *host_out);
 
 // Gram G^u and symmetric local block M^u of every cluster (dense c_u x c_u,
 // row-major at goff[u]) and the rotation search of Algorithm 2.

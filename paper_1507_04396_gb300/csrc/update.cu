@@ -444,6 +444,18 @@ pmmf_status launch_rows(RowArgs &a, int64_t nnz_in, int64_t nnz_out, cudaStream_
     return launched("rows");
 }
 
+// Pass 2's capacity, its longest row, W's exact size and pass 1's overflow
+// flag, gathered for one readback.
+__global__ void k_pass2_sizes(const int64_t *cap, const int64_t *maxlen, const int64_t *wsize,
+                              const unsigned *wover, int64_t *out) {
+    if (threadIdx.x == 0) {
+        out[0] = *cap;
+        out[1] = *maxlen;
+        out[2] = *wsize;
+        out[3] = (int64_t)*wover;
+    }
+}
+
 }  // namespace
 
 pmmf_status set_positions(const int32_t *act, int64_t s, int32_t *pos, cudaStream_t st) {
@@ -547,6 +559,9 @@ pmmf_status update_stage(const Csr &A, const int32_t *act, int64_t n, const int3
     PMMF_TRY(maxlen.alloc(1, st));
     // hv: pass 2's capacity and longest row, W's exact size, pass 1's overflow
     int64_t hv[4] = {0, 0, 0, 0};
+    int64_t *mb_d = nullptr;
+    const volatile int64_t *mb = host_mailbox(&mb_d);
+    if (!mb) return PMMF_ERR_CUDA;
     auto pass2_count = [&]() -> pmmf_status {
         PMMF_CUDA_TRY(cudaMemsetAsync(caprp.p, 0, sizeof(int64_t) * (size_t)(s2 + 1), st));
         PMMF_CUDA_TRY(cudaMemsetAsync(maxlen.p, 0, sizeof(int64_t), st));
@@ -559,13 +574,12 @@ pmmf_status update_stage(const Csr &A, const int32_t *act, int64_t n, const int3
         a.maxlen = maxlen.p;
         PMMF_TRY(launch_rows<P2_COUNT>(a, wcap, 0, st));
         PMMF_TRY(scan_i64(caprp.p, caprp.p, s2, st));
-        unsigned ov = 0;
-        PMMF_CUDA_TRY(cudaMemcpyAsync(&hv[0], caprp.p + s2, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
-        PMMF_CUDA_TRY(cudaMemcpyAsync(&hv[1], maxlen.p, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
-        PMMF_CUDA_TRY(cudaMemcpyAsync(&hv[2], wrp.p + s, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
-        PMMF_CUDA_TRY(cudaMemcpyAsync(&ov, wover.p, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
+        // the four sizes in one write to the host mailbox
+        k_pass2_sizes<<<1, 32, 0, st>>>(caprp.p + s2, maxlen.p, wrp.p + s, wover.p,
+                                        mb_d + MB_PASS2);
+        PMMF_TRY(launched("pass2_sizes"));
         PMMF_CUDA_TRY(cudaStreamSynchronize(st));
-        hv[3] = ov;
+        for (int i = 0; i < 4; ++i) hv[i] = mb[MB_PASS2 + i];
         return PMMF_OK;
     };
     PMMF_TRY(pass2_count());
