@@ -51,6 +51,9 @@ struct RowArgs {
     const double *kO;
     int64_t cmax;
     int outcap;
+    // counting passes: reach sets (NULL: run the level loop on the pattern)
+    const uint32_t *reach;
+    int reach_words;           // words per coordinate (a multiple of 4)
     // pass 1
     int64_t *wcnt;             // W row counts (COUNT)
     int64_t *wcur;             // W write cursors (WRITE)
@@ -91,6 +94,52 @@ __host__ __device__ inline int64_t rows_per_warp(int64_t cmax, int64_t outcap, b
 // Row entries a lane keeps in registers (rows up to 32 * ROW_CACHE entries
 // are read from global memory once; longer rows are re-read per segment).
 constexpr int ROW_CACHE = 2;
+
+// Reach sets of a stage's rotations: R_u[x] = the local coordinates of
+// cluster u that a nonzero at x (before the stage) makes nonzero, i.e. those
+// reachable from x through rotations taken in step order.  A rotation makes
+// all of its coordinates nonzero when one is, so the pattern a row segment
+// has after the cluster's rotations is the union of R_u over its entries.
+// Built backwards: R[x] = {x}, then for each rotation from the last to the
+// first, every coordinate of its tuple receives the union of the tuple's sets.
+// One warp per cluster; lane w owns word w of every set (words never mix, so
+// the lanes need no synchronisation); the sets live in shared memory.
+constexpr int REACH_MAX_C = 1024;   // 32 words per set: one word per lane
+
+__global__ void k_reach(const int64_t *coff, const int64_t *roff, const RotRec *rec, int K,
+                        const int32_t *kidx, const int32_t *kkv, int words, uint32_t *reach) {
+    extern __shared__ uint32_t rs[];
+    const int64_t u = blockIdx.x;
+    const int64_t cb = coff[u];
+    const int c = (int)(coff[u + 1] - cb);
+    const int nw = (c + 31) / 32;
+    const int w = threadIdx.x;
+    const int64_t r0 = roff[u];
+    const int e = (int)(roff[u + 1] - r0);
+    if (w < nw) {
+        for (int x = 0; x < c; ++x) rs[x * 32 + w] = (x >> 5) == w ? 1u << (x & 31) : 0u;
+        if (K <= 2) {
+#pragma unroll 4
+            for (int t = e - 1; t >= 0; --t) {
+                const RotRec q = rec[r0 + t];
+                const uint32_t v = rs[q.li * 32 + w] | rs[q.lj * 32 + w];
+                rs[q.li * 32 + w] = v;
+                rs[q.lj * 32 + w] = v;
+            }
+        } else {
+            for (int t = e - 1; t >= 0; --t) {
+                const int kk = kkv[r0 + t];
+                const int32_t *T = kidx + (r0 + t) * K;
+                uint32_t v = 0u;
+                for (int q = 0; q < kk; ++q) v |= rs[T[q] * 32 + w];
+                for (int q = 0; q < kk; ++q) rs[T[q] * 32 + w] = v;
+            }
+        }
+    }
+    // rows of 'words' words, zero beyond the cluster's own
+    if (w < words)
+        for (int x = 0; x < c; ++x) reach[(cb + x) * words + w] = w < nw ? rs[x * 32 + w] : 0u;
+}
 
 // KP: the stage's rotations are k-point (k >= 3) blocks; the k = 2
 // instantiation carries no k-point code (fewer registers, more warps).
@@ -158,7 +207,30 @@ __global__ void __launch_bounds__(256, 4) k_rows(RowArgs a) {
             const int64_t cb = a.coff[mu];
             const int c = (int)(a.coff[mu + 1] - cb);
             const int nw = (c + 31) / 32;
-            if (cached) {
+            if (COUNT && a.reach) {
+                // the segment's pattern after the cluster's rotations: the
+                // union of its entries' reach sets
+                auto add_reach = [&](int l) {
+                    const uint4 *R = (const uint4 *)(a.reach + (cb + l) * a.reach_words);
+                    for (int w4 = 0; 4 * w4 < nw; ++w4) {
+                        const uint4 v = __ldg(R + w4);
+                        const uint32_t vv[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+                        for (int z = 0; z < 4; ++z)
+                            if (4 * w4 + z < nw && vv[z]) atomicOr(&tb[4 * w4 + z], vv[z]);
+                    }
+                };
+                if (cached) {
+#pragma unroll
+                    for (int k = 0; k < ROW_CACHE; ++k)
+                        if (cu[k] == mu) add_reach(cloc[k]);
+                } else {
+                    for (int64_t q = e0 + lane; q < e1; q += 32) {
+                        const int32_t g = a.ci[q];
+                        if (a.cl[g] == mu) add_reach(a.loc[g]);
+                    }
+                }
+            } else if (cached) {
 #pragma unroll
                 for (int k = 0; k < ROW_CACHE; ++k)
                     if (cu[k] == mu) {
@@ -178,7 +250,7 @@ __global__ void __launch_bounds__(256, 4) k_rows(RowArgs a) {
             }
             __syncwarp();
             const int32_t *lo = a.lvl_off + a.roff[mu] + mu;
-            const int nl = a.nlev[mu];
+            const int nl = (COUNT && a.reach) ? 0 : a.nlev[mu];
             if (!KP) {
                 // level offsets in registers (lane L holds lo[L]) and the first
                 // 32 rotations of the next level loaded while this one runs
@@ -508,6 +580,21 @@ pmmf_status update_stage(const Csr &A, const int32_t *act, int64_t n, const int3
     a.contrib = contrib;
     a.contrib_cl = contrib_cl;
     a.hdiag = hdiag;
+
+    // the counting passes take the fill pattern from the reach sets
+    DBuf<uint32_t> reach;
+    if (cmax <= REACH_MAX_C && s > 0 && cls.m > 0) {
+        const int words = (int)((rows_mask_words(cmax) + 3) / 4 * 4);
+        PMMF_TRY(reach.alloc(s * words, st));
+        const size_t sh = sizeof(uint32_t) * 32 * (size_t)cmax;
+        if (sh > 48 * 1024)
+            PMMF_CUDA_TRY(cudaFuncSetAttribute(k_reach, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh));
+        k_reach<<<(unsigned)cls.m, 32, sh, st>>>(cls.coff.p, rot.roff.p, rot.rec.p, rot.K, rot.kidx.p,
+                                                 rot.kk.p, words, reach.p);
+        PMMF_TRY(launched("reach"));
+        a.reach = reach.p;
+        a.reach_words = words;
+    }
 
     // pass 1: V = A Q^T, scattered straight into the rows of W = V^T
     DBuf<int64_t> wrp, wcur;
