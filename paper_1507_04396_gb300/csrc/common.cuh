@@ -232,6 +232,8 @@ struct DBuf {
 // Exclusive scan of int64 counts: out[i] = sum_{j<i} in[j], out[n] = total.
 // in may alias out (in place, n+1 slots).  tmp is managed internally.
 pmmf_status scan_i64(const int64_t *in, int64_t *out, int64_t n, cudaStream_t st);
+// The same, the result written to out and to out2 (which must not alias in).
+pmmf_status scan_i64_dup(const int64_t *in, int64_t *out, int64_t *out2, int64_t n, cudaStream_t st);
 // Same for int32 input, int64 output.
 pmmf_status scan_i32_to_i64(const int32_t *in, int64_t *out, int64_t n, cudaStream_t st);
 

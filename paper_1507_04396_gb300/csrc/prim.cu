@@ -6,6 +6,8 @@
 #include <vector>
 #include <string>
 
+#include <cooperative_groups.h>
+
 #include "common.cuh"
 
 namespace pmmf {
@@ -123,57 +125,66 @@ __device__ int64_t block_exclusive_scan(int64_t v, int64_t *total) {
     return r;
 }
 
+// Longer inputs: one cooperative launch in three phases separated by grid
+// barriers (tile sums; the tile sums scanned by block 0, partial[nb] = total;
+// every tile scanned with its offset), each block taking tiles b, b + grid, ...
+// Every read of 'in' (phase 1 reads all of it) precedes the first write of
+// 'out', so the two may alias.
 template <class T>
-__global__ void k_scan_partials(const T *in, int64_t n, int64_t *partial) {
-    int64_t base = (int64_t)blockIdx.x * SCAN_TILE + (int64_t)threadIdx.x * SCAN_ITEMS;
-    int64_t s = 0;
-    for (int q = 0; q < SCAN_ITEMS; ++q)
-        if (base + q < n) s += (int64_t)in[base + q];
+__global__ void __launch_bounds__(SCAN_THREADS) k_scan_coop(const T *in, int64_t *out, int64_t *out2,
+                                                            int64_t n, int64_t nb, int64_t *partial) {
+    namespace cg = cooperative_groups;
+    cg::grid_group grid = cg::this_grid();
     __shared__ int64_t tot;
-    block_exclusive_scan<int64_t>(s, &tot);
-    if (threadIdx.x == 0) partial[blockIdx.x] = tot;
-}
-
-__global__ void k_scan_small(int64_t *partial, int64_t nb) {
-    __shared__ int64_t carry;
-    __shared__ int64_t tot;
-    if (threadIdx.x == 0) carry = 0;
-    __syncthreads();
-    for (int64_t base = 0; base < nb; base += SCAN_THREADS) {
-        int64_t i = base + threadIdx.x;
-        int64_t v = i < nb ? partial[i] : 0;
-        int64_t ex = block_exclusive_scan<int64_t>(v, &tot);
-        if (i < nb) partial[i] = ex + carry;
-        __syncthreads();
-        if (threadIdx.x == 0) carry += tot;
-        __syncthreads();
+    for (int64_t b = blockIdx.x; b < nb; b += gridDim.x) {
+        const int64_t base = b * SCAN_TILE + (int64_t)threadIdx.x * SCAN_ITEMS;
+        int64_t sum = 0;
+        for (int q = 0; q < SCAN_ITEMS; ++q)
+            if (base + q < n) sum += (int64_t)in[base + q];
+        block_exclusive_scan<int64_t>(sum, &tot);
+        if (threadIdx.x == 0) partial[b] = tot;
     }
-    if (threadIdx.x == 0) partial[nb] = carry;
-}
-
-template <class T>
-__global__ void k_scan_final(const T *in, int64_t *out, int64_t n, const int64_t *partial) {
-    int64_t base = (int64_t)blockIdx.x * SCAN_TILE + (int64_t)threadIdx.x * SCAN_ITEMS;
-    int64_t v[SCAN_ITEMS];
-    int64_t s = 0;
-    for (int q = 0; q < SCAN_ITEMS; ++q) {
-        v[q] = base + q < n ? (int64_t)in[base + q] : 0;
-        s += v[q];
+    grid.sync();
+    if (blockIdx.x == 0) {
+        int64_t carry = 0;
+        for (int64_t b0 = 0; b0 < nb; b0 += SCAN_THREADS) {
+            const int64_t b = b0 + threadIdx.x;
+            const int64_t v = b < nb ? partial[b] : 0;
+            const int64_t ex = block_exclusive_scan<int64_t>(v, &tot);
+            if (b < nb) partial[b] = ex + carry;
+            carry += tot;
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) partial[nb] = carry;
     }
-    __shared__ int64_t tot;
-    int64_t ex = block_exclusive_scan<int64_t>(s, &tot) + partial[blockIdx.x];
-    __syncthreads();  // every read of 'in' precedes any write of 'out' (aliasing)
-    for (int q = 0; q < SCAN_ITEMS; ++q) {
-        if (base + q < n) out[base + q] = ex;
-        ex += v[q];
+    grid.sync();
+    for (int64_t b = blockIdx.x; b < nb; b += gridDim.x) {
+        const int64_t base = b * SCAN_TILE + (int64_t)threadIdx.x * SCAN_ITEMS;
+        int64_t v[SCAN_ITEMS];
+        int64_t sum = 0;
+        for (int q = 0; q < SCAN_ITEMS; ++q) {
+            v[q] = base + q < n ? (int64_t)in[base + q] : 0;
+            sum += v[q];
+        }
+        int64_t ex = block_exclusive_scan<int64_t>(sum, &tot) + partial[b];
+        for (int q = 0; q < SCAN_ITEMS; ++q) {
+            if (base + q < n) {
+                out[base + q] = ex;
+                if (out2) out2[base + q] = ex;
+            }
+            ex += v[q];
+        }
     }
-    if (blockIdx.x == gridDim.x - 1 && threadIdx.x == 0) out[n] = partial[gridDim.x];
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        out[n] = partial[nb];
+        if (out2) out2[n] = partial[nb];
+    }
 }
 
 // Short inputs: one CTA walks the tiles in order with a running carry (one
 // launch instead of three).
 template <class T>
-__global__ void k_scan_one(const T *in, int64_t *out, int64_t n) {
+__global__ void k_scan_one(const T *in, int64_t *out, int64_t *out2, int64_t n) {
     __shared__ int64_t tot;
     int64_t carry = 0;
     for (int64_t t0 = 0; t0 < n; t0 += SCAN_TILE) {
@@ -187,44 +198,64 @@ __global__ void k_scan_one(const T *in, int64_t *out, int64_t n) {
         int64_t ex = block_exclusive_scan<int64_t>(sum, &tot) + carry;
         __syncthreads();  // reads of this tile precede its writes (aliasing)
         for (int q = 0; q < SCAN_ITEMS; ++q) {
-            if (base + q < n) out[base + q] = ex;
+            if (base + q < n) {
+                out[base + q] = ex;
+                if (out2) out2[base + q] = ex;
+            }
             ex += v[q];
         }
         carry += tot;
         __syncthreads();
     }
-    if (threadIdx.x == 0) out[n] = carry;
+    if (threadIdx.x == 0) {
+        out[n] = carry;
+        if (out2) out2[n] = carry;
+    }
 }
 
 template <class T>
-pmmf_status scan_impl(const T *in, int64_t *out, int64_t n, cudaStream_t st) {
+pmmf_status scan_impl(const T *in, int64_t *out, int64_t *out2, int64_t n, cudaStream_t st) {
     if (n <= 0) {
         PMMF_CUDA_TRY(cudaMemsetAsync(out, 0, sizeof(int64_t), st));
+        if (out2) PMMF_CUDA_TRY(cudaMemsetAsync(out2, 0, sizeof(int64_t), st));
         return PMMF_OK;
     }
     if (n <= 4 * SCAN_TILE) {
-        k_scan_one<T><<<1, SCAN_THREADS, 0, st>>>(in, out, n);
+        k_scan_one<T><<<1, SCAN_THREADS, 0, st>>>(in, out, out2, n);
         return launched("scan_one");
     }
-    int64_t nb = (n + SCAN_TILE - 1) / SCAN_TILE;
+    const int64_t nb = (n + SCAN_TILE - 1) / SCAN_TILE;
     DBuf<int64_t> part;
     PMMF_TRY(part.alloc(nb + 1, st));
-    k_scan_partials<T><<<(unsigned)nb, SCAN_THREADS, 0, st>>>(in, n, part.p);
-    PMMF_TRY(launched("scan_partials"));
-    k_scan_small<<<1, SCAN_THREADS, 0, st>>>(part.p, nb);
-    PMMF_TRY(launched("scan_small"));
-    k_scan_final<T><<<(unsigned)nb, SCAN_THREADS, 0, st>>>(in, out, n, part.p);
-    PMMF_TRY(launched("scan_final"));
-    return PMMF_OK;
+    // co-resident blocks for the grid barriers (queried once per element type)
+    static int resident = 0;
+    if (resident == 0) {
+        int dev = 0, nsm = 0, per = 0;
+        PMMF_CUDA_TRY(cudaGetDevice(&dev));
+        PMMF_CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+        PMMF_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_scan_coop<T>, SCAN_THREADS, 0));
+        resident = std::max(1, nsm * per);
+    }
+    const unsigned g = (unsigned)std::min<int64_t>(nb, resident);
+    const T *a_in = in;
+    int64_t *a_out = out, *a_out2 = out2, *a_part = part.p;
+    int64_t a_n = n, a_nb = nb;
+    void *args[] = {&a_in, &a_out, &a_out2, &a_n, &a_nb, &a_part};
+    PMMF_CUDA_TRY(cudaLaunchCooperativeKernel((const void *)k_scan_coop<T>, dim3(g), dim3(SCAN_THREADS),
+                                              args, 0, st));
+    return launched("scan");
 }
 
 }  // namespace
 
 pmmf_status scan_i64(const int64_t *in, int64_t *out, int64_t n, cudaStream_t st) {
-    return scan_impl<int64_t>(in, out, n, st);
+    return scan_impl<int64_t>(in, out, nullptr, n, st);
+}
+pmmf_status scan_i64_dup(const int64_t *in, int64_t *out, int64_t *out2, int64_t n, cudaStream_t st) {
+    return scan_impl<int64_t>(in, out, out2, n, st);
 }
 pmmf_status scan_i32_to_i64(const int32_t *in, int64_t *out, int64_t n, cudaStream_t st) {
-    return scan_impl<int32_t>(in, out, n, st);
+    return scan_impl<int32_t>(in, out, nullptr, n, st);
 }
 
 // ---------------------------------------------------------------- stable counting sort

@@ -869,8 +869,7 @@ pmmf_status gram_and_select(const Csr &A, const int32_t *act_ids, const int32_t 
     PMMF_TRY(tv.alloc(std::max<int64_t>(A.nnz, 1), st));
     k_tcount<<<grid_for(A.nnz, 256), 256, 0, st>>>(A.rowptr.p, A.col.p, s, pos, trp.p);
     PMMF_TRY(launched("tcount"));
-    PMMF_TRY(scan_i64(trp.p, trp.p, s, st));
-    PMMF_CUDA_TRY(cudaMemcpyAsync(tcur.p, trp.p, sizeof(int64_t) * (size_t)(s + 1), cudaMemcpyDeviceToDevice, st));
+    PMMF_TRY(scan_i64_dup(trp.p, trp.p, tcur.p, s, st));
     k_tscatter<<<grid_for(s * 32, 256), 256, 0, st>>>(A.rowptr.p, A.col.p, A.val.p, s, pos,
                                                        act_ids, tcur.p, tci.p, tv.p);
     PMMF_TRY(launched("tscatter"));

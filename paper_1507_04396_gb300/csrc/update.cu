@@ -17,9 +17,12 @@
 // The counting passes that size the outputs run on the sparsity pattern only
 // (a rotation makes both of its coordinates nonzero when either is): integer
 // work, no FP64, and an upper bound of the numeric counts, which differ only
-// where a value cancels to exactly zero.  Pass 1 writes W into rows of that
-// capacity (each row's end is its write cursor); pass 2 writes A_p into rows
-// of that capacity and a compaction copies them to their exact positions.
+// where a value cancels to exactly zero.  For clusters of up to 1,024
+// coordinates the pattern of a row segment is the union of per-coordinate
+// reach sets computed once per stage; larger clusters run the level loop on
+// the pattern.  Pass 1 writes W into rows of that capacity (each row's end is
+// its write cursor); pass 2 writes A_p into rows of that capacity and a
+// compaction copies them to their exact positions.
 #include <climits>
 
 #include "common.cuh"
@@ -61,7 +64,7 @@ struct RowArgs {
     double *wval;
     const int64_t *wtotal;     // WRITE: W's entries (the scan's total) ...
     int64_t wcap;              // ... must fit the allocation, else nothing is written
-    unsigned *wover;           // and this flag is set
+    unsigned long long *wover; // and this flag is set
     // pass 2
     const int32_t *elimflag;
     int32_t stage;
@@ -75,7 +78,7 @@ struct RowArgs {
     double *contrib;
     double *contrib_cl;        // optional: per-cluster residual (indexed by cl of the row)
     unsigned *status;
-    int64_t *maxlen;
+    unsigned long long *maxlen;
 };
 
 // Per-warp shared memory of the row kernel: the dense local vector (cmax
@@ -150,7 +153,7 @@ __global__ void __launch_bounds__(256, 4) k_rows(RowArgs a) {
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const int wpb = blockDim.x >> 5;
     if (MODE == P1_WRITE && *a.wtotal > a.wcap) {
-        if (threadIdx.x == 0 && blockIdx.x == 0) *a.wover = 1u;
+        if (threadIdx.x == 0 && blockIdx.x == 0) *a.wover = 1ull;
         return;
     }
     const int64_t per_warp = rows_per_warp(a.cmax, a.outcap, MODE == P2_WRITE);
@@ -410,7 +413,7 @@ __global__ void __launch_bounds__(256, 4) k_rows(RowArgs a) {
         }
         if (MODE == P2_COUNT && !yelim && lane == 0) {
             a.ocnt[a.newrow[r]] = nout;
-            atomicMax((unsigned long long *)a.maxlen, (unsigned long long)nout);
+            atomicMax(a.maxlen, (unsigned long long)nout);
         }
         if (MODE == P2_WRITE && !yelim) {
             if (lane == 0) a.acnt[a.newrow[r]] = nout;
@@ -518,11 +521,11 @@ pmmf_status launch_rows(RowArgs &a, int64_t nnz_in, int64_t nnz_out, cudaStream_
 
 // Pass 2's capacity, its longest row, W's exact size and pass 1's overflow
 // flag, gathered for one readback.
-__global__ void k_pass2_sizes(const int64_t *cap, const int64_t *maxlen, const int64_t *wsize,
-                              const unsigned *wover, int64_t *out) {
+__global__ void k_pass2_sizes(const int64_t *cap, const unsigned long long *maxlen,
+                              const int64_t *wsize, const unsigned long long *wover, int64_t *out) {
     if (threadIdx.x == 0) {
         out[0] = *cap;
-        out[1] = *maxlen;
+        out[1] = (int64_t)*maxlen;
         out[2] = *wsize;
         out[3] = (int64_t)*wover;
     }
@@ -605,7 +608,9 @@ pmmf_status update_stage(const Csr &A, const int32_t *act, int64_t n, const int3
     a.rows = s;
     a.wcnt = wrp.p;
     PMMF_TRY(launch_rows<P1_COUNT>(a, A.nnz, 0, st));
-    PMMF_TRY(scan_i64(wrp.p, wrp.p, s, st));
+    // row starts of W, and a copy as the write cursors of pass 1
+    PMMF_TRY(wcur.alloc(s + 1, st));
+    PMMF_TRY(scan_i64_dup(wrp.p, wrp.p, wcur.p, s, st));
     // W is allocated from an estimate, without waiting for the count: when the
     // count exceeds it, pass 1 writes nothing, W's rows stay empty, and the
     // size read with pass 2's below triggers a second, exact round
@@ -613,14 +618,16 @@ pmmf_status update_stage(const Csr &A, const int32_t *act, int64_t n, const int3
     W.rows = s;
     int64_t wcap = out.w_hint > 0 ? out.w_hint
                                   : (int64_t)tuned(TUNE_PASS1_ESTIMATE, 0, 8) * A.nnz + 1024;
-    DBuf<unsigned> wover;
-    PMMF_TRY(wover.zeros(1, st));
+    // pass 1's overflow flag and pass 2's longest row, zeroed together
+    DBuf<unsigned long long> flags;
+    PMMF_TRY(flags.zeros(2, st));
+    unsigned long long *wover = flags.p, *maxlen = flags.p + 1;
     PMMF_TRY(W.col.alloc(wcap, st));
     PMMF_TRY(W.val.alloc(wcap, st));
-    PMMF_TRY(wcur.alloc(s + 1, st));
-    auto pass1_write = [&]() -> pmmf_status {
-        PMMF_CUDA_TRY(cudaMemcpyAsync(wcur.p, wrp.p, sizeof(int64_t) * (size_t)(s + 1),
-                                      cudaMemcpyDeviceToDevice, st));
+    auto pass1_write = [&](bool again) -> pmmf_status {
+        if (again)
+            PMMF_CUDA_TRY(cudaMemcpyAsync(wcur.p, wrp.p, sizeof(int64_t) * (size_t)(s + 1),
+                                          cudaMemcpyDeviceToDevice, st));
         a.rp = A.rowptr.p;
         a.rend = nullptr;
         a.ci = A.col.p;
@@ -630,39 +637,37 @@ pmmf_status update_stage(const Csr &A, const int32_t *act, int64_t n, const int3
         a.wval = W.val.p;
         a.wtotal = wrp.p + s;
         a.wcap = wcap;
-        a.wover = wover.p;
+        a.wover = wover;
         return launch_rows<P1_WRITE>(a, A.nnz, wcap, st);
     };
-    PMMF_TRY(pass1_write());
+    PMMF_TRY(pass1_write(false));
     // W's row r holds wrp[r] .. wcur[r] - 1 (the written part of its capacity)
 
     const int64_t s2 = sv.count;       // one elimination per rotation
 
     // pass 2: A_p = W Q^T with accounting and compaction
     out.next.rows = s2;
-    DBuf<int64_t> caprp, acnt, maxlen;
+    // every surviving row writes its slot of caprp and acnt: no zeroing
+    DBuf<int64_t> caprp, acnt;
     PMMF_TRY(caprp.alloc(s2 + 1, st));
-    PMMF_TRY(acnt.zeros(s2 + 1, st));
-    PMMF_TRY(maxlen.alloc(1, st));
+    PMMF_TRY(acnt.alloc(s2 + 1, st));
     // hv: pass 2's capacity and longest row, W's exact size, pass 1's overflow
     int64_t hv[4] = {0, 0, 0, 0};
     int64_t *mb_d = nullptr;
     const volatile int64_t *mb = host_mailbox(&mb_d);
     if (!mb) return PMMF_ERR_CUDA;
     auto pass2_count = [&]() -> pmmf_status {
-        PMMF_CUDA_TRY(cudaMemsetAsync(caprp.p, 0, sizeof(int64_t) * (size_t)(s2 + 1), st));
-        PMMF_CUDA_TRY(cudaMemsetAsync(maxlen.p, 0, sizeof(int64_t), st));
         a.rp = wrp.p;
         a.rend = wcur.p;
         a.ci = W.col.p;
         a.v = W.val.p;
         a.newrow = sv.newrow.p;
         a.ocnt = caprp.p;
-        a.maxlen = maxlen.p;
+        a.maxlen = maxlen;
         PMMF_TRY(launch_rows<P2_COUNT>(a, wcap, 0, st));
         PMMF_TRY(scan_i64(caprp.p, caprp.p, s2, st));
         // the four sizes in one write to the host mailbox
-        k_pass2_sizes<<<1, 32, 0, st>>>(caprp.p + s2, maxlen.p, wrp.p + s, wover.p,
+        k_pass2_sizes<<<1, 32, 0, st>>>(caprp.p + s2, maxlen, wrp.p + s, wover,
                                         mb_d + MB_PASS2);
         PMMF_TRY(launched("pass2_sizes"));
         PMMF_CUDA_TRY(cudaStreamSynchronize(st));
@@ -676,8 +681,8 @@ pmmf_status update_stage(const Csr &A, const int32_t *act, int64_t n, const int3
         wcap = hv[2];
         PMMF_TRY(W.col.alloc(wcap, st));
         PMMF_TRY(W.val.alloc(wcap, st));
-        PMMF_CUDA_TRY(cudaMemsetAsync(wover.p, 0, sizeof(unsigned), st));
-        PMMF_TRY(pass1_write());
+        PMMF_CUDA_TRY(cudaMemsetAsync(flags.p, 0, 2 * sizeof(unsigned long long), st));
+        PMMF_TRY(pass1_write(true));
         PMMF_TRY(pass2_count());
     }
     out.w_nnz = hv[2];
