@@ -71,7 +71,8 @@ pmmf_status fail(pmmf_status s, const char *msg) {
 // The loop's results gathered for one readback: out[0] = status bits,
 // out[1 + q] = stage q's dependency levels (max over its clusters),
 // out[1 + P + q] = its matrix's entry count, out[1 + 2P + q] = the bits of its
-// residual contribution.  One block per stage of a chunk of up to 32.
+// residual contribution, out[1 + 3P] = the bits of ||A||_F^2.  One block per
+// stage of a chunk of up to 32.
 constexpr int SUMMARY_CHUNK = 32;
 struct SummaryChunk {
     const int32_t *nlev[SUMMARY_CHUNK];
@@ -81,12 +82,16 @@ struct SummaryChunk {
 
 __global__ void __launch_bounds__(256) k_stage_summary(SummaryChunk c, int64_t q0, int64_t P,
                                                        const unsigned *status,
-                                                       const double *contrib, int64_t *out) {
+                                                       const double *contrib,
+                                                       const double *sumsq, int64_t *out) {
     __shared__ int32_t red[8];
     const int b = blockIdx.x;
     const int64_t q = q0 + b;
     if (q0 == 0 && b == 0) {
-        if (threadIdx.x == 0) out[0] = (int64_t)*status;
+        if (threadIdx.x == 0) {
+            out[0] = (int64_t)*status;
+            out[1 + 3 * P] = (int64_t)__double_as_longlong(*sumsq);
+        }
         for (int64_t i = threadIdx.x; i < P; i += blockDim.x) {
             out[1 + 2 * P + i] = (int64_t)__double_as_longlong(contrib[i]);
         }
@@ -116,10 +121,9 @@ pmmf_status exact_nnz(Csr &A, cudaStream_t st) {
 }
 
 // A second stream on which the next stage's clustering and schedule run while
-// the current stage's update runs on the caller's stream.  Declare it before
-// the buffers allocated on it (they are freed on it, so it must outlive them)
-// and a SideDrain after every buffer it touches: the drain waits for the
-// stream before those are freed.
+// the current stage's update runs on the caller's stream.  Declare a SideDrain
+// after every buffer the stream touches: the drain waits for the stream before
+// those are freed.
 struct SideDrain {
     cudaStream_t s = nullptr;
     ~SideDrain() {
@@ -130,24 +134,22 @@ struct SideDrain {
 struct SideStream {
     cudaStream_t s = nullptr;
     cudaEvent_t fork = nullptr, join = nullptr;
-    SideStream() = default;
-    SideStream(const SideStream &) = delete;
-    SideStream &operator=(const SideStream &) = delete;
-    ~SideStream() {
-        if (s) {
-            cudaStreamSynchronize(s);
-            cudaStreamDestroy(s);
-        }
-        if (fork) cudaEventDestroy(fork);
-        if (join) cudaEventDestroy(join);
-    }
-    pmmf_status init() {
-        PMMF_CUDA_TRY(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
-        PMMF_CUDA_TRY(cudaEventCreateWithFlags(&fork, cudaEventDisableTiming));
-        PMMF_CUDA_TRY(cudaEventCreateWithFlags(&join, cudaEventDisableTiming));
-        return PMMF_OK;
-    }
 };
+
+// One side stream (and its two events) per host thread, created on first use
+// and kept: creating a stream costs more host time than a small stage.
+pmmf_status side_stream(SideStream *&out) {
+    thread_local SideStream ss;
+    if (!ss.s) {
+        SideStream t;
+        PMMF_CUDA_TRY(cudaStreamCreateWithFlags(&t.s, cudaStreamNonBlocking));
+        PMMF_CUDA_TRY(cudaEventCreateWithFlags(&t.fork, cudaEventDisableTiming));
+        PMMF_CUDA_TRY(cudaEventCreateWithFlags(&t.join, cudaEventDisableTiming));
+        ss = t;
+    }
+    out = &ss;
+    return PMMF_OK;
+}
 
 void set_pool_threshold() {
     static bool done = false;
@@ -310,15 +312,10 @@ pmmf_status factor_impl(const pmmf_matrix *A, const pmmf_params *prm, pmmf_handl
     Csr cur;
     PMMF_TRY(stage_input(A, cur, status.p, st));
     h->nnz_in = cur.nnz;
-    {
-        DBuf<double> ss;
-        PMMF_TRY(ss.alloc(1, st));
-        PMMF_TRY(sum_squares(cur.val.p, cur.nnz, ss.p, st));
-        double hs = 0.0;
-        PMMF_CUDA_TRY(cudaMemcpyAsync(&hs, ss.p, sizeof(double), cudaMemcpyDeviceToHost, st));
-        PMMF_CUDA_TRY(cudaStreamSynchronize(st));
-        h->norm_a = std::sqrt(hs);
-    }
+    // ||A||_F^2, read with the loop's results at the end
+    DBuf<double> sumsq;
+    PMMF_TRY(sumsq.alloc(1, st));
+    PMMF_TRY(sum_squares(cur.val.p, cur.nnz, sumsq.p, st));
 
     // clustering geometry
     const bool geo = prm->coords != nullptr;
@@ -387,8 +384,9 @@ pmmf_status factor_impl(const pmmf_matrix *A, const pmmf_params *prm, pmmf_handl
     auto more_stages = [&](int64_t ss, int64_t pp) {
         return ss > prm->core_size && (prm->max_stages <= 0 || pp < prm->max_stages);
     };
-    SideStream side;
-    PMMF_TRY(side.init());
+    SideStream *sidep = nullptr;
+    PMMF_TRY(side_stream(sidep));
+    const SideStream &side = *sidep;
     // the next stage's positions and cluster maps (swapped in after each stage)
     DBuf<int32_t> posN, clN, locN;
     PMMF_TRY(posN.alloc(n, st));
@@ -520,10 +518,10 @@ pmmf_status factor_impl(const pmmf_matrix *A, const pmmf_params *prm, pmmf_handl
     // status bits, each stage's dependency levels, entry count and residual
     // contribution: gathered on the device, read with one copy
     const int64_t P = (int64_t)h->st.size();
-    std::vector<int64_t> summ((size_t)(1 + 3 * P));
+    std::vector<int64_t> summ((size_t)(2 + 3 * P));
     {
         DBuf<int64_t> summ_d;
-        PMMF_TRY(summ_d.alloc(1 + 3 * P, st));
+        PMMF_TRY(summ_d.alloc(2 + 3 * P, st));
         for (int64_t q0 = 0; q0 == 0 || q0 < P; q0 += SUMMARY_CHUNK) {
             SummaryChunk c{};
             const int64_t nb = std::max<int64_t>(1, std::min<int64_t>(SUMMARY_CHUNK, P - q0));
@@ -533,7 +531,8 @@ pmmf_status factor_impl(const pmmf_matrix *A, const pmmf_params *prm, pmmf_handl
                 c.nnz[b] = S.nnz_d.p;
                 c.m[b] = S.rot.nlev.p ? S.m : 0;
             }
-            k_stage_summary<<<(unsigned)nb, 256, 0, st>>>(c, q0, P, status.p, contribs.p, summ_d.p);
+            k_stage_summary<<<(unsigned)nb, 256, 0, st>>>(c, q0, P, status.p, contribs.p, sumsq.p,
+                                                          summ_d.p);
             PMMF_TRY(launched("stage_summary"));
         }
         PMMF_CUDA_TRY(cudaMemcpyAsync(summ.data(), summ_d.p, sizeof(int64_t) * summ.size(),
@@ -550,6 +549,11 @@ pmmf_status factor_impl(const pmmf_matrix *A, const pmmf_params *prm, pmmf_handl
     PMMF_TRY(set_positions(act.p, s, h->core_pos.p, st));
     PMMF_CUDA_TRY(cudaStreamSynchronize(st));
     const unsigned hs = (unsigned)summ[0];
+    {
+        double a2;
+        std::memcpy(&a2, &summ[(size_t)(1 + 3 * P)], sizeof(a2));
+        h->norm_a = std::sqrt(a2);
+    }
     if (hs & ST_ROW_TOO_LONG) return fail(PMMF_ERR_UNSUPPORTED, "update: output row too long");
     if (hs & ST_NOT_CONVERGED)
         return fail(PMMF_ERR_NOT_CONVERGED, "k x k Jacobi did not converge in 32 sweeps");
