@@ -387,13 +387,18 @@ pmmf_status pmmf_get_stage_matrix(const pmmf_handle *f, int p, int64_t *rowptr_n
  * PMMF_TUNE_PASS1_ESTIMATE (the first stage allocates the blocked update's
  * intermediate for this many times the input's entries, 1..32, default 8;
  * later stages scale the previous stage's size; a short estimate costs a
- * second pass, never a wrong result; use max_size 1).  A value
+ * second pass, never a wrong result; use max_size 1), PMMF_TUNE_REACH_CLUSTERS
+ * (the blocked update's counting passes take each row segment's fill pattern
+ * from per-cluster reach sets when the stage has at least this many clusters,
+ * default 64, else they run the rotation levels on the pattern; both give the
+ * same counts; 1..2^31-1, use max_size 1).  A value
  * applies to launches whose largest cluster has at most max_size coordinates
  * and no smaller bucket matches; shared-memory limits still halve the row and
  * Gram warps when needed.  Process wide; INVALID_ARG for an unknown param or
- * a value outside 1..32 (outside {8, 16} for the search). */
+ * a value outside 1..32 (outside {8, 16} for the search; any positive value for
+ * the reach threshold). */
 enum { PMMF_TUNE_ROWS_WARPS = 0, PMMF_TUNE_GRAM_WARPS = 1, PMMF_TUNE_SELECT_WARPS = 2,
-       PMMF_TUNE_PASS1_ESTIMATE = 3 };
+       PMMF_TUNE_PASS1_ESTIMATE = 3, PMMF_TUNE_REACH_CLUSTERS = 4 };
 pmmf_status pmmf_set_tuning(int param, int64_t max_size, int value);
 void pmmf_clear_tuning(void);
 

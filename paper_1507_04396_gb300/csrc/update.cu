@@ -110,38 +110,60 @@ constexpr int ROW_CACHE = 2;
 constexpr int REACH_MAX_C = 1024;   // 32 words per set: one word per lane
 
 __global__ void k_reach(const int64_t *coff, const int64_t *roff, const RotRec *rec, int K,
-                        const int32_t *kidx, const int32_t *kkv, int words, uint32_t *reach) {
+                        const int32_t *kidx, const int32_t *kkv, int words, int64_t cmax,
+                        uint32_t *reach) {
     extern __shared__ uint32_t rs[];
     const int64_t u = blockIdx.x;
     const int64_t cb = coff[u];
     const int c = (int)(coff[u + 1] - cb);
     const int nw = (c + 31) / 32;
-    const int w = threadIdx.x;
+    const int lane = threadIdx.x;
     const int64_t r0 = roff[u];
     const int e = (int)(roff[u + 1] - r0);
-    if (w < nw) {
-        for (int x = 0; x < c; ++x) rs[x * 32 + w] = (x >> 5) == w ? 1u << (x & 31) : 0u;
+    // the sets (stride 32 words), then the rotations' tuples (KS slots each;
+    // slot K holds the tuple size for k >= 3), staged by all lanes
+    const int KS = K <= 2 ? 2 : K + 1;
+    int32_t *tup = (int32_t *)(rs + 32 * cmax);
+    for (int t = lane; t < e; t += 32) {
         if (K <= 2) {
-#pragma unroll 4
+            const RotRec q = rec[r0 + t];
+            tup[2 * t] = q.li;
+            tup[2 * t + 1] = q.lj;
+        } else {
+            for (int z = 0; z < K; ++z) tup[t * KS + z] = kidx[(r0 + t) * K + z];
+            tup[t * KS + K] = kkv[r0 + t];
+        }
+    }
+    for (int idx = lane; idx < c * nw; idx += 32) {
+        const int x = idx / nw, w = idx - x * nw;
+        rs[x * 32 + w] = (x >> 5) == w ? 1u << (x & 31) : 0u;
+    }
+    __syncwarp();
+    if (lane < nw) {
+        const int w = lane;
+        if (K <= 2) {
             for (int t = e - 1; t >= 0; --t) {
-                const RotRec q = rec[r0 + t];
-                const uint32_t v = rs[q.li * 32 + w] | rs[q.lj * 32 + w];
-                rs[q.li * 32 + w] = v;
-                rs[q.lj * 32 + w] = v;
+                const int li = tup[2 * t], lj = tup[2 * t + 1];
+                const uint32_t v = rs[li * 32 + w] | rs[lj * 32 + w];
+                rs[li * 32 + w] = v;
+                rs[lj * 32 + w] = v;
             }
         } else {
             for (int t = e - 1; t >= 0; --t) {
-                const int kk = kkv[r0 + t];
-                const int32_t *T = kidx + (r0 + t) * K;
+                const int32_t *T = tup + t * KS;
+                const int kk = T[K];
                 uint32_t v = 0u;
                 for (int q = 0; q < kk; ++q) v |= rs[T[q] * 32 + w];
                 for (int q = 0; q < kk; ++q) rs[T[q] * 32 + w] = v;
             }
         }
     }
-    // rows of 'words' words, zero beyond the cluster's own
-    if (w < words)
-        for (int x = 0; x < c; ++x) reach[(cb + x) * words + w] = w < nw ? rs[x * 32 + w] : 0u;
+    __syncwarp();
+    // rows of 'words' words, zero beyond the cluster's own (coalesced)
+    for (int idx = lane; idx < c * words; idx += 32) {
+        const int x = idx / words, w = idx - x * words;
+        reach[(cb + x) * words + w] = w < nw ? rs[x * 32 + w] : 0u;
+    }
 }
 
 // KP: the stage's rotations are k-point (k >= 3) blocks; the k = 2
@@ -584,16 +606,20 @@ pmmf_status update_stage(const Csr &A, const int32_t *act, int64_t n, const int3
     a.contrib_cl = contrib_cl;
     a.hdiag = hdiag;
 
-    // the counting passes take the fill pattern from the reach sets
+    // the counting passes take the fill pattern from the reach sets when the
+    // stage has enough clusters to amortise building them (one warp per
+    // cluster walks its rotations, ~10-20 us whatever the stage's size)
     DBuf<uint32_t> reach;
-    if (cmax <= REACH_MAX_C && s > 0 && cls.m > 0) {
+    if (cmax <= REACH_MAX_C && s > 0 && cls.m >= tuned(TUNE_REACH_CLUSTERS, 1, 64)) {
         const int words = (int)((rows_mask_words(cmax) + 3) / 4 * 4);
         PMMF_TRY(reach.alloc(s * words, st));
-        const size_t sh = sizeof(uint32_t) * 32 * (size_t)cmax;
+        // sets (32 words per coordinate) and tuples (at most cmax rotations)
+        const int KS = rot.K <= 2 ? 2 : rot.K + 1;
+        const size_t sh = sizeof(uint32_t) * (32 + (size_t)KS) * (size_t)cmax;
         if (sh > 48 * 1024)
             PMMF_CUDA_TRY(cudaFuncSetAttribute(k_reach, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh));
         k_reach<<<(unsigned)cls.m, 32, sh, st>>>(cls.coff.p, rot.roff.p, rot.rec.p, rot.K, rot.kidx.p,
-                                                 rot.kk.p, words, reach.p);
+                                                 rot.kk.p, words, cmax, reach.p);
         PMMF_TRY(launched("reach"));
         a.reach = reach.p;
         a.reach_words = words;

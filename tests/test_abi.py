@@ -76,6 +76,8 @@ def test_tuning_table_validation_and_json(tmp_path):
     assert lib.pmmf_set_tuning(2, 512, 16) == pmmf.OK                 # search width
     assert lib.pmmf_set_tuning(2, 512, 12) == pmmf.ERR_INVALID_ARG    # only 8 or 16 warps
     assert lib.pmmf_set_tuning(3, 1, 4) == pmmf.OK                    # pass-1 estimate
+    assert lib.pmmf_set_tuning(3, 1, 33) == pmmf.ERR_INVALID_ARG      # above 32
+    assert lib.pmmf_set_tuning(4, 1, 1 << 30) == pmmf.OK              # reach threshold
     path = tmp_path / "tuning.json"
     path.write_text(json.dumps({"buckets": {"rows_warps": [[256, 4], [1024, 2]],
                                             "gram_warps": [[512, 8]]}}))

@@ -241,6 +241,28 @@ def test_short_pass1_estimate_retries_exactly():
         g, o = factor_both(a, k=2, eta=0.5, cluster_size=150, core_size=60, seed=6)
         assert_same_factorization(g, o)
     finally:
+        L.pmmf_clear_tuning()
+        pm.apply_tuning(pm.TUNING_PATH)
+
+
+@gpu
+@pytest.mark.parametrize("k", [2, 3])
+@pytest.mark.parametrize("mode", ["reach", "levels"])
+def test_counting_pass_modes_agree_with_oracle(k, mode):
+    """The blocked update's counting passes take the fill pattern either from
+    per-cluster reach sets or by running the rotation levels on the pattern
+    (chosen by the stage's cluster count); each mode, forced on every stage,
+    gives the oracle's factorization bit for bit (k = 2 and k-point)."""
+    pm = gpu_lib()
+    L = pm.load()
+    a = I.knn_laplacian(3000, seed=5)
+    try:
+        thr = 1 if mode == "reach" else (1 << 30)
+        assert L.pmmf_set_tuning(pm.TUNE_PARAMS["reach_clusters"], 1, thr) == 0
+        g, o = factor_both(a, k=k, eta=0.5, cluster_size=150, core_size=60, seed=6)
+        assert_same_factorization(g, o)
+    finally:
+        L.pmmf_clear_tuning()
         pm.apply_tuning(pm.TUNING_PATH)
 
 
