@@ -199,7 +199,7 @@ __device__ __forceinline__ Cand warp_argmax(Cand c) {
 
 // Warp argmax that moves only (key, index) between lanes; the lane that holds
 // the winner writes the full candidate to *out.
-__device__ __forceinline__ void warp_argmax_to(const Cand &mine, Cand *out) {
+__device__ __forceinline__ int warp_argmax_to(const Cand &mine, Cand *out) {
     unsigned long long k = mine.key;
     int32_t id = mine.idx;
     for (int o = 16; o > 0; o >>= 1) {
@@ -216,6 +216,7 @@ __device__ __forceinline__ void warp_argmax_to(const Cand &mine, Cand *out) {
     } else if ((threadIdx.x & 31) == __ffs(own) - 1) {
         *out = mine;
     }
+    return own ? id : -1;   // the warp's best index, in every lane
 }
 
 __device__ __forceinline__ bool is_active(const uint32_t *mask, int y) {
@@ -763,8 +764,15 @@ k_select_fast(const int64_t *coff, const int32_t *members, const int64_t *goff, 
                                                                w[y], y));
                         }
                     }
-                    warp_argmax_to(nbest, &wbest[wid]);
+                    const int pb = warp_argmax_to(nbest, &wbest[wid]);
                     asm volatile("bar.arrive 2, %0;" ::"n"(NT) : "memory");
+                    // the next partner is one of the column warps' bests or
+                    // the survivor: start moving this warp's best rows of G
+                    // and M into L2 (the first stages' Gram blocks exceed it)
+                    if (pb >= 0 && pb < c && lane * 16 < c) {
+                        asm volatile("prefetch.L2 [%0];" ::"l"(G + (int64_t)pb * c + lane * 16));
+                        asm volatile("prefetch.L2 [%0];" ::"l"(M + (int64_t)pb * c + lane * 16));
+                    }
                     // (B) only the survivor's row and column are read again, so
                     // only its output of each rotated pair is formed
                     for (int q = ct; q < nwork; q += NCTT) {
