@@ -72,17 +72,21 @@ __global__ void k_tcount(const int64_t *rp, const int32_t *ci, int64_t s, const 
         atomicAdd((unsigned long long *)&tcnt[pos[ci[q]]], 1ull);
 }
 
+// Each transposed entry keeps its row's cluster and local index, packed as
+// (cluster << 32) | local index, so the Gram kernel tests and places it with
+// one load instead of a dependent id -> cluster, local index chain.
 __global__ void k_tscatter(const int64_t *rp, const int32_t *ci, const double *v, int64_t s,
-                           const int32_t *pos, const int32_t *act, int64_t *tcur, int32_t *tci,
-                           double *tv) {
+                           const int32_t *pos, const int32_t *act, const int32_t *cl,
+                           const int32_t *loc, int64_t *tcur, int64_t *tul, double *tv) {
     const int lane = threadIdx.x & 31;
     const int64_t w = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
     for (int64_t r = w; r < s; r += nw) {
         const int32_t g = act[r];
+        const int64_t ul = ((int64_t)cl[g] << 32) | (int64_t)(uint32_t)loc[g];
         for (int64_t q = rp[r] + lane; q < rp[r + 1]; q += 32) {
             const int64_t slot = (int64_t)atomicAdd((unsigned long long *)&tcur[pos[ci[q]]], 1ull);
-            tci[slot] = g;
+            tul[slot] = ul;
             tv[slot] = v[q];
         }
     }
@@ -96,7 +100,7 @@ __global__ void k_tscatter(const int64_t *rp, const int32_t *ci, const double *v
 // G_ba agree).  Whole rows are written, coalesced.  M row a: A[x_a][x_b] for
 // b >= a from row x_a, A[x_b][x_a] for b < a from column x_a.
 __global__ void k_gram_rows(const int64_t *rp, const int32_t *ci, const double *v,
-                            const int64_t *trp, const int32_t *tci, const double *tv,
+                            const int64_t *trp, const int64_t *tul, const double *tv,
                             const int32_t *pos, const int32_t *cl, const int32_t *loc,
                             const int64_t *coff, const int32_t *members, int64_t s, int64_t cmax,
                             const int64_t *goff, double *G, double *M) {
@@ -114,17 +118,33 @@ __global__ void k_gram_rows(const int64_t *rp, const int32_t *ci, const double *
         const int64_t ra = pos[xa];
         for (int b = lane; b < c; b += 32) acc[b] = 0.0;
         __syncwarp();
-        for (int64_t q = rp[ra]; q < rp[ra + 1]; ++q) {
-            const double va = v[q];
-            const int64_t rr = pos[ci[q]];
-            for (int64_t e = trp[rr] + lane; e < trp[rr + 1]; e += 32) {
-                const int32_t xb = tci[e];
-                if (cl[xb] == u) {
-                    const int lb = loc[xb];
-                    acc[lb] = __fma_rn(va, tv[e], acc[lb]);
-                }
+        // row x_a's entries 32 at a time: lane t loads entry t's value and
+        // its transposed column's range (one load chain for all of them),
+        // then the entries are taken in ascending order from the registers
+        const int64_t q0 = rp[ra], q1 = rp[ra + 1];
+        for (int64_t qb = q0; qb < q1; qb += 32) {
+            double va_l = 0.0;
+            int64_t e0_l = 0, e1_l = 0;
+            if (qb + lane < q1) {
+                va_l = v[qb + lane];
+                const int64_t rr = pos[ci[qb + lane]];
+                e0_l = trp[rr];
+                e1_l = trp[rr + 1];
             }
-            __syncwarp();
+            const int nq = (int)(q1 - qb < 32 ? q1 - qb : 32);
+            for (int t = 0; t < nq; ++t) {
+                const double va = __shfl_sync(0xffffffffu, va_l, t);
+                const int64_t e0 = __shfl_sync(0xffffffffu, e0_l, t);
+                const int64_t e1 = __shfl_sync(0xffffffffu, e1_l, t);
+                for (int64_t e = e0 + lane; e < e1; e += 32) {
+                    const int64_t ul = tul[e];
+                    if ((int32_t)(ul >> 32) == u) {
+                        const int lb = (int)(uint32_t)ul;
+                        acc[lb] = __fma_rn(va, tv[e], acc[lb]);
+                    }
+                }
+                __syncwarp();
+            }
         }
         double *Gr = G + goff[u] + (int64_t)a * c;
         for (int b = lane; b < c; b += 32) Gr[b] = acc[b];
@@ -136,8 +156,9 @@ __global__ void k_gram_rows(const int64_t *rp, const int32_t *ci, const double *
             if (cl[xb] == u && loc[xb] >= a) acc[loc[xb]] = v[q];
         }
         for (int64_t e = trp[ra] + lane; e < trp[ra + 1]; e += 32) {
-            const int32_t xb = tci[e];
-            if (cl[xb] == u && loc[xb] < a) acc[loc[xb]] = tv[e];
+            const int64_t ul = tul[e];
+            const int lb = (int)(uint32_t)ul;
+            if ((int32_t)(ul >> 32) == u && lb < a) acc[lb] = tv[e];
         }
         __syncwarp();
         double *Mr = M + goff[u] + (int64_t)a * c;
@@ -868,18 +889,17 @@ pmmf_status gram_and_select(const Csr &A, const int32_t *act_ids, const int32_t 
     PMMF_TRY(gram_blocks(cls, gb, st, gram_total));
     const int64_t s = A.rows;
     // the transpose of the active matrix
-    DBuf<int64_t> trp, tcur;
-    DBuf<int32_t> tci;
+    DBuf<int64_t> trp, tcur, tul;
     DBuf<double> tv;
     PMMF_TRY(trp.zeros(s + 1, st));
     PMMF_TRY(tcur.alloc(s + 1, st));
-    PMMF_TRY(tci.alloc(std::max<int64_t>(A.nnz, 1), st));
+    PMMF_TRY(tul.alloc(std::max<int64_t>(A.nnz, 1), st));
     PMMF_TRY(tv.alloc(std::max<int64_t>(A.nnz, 1), st));
     k_tcount<<<grid_for(A.nnz, 256), 256, 0, st>>>(A.rowptr.p, A.col.p, s, pos, trp.p);
     PMMF_TRY(launched("tcount"));
     PMMF_TRY(scan_i64_dup(trp.p, trp.p, tcur.p, s, st));
     k_tscatter<<<grid_for(s * 32, 256), 256, 0, st>>>(A.rowptr.p, A.col.p, A.val.p, s, pos,
-                                                       act_ids, tcur.p, tci.p, tv.p);
+                                                       act_ids, cl, loc, tcur.p, tul.p, tv.p);
     PMMF_TRY(launched("tscatter"));
     int warps = tuned(TUNE_GRAM_WARPS, cmax, 8);
     while (warps > 1 && sizeof(double) * (size_t)cmax * warps > 96 * 1024) warps >>= 1;
@@ -888,11 +908,12 @@ pmmf_status gram_and_select(const Csr &A, const int32_t *act_ids, const int32_t 
         PMMF_CUDA_TRY(cudaFuncSetAttribute(k_gram_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gsh));
     prof_begin(KF_GRAM, st);
     k_gram_rows<<<grid_for(s * 32, 32 * warps), 32 * warps, gsh, st>>>(
-        A.rowptr.p, A.col.p, A.val.p, trp.p, tci.p, tv.p, pos, cl, loc, cls.coff.p, cls.members.p,
+        A.rowptr.p, A.col.p, A.val.p, trp.p, tul.p, tv.p, pos, cl, loc, cls.coff.p, cls.members.p,
         s, cmax, gb.goff.p, gb.G.p, gb.M.p);
-    // compulsory traffic: the active matrix and its transpose once (12 B per
-    // entry, 8 B per row pointer) and both c_u x c_u outputs
-    prof_end(KF_GRAM, st, 24.0 * (double)A.nnz + 16.0 * (double)s + 16.0 * (double)gb.total, 0.0);
+    // compulsory traffic: the active matrix (12 B per entry) and its
+    // transpose (16 B per entry) once, their row pointers, and both c_u x c_u
+    // outputs
+    prof_end(KF_GRAM, st, 28.0 * (double)A.nnz + 16.0 * (double)s + 16.0 * (double)gb.total, 0.0);
     PMMF_TRY(launched("gram"));
     return select_stage(cls, cmax, gb, seed, stage, rot, elimflag, st, order, useed, status);
 }
