@@ -132,11 +132,38 @@ __global__ void k_gram_rows(const int64_t *rp, const int32_t *ci, const double *
                 e1_l = trp[rr + 1];
             }
             const int nq = (int)(q1 - qb < 32 ? q1 - qb : 32);
+            // the first 32 entries of the next column are loaded while the
+            // current one is accumulated
+            int64_t ul_n = -1;
+            double tv_n = 0.0;
+            {
+                const int64_t e0 = __shfl_sync(0xffffffffu, e0_l, 0);
+                const int64_t e1 = __shfl_sync(0xffffffffu, e1_l, 0);
+                if (e0 + lane < e1) {
+                    ul_n = tul[e0 + lane];
+                    tv_n = tv[e0 + lane];
+                }
+            }
             for (int t = 0; t < nq; ++t) {
                 const double va = __shfl_sync(0xffffffffu, va_l, t);
                 const int64_t e0 = __shfl_sync(0xffffffffu, e0_l, t);
                 const int64_t e1 = __shfl_sync(0xffffffffu, e1_l, t);
-                for (int64_t e = e0 + lane; e < e1; e += 32) {
+                const int64_t ul0 = ul_n;
+                const double tv0 = tv_n;
+                if (t + 1 < nq) {
+                    const int64_t f0 = __shfl_sync(0xffffffffu, e0_l, t + 1);
+                    const int64_t f1 = __shfl_sync(0xffffffffu, e1_l, t + 1);
+                    ul_n = -1;
+                    if (f0 + lane < f1) {
+                        ul_n = tul[f0 + lane];
+                        tv_n = tv[f0 + lane];
+                    }
+                }
+                if (e0 + lane < e1 && (int32_t)(ul0 >> 32) == u) {
+                    const int lb = (int)(uint32_t)ul0;
+                    acc[lb] = __fma_rn(va, tv0, acc[lb]);
+                }
+                for (int64_t e = e0 + 32 + lane; e < e1; e += 32) {
                     const int64_t ul = tul[e];
                     if ((int32_t)(ul >> 32) == u) {
                         const int lb = (int)(uint32_t)ul;
