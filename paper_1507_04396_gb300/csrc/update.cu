@@ -45,7 +45,6 @@ struct RowArgs {
     const int32_t *pos;        // global id -> row (stage start)
     const int32_t *cl, *loc;
     const int64_t *coff;
-    const int32_t *members;
     const int64_t *roff;
     const int32_t *lvl_off, *nlev;
     const Rot2 *lvlrot;
@@ -54,6 +53,10 @@ struct RowArgs {
     const double *kO;
     int64_t cmax;
     int outcap;
+    // per cluster member j (cluster order): its stage position (pass 1's
+    // destination row) and its global id with bit 31 set when this stage
+    // eliminates it (pass 2), so an emitted entry needs one load, not two
+    const int32_t *mpos, *mge;
     // counting passes: reach sets (NULL: run the level loop on the pattern)
     const uint32_t *reach;
     int reach_words;           // words per coordinate (a multiple of 4)
@@ -385,16 +388,18 @@ __global__ void __launch_bounds__(256, 4) k_rows(RowArgs a) {
                     dense[l] = 0.0;
                     nz = nonzero_bits(x);
                 }
-                const int32_t g = nz ? a.members[cb + l] : 0;
                 if (MODE == P1_COUNT) {
-                    if (nz) atomicAdd((unsigned long long *)&a.wcnt[a.pos[g]], 1ull);
+                    if (nz) atomicAdd((unsigned long long *)&a.wcnt[a.mpos[cb + l]], 1ull);
                 } else if (MODE == P1_WRITE) {
                     if (nz) {
-                        const int64_t slot = (int64_t)atomicAdd((unsigned long long *)&a.wcur[a.pos[g]], 1ull);
+                        const int64_t slot =
+                            (int64_t)atomicAdd((unsigned long long *)&a.wcur[a.mpos[cb + l]], 1ull);
                         a.wcol[slot] = y;
                         a.wval[slot] = x;
                     }
                 } else {
+                    const int32_t mg = nz ? a.mge[cb + l] : 0;
+                    const int32_t g = mg & 0x7fffffff;
                     bool keep = false;
                     if (nz) {
                         bool term = false;
@@ -404,7 +409,7 @@ __global__ void __launch_bounds__(256, 4) k_rows(RowArgs a) {
                             } else {
                                 term = true;
                             }
-                        } else if (a.elimflag[g] == a.stage) {
+                        } else if (mg < 0) {
                             term = true;
                         } else {
                             keep = true;
@@ -464,6 +469,17 @@ __global__ void __launch_bounds__(256, 4) k_rows(RowArgs a) {
     if (MODE == P2_WRITE) {
         part = warp_sum(part);
         if (lane == 0 && part != 0.0) atomicAdd(a.contrib, part);
+    }
+}
+
+// Member maps of a stage (see RowArgs::mpos, mge).
+__global__ void k_member_maps(const int32_t *members, int64_t s, const int32_t *pos,
+                              const int32_t *elimflag, int32_t stage, int32_t *mpos, int32_t *mge) {
+    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < s;
+         j += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t g = members[j];
+        mpos[j] = pos[g];
+        mge[j] = elimflag[g] == stage ? (int32_t)((uint32_t)g | 0x80000000u) : g;
     }
 }
 
@@ -588,7 +604,6 @@ pmmf_status update_stage(const Csr &A, const int32_t *act, int64_t n, const int3
     a.cl = cl;
     a.loc = loc;
     a.coff = cls.coff.p;
-    a.members = cls.members.p;
     a.roff = rot.roff.p;
     a.lvl_off = rot.lvl_off.p;
     a.nlev = rot.nlev.p;
@@ -605,6 +620,17 @@ pmmf_status update_stage(const Csr &A, const int32_t *act, int64_t n, const int3
     a.contrib = contrib;
     a.contrib_cl = contrib_cl;
     a.hdiag = hdiag;
+
+    DBuf<int32_t> mpos, mge;
+    PMMF_TRY(mpos.alloc(std::max<int64_t>(s, 1), st));
+    PMMF_TRY(mge.alloc(std::max<int64_t>(s, 1), st));
+    if (s > 0) {
+        k_member_maps<<<grid_for(s, 256), 256, 0, st>>>(cls.members.p, s, pos, elimflag,
+                                                        (int32_t)stage, mpos.p, mge.p);
+        PMMF_TRY(launched("member_maps"));
+    }
+    a.mpos = mpos.p;
+    a.mge = mge.p;
 
     // the counting passes take the fill pattern from the reach sets when the
     // stage has enough clusters to amortise building them (one warp per
