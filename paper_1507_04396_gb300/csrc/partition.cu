@@ -182,10 +182,15 @@ __global__ void k_assign(const int32_t *act, int64_t s, const int32_t *q, const 
 // into the centroids in its own shared memory, and the next one, zeroed
 // meanwhile; sum and cnt hold 3 m DIM and 3 m entries, buffer 0 zero on
 // entry).  The last iteration's counts are in buffer (iters - 1) % 3.
+// Points are taken in Morton order (order[r'] = the r'-th active point's id,
+// pos[id] = its active index), so a warp's points are neighbours that mostly
+// share their nearest centroid: lanes with the same centroid add their
+// coordinates and count with one atomic each (integer sums, so the order of
+// the additions does not matter).
 template <int DIM>
-__global__ void k_lloyd(const int32_t *act, int64_t s, const int32_t *q, const int32_t *cen,
-                        int64_t m, int iters, int32_t *label, unsigned long long *sum,
-                        unsigned long long *cnt) {
+__global__ void k_lloyd(const int32_t *order, const int32_t *pos, int64_t s, const int32_t *q,
+                        const int32_t *cen, int64_t m, int iters, int32_t *label,
+                        unsigned long long *sum, unsigned long long *cnt) {
     namespace cg = cooperative_groups;
     cg::grid_group grid = cg::this_grid();
     extern __shared__ int32_t sc[];
@@ -211,7 +216,7 @@ __global__ void k_lloyd(const int32_t *act, int64_t s, const int32_t *q, const i
         }
         __syncthreads();
         for (int64_t r = gt; r < s; r += gs) {
-            const int32_t g = act[r];
+            const int32_t g = order[r];
             int32_t p[DIM];
             for (int d = 0; d < DIM; ++d) p[d] = q[(int64_t)g * DIM + d];
             uint32_t best = 0xffffffffu;
@@ -224,9 +229,16 @@ __global__ void k_lloyd(const int32_t *act, int64_t s, const int32_t *q, const i
                 }
                 if (dd < best) { best = dd; bt = t; }
             }
-            label[r] = (int32_t)bt;
-            for (int d = 0; d < DIM; ++d) atomicAdd(&sacc[bt * DIM + d], (unsigned long long)p[d]);
-            atomicAdd(&cacc[bt], 1ull);
+            label[pos[g]] = (int32_t)bt;
+            // quantized coordinates are below 2^16, so 32 of them sum in 32 bits
+            const unsigned live = __activemask();
+            const unsigned grp = __match_any_sync(live, (int)bt);
+            const bool leader = (threadIdx.x & 31) == __ffs(grp) - 1;
+            for (int d = 0; d < DIM; ++d) {
+                const unsigned v = __reduce_add_sync(grp, (unsigned)p[d]);
+                if (leader) atomicAdd(&sacc[bt * DIM + d], (unsigned long long)v);
+            }
+            if (leader) atomicAdd(&cacc[bt], (unsigned long long)__popc(grp));
         }
         grid.sync();
     }
@@ -561,14 +573,15 @@ pmmf_status partition_stage(const PartitionIn &in, int64_t m, int iters, StageCl
         const unsigned g = (unsigned)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)nsm * per_sm));
         PMMF_TRY(lsum.zeros(3 * m * dim, st));
         PMMF_TRY(lcnt.zeros(3 * m, st));
-        const int32_t *a_act = in.act;
+        const int32_t *a_order = amorder.p;
+        const int32_t *a_pos = in.pos;
         const int32_t *a_q = in.q;
         const int32_t *a_cen = cen.p;
         int32_t *a_label = label.p;
         int64_t a_s = s, a_m = m;
         int a_it = iters;
         unsigned long long *a_sum = lsum.p, *a_cnt = lcnt.p;
-        void *args[] = {&a_act, &a_s, &a_q, &a_cen, &a_m, &a_it, &a_label, &a_sum, &a_cnt};
+        void *args[] = {&a_order, &a_pos, &a_s, &a_q, &a_cen, &a_m, &a_it, &a_label, &a_sum, &a_cnt};
         prof_begin(KF_PARTITION, st);
         PMMF_CUDA_TRY(cudaLaunchCooperativeKernel(lloyd, dim3(g), dim3(256), args, sh, st));
         prof_end(KF_PARTITION, st, (double)iters * (double)s * (8.0 + 4.0 * dim),
