@@ -304,17 +304,26 @@ __global__ void k_sort_scatter(const uint32_t *key, int64_t n, int64_t nbins, in
     }
 }
 
-__global__ void k_digit(const uint64_t *key, const int32_t *cur, int64_t n, int shift,
-                        uint32_t *d) {
+constexpr int RADIX_BITS = 11;
+constexpr uint32_t RADIX_MASK = (1u << RADIX_BITS) - 1u;
+
+// First pass's digits (identity order).
+__global__ void k_digit(const uint64_t *key, int64_t n, uint32_t *d) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x)
-        d[i] = (uint32_t)((key[cur[i]] >> shift) & 0xFFu);
+        d[i] = (uint32_t)(key[i] & RADIX_MASK);
 }
 
-__global__ void k_compose(const int32_t *cur, const int32_t *perm, int64_t n, int32_t *next) {
+// next = cur o perm (cur NULL: the identity), and unless shift < 0 the next
+// pass's digits in that order.
+__global__ void k_compose(const int32_t *cur, const int32_t *perm, int64_t n, int32_t *next,
+                          const uint64_t *key, int shift, uint32_t *d) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
-         i += (int64_t)gridDim.x * blockDim.x)
-        next[i] = cur[perm[i]];
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t x = cur ? cur[perm[i]] : perm[i];
+        next[i] = x;
+        if (shift >= 0) d[i] = (uint32_t)((key[x] >> shift) & RADIX_MASK);
+    }
 }
 
 __global__ void k_iota(int32_t *p, int64_t n) {
@@ -361,23 +370,26 @@ pmmf_status stable_sort_by_key(const uint32_t *key, int64_t n, int64_t nbins, in
 pmmf_status radix_sort_u64(const uint64_t *key, int64_t n, int bits, int32_t *perm,
                            cudaStream_t st) {
     if (n <= 0) return PMMF_OK;
-    DBuf<int32_t> cur, tmp;
+    if (bits <= 0) return iota_i32(perm, n, st);
+    // LSD passes of RADIX_BITS bits; the permutation so far alternates
+    // between 'other' and perm so that the last pass writes perm
+    const int passes = (bits + RADIX_BITS - 1) / RADIX_BITS;
+    DBuf<int32_t> other, tmp;
     DBuf<uint32_t> digit;
-    PMMF_TRY(cur.alloc(n, st));
+    PMMF_TRY(other.alloc(n, st));
     PMMF_TRY(tmp.alloc(n, st));
     PMMF_TRY(digit.alloc(n, st));
-    PMMF_TRY(iota_i32(cur.p, n, st));
-    for (int shift = 0; shift < bits; shift += 8) {
-        k_digit<<<grid_for(n, 256), 256, 0, st>>>(key, cur.p, n, shift, digit.p);
-        PMMF_TRY(launched("radix_digit"));
-        PMMF_TRY(stable_sort_by_key(digit.p, n, 256, tmp.p, st));
-        k_compose<<<grid_for(n, 256), 256, 0, st>>>(cur.p, tmp.p, n, perm);
+    k_digit<<<grid_for(n, 256), 256, 0, st>>>(key, n, digit.p);
+    PMMF_TRY(launched("radix_digit"));
+    const int32_t *cur = nullptr;
+    for (int p = 0; p < passes; ++p) {
+        PMMF_TRY(stable_sort_by_key(digit.p, n, int64_t(1) << RADIX_BITS, tmp.p, st));
+        int32_t *next = ((passes - 1 - p) % 2 == 0) ? perm : other.p;
+        const int shift = p + 1 < passes ? (p + 1) * RADIX_BITS : -1;
+        k_compose<<<grid_for(n, 256), 256, 0, st>>>(cur, tmp.p, n, next, key, shift, digit.p);
         PMMF_TRY(launched("radix_compose"));
-        PMMF_CUDA_TRY(cudaMemcpyAsync(cur.p, perm, sizeof(int32_t) * (size_t)n,
-                                      cudaMemcpyDeviceToDevice, st));
+        cur = next;
     }
-    if (bits <= 0) PMMF_CUDA_TRY(cudaMemcpyAsync(perm, cur.p, sizeof(int32_t) * (size_t)n,
-                                                 cudaMemcpyDeviceToDevice, st));
     return PMMF_OK;
 }
 
@@ -502,11 +514,18 @@ __global__ void k_sumsq_partial(const double *v, int64_t n, double *part) {
     }
 }
 
-__global__ void k_sum_serial(const double *part, int np, double *out) {
-    if (threadIdx.x == 0 && blockIdx.x == 0) {
-        double t = 0.0;
-        for (int q = 0; q < np; ++q) t += part[q];
-        *out = t;
+// Sum of the partials in a fixed tree order (one block, one thread per
+// partial, np <= blockDim.x <= 1024): deterministic, no serial chain.
+__global__ void k_sum_tree(const double *part, int np, double *out) {
+    double t = threadIdx.x < (unsigned)np ? part[threadIdx.x] : 0.0;
+    t = warp_sum(t);
+    __shared__ double ws[32];
+    if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = t;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        t = threadIdx.x < (blockDim.x >> 5) ? ws[threadIdx.x] : 0.0;
+        t = warp_sum(t);
+        if (threadIdx.x == 0) *out = t;
     }
 }
 
@@ -554,8 +573,8 @@ pmmf_status sum_squares(const double *v, int64_t n, double *out, cudaStream_t st
     PMMF_TRY(part.alloc(RED_BLOCKS, st));
     k_sumsq_partial<<<RED_BLOCKS, 256, 0, st>>>(v, n, part.p);
     PMMF_TRY(launched("sumsq_partial"));
-    k_sum_serial<<<1, 32, 0, st>>>(part.p, RED_BLOCKS, out);
-    return launched("sum_serial");
+    k_sum_tree<<<1, (RED_BLOCKS + 31) / 32 * 32, 0, st>>>(part.p, RED_BLOCKS, out);
+    return launched("sum_tree");
 }
 
 }  // namespace pmmf
