@@ -231,7 +231,7 @@ pmmf_status stage_input(const pmmf_matrix *A, Csr &out, unsigned *status_d, cuda
         // structure first (monotone rows, columns in range and ascending), on
         // the stored entries; then drop exact zeros and check symmetry
         PMMF_CUDA_TRY(cudaMemsetAsync(status_d, 0, sizeof(unsigned), st));
-        PMMF_TRY(validate_csr(n, rp, ci, v, status_d, st));
+        PMMF_TRY(validate_csr(n, rp, ci, v, status_d, st, false));
         unsigned hs = 0;
         PMMF_CUDA_TRY(cudaMemcpyAsync(&hs, status_d, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
         PMMF_CUDA_TRY(cudaStreamSynchronize(st));

@@ -251,8 +251,10 @@ pmmf_status dense_to_csr(const double *a, int64_t n, int64_t ld, DBuf<int64_t> &
 pmmf_status csr_drop_zeros(int64_t n, const int64_t *rp, const int32_t *ci, const double *v,
                            DBuf<int64_t> &rowptr, DBuf<int32_t> &col, DBuf<double> &val,
                            cudaStream_t st);
+// Structure (rows monotone, columns in range and ascending) and finiteness;
+// with symmetry, also exact symmetry (every (i, j, x) has (j, i, x) stored).
 pmmf_status validate_csr(int64_t n, const int64_t *rp, const int32_t *ci, const double *v,
-                         unsigned *status, cudaStream_t st);
+                         unsigned *status, cudaStream_t st, bool symmetry = true);
 pmmf_status sum_squares(const double *v, int64_t n, double *out, cudaStream_t st);
 pmmf_status iota_i32(int32_t *p, int64_t n, cudaStream_t st);
 

@@ -464,8 +464,10 @@ __global__ void k_csr_write(int64_t n, const int64_t *rp, const int32_t *ci, con
     }
 }
 
-// Structure (rows, ascending columns), finiteness and exact symmetry: the
-// entry (y, x) must exist for every stored (x, y) and carry the same bits.
+// Structure (rows, ascending columns), finiteness and, with SYM, exact
+// symmetry: the entry (y, x) must exist for every stored (x, y) and carry the
+// same bits.
+template <bool SYM>
 __global__ void k_validate(int64_t n, const int64_t *rp, const int32_t *ci, const double *v,
                            unsigned *status) {
     int lane = threadIdx.x & 31;
@@ -480,6 +482,7 @@ __global__ void k_validate(int64_t n, const int64_t *rp, const int32_t *ci, cons
             double x = v[q];
             if (y < 0 || y >= n || (q > b && ci[q - 1] >= y)) { bad |= ST_BAD_CSR; continue; }
             if (!isfinite(x)) bad |= ST_NONFINITE;
+            if (!SYM) continue;
             int64_t lo = rp[y], hi = rp[y + 1];
             bool found = false;
             while (lo < hi) {
@@ -563,8 +566,9 @@ pmmf_status csr_drop_zeros(int64_t n, const int64_t *rp, const int32_t *ci, cons
 }
 
 pmmf_status validate_csr(int64_t n, const int64_t *rp, const int32_t *ci, const double *v,
-                         unsigned *status, cudaStream_t st) {
-    k_validate<<<grid_for(n * 32, 256), 256, 0, st>>>(n, rp, ci, v, status);
+                         unsigned *status, cudaStream_t st, bool symmetry) {
+    if (symmetry) k_validate<true><<<grid_for(n * 32, 256), 256, 0, st>>>(n, rp, ci, v, status);
+    else k_validate<false><<<grid_for(n * 32, 256), 256, 0, st>>>(n, rp, ci, v, status);
     return launched("validate");
 }
 
