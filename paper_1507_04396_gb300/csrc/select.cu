@@ -738,7 +738,17 @@ k_select_fast(const int64_t *coff, const int32_t *members, const int64_t *goff, 
                 }
                 fp_sync();
                 const double na = s_x[0], nd = s_x[1], ma = s_x[2], md2 = s_x[3];
-                if (wid == 2 && lane == 0) {
+                if (wid < 2) {
+                    // the new weights of i (warp 0) and j (warp 1), next to the
+                    // elimination rather than after it; the survivor's is
+                    // merged in P2 (the eliminated one is never read again)
+                    const double x = wid == 0 ? na : nd;
+                    const double wv = pos_bits(x) ? __ddiv_rn(1.0, __dsqrt_rn(x)) : 0.0;
+                    if (lane == 0) {
+                        s_wn[par][wid] = wv;
+                        w[wid == 0 ? i : j] = wv;
+                    }
+                } else if (wid == 2 && lane == 0) {
                     const double di = __dsub_rn(na, __dmul_rn(ma, ma));
                     const double dj = __dsub_rn(nd, __dmul_rn(md2, md2));
                     const int le = lt_bits(di, dj) ? i : j;
@@ -766,23 +776,27 @@ k_select_fast(const int64_t *coff, const int32_t *members, const int64_t *goff, 
                     s_nb[par][lane] = select_bit(mask, nwords, p2 + (lane & 1), lane < 2 ? i : j);
                 }
             }
-            __syncthreads();
+            // S1 (barrier 4): the column warps and FP64 warps 2 and 3, once per
+            // step.  Warps 0 and 1 (the weights) go straight on to barrier 2
+            // and read the elimination from behind it.
+            if (wid >= 2) asm volatile("bar.sync 4, %0;" ::"n"(NT - 64) : "memory");
             // ---- P2.  Column warps: (A) score the candidates of the next
             // pivot and publish each warp's best (barrier 2, arrive), (B) write
             // the survivor's rotated row and column into G and M, then take the
-            // next step's (i, j) (barrier 3, wait).  FP64 warps: the survivor's
-            // new weight, then (barrier 2, wait) the block's best partner,
-            // published with barrier 3 (arrive), and on to the next step's
-            // chain while the column warps are still writing.  Both roles pass
-            // each barrier exactly once per step with a next step; the column
-            // warps' writes are visible to their next loads through barrier 3.
-            const double cc = s_c, ss = s_s;
-            const int le = s_le;
-            const int surv = le == i ? j : i;
-            // the pivot of step t + 1 is the p-th survivor: a1 unless the
-            // eliminated index sits at or before it
-            const int inext = more ? (le <= a1 ? a2 : a1) : -1;
+            // next step's (i, j) (barrier 3, wait).  FP64 warps: (barrier 2,
+            // wait) the block's best partner merged with the survivor's own
+            // candidate, published with barrier 3 (arrive), and on to the next
+            // step's chain while the column warps are still writing.  Both
+            // roles pass barriers 2 and 3 exactly once per step with a next
+            // step; the column warps' writes are visible to their next loads
+            // through barrier 3.
             if (ct >= 0) {
+                const double cc = s_c, ss = s_s;
+                const int le = s_le;
+                const int surv = le == i ? j : i;
+                // the pivot of step t + 1 is the p-th survivor: a1 unless the
+                // eliminated index sits at or before it
+                const int inext = more ? (le <= a1 ? a2 : a1) : -1;
                 if (more) {
                     const int nwork = s_nwork[par];
                     const bool si = surv == i;
@@ -846,21 +860,16 @@ k_select_fast(const int64_t *coff, const int32_t *members, const int64_t *goff, 
                     mij = s_nxm;
                 }
             } else {
-                if (wid == 0) {
-                    // the survivor's new weight (for the merge below)
-                    const double x = gd[surv];
-                    const double ws = pos_bits(x) ? __ddiv_rn(1.0, __dsqrt_rn(x)) : 0.0;
-                    if (lane == 0) {
-                        w[surv] = ws;
-                        s_wn[par][0] = ws;
-                    }
-                }
                 if (more) {
                     if (lane == 0) wbest[wid] = cand_none();
                     asm volatile("bar.sync 2, %0;" ::"n"(NT) : "memory");
+                    const int le = s_le;
+                    const int surv = le == i ? j : i;
+                    const int inext = le <= a1 ? a2 : a1;
                     Cand nbest = block_best<NW>(wbest);
                     if (inext != i && inext != j)
-                        cand_merge(nbest, cand_make_sparse(s_survg[par], s_survm[par], s_wn[par][0], surv));
+                        cand_merge(nbest, cand_make_sparse(s_survg[par], s_survm[par],
+                                                           s_wn[par][surv == i ? 0 : 1], surv));
                     if (t + 2 < e) {
                         a1 = le == i ? s_nb[par][0] : s_nb[par][2];
                         a2 = le == i ? s_nb[par][1] : s_nb[par][3];
