@@ -521,16 +521,22 @@ __device__ __forceinline__ Cand block_best(const Cand *wb) {
 
 // Restructured search for clusters of up to KPT * NCT coordinates (column
 // thread t owns columns t, t + NCT, ...).  Per step t with pivot i, partner j:
-//   P1   FP64 warps: the angle (prefix computed by all four, then c and s by
-//        two), the four new diagonal entries of the 2x2 blocks (one each), the
-//        new weights of i and j and the elimination; bookkeeping.  Column
-//        threads: load their columns of rows i, j and of the two rows a1, a2
-//        that can be the pivot of step t + 1, classify them and list those
-//        that may need FP64 work.
+//   P1   FP64 warps: the angle (prefix computed by warps 0 and 1, then c by
+//        one and s by the other), the four new diagonal entries of the 2x2
+//        blocks (one each); then the new weights of i and j (warps 0 and 1)
+//        beside the elimination and bookkeeping (warp 2) and the candidates
+//        for the pivot of step t + 2 (warp 3).  Column threads: load their
+//        columns of rows i, j and of the two rows a1, a2 that can be the pivot
+//        of step t + 1, classify them and list those that may need FP64 work.
 //   P2   column threads: FP64 work on the listed columns (the survivor's row
 //        and column; the eliminated coordinate's are never read again), zero
-//        and nonzero candidates for the next pivot; warp argmax.
-// Two block barriers per step.  The arithmetic, and so every bit, is k_select's.
+//        and nonzero candidates for the next pivot; warp argmax.  FP64 warps:
+//        the block's best merged with the survivor's own candidate.
+// Barriers per step: named barrier 4 between P1 and P2 (every warp but FP64
+// warps 0 and 1), 2 (column warps arrive with their bests, FP64 warps wait)
+// and 3 (FP64 warps arrive with the next (i, j), column warps wait); FP64
+// warps also meet at named barrier 1.  The arithmetic, and so every bit, is
+// k_select's.
 template <int KPT, int NT>
 __global__ void __launch_bounds__(NT)
 k_select_fast(const int64_t *coff, const int32_t *members, const int64_t *goff, double *Gall,
