@@ -538,7 +538,7 @@ __device__ __forceinline__ Cand block_best(const Cand *wb) {
 // warps also meet at named barrier 1.  The arithmetic, and so every bit, is
 // k_select's.
 template <int KPT, int NT>
-__global__ void __launch_bounds__(NT)
+__global__ void __launch_bounds__(NT, NT <= 256 ? 2 : 1)
 k_select_fast(const int64_t *coff, const int32_t *members, const int64_t *goff, double *Gall,
               double *Mall, const int64_t *roff, uint64_t seed, int64_t stage, RotRec *rec,
               Rot2 *lvlrot, int32_t *lvl_off, int32_t *nlev, int32_t *elimflag,
