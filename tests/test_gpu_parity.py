@@ -286,3 +286,37 @@ def test_stage_pipeline_edge_cases(case):
         g, o = factor_both(a, max_stages=2, **kw)
         assert g.info().stages == 2
     assert_same_factorization(g, o)
+
+
+@gpu
+def test_concurrent_host_threads_match_oracle():
+    """Two host threads factor at the same time, each on its own CUDA stream
+    (each thread has its own mapped readback words and its own side stream):
+    both factorizations equal the oracle's, bit for bit."""
+    import threading
+    import torch
+    pm = gpu_lib()
+    cases = [I.knn_laplacian(3000, seed=5), I.knn_laplacian(2500, seed=7)]
+    kw = dict(k=2, eta=0.5, cluster_size=150, core_size=60, seed=6)
+    out = [None, None]
+    errs = []
+
+    def run(q):
+        try:
+            s = torch.cuda.Stream()
+            f = pm.factor(cases[q], record_stages=True, stream=s, **kw)
+            s.synchronize()
+            out[q] = f
+        except Exception as e:  # reported below, on the main thread
+            errs.append(e)
+
+    threads = [threading.Thread(target=run, args=(q,)) for q in range(2)]
+    for t in threads:
+        t.start()
+    for t in threads:
+        t.join()
+    assert not errs, errs
+    for q, a in enumerate(cases):
+        o = O.factor(a.n, a.rowptr, a.col, a.val, a.coords, record=True, **kw)
+        assert o.status == 0
+        assert_same_factorization(out[q], o)
