@@ -23,13 +23,15 @@ namespace {
 constexpr int AP_THREADS = 256;
 
 // One CTA per cluster: gather x[members][0..nr), apply the levels, scatter.
-template <bool TRANSPOSE>
+// NR > 0: nr is NR, known at compile time (the divisions by nr become shifts).
+template <bool TRANSPOSE, int NR>
 __global__ void __launch_bounds__(AP_THREADS)
 k_apply_stage(const int64_t *coff, const int32_t *members, const int64_t *roff,
               const int32_t *lvl_off, const int32_t *nlev, const Rot2 *lvlrot, double *x,
-              int64_t ld, int64_t r0, int nr, int K, const int32_t *kidx, const int32_t *kkv,
+              int64_t ld, int64_t r0, int nr_rt, int K, const int32_t *kidx, const int32_t *kkv,
               const int32_t *lvlidx, const double *kO) {
     extern __shared__ double sx[];
+    const int nr = NR > 0 ? NR : nr_rt;
     const int64_t u = blockIdx.x;
     const int64_t base = coff[u];
     const int c = (int)(coff[u + 1] - base);
@@ -333,20 +335,18 @@ pmmf_status apply_rotations(const ApplyStages &S, bool transpose, double *x, int
         for (int64_t r0 = 0; r0 < nrhs; r0 += chunk) {
             int nr = (int)(nrhs - r0 < chunk ? nrhs - r0 : chunk);
             size_t sh = sizeof(double) * (size_t)a.cmax * (size_t)nr;
+            // one right-hand side and blocks of 8 (PCG's usual widths) get
+            // instantiations with the width fixed
+            auto kern = transpose ? (nr == 8 ? k_apply_stage<true, 8> : nr == 1 ? k_apply_stage<true, 1>
+                                                                      : k_apply_stage<true, 0>)
+                                  : (nr == 8 ? k_apply_stage<false, 8> : nr == 1 ? k_apply_stage<false, 1>
+                                                                       : k_apply_stage<false, 0>);
             prof_begin(KF_APPLY, st);
-            if (transpose) {
-                if (sh > 48 * 1024)
-                    PMMF_CUDA_TRY(cudaFuncSetAttribute(k_apply_stage<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh));
-                k_apply_stage<true><<<(unsigned)a.m, AP_THREADS, sh, st>>>(
-                    a.coff, a.members, a.roff, a.lvl_off, a.nlev, a.lvlrot, x, ld, r0, nr, a.K,
-                    a.kidx, a.kkv, a.lvlidx, a.kO);
-            } else {
-                if (sh > 48 * 1024)
-                    PMMF_CUDA_TRY(cudaFuncSetAttribute(k_apply_stage<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh));
-                k_apply_stage<false><<<(unsigned)a.m, AP_THREADS, sh, st>>>(
-                    a.coff, a.members, a.roff, a.lvl_off, a.nlev, a.lvlrot, x, ld, r0, nr, a.K,
-                    a.kidx, a.kkv, a.lvlidx, a.kO);
-            }
+            if (sh > 48 * 1024)
+                PMMF_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh));
+            kern<<<(unsigned)a.m, AP_THREADS, sh, st>>>(a.coff, a.members, a.roff, a.lvl_off, a.nlev,
+                                                        a.lvlrot, x, ld, r0, nr, a.K, a.kidx, a.kkv,
+                                                        a.lvlidx, a.kO);
             // the stage's coordinates read and written once per right-hand side,
             // their ids, and the rotations (24 B each) with their level offsets
             prof_end(KF_APPLY, st,
