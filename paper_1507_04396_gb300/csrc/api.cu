@@ -45,6 +45,7 @@ struct pmmf_handle {
     int inv_state = 0;  // 0 not formed, 1 formed, 2 not SPD
     pmmf::DBuf<double> core_isqrt;       // core^{-1/2} per block (xi = 1/2)
     int isqrt_state = 0;                 // as inv_state
+    pmmf::DBuf<double> hrcp, hisr;       // 1 / h_i, 1 / sqrt(h_i): formed with core_inv, core_isqrt
     int isqrt_iters = 0;                 // Newton-Schulz steps it took
     pmmf::ApplyStages views;
     // core blocks (one for a single factorization, one per matrix of a batch)
@@ -1235,6 +1236,8 @@ pmmf_status ensure_inverse(pmmf_handle *f, cudaStream_t st) {
         f->inv_state = 2;
         return fail(PMMF_ERR_NOT_SPD, "H is not positive definite");
     }
+    PMMF_TRY(f->hrcp.alloc(f->n, st));
+    PMMF_TRY(h_reciprocals(f->hdiag.p, f->n, false, f->hrcp.p, st));
     f->inv_state = 1;
     return PMMF_OK;
 }
@@ -1260,6 +1263,8 @@ pmmf_status ensure_isqrt(pmmf_handle *f, cudaStream_t st) {
         f->isqrt_state = 2;
         return fail(PMMF_ERR_NOT_SPD, "H is not positive definite");
     }
+    PMMF_TRY(f->hisr.alloc(f->n, st));
+    PMMF_TRY(h_reciprocals(f->hdiag.p, f->n, true, f->hisr.p, st));
     f->isqrt_state = 1;
     return PMMF_OK;
 }
@@ -1277,6 +1282,8 @@ HData hdata(const pmmf_handle *f) {
     H.core = f->core.p;
     H.core_inv = f->core_inv.p;
     H.core_isqrt = f->core_isqrt.p;
+    H.hrcp = f->inv_state == 1 ? f->hrcp.p : nullptr;
+    H.hisr = f->isqrt_state == 1 ? f->hisr.p : nullptr;
     return H;
 }
 

@@ -94,18 +94,29 @@ __global__ void k_copy_block(const double *x, int64_t ldx, double *y, int64_t ld
 
 // Wavelet part of H (MODE 0), H^-1 (1) or H^-1/2 (2) (core coordinates
 // untouched here); gathers the core slice into zc.
+// rc (may be NULL): the per-coordinate reciprocals of MODE 1 or 2, so the
+// wavelet part is one multiply (within an ulp of the divide) instead of an
+// FP64 divide (and square root) per entry.
 template <int MODE>
 __global__ void k_h_diag(double *x, int64_t ld, int64_t n, int64_t nrhs, const double *hdiag,
-                         const int32_t *core_pos, double *zc) {
+                         const int32_t *core_pos, double *zc, const double *rc) {
     for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n * nrhs;
          q += (int64_t)gridDim.x * blockDim.x) {
         int64_t i = q / nrhs, r = q - i * nrhs;
         int32_t cp = core_pos[i];
         double v = x[i * ld + r];
         if (cp >= 0) zc[(int64_t)cp * nrhs + r] = v;
+        else if (MODE != 0 && rc) x[i * ld + r] = __dmul_rn(rc[i], v);
         else x[i * ld + r] = MODE == 2 ? __ddiv_rn(v, __dsqrt_rn(hdiag[i]))
                            : MODE == 1 ? __ddiv_rn(v, hdiag[i]) : __dmul_rn(hdiag[i], v);
     }
+}
+
+template <bool ROOT>
+__global__ void k_recip(const double *h, int64_t n, double *out) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = ROOT ? __ddiv_rn(1.0, __dsqrt_rn(h[i])) : __ddiv_rn(1.0, h[i]);
 }
 
 // Core part: x[core_idx[a]] = sum_b C[a][b] zc[b] over the slots b of a's
@@ -364,12 +375,19 @@ pmmf_status copy_block(const double *x, int64_t ldx, double *y, int64_t ldy, int
     return launched("copy_block");
 }
 
+pmmf_status h_reciprocals(const double *hdiag, int64_t n, bool root, double *out, cudaStream_t st) {
+    if (n <= 0) return PMMF_OK;
+    if (root) k_recip<true><<<grid_for(n, 256), 256, 0, st>>>(hdiag, n, out);
+    else k_recip<false><<<grid_for(n, 256), 256, 0, st>>>(hdiag, n, out);
+    return launched("h_reciprocals");
+}
+
 pmmf_status apply_h_scratch(const HData &H, int mode, double *x, int64_t ld, int64_t nrhs,
                             double *zc, cudaStream_t st) {
     const unsigned g = grid_for(H.n * nrhs, 256);
-    if (mode == 2) k_h_diag<2><<<g, 256, 0, st>>>(x, ld, H.n, nrhs, H.hdiag, H.core_pos, zc);
-    else if (mode == 1) k_h_diag<1><<<g, 256, 0, st>>>(x, ld, H.n, nrhs, H.hdiag, H.core_pos, zc);
-    else k_h_diag<0><<<g, 256, 0, st>>>(x, ld, H.n, nrhs, H.hdiag, H.core_pos, zc);
+    if (mode == 2) k_h_diag<2><<<g, 256, 0, st>>>(x, ld, H.n, nrhs, H.hdiag, H.core_pos, zc, H.hisr);
+    else if (mode == 1) k_h_diag<1><<<g, 256, 0, st>>>(x, ld, H.n, nrhs, H.hdiag, H.core_pos, zc, H.hrcp);
+    else k_h_diag<0><<<g, 256, 0, st>>>(x, ld, H.n, nrhs, H.hdiag, H.core_pos, zc, nullptr);
     PMMF_TRY(launched("h_diag"));
     const double *C = mode == 2 ? H.core_isqrt : mode == 1 ? H.core_inv : H.core;
     k_core_gemv<<<grid_for(H.m * nrhs, 64), 64, 0, st>>>(C, H.nblk, H.bs, H.bdim, zc, nrhs,

@@ -37,7 +37,14 @@ struct HData {
     const double *core = nullptr;        // nblk * bs * bs
     const double *core_inv = nullptr;    // nblk * bs * bs
     const double *core_isqrt = nullptr;  // bs * bs (single core): core^{-1/2}
+    // n: 1 / h_i and 1 / sqrt(h_i) of the diagonal (formed with core_inv and
+    // core_isqrt; NULL: the wavelet part divides instead of multiplying)
+    const double *hrcp = nullptr;
+    const double *hisr = nullptr;
 };
+
+// out[i] = 1 / h_i (root false) or 1 / sqrt(h_i) (root true), i < n.
+pmmf_status h_reciprocals(const double *hdiag, int64_t n, bool root, double *out, cudaStream_t st);
 
 struct DevCsr {
     int64_t n = 0;
