@@ -371,6 +371,13 @@ pmmf_status apply_rotations(const ApplyStages &S, bool transpose, double *x, int
 
 pmmf_status copy_block(const double *x, int64_t ldx, double *y, int64_t ldy, int64_t n,
                        int64_t nrhs, cudaStream_t st) {
+    if (ldx == nrhs && ldy == nrhs) {
+        // contiguous: one device copy, no per-entry index arithmetic
+        if (n * nrhs > 0)
+            PMMF_CUDA_TRY(cudaMemcpyAsync(y, x, sizeof(double) * (size_t)(n * nrhs),
+                                          cudaMemcpyDeviceToDevice, st));
+        return PMMF_OK;
+    }
     k_copy_block<<<grid_for(n * nrhs, 256), 256, 0, st>>>(x, ldx, y, ldy, n, nrhs);
     return launched("copy_block");
 }
