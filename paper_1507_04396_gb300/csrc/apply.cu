@@ -97,9 +97,11 @@ __global__ void k_copy_block(const double *x, int64_t ldx, double *y, int64_t ld
 // rc (may be NULL): the per-coordinate reciprocals of MODE 1 or 2, so the
 // wavelet part is one multiply (within an ulp of the divide) instead of an
 // FP64 divide (and square root) per entry.
-template <int MODE>
-__global__ void k_h_diag(double *x, int64_t ld, int64_t n, int64_t nrhs, const double *hdiag,
+// NRC > 0: nrhs is NRC, known at compile time.
+template <int MODE, int NRC>
+__global__ void k_h_diag(double *x, int64_t ld, int64_t n, int64_t nrhs_rt, const double *hdiag,
                          const int32_t *core_pos, double *zc, const double *rc) {
+    const int64_t nrhs = NRC > 0 ? NRC : nrhs_rt;
     for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n * nrhs;
          q += (int64_t)gridDim.x * blockDim.x) {
         int64_t i = q / nrhs, r = q - i * nrhs;
@@ -392,9 +394,16 @@ pmmf_status h_reciprocals(const double *hdiag, int64_t n, bool root, double *out
 pmmf_status apply_h_scratch(const HData &H, int mode, double *x, int64_t ld, int64_t nrhs,
                             double *zc, cudaStream_t st) {
     const unsigned g = grid_for(H.n * nrhs, 256);
-    if (mode == 2) k_h_diag<2><<<g, 256, 0, st>>>(x, ld, H.n, nrhs, H.hdiag, H.core_pos, zc, H.hisr);
-    else if (mode == 1) k_h_diag<1><<<g, 256, 0, st>>>(x, ld, H.n, nrhs, H.hdiag, H.core_pos, zc, H.hrcp);
-    else k_h_diag<0><<<g, 256, 0, st>>>(x, ld, H.n, nrhs, H.hdiag, H.core_pos, zc, nullptr);
+    // blocks of 8 right-hand sides (PCG's usual width) with the width fixed
+    if (nrhs == 8) {
+        if (mode == 2) k_h_diag<2, 8><<<g, 256, 0, st>>>(x, ld, H.n, nrhs, H.hdiag, H.core_pos, zc, H.hisr);
+        else if (mode == 1) k_h_diag<1, 8><<<g, 256, 0, st>>>(x, ld, H.n, nrhs, H.hdiag, H.core_pos, zc, H.hrcp);
+        else k_h_diag<0, 8><<<g, 256, 0, st>>>(x, ld, H.n, nrhs, H.hdiag, H.core_pos, zc, nullptr);
+    } else {
+        if (mode == 2) k_h_diag<2, 0><<<g, 256, 0, st>>>(x, ld, H.n, nrhs, H.hdiag, H.core_pos, zc, H.hisr);
+        else if (mode == 1) k_h_diag<1, 0><<<g, 256, 0, st>>>(x, ld, H.n, nrhs, H.hdiag, H.core_pos, zc, H.hrcp);
+        else k_h_diag<0, 0><<<g, 256, 0, st>>>(x, ld, H.n, nrhs, H.hdiag, H.core_pos, zc, nullptr);
+    }
     PMMF_TRY(launched("h_diag"));
     const double *C = mode == 2 ? H.core_isqrt : mode == 1 ? H.core_inv : H.core;
     k_core_gemv<<<grid_for(H.m * nrhs, 64), 64, 0, st>>>(C, H.nblk, H.bs, H.bdim, zc, nrhs,
