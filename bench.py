@@ -163,6 +163,105 @@ def run_reference(args):
     return 0
 
 
+def host_cpu():
+    """(logical cores, CPU model) of this host."""
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except Exception:
+        pass
+    if model is None:
+        try:
+            for line in open("/proc/cpuinfo"):
+                if line.lower().startswith(("model name", "cpu part")):
+                    model = line.split(":", 1)[1].strip()
+                    break
+        except Exception:
+            pass
+    return os.cpu_count(), model
+
+
+def fp64_peak(stream):
+    """Measured FP64 FMA throughput (TFLOP/s) of this GPU from the library's
+    probe, else GB300's nominal rate."""
+    from paper_1507_04396_gb300 import pmmf
+    try:
+        return pmmf.pmmf_probe_fp64(stream), "measured (pmmf_probe_fp64, FP64 FMA throughput)"
+    except Exception:
+        return FP64_NOMINAL_TFLOPS, "nominal FP64"
+
+
+def roofline_of(dominant, prof, hbm, hbm_kind, f64, f64_kind):
+    """Roofline object of one kernel family from its profiled launches."""
+    if dominant in ("gram", "rows", "apply"):
+        ach = prof["bytes"] / (prof["ms"] / 1e3) / 1e9
+        roof = {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
+                "traffic": None, "kernel_family": dominant, "peak_kind": hbm_kind}
+    else:
+        ach = prof["flops"] / (prof["ms"] / 1e3) / 1e12
+        roof = {"bound": "alu", "achieved": ach, "peak": f64, "unit": "TFLOP/s", "frac": ach / f64,
+                "traffic": None, "kernel_family": dominant, "peak_kind": f64_kind}
+    roof["launches_profiled"] = prof["launches"]
+    roof["avg_launch_ms"] = prof["ms"] / max(prof["launches"], 1)
+    return roof
+
+
+def poisson_extras(dev, stream, flush, hbm):
+    """The 128^3 Poisson workload beside the headline: factor time, the
+    blocked update's GB/s on its first two stages, the matrix-free A~^-1 x
+    GB/s on 8 right-hand sides."""
+    import torch
+    from paper_1507_04396_gb300 import inputs as I, pmmf
+    a = I.poisson3d(POISSON["nx"], seed=POISSON["gen_seed"])
+    A = I.SymCSR(a.n, torch.from_numpy(a.rowptr).to(dev), torch.from_numpy(a.col).to(dev),
+                 torch.from_numpy(a.val).to(dev))
+    co = torch.from_numpy(a.coords).to(dev)
+    nx = POISSON["nx"]
+    bricks = torch.from_numpy(I.grid_bricks(nx, nx, nx, 8, 8, 4)).to(dev)
+    kw = dict(k=POISSON["k"], eta=POISSON["eta"], cluster_size=POISSON["cluster_size"],
+              core_size=POISSON["core_size"], seed=POISSON["seed"])
+    fac = lambda **x: pmmf.factor(A, coords=co, labels=bricks, stream=stream, **dict(kw, **x))
+    fac().close()
+    ts = []
+    for _ in range(3):
+        ms, f = _timed(stream, fac, 1, flush)
+        ts.append(ms)
+        info = f.info()
+        if _ < 2:
+            f.close()
+    # blocked update on stages 1-2 (the stages with >= 100 MB of traffic)
+    pmmf.pmmf_profile_begin(["rows"])
+    fac(max_stages=2).close()
+    rows = pmmf.pmmf_profile_end()["rows"]
+    rows_gbs = rows["bytes"] / (rows["ms"] / 1e3) / 1e9
+    x = torch.randn(a.n, POISSON["nrhs"], dtype=torch.float64, device=dev)
+    y = torch.empty_like(x)
+    for _ in range(3):
+        f.apply(pmmf.OP_A_INV, x, y, stream)
+    torch.cuda.synchronize()
+    pmmf.pmmf_profile_begin(["apply"])
+    for _ in range(10):
+        f.apply(pmmf.OP_A_INV, x, y, stream)
+    ap = pmmf.pmmf_profile_end()["apply"]
+    f.close()
+    apply_gbs = ap["bytes"] / (ap["ms"] / 1e3) / 1e9
+    return {
+        "workload": "poisson3d 128^3 (7-point FV, log-normal sigma=1, seed 4), FP64 CSR; stage 1: "
+                    "8x8x4 grid bricks, then k-means clusters of 256; k=2, eta=0.5, core 1024",
+        "n": a.n, "nnz": a.nnz, "stages": info.stages, "frobenius_error": info.error,
+        "factor_ms": sorted(ts)[1], "nnz_per_s": a.nnz / (sorted(ts)[1] / 1e3),
+        "update_stages_1_2": {"gbs": rows_gbs, "frac_of_hbm": rows_gbs / hbm,
+                              "algorithmic_bytes": rows["bytes"], "ms": rows["ms"],
+                              "launches": rows["launches"]},
+        "apply_a_inv_8rhs": {"gbs": apply_gbs, "frac_of_hbm": apply_gbs / hbm,
+                             "ms_per_apply": ap["ms"] / 10},
+    }
+
+
 def run_gpu(args):
     import numpy as np
     import torch
@@ -195,14 +294,7 @@ def run_gpu(args):
     for _ in range(max(args.warmup, 0)):
         factor().close()
 
-    # which kernel family dominates (one untimed profiled factorization)
-    pmmf.pmmf_profile_begin(pmmf.FAMILIES)
-    factor().close()
-    breakdown = pmmf.pmmf_profile_end()
-    dominant = max((f for f in breakdown if breakdown[f]["launches"] > 0),
-                   key=lambda f: breakdown[f]["ms"])
-
-    # timed region
+    # timed region: the product path as shipped (no profiling hooks)
     clocks = Clocks(local)
     l0 = pmmf.pmmf_launch_count()
     total_ms = 0.0
@@ -212,7 +304,6 @@ def run_gpu(args):
         torch.distributed.barrier()
     torch.cuda.synchronize()
     clocks.start()
-    pmmf.pmmf_profile_begin([dominant])
     for _ in range(args.steps):
         flush.zero_()
         e0 = torch.cuda.Event(enable_timing=True)
@@ -225,7 +316,6 @@ def run_gpu(args):
         info = f.info()
         err = info.error
         f.close()
-    prof = pmmf.pmmf_profile_end()[dominant]
     torch.cuda.synchronize()
     clk = clocks.stop()
     launches = pmmf.pmmf_launch_count() - l0
@@ -235,18 +325,20 @@ def run_gpu(args):
         total_ms = float(t.item())
     value = a.nnz * args.steps * ws / (total_ms / 1e3)
 
+    # per-kernel figures from a separate profiled pass (CUDA events around
+    # every launch on its stream; the search's flop count needs a readback,
+    # so this pass is slower than the timed one and is not the headline)
+    prof_steps = 3
+    pmmf.pmmf_profile_begin(pmmf.FAMILIES)
+    for _ in range(prof_steps):
+        flush.zero_()
+        factor().close()
+    breakdown = pmmf.pmmf_profile_end()
+    dominant = max((f for f in breakdown if breakdown[f]["launches"] > 0),
+                   key=lambda f: breakdown[f]["ms"])
     hbm, hbm_kind = peaks()
-    if dominant in ("gram", "rows", "apply"):
-        ach = prof["bytes"] / (prof["ms"] / 1e3) / 1e9
-        roof = {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
-                "traffic": None, "kernel_family": dominant, "peak_kind": hbm_kind}
-    else:
-        ach = prof["flops"] / (prof["ms"] / 1e3) / 1e12
-        roof = {"bound": "alu", "achieved": ach, "peak": FP64_NOMINAL_TFLOPS, "unit": "TFLOP/s",
-                "frac": ach / FP64_NOMINAL_TFLOPS, "traffic": None, "kernel_family": dominant,
-                "peak_kind": "nominal FP64"}
-    roof["launches_timed"] = prof["launches"]
-    roof["avg_launch_ms"] = prof["ms"] / max(prof["launches"], 1)
+    f64, f64_kind = fp64_peak(stream)
+    roof = roofline_of(dominant, breakdown[dominant], hbm, hbm_kind, f64, f64_kind)
 
     # matrix-free apply: y = U^T H U x on 8 right-hand sides
     f = factor()
@@ -265,7 +357,6 @@ def run_gpu(args):
     for _ in range(3):
         f.apply(pmmf.OP_A, x, y, stream)
     torch.cuda.synchronize()
-    pmmf.pmmf_profile_begin(["apply"])
     reps = 20
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
@@ -274,8 +365,11 @@ def run_gpu(args):
         f.apply(pmmf.OP_A, x, y, stream)
     e1.record(stream)
     e1.synchronize()
-    ap = pmmf.pmmf_profile_end()["apply"]
     apply_ms = e0.elapsed_time(e1) / reps
+    pmmf.pmmf_profile_begin(["apply"])
+    for _ in range(reps):
+        f.apply(pmmf.OP_A, x, y, stream)
+    ap = pmmf.pmmf_profile_end()["apply"]
     apply_gbs = ap["bytes"] / (ap["ms"] / 1e3) / 1e9 if ap["ms"] > 0 else None
     f.close()
 
@@ -295,14 +389,27 @@ def run_gpu(args):
     e2e = {"value": a.nnz * args.steps * ws / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
            "d2h_bytes_per_step": int(hd.nbytes)}
 
-    cpu = None
+    poisson = None
+    if rank == 0 and not args.no_extras:
+        poisson = poisson_extras(dev, stream, flush, hbm)
+
+    cpu = cpu_omp = None
     oracle_err = None
     if rank == 0 and ws == 1 and not args.no_cpu:
         from oracle import oracle as O
         O.build()
         t, oracle_err = cpu_oracle_run(a, runs=3)
+        cores, model = host_cpu()
         cpu = {"value": a.nnz / t, "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": "full workload, median of 3 single-thread factorizations"}
+               "sample": "full workload, median of 3 single-thread factorizations",
+               "host_cores": cores, "cpu_model": model}
+        r = O.time_factor_openmp(a.n, a.rowptr, a.col, a.val, a.coords, runs=3, **kw)
+        if r is not None:
+            tt, e_omp, threads = r
+            cpu_omp = {"value": a.nnz / tt, "unit": UNIT, "cores": threads, "kind": "oracle (OpenMP)",
+                       "sample": "full workload, median of 3 factorizations, clusters and rows "
+                                 "spread over the host's cores",
+                       "frobenius_error": e_omp, "host_cores": cores, "cpu_model": model}
 
     if rank == 0:
         line = {
@@ -313,13 +420,18 @@ def run_gpu(args):
                        "stages": info.stages, "rotations": info.rotations,
                        "frobenius_error": err, "oracle_frobenius_error": oracle_err,
                        "l2": "256 MiB buffer written between timed steps",
-                       "parallelism": "replicas" if ws > 1 else "single GPU"},
+                       "parallelism": "replicas" if ws > 1 else "single GPU",
+                       "timed_region": "no profiling hooks; per-kernel figures from a separate "
+                                       f"profiled pass of {prof_steps} factorizations"},
             "roofline": roof,
             "apply": {"op": "U^T H U x", "nrhs": NRHS_APPLY, "ms": apply_ms,
                       "rotation_pass_gbs": apply_gbs,
                       "frac_of_hbm": (apply_gbs / hbm) if apply_gbs else None},
-            "kernel_breakdown_ms": {k: round(v["ms"], 4) for k, v in breakdown.items() if v["launches"]},
-            "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches), "clocks": clk,
+            "kernel_breakdown_ms": {k: round(v["ms"] / prof_steps, 4)
+                                    for k, v in breakdown.items() if v["launches"]},
+            "poisson_128": poisson,
+            "cpu_baseline": cpu, "cpu_baseline_openmp": cpu_omp, "e2e": e2e,
+            "gpu_launches": int(launches), "clocks": clk,
         }
         print(json.dumps(line))
     if ws > 1:
@@ -427,7 +539,6 @@ def run_gpu_batch(args):
         torch.distributed.barrier()
     torch.cuda.synchronize()
     clocks.start()
-    pmmf.pmmf_profile_begin([dominant])
     info = errs = None
     for _ in range(args.steps):
         flush.zero_()
@@ -441,7 +552,6 @@ def run_gpu_batch(args):
         info = f.info()
         errs = f.batch()["errors"]
         f.close()
-    prof = pmmf.pmmf_profile_end()[dominant]
     torch.cuda.synchronize()
     clk = clocks.stop()
     launches = pmmf.pmmf_launch_count() - l0
@@ -452,17 +562,8 @@ def run_gpu_batch(args):
     value = big.nnz * args.steps * ws / (total_ms / 1e3)
 
     hbm, hbm_kind = peaks()
-    if dominant in ("gram", "rows", "apply"):
-        ach = prof["bytes"] / (prof["ms"] / 1e3) / 1e9
-        roof = {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
-                "traffic": None, "kernel_family": dominant, "peak_kind": hbm_kind}
-    else:
-        ach = prof["flops"] / (prof["ms"] / 1e3) / 1e12
-        roof = {"bound": "alu", "achieved": ach, "peak": FP64_NOMINAL_TFLOPS, "unit": "TFLOP/s",
-                "frac": ach / FP64_NOMINAL_TFLOPS, "traffic": None, "kernel_family": dominant,
-                "peak_kind": "nominal FP64"}
-    roof["launches_timed"] = prof["launches"]
-    roof["avg_launch_ms"] = prof["ms"] / max(prof["launches"], 1)
+    f64, f64_kind = fp64_peak(stream)
+    roof = roofline_of(dominant, breakdown[dominant], hbm, hbm_kind, f64, f64_kind)
 
     # the same matrices factored one pmmf_factor call each (per-matrix launches),
     # on every 16th matrix of the batch
@@ -557,6 +658,33 @@ def _timed(stream, fn, steps, flush):
     return total, out
 
 
+def tf32_peak(dev):
+    """Measured TF32 tensor throughput (TFLOP/s): cuBLAS FP32 GEMM with TF32
+    allowed, 8192^3, best of 5 after warm-up (CUDA events)."""
+    import torch
+    prev = torch.backends.cuda.matmul.allow_tf32
+    torch.backends.cuda.matmul.allow_tf32 = True
+    try:
+        n = 8192
+        a = torch.randn(n, n, device=dev)
+        b = torch.randn(n, n, device=dev)
+        for _ in range(3):
+            a @ b
+        best = None
+        for _ in range(5):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            a @ b
+            e1.record()
+            e1.synchronize()
+            t = e0.elapsed_time(e1)
+            best = t if best is None else min(best, t)
+        return 2.0 * n ** 3 / (best / 1e3) / 1e12, "measured tf32 (cuBLAS FP32 GEMM, TF32 allowed)"
+    finally:
+        torch.backends.cuda.matmul.allow_tf32 = prev
+
+
 def run_gpu_rbf(args):
     """Dense Gaussian RBF kernel (3-D mixture), k = 3, clusters of 512: the
     dense path in FP64 and, with --precision, the tensor-core Gram shortlist."""
@@ -584,14 +712,13 @@ def run_gpu_rbf(args):
     pmmf.pmmf_profile_begin(pmmf.FAMILIES)
     run(prec)().close()
     breakdown = pmmf.pmmf_profile_end()
+    gram = breakdown["gram"]
     clocks = Clocks(0)
     torch.cuda.synchronize()
     clocks.start()
-    pmmf.pmmf_profile_begin(["gram"])
     l0 = pmmf.pmmf_launch_count()
     ms, f = _timed(stream, run(prec), args.steps, flush)
     launches = pmmf.pmmf_launch_count() - l0
-    gram = pmmf.pmmf_profile_end()["gram"]
     clk = clocks.stop()
     info, st = f.info(), f.precision_stats()
     rots = [f.rotations(p) for p in range(info.stages)]
@@ -608,19 +735,22 @@ def run_gpu_rbf(args):
         g.close()
     value = n * n * args.steps / (ms / 1e3)
     if prec != 0:
-        peak = float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["bf16_tflops"]) \
-            if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")) else 1933.5
-        # tf32 runs at half the bf16 rate; the split does three products per term
-        pk = peak / 2 if prec == 1 else peak
+        if prec == 1:
+            pk, pk_kind = tf32_peak(dev)
+        else:
+            pk = float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["bf16_tflops"]) \
+                if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")) else 1900.0
+            pk_kind = "measured bf16 (cuBLAS)"
         ach = gram["flops"] / (gram["ms"] / 1e3) / 1e12
         roof = {"bound": "tensor", "achieved": ach, "peak": pk, "unit": "TFLOP/s", "frac": ach / pk,
                 "traffic": None, "kernel_family": "gram (tensor-core split product)",
-                "peak_kind": "measured bf16" + (" x 1/2 (tf32)" if prec == 1 else "")}
+                "peak_kind": pk_kind}
     else:
+        f64, f64_kind = fp64_peak(stream)
         ach = gram["flops"] / (gram["ms"] / 1e3) / 1e12
-        roof = {"bound": "alu", "achieved": ach, "peak": FP64_NOMINAL_TFLOPS, "unit": "TFLOP/s",
-                "frac": ach / FP64_NOMINAL_TFLOPS, "traffic": None, "kernel_family": "gram (FP64)",
-                "peak_kind": "nominal FP64"}
+        roof = {"bound": "alu", "achieved": ach, "peak": f64, "unit": "TFLOP/s",
+                "frac": ach / f64, "traffic": None, "kernel_family": "gram (FP64)",
+                "peak_kind": f64_kind}
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
@@ -822,6 +952,8 @@ def main():
     ap.add_argument("--impl", choices=["gpu", "reference"], default="gpu")
     ap.add_argument("--n", type=int, default=WORK["n"])
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the 128^3 Poisson figures beside the headline")
     ap.add_argument("--workload", choices=["knn", "er_batch", "rbf_dense", "poisson", "scaling",
                                            "quality"],
                     default="knn",

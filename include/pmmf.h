@@ -405,6 +405,20 @@ void pmmf_clear_tuning(void);
 /* Number of GPU kernel launches this process has issued through the library. */
 uint64_t pmmf_launch_count(void);
 
+/* Number of device allocations this process has requested through the
+ * library (every device buffer it owns, transient or kept, is one request).
+ * A diagnostic with no counterpart in the paper: a caller can check that a
+ * call it expects to be allocation-free (pmmf_apply_noalloc) made none. */
+uint64_t pmmf_alloc_count(void);
+
+/* FP64 FMA throughput of the current device in TFLOP/s (HOST output), the
+ * denominator of the roofline fraction of the FP64-bound kernels.  A
+ * measurement aid with no counterpart in the paper: every SM runs 8 CTAs of
+ * 256 threads, each thread 8 independent chains of 4,096 dependent fmas;
+ * the best of three timed launches (CUDA events on stream, after one
+ * warm-up launch) counts 2 flops per fma.  Synchronizes the stream. */
+pmmf_status pmmf_probe_fp64(double *tflops, void *stream);
+
 /* ---- profiling (measurement aid; no counterpart in the paper) -------------
  * Kernel families: 0 partition (k-means assignment), 1 Gram, 2 rotation
  * search, 3 blocked-update row kernels, 4 matrix-free apply, 5 other.

@@ -41,7 +41,87 @@ def build(force: bool = False) -> str:
     return _SO
 
 
+_SO_OMP = os.path.join(_BUILD, "liboracle_omp.so")
+
+
+def build_openmp(force: bool = False):
+    """The same source compiled with OpenMP (clusters and rows spread over the
+    host's cores, the paper's m-fold CPU parallelism).  Used only to time a
+    multi-core CPU baseline; its results equal the single-thread build's.
+    Returns the library path, or None if the compiler has no OpenMP."""
+    os.makedirs(_BUILD, exist_ok=True)
+    if force or not os.path.exists(_SO_OMP) or os.path.getmtime(_SO_OMP) < max(
+            os.path.getmtime(_SRC), os.path.getmtime(os.path.join(_HERE, "pmmf_oracle.h"))):
+        tmp = _SO_OMP + f".{os.getpid()}.tmp"
+        try:
+            subprocess.check_call(["gcc", "-std=c11", "-O2", "-ffp-contract=off", "-fno-fast-math",
+                                   "-fopenmp", "-Wall", "-Wextra", "-Wno-unused-parameter", "-fPIC",
+                                   "-shared", "-o", tmp, _SRC, "-lm"],
+                                  stdout=subprocess.DEVNULL, stderr=subprocess.DEVNULL)
+        except (subprocess.CalledProcessError, OSError):
+            return None
+        os.replace(tmp, _SO_OMP)
+    return _SO_OMP
+
+
 _lib = None
+_lib_omp = None
+
+
+def _declare_factor(L):
+    vp = C.c_void_p
+    L.or_factor.restype = vp
+    L.or_factor.argtypes = [C.c_int64, vp, vp, vp, vp, C.c_int, vp, C.c_int]
+    L.or_free.argtypes = [vp]
+    L.or_status.restype = C.c_int
+    L.or_status.argtypes = [vp]
+    L.or_error.restype = C.c_double
+    L.or_error.argtypes = [vp]
+    L.or_threads.restype = C.c_int
+    L.or_threads.argtypes = []
+    L.or_hdiag.argtypes = [vp, vp]
+
+
+def time_factor_openmp(n, rowptr, col, val, coords=None, *, runs=1, k=2, eta=0.5,
+                       cluster_size=256, core_size=16, seed=0, labels=None, hdiag_out=None):
+    """Median wall time of `runs` factorizations with the OpenMP build:
+    (seconds, relative error, threads), or None without OpenMP.  hdiag_out
+    (float64[n], optional) receives the diagonal of H of the last run."""
+    import time
+    global _lib_omp
+    if _lib_omp is None:
+        path = build_openmp()
+        if path is None:
+            return None
+        _lib_omp = C.CDLL(path)
+        _declare_factor(_lib_omp)
+    L = _lib_omp
+    rowptr = np.ascontiguousarray(rowptr, dtype=np.int64)
+    col = np.ascontiguousarray(col, dtype=np.int32)
+    val = np.ascontiguousarray(val, dtype=np.float64)
+    dim, cp = 0, None
+    if coords is not None:
+        coords = np.ascontiguousarray(coords, dtype=np.float64)
+        dim, cp = coords.shape[1], _p(coords)
+    lab = None if labels is None else np.ascontiguousarray(labels, dtype=np.int32)
+    prm = _Params(k, eta, cluster_size, core_size, seed, 0, 10,
+                  None if lab is None else _p(lab), 0 if lab is None else int(lab.max()) + 1)
+    ts, err = [], None
+    for _ in range(runs):
+        t0 = time.perf_counter()
+        h = L.or_factor(n, _p(rowptr), _p(col), _p(val), cp, dim, C.byref(prm), 0)
+        ts.append(time.perf_counter() - t0)
+        if not h:
+            raise MemoryError("oracle allocation failed")
+        st = L.or_status(h)
+        err = L.or_error(h)
+        if hdiag_out is not None and st == 0:
+            L.or_hdiag(h, _p(hdiag_out))
+        L.or_free(h)
+        if st:
+            raise RuntimeError(f"oracle failed with status {st}")
+    ts.sort()
+    return ts[len(ts) // 2], err, int(L.or_threads())
 
 
 def lib():
@@ -102,6 +182,8 @@ def lib():
         L.or_set_rotation.argtypes = [vp, i32, i64, vp]
         L.or_set_h.restype = i32
         L.or_set_h.argtypes = [vp, vp, vp]
+        L.or_threads.restype = i32
+        L.or_threads.argtypes = []
         _lib = L
     return _lib
 

@@ -43,6 +43,19 @@
 #include <math.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+/* Host threads a factorization uses: 1 for the plain build; the OpenMP
+ * build (timing baseline only) spreads clusters and rows over this many. */
+int or_threads(void) {
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
 
 #define KMAX 8
 
@@ -475,6 +488,42 @@ static int transform_row(xform_ctx *cx, const orow *in, orow *out) {
     return OR_OK;
 }
 
+/* out[x] = in[x] Q^T for every active row x (rows are independent; with
+ * OpenMP they are spread over the host's cores, each thread with its own
+ * scratch, and the results do not depend on the thread count). */
+static int transform_rows(const ostage *st, const int32_t *cl, const int32_t *loc, int K,
+                          int64_t s, int64_t cmax, const orow *in, const int32_t *act,
+                          orow *out) {
+    int status = OR_OK;
+#ifdef _OPENMP
+#pragma omp parallel
+#endif
+    {
+        xform_ctx cx;
+        cx.st = st; cx.cl = cl; cx.loc = loc; cx.K = K;
+        cx.ocap = s;
+        cx.dense = (double *)malloc(sizeof(double) * (size_t)(cmax ? cmax : 1));
+        cx.touched = (int32_t *)malloc(sizeof(int32_t) * (size_t)(s ? s : 1));
+        cx.ocol = (int32_t *)malloc(sizeof(int32_t) * (size_t)(s ? s : 1));
+        cx.oval = (double *)malloc(sizeof(double) * (size_t)(s ? s : 1));
+        const int ok = cx.dense && cx.touched && cx.ocol && cx.oval;
+#ifdef _OPENMP
+#pragma omp for schedule(dynamic, 64)
+#endif
+        for (int64_t r = 0; r < s; ++r) {
+            int sr = ok ? transform_row(&cx, &in[act[r]], &out[act[r]]) : OR_ERR_OOM;
+            if (sr != OR_OK) {
+#ifdef _OPENMP
+#pragma omp critical
+#endif
+                if (status == OR_OK) status = sr;
+            }
+        }
+        free(cx.dense); free(cx.touched); free(cx.ocol); free(cx.oval);
+    }
+    return status;
+}
+
 /* Transpose rows (indexed by global id, only rows in act[0..s)); entries of
  * each output row come out sorted by the source row id. */
 static orow *transpose_rows(const orow *in, int64_t n, const int32_t *act, int64_t s) {
@@ -776,12 +825,43 @@ or_fact *or_factor(int64_t n, const int64_t *rowptr, const int32_t *col, const d
                 memcpy(vv + rp[i], A[i].val, sizeof(double) * (size_t)A[i].len);
                 rp[i + 1] = rp[i] + A[i].len;
             }
-            int64_t rpos = 0;
             int status = OR_OK;
-            for (int64_t u = 0; u < mm && status == OR_OK; ++u) {
-                int64_t cu = st->coff[u + 1] - st->coff[u];
-                or_gram(n, rp, cc, vv, cu, st->members + st->coff[u], G, M);
-                status = find_rotations(st, u, e[u], G, M, prm, p, K, &rpos);
+            /* Clusters are independent (Sec. 2.1): each writes its rotations
+             * from its own offset roff[u].  Built with OpenMP, the clusters
+             * are spread over the host's cores (the paper's m-fold
+             * parallelism), each thread with its own G and M; the results do
+             * not depend on the thread count. */
+#ifdef _OPENMP
+#pragma omp parallel
+#endif
+            {
+                double *Gt = G, *Mt = M;
+#ifdef _OPENMP
+                if (omp_get_thread_num() != 0) {
+                    Gt = (double *)malloc(sizeof(double) * (size_t)(cmax * cmax));
+                    Mt = (double *)malloc(sizeof(double) * (size_t)(cmax * cmax));
+                }
+#pragma omp for schedule(dynamic, 1)
+#endif
+                for (int64_t u = 0; u < mm; ++u) {
+                    int su = OR_OK;
+                    if (!Gt || !Mt) {
+                        su = OR_ERR_OOM;
+                    } else {
+                        int64_t cu = st->coff[u + 1] - st->coff[u];
+                        int64_t rpos = st->roff[u];
+                        or_gram(n, rp, cc, vv, cu, st->members + st->coff[u], Gt, Mt);
+                        su = find_rotations(st, u, e[u], Gt, Mt, prm, p, K, &rpos);
+                    }
+                    if (su != OR_OK) {
+#ifdef _OPENMP
+#pragma omp critical
+#endif
+                        if (status == OR_OK) status = su;
+                    }
+                }
+                if (Gt != G) free(Gt);
+                if (Mt != M) free(Mt);
             }
             free(G); free(M); free(rp); free(cc); free(vv);
             if (status != OR_OK) { free(e); f->status = status; goto done; }
@@ -794,30 +874,16 @@ or_fact *or_factor(int64_t n, const int64_t *rowptr, const int32_t *col, const d
             int64_t maxlen = 1;
             for (int64_t r = 0; r < s; ++r)
                 if (A[act[r]].len > maxlen) maxlen = A[act[r]].len;
-            xform_ctx cx;
-            cx.st = st; cx.cl = cl; cx.loc = loc; cx.K = K;
-            cx.ocap = s;
-            cx.dense = (double *)malloc(sizeof(double) * (size_t)(cmax ? cmax : 1));
-            cx.touched = (int32_t *)malloc(sizeof(int32_t) * (size_t)s);
-            cx.ocol = (int32_t *)malloc(sizeof(int32_t) * (size_t)s);
-            cx.oval = (double *)malloc(sizeof(double) * (size_t)s);
             orow *V = (orow *)calloc((size_t)n, sizeof(orow));
-            if (!cx.dense || !cx.touched || !cx.ocol || !cx.oval || !V) {
-                free(cx.dense); free(cx.touched); free(cx.ocol); free(cx.oval); free(V);
-                goto oom;
-            }
-            int status = OR_OK;
-            for (int64_t r = 0; r < s && status == OR_OK; ++r)
-                status = transform_row(&cx, &A[act[r]], &V[act[r]]);
+            if (!V) goto oom;
+            int status = transform_rows(st, cl, loc, K, s, cmax, A, act, V);
             orow *W = status == OR_OK ? transpose_rows(V, n, act, s) : NULL;
             rows_free(V, n);
             if (!W) status = status ? status : OR_ERR_OOM;
             orow *Ap = (orow *)calloc((size_t)n, sizeof(orow));
             if (!Ap) status = OR_ERR_OOM;
-            for (int64_t r = 0; r < s && status == OR_OK; ++r)
-                status = transform_row(&cx, &W[act[r]], &Ap[act[r]]);
+            if (status == OR_OK) status = transform_rows(st, cl, loc, K, s, cmax, W, act, Ap);
             rows_free(W, n);
-            free(cx.dense); free(cx.touched); free(cx.ocol); free(cx.oval);
             if (status != OR_OK) { rows_free(Ap, n); f->status = status; goto done; }
 
             /* ---- residual, H diagonal, compaction to S_p (Alg. 1; R4) ---- */

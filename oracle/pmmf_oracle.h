@@ -77,6 +77,7 @@ int64_t or_stage_nnz(const or_fact *f, int p);              /* nnz of A_p[S_p,S_
 int64_t or_stage_matrix(const or_fact *f, int p, int64_t *rowptr_n1, int32_t *col, double *val);
 
 double or_error(const or_fact *f);          /* ||A - U^T H U||_F / ||A||_F */
+int or_threads(void);                        /* host threads a factorization uses */
 double or_norm_a(const or_fact *f);
 int64_t or_core_size(const or_fact *f);
 void or_core(const or_fact *f, int32_t *idx, double *core);

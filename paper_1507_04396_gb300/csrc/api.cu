@@ -965,6 +965,7 @@ extern "C" {
 const char *pmmf_last_error(void) { return last_error_cstr(); }
 
 uint64_t pmmf_launch_count(void) { return g_launches.load(); }
+uint64_t pmmf_alloc_count(void) { return g_allocs.load(); }
 
 pmmf_status pmmf_factor(const pmmf_matrix *A, const pmmf_params *p, pmmf_handle **out,
                         void *stream) {
@@ -1229,15 +1230,19 @@ pmmf_status ensure_inverse(pmmf_handle *f, cudaStream_t st) {
     else
         PMMF_TRY(invert_core(f->core.p, f->ncore, f->hdiag.p, f->core_pos.p, f->n, f->core_inv.p,
                              status.p, st));
+    // The reciprocals are formed before the status readback, so the one
+    // synchronization below also finishes them: once the state says "formed",
+    // any stream or host thread may read them without further ordering.
+    PMMF_TRY(f->hrcp.alloc(f->n, st));
+    PMMF_TRY(h_reciprocals(f->hdiag.p, f->n, false, f->hrcp.p, st));
     unsigned hs = 0;
     PMMF_CUDA_TRY(cudaMemcpyAsync(&hs, status.p, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
     PMMF_CUDA_TRY(cudaStreamSynchronize(st));
     if (hs & ST_NOT_SPD) {
+        f->hrcp.reset();
         f->inv_state = 2;
         return fail(PMMF_ERR_NOT_SPD, "H is not positive definite");
     }
-    PMMF_TRY(f->hrcp.alloc(f->n, st));
-    PMMF_TRY(h_reciprocals(f->hdiag.p, f->n, false, f->hrcp.p, st));
     f->inv_state = 1;
     return PMMF_OK;
 }
@@ -1256,15 +1261,18 @@ pmmf_status ensure_isqrt(pmmf_handle *f, cudaStream_t st) {
         return cs;
     }
     PMMF_TRY(cs);
+    // Formed before the readback, as in ensure_inverse: the synchronization
+    // below orders them before every later use on any stream.
+    PMMF_TRY(f->hisr.alloc(f->n, st));
+    PMMF_TRY(h_reciprocals(f->hdiag.p, f->n, true, f->hisr.p, st));
     unsigned hs = 0;
     PMMF_CUDA_TRY(cudaMemcpyAsync(&hs, status.p, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
     PMMF_CUDA_TRY(cudaStreamSynchronize(st));
     if (hs & ST_NOT_SPD) {
+        f->hisr.reset();
         f->isqrt_state = 2;
         return fail(PMMF_ERR_NOT_SPD, "H is not positive definite");
     }
-    PMMF_TRY(f->hisr.alloc(f->n, st));
-    PMMF_TRY(h_reciprocals(f->hdiag.p, f->n, true, f->hisr.p, st));
     f->isqrt_state = 1;
     return PMMF_OK;
 }

@@ -95,8 +95,11 @@ __global__ void k_copy_block(const double *x, int64_t ldx, double *y, int64_t ld
 // Wavelet part of H (MODE 0), H^-1 (1) or H^-1/2 (2) (core coordinates
 // untouched here); gathers the core slice into zc.
 // rc (may be NULL): the per-coordinate reciprocals of MODE 1 or 2, so the
-// wavelet part is one multiply (within an ulp of the divide) instead of an
-// FP64 divide (and square root) per entry.
+// wavelet part is one multiply instead of an FP64 divide (and square root) per
+// entry.  The product rounds twice (1/h, then v * 1/h; three times with the
+// square root), so it can differ from the correctly rounded quotient by a few
+// ulps, not only one; the inverse ops are therefore compared with the oracle
+// to a tolerance.
 // NRC > 0: nrhs is NRC, known at compile time.
 template <int MODE, int NRC>
 __global__ void k_h_diag(double *x, int64_t ld, int64_t n, int64_t nrhs_rt, const double *hdiag,

@@ -15,6 +15,7 @@ namespace pmmf {
 
 void set_error(const std::string &msg);
 extern std::atomic<uint64_t> g_launches;
+extern std::atomic<uint64_t> g_allocs;   // device allocations requested (dev_alloc)
 
 struct Err {
     pmmf_status st = PMMF_OK;

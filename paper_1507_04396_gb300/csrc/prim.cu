@@ -13,6 +13,7 @@
 namespace pmmf {
 
 std::atomic<uint64_t> g_launches{0};
+std::atomic<uint64_t> g_allocs{0};
 
 namespace {
 thread_local std::string t_last_error;
@@ -68,6 +69,7 @@ pmmf_status dev_alloc(void **p, size_t bytes, cudaStream_t st) {
         }
         g_alloc_countdown.fetch_sub(1);
     }
+    g_allocs.fetch_add(1, std::memory_order_relaxed);
     cudaError_t e = cudaMallocAsync(p, bytes, st);
     if (e != cudaSuccess) {
         *p = nullptr;

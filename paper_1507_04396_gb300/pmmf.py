@@ -69,7 +69,7 @@ EXPORTS = ["pmmf_factor", "pmmf_apply", "pmmf_solve_precond", "pmmf_free", "pmmf
            "pmmf_profile_begin", "pmmf_profile_end", "pmmf_apply_noalloc",
            "pmmf_get_info", "pmmf_get_stage_info", "pmmf_get_stage_clusters",
            "pmmf_get_stage_rotations", "pmmf_get_h", "pmmf_get_stage_matrix",
-           "pmmf_launch_count", "pmmf_apply_backward", "pmmf_get_angles", "pmmf_set_angles",
+           "pmmf_launch_count", "pmmf_alloc_count", "pmmf_probe_fp64", "pmmf_apply_backward", "pmmf_get_angles", "pmmf_set_angles",
            "pmmf_set_h", "pmmf_factor_blockdiag", "pmmf_factor_batched", "pmmf_get_batch",
            "pmmf_get_precision_stats", "pmmf_set_tuning", "pmmf_clear_tuning",
            "pmmf_solve_precond_sym", "pmmf_block_angle_grad"]
@@ -113,6 +113,10 @@ def load(path: str = LIB_PATH):
     L.pmmf_get_stage_matrix.argtypes = [vp, i32, vp, vp, vp, vp]
     L.pmmf_launch_count.restype = C.c_uint64
     L.pmmf_launch_count.argtypes = []
+    L.pmmf_alloc_count.restype = C.c_uint64
+    L.pmmf_alloc_count.argtypes = []
+    L.pmmf_probe_fp64.restype = i32
+    L.pmmf_probe_fp64.argtypes = [vp, vp]
     L.pmmf_apply_noalloc.restype = i32
     L.pmmf_apply_noalloc.argtypes = [vp, i32, vp, vp, i64, i64, vp]
     L.pmmf_apply_backward.restype = i32
@@ -306,6 +310,17 @@ def pmmf_free(handle: int):
 
 def pmmf_launch_count() -> int:
     return int(load().pmmf_launch_count())
+
+
+def pmmf_alloc_count() -> int:
+    return int(load().pmmf_alloc_count())
+
+
+def pmmf_probe_fp64(stream=None) -> float:
+    """Measured FP64 FMA throughput of the current device, TFLOP/s."""
+    v = C.c_double()
+    _check(load().pmmf_probe_fp64(C.byref(v), _stream(stream)))
+    return float(v.value)
 
 
 # ---------------------------------------------------------------- convenience

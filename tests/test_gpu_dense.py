@@ -52,3 +52,15 @@ def test_dense_apply_matches_oracle():
     xd = torch.from_numpy(x).cuda()
     for op in (O.OP_U, O.OP_UT, O.OP_H, O.OP_A):
         assert np.array_equal(g.apply(op, xd).cpu().numpy(), o.apply(op, x)), op
+
+
+def test_dense_rbf_c3_shape():
+    """The shape of the dense RBF workload (20-component 3-D mixture, k-means
+    clusters of 512, 3-point rotations, core 512) at n = 4,096: eight clusters
+    of ~512 at the first stage, so the k-point search runs at its largest
+    cluster size.  Bit-identical to the oracle."""
+    a = I.rbf_mixture(4096, components=20, seed=2)
+    g, o = _both(a, a.coords, k=3, eta=0.5, cluster_size=512, core_size=512, seed=0)
+    sizes = np.diff(o.stages[0].offsets)
+    assert len(sizes) == 8 and sizes.max() > 400, sizes
+    assert_same_factorization(g, o)

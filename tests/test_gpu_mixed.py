@@ -1,16 +1,17 @@
 """Reduced-precision (TF32 / BF16 tensor-core) Gram shortlist on dense inputs.
 
 The shortlist only screens partners; the choice is made on FP64 scores, so
-the selections must equal those of the FP64 mode (which is bit-identical to
-the oracle), and the relative error must match it closely.  The shortlist
-must stay short (full-row fallbacks rare), which also shows that the
-tensor-core Gram is accurate to its bound.
+the selections (clusters, tuples, eliminated coordinates) must equal the
+oracle's, and the relative error must match the oracle's closely (stated per
+test below).  The shortlist must stay short (full-row fallbacks rare), which
+also shows that the tensor-core Gram is accurate to its bound.
 """
 
 import numpy as np
 import pytest
 
 from helpers import gpu, gpu_lib
+from oracle import oracle as O
 from paper_1507_04396_gb300 import inputs as I
 
 pytestmark = gpu
@@ -55,3 +56,43 @@ def test_shortlist_rejects_sparse_input():
     with pytest.raises(pm.PmmfError) as e:
         pm.factor(a, k=2, eta=0.5, cluster_size=64, core_size=20, precision=1)
     assert e.value.status == pm.ERR_UNSUPPORTED
+
+
+def _against_oracle(a, precision, **kw):
+    mp = _run(a, precision, **kw)
+    o = O.factor(a.n, a.rowptr, a.col, a.val, a.coords, **kw)
+    assert o.status == 0
+    assert mp.info().stages == len(o.stages)
+    for p, so in enumerate(o.stages):
+        off, mem = mp.clusters(p)
+        np.testing.assert_array_equal(off, so.offsets)
+        np.testing.assert_array_equal(mem, so.members)
+        r = mp.rotations(p)
+        np.testing.assert_array_equal(r[2], so.rot_idx)      # tuples
+        np.testing.assert_array_equal(r[4], so.rot_elim)     # eliminated coordinates
+        # the blocks come from FP64 rows rotated and re-dotted rather than an
+        # FP64 Gram rotated: equal to rounding
+        np.testing.assert_allclose(r[3], so.rot_O, rtol=0, atol=1e-9)
+    hd, ci, core = mp.h()
+    np.testing.assert_array_equal(ci, o.core_idx)
+    # the error against the oracle's: relative gap stated and bounded
+    gap = abs(mp.info().error - o.error) / o.error
+    assert gap <= 1e-8, gap
+    return mp, o
+
+
+@pytest.mark.parametrize("precision", [1, 2])
+@pytest.mark.parametrize("k", [2, 3])
+def test_shortlist_selects_like_the_oracle(precision, k):
+    """TF32 (1) and BF16 (2) shortlists against the FP64 oracle directly."""
+    a = I.rbf_mixture(1024, components=8, seed=5)
+    _against_oracle(a, precision, k=k, eta=0.5, cluster_size=128, core_size=64, seed=3)
+
+
+@pytest.mark.parametrize("precision", [1, 2])
+def test_shortlist_rbf_workload_shape(precision):
+    """The dense RBF workload's shape (20-component mixture, clusters of 512,
+    k = 3, core 512) at n = 2,048: four clusters of ~512 per early stage."""
+    a = I.rbf_mixture(2048, components=20, seed=2)
+    mp, o = _against_oracle(a, precision, k=3, eta=0.5, cluster_size=512, core_size=512, seed=0)
+    assert np.diff(o.stages[0].offsets).max() > 400

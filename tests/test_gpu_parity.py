@@ -320,3 +320,53 @@ def test_concurrent_host_threads_match_oracle():
         o = O.factor(a.n, a.rowptr, a.col, a.val, a.coords, record=True, **kw)
         assert o.status == 0
         assert_same_factorization(out[q], o)
+
+
+@pytest.mark.parametrize("k", [2, 3])
+def test_apply_eight_right_hand_sides(k):
+    """Eight right-hand sides take the apply kernels' fixed-width
+    instantiations (the width the solvers use): U, U^T, H, A~ bit for bit;
+    the inverse ops to the tolerance of the other apply tests.  Also a strided
+    block (ld > nrhs), which takes the element-wise copy."""
+    import torch
+    a = I.knn_laplacian(2400, seed=12)
+    g, o = factor_both(a, k=k, eta=0.5, cluster_size=120, core_size=48, seed=5)
+    x = np.random.default_rng(8).standard_normal((a.n, 8))
+    xd = torch.from_numpy(x).cuda()
+    for op in (O.OP_U, O.OP_UT, O.OP_H, O.OP_A):
+        assert np.array_equal(g.apply(op, xd).cpu().numpy(), o.apply(op, x)), op
+    for op, tol in ((O.OP_A_INV, 1e-10), (O.OP_H_INV, 1e-10), (O.OP_A_INV_SQRT, 1e-9),
+                    (O.OP_H_INV_SQRT, 1e-9)):
+        want = o.apply(op, x)
+        got = g.apply(op, xd).cpu().numpy()
+        assert np.abs(got - want).max() <= tol * np.abs(want).max(), op
+    pm = gpu_lib()
+    ld = 11
+    wide = torch.zeros(a.n, ld, dtype=torch.float64, device="cuda")
+    wide[:, :8] = xd
+    out = torch.full_like(wide, 7.0)
+    for op in (O.OP_U, O.OP_A):
+        pm.pmmf_apply(g.handle, op, wide, out, 8, ld)
+        torch.cuda.synchronize()
+        assert np.array_equal(out[:, :8].cpu().numpy(), o.apply(op, x)), op
+        assert bool((out[:, 8:] == 7.0).all())
+
+
+def test_wide_search_cta_clusters_above_512():
+    """Clusters of ~600 coordinates: the k = 2 search runs its 512-thread CTA
+    (12 column warps) on a single factorization, not only in a batch."""
+    a = I.knn_laplacian(6000, seed=13)
+    g, o = factor_both(a, k=2, eta=0.5, cluster_size=600, core_size=100, seed=3)
+    sizes = np.diff(o.stages[0].offsets)
+    assert sizes.max() > 512 and sizes.max() <= 1536, sizes
+    assert_same_factorization(g, o)
+
+
+def test_generic_search_one_cluster_above_1536():
+    """One cluster of 2,048 coordinates (no points: one cluster per stage):
+    the first stage runs the generic k = 2 search kernel (beyond 1,536
+    coordinates), later stages the 512- and 256-thread ones."""
+    a = I.knn_laplacian(2048, seed=14)
+    g, o = factor_both(a, coords=None, k=2, eta=0.5, cluster_size=2048, core_size=64, seed=4)
+    assert len(o.stages[0].offsets) == 2 and o.stages[0].active == 2048
+    assert_same_factorization(g, o)

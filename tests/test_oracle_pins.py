@@ -433,3 +433,27 @@ def test_stage1_labels_reproduce_kmeans_and_bricks():
     bad = lab.copy()
     bad[7] = -1
     assert O.factor_csr(a, labels=bad, **kw).status == O.ERR_INVALID_ARG
+
+
+# ---------------------------------------------------------------- the multi-core timing build
+
+def test_openmp_build_gives_the_same_factorization():
+    """The OpenMP build (clusters and rows spread over the host's cores; used
+    only for the multi-core CPU timing) must give the single-thread build's
+    factorization: the same error and H diagonal, bit for bit, on clustered
+    k = 2 and k = 3 cases."""
+    import os
+    if O.build_openmp() is None:
+        pytest.skip("gcc without OpenMP")
+    os.environ.setdefault("OMP_NUM_THREADS", "4")
+    for a, kw in ((I.knn_laplacian(3000, seed=4), dict(k=2, cluster_size=128, core_size=40)),
+                  (I.rbf_mixture(600, components=6, seed=2), dict(k=3, cluster_size=64, core_size=30))):
+        kw = dict(kw, eta=0.5, seed=5)
+        f = O.factor_csr(a, **kw)
+        assert f.status == 0
+        hd = np.empty(a.n)
+        t, err, threads = O.time_factor_openmp(a.n, a.rowptr, a.col, a.val, a.coords,
+                                               hdiag_out=hd, **kw)
+        assert threads >= 1
+        assert err == f.error
+        assert np.array_equal(hd.view(np.uint64), f.hdiag.view(np.uint64))

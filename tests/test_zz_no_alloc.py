@@ -57,12 +57,14 @@ def test_noalloc_apply_matches_apply_twice_without_allocating():
 
     pool = _Pool(torch.cuda.current_device())
     used_before = pool.get(_USED_MEM_CURRENT)
+    allocs_before = pm.pmmf_alloc_count()
     pool.reset_high()
     for call in range(2):
         for op in ops:
             pm.pmmf_apply_noalloc(f.handle, op, x, outs[op][call], nrhs, nrhs)
     torch.cuda.synchronize()
     assert pool.get(_USED_MEM_HIGH) <= used_before, "the allocation-free apply allocated"
+    assert pm.pmmf_alloc_count() == allocs_before, "the allocation-free apply requested memory"
 
     for op in ops:
         want = ref[op].cpu().numpy()
@@ -98,4 +100,34 @@ def test_noalloc_rejects_oversize_and_unformed_inverse():
     with pytest.raises(pm.PmmfError) as e:
         pm.pmmf_apply_noalloc(f.handle, pm.OP_A_INV_SQRT, x[:, :2].contiguous(), y[:, :2].contiguous(), 2, 2)
     assert e.value.status == pm.ERR_INVALID_ARG
+    f.close()
+
+
+def test_noalloc_on_a_second_stream_right_after_forming():
+    """The inverse and inverse square root are formed by pmmf_apply on one
+    stream; pmmf_apply_noalloc then runs on a new stream with no synchronize
+    in between.  Its results must equal the allocating apply's bit for bit
+    (the formed reciprocals and core factors are complete once pmmf_apply
+    returns from forming them)."""
+    import torch
+    pm = gpu_lib()
+    a = I.knn_laplacian(2500, seed=11)
+    f = pm.factor(a, k=2, eta=0.5, cluster_size=128, core_size=50, seed=2)
+    nrhs = 8
+    x = torch.from_numpy(np.random.default_rng(7).standard_normal((a.n, nrhs))).cuda()
+    s1, s2 = torch.cuda.Stream(), torch.cuda.Stream()
+    torch.cuda.synchronize()
+    with torch.cuda.stream(s1):
+        r_inv = f.apply(pm.OP_A_INV, x, stream=s1)        # forms the core inverse on s1
+        r_isq = f.apply(pm.OP_A_INV_SQRT, x, stream=s1)   # forms core^{-1/2} on s1
+    y_inv = torch.empty_like(x)
+    y_isq = torch.empty_like(x)
+    allocs_before = pm.pmmf_alloc_count()
+    with torch.cuda.stream(s2):
+        pm.pmmf_apply_noalloc(f.handle, pm.OP_A_INV, x, y_inv, nrhs, nrhs, s2)
+        pm.pmmf_apply_noalloc(f.handle, pm.OP_A_INV_SQRT, x, y_isq, nrhs, nrhs, s2)
+    torch.cuda.synchronize()
+    assert pm.pmmf_alloc_count() == allocs_before
+    assert torch.equal(y_inv, r_inv)
+    assert torch.equal(y_isq, r_isq)
     f.close()
