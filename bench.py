@@ -233,11 +233,14 @@ def poisson_extras(dev, stream, flush, hbm):
         info = f.info()
         if _ < 2:
             f.close()
-    # blocked update on stages 1-2 (the stages with >= 100 MB of traffic)
+    # the blocked update's launches that carry >= 100 MB of algorithmic bytes
+    # (the first two stages)
     pmmf.pmmf_profile_begin(["rows"])
-    fac(max_stages=2).close()
-    rows = pmmf.pmmf_profile_end()["rows"]
-    rows_gbs = rows["bytes"] / (rows["ms"] / 1e3) / 1e9
+    fac().close()
+    recs = [r for r in pmmf.pmmf_profile_records() if r[0] == "rows" and r[2] >= 100e6]
+    pmmf.pmmf_profile_end()
+    rows = {"ms": sum(r[1] for r in recs), "bytes": sum(r[2] for r in recs), "launches": len(recs)}
+    rows_gbs = rows["bytes"] / (rows["ms"] / 1e3) / 1e9 if rows["ms"] > 0 else 0.0
     x = torch.randn(a.n, POISSON["nrhs"], dtype=torch.float64, device=dev)
     y = torch.empty_like(x)
     for _ in range(3):
@@ -254,7 +257,7 @@ def poisson_extras(dev, stream, flush, hbm):
                     "8x8x4 grid bricks, then k-means clusters of 256; k=2, eta=0.5, core 1024",
         "n": a.n, "nnz": a.nnz, "stages": info.stages, "frobenius_error": info.error,
         "factor_ms": sorted(ts)[1], "nnz_per_s": a.nnz / (sorted(ts)[1] / 1e3),
-        "update_stages_1_2": {"gbs": rows_gbs, "frac_of_hbm": rows_gbs / hbm,
+        "update_launches_over_100MB": {"gbs": rows_gbs, "frac_of_hbm": rows_gbs / hbm,
                               "algorithmic_bytes": rows["bytes"], "ms": rows["ms"],
                               "launches": rows["launches"]},
         "apply_a_inv_8rhs": {"gbs": apply_gbs, "frac_of_hbm": apply_gbs / hbm,

@@ -430,6 +430,12 @@ pmmf_status pmmf_probe_fp64(double *tflops, void *stream);
  * family), then disables profiling. */
 pmmf_status pmmf_profile_begin(unsigned family_mask);
 pmmf_status pmmf_profile_end(double *ms, int64_t *launches, double *bytes, double *flops);
+/* The launches recorded since pmmf_profile_begin, one by one in launch order
+ * (HOST arrays of cap entries; cap may be 0 to query the count): family,
+ * duration (ms), algorithmic bytes and flops.  Synchronizes the device; the
+ * records stay until pmmf_profile_end or the next pmmf_profile_begin. */
+pmmf_status pmmf_profile_records(int64_t cap, int32_t *family, double *ms, double *bytes,
+                                 double *flops, int64_t *count);
 
 #ifdef __cplusplus
 }

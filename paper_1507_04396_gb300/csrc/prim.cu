@@ -669,6 +669,27 @@ pmmf_status pmmf_profile_begin(unsigned family_mask) {
     return PMMF_OK;
 }
 
+pmmf_status pmmf_profile_records(int64_t cap, int32_t *family, double *ms, double *bytes,
+                                 double *flops, int64_t *count) {
+    if (!count || (cap > 0 && (!family || !ms || !bytes || !flops))) {
+        pmmf::set_error("NULL output");
+        return PMMF_ERR_INVALID_ARG;
+    }
+    cudaDeviceSynchronize();
+    std::lock_guard<std::mutex> lk(pmmf::g_prof_mu);
+    *count = (int64_t)pmmf::g_prof.size();
+    for (int64_t i = 0; i < cap && i < *count; ++i) {
+        const auto &r = pmmf::g_prof[(size_t)i];
+        float t = 0.f;
+        cudaEventElapsedTime(&t, r.a, r.b);
+        family[i] = r.family;
+        ms[i] = t;
+        bytes[i] = r.bytes;
+        flops[i] = r.flops;
+    }
+    return PMMF_OK;
+}
+
 pmmf_status pmmf_profile_end(double *ms, int64_t *launches, double *bytes, double *flops) {
     cudaDeviceSynchronize();
     std::lock_guard<std::mutex> lk(pmmf::g_prof_mu);

@@ -981,7 +981,9 @@ pmmf_status select_stage(const StageClusters &cls, int64_t cmax, GramBlocks &gb,
     const size_t shb = sizeof(double) * 3 * (size_t)cmax + sizeof(uint32_t) * (size_t)((cmax + 31) / 32) +
                        sizeof(int32_t) * (size_t)(2 * cmax + 4);
     const size_t shf = shb + sizeof(uint64_t) * (size_t)(cmax + 1) + sizeof(Work) * (size_t)cmax + 16;
-    if (shf > 220 * 1024) {
+    // the fast kernels need shf bytes of shared memory, the generic one shb
+    const bool fits_fast = shf <= 220 * 1024;
+    if (shb > 220 * 1024) {
         set_error("cluster too large for the selection kernel");
         return PMMF_ERR_UNSUPPORTED;
     }
@@ -1018,12 +1020,12 @@ pmmf_status select_stage(const StageClusters &cls, int64_t cmax, GramBlocks &gb,
                                            rot.nlev.p, elimflag, order, useed);
         return PMMF_OK;
     };
-    if (sw == 8 && kpt <= 1) PMMF_TRY(launch(k_select_fast<1, 256>, 256));
-    else if (sw == 8 && kpt <= 2) PMMF_TRY(launch(k_select_fast<2, 256>, 256));
-    else if (sw == 8 && kpt <= 4) PMMF_TRY(launch(k_select_fast<4, 256>, 256));
-    else if (kpt512 <= 1) PMMF_TRY(launch(k_select_fast<1, 512>, 512));
-    else if (kpt512 <= 2) PMMF_TRY(launch(k_select_fast<2, 512>, 512));
-    else if (kpt512 <= 4) PMMF_TRY(launch(k_select_fast<4, 512>, 512));
+    if (fits_fast && sw == 8 && kpt <= 1) PMMF_TRY(launch(k_select_fast<1, 256>, 256));
+    else if (fits_fast && sw == 8 && kpt <= 2) PMMF_TRY(launch(k_select_fast<2, 256>, 256));
+    else if (fits_fast && sw == 8 && kpt <= 4) PMMF_TRY(launch(k_select_fast<4, 256>, 256));
+    else if (fits_fast && kpt512 <= 1) PMMF_TRY(launch(k_select_fast<1, 512>, 512));
+    else if (fits_fast && kpt512 <= 2) PMMF_TRY(launch(k_select_fast<2, 512>, 512));
+    else if (fits_fast && kpt512 <= 4) PMMF_TRY(launch(k_select_fast<4, 512>, 512));
     else {
         if (shb > 48 * 1024)
             PMMF_CUDA_TRY(cudaFuncSetAttribute(k_select, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shb));

@@ -66,7 +66,7 @@ class StageInfo(C.Structure):
 
 
 EXPORTS = ["pmmf_factor", "pmmf_apply", "pmmf_solve_precond", "pmmf_free", "pmmf_last_error",
-           "pmmf_profile_begin", "pmmf_profile_end", "pmmf_apply_noalloc",
+           "pmmf_profile_begin", "pmmf_profile_end", "pmmf_profile_records", "pmmf_apply_noalloc",
            "pmmf_get_info", "pmmf_get_stage_info", "pmmf_get_stage_clusters",
            "pmmf_get_stage_rotations", "pmmf_get_h", "pmmf_get_stage_matrix",
            "pmmf_launch_count", "pmmf_alloc_count", "pmmf_probe_fp64", "pmmf_apply_backward", "pmmf_get_angles", "pmmf_set_angles",
@@ -146,6 +146,8 @@ def load(path: str = LIB_PATH):
     L.pmmf_profile_begin.argtypes = [C.c_uint]
     L.pmmf_profile_end.restype = i32
     L.pmmf_profile_end.argtypes = [vp, vp, vp, vp]
+    L.pmmf_profile_records.restype = i32
+    L.pmmf_profile_records.argtypes = [i64, vp, vp, vp, vp, vp]
     _lib = L
     apply_tuning(os.environ.get("PMMF_TUNING", TUNING_PATH))
     return L
@@ -180,6 +182,20 @@ def pmmf_profile_begin(families) -> None:
     for f in families:
         mask |= 1 << FAMILIES.index(f)
     _check(load().pmmf_profile_begin(mask))
+
+
+def pmmf_profile_records() -> list:
+    """Launches recorded since pmmf_profile_begin, in launch order:
+    [(family, ms, bytes, flops)]."""
+    L = load()
+    cnt = C.c_int64()
+    _check(L.pmmf_profile_records(0, None, None, None, None, C.byref(cnt)))
+    n = cnt.value
+    fam = np.zeros(max(n, 1), dtype=np.int32)
+    ms, by, fl = (np.zeros(max(n, 1)) for _ in range(3))
+    _check(L.pmmf_profile_records(n, fam.ctypes.data, ms.ctypes.data, by.ctypes.data,
+                                  fl.ctypes.data, C.byref(cnt)))
+    return [(FAMILIES[fam[i]], float(ms[i]), float(by[i]), float(fl[i])) for i in range(n)]
 
 
 def pmmf_profile_end() -> dict:
