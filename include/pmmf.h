@@ -391,14 +391,18 @@ pmmf_status pmmf_get_stage_matrix(const pmmf_handle *f, int p, int64_t *rowptr_n
  * (the blocked update's counting passes take each row segment's fill pattern
  * from per-cluster reach sets when the stage has at least this many clusters,
  * default 64, else they run the rotation levels on the pattern; both give the
- * same counts; 1..2^31-1, use max_size 1).  A value
+ * same counts; 1..2^31-1, use max_size 1), PMMF_TUNE_ROWS_KERNEL (the blocked
+ * update's kernel: 2 = one thread per row, applying to each row segment only
+ * the rotations that reach its pattern (the default for clusters of up to
+ * 1,024 coordinates), 1 = one warp per row running every rotation level of
+ * the segment's cluster; both give the same bits).  A value
  * applies to launches whose largest cluster has at most max_size coordinates
  * and no smaller bucket matches; shared-memory limits still halve the row and
  * Gram warps when needed.  Process wide; INVALID_ARG for an unknown param or
  * a value outside 1..32 (outside {8, 16} for the search; any positive value for
  * the reach threshold). */
 enum { PMMF_TUNE_ROWS_WARPS = 0, PMMF_TUNE_GRAM_WARPS = 1, PMMF_TUNE_SELECT_WARPS = 2,
-       PMMF_TUNE_PASS1_ESTIMATE = 3, PMMF_TUNE_REACH_CLUSTERS = 4 };
+       PMMF_TUNE_PASS1_ESTIMATE = 3, PMMF_TUNE_REACH_CLUSTERS = 4, PMMF_TUNE_ROWS_KERNEL = 5 };
 pmmf_status pmmf_set_tuning(int param, int64_t max_size, int value);
 void pmmf_clear_tuning(void);
 

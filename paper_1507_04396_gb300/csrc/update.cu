@@ -23,6 +23,7 @@
 // the pattern.  Pass 1 writes W into rows of that capacity (each row's end is
 // its write cursor); pass 2 writes A_p into rows of that capacity and a
 // compaction copies them to their exact positions.
+#include <algorithm>
 #include <climits>
 
 #include "common.cuh"
@@ -48,6 +49,7 @@ struct RowArgs {
     const int64_t *roff;
     const int32_t *lvl_off, *nlev;
     const Rot2 *lvlrot;
+    const RotRec *rec;         // k = 2: the rotations in step order
     int K;                     // k >= 3: tuples, blocks and level slots below
     const int32_t *kidx, *kkv, *lvlidx;
     const double *kO;
@@ -472,6 +474,315 @@ __global__ void __launch_bounds__(256, 4) k_rows(RowArgs a) {
     }
 }
 
+// ---------------------------------------------------------------- thread-per-row update
+//
+// The same four passes with one thread per row instead of one warp.  A row
+// segment (the row's entries in one cluster) needs only the few rotations of
+// its cluster that touch its growing pattern (4 to 10 of ~c/2 on the sparse
+// workloads), so the thread applies exactly those, in step order: every
+// pattern coordinate carries its position in its incidence list (the steps of
+// the rotations it belongs to, ascending), the next rotation is the smallest
+// step among them, and a coordinate a rotation reaches joins the pattern with
+// value 0.  Applying the rotations of one segment in step order and skipping
+// only rotations whose inputs are all zero is what the warp kernel (and the
+// oracle's dense vector) computes, bit for bit; the FP64 instructions of a
+// warp now carry up to 32 rows' rotations instead of a few lanes of one row.
+// The counting passes take each segment's pattern from the reach sets.
+//
+// A thread's pattern lives in LANE_PS slots in shared memory (slot-major, so a
+// warp's threads touch distinct banks) and, beyond them, in its own region of
+// a global scratch buffer (cmax - LANE_PS slots), so no segment overflows:
+// a pattern never leaves its cluster.
+constexpr int LANE_NT = 128;                 // threads per CTA
+constexpr int LANE_PS = 32;                  // pattern slots per thread in shared memory
+constexpr int LANE_CTAS_PER_SM = 3;          // 64 KB of slots per CTA
+constexpr int LANE_MAX_C = 1024;             // cluster sizes the thread path takes
+constexpr uint32_t INC_END = 0xffffu;        // end of an incidence list (a step never reaches it)
+constexpr size_t LANE_SMEM = (sizeof(uint2) + sizeof(double)) * LANE_PS * LANE_NT;   // 64 KB
+
+struct LaneArgs {
+    const int32_t *inc_off;    // s + 1, by cluster member position coff[u] + l
+    const uint16_t *inc;       // each member's steps, ascending, then INC_END
+    uint2 *ometa;              // overflow slots, ovf per thread
+    double *oval;
+    int ovf;
+};
+
+// Incidence lists, pass 1: every member's list length (its rotations plus the
+// end marker).  One CTA per cluster.
+__global__ void k_inc_count(const int64_t *coff, const int64_t *roff, const RotRec *rec, int K,
+                            const int32_t *kidx, const int32_t *kkv, int64_t *cnt) {
+    const int64_t u = blockIdx.x;
+    const int64_t cb = coff[u];
+    const int c = (int)(coff[u + 1] - cb);
+    const int64_t r0 = roff[u];
+    const int e = (int)(roff[u + 1] - r0);
+    for (int l = threadIdx.x; l < c; l += blockDim.x) atomicAdd((unsigned long long *)&cnt[cb + l], 1ull);
+    for (int t = threadIdx.x; t < e; t += blockDim.x) {
+        if (K <= 2) {
+            const RotRec q = rec[r0 + t];
+            atomicAdd((unsigned long long *)&cnt[cb + q.li], 1ull);
+            atomicAdd((unsigned long long *)&cnt[cb + q.lj], 1ull);
+        } else {
+            const int kk = kkv[r0 + t];
+            for (int z = 0; z < kk; ++z)
+                atomicAdd((unsigned long long *)&cnt[cb + kidx[(r0 + t) * K + z]], 1ull);
+        }
+    }
+}
+
+// Pass 2: the steps, in any order (cursor per member), as 16-bit steps.
+__global__ void k_inc_fill(const int64_t *coff, const int64_t *roff, const RotRec *rec, int K,
+                           const int32_t *kidx, const int32_t *kkv, int64_t *cur, uint16_t *inc) {
+    const int64_t u = blockIdx.x;
+    const int64_t cb = coff[u];
+    const int64_t r0 = roff[u];
+    const int e = (int)(roff[u + 1] - r0);
+    for (int t = threadIdx.x; t < e; t += blockDim.x) {
+        if (K <= 2) {
+            const RotRec q = rec[r0 + t];
+            inc[atomicAdd((unsigned long long *)&cur[cb + q.li], 1ull)] = (uint16_t)t;
+            inc[atomicAdd((unsigned long long *)&cur[cb + q.lj], 1ull)] = (uint16_t)t;
+        } else {
+            const int kk = kkv[r0 + t];
+            for (int z = 0; z < kk; ++z)
+                inc[atomicAdd((unsigned long long *)&cur[cb + kidx[(r0 + t) * K + z]], 1ull)] =
+                    (uint16_t)t;
+        }
+    }
+}
+
+// Pass 3: each list sorted ascending (they are short) and ended by INC_END;
+// the offsets narrowed to int32.
+__global__ void k_inc_finish(const int64_t *off64, int64_t s, uint16_t *inc, int32_t *off32) {
+    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j <= s;
+         j += (int64_t)gridDim.x * blockDim.x) {
+        off32[j] = (int32_t)off64[j];
+        if (j == s) continue;
+        const int64_t b = off64[j], n = off64[j + 1] - b - 1;   // the last slot is the end marker
+        for (int64_t x = 1; x < n; ++x) {
+            const uint16_t v = inc[b + x];
+            int64_t y = x - 1;
+            while (y >= 0 && inc[b + y] > v) {
+                inc[b + y + 1] = inc[b + y];
+                --y;
+            }
+            inc[b + y + 1] = v;
+        }
+        inc[b + n] = (uint16_t)INC_END;
+    }
+}
+
+// A pattern slot: .x = next step << 16 | local index, .y = position in the
+// member's incidence list of that next step.
+__device__ __forceinline__ uint32_t slot_loc(uint2 m) { return m.x & 0xffffu; }
+__device__ __forceinline__ uint32_t slot_next(uint2 m) { return m.x >> 16; }
+
+template <int MODE, bool KP>
+__global__ void __launch_bounds__(LANE_NT) k_rows_lane(RowArgs a, LaneArgs b) {
+    constexpr bool COUNT = MODE == P1_COUNT || MODE == P2_COUNT;
+    // LANE_SMEM bytes of dynamic shared memory: the slots' metadata, then values
+    extern __shared__ __align__(16) unsigned char lane_sh[];
+    uint2 *smeta = (uint2 *)lane_sh;
+    double *sval = (double *)(lane_sh + sizeof(uint2) * LANE_PS * LANE_NT);
+    const int tid = threadIdx.x;
+    const int64_t gt = blockIdx.x * (int64_t)LANE_NT + tid;
+    const int64_t gs = (int64_t)gridDim.x * LANE_NT;
+    if (MODE == P1_WRITE && *a.wtotal > a.wcap) {
+        if (gt == 0) *a.wover = 1ull;
+        return;
+    }
+    uint2 *gmeta = b.ometa + gt * (int64_t)b.ovf;
+    double *gval = b.oval + gt * (int64_t)b.ovf;
+    auto meta = [&](int k) -> uint2 & { return k < LANE_PS ? smeta[k * LANE_NT + tid] : gmeta[k - LANE_PS]; };
+    auto val = [&](int k) -> double & { return k < LANE_PS ? sval[k * LANE_NT + tid] : gval[k - LANE_PS]; };
+    double part = 0.0;
+    for (int64_t r = gt; r < a.rows; r += gs) {
+        const int64_t e0 = a.rp[r], e1 = a.rend ? a.rend[r] : a.rp[r + 1];
+        const int32_t y = a.act[r];
+        const bool yelim = (MODE >= P2_COUNT) && a.elimflag[y] == a.stage;
+        int64_t nout = 0;
+        int64_t ob = 0, ocap = 0;     // the output row's capacity slots
+        if (MODE == P2_WRITE && !yelim) {
+            ob = a.orp[a.newrow[r]];
+            ocap = a.orp[a.newrow[r] + 1] - ob;
+        }
+        double prow = 0.0;
+        int prev = -1;
+        for (;;) {
+            // the next cluster segment of the row (ascending cluster ordinal)
+            int mu = INT_MAX;
+            for (int64_t q = e0; q < e1; ++q) {
+                const int uq = a.cl[a.ci[q]];
+                if (uq > prev && uq < mu) mu = uq;
+            }
+            if (mu == INT_MAX) break;
+            prev = mu;
+            const int64_t cb = a.coff[mu];
+            // the segment's entries: local index, value, first incidence
+            int np = 0;
+            for (int64_t q = e0; q < e1; ++q) {
+                const int32_t g = a.ci[q];
+                if (a.cl[g] != mu) continue;
+                const uint32_t l = (uint32_t)a.loc[g];
+                if (COUNT) {
+                    meta(np) = make_uint2(l, 0u);
+                } else {
+                    const int32_t p = b.inc_off[cb + l];
+                    meta(np) = make_uint2(((uint32_t)b.inc[p] << 16) | l, (uint32_t)p);
+                    val(np) = a.v[q];
+                }
+                ++np;
+            }
+            if (COUNT) {
+                // the pattern after the cluster's rotations: union of the
+                // entries' reach sets, one word at a time
+                const int c = (int)(a.coff[mu + 1] - cb);
+                const int nw = (c + 31) / 32;
+                for (int w = 0; w < nw; ++w) {
+                    uint32_t f = 0u;
+                    for (int k = 0; k < np; ++k)
+                        f |= __ldg(a.reach + (cb + slot_loc(meta(k))) * a.reach_words + w);
+                    for (; f; f &= f - 1u) {
+                        const int z = w * 32 + __ffs(f) - 1;
+                        if (MODE == P1_COUNT) {
+                            atomicAdd((unsigned long long *)&a.wcnt[a.mpos[cb + z]], 1ull);
+                        } else if (!yelim && a.mge[cb + z] >= 0) {
+                            ++nout;
+                        }
+                    }
+                }
+                continue;
+            }
+            const int64_t r0 = a.roff[mu];
+            auto find = [&](uint32_t l) -> int {
+                for (int k = 0; k < np; ++k)
+                    if (slot_loc(meta(k)) == l) return k;
+                return -1;
+            };
+            // a coordinate reached by the rotation at step t joins with value 0
+            auto join = [&](uint32_t l, uint32_t t) -> int {
+                int32_t p = b.inc_off[cb + l];
+                while (b.inc[p] != t && b.inc[p] != (uint16_t)INC_END) ++p;
+                const int k = np++;
+                meta(k) = make_uint2((t << 16) | l, (uint32_t)p);
+                val(k) = 0.0;
+                return k;
+            };
+            // past step t (a slot at its end marker stays there, so the read
+            // never leaves the incidence array)
+            auto advance = [&](int k) {
+                const uint2 m = meta(k);
+                const uint32_t p = b.inc[m.y] == (uint16_t)INC_END ? m.y : m.y + 1u;
+                meta(k) = make_uint2(((uint32_t)b.inc[p] << 16) | slot_loc(m), p);
+            };
+            for (;;) {
+                uint32_t t = INC_END;
+                for (int k = 0; k < np; ++k) t = min(t, slot_next(meta(k)));
+                if (t == INC_END) break;
+                if (!KP) {
+                    const RotRec q = a.rec[r0 + t];
+                    int ka = find((uint32_t)q.li), kb = find((uint32_t)q.lj);
+                    if (ka < 0) ka = join((uint32_t)q.li, t);
+                    if (kb < 0) kb = join((uint32_t)q.lj, t);
+                    const double vi = val(ka), vj = val(kb);
+                    if (nonzero_bits(vi) || nonzero_bits(vj)) {
+                        double ni, nj;
+                        rot_pair(q.c, q.s, vi, vj, ni, nj);
+                        val(ka) = ni;
+                        val(kb) = nj;
+                    }
+                    advance(ka);
+                    advance(kb);
+                } else {
+                    const int64_t tg = r0 + t;
+                    const int kk = a.kkv[tg];
+                    const int32_t *T = a.kidx + tg * a.K;
+                    int ks[8];
+                    double in[8];
+                    bool nz = false;
+                    for (int z = 0; z < kk; ++z) {
+                        int k = find((uint32_t)T[z]);
+                        if (k < 0) k = join((uint32_t)T[z], t);
+                        ks[z] = k;
+                        in[z] = val(k);
+                        nz |= nonzero_bits(in[z]);
+                    }
+                    if (nz) {
+                        const double *O = a.kO + tg * a.K * a.K;
+                        for (int z = 0; z < kk; ++z) val(ks[z]) = rot_row(O, kk, z, in);
+                    }
+                    for (int z = 0; z < kk; ++z) advance(ks[z]);
+                }
+            }
+            // emit the segment's nonzero entries
+            for (int k = 0; k < np; ++k) {
+                const double x = val(k);
+                if (!nonzero_bits(x)) continue;
+                const uint32_t l = slot_loc(meta(k));
+                if (MODE == P1_WRITE) {
+                    const int64_t slot =
+                        (int64_t)atomicAdd((unsigned long long *)&a.wcur[a.mpos[cb + l]], 1ull);
+                    a.wcol[slot] = y;
+                    a.wval[slot] = x;
+                } else {
+                    const int32_t mg = a.mge[cb + l];
+                    const int32_t g = mg & 0x7fffffff;
+                    bool term = false;
+                    if (yelim) {
+                        if (g == y) a.hdiag[y] = x;
+                        else term = true;
+                    } else if (mg < 0) {
+                        term = true;
+                    } else {
+                        if (nout < ocap) {
+                            a.ocol[ob + nout] = g;
+                            a.oval[ob + nout] = x;
+                        }
+                        ++nout;
+                    }
+                    if (term) {
+                        if (a.contrib_cl) prow = __fma_rn(x, x, prow);
+                        else part = __fma_rn(x, x, part);
+                    }
+                }
+            }
+        }
+        if (MODE == P2_COUNT && !yelim) {
+            a.ocnt[a.newrow[r]] = nout;
+            atomicMax(a.maxlen, (unsigned long long)nout);
+        }
+        if (MODE == P2_WRITE) {
+            if (a.contrib_cl && prow != 0.0) atomicAdd(a.contrib_cl + a.cl[y], prow);
+            if (!yelim) {
+                a.acnt[a.newrow[r]] = nout;
+                if (nout > ocap) {
+                    atomicOr(a.status, ST_ROW_TOO_LONG);
+                } else {
+                    // the row's kept entries by ascending global id (short rows:
+                    // insertion sort in place)
+                    for (int64_t x = 1; x < nout; ++x) {
+                        const int32_t g = a.ocol[ob + x];
+                        const double v = a.oval[ob + x];
+                        int64_t z = x - 1;
+                        while (z >= 0 && a.ocol[ob + z] > g) {
+                            a.ocol[ob + z + 1] = a.ocol[ob + z];
+                            a.oval[ob + z + 1] = a.oval[ob + z];
+                            --z;
+                        }
+                        a.ocol[ob + z + 1] = g;
+                        a.oval[ob + z + 1] = v;
+                    }
+                }
+            }
+        }
+    }
+    if (MODE == P2_WRITE) {
+        part = warp_sum(part);
+        if ((tid & 31) == 0 && part != 0.0) atomicAdd(a.contrib, part);
+    }
+}
+
 // Member maps of a stage (see RowArgs::mpos, mge).
 __global__ void k_member_maps(const int32_t *members, int64_t s, const int32_t *pos,
                               const int32_t *elimflag, int32_t stage, int32_t *mpos, int32_t *mge) {
@@ -533,8 +844,41 @@ __global__ void k_core(const int64_t *rp, const int32_t *ci, const double *v, in
     }
 }
 
+int sm_count() {
+    static int n = 0;
+    if (n == 0) {
+        int dev = 0, v = 0;
+        if (cudaGetDevice(&dev) == cudaSuccess &&
+            cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && v > 0)
+            n = v;
+        else
+            n = 152;
+    }
+    return n;
+}
+
+// CTAs of the thread-per-row kernel: LANE_CTAS_PER_SM per SM at most (its
+// shared memory), fewer for small stages.
+unsigned lane_grid(int64_t rows) {
+    const int64_t full = (int64_t)sm_count() * LANE_CTAS_PER_SM;
+    const int64_t need = (rows + LANE_NT - 1) / LANE_NT;
+    return (unsigned)std::max<int64_t>(1, std::min(full, need));
+}
+
 template <int MODE>
-pmmf_status launch_rows(RowArgs &a, int64_t nnz_in, int64_t nnz_out, cudaStream_t st) {
+pmmf_status launch_rows(RowArgs &a, int64_t nnz_in, int64_t nnz_out, cudaStream_t st,
+                        const LaneArgs *lb = nullptr) {
+    if (lb) {
+        auto kern = a.K > 2 ? k_rows_lane<MODE, true> : k_rows_lane<MODE, false>;
+        PMMF_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)LANE_SMEM));
+        prof_begin(KF_ROWS, st);
+        kern<<<lane_grid(a.rows), LANE_NT, LANE_SMEM, st>>>(a, *lb);
+        double bytes = 12.0 * (double)nnz_in + 8.0 * (double)(a.rows + 1);
+        if (MODE == P1_WRITE || MODE == P2_WRITE) bytes += 12.0 * (double)nnz_out;
+        prof_end(KF_ROWS, st, bytes, 0.0);
+        return launched("rows_lane");
+    }
     const int64_t per_warp = rows_per_warp(a.cmax, a.outcap, MODE == P2_WRITE);
     size_t per = sizeof(double) * (size_t)per_warp;
     int warps = tuned(TUNE_ROWS_WARPS, a.cmax, 8);
@@ -608,6 +952,7 @@ pmmf_status update_stage(const Csr &A, const int32_t *act, int64_t n, const int3
     a.lvl_off = rot.lvl_off.p;
     a.nlev = rot.nlev.p;
     a.lvlrot = rot.lvl.p;
+    a.rec = rot.rec.p;
     a.K = rot.K;
     a.kidx = rot.kidx.p;
     a.kkv = rot.kk.p;
@@ -632,11 +977,16 @@ pmmf_status update_stage(const Csr &A, const int32_t *act, int64_t n, const int3
     a.mpos = mpos.p;
     a.mge = mge.p;
 
+    // thread-per-row passes (clusters of up to LANE_MAX_C; the tuning knob
+    // PMMF_TUNE_ROWS_KERNEL = 1 keeps the warp-per-row kernel)
+    const bool lane = s > 0 && cmax <= LANE_MAX_C && cmax <= REACH_MAX_C &&
+                      tuned(TUNE_ROWS_KERNEL, cmax, 2) == 2;
     // the counting passes take the fill pattern from the reach sets when the
     // stage has enough clusters to amortise building them (one warp per
-    // cluster walks its rotations, ~10-20 us whatever the stage's size)
+    // cluster walks its rotations, ~10-20 us whatever the stage's size), and
+    // always on the thread-per-row path
     DBuf<uint32_t> reach;
-    if (cmax <= REACH_MAX_C && s > 0 && cls.m >= tuned(TUNE_REACH_CLUSTERS, 1, 64)) {
+    if (cmax <= REACH_MAX_C && s > 0 && (lane || cls.m >= tuned(TUNE_REACH_CLUSTERS, 1, 64))) {
         const int words = (int)((rows_mask_words(cmax) + 3) / 4 * 4);
         PMMF_TRY(reach.alloc(s * words, st));
         // sets (32 words per coordinate) and tuples (at most cmax rotations)
@@ -651,6 +1001,46 @@ pmmf_status update_stage(const Csr &A, const int32_t *act, int64_t n, const int3
         a.reach_words = words;
     }
 
+    // incidence lists and the threads' overflow slots of the thread-per-row path
+    LaneArgs lb{};
+    DBuf<int64_t> inc_cnt, inc_cur;
+    DBuf<int32_t> inc_off;
+    DBuf<uint16_t> inc;
+    DBuf<uint2> ometa;
+    DBuf<double> oval;
+    if (lane) {
+        PMMF_TRY(inc_cnt.zeros(s + 1, st));
+        PMMF_TRY(inc_cur.alloc(s + 1, st));
+        k_inc_count<<<(unsigned)cls.m, 128, 0, st>>>(cls.coff.p, rot.roff.p, rot.rec.p, rot.K,
+                                                     rot.kidx.p, rot.kk.p, inc_cnt.p);
+        PMMF_TRY(launched("inc_count"));
+        PMMF_TRY(scan_i64_dup(inc_cnt.p, inc_cnt.p, inc_cur.p, s, st));
+        // at most K entries per rotation plus one end marker per member
+        const int64_t inc_cap = (int64_t)std::max(rot.K, 2) * rot.nrot + s;
+        if (inc_cap >= INT32_MAX) {
+            set_error("blocked update: incidence lists exceed 2^31 entries");
+            return PMMF_ERR_UNSUPPORTED;
+        }
+        PMMF_TRY(inc.alloc(inc_cap, st));
+        PMMF_TRY(inc_off.alloc(s + 1, st));
+        k_inc_fill<<<(unsigned)cls.m, 128, 0, st>>>(cls.coff.p, rot.roff.p, rot.rec.p, rot.K,
+                                                    rot.kidx.p, rot.kk.p, inc_cur.p, inc.p);
+        PMMF_TRY(launched("inc_fill"));
+        k_inc_finish<<<grid_for(s + 1, 256), 256, 0, st>>>(inc_cnt.p, s, inc.p, inc_off.p);
+        PMMF_TRY(launched("inc_finish"));
+        lb.inc_off = inc_off.p;
+        lb.inc = inc.p;
+        lb.ovf = (int)std::max<int64_t>(0, cmax - LANE_PS);
+        if (lb.ovf > 0) {
+            const int64_t threads = (int64_t)lane_grid(s) * LANE_NT;
+            PMMF_TRY(ometa.alloc(threads * lb.ovf, st));
+            PMMF_TRY(oval.alloc(threads * lb.ovf, st));
+            lb.ometa = ometa.p;
+            lb.oval = oval.p;
+        }
+    }
+    const LaneArgs *lbp = lane ? &lb : nullptr;
+
     // pass 1: V = A Q^T, scattered straight into the rows of W = V^T
     DBuf<int64_t> wrp, wcur;
     PMMF_TRY(wrp.zeros(s + 1, st));
@@ -659,7 +1049,7 @@ pmmf_status update_stage(const Csr &A, const int32_t *act, int64_t n, const int3
     a.v = A.val.p;
     a.rows = s;
     a.wcnt = wrp.p;
-    PMMF_TRY(launch_rows<P1_COUNT>(a, A.nnz, 0, st));
+    PMMF_TRY(launch_rows<P1_COUNT>(a, A.nnz, 0, st, lbp));
     // row starts of W, and a copy as the write cursors of pass 1
     PMMF_TRY(wcur.alloc(s + 1, st));
     PMMF_TRY(scan_i64_dup(wrp.p, wrp.p, wcur.p, s, st));
@@ -690,7 +1080,7 @@ pmmf_status update_stage(const Csr &A, const int32_t *act, int64_t n, const int3
         a.wtotal = wrp.p + s;
         a.wcap = wcap;
         a.wover = wover;
-        return launch_rows<P1_WRITE>(a, A.nnz, wcap, st);
+        return launch_rows<P1_WRITE>(a, A.nnz, wcap, st, lbp);
     };
     PMMF_TRY(pass1_write(false));
     // W's row r holds wrp[r] .. wcur[r] - 1 (the written part of its capacity)
@@ -716,7 +1106,7 @@ pmmf_status update_stage(const Csr &A, const int32_t *act, int64_t n, const int3
         a.newrow = sv.newrow.p;
         a.ocnt = caprp.p;
         a.maxlen = maxlen;
-        PMMF_TRY(launch_rows<P2_COUNT>(a, wcap, 0, st));
+        PMMF_TRY(launch_rows<P2_COUNT>(a, wcap, 0, st, lbp));
         PMMF_TRY(scan_i64(caprp.p, caprp.p, s2, st));
         // the four sizes in one write to the host mailbox
         k_pass2_sizes<<<1, 32, 0, st>>>(caprp.p + s2, maxlen, wrp.p + s, wover,
@@ -747,7 +1137,7 @@ pmmf_status update_stage(const Csr &A, const int32_t *act, int64_t n, const int3
     a.ocol = tcol.p;
     a.oval = tval.p;
     a.acnt = acnt.p;
-    PMMF_TRY(launch_rows<P2_WRITE>(a, hv[2], hv[0], st));
+    PMMF_TRY(launch_rows<P2_WRITE>(a, hv[2], hv[0], st, lbp));
     // exact row pointers, and the rows moved there; nnz is the capacity (an
     // upper bound), the exact count is rowptr[s2] on the device
     PMMF_TRY(out.next.rowptr.alloc(s2 + 1, st));

@@ -370,3 +370,34 @@ def test_generic_search_one_cluster_above_1536():
     g, o = factor_both(a, coords=None, k=2, eta=0.5, cluster_size=2048, core_size=64, seed=4)
     assert len(o.stages[0].offsets) == 2 and o.stages[0].active == 2048
     assert_same_factorization(g, o)
+
+
+@pytest.mark.parametrize("kernel", [1, 2])
+@pytest.mark.parametrize("case", ["knn-k2", "knn-k3", "poisson-bricks", "small-clusters", "c700"])
+def test_update_kernels_agree_with_oracle(kernel, case):
+    """The blocked update with one warp per row (1) and with one thread per row
+    applying only the rotations that reach each segment's pattern (2), forced
+    on every stage: the oracle's factorization bit for bit (every stage's A_p),
+    for Givens and 3-point rotations, given bricks, clusters of ~8 (patterns
+    within the shared-memory slots) and of ~700 (patterns that spill into the
+    global slots)."""
+    pm = gpu_lib()
+    L = pm.load()
+    if case == "knn-k2":
+        a, kw = I.knn_laplacian(3000, seed=5), dict(k=2, cluster_size=150, core_size=60)
+    elif case == "knn-k3":
+        a, kw = I.knn_laplacian(3000, seed=5), dict(k=3, cluster_size=150, core_size=60)
+    elif case == "poisson-bricks":
+        a, kw = I.poisson3d(16, seed=4), dict(k=2, cluster_size=128, core_size=64,
+                                               labels=I.grid_bricks(16, 16, 16, 8, 8, 2))
+    elif case == "small-clusters":
+        a, kw = I.knn_laplacian(1200, seed=9), dict(k=2, cluster_size=8, core_size=30)
+    else:
+        a, kw = I.knn_laplacian(4096, seed=3), dict(k=2, cluster_size=700, core_size=256)
+    try:
+        assert L.pmmf_set_tuning(pm.TUNE_PARAMS["rows_kernel"], 1 << 30, kernel) == 0
+        g, o = factor_both(a, eta=0.5, seed=6, **kw)
+        assert_same_factorization(g, o)
+    finally:
+        L.pmmf_clear_tuning()
+        pm.apply_tuning(pm.TUNING_PATH)
