@@ -392,10 +392,10 @@ pmmf_status pmmf_get_stage_matrix(const pmmf_handle *f, int p, int64_t *rowptr_n
  * from per-cluster reach sets when the stage has at least this many clusters,
  * default 64, else they run the rotation levels on the pattern; both give the
  * same counts; 1..2^31-1, use max_size 1), PMMF_TUNE_ROWS_KERNEL (the blocked
- * update's kernel: 2 = one thread per row, applying to each row segment only
- * the rotations that reach its pattern (the default for clusters of up to
- * 1,024 coordinates), 1 = one warp per row running every rotation level of
- * the segment's cluster; both give the same bits).  A value
+ * update's kernel: 1 = one warp per row running every rotation level of the
+ * segment's cluster (the default), 2 = one thread per row, applying to each
+ * row segment only the rotations that reach its pattern (clusters of up to
+ * 1,024 coordinates); both give the same bits).  A value
  * applies to launches whose largest cluster has at most max_size coordinates
  * and no smaller bucket matches; shared-memory limits still halve the row and
  * Gram warps when needed.  Process wide; INVALID_ARG for an unknown param or

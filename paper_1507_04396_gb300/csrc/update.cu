@@ -977,10 +977,13 @@ pmmf_status update_stage(const Csr &A, const int32_t *act, int64_t n, const int3
     a.mpos = mpos.p;
     a.mge = mge.p;
 
-    // thread-per-row passes (clusters of up to LANE_MAX_C; the tuning knob
-    // PMMF_TUNE_ROWS_KERNEL = 1 keeps the warp-per-row kernel)
+    // thread-per-row passes (clusters of up to LANE_MAX_C) when the tuning
+    // knob PMMF_TUNE_ROWS_KERNEL asks for them (2); the warp-per-row kernel is
+    // the default: measured on GB300 it is faster on every workload here (a
+    // thread's dependent loads of its row are serialized, and the threads of
+    // a warp diverge across segments and rows)
     const bool lane = s > 0 && cmax <= LANE_MAX_C && cmax <= REACH_MAX_C &&
-                      tuned(TUNE_ROWS_KERNEL, cmax, 2) == 2;
+                      tuned(TUNE_ROWS_KERNEL, cmax, 1) == 2;
     // the counting passes take the fill pattern from the reach sets when the
     // stage has enough clusters to amortise building them (one warp per
     // cluster walks its rotations, ~10-20 us whatever the stage's size), and
