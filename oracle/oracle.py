@@ -459,3 +459,106 @@ def block_angle_grad(theta: np.ndarray, D: np.ndarray, dO: np.ndarray) -> np.nda
     dth = np.zeros(kk * (kk - 1) // 2)
     lib().or_block_angle_grad(kk, _p(theta), _p(D), _p(dO), _p(dth))
     return dth
+
+
+# ---- one stage's steps, one at a time (for running a stage split over
+# several processes in tests) -----------------------------------------------
+
+def _step_lib():
+    L = lib()
+    if not hasattr(L, "_step_ready"):
+        vp, i64, i32 = C.c_void_p, C.c_int64, C.c_int
+        L.or_step_clusters.restype = i32
+        L.or_step_clusters.argtypes = [i64, vp, i32, i64, vp, i32, vp, vp, vp, vp, vp]
+        L.or_step_search.restype = i32
+        L.or_step_search.argtypes = [i64, vp, vp, vp, i64, vp, vp, vp, i64, vp, i32, vp, vp, vp, vp,
+                                     vp, vp]
+        L.or_step_transform.restype = i32
+        L.or_step_transform.argtypes = [i64, i64, vp, vp, vp, i64, vp, vp, vp, vp, vp, vp, i32, vp,
+                                        vp, vp, i64, vp]
+        L._step_ready = True
+    return L
+
+
+def _params(k, eta, cluster_size, core_size, seed, lloyd_iters=10, labels=None):
+    lab = None if labels is None else np.ascontiguousarray(labels, dtype=np.int32)
+    prm = _Params(k, eta, cluster_size, core_size, seed, 0, lloyd_iters,
+                  None if lab is None else _p(lab), 0 if lab is None else int(lab.max()) + 1)
+    return prm, lab
+
+
+def step_clusters(n, coords, act, p, *, k, eta, cluster_size, core_size, seed, labels=None):
+    """Stage p's clusters of the active set act (ascending global ids) and
+    their rotation counts (Alg. 1 "cluster", R10, R11): coff, members, e."""
+    L = _step_lib()
+    act = np.ascontiguousarray(act, dtype=np.int32)
+    s = len(act)
+    prm, lab = _params(k, eta, cluster_size, core_size, seed, labels=labels)
+    dim, cp = 0, None
+    if coords is not None:
+        coords = np.ascontiguousarray(coords, dtype=np.float64)
+        dim, cp = coords.shape[1], _p(coords)
+    m = C.c_int64()
+    coff = np.zeros(s + 1, dtype=np.int64)
+    members = np.zeros(max(s, 1), dtype=np.int32)
+    e = np.zeros(max(s, 1), dtype=np.int64)
+    st = L.or_step_clusters(n, cp, dim, s, _p(act), p, C.byref(prm), C.byref(m), _p(coff),
+                            _p(members), _p(e))
+    if st:
+        raise RuntimeError(f"or_step_clusters failed with status {st}")
+    mm = m.value
+    return coff[:mm + 1].copy(), members[:s].copy(), e[:mm].copy()
+
+
+def step_search(n, rowptr, col, val, coff, members, e, own, p, *, k, eta, cluster_size, core_size,
+                seed):
+    """Rotation search (Alg. 2) of the clusters own (ordinals) on a CSR over
+    all n rows in which at least their members' rows are present: the owned
+    clusters' rotations in order: (cluster, kk, idx [T, k], O [T, k*k], elim)."""
+    L = _step_lib()
+    own = np.ascontiguousarray(own, dtype=np.int32)
+    T = int(sum(int(e[u]) for u in own))
+    rc = np.zeros(max(T, 1), dtype=np.int32)
+    rk = np.zeros(max(T, 1), dtype=np.int32)
+    ri = np.zeros((max(T, 1), k), dtype=np.int32)
+    ro = np.zeros((max(T, 1), k * k))
+    re = np.zeros(max(T, 1), dtype=np.int32)
+    prm, _ = _params(k, eta, cluster_size, core_size, seed)
+    rowptr = np.ascontiguousarray(rowptr, dtype=np.int64)
+    col = np.ascontiguousarray(col, dtype=np.int32)
+    val = np.ascontiguousarray(val, dtype=np.float64)
+    coff = np.ascontiguousarray(coff, dtype=np.int64)
+    members = np.ascontiguousarray(members, dtype=np.int32)
+    e = np.ascontiguousarray(e, dtype=np.int64)
+    st = L.or_step_search(n, _p(rowptr), _p(col), _p(val), len(coff) - 1, _p(coff), _p(members),
+                          _p(e), len(own), _p(own), p, C.byref(prm), _p(rc), _p(rk), _p(ri),
+                          _p(ro), _p(re))
+    if st:
+        raise RuntimeError(f"or_step_search failed with status {st}")
+    return rc[:T], rk[:T], ri[:T], ro[:T], re[:T]
+
+
+def step_transform(n, rowptr, col, val, coff, members, roff, rk, ridx, rO, k):
+    """out = in Q^T for the given rows (CSR over them, global column ids) with
+    every cluster's rotations of the stage: (rowptr, col, val) of the output."""
+    L = _step_lib()
+    rowptr = np.ascontiguousarray(rowptr, dtype=np.int64)
+    col = np.ascontiguousarray(col, dtype=np.int32)
+    val = np.ascontiguousarray(val, dtype=np.float64)
+    args = [np.ascontiguousarray(x, dtype=t) for x, t in
+            ((coff, np.int64), (members, np.int32), (roff, np.int64), (rk, np.int32),
+             (ridx, np.int32), (rO, np.float64))]
+    nr = len(rowptr) - 1
+    orp = np.zeros(nr + 1, dtype=np.int64)
+    need = C.c_int64()
+    st = L.or_step_transform(n, nr, _p(rowptr), _p(col), _p(val), len(args[0]) - 1, *map(_p, args),
+                             k, _p(orp), None, None, 0, C.byref(need))
+    if st:
+        raise RuntimeError(f"or_step_transform failed with status {st}")
+    oc = np.zeros(max(need.value, 1), dtype=np.int32)
+    ov = np.zeros(max(need.value, 1))
+    st = L.or_step_transform(n, nr, _p(rowptr), _p(col), _p(val), len(args[0]) - 1, *map(_p, args),
+                             k, _p(orp), _p(oc), _p(ov), need.value, C.byref(need))
+    if st:
+        raise RuntimeError(f"or_step_transform failed with status {st}")
+    return orp, oc[:need.value], ov[:need.value]

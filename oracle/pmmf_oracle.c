@@ -492,8 +492,8 @@ static int transform_row(xform_ctx *cx, const orow *in, orow *out) {
  * OpenMP they are spread over the host's cores, each thread with its own
  * scratch, and the results do not depend on the thread count). */
 static int transform_rows(const ostage *st, const int32_t *cl, const int32_t *loc, int K,
-                          int64_t s, int64_t cmax, const orow *in, const int32_t *act,
-                          orow *out) {
+                          int64_t s, int64_t cmax, int64_t rowcap, const orow *in,
+                          const int32_t *act, orow *out) {
     int status = OR_OK;
 #ifdef _OPENMP
 #pragma omp parallel
@@ -501,17 +501,18 @@ static int transform_rows(const ostage *st, const int32_t *cl, const int32_t *lo
     {
         xform_ctx cx;
         cx.st = st; cx.cl = cl; cx.loc = loc; cx.K = K;
-        cx.ocap = s;
+        cx.ocap = rowcap;
         cx.dense = (double *)malloc(sizeof(double) * (size_t)(cmax ? cmax : 1));
-        cx.touched = (int32_t *)malloc(sizeof(int32_t) * (size_t)(s ? s : 1));
-        cx.ocol = (int32_t *)malloc(sizeof(int32_t) * (size_t)(s ? s : 1));
-        cx.oval = (double *)malloc(sizeof(double) * (size_t)(s ? s : 1));
+        cx.touched = (int32_t *)malloc(sizeof(int32_t) * (size_t)(rowcap ? rowcap : 1));
+        cx.ocol = (int32_t *)malloc(sizeof(int32_t) * (size_t)(rowcap ? rowcap : 1));
+        cx.oval = (double *)malloc(sizeof(double) * (size_t)(rowcap ? rowcap : 1));
         const int ok = cx.dense && cx.touched && cx.ocol && cx.oval;
 #ifdef _OPENMP
 #pragma omp for schedule(dynamic, 64)
 #endif
         for (int64_t r = 0; r < s; ++r) {
-            int sr = ok ? transform_row(&cx, &in[act[r]], &out[act[r]]) : OR_ERR_OOM;
+            const int64_t x = act ? act[r] : r;   /* act NULL: rows in order */
+            int sr = ok ? transform_row(&cx, &in[x], &out[x]) : OR_ERR_OOM;
             if (sr != OR_OK) {
 #ifdef _OPENMP
 #pragma omp critical
@@ -659,6 +660,98 @@ static int validate(int64_t n, const int64_t *rowptr, const int32_t *col, const 
     return OR_OK;
 }
 
+/* ------------------------------------------------------------------------ */
+/* The clusters of stage p (Alg. 1 "cluster"; R10) and their rotation counts
+ * (R11) for the active set act[0..s) (ascending): *mm clusters, offsets
+ * coff[mm + 1] into members[s] (ascending inside each cluster), e[mm]
+ * rotations each, all allocated here; cl / loc receive every active
+ * coordinate's cluster and index inside it.  q: the quantized points of all
+ * coordinates (have_coords = 0: one cluster per stage).                     */
+
+static int stage_clusters(const uint32_t *q, int dim, int have_coords, int64_t s,
+                          const int32_t *act, int p, const or_params *prm, int64_t *mm_out,
+                          int64_t **coff_out, int32_t **members_out, int64_t **e_out,
+                          int32_t *cl, int32_t *loc) {
+    *coff_out = NULL;
+    *members_out = NULL;
+    *e_out = NULL;
+    int64_t m = (s + prm->cluster_size / 2) / prm->cluster_size;
+    if (m < 1) m = 1;
+    if (!have_coords) m = 1;
+    if (p == 1 && prm->labels) m = prm->num_labels;
+    int32_t *label = (int32_t *)calloc((size_t)s, sizeof(int32_t));
+    if (!label) return OR_ERR_OOM;
+    if (p == 1 && prm->labels) {
+        /* given stage-1 clusters (R10: grid bricks for structured grids) */
+        for (int64_t r = 0; r < s; ++r) {
+            int32_t l = prm->labels[act[r]];
+            if (l < 0 || l >= m) { free(label); return OR_ERR_INVALID_ARG; }
+            label[r] = l;
+        }
+    } else if (m > 1) {
+        int ps = partition_q(q, dim, s, act, m, prm->lloyd_iters, label);
+        if (ps) { free(label); return ps; }
+    }
+    /* nonempty labels in ascending order become cluster ordinals */
+    int64_t *lcount = (int64_t *)calloc((size_t)m, sizeof(int64_t));
+    int64_t *lmap = (int64_t *)malloc(sizeof(int64_t) * (size_t)m);
+    if (!lcount || !lmap) { free(label); free(lcount); free(lmap); return OR_ERR_OOM; }
+    for (int64_t r = 0; r < s; ++r) lcount[label[r]]++;
+    int64_t mm = 0;
+    for (int64_t t = 0; t < m; ++t) lmap[t] = lcount[t] ? mm++ : -1;
+    /* elimination counts (R11) */
+    int64_t *coff = (int64_t *)calloc((size_t)(mm + 1), sizeof(int64_t));
+    int64_t *e = (int64_t *)calloc((size_t)(mm ? mm : 1), sizeof(int64_t));
+    int32_t *members = (int32_t *)malloc(sizeof(int32_t) * (size_t)(s ? s : 1));
+    int64_t *fill = (int64_t *)calloc((size_t)(mm ? mm : 1), sizeof(int64_t));
+    if (!coff || !e || !members || !fill) {
+        free(label); free(lcount); free(lmap); free(coff); free(e); free(members); free(fill);
+        return OR_ERR_OOM;
+    }
+    for (int64_t t = 0; t < m; ++t)
+        if (lcount[t]) coff[lmap[t] + 1] = lcount[t];
+    for (int64_t u = 0; u < mm; ++u) coff[u + 1] += coff[u];
+    int64_t esum = 0;
+    for (int64_t u = 0; u < mm; ++u) {
+        e[u] = (int64_t)floor(prm->eta * (double)(coff[u + 1] - coff[u]));
+        esum += e[u];
+    }
+    int64_t target = s - prm->core_size;
+    while (esum > target) {
+        int64_t bu = 0;
+        for (int64_t u = 1; u < mm; ++u)
+            if (e[u] > e[bu]) bu = u;
+        e[bu]--;
+        esum--;
+    }
+    if (esum == 0) {
+        /* every cluster too small to rotate: one cluster for this stage */
+        for (int64_t r = 0; r < s; ++r) label[r] = 0;
+        mm = 1;
+        lmap[0] = 0;
+        for (int64_t t = 1; t < m; ++t) lmap[t] = 0;
+        coff[0] = 0;
+        coff[1] = s;
+        int64_t ee = (int64_t)floor(prm->eta * (double)s);
+        if (ee > target) ee = target;
+        if (ee < 1) ee = 1;
+        e[0] = ee;
+    }
+    for (int64_t r = 0; r < s; ++r) {
+        int64_t u = lmap[label[r]];
+        int64_t pos = coff[u] + fill[u]++;
+        members[pos] = act[r];
+        cl[act[r]] = (int32_t)u;
+        loc[act[r]] = (int32_t)(pos - coff[u]);
+    }
+    free(fill); free(label); free(lcount); free(lmap);
+    *mm_out = mm;
+    *coff_out = coff;
+    *members_out = members;
+    *e_out = e;
+    return OR_OK;
+}
+
 or_fact *or_factor(int64_t n, const int64_t *rowptr, const int32_t *col, const double *val,
                    const double *coords, int dim, const or_params *prm, int record) {
     or_fact *f = (or_fact *)calloc(1, sizeof(or_fact));
@@ -715,82 +808,18 @@ or_fact *or_factor(int64_t n, const int64_t *rowptr, const int32_t *col, const d
         memset(st, 0, sizeof(*st));
         st->s = s;
 
-        /* ---- cluster the active coordinates (Alg. 1; R10) ---- */
-        int64_t m = (s + prm->cluster_size / 2) / prm->cluster_size;
-        if (m < 1) m = 1;
-        if (!coords) m = 1;
-        if (p == 1 && prm->labels) m = prm->num_labels;
-        int32_t *label = (int32_t *)calloc((size_t)s, sizeof(int32_t));
+        /* ---- cluster the active coordinates (Alg. 1; R10) and count the
+         *      stage's rotations per cluster (R11) ---- */
+        int64_t mm = 0, esum = 0;
         int64_t *e = NULL;
-        if (!label) goto oom;
-        if (p == 1 && prm->labels) {
-            /* given stage-1 clusters (R10: grid bricks for structured grids) */
-            for (int64_t r = 0; r < s; ++r) {
-                int32_t l = prm->labels[act[r]];
-                if (l < 0 || l >= m) { free(label); f->status = OR_ERR_INVALID_ARG; goto done; }
-                label[r] = l;
-            }
-        } else if (m > 1) {
-            int ps = partition_q(q, dim, s, act, m, prm->lloyd_iters, label);
-            if (ps) { free(label); goto oom; }
-        }
-        /* nonempty labels in ascending order become cluster ordinals */
-        int64_t *lcount = (int64_t *)calloc((size_t)m, sizeof(int64_t));
-        int64_t *lmap = (int64_t *)malloc(sizeof(int64_t) * (size_t)m);
-        if (!lcount || !lmap) { free(label); free(lcount); free(lmap); goto oom; }
-        for (int64_t r = 0; r < s; ++r) lcount[label[r]]++;
-        int64_t mm = 0;
-        for (int64_t t = 0; t < m; ++t) lmap[t] = lcount[t] ? mm++ : -1;
-        /* elimination counts (R11) */
-        st->coff = (int64_t *)calloc((size_t)(mm + 1), sizeof(int64_t));
-        e = (int64_t *)calloc((size_t)mm, sizeof(int64_t));
-        if (!st->coff || !e) { free(label); free(lcount); free(lmap); free(e); goto oom; }
-        for (int64_t t = 0; t < m; ++t)
-            if (lcount[t]) st->coff[lmap[t] + 1] = lcount[t];
-        for (int64_t u = 0; u < mm; ++u) st->coff[u + 1] += st->coff[u];
-        int64_t esum = 0;
-        for (int64_t u = 0; u < mm; ++u) {
-            e[u] = (int64_t)floor(prm->eta * (double)(st->coff[u + 1] - st->coff[u]));
-            esum += e[u];
-        }
-        int64_t target = s - prm->core_size;
-        while (esum > target) {
-            int64_t bu = 0;
-            for (int64_t u = 1; u < mm; ++u)
-                if (e[u] > e[bu]) bu = u;
-            e[bu]--;
-            esum--;
-        }
-        if (esum == 0) {
-            /* every cluster too small to rotate: one cluster for this stage */
-            for (int64_t r = 0; r < s; ++r) label[r] = 0;
-            mm = 1;
-            lmap[0] = 0;
-            for (int64_t t = 1; t < m; ++t) lmap[t] = 0;
-            st->coff[0] = 0;
-            st->coff[1] = s;
-            int64_t ee = (int64_t)floor(prm->eta * (double)s);
-            if (ee > target) ee = target;
-            if (ee < 1) ee = 1;
-            e[0] = ee;
-            esum = ee;
+        {
+            int cs = stage_clusters(q, dim, coords != NULL, s, act, p, prm, &mm, &st->coff,
+                                    &st->members, &e, cl, loc);
+            if (cs == OR_ERR_INVALID_ARG) { f->status = cs; goto done; }
+            if (cs != OR_OK) goto oom;
         }
         st->m = mm;
-        st->members = (int32_t *)malloc(sizeof(int32_t) * (size_t)s);
-        if (!st->members) { free(label); free(lcount); free(lmap); free(e); goto oom; }
-        {
-            int64_t *fill = (int64_t *)calloc((size_t)mm, sizeof(int64_t));
-            if (!fill) { free(label); free(lcount); free(lmap); free(e); goto oom; }
-            for (int64_t r = 0; r < s; ++r) {
-                int64_t u = lmap[label[r]];
-                int64_t pos = st->coff[u] + fill[u]++;
-                st->members[pos] = act[r];
-                cl[act[r]] = (int32_t)u;
-                loc[act[r]] = (int32_t)(pos - st->coff[u]);
-            }
-            free(fill);
-        }
-        free(label); free(lcount); free(lmap);
+        for (int64_t u = 0; u < mm; ++u) esum += e[u];
 
         /* ---- per-cluster rotation search (Alg. 2) ---- */
         st->nrot = esum;
@@ -876,13 +905,13 @@ or_fact *or_factor(int64_t n, const int64_t *rowptr, const int32_t *col, const d
                 if (A[act[r]].len > maxlen) maxlen = A[act[r]].len;
             orow *V = (orow *)calloc((size_t)n, sizeof(orow));
             if (!V) goto oom;
-            int status = transform_rows(st, cl, loc, K, s, cmax, A, act, V);
+            int status = transform_rows(st, cl, loc, K, s, cmax, s, A, act, V);
             orow *W = status == OR_OK ? transpose_rows(V, n, act, s) : NULL;
             rows_free(V, n);
             if (!W) status = status ? status : OR_ERR_OOM;
             orow *Ap = (orow *)calloc((size_t)n, sizeof(orow));
             if (!Ap) status = OR_ERR_OOM;
-            if (status == OR_OK) status = transform_rows(st, cl, loc, K, s, cmax, W, act, Ap);
+            if (status == OR_OK) status = transform_rows(st, cl, loc, K, s, cmax, s, W, act, Ap);
             rows_free(W, n);
             if (status != OR_OK) { rows_free(Ap, n); f->status = status; goto done; }
 
@@ -1685,4 +1714,133 @@ void or_block_angle_grad(int kk, const double *theta, const double *D, const dou
         dtheta[i] = acc;
         givens_rows(Lam, kk, j, l, c, s);   /* Lam_{i+1} = G_i Lam_i */
     }
+}
+
+/* ------------------------------------------------------------------------ */
+/* The steps of one stage, one at a time (Sec. 2.3: the clusters' searches
+ * are independent, and the blocked update needs every cluster's rotations).
+ * They let a test run the stage split over several processes, each with a
+ * part of the clusters, and compare the merged result with or_factor.  The
+ * arithmetic is or_factor's own: these only call its functions.            */
+
+int or_step_clusters(int64_t n, const double *coords, int dim, int64_t s, const int32_t *act,
+                      int p, const or_params *prm, int64_t *m_out, int64_t *coff,
+                      int32_t *members, int64_t *e) {
+    uint32_t *q = NULL;
+    if (coords) {
+        q = (uint32_t *)malloc(sizeof(uint32_t) * (size_t)(n * dim));
+        if (!q) return OR_ERR_OOM;
+        or_quantize(n, coords, dim, q);
+    }
+    int32_t *cl = (int32_t *)malloc(sizeof(int32_t) * (size_t)n);
+    int32_t *loc = (int32_t *)malloc(sizeof(int32_t) * (size_t)n);
+    int64_t mm = 0, *c = NULL, *ee = NULL;
+    int32_t *mem = NULL;
+    int st = (cl && loc) ? stage_clusters(q, dim, coords != NULL, s, act, p, prm, &mm, &c, &mem,
+                                          &ee, cl, loc)
+                         : OR_ERR_OOM;
+    if (st == OR_OK) {
+        *m_out = mm;
+        memcpy(coff, c, sizeof(int64_t) * (size_t)(mm + 1));
+        memcpy(members, mem, sizeof(int32_t) * (size_t)s);
+        memcpy(e, ee, sizeof(int64_t) * (size_t)mm);
+    }
+    free(q); free(cl); free(loc); free(c); free(mem); free(ee);
+    return st;
+}
+
+/* The rotation search of the clusters own[0..nown) of a stage (Alg. 2), each
+ * with its own ordinal in the random draws: the Gram of a cluster reads only
+ * its members' rows, so rows of other clusters may be empty.  Outputs, the
+ * owned clusters' rotations in order (step order inside a cluster): cluster
+ * ordinal, tuple size, tuple (K slots), block (K*K slots), eliminated id. */
+int or_step_search(int64_t n, const int64_t *rowptr, const int32_t *col, const double *val,
+                    int64_t m, const int64_t *coff, const int32_t *members, const int64_t *e,
+                    int64_t nown, const int32_t *own, int p, const or_params *prm, int32_t *rcl,
+                    int32_t *rk, int32_t *ridx, double *rO, int32_t *relim) {
+    ostage st;
+    memset(&st, 0, sizeof(st));
+    st.m = m;
+    st.coff = (int64_t *)coff;
+    st.members = (int32_t *)members;
+    st.rcl = rcl;
+    st.rk = rk;
+    st.ridx = ridx;
+    st.rO = rO;
+    st.relim = relim;
+    int64_t cmax = 0;
+    for (int64_t a = 0; a < nown; ++a) {
+        const int64_t u = own[a];
+        if (u < 0 || u >= m) return OR_ERR_INVALID_ARG;
+        if (coff[u + 1] - coff[u] > cmax) cmax = coff[u + 1] - coff[u];
+    }
+    double *G = (double *)malloc(sizeof(double) * (size_t)(cmax > 0 ? cmax * cmax : 1));
+    double *M = (double *)malloc(sizeof(double) * (size_t)(cmax > 0 ? cmax * cmax : 1));
+    if (!G || !M) { free(G); free(M); return OR_ERR_OOM; }
+    int64_t rpos = 0;
+    int status = OR_OK;
+    for (int64_t a = 0; a < nown && status == OR_OK; ++a) {
+        const int64_t u = own[a];
+        const int64_t cu = coff[u + 1] - coff[u];
+        or_gram(n, rowptr, col, val, cu, members + coff[u], G, M);
+        status = find_rotations(&st, u, e[u], G, M, prm, p, prm->k, &rpos);
+    }
+    free(G); free(M);
+    return status;
+}
+
+/* out[r] = in[r] Q^T for the rows ids[0..nrows) (CSR rowptr/col/val over
+ * those rows, columns global ids): every cluster's rotations of the stage
+ * (roff[m + 1] into rk / ridx (global ids) / rO, step order) applied to the
+ * row's entries in that cluster, exact zeros dropped, columns ascending.
+ * orowptr[nrows + 1] always receives the output's offsets; ocol / oval only
+ * when *needed (the output's entry count) fits cap. */
+int or_step_transform(int64_t n, int64_t nrows, const int64_t *rowptr, const int32_t *col,
+                       const double *val, int64_t m, const int64_t *coff, const int32_t *members,
+                       const int64_t *roff, const int32_t *rk, const int32_t *ridx,
+                       const double *rO, int K, int64_t *orowptr, int32_t *ocol, double *oval,
+                       int64_t cap, int64_t *needed) {
+    ostage st;
+    memset(&st, 0, sizeof(st));
+    st.m = m;
+    st.coff = (int64_t *)coff;
+    st.members = (int32_t *)members;
+    st.roff = (int64_t *)roff;
+    st.rk = (int32_t *)rk;
+    st.ridx = (int32_t *)ridx;
+    st.rO = (double *)rO;
+    int32_t *cl = (int32_t *)malloc(sizeof(int32_t) * (size_t)n);
+    int32_t *loc = (int32_t *)malloc(sizeof(int32_t) * (size_t)n);
+    orow *in = (orow *)calloc((size_t)(nrows ? nrows : 1), sizeof(orow));
+    orow *out = (orow *)calloc((size_t)(nrows ? nrows : 1), sizeof(orow));
+    int64_t cmax = 1;
+    if (!cl || !loc || !in || !out) { free(cl); free(loc); free(in); free(out); return OR_ERR_OOM; }
+    for (int64_t u = 0; u < m; ++u) {
+        if (coff[u + 1] - coff[u] > cmax) cmax = coff[u + 1] - coff[u];
+        for (int64_t l = coff[u]; l < coff[u + 1]; ++l) {
+            cl[members[l]] = (int32_t)u;
+            loc[members[l]] = (int32_t)(l - coff[u]);
+        }
+    }
+    for (int64_t r = 0; r < nrows; ++r) {
+        in[r].len = rowptr[r + 1] - rowptr[r];
+        in[r].col = (int32_t *)(col + rowptr[r]);
+        in[r].val = (double *)(val + rowptr[r]);
+    }
+    int status = transform_rows(&st, cl, loc, K, nrows, cmax, n, in, NULL, out);
+    int64_t tot = 0;
+    orowptr[0] = 0;
+    for (int64_t r = 0; r < nrows; ++r) {
+        tot += out[r].len;
+        orowptr[r + 1] = tot;
+    }
+    *needed = tot;
+    if (status == OR_OK && tot <= cap)
+        for (int64_t r = 0; r < nrows; ++r) {
+            memcpy(ocol + orowptr[r], out[r].col, sizeof(int32_t) * (size_t)out[r].len);
+            memcpy(oval + orowptr[r], out[r].val, sizeof(double) * (size_t)out[r].len);
+        }
+    rows_free(out, nrows);
+    free(in); free(cl); free(loc);
+    return status;
 }

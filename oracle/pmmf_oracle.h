@@ -78,6 +78,29 @@ int64_t or_stage_matrix(const or_fact *f, int p, int64_t *rowptr_n1, int32_t *co
 
 double or_error(const or_fact *f);          /* ||A - U^T H U||_F / ||A||_F */
 int or_threads(void);                        /* host threads a factorization uses */
+
+/* The steps of one stage one at a time, for running a stage split over
+ * several processes (each with a part of the clusters) in tests:
+ *   or_step_clusters    stage p's clusters of the active set act[s] and their
+ *                       rotation counts: *m, coff[m + 1] (capacity s + 1),
+ *                       members[s], e[m] (capacity s);
+ *   or_step_search      the search of the clusters own[nown] (rotations in
+ *                       order: cluster, tuple size, tuple, block, eliminated);
+ *   or_step_transform   out = in Q^T for a set of rows with every cluster's
+ *                       rotations of the stage (offsets always, entries when
+ *                       they fit cap; *needed = the entry count). */
+int or_step_clusters(int64_t n, const double *coords, int dim, int64_t s, const int32_t *act,
+                      int p, const or_params *prm, int64_t *m_out, int64_t *coff,
+                      int32_t *members, int64_t *e);
+int or_step_search(int64_t n, const int64_t *rowptr, const int32_t *col, const double *val,
+                    int64_t m, const int64_t *coff, const int32_t *members, const int64_t *e,
+                    int64_t nown, const int32_t *own, int p, const or_params *prm, int32_t *rcl,
+                    int32_t *rk, int32_t *ridx, double *rO, int32_t *relim);
+int or_step_transform(int64_t n, int64_t nrows, const int64_t *rowptr, const int32_t *col,
+                       const double *val, int64_t m, const int64_t *coff, const int32_t *members,
+                       const int64_t *roff, const int32_t *rk, const int32_t *ridx,
+                       const double *rO, int K, int64_t *orowptr, int32_t *ocol, double *oval,
+                       int64_t cap, int64_t *needed);
 double or_norm_a(const or_fact *f);
 int64_t or_core_size(const or_fact *f);
 void or_core(const or_fact *f, int32_t *idx, double *core);
