@@ -341,6 +341,63 @@ pmmf_status pmmf_block_angle_grad(const pmmf_handle *f, const double *dO, double
  * inverse is dropped and formed again on the next inverse request. */
 pmmf_status pmmf_set_h(pmmf_handle *f, const double *hdiag, const double *core, void *stream);
 
+/* ---- one stage's steps as separate calls (a stage split over GPUs) --------
+ * Sec. 2.3 runs the clusters' searches independently and the blocked update
+ * block by block, redistributing the matrix between stages.  These calls are
+ * the steps of pmmf_factor's stage (same kernels, same bits) for a caller that
+ * spreads the clusters of every stage over several GPUs and moves rows and
+ * rotations between them itself (paper_1507_04396_gb300/shard.py does, over
+ * torch.distributed).  All arrays are DEVICE memory unless marked HOST; ids
+ * are global coordinate ids; stage is 1-based (it enters the random draws).
+ *
+ * pmmf_shard_create: per-factorization state: the parameters (pmmf_params as
+ *   for pmmf_factor; coords and labels copied), the quantized points.
+ * pmmf_shard_clusters: stage's clusters of the active set act[s] (ascending)
+ *   and their rotation counts (Algorithm 1 "cluster", the schedule):
+ *   *m (HOST), coff[m + 1] (capacity s + 1), members[s], e[m] (capacity s).
+ * pmmf_shard_search: Algorithm 2 for the clusters own[nown] (ascending
+ *   ordinals of coff / members): rowptr/col/val is a CSR over the whole active
+ *   set in act order in which at least these clusters' members' rows are
+ *   filled (the others may be empty); outputs, the owned clusters' rotations
+ *   in order (sum of e over own entries): cluster ordinal, tuple size, tuple
+ *   (k slots, -1 unused), block (k * k slots), eliminated id.
+ * pmmf_shard_transform: out = R Q^T for the rows R (ids[nrows], CSR) with the
+ *   rotations of every cluster of the stage (in the layout of
+ *   pmmf_shard_search's outputs, ordered by cluster ordinal), exact zeros
+ *   dropped, columns ascending.  account != 0 adds the stage's accounting: an
+ *   eliminated row writes hdiag[id] (its diagonal) and adds its other
+ *   entries' squares to contrib[0]; an entry at an eliminated column adds its
+ *   square and is dropped; only the surviving rows are kept.  *out_rows and
+ *   *out_nnz (HOST) receive the result's size; pmmf_shard_result copies it
+ *   (ids[out_rows], rowptr[out_rows + 1], col / val[out_nnz], any may be
+ *   NULL) into caller buffers, until the next transform.
+ * pmmf_shard_sumsq: the sum of squares of val[nnz] into *out (HOST), for the
+ *   norm ||A||_F of the relative error; synchronizes the stream.
+ * Errors: INVALID_ARG, OOM, CUDA, UNSUPPORTED (a cluster or row too large for
+ * the kernels), NOT_CONVERGED (a k x k Jacobi). */
+typedef struct pmmf_shard pmmf_shard;
+pmmf_status pmmf_shard_create(int64_t n, const pmmf_params *p, pmmf_shard **out, void *stream);
+pmmf_status pmmf_shard_clusters(pmmf_shard *sh, int64_t stage, int64_t s, const int32_t *act,
+                                int64_t *m, int64_t *coff, int32_t *members, int64_t *e,
+                                void *stream);
+pmmf_status pmmf_shard_search(pmmf_shard *sh, int64_t stage, int64_t s, const int32_t *act,
+                              const int64_t *rowptr, const int32_t *col, const double *val,
+                              int64_t m, const int64_t *coff, const int32_t *members,
+                              const int64_t *e, int64_t nown, const int32_t *own,
+                              int32_t *rcluster, int32_t *rkk, int32_t *ridx, double *rO,
+                              int32_t *relim, void *stream);
+pmmf_status pmmf_shard_transform(pmmf_shard *sh, int64_t stage, int account, int64_t nrows,
+                                 const int32_t *ids, const int64_t *rowptr, const int32_t *col,
+                                 const double *val, int64_t s, int64_t m, const int64_t *coff,
+                                 const int32_t *members, int64_t nrot, const int32_t *rcluster,
+                                 const int32_t *rkk, const int32_t *ridx, const double *rO,
+                                 const int32_t *relim, double *hdiag, double *contrib,
+                                 int64_t *out_rows, int64_t *out_nnz, void *stream);
+pmmf_status pmmf_shard_result(const pmmf_shard *sh, int32_t *ids, int64_t *rowptr, int32_t *col,
+                              double *val, void *stream);
+pmmf_status pmmf_shard_sumsq(const double *val, int64_t nnz, double *out, void *stream);
+void pmmf_shard_free(pmmf_shard *sh);
+
 /* Release a handle (NULL-safe). */
 void pmmf_free(pmmf_handle *f);
 

@@ -334,7 +334,7 @@ __global__ void __launch_bounds__(SEL_THREADS)
 k_select(const int64_t *coff, const int32_t *members, const int64_t *goff, double *Gall,
          double *Mall, const int64_t *roff, uint64_t seed, int64_t stage, RotRec *rec, Rot2 *lvlrot,
          int32_t *lvl_off, int32_t *nlev, int32_t *elimflag, const int32_t *order,
-         const uint64_t *useed) {
+         const uint64_t *useed, const int32_t *ords) {
     extern __shared__ double sh[];
     const int64_t u = order ? order[blockIdx.x] : blockIdx.x;
     const int64_t base = coff[u];
@@ -370,7 +370,7 @@ k_select(const int64_t *coff, const int32_t *members, const int64_t *goff, doubl
     __syncthreads();
     if (tid == 0) {
         s_maxlev = 0;
-        if (e > 0) s_i = select_bit(mask, nwords, (int64_t)__umul64hi(draw(useed ? useed[u] : seed, stage, useed ? 0 : u, 0), (uint64_t)c), -1);
+        if (e > 0) s_i = select_bit(mask, nwords, (int64_t)__umul64hi(draw(useed ? useed[u] : seed, stage, useed ? 0 : (ords ? ords[u] : u), 0), (uint64_t)c), -1);
     }
     __syncthreads();
 
@@ -425,7 +425,7 @@ k_select(const int64_t *coff, const int32_t *members, const int64_t *goff, doubl
             s_s = ss;
             if (t + 1 < e)
                 s_i = select_bit(mask, nwords,
-                                 (int64_t)__umul64hi(draw(useed ? useed[u] : seed, stage, useed ? 0 : u, t + 1), (uint64_t)(c - t - 1)), -1);
+                                 (int64_t)__umul64hi(draw(useed ? useed[u] : seed, stage, useed ? 0 : (ords ? ords[u] : u), t + 1), (uint64_t)(c - t - 1)), -1);
         }
         __syncthreads();
         // rows/columns i and j of G and M for every other active coordinate
@@ -542,7 +542,7 @@ __global__ void __launch_bounds__(NT, NT <= 256 ? 2 : 1)
 k_select_fast(const int64_t *coff, const int32_t *members, const int64_t *goff, double *Gall,
               double *Mall, const int64_t *roff, uint64_t seed, int64_t stage, RotRec *rec,
               Rot2 *lvlrot, int32_t *lvl_off, int32_t *nlev, int32_t *elimflag,
-              const int32_t *order, const uint64_t *useed) {
+              const int32_t *order, const uint64_t *useed, const int32_t *ords) {
     constexpr int NW = NT / 32;                 // warps
     constexpr int NCTT = NT - 32 * FP_WARPS;    // column threads
     extern __shared__ double sh[];
@@ -587,7 +587,7 @@ k_select_fast(const int64_t *coff, const int32_t *members, const int64_t *goff, 
         const int rem = c - wi * 32;
         mask[wi] = rem >= 32 ? 0xffffffffu : ((1u << rem) - 1u);
     }
-    for (int t = tid; t < e; t += NT) draws[t] = draw(useed ? useed[u] : seed, stage, useed ? 0 : u, t);
+    for (int t = tid; t < e; t += NT) draws[t] = draw(useed ? useed[u] : seed, stage, useed ? 0 : (ords ? ords[u] : u), t);
     for (int q = tid; q < e + 2; q += NT) lcnt[q] = 0;
     __syncthreads();
     if (tid == 0) {
@@ -926,7 +926,8 @@ pmmf_status gram_and_select(const Csr &A, const int32_t *act_ids, const int32_t 
                             const int32_t *cl, const int32_t *loc, const StageClusters &cls,
                             int64_t cmax, uint64_t seed, int64_t stage, StageRotations &rot,
                             int32_t *elimflag, cudaStream_t st, const int32_t *order,
-                            const uint64_t *useed, unsigned *status, int64_t gram_total) {
+                            const uint64_t *useed, unsigned *status, int64_t gram_total,
+                            const int32_t *ords, int64_t nmem) {
     GramBlocks gb;
     PMMF_TRY(gram_blocks(cls, gb, st, gram_total));
     const int64_t s = A.rows;
@@ -951,18 +952,19 @@ pmmf_status gram_and_select(const Csr &A, const int32_t *act_ids, const int32_t 
     prof_begin(KF_GRAM, st);
     k_gram_rows<<<grid_for(s * 32, 32 * warps), 32 * warps, gsh, st>>>(
         A.rowptr.p, A.col.p, A.val.p, trp.p, tul.p, tv.p, pos, cl, loc, cls.coff.p, cls.members.p,
-        s, cmax, gb.goff.p, gb.G.p, gb.M.p);
+        nmem >= 0 ? nmem : s, cmax, gb.goff.p, gb.G.p, gb.M.p);
     // compulsory traffic: the active matrix (12 B per entry) and its
     // transpose (16 B per entry) once, their row pointers, and both c_u x c_u
     // outputs
     prof_end(KF_GRAM, st, 28.0 * (double)A.nnz + 16.0 * (double)s + 16.0 * (double)gb.total, 0.0);
     PMMF_TRY(launched("gram"));
-    return select_stage(cls, cmax, gb, seed, stage, rot, elimflag, st, order, useed, status);
+    return select_stage(cls, cmax, gb, seed, stage, rot, elimflag, st, order, useed, status, ords);
 }
 
 pmmf_status select_stage(const StageClusters &cls, int64_t cmax, GramBlocks &gb, uint64_t seed,
                          int64_t stage, StageRotations &rot, int32_t *elimflag, cudaStream_t st,
-                         const int32_t *order, const uint64_t *useed, unsigned *status) {
+                         const int32_t *order, const uint64_t *useed, unsigned *status,
+                         const int32_t *ords) {
     const int64_t m = cls.m;
     DBuf<int64_t> &goff = gb.goff;
     DBuf<double> &G = gb.G, &M = gb.M;
@@ -972,7 +974,7 @@ pmmf_status select_stage(const StageClusters &cls, int64_t cmax, GramBlocks &gb,
             return PMMF_ERR_INVALID_ARG;
         }
         return select_kpoint(cls, cmax, goff.p, G.p, M.p, seed, stage, rot, elimflag, st, order,
-                             useed, status);
+                             useed, status, ords);
     }
     PMMF_TRY(rot.rec.alloc(rot.nrot > 0 ? rot.nrot : 1, st));
     PMMF_TRY(rot.lvl.alloc(rot.nrot > 0 ? rot.nrot : 1, st));
@@ -1017,7 +1019,7 @@ pmmf_status select_stage(const StageClusters &cls, int64_t cmax, GramBlocks &gb,
             PMMF_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shf));
         kern<<<(unsigned)m, nt, shf, st>>>(cls.coff.p, cls.members.p, goff.p, G.p, M.p, rot.roff.p,
                                            seed, stage, rot.rec.p, rot.lvl.p, rot.lvl_off.p,
-                                           rot.nlev.p, elimflag, order, useed);
+                                           rot.nlev.p, elimflag, order, useed, ords);
         return PMMF_OK;
     };
     if (fits_fast && sw == 8 && kpt <= 1) PMMF_TRY(launch(k_select_fast<1, 256>, 256));
@@ -1032,7 +1034,7 @@ pmmf_status select_stage(const StageClusters &cls, int64_t cmax, GramBlocks &gb,
         k_select<<<(unsigned)m, SEL_THREADS, shb, st>>>(cls.coff.p, cls.members.p, goff.p, G.p, M.p,
                                                         rot.roff.p, seed, stage, rot.rec.p, rot.lvl.p,
                                                         rot.lvl_off.p, rot.nlev.p, elimflag, order,
-                                                        useed);
+                                                        useed, ords);
     }
     prof_end(KF_SELECT, st, 0.0, sel_flops);
     PMMF_TRY(launched("select"));

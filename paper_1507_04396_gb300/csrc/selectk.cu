@@ -68,7 +68,7 @@ k_select_k(const int64_t *coff, const int32_t *members, const int64_t *goff, dou
            double *Mall, const int64_t *roff, uint64_t seed, int64_t stage, int K, int32_t *kidx,
            int32_t *kkv, int32_t *kel, int32_t *klvl, double *kO, int32_t *lvlidx,
            int32_t *lvl_off, int32_t *nlev, int32_t *elimflag, const int32_t *order,
-           const uint64_t *useed, unsigned *status) {
+           const uint64_t *useed, unsigned *status, const int32_t *ords) {
     extern __shared__ double sh[];
     const int64_t u = order ? order[blockIdx.x] : blockIdx.x;
     const int64_t base = coff[u];
@@ -91,7 +91,7 @@ k_select_k(const int64_t *coff, const int32_t *members, const int64_t *goff, dou
     __shared__ int s_bi[KS_WARPS];
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     const uint64_t sd = useed ? useed[u] : seed;
-    const uint64_t uu = useed ? 0 : (uint64_t)u;
+    const uint64_t uu = useed ? 0 : (uint64_t)(ords ? ords[u] : u);
 
     for (int a = tid; a < c; a += KS_THREADS) {
         const double g = G[(int64_t)a * c + a];
@@ -282,7 +282,7 @@ k_select_k(const int64_t *coff, const int32_t *members, const int64_t *goff, dou
 pmmf_status select_kpoint(const StageClusters &cls, int64_t cmax, const int64_t *goff, double *G,
                           double *M, uint64_t seed, int64_t stage, StageRotations &rot,
                           int32_t *elimflag, cudaStream_t st, const int32_t *order,
-                          const uint64_t *useed, unsigned *status) {
+                          const uint64_t *useed, unsigned *status, const int32_t *ords) {
     const int64_t m = cls.m, nr = rot.nrot > 0 ? rot.nrot : 1;
     const int K = rot.K;
     PMMF_TRY(rot.kidx.alloc(nr * K, st));
@@ -307,7 +307,7 @@ pmmf_status select_kpoint(const StageClusters &cls, int64_t cmax, const int64_t 
                                                    rot.roff.p, seed, stage, K, rot.kidx.p, rot.kk.p,
                                                    rot.kel.p, rot.klvl.p, rot.kO.p, rot.lvlidx.p,
                                                    rot.lvl_off.p, rot.nlev.p, elimflag, order,
-                                                   useed, status);
+                                                   useed, status, ords);
     prof_end(KF_SELECT, st, 0.0, 0.0);
     return launched("select_k");
 }

@@ -98,24 +98,30 @@ struct GramBlocks {
 pmmf_status gram_blocks(const StageClusters &cls, GramBlocks &gb, cudaStream_t st,
                         int64_t total = -1);
 // Rotation search of every cluster on formed Gram blocks.
+// ords (optional): per cluster the ordinal its random draws use (default the
+// cluster's own index): a subset of a stage's clusters, renumbered, searched
+// exactly as in the whole stage.
 pmmf_status select_stage(const StageClusters &cls, int64_t cmax, GramBlocks &gb, uint64_t seed,
                          int64_t stage, StageRotations &rot, int32_t *elimflag, cudaStream_t st,
                          const int32_t *order = nullptr, const uint64_t *useed = nullptr,
-                         unsigned *status = nullptr);
+                         unsigned *status = nullptr, const int32_t *ords = nullptr);
 
 // rot.K selects Givens (2) or k-point (>= 3) rotations; status receives
-// ST_NOT_CONVERGED when a k x k Jacobi did not converge.
+// ST_NOT_CONVERGED when a k x k Jacobi did not converge.  nmem (optional): the
+// clusters' member count when they cover only part of A's rows (the other
+// rows empty, their cl -1); ords as for select_stage.
 pmmf_status gram_and_select(const Csr &A, const int32_t *act, const int32_t *pos,
                             const int32_t *cl, const int32_t *loc, const StageClusters &cls,
                             int64_t cmax, uint64_t seed, int64_t stage, StageRotations &rot,
                             int32_t *elimflag, cudaStream_t st, const int32_t *order = nullptr,
                             const uint64_t *useed = nullptr, unsigned *status = nullptr,
-                            int64_t gram_total = -1);
+                            int64_t gram_total = -1, const int32_t *ords = nullptr,
+                            int64_t nmem = -1);
 // The k >= 3 search on Gram blocks already formed (selectk.cu).
 pmmf_status select_kpoint(const StageClusters &cls, int64_t cmax, const int64_t *goff, double *G,
                           double *M, uint64_t seed, int64_t stage, StageRotations &rot,
                           int32_t *elimflag, cudaStream_t st, const int32_t *order,
-                          const uint64_t *useed, unsigned *status);
+                          const uint64_t *useed, unsigned *status, const int32_t *ords = nullptr);
 
 // Blocked update A_p = (A Q^T)^T Q^T, residual accounting, H diagonal and
 // compaction to the surviving coordinates.
@@ -141,6 +147,20 @@ pmmf_status update_stage(const Csr &A, const int32_t *act, int64_t n, const int3
                          int64_t stage, const Survivors &sv, double *hdiag, double *contrib,
                          UpdateOut &out, unsigned *status, cudaStream_t st,
                          double *contrib_cl = nullptr);
+
+// out = R Q^T for the rows of R (row r is global id ids[r]) with every
+// cluster's rotations of a stage, exact zeros dropped, columns ascending (the
+// blocked update's second pass on a set of rows).  stage >= 0 adds the
+// accounting of that stage's eliminations (elimflag[x] == stage): an
+// eliminated row gives hdiag[id] (its diagonal) and adds its other entries'
+// squares to *contrib, an entry at an eliminated column adds its square and is
+// dropped, and out (rows out_ids) holds the surviving rows only.  stage < 0:
+// every row and entry is kept.  Synchronizes st (output sizes).
+pmmf_status transform_stage(const Csr &R, const int32_t *ids, const int32_t *cl, const int32_t *loc,
+                            const StageClusters &cls, int64_t cmax, const StageRotations &rot,
+                            const int32_t *elimflag, int32_t stage, double *hdiag,
+                            double *contrib, Csr &out, DBuf<int32_t> &out_ids,
+                            unsigned *status, cudaStream_t st);
 
 pmmf_status set_positions(const int32_t *act, int64_t s, int32_t *pos, cudaStream_t st);
 pmmf_status extract_core(const Csr &A, const int32_t *pos, int64_t s, double *core, double *hdiag,

@@ -794,6 +794,16 @@ __global__ void k_member_maps(const int32_t *members, int64_t s, const int32_t *
     }
 }
 
+// mge of RowArgs alone (the row passes that need no destination positions).
+__global__ void k_member_ge(const int32_t *members, int64_t s, const int32_t *elimflag,
+                            int32_t stage, int32_t *mge) {
+    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < s;
+         j += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t g = members[j];
+        mge[j] = elimflag[g] == stage ? (int32_t)((uint32_t)g | 0x80000000u) : g;
+    }
+}
+
 __global__ void k_survivors(const int32_t *act, int64_t s, const int32_t *elimflag, int32_t stage,
                             int32_t *flag) {
     for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < s;
@@ -1154,6 +1164,108 @@ pmmf_status update_stage(const Csr &A, const int32_t *act, int64_t n, const int3
                                                                 tval.p, out.next.col.p, out.next.val.p);
         PMMF_TRY(launched("compact_rows"));
     }
+    return PMMF_OK;
+}
+
+pmmf_status transform_stage(const Csr &R, const int32_t *ids, const int32_t *cl, const int32_t *loc,
+                            const StageClusters &cls, int64_t cmax, const StageRotations &rot,
+                            const int32_t *elimflag, int32_t stage, double *hdiag,
+                            double *contrib, Csr &out, DBuf<int32_t> &out_ids,
+                            unsigned *status, cudaStream_t st) {
+    const int64_t s = R.rows;
+    RowArgs a{};
+    a.act = ids;
+    a.cl = cl;
+    a.loc = loc;
+    a.coff = cls.coff.p;
+    a.roff = rot.roff.p;
+    a.lvl_off = rot.lvl_off.p;
+    a.nlev = rot.nlev.p;
+    a.lvlrot = rot.lvl.p;
+    a.rec = rot.rec.p;
+    a.K = rot.K;
+    a.kidx = rot.kidx.p;
+    a.kkv = rot.kk.p;
+    a.lvlidx = rot.lvlidx.p;
+    a.kO = rot.kO.p;
+    a.cmax = cmax;
+    a.elimflag = elimflag;
+    a.stage = stage;
+    a.status = status;
+    a.contrib = contrib;
+    a.hdiag = hdiag;
+    // member -> global id, with bit 31 when this stage eliminates it
+    int64_t nmem = 0;
+    PMMF_CUDA_TRY(cudaMemcpyAsync(&nmem, cls.coff.p + cls.m, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+    PMMF_CUDA_TRY(cudaStreamSynchronize(st));
+    DBuf<int32_t> mge;
+    PMMF_TRY(mge.alloc(std::max<int64_t>(nmem, 1), st));
+    if (nmem > 0) {
+        k_member_ge<<<grid_for(nmem, 256), 256, 0, st>>>(cls.members.p, nmem, elimflag, stage, mge.p);
+        PMMF_TRY(launched("member_ge"));
+    }
+    a.mge = mge.p;
+    // the surviving rows and their output positions
+    Survivors sv;
+    PMMF_TRY(sv.flag.alloc(std::max<int64_t>(s, 1), st));
+    PMMF_TRY(sv.newrow.alloc(s + 1, st));
+    int64_t s2 = 0;
+    if (s > 0) {
+        k_survivors<<<grid_for(s, 256), 256, 0, st>>>(ids, s, elimflag, stage, sv.flag.p);
+        PMMF_TRY(launched("survivors"));
+    }
+    PMMF_TRY(scan_i32_to_i64(sv.flag.p, sv.newrow.p, s, st));
+    PMMF_CUDA_TRY(cudaMemcpyAsync(&s2, sv.newrow.p + s, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+    PMMF_CUDA_TRY(cudaStreamSynchronize(st));
+    PMMF_TRY(out_ids.alloc(std::max<int64_t>(s2, 1), st));
+    if (s > 0) {
+        k_compact_act<<<grid_for(s, 256), 256, 0, st>>>(ids, s, sv.flag.p, sv.newrow.p, out_ids.p);
+        PMMF_TRY(launched("compact_ids"));
+    }
+    a.rp = R.rowptr.p;
+    a.rend = nullptr;
+    a.ci = R.col.p;
+    a.v = R.val.p;
+    a.rows = s;
+    a.newrow = sv.newrow.p;
+    DBuf<int64_t> caprp, acnt;
+    DBuf<unsigned long long> maxlen;
+    PMMF_TRY(caprp.alloc(s2 + 1, st));
+    PMMF_TRY(acnt.alloc(s2 + 1, st));
+    PMMF_TRY(maxlen.zeros(1, st));
+    a.ocnt = caprp.p;
+    a.maxlen = maxlen.p;
+    if (s > 0) PMMF_TRY(launch_rows<P2_COUNT>(a, R.nnz, 0, st));
+    PMMF_TRY(scan_i64(caprp.p, caprp.p, s2, st));
+    int64_t cap = 0;
+    unsigned long long ml = 0;
+    PMMF_CUDA_TRY(cudaMemcpyAsync(&cap, caprp.p + s2, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+    PMMF_CUDA_TRY(cudaMemcpyAsync(&ml, maxlen.p, sizeof(ml), cudaMemcpyDeviceToHost, st));
+    PMMF_CUDA_TRY(cudaStreamSynchronize(st));
+    DBuf<int32_t> tcol;
+    DBuf<double> tval;
+    PMMF_TRY(tcol.alloc(std::max<int64_t>(cap, 1), st));
+    PMMF_TRY(tval.alloc(std::max<int64_t>(cap, 1), st));
+    a.outcap = (int)(ml > 0 ? ml : 1);
+    a.orp = caprp.p;
+    a.ocol = tcol.p;
+    a.oval = tval.p;
+    a.acnt = acnt.p;
+    if (s > 0) PMMF_TRY(launch_rows<P2_WRITE>(a, R.nnz, cap, st));
+    out.rows = s2;
+    PMMF_TRY(out.rowptr.alloc(s2 + 1, st));
+    PMMF_TRY(scan_i64(acnt.p, out.rowptr.p, s2, st));
+    PMMF_CUDA_TRY(cudaMemcpyAsync(&out.nnz, out.rowptr.p + s2, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+    PMMF_CUDA_TRY(cudaStreamSynchronize(st));
+    out.nnz_exact = true;
+    PMMF_TRY(out.col.alloc(std::max<int64_t>(out.nnz, 1), st));
+    PMMF_TRY(out.val.alloc(std::max<int64_t>(out.nnz, 1), st));
+    if (s2 > 0) {
+        k_compact_rows<<<grid_for(s2 * 32, 256), 256, 0, st>>>(caprp.p, out.rowptr.p, s2, tcol.p,
+                                                                tval.p, out.col.p, out.val.p);
+        PMMF_TRY(launched("compact_rows"));
+    }
+    // the scratch above is freed stream-ordered on st; the results stay
     return PMMF_OK;
 }
 

@@ -72,7 +72,9 @@ EXPORTS = ["pmmf_factor", "pmmf_apply", "pmmf_solve_precond", "pmmf_free", "pmmf
            "pmmf_launch_count", "pmmf_alloc_count", "pmmf_probe_fp64", "pmmf_apply_backward", "pmmf_get_angles", "pmmf_set_angles",
            "pmmf_set_h", "pmmf_factor_blockdiag", "pmmf_factor_batched", "pmmf_get_batch",
            "pmmf_get_precision_stats", "pmmf_set_tuning", "pmmf_clear_tuning",
-           "pmmf_solve_precond_sym", "pmmf_block_angle_grad"]
+           "pmmf_solve_precond_sym", "pmmf_block_angle_grad", "pmmf_shard_create",
+           "pmmf_shard_clusters", "pmmf_shard_search", "pmmf_shard_transform",
+           "pmmf_shard_result", "pmmf_shard_sumsq", "pmmf_shard_free"]
 
 _lib = None
 
@@ -142,6 +144,23 @@ def load(path: str = LIB_PATH):
     L.pmmf_set_tuning.argtypes = [i32, i64, i32]
     L.pmmf_clear_tuning.restype = None
     L.pmmf_clear_tuning.argtypes = []
+    L.pmmf_shard_create.restype = i32
+    L.pmmf_shard_create.argtypes = [i64, C.POINTER(Params), C.POINTER(vp), vp]
+    L.pmmf_shard_clusters.restype = i32
+    L.pmmf_shard_clusters.argtypes = [vp, i64, i64, vp, C.POINTER(i64), vp, vp, vp, vp]
+    L.pmmf_shard_search.restype = i32
+    L.pmmf_shard_search.argtypes = [vp, i64, i64, vp, vp, vp, vp, i64, vp, vp, vp, i64, vp, vp, vp,
+                                    vp, vp, vp, vp]
+    L.pmmf_shard_transform.restype = i32
+    L.pmmf_shard_transform.argtypes = [vp, i64, i32, i64, vp, vp, vp, vp, i64, i64, vp, vp, i64,
+                                       vp, vp, vp, vp, vp, vp, vp, C.POINTER(i64), C.POINTER(i64),
+                                       vp]
+    L.pmmf_shard_result.restype = i32
+    L.pmmf_shard_result.argtypes = [vp, vp, vp, vp, vp, vp]
+    L.pmmf_shard_sumsq.restype = i32
+    L.pmmf_shard_sumsq.argtypes = [vp, i64, vp, vp]
+    L.pmmf_shard_free.restype = None
+    L.pmmf_shard_free.argtypes = [vp]
     L.pmmf_profile_begin.restype = i32
     L.pmmf_profile_begin.argtypes = [C.c_uint]
     L.pmmf_profile_end.restype = i32

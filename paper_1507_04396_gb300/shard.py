@@ -282,3 +282,148 @@ def factor_sharded(backend, n: int, rowptr, col, val, *, core_size: int, max_sta
     out.norm_a = float(np.sqrt(norm2))
     out.error = float(np.sqrt(total) / out.norm_a) if out.norm_a > 0 else 0.0
     return out
+
+
+# ---------------------------------------------------------------- the GPU backend
+
+class GpuStageBackend:
+    """Each rank's compute on its GPU through the library's stage calls
+    (pmmf_shard_*): the same kernels as pmmf_factor.  This class only
+    arranges device arrays (row orders, the transposed parts of W) for them."""
+
+    def __init__(self, n, coords, *, k, eta, cluster_size, core_size, seed, labels=None,
+                 lloyd_iters=10, device=None, stream=None):
+        import ctypes as C
+        from . import pmmf
+        self.C, self.pm = C, pmmf
+        self.L = pmmf.load()
+        self.device = torch.device(device) if device is not None else torch.device(
+            "cuda", torch.cuda.current_device())
+        self.n, self.k = n, k
+        self.stream = stream
+        self._keep = []
+        cp, cd, cl = None, 0, pmmf.HOST
+        if coords is not None:
+            co = np.ascontiguousarray(coords, dtype=np.float64)
+            self._keep.append(co)
+            cp, cd = co.ctypes.data, co.shape[1]
+        lp, nl = None, 0
+        if labels is not None:
+            lab = np.ascontiguousarray(labels, dtype=np.int32)
+            self._keep.append(lab)
+            lp, nl = lab.ctypes.data, int(lab.max()) + 1
+        prm = pmmf.Params(k, eta, cluster_size, core_size, seed, 0, lloyd_iters, cp, cd, cl, 0, 0,
+                          lp, pmmf.HOST, nl)
+        h = C.c_void_p()
+        pmmf._check(self.L.pmmf_shard_create(n, C.byref(prm), C.byref(h), self._s()))
+        self.h = h.value
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.L.pmmf_shard_free(self.h)
+            self.h = None
+
+    def __del__(self):
+        self.close()
+
+    def _s(self):
+        return self.pm._stream(self.stream)
+
+    @staticmethod
+    def _p(t):
+        return t.data_ptr() if t is not None and t.numel() > 0 else None
+
+    def clusters(self, p, act):
+        C = self.C
+        a32 = act.to(torch.int32).contiguous()
+        s = a32.numel()
+        coff = torch.empty(s + 1, dtype=torch.int64, device=self.device)
+        mem = torch.empty(s, dtype=torch.int32, device=self.device)
+        e = torch.empty(s, dtype=torch.int64, device=self.device)
+        m = C.c_int64()
+        self.pm._check(self.L.pmmf_shard_clusters(self.h, p, s, self._p(a32), C.byref(m),
+                                                   self._p(coff), self._p(mem), self._p(e),
+                                                   self._s()))
+        mm = m.value
+        return coff[:mm + 1].clone(), mem.to(torch.int64), e[:mm].clone()
+
+    def search(self, p, rows, act, coff, members, e, own):
+        k = self.k
+        s = act.numel()
+        # the held rows as a CSR over the whole active set (ids ascending, so
+        # their entries are already in the active order)
+        pos = torch.full((self.n,), -1, dtype=torch.int64, device=self.device)
+        pos[act] = torch.arange(s, device=self.device)
+        lens = torch.zeros(s, dtype=torch.int64, device=self.device)
+        lens[pos[rows.ids]] = rows.rowptr[1:] - rows.rowptr[:-1]
+        rp = torch.zeros(s + 1, dtype=torch.int64, device=self.device)
+        rp[1:] = torch.cumsum(lens, 0)
+        col = rows.col.to(torch.int32).contiguous()
+        val = rows.val.contiguous()
+        T = int(e[own].sum()) if own.numel() else 0
+        rc = torch.empty(max(T, 1), dtype=torch.int32, device=self.device)
+        rk = torch.empty(max(T, 1), dtype=torch.int32, device=self.device)
+        ri = torch.empty(max(T, 1) * k, dtype=torch.int32, device=self.device)
+        ro = torch.empty(max(T, 1) * k * k, dtype=torch.float64, device=self.device)
+        re = torch.empty(max(T, 1), dtype=torch.int32, device=self.device)
+        a32 = act.to(torch.int32).contiguous()
+        m32 = members.to(torch.int32).contiguous()
+        o32 = own.to(torch.int32).contiguous()
+        self.pm._check(self.L.pmmf_shard_search(
+            self.h, p, s, self._p(a32), rp.data_ptr(), self._p(col), self._p(val), coff.numel() - 1,
+            coff.data_ptr(), m32.data_ptr(), e.data_ptr(), o32.numel(), self._p(o32), rc.data_ptr(),
+            rk.data_ptr(), ri.data_ptr(), ro.data_ptr(), re.data_ptr(), self._s()))
+        i64 = lambda x: x[:T].to(torch.int64)
+        return (i64(rc), i64(rk), ri[:T * k].to(torch.int64).reshape(T, k),
+                ro[:T * k * k].reshape(T, k * k), i64(re))
+
+    def _transform(self, p, account, rows, act, coff, members, rot, hdiag=None, contrib=None):
+        C = self.C
+        i32 = lambda x: x.to(torch.int32).contiguous()
+        ids, col = i32(rows.ids), i32(rows.col)
+        rc, rk, ri, el = i32(rot.cluster), i32(rot.kk), i32(rot.idx.reshape(-1)), i32(rot.elim)
+        O = rot.O.reshape(-1).contiguous()
+        m32 = i32(members)
+        nr, nz = C.c_int64(), C.c_int64()
+        self.pm._check(self.L.pmmf_shard_transform(
+            self.h, p, account, rows.count, self._p(ids), rows.rowptr.contiguous().data_ptr(),
+            self._p(col), self._p(rows.val.contiguous()), act.numel(), coff.numel() - 1,
+            coff.data_ptr(), m32.data_ptr(), rc.numel(), self._p(rc), self._p(rk), self._p(ri),
+            self._p(O), self._p(el), self._p(hdiag), self._p(contrib), C.byref(nr), C.byref(nz),
+            self._s()))
+        oi = torch.empty(nr.value, dtype=torch.int32, device=self.device)
+        orp = torch.empty(nr.value + 1, dtype=torch.int64, device=self.device)
+        oc = torch.empty(nz.value, dtype=torch.int32, device=self.device)
+        ov = torch.empty(nz.value, dtype=torch.float64, device=self.device)
+        self.pm._check(self.L.pmmf_shard_result(self.h, self._p(oi), orp.data_ptr(), self._p(oc),
+                                                 self._p(ov), self._s()))
+        torch.cuda.current_stream(self.device).synchronize()
+        return Rows(oi.to(torch.int64), orp, oc.to(torch.int64), ov)
+
+    def pass1(self, p, rows, act, coff, members, roff, rot):
+        V = self._transform(p, 0, rows, act, coff, members, rot)
+        # the rows of W = V^T, parts from this rank's rows: entry (x, y) of V
+        # becomes entry (y, x) of W; rows by y, entries by x
+        x = torch.repeat_interleave(V.ids, V.rowptr[1:] - V.rowptr[:-1])
+        order = torch.sort(V.col * (self.n + 1) + x).indices
+        y, x, v = V.col[order], x[order], V.val[order]
+        uid, cnt = torch.unique_consecutive(y, return_counts=True)
+        rp = torch.zeros(uid.numel() + 1, dtype=torch.int64, device=self.device)
+        rp[1:] = torch.cumsum(cnt, 0)
+        return Rows(uid, rp, x, v)
+
+    def pass2(self, p, wrows, act, coff, members, roff, rot):
+        hd = torch.zeros(self.n, dtype=torch.float64, device=self.device)
+        contrib = torch.zeros(1, dtype=torch.float64, device=self.device)
+        out = self._transform(p, 1, wrows, act, coff, members, rot, hd, contrib)
+        el = torch.zeros(self.n, dtype=torch.bool, device=self.device)
+        el[rot.elim] = True
+        h_ids = wrows.ids[el[wrows.ids]]
+        return out, h_ids, hd[h_ids], float(contrib.item())
+
+    def sumsq(self, rows):
+        C = self.C
+        out = C.c_double()
+        v = rows.val.contiguous()
+        self.pm._check(self.L.pmmf_shard_sumsq(self._p(v), v.numel(), C.byref(out), self._s()))
+        return float(out.value)
