@@ -452,14 +452,19 @@ pmmf_status pmmf_get_stage_matrix(const pmmf_handle *f, int p, int64_t *rowptr_n
  * update's kernel: 1 = one warp per row running every rotation level of the
  * segment's cluster (the default), 2 = one thread per row, applying to each
  * row segment only the rotations that reach its pattern (clusters of up to
- * 1,024 coordinates); both give the same bits).  A value
+ * 1,024 coordinates); both give the same bits), PMMF_TUNE_DENSE_TILES (the
+ * dense update: 1 = the block in cluster order moved in TMA tiles, each CTA
+ * staging one cluster's rotations (the default; clusters whose tiles do not
+ * fit shared memory fall back to 2), 2 = one CTA per row applying every
+ * cluster's rotations; both give the same bits).  A value
  * applies to launches whose largest cluster has at most max_size coordinates
  * and no smaller bucket matches; shared-memory limits still halve the row and
  * Gram warps when needed.  Process wide; INVALID_ARG for an unknown param or
  * a value outside 1..32 (outside {8, 16} for the search; any positive value for
  * the reach threshold). */
 enum { PMMF_TUNE_ROWS_WARPS = 0, PMMF_TUNE_GRAM_WARPS = 1, PMMF_TUNE_SELECT_WARPS = 2,
-       PMMF_TUNE_PASS1_ESTIMATE = 3, PMMF_TUNE_REACH_CLUSTERS = 4, PMMF_TUNE_ROWS_KERNEL = 5 };
+       PMMF_TUNE_PASS1_ESTIMATE = 3, PMMF_TUNE_REACH_CLUSTERS = 4, PMMF_TUNE_ROWS_KERNEL = 5,
+       PMMF_TUNE_DENSE_TILES = 6 };
 pmmf_status pmmf_set_tuning(int param, int64_t max_size, int value);
 void pmmf_clear_tuning(void);
 

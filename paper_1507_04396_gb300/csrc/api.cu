@@ -706,6 +706,8 @@ pmmf_status factor_dense_impl(const pmmf_matrix *A, const pmmf_params *prm, pmmf
             PMMF_CUDA_TRY(cudaStreamSynchronize(st));
             if (hs & ST_NOT_CONVERGED)
                 return fail(PMMF_ERR_NOT_CONVERGED, "k x k Jacobi did not converge in 32 sweeps");
+            if (hs & ST_TIMEOUT)
+                return fail(PMMF_ERR_TIMEOUT, "dense update: a tile copy did not complete");
             for (int32_t v : nl) nlv = std::max(nlv, v);
             S.max_levels = nlv;
         }
@@ -714,8 +716,14 @@ pmmf_status factor_dense_impl(const pmmf_matrix *A, const pmmf_params *prm, pmmf
         DBuf<double> Dn;
         DBuf<int32_t> nact;
         int64_t s2 = 0;
-        PMMF_TRY(dense_update(D, s, lv, act.p, elimflag.p, p, h->hdiag.p, contribs.p + (p - 1), Dn,
-                              nact, s2, st));
+        bool tiled = false;
+        if (tuned(TUNE_DENSE_TILES, S.cmax, 1) == 1)
+            PMMF_TRY(dense_update_tiles(D, s, S.cls, hc, S.rot, pos.p, act.p, elimflag.p, p,
+                                        h->hdiag.p, contribs.p + (p - 1), Dn, nact, s2, status.p, st,
+                                        &tiled));
+        if (!tiled)
+            PMMF_TRY(dense_update(D, s, lv, act.p, elimflag.p, p, h->hdiag.p, contribs.p + (p - 1), Dn,
+                                  nact, s2, st));
         PMMF_CUDA_TRY(cudaMemsetAsync(pos.p, 0xFF, sizeof(int32_t) * (size_t)n, st));
         PMMF_TRY(set_positions(nact.p, s2, pos.p, st));
         s = s2;
@@ -744,7 +752,10 @@ pmmf_status factor_dense_impl(const pmmf_matrix *A, const pmmf_params *prm, pmmf
     std::vector<double> hcb((size_t)p + 1, 0.0);
     if (p > 0)
         PMMF_CUDA_TRY(cudaMemcpyAsync(hcb.data(), contribs.p, sizeof(double) * (size_t)p, cudaMemcpyDeviceToHost, st));
+    unsigned hst = 0;
+    PMMF_CUDA_TRY(cudaMemcpyAsync(&hst, status.p, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
     PMMF_CUDA_TRY(cudaStreamSynchronize(st));
+    if (hst & ST_TIMEOUT) return fail(PMMF_ERR_TIMEOUT, "dense update: a tile copy did not complete");
     double tot = 0.0;
     for (int64_t i = 0; i < p; ++i) {
         h->st[i].contrib = hcb[i];

@@ -62,7 +62,7 @@ inline unsigned grid_for(int64_t items, int per_block, int64_t cap = 152 * 64) {
 // smallest bucket whose bound is >= size, else fallback.
 enum TuneParam : int {
     TUNE_ROWS_WARPS = 0, TUNE_GRAM_WARPS = 1, TUNE_SELECT_WARPS = 2, TUNE_PASS1_ESTIMATE = 3,
-    TUNE_REACH_CLUSTERS = 4, TUNE_ROWS_KERNEL = 5, TUNE_COUNT = 6
+    TUNE_REACH_CLUSTERS = 4, TUNE_ROWS_KERNEL = 5, TUNE_DENSE_TILES = 6, TUNE_COUNT = 7
 };
 int tuned(int param, int64_t size, int fallback);
 
@@ -88,6 +88,7 @@ enum : unsigned {
     ST_CLUSTER_TOO_BIG = 32u,
     ST_NOT_CONVERGED = 64u,
     ST_BAD_LABEL = 128u,
+    ST_TIMEOUT = 256u,        // a kernel's bounded wait ran out
 };
 
 // ---------------------------------------------------------------- rotations

@@ -9,6 +9,11 @@
 //             (all clusters at once, one dependency level after another, a
 //             rotation with two zero inputs skipped), a transpose, and again
 //   account   residual of the eliminated coordinates, H diagonal, compaction
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+#include <algorithm>
+
 #include "dense.cuh"
 
 namespace pmmf {
@@ -271,6 +276,274 @@ __global__ void k_map_cols(int32_t *col, int64_t nnz, const int32_t *act) {
         col[q] = act[col[q]];
 }
 
+// ---------------------------------------------------------------- cluster-ordered tiles
+
+// The blocked update in the layout of the stage's clusters: the columns of
+// the active block (and, after a transpose that also reorders, its rows) are
+// permuted so that every cluster's coordinates are contiguous, each cluster's
+// run padded to a multiple of TILE_W columns (128 bytes).  A cluster's
+// rotations then act on one contiguous run of every row, so a CTA takes one
+// cluster and a group of rows: it stages the cluster's level-ordered
+// rotations in shared memory once, and moves RB-row tiles of the run in and
+// out with TMA tensor copies (boxes of RB rows x TILE_W columns) on a
+// double-buffered mbarrier pipeline, applying the rotations level by level
+// (one task per (row, rotation) pair of a level).  Per row the rotations of
+// a cluster are applied in level order, as in k_dense_rows, so the bits are
+// the same.
+constexpr int TILE_W = 16;
+
+// padded cluster-ordered position of every active position (cp), and the
+// active position of every padded position (rowof, -1 for padding; set to -1
+// beforehand).  One CTA per cluster.
+__global__ void k_cluster_positions(const int64_t *coff, const int32_t *members, const int32_t *pos,
+                                    const int64_t *poff, int32_t *cp, int32_t *rowof) {
+    const int64_t u = blockIdx.x;
+    for (int64_t j = coff[u] + threadIdx.x; j < coff[u + 1]; j += blockDim.x) {
+        const int32_t r = pos[members[j]];
+        const int64_t a = poff[u] + (j - coff[u]);
+        cp[r] = (int32_t)a;
+        rowof[a] = r;
+    }
+}
+
+// Dc[r][a] = D[r][rowof[a]] (0 on padding), r < s, a < S.
+__global__ void k_gather_cols(const double *D, int64_t s, const int32_t *rowof, int64_t S, double *Dc) {
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < s * S;
+         q += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t r = q / S, a = q - r * S;
+        const int32_t j = rowof[a];
+        Dc[q] = j >= 0 ? D[r * s + j] : 0.0;
+    }
+}
+
+// T[a][b] = Dc[rowof[b]][a] (0 where b is padding): the transpose with the
+// rows taken in cluster order; T is S x S.
+__global__ void k_transpose_perm(const double *Dc, int64_t S, const int32_t *rowof, double *T) {
+    __shared__ double t[32][33];
+    const int64_t a0 = blockIdx.x * 32, b0 = blockIdx.y * 32;
+    for (int j = threadIdx.y; j < 32; j += blockDim.y) {
+        const int64_t b = b0 + j, a = a0 + threadIdx.x;
+        double v = 0.0;
+        if (b < S && a < S) {
+            const int32_t r = rowof[b];
+            if (r >= 0) v = Dc[(int64_t)r * S + a];
+        }
+        t[j][threadIdx.x] = v;
+    }
+    __syncthreads();
+    for (int j = threadIdx.y; j < 32; j += blockDim.y) {
+        const int64_t a = a0 + j, b = b0 + threadIdx.x;
+        if (a < S && b < S) T[a * S + b] = t[threadIdx.x][j];
+    }
+}
+
+struct TileRot {
+    int K;
+    const int64_t *roff;
+    const int32_t *lvl_off, *nlev;
+    const Rot2 *lvlrot;
+    const int32_t *lvlidx, *kkv, *kidx;
+    const double *kO;
+};
+
+__device__ __forceinline__ uint32_t smem_addr(const void *p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+// Bounded wait for phase `parity` of an mbarrier; false on timeout.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
+    const uint32_t a = smem_addr(bar);
+    for (int it = 0; it < (1 << 24); ++it) {
+        uint32_t done;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(done)
+            : "r"(a), "r"(parity)
+            : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+
+// Element (row i, column c) of a tile: boxes of RB x TILE_W, box-major.
+template <int RB>
+__device__ __forceinline__ double &tile_at(double *buf, int i, int c) {
+    return buf[(c / TILE_W) * (RB * TILE_W) + i * TILE_W + (c % TILE_W)];
+}
+
+// One CTA per (cluster, row group); see above.  rows: the rows of the tensor
+// (s for the column-permuted block, S for the transposed one).
+template <int RB>
+__global__ void __launch_bounds__(256)
+k_dense_tiles(const __grid_constant__ CUtensorMap tmap, int64_t rows, const int64_t *coff,
+              const int64_t *poff, TileRot R, int64_t rows_per_group, unsigned *status) {
+    extern __shared__ __align__(1024) unsigned char tsm[];
+    const int64_t u = blockIdx.x;
+    const int tid = threadIdx.x;
+    const int64_t r_begin = blockIdx.y * rows_per_group;
+    const int64_t r_end = min(rows, r_begin + rows_per_group);
+    if (r_begin >= r_end) return;
+    const int nblk = (int)((r_end - r_begin + RB - 1) / RB);
+    const int nch = (int)((poff[u + 1] - poff[u]) / TILE_W);
+    const int64_t x0 = poff[u];
+    const int64_t rr0 = R.roff[u];
+    const int32_t *lo = R.lvl_off + rr0 + u;
+    const int nl = R.nlev[u];
+    const int64_t q0 = lo[0];
+    const int ne = (int)(lo[nl] - q0);
+    const int K = R.K;
+    // layout: two tile buffers, the level offsets, the rotations, two mbarriers
+    const size_t tbytes = (size_t)nch * RB * TILE_W * sizeof(double);
+    double *buf0 = (double *)tsm;
+    double *buf1 = (double *)(tsm + tbytes);
+    int32_t *lvo = (int32_t *)(tsm + 2 * tbytes);
+    unsigned char *rt = (unsigned char *)(lvo + ((nl + 2) & ~1));
+    // k = 2: Rot2 per slot; k >= 3: kk, K local indices and K*K block per slot
+    Rot2 *r2 = (Rot2 *)rt;
+    // bytes per k-point slot: kk and the K indices, rounded up to 8, then
+    // the K*K block (so every slot's doubles are 8-aligned)
+    const int kstride = ((4 + 4 * K + 7) & ~7) + 8 * K * K;
+    uint64_t *bar = (uint64_t *)(rt + (size_t)ne * (K <= 2 ? sizeof(Rot2) : (size_t)kstride));
+    for (int L = tid; L <= nl; L += blockDim.x) lvo[L] = (int32_t)(lo[L] - q0);
+    if (K <= 2) {
+        for (int q = tid; q < ne; q += blockDim.x) r2[q] = R.lvlrot[q0 + q];
+    } else {
+        for (int q = tid; q < ne; q += blockDim.x) {
+            const int64_t t = R.lvlidx[q0 + q];
+            unsigned char *d = rt + (size_t)q * kstride;
+            *(int32_t *)d = R.kkv[t];
+            for (int a = 0; a < K; ++a) ((int32_t *)(d + 4))[a] = R.kidx[t * K + a];
+            double *O = (double *)(d + ((4 + 4 * K + 7) & ~7));
+            for (int a = 0; a < K * K; ++a) O[a] = R.kO[t * K * K + a];
+        }
+    }
+    if (tid == 0) {
+        for (int i = 0; i < 2; ++i)
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&bar[i])) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    const uint32_t txb = (uint32_t)tbytes;
+    auto issue_load = [&](int b, double *dst, uint64_t *mb) {
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(mb)),
+                     "r"(txb) : "memory");
+        const int y = (int)(r_begin + (int64_t)b * RB);
+        for (int k = 0; k < nch; ++k) {
+            const int x = (int)(x0 + (int64_t)k * TILE_W);
+            asm volatile(
+                "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes "
+                "[%0], [%1, {%2, %3}], [%4];" ::"r"(smem_addr(dst + (size_t)k * RB * TILE_W)),
+                "l"(&tmap), "r"(x), "r"(y), "r"(smem_addr(mb))
+                : "memory");
+        }
+    };
+    auto issue_store = [&](int b, double *src) {
+        const int y = (int)(r_begin + (int64_t)b * RB);
+        for (int k = 0; k < nch; ++k) {
+            const int x = (int)(x0 + (int64_t)k * TILE_W);
+            asm volatile(
+                "cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%1, %2}], [%3];" ::"l"(&tmap),
+                "r"(x), "r"(y), "r"(smem_addr(src + (size_t)k * RB * TILE_W))
+                : "memory");
+        }
+        asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+    };
+    if (tid == 0) issue_load(0, buf0, &bar[0]);
+    bool ok = true;
+    for (int b = 0; b < nblk && ok; ++b) {
+        double *cur = (b & 1) ? buf1 : buf0;
+        if (tid == 0 && b + 1 < nblk) {
+            // the other buffer's last store has read its data
+            asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+            issue_load(b + 1, (b & 1) ? buf0 : buf1, &bar[(b + 1) & 1]);
+        }
+        if (!mbar_wait(&bar[b & 1], (uint32_t)((b >> 1) & 1))) {
+            if (tid == 0) atomicOr(status, ST_TIMEOUT);
+            ok = false;
+        }
+        if (__syncthreads_or(!ok)) {
+            if (tid == 0) {
+                // the loads of blocks b and b + 1 may still be in flight: give
+                // them time to land (bounded) before the CTA's shared memory
+                // is released
+                mbar_wait(&bar[b & 1], (uint32_t)((b >> 1) & 1));
+                if (b + 1 < nblk) mbar_wait(&bar[(b + 1) & 1], (uint32_t)(((b + 1) >> 1) & 1));
+            }
+            ok = false;
+            break;
+        }
+        const int64_t left = r_end - (r_begin + (int64_t)b * RB);
+        const int nrows = (int)(left < RB ? left : RB);
+        for (int L = 0; L < nl; ++L) {
+            const int s0 = lvo[L], ns = lvo[L + 1] - s0;
+            const int tasks = nrows * ns;
+            for (int q = tid; q < tasks; q += blockDim.x) {
+                const int i = q / ns, slot = s0 + (q - i * ns);
+                if (K <= 2) {
+                    const Rot2 t = r2[slot];
+                    double &ra = tile_at<RB>(cur, i, t.li);
+                    double &rb = tile_at<RB>(cur, i, t.lj);
+                    const double a = ra, bb = rb;
+                    if (nonzero_bits(a) || nonzero_bits(bb)) {
+                        double na, nb;
+                        rot_pair(t.c, t.s, a, bb, na, nb);
+                        ra = na;
+                        rb = nb;
+                    }
+                } else {
+                    const unsigned char *d = rt + (size_t)slot * kstride;
+                    const int kk = *(const int32_t *)d;
+                    const int32_t *P = (const int32_t *)(d + 4);
+                    const double *O = (const double *)(d + ((4 + 4 * K + 7) & ~7));
+                    double in[8];
+                    bool nz = false;
+                    for (int a = 0; a < kk; ++a) {
+                        in[a] = tile_at<RB>(cur, i, P[a]);
+                        nz |= nonzero_bits(in[a]);
+                    }
+                    if (nz) {
+                        double out[8];
+                        for (int a = 0; a < kk; ++a) out[a] = rot_row(O, kk, a, in);
+                        for (int a = 0; a < kk; ++a) tile_at<RB>(cur, i, P[a]) = out[a];
+                    }
+                }
+            }
+            __syncthreads();
+        }
+        // the threads' writes before the TMA store reads the tile
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncthreads();
+        if (tid == 0) issue_store(b, cur);
+    }
+    if (tid == 0) asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
+    __syncthreads();
+}
+
+// Per padded position: eliminated in this stage (from the flags of the active
+// positions; 0 on padding), and its global id (0 on padding).
+__global__ void k_pad_flags(const int32_t *cp, const int32_t *act, int64_t s, const int32_t *el,
+                            int32_t *elp, int32_t *actp) {
+    for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < s;
+         r += (int64_t)gridDim.x * blockDim.x) {
+        elp[cp[r]] = el[r];
+        actp[cp[r]] = act[r];
+    }
+}
+
+// Survivors in active order: their padded positions and global ids.
+__global__ void k_pad_survivors(const int32_t *act, int64_t s, const int32_t *keep,
+                                const int64_t *newpos, const int32_t *cp, int32_t *sidx,
+                                int32_t *nact) {
+    for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < s;
+         r += (int64_t)gridDim.x * blockDim.x)
+        if (keep[r]) {
+            sidx[newpos[r]] = cp[r];
+            nact[newpos[r]] = act[r];
+        }
+}
+
 }  // namespace
 
 pmmf_status dense_load(const double *A, int64_t n, int64_t ld, DBuf<double> &D, unsigned *status,
@@ -392,6 +665,182 @@ pmmf_status dense_update(DBuf<double> &D, int64_t s, const DenseLevels &lv, cons
     PMMF_TRY(Dnext.alloc(std::max<int64_t>(s2 * s2, 1), st));
     k_dense_compact<<<grid_for(s2 * s2, 256), 256, 0, st>>>(T.p, s, sidx.p, s2, Dnext.p);
     return launched("dense_compact");
+}
+
+namespace {
+
+// cuTensorMapEncodeTiled from the driver (looked up once).
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static bool tried = false;
+    if (!tried) {
+        tried = true;
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                             &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
+        else
+            cudaGetLastError();
+    }
+    return fn;
+}
+
+// A rows x cols FP64 row-major block as a tensor map with RB x TILE_W boxes.
+pmmf_status tile_map(CUtensorMap *m, double *base, int64_t rows, int64_t cols, int rb) {
+    auto fn = encode_fn();
+    if (!fn) {
+        set_error("cuTensorMapEncodeTiled is not available");
+        return PMMF_ERR_CUDA;
+    }
+    cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+    cuuint64_t strides[1] = {(cuuint64_t)cols * sizeof(double)};
+    cuuint32_t box[2] = {(cuuint32_t)TILE_W, (cuuint32_t)rb};
+    cuuint32_t es[2] = {1, 1};
+    CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 2, base, dims, strides, box, es,
+                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                    CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) {
+        set_error("cuTensorMapEncodeTiled failed");
+        return PMMF_ERR_CUDA;
+    }
+    return PMMF_OK;
+}
+
+template <int RB>
+pmmf_status launch_tiles(const CUtensorMap &map, int64_t rows, int64_t m, const int64_t *coff,
+                         const int64_t *poff, const TileRot &R, size_t smem, unsigned *status,
+                         cudaStream_t st) {
+    int dev = 0, nsm = 152;
+    if (cudaGetDevice(&dev) == cudaSuccess)
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    const int64_t groups = std::max<int64_t>(1, (2 * (int64_t)nsm + m - 1) / m);
+    int64_t rpg = (rows + groups - 1) / groups;
+    rpg = (rpg + RB - 1) / RB * RB;
+    const int64_t gy = (rows + rpg - 1) / rpg;
+    PMMF_CUDA_TRY(cudaFuncSetAttribute(k_dense_tiles<RB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem));
+    k_dense_tiles<RB><<<dim3((unsigned)m, (unsigned)gy), 256, smem, st>>>(map, rows, coff, poff, R, rpg,
+                                                                       status);
+    return launched("dense_tiles");
+}
+
+}  // namespace
+
+pmmf_status dense_update_tiles(DBuf<double> &D, int64_t s, const StageClusters &cls,
+                               const std::vector<int64_t> &hc, const StageRotations &rot,
+                               const int32_t *pos, const int32_t *act, const int32_t *elimflag,
+                               int64_t stage, double *hdiag, double *contrib, DBuf<double> &Dnext,
+                               DBuf<int32_t> &nact, int64_t &s2, unsigned *status, cudaStream_t st,
+                               bool *used) {
+    *used = false;
+    const int64_t m = cls.m;
+    const int K = rot.K;
+    std::vector<int64_t> poff((size_t)m + 1, 0), roff;
+    std::vector<int32_t> nlev;
+    roff.resize((size_t)m + 1);
+    nlev.resize((size_t)m);
+    PMMF_CUDA_TRY(cudaMemcpyAsync(roff.data(), rot.roff.p, sizeof(int64_t) * (size_t)(m + 1), cudaMemcpyDeviceToHost, st));
+    PMMF_CUDA_TRY(cudaMemcpyAsync(nlev.data(), rot.nlev.p, sizeof(int32_t) * (size_t)m, cudaMemcpyDeviceToHost, st));
+    PMMF_CUDA_TRY(cudaStreamSynchronize(st));
+    int64_t cpad_max = 0, e_max = 0;
+    int nl_max = 0;
+    for (int64_t u = 0; u < m; ++u) {
+        const int64_t c = hc[u + 1] - hc[u];
+        const int64_t cp = (c + TILE_W - 1) / TILE_W * TILE_W;
+        poff[u + 1] = poff[u] + cp;
+        cpad_max = std::max(cpad_max, cp);
+        e_max = std::max(e_max, roff[u + 1] - roff[u]);
+        nl_max = std::max(nl_max, nlev[u]);
+    }
+    const int64_t S = poff[m];
+    const size_t kstride = (size_t)((4 + 4 * K + 7) & ~7) + 8 * (size_t)K * K;
+    const size_t rbytes = (size_t)e_max * (K <= 2 ? sizeof(Rot2) : kstride);
+    const size_t fixed = 4 * (size_t)((nl_max + 2) & ~1) + rbytes + 64;
+    int rb = 0;
+    for (int cand : {16, 8, 4}) {
+        const size_t need = 2 * (size_t)cpad_max * cand * sizeof(double) + fixed;
+        if (need <= 200 * 1024) {
+            rb = cand;
+            break;
+        }
+    }
+    if (rb == 0 || S >= INT32_MAX || s >= INT32_MAX || !encode_fn()) return PMMF_OK;   // caller falls back
+    const size_t smem = 2 * (size_t)cpad_max * rb * sizeof(double) + fixed;
+    DBuf<int64_t> dpoff;
+    PMMF_TRY(dpoff.alloc(m + 1, st));
+    PMMF_CUDA_TRY(cudaMemcpyAsync(dpoff.p, poff.data(), sizeof(int64_t) * poff.size(), cudaMemcpyHostToDevice, st));
+    DBuf<int32_t> cp, rowof;
+    PMMF_TRY(cp.alloc(std::max<int64_t>(s, 1), st));
+    PMMF_TRY(rowof.alloc(S, st));
+    PMMF_CUDA_TRY(cudaMemsetAsync(rowof.p, 0xFF, sizeof(int32_t) * (size_t)S, st));
+    k_cluster_positions<<<(unsigned)m, 128, 0, st>>>(cls.coff.p, cls.members.p, pos, dpoff.p, cp.p,
+                                                     rowof.p);
+    PMMF_TRY(launched("cluster_positions"));
+    // the columns in cluster order
+    DBuf<double> Dc;
+    PMMF_TRY(Dc.alloc(s * S, st));
+    k_gather_cols<<<grid_for(s * S, 256), 256, 0, st>>>(D.p, s, rowof.p, S, Dc.p);
+    PMMF_TRY(launched("gather_cols"));
+    TileRot R;
+    R.K = K;
+    R.roff = rot.roff.p;
+    R.lvl_off = rot.lvl_off.p;
+    R.nlev = rot.nlev.p;
+    R.lvlrot = rot.lvl.p;
+    R.lvlidx = rot.lvlidx.p;
+    R.kkv = rot.kk.p;
+    R.kidx = rot.kidx.p;
+    R.kO = rot.kO.p;
+    auto tiles = [&](const CUtensorMap &map, int64_t rows) -> pmmf_status {
+        if (rb == 16) return launch_tiles<16>(map, rows, m, cls.coff.p, dpoff.p, R, smem, status, st);
+        if (rb == 8) return launch_tiles<8>(map, rows, m, cls.coff.p, dpoff.p, R, smem, status, st);
+        return launch_tiles<4>(map, rows, m, cls.coff.p, dpoff.p, R, smem, status, st);
+    };
+    CUtensorMap m1, m2;
+    PMMF_TRY(tile_map(&m1, Dc.p, s, S, rb));
+    // pass 1: every row of A Q^T
+    prof_begin(KF_ROWS, st);
+    PMMF_TRY(tiles(m1, s));
+    prof_end(KF_ROWS, st, 16.0 * (double)s * (double)S, 0.0);
+    DBuf<double> T;
+    PMMF_TRY(T.alloc(S * S, st));
+    dim3 tg((unsigned)((S + 31) / 32), (unsigned)((S + 31) / 32)), tb(32, 8);
+    k_transpose_perm<<<tg, tb, 0, st>>>(Dc.p, S, rowof.p, T.p);
+    PMMF_TRY(launched("transpose_perm"));
+    Dc.reset();
+    PMMF_TRY(tile_map(&m2, T.p, S, S, rb));
+    // pass 2: every row of the transpose
+    prof_begin(KF_ROWS, st);
+    PMMF_TRY(tiles(m2, S));
+    prof_end(KF_ROWS, st, 16.0 * (double)S * (double)S, 0.0);
+    // accounting on the padded layout, survivors in active order
+    DBuf<int32_t> el, keep, elp, actp, sidx;
+    DBuf<int64_t> newpos;
+    PMMF_TRY(el.alloc(s, st));
+    PMMF_TRY(keep.alloc(s, st));
+    PMMF_TRY(elp.zeros(S, st));
+    PMMF_TRY(actp.zeros(S, st));
+    PMMF_TRY(newpos.alloc(s + 1, st));
+    k_dense_flags<<<grid_for(s, 256), 256, 0, st>>>(act, s, elimflag, (int32_t)stage, el.p, keep.p);
+    PMMF_TRY(launched("dense_flags"));
+    k_pad_flags<<<grid_for(s, 256), 256, 0, st>>>(cp.p, act, s, el.p, elp.p, actp.p);
+    PMMF_TRY(launched("pad_flags"));
+    k_dense_account<<<(unsigned)S, 256, 0, st>>>(T.p, S, elp.p, actp.p, hdiag, contrib);
+    PMMF_TRY(launched("dense_account"));
+    PMMF_TRY(scan_i32_to_i64(keep.p, newpos.p, s, st));
+    PMMF_CUDA_TRY(cudaMemcpyAsync(&s2, newpos.p + s, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+    PMMF_CUDA_TRY(cudaStreamSynchronize(st));
+    PMMF_TRY(sidx.alloc(std::max<int64_t>(s2, 1), st));
+    PMMF_TRY(nact.alloc(std::max<int64_t>(s2, 1), st));
+    k_pad_survivors<<<grid_for(s, 256), 256, 0, st>>>(act, s, keep.p, newpos.p, cp.p, sidx.p, nact.p);
+    PMMF_TRY(launched("pad_survivors"));
+    PMMF_TRY(Dnext.alloc(std::max<int64_t>(s2 * s2, 1), st));
+    k_dense_compact<<<grid_for(s2 * s2, 256), 256, 0, st>>>(T.p, S, sidx.p, s2, Dnext.p);
+    PMMF_TRY(launched("dense_compact"));
+    *used = true;
+    return PMMF_OK;
 }
 
 pmmf_status dense_nonzeros(const double *D, int64_t cnt, int64_t *out, cudaStream_t st) {

@@ -45,6 +45,16 @@ pmmf_status dense_levels(const StageClusters &cls, const StageRotations &rot, co
 pmmf_status dense_update(DBuf<double> &D, int64_t s, const DenseLevels &lv, const int32_t *act,
                          const int32_t *elimflag, int64_t stage, double *hdiag, double *contrib,
                          DBuf<double> &Dnext, DBuf<int32_t> &nact, int64_t &s2, cudaStream_t st);
+// The same update with the block laid out in padded cluster order and moved
+// in tiles by TMA (the rotations staged once per CTA).  *used = false (and
+// nothing done) when a cluster's tiles do not fit shared memory or the tensor
+// map call is unavailable; the caller then runs dense_update.
+pmmf_status dense_update_tiles(DBuf<double> &D, int64_t s, const StageClusters &cls,
+                               const std::vector<int64_t> &hc, const StageRotations &rot,
+                               const int32_t *pos, const int32_t *act, const int32_t *elimflag,
+                               int64_t stage, double *hdiag, double *contrib, DBuf<double> &Dnext,
+                               DBuf<int32_t> &nact, int64_t &s2, unsigned *status, cudaStream_t st,
+                               bool *used);
 // Number of entries that are not +-0.
 pmmf_status dense_nonzeros(const double *D, int64_t cnt, int64_t *out, cudaStream_t st);
 pmmf_status dense_core(const double *D, int64_t s, const int32_t *act, double *core, double *hdiag,

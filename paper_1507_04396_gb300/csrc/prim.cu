@@ -723,7 +723,8 @@ pmmf_status pmmf_set_tuning(int param, int64_t max_size, int value) {
     if (param < 0 || param >= TUNE_COUNT || max_size < 1 || value < 1 ||
         (value > 32 && param != TUNE_REACH_CLUSTERS) ||
         (param == TUNE_SELECT_WARPS && value != 8 && value != 16) ||
-        (param == TUNE_ROWS_KERNEL && value != 1 && value != 2)) {
+        (param == TUNE_ROWS_KERNEL && value != 1 && value != 2) ||
+        (param == TUNE_DENSE_TILES && value != 1 && value != 2)) {
         set_error("pmmf_set_tuning: unknown parameter or value out of range");
         return PMMF_ERR_INVALID_ARG;
     }

@@ -64,3 +64,22 @@ def test_dense_rbf_c3_shape():
     sizes = np.diff(o.stages[0].offsets)
     assert len(sizes) == 8 and sizes.max() > 400, sizes
     assert_same_factorization(g, o)
+
+
+@pytest.mark.parametrize("kernel", [1, 2])
+@pytest.mark.parametrize("k", [2, 3])
+def test_dense_update_kernels_agree_with_oracle(kernel, k):
+    """The dense update in cluster-ordered TMA tiles (1, the default) and one
+    CTA per row (2), each forced: bit-identical to the oracle, with ragged
+    k-means clusters (runs padded to 16 columns) and a row count that leaves
+    partial tiles."""
+    pm = gpu_lib()
+    L = pm.load()
+    a = I.rbf_mixture(1000, components=7, seed=8)
+    try:
+        assert L.pmmf_set_tuning(pm.TUNE_PARAMS["dense_tiles"], 1 << 30, kernel) == 0
+        g, o = _both(a, a.coords, k=k, eta=0.5, cluster_size=90, core_size=37, seed=4)
+        assert_same_factorization(g, o)
+    finally:
+        L.pmmf_clear_tuning()
+        pm.apply_tuning(pm.TUNING_PATH)
