@@ -135,7 +135,9 @@ __global__ void k_local_block(const double *D, int64_t s, const int32_t *pos, co
 //   C c0..c3 = (g, 2t), (g, 2t+1), (g+8, 2t), (g+8, 2t+1);  g = lane / 4, t = lane % 4.
 constexpr int TG = 64;      // output tile
 constexpr int TKB = 32;     // k chunk staged in shared memory (elements)
-constexpr int KFLUSH = 128; // FP32 accumulation length before the FP64 sum
+constexpr int KFLUSH = 16;  // FP32 accumulation length before the FP64 sum (a
+                            // multiple of the MMA's k step): the FP32 part of the
+                            // certified bound grows with it, the FP64 adds shrink
 
 __device__ __forceinline__ void mma_bf16(float *d, const uint32_t *a, const uint32_t *b) {
     asm volatile(
@@ -228,17 +230,21 @@ k_tc_gram(const void *XH, const void *XL, int64_t sp /* padded row length */,
                         mma_tf32(acc[i][j], ah[i], bh[j]);
                     }
                 }
+            // every KFLUSH terms the FP32 sums move into the FP64 ones
+            if (((kk + 1) * KSTEP) % KFLUSH == 0) {
+                for (int i = 0; i < 2; ++i)
+                    for (int j = 0; j < 4; ++j)
+                        for (int q = 0; q < 4; ++q) {
+                            dacc[i][j][q] = __dadd_rn(dacc[i][j][q], (double)acc[i][j][q]);
+                            acc[i][j][q] = 0.0f;
+                        }
+            }
         }
         __syncthreads();
-        if ((k0 + TKB) % KFLUSH == 0 || k0 + TKB >= sp) {
-            for (int i = 0; i < 2; ++i)
-                for (int j = 0; j < 4; ++j)
-                    for (int q = 0; q < 4; ++q) {
-                        dacc[i][j][q] = __dadd_rn(dacc[i][j][q], (double)acc[i][j][q]);
-                        acc[i][j][q] = 0.0f;
-                    }
-        }
     }
+    for (int i = 0; i < 2; ++i)
+        for (int j = 0; j < 4; ++j)
+            for (int q = 0; q < 4; ++q) dacc[i][j][q] = __dadd_rn(dacc[i][j][q], (double)acc[i][j][q]);
     float *Gu = G + goff[u];
     for (int i = 0; i < 2; ++i)
         for (int j = 0; j < 4; ++j)
@@ -722,8 +728,8 @@ pmmf_status mixed_stage_select(const DBuf<double> &D, int64_t s, const int32_t *
     // eps, relative to |x||y| per term: the split leaves |x - hi - lo| <= u^2 |x|
     // (u = 2^-11 TF32, 2^-8 BF16), the dropped lo lo^T term is <= u^2 |x||y|,
     // so the three products miss x y by <= 3 u^2 (1 + u) |x||y|; FP32
-    // accumulation of 3 KFLUSH products per chunk (taken at twice the
-    // round-to-nearest bound) and the FP64 sum of the chunks and the final
+    // accumulation of 3 KFLUSH products per chunk of KFLUSH terms (taken at
+    // twice the round-to-nearest bound) and the FP64 sum of the chunks and the final
     // FP32 rounding add the rest; Cauchy-Schwarz turns sum |x||y| into
     // sqrt(G_ii G_jj).  10% margin.
     const double uin = precision == PMMF_PREC_BF16 ? 0x1p-8 : 0x1p-11;
