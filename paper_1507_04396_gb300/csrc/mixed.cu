@@ -16,6 +16,9 @@
 // products of the current rows), the rows themselves are rotated in FP64, and
 // the FP64 diagonal follows the FP64 k x k block.  Only the Gram matrix, its
 // error bound and their rotation are in reduced precision.
+#include <climits>
+
+#include <cooperative_groups.h>
 #include <cuda_bf16.h>
 
 #include <vector>
@@ -26,7 +29,10 @@
 namespace pmmf {
 namespace {
 
+namespace cg = cooperative_groups;
+
 constexpr int MX_THREADS = 512;
+constexpr int PAIRS = 28;            // tuple pairs (k <= 8)
 constexpr int MX_WARPS = MX_THREADS / 32;
 constexpr int SL_MAX = 64;           // shortlists above this are counted as long
 constexpr int DOT_BATCH = 8;
@@ -272,14 +278,14 @@ __device__ __forceinline__ double block_max(double v, double *red) {
     return r;
 }
 
-// Sums of DOT_BATCH dot products of row xi with the rows xs[0..nb) (length s),
-// a fixed reduction order; result in out[0..nb) (all threads see it after the
-// trailing barrier).
-__device__ void block_dots(const double *xi, const double *const *xs, int nb, int64_t s,
-                           double *red, double *out) {
+// Partial dot products of row xi with the rows xs[0..nb) over the columns
+// [r0, r1) (this CTA's slice), reduced over the CTA in a fixed order; thread b
+// < nb returns the b-th sum (others 0).  Ends with a barrier.
+__device__ double slice_dots(const double *xi, const double *const *xs, int nb, int64_t r0,
+                             int64_t r1, double *red) {
     double acc[DOT_BATCH];
     for (int b = 0; b < DOT_BATCH; ++b) acc[b] = 0.0;
-    for (int64_t r = threadIdx.x; r < s; r += MX_THREADS) {
+    for (int64_t r = r0 + threadIdx.x; r < r1; r += MX_THREADS) {
         const double a = xi[r];
         for (int b = 0; b < nb; ++b) acc[b] = __fma_rn(a, xs[b][r], acc[b]);
     }
@@ -289,31 +295,44 @@ __device__ void block_dots(const double *xi, const double *const *xs, int nb, in
         if (lane == 0) red[b * MX_WARPS + w] = v;
     }
     __syncthreads();
-    if (threadIdx.x < (unsigned)nb) {
-        double v = 0.0;
+    double v = 0.0;
+    if (threadIdx.x < (unsigned)nb)
         for (int q = 0; q < MX_WARPS; ++q) v = __dadd_rn(v, red[threadIdx.x * MX_WARPS + q]);
-        out[threadIdx.x] = v;
-    }
     __syncthreads();
+    return v;
 }
 
+// The search of one cluster by CL CTAs (a thread-block cluster for CL > 1):
+// every CTA runs the step's decisions (scores, shortlist, angles, bookkeeping)
+// on its own copy of G~, B and M, with identical inputs and so identical
+// results, while the long FP64 work is split by columns of the FP64 rows:
+// CTA r computes the shortlist's dot products over its slice of the s columns
+// (the partial sums go to every CTA's shared memory, double-buffered by step
+// parity, and are added in rank order after one cluster barrier) and rotates
+// its slice of the rows.  Only CTA 0 writes the results.
+template <int CL>
 __global__ void __launch_bounds__(MX_THREADS)
 k_select_mixed(int64_t s, const int64_t *coff, const int32_t *members, const int64_t *goff,
-               double *Xs, float *Gt, float *Bd, double *Mall, const double *gdiag0,
-               const int64_t *roff, uint64_t seed, int64_t stage, int K, double eps, int32_t *kidx,
-               int32_t *kkv, int32_t *kel, int32_t *klvl, double *kO, int32_t *lvlidx,
-               int32_t *lvl_off, int32_t *nlev, int32_t *elimflag, unsigned long long *stats,
-               unsigned *status) {
+               int64_t gcopy, double *Xs, float *Gt, float *Bd, double *Mall,
+               const double *gdiag0, const int64_t *roff, uint64_t seed, int64_t stage, int K,
+               double eps, int32_t *kidx, int32_t *kkv, int32_t *kel, int32_t *klvl, double *kO,
+               int32_t *lvlidx, int32_t *lvl_off, int32_t *nlev, int32_t *elimflag,
+               unsigned long long *stats, unsigned *status) {
     extern __shared__ double sh[];
-    const int64_t u = blockIdx.x;
+    const int64_t u = blockIdx.x / CL;
+    int rank = 0;
+    if constexpr (CL > 1) rank = (int)cg::this_cluster().block_rank();
+    const bool lead = rank == 0;
     const int64_t base = coff[u];
     const int c = (int)(coff[u + 1] - base);
     const int64_t r0 = roff[u];
     const int e = (int)(roff[u + 1] - r0);
+    // this CTA's columns of the FP64 rows
+    const int64_t cs0 = s * rank / CL, cs1 = s * (rank + 1) / CL;
     double *X = Xs + base * s;
-    float *G = Gt + goff[u];
-    float *B = Bd + goff[u];
-    double *M = Mall + goff[u];
+    float *G = Gt + gcopy * rank + goff[u];
+    float *B = Bd + gcopy * rank + goff[u];
+    double *M = Mall + gcopy * rank + goff[u];
     double *gd = sh;
     double *md = gd + c;
     double *w = md + c;
@@ -325,10 +344,19 @@ k_select_mixed(int64_t s, const int64_t *coff, const int32_t *members, const int
     int32_t *lvl = (int32_t *)(mask + nwords);
     int32_t *lcnt = lvl + c;                    // e + 2
     int32_t *sl = lcnt + e + 2;                 // shortlist, c
+    // partial dot sums from every CTA: [parity][rank][candidate] (c slots),
+    // then the pairs of the tuple [parity][rank][pair] (PAIRS slots)
+    double *pd = (double *)(((uintptr_t)(sl + c) + 15) & ~(uintptr_t)15);
+    double *pd2 = pd + 2 * CL * c;
     __shared__ int s_T[8], s_kk, s_maxlev, s_nsl, s_fall;
-    __shared__ double s_O[64], s_GT[64], s_dots[DOT_BATCH], s_es[SL_MAX + 8];
+    __shared__ double s_O[64], s_GT[64], s_es[SL_MAX + 8];
     __shared__ int s_wcnt[MX_WARPS];
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    // the CTAs of the cluster meet (one CTA: the block barrier)
+    auto csync = [&]() {
+        if constexpr (CL > 1) cg::this_cluster().sync();
+        else __syncthreads();
+    };
 
     for (int a = tid; a < c; a += MX_THREADS) {
         gd[a] = gdiag0[base + a];
@@ -383,13 +411,22 @@ k_select_mixed(int64_t s, const int64_t *coff, const int32_t *members, const int
             mv = block_max(mv, red);
             tau = mv;
             if (a + 1 < kk) {
+                // the lowest index holding the maximum, found by all threads
+                int first = INT_MAX;
+                for (int y = tid; y < c; y += MX_THREADS)
+                    if (lo[y] == mv) {
+                        first = y;
+                        break;
+                    }
+                for (int o = 16; o > 0; o >>= 1) first = min(first, __shfl_xor_sync(0xffffffffu, first, o));
                 __syncthreads();
-                if (tid == 0)
-                    for (int y = 0; y < c; ++y)
-                        if (lo[y] == mv) {
-                            lo[y] = -1.0;
-                            break;
-                        }
+                if (lane == 0) s_wcnt[wid] = first;
+                __syncthreads();
+                if (tid == 0) {
+                    int f = s_wcnt[0];
+                    for (int q = 1; q < MX_WARPS; ++q) f = min(f, s_wcnt[q]);
+                    if (f < c) lo[f] = -1.0;
+                }
                 __syncthreads();
             }
         }
@@ -429,15 +466,30 @@ k_select_mixed(int64_t s, const int64_t *coff, const int32_t *members, const int
             best_y[a] = 0x7fffffff;
             best_g[a] = 0.0;
         }
+        // this CTA's partial sums (its columns) of every shortlisted dot
+        // product, into every CTA's buffer of this step's parity
+        const int par = t & 1;
         for (int q0 = 0; q0 < nsl; q0 += DOT_BATCH) {
             const int nb = min(DOT_BATCH, nsl - q0);
             const double *xs[DOT_BATCH];
             for (int b = 0; b < DOT_BATCH; ++b) xs[b] = X + (int64_t)sl[q0 + (b < nb ? b : 0)] * s;
-            block_dots(X + (int64_t)i * s, xs, nb, s, red, s_dots);
-            // every thread keeps the same running top list
-            for (int b = 0; b < nb; ++b) {
-                const int y = sl[q0 + b];
-                const double gv = s_dots[b];
+            const double v = slice_dots(X + (int64_t)i * s, xs, nb, cs0, cs1, red);
+            if (tid < nb) {
+                const int64_t slot = (int64_t)(par * CL + rank) * c + q0 + tid;
+                if constexpr (CL > 1) {
+                    for (int d = 0; d < CL; ++d) cg::this_cluster().map_shared_rank(pd, d)[slot] = v;
+                } else {
+                    pd[slot] = v;
+                }
+            }
+        }
+        csync();
+        for (int q = 0; q < nsl; ++q) {
+            // the FP64 dot product: the CTAs' partial sums in rank order
+            const int y = sl[q];
+            double gv = pd[(int64_t)(par * CL) * c + q];
+            for (int r = 1; r < CL; ++r) gv = __dadd_rn(gv, pd[(int64_t)(par * CL + r) * c + q]);
+            {
                 const double sc = f64_from_bits(f64_bits(__dmul_rn(gv, w[y])) & F64_ABS);
                 // insert into the top kk-1 (ties to the smaller index)
                 int pos2 = kk - 1;
@@ -454,7 +506,6 @@ k_select_mixed(int64_t s, const int64_t *coff, const int32_t *members, const int
                     best_g[pos2] = gv;
                 }
             }
-            __syncthreads();
         }
         int T[8];
         T[0] = i;
@@ -481,17 +532,36 @@ k_select_mixed(int64_t s, const int64_t *coff, const int32_t *members, const int
                 s_GT[a * kk] = best_g[a - 1];
             }
         }
-        for (int a = 1; a < kk; ++a) {
-            const int nb = kk - 1 - a;
-            if (nb <= 0) continue;
-            const double *xs[DOT_BATCH];
-            for (int b = 0; b < DOT_BATCH; ++b) xs[b] = X + (int64_t)T[a + 1 + (b < nb ? b : 0)] * s;
-            block_dots(X + (int64_t)T[a] * s, xs, nb, s, red, s_dots);
-            if (tid == 0)
-                for (int b = 0; b < nb; ++b) {
-                    s_GT[a * kk + a + 1 + b] = s_dots[b];
-                    s_GT[(a + 1 + b) * kk + a] = s_dots[b];
+        if (kk >= 3) {
+            // the partners' pairs (a < b, both >= 1): partial sums as above
+            int pi = 0;
+            for (int a = 1; a < kk; ++a) {
+                const int nb = kk - 1 - a;
+                if (nb <= 0) continue;
+                const double *xs[DOT_BATCH];
+                for (int b = 0; b < DOT_BATCH; ++b) xs[b] = X + (int64_t)T[a + 1 + (b < nb ? b : 0)] * s;
+                const double v = slice_dots(X + (int64_t)T[a] * s, xs, nb, cs0, cs1, red);
+                if (tid < nb) {
+                    const int64_t slot = (int64_t)(par * CL + rank) * PAIRS + pi + tid;
+                    if constexpr (CL > 1) {
+                        for (int d = 0; d < CL; ++d) cg::this_cluster().map_shared_rank(pd2, d)[slot] = v;
+                    } else {
+                        pd2[slot] = v;
+                    }
                 }
+                pi += nb;
+            }
+            csync();
+            if (tid == 0) {
+                int q = 0;
+                for (int a = 1; a < kk; ++a)
+                    for (int b = a + 1; b < kk; ++b, ++q) {
+                        double v = pd2[(int64_t)(par * CL) * PAIRS + q];
+                        for (int r = 1; r < CL; ++r) v = __dadd_rn(v, pd2[(int64_t)(par * CL + r) * PAIRS + q]);
+                        s_GT[a * kk + b] = v;
+                        s_GT[b * kk + a] = v;
+                    }
+            }
         }
         if (tid == 0) {
             double O[64];
@@ -508,8 +578,8 @@ k_select_mixed(int64_t s, const int64_t *coff, const int32_t *members, const int
             for (int a = 0; a < kk * kk; ++a) s_O[a] = O[a];
         }
         __syncthreads();
-        // FP64 rows X_T <- O X_T
-        for (int64_t r = tid; r < s; r += MX_THREADS) {
+        // FP64 rows X_T <- O X_T (this CTA's columns)
+        for (int64_t r = cs0 + tid; r < cs1; r += MX_THREADS) {
             double in[8], out[8];
             for (int a = 0; a < kk; ++a) in[a] = X[(int64_t)T[a] * s + r];
             for (int a = 0; a < kk; ++a) out[a] = rot_row(s_O, kk, a, in);
@@ -607,15 +677,21 @@ k_select_mixed(int64_t s, const int64_t *coff, const int32_t *members, const int
             for (int a = 0; a < kk; ++a) lvl[T[a]] = L;
             s_maxlev = max(s_maxlev, L);
             mask[le >> 5] &= ~(1u << (le & 31));
-            const int64_t rr = r0 + t;
-            for (int a = 0; a < K; ++a) kidx[rr * K + a] = a < kk ? T[a] : -1;
-            for (int a = 0; a < K * K; ++a) kO[rr * K * K + a] = a < kk * kk ? s_O[a] : 0.0;
-            kkv[rr] = kk;
-            kel[rr] = le;
-            klvl[rr] = L;
+            if (lead) {
+                const int64_t rr = r0 + t;
+                for (int a = 0; a < K; ++a) kidx[rr * K + a] = a < kk ? T[a] : -1;
+                for (int a = 0; a < K * K; ++a) kO[rr * K * K + a] = a < kk * kk ? s_O[a] : 0.0;
+                kkv[rr] = kk;
+                kel[rr] = le;
+                klvl[rr] = L;
+            }
         }
         __syncthreads();
     }
+    // no CTA leaves while another may still write into its shared memory;
+    // the records are CTA 0's to finish
+    if constexpr (CL > 1) cg::this_cluster().sync();
+    if (!lead) return;
     if (tid == 0) {
         atomicAdd(&stats[0], n_rescored);
         atomicAdd(&stats[1], n_fall);
@@ -678,8 +754,21 @@ pmmf_status mixed_stage_select(const DBuf<double> &D, int64_t s, const int32_t *
     PMMF_TRY(XH.alloc(precision == PMMF_PREC_BF16 ? s * sp / 2 : s * s, st));
     PMMF_TRY(XL.alloc(precision == PMMF_PREC_BF16 ? s * sp / 2 : s * s, st));
     PMMF_TRY(gd0.alloc(s, st));
-    PMMF_TRY(Gt.alloc(gb.total, st));
-    PMMF_TRY(Bd.alloc(gb.total, st));
+    // CTAs per cluster: as many as the SMs allow (up to the portable 8), so
+    // stages with few clusters still spread their FP64 work over the GPU;
+    // every CTA has its own copy of G~, B and M
+    int nsm = 152;
+    {
+        int dev = 0;
+        if (cudaGetDevice(&dev) == cudaSuccess)
+            cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    }
+    int CLn = 1;
+    while (CLn < 8 && m * (int64_t)CLn * 2 <= (int64_t)nsm) CLn *= 2;
+    PMMF_TRY(Gt.alloc(gb.total * CLn, st));
+    PMMF_TRY(Bd.alloc(gb.total * CLn, st));
+    DBuf<double> Mc;
+    PMMF_TRY(Mc.alloc(gb.total * CLn, st));
     if (precision == PMMF_PREC_BF16)
         k_build_slab<PMMF_PREC_BF16><<<(unsigned)s, 256, 0, st>>>(D.p, s, sp, pos, cls.members.p, X.p,
                                                                   XH.p, XL.p);
@@ -745,20 +834,50 @@ pmmf_status mixed_stage_select(const DBuf<double> &D, int64_t s, const int32_t *
     PMMF_TRY(rot.lvlidx.alloc(nr, st));
     PMMF_TRY(rot.lvl_off.alloc(rot.nrot + m + 1, st));
     PMMF_TRY(rot.nlev.zeros(m, st));
-    const size_t sh = sizeof(double) * (5 * (size_t)cmax + MX_WARPS * DOT_BATCH) +
-                      sizeof(uint32_t) * (size_t)((cmax + 31) / 32) +
-                      sizeof(int32_t) * (size_t)(3 * cmax + 4);
+    // the copies of G~ and M for the cluster's other CTAs
+    for (int r = 0; r < CLn; ++r) {
+        if (r > 0 && gb.total > 0)
+            PMMF_CUDA_TRY(cudaMemcpyAsync(Gt.p + r * gb.total, Gt.p, sizeof(float) * (size_t)gb.total,
+                                          cudaMemcpyDeviceToDevice, st));
+        if (gb.total > 0)
+            PMMF_CUDA_TRY(cudaMemcpyAsync(Mc.p + r * gb.total, gb.M.p, sizeof(double) * (size_t)gb.total,
+                                          cudaMemcpyDeviceToDevice, st));
+    }
+    size_t sh = sizeof(double) * (5 * (size_t)cmax + MX_WARPS * DOT_BATCH) +
+                sizeof(uint32_t) * (size_t)((cmax + 31) / 32) +
+                sizeof(int32_t) * (size_t)(3 * cmax + 4) + 16;
+    sh += sizeof(double) * 2 * (size_t)CLn * ((size_t)cmax + PAIRS);   // partial dot sums
     if (sh > 200 * 1024) {
         set_error("cluster too large for the shortlist search");
         return PMMF_ERR_UNSUPPORTED;
     }
-    if (sh > 48 * 1024)
-        PMMF_CUDA_TRY(cudaFuncSetAttribute(k_select_mixed, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh));
+    auto launch = [&](auto kern, int cl) -> pmmf_status {
+        PMMF_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh));
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3((unsigned)(m * cl), 1, 1);
+        cfg.blockDim = dim3(MX_THREADS, 1, 1);
+        cfg.dynamicSmemBytes = sh;
+        cfg.stream = st;
+        cudaLaunchAttribute at[1];
+        at[0].id = cudaLaunchAttributeClusterDimension;
+        at[0].val.clusterDim.x = (unsigned)cl;
+        at[0].val.clusterDim.y = 1;
+        at[0].val.clusterDim.z = 1;
+        cfg.attrs = at;
+        cfg.numAttrs = cl > 1 ? 1 : 0;
+        PMMF_CUDA_TRY(cudaLaunchKernelEx(&cfg, kern, s, (const int64_t *)cls.coff.p,
+                                         (const int32_t *)cls.members.p, (const int64_t *)gb.goff.p,
+                                         gb.total, X.p, Gt.p, Bd.p, Mc.p, (const double *)gd0.p,
+                                         (const int64_t *)rot.roff.p, seed, stage, K, eps, rot.kidx.p,
+                                         rot.kk.p, rot.kel.p, rot.klvl.p, rot.kO.p, rot.lvlidx.p,
+                                         rot.lvl_off.p, rot.nlev.p, elimflag, stats, status));
+        return PMMF_OK;
+    };
     prof_begin(KF_SELECT, st);
-    k_select_mixed<<<(unsigned)m, MX_THREADS, sh, st>>>(
-        s, cls.coff.p, cls.members.p, gb.goff.p, X.p, Gt.p, Bd.p, gb.M.p, gd0.p, rot.roff.p, seed,
-        stage, K, eps, rot.kidx.p, rot.kk.p, rot.kel.p, rot.klvl.p, rot.kO.p, rot.lvlidx.p,
-        rot.lvl_off.p, rot.nlev.p, elimflag, stats, status);
+    if (CLn == 8) PMMF_TRY(launch(k_select_mixed<8>, 8));
+    else if (CLn == 4) PMMF_TRY(launch(k_select_mixed<4>, 4));
+    else if (CLn == 2) PMMF_TRY(launch(k_select_mixed<2>, 2));
+    else PMMF_TRY(launch(k_select_mixed<1>, 1));
     prof_end(KF_SELECT, st, 0.0, 0.0);
     PMMF_TRY(launched("select_mixed"));
     if (K == 2) {
