@@ -298,10 +298,18 @@ class Factorization:
 
 
 def factor(n, rowptr, col, val, coords=None, *, k=2, eta=0.5, cluster_size=256, core_size=16,
-           seed=0, max_stages=0, lloyd_iters=10, record=False, labels=None) -> Factorization:
+           seed=0, max_stages=0, lloyd_iters=10, record=False, labels=None,
+           rows_all=False) -> Factorization:
     """Run the oracle's pMMF (Algorithm 1) and copy every result out.  labels:
-    optional stage-1 cluster label per coordinate (0 .. max), e.g. grid bricks."""
+    optional stage-1 cluster label per coordinate (0 .. max), e.g. grid bricks.
+    rows_all: the variant whose Grams sum over all n rows of the uncompacted
+    matrix (dense, small n; record is ignored)."""
     L = lib()
+    if not hasattr(L, "_rows_all_ready"):
+        L.or_factor_rows_all.restype = C.c_void_p
+        L.or_factor_rows_all.argtypes = [C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                                         C.c_int, C.c_void_p]
+        L._rows_all_ready = True
     rowptr = np.ascontiguousarray(rowptr, dtype=np.int64)
     col = np.ascontiguousarray(col, dtype=np.int32)
     val = np.ascontiguousarray(val, dtype=np.float64)
@@ -317,7 +325,10 @@ def factor(n, rowptr, col, val, coords=None, *, k=2, eta=0.5, cluster_size=256, 
         assert lab.shape == (n,)
     prm = _Params(k, eta, cluster_size, core_size, seed, max_stages, lloyd_iters,
                   None if lab is None else _p(lab), 0 if lab is None else int(lab.max()) + 1)
-    h = L.or_factor(n, _p(rowptr), _p(col), _p(val), cp, dim, C.byref(prm), 1 if record else 0)
+    if rows_all:
+        h = L.or_factor_rows_all(n, _p(rowptr), _p(col), _p(val), cp, dim, C.byref(prm))
+    else:
+        h = L.or_factor(n, _p(rowptr), _p(col), _p(val), cp, dim, C.byref(prm), 1 if record else 0)
     if not h:
         raise MemoryError("oracle allocation failed")
     f = Factorization(status=L.or_status(h), n=n, K=k, _h=h)

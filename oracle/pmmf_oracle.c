@@ -1844,3 +1844,176 @@ int or_step_transform(int64_t n, int64_t nrows, const int64_t *rowptr, const int
     free(in); free(cl); free(loc);
     return status;
 }
+
+/* ------------------------------------------------------------------------ */
+/* The literal reading of the Gram's rows (R2 variant PMMF_ROWS_ALL): the
+ * columns of Alg. 2 are the full n-row columns, so the matrix is never
+ * compacted: every stage rotates all n rows and columns (a rotation acts on
+ * its active coordinates; the rows and columns of coordinates eliminated
+ * earlier are carried along), each cluster's Gram sums over all n rows, and
+ * d(x) = G_xx - A_xx^2 uses the full column norm.  Dense n x n storage (small
+ * n only).  H = the diagonal entries at elimination (later rotations never
+ * touch them) and the final active block; the error is the Frobenius norm of
+ * everything else in the final matrix (orthogonal invariance), and stage p's
+ * contribution the change of that sum with S_p taken as the core.          */
+
+static double off_structure(const double *D, int64_t n, const int8_t *act) {
+    double s = 0.0;
+    for (int64_t x = 0; x < n; ++x)
+        for (int64_t y = 0; y < n; ++y)
+            if (x != y && !(act[x] && act[y])) s = s + D[x * n + y] * D[x * n + y];
+    return s;
+}
+
+or_fact *or_factor_rows_all(int64_t n, const int64_t *rowptr, const int32_t *col,
+                            const double *val, const double *coords, int dim,
+                            const or_params *prm) {
+    or_fact *f = (or_fact *)calloc(1, sizeof(or_fact));
+    if (!f) return NULL;
+    f->n = n;
+    f->K = prm->k;
+    if (n < 1 || prm->k < 2 || prm->k > KMAX || !(prm->eta > 0.0 && prm->eta < 1.0) ||
+        prm->cluster_size < prm->k || prm->core_size < 1 || prm->core_size > n ||
+        (coords && (dim < 1 || dim > 3))) {
+        f->status = OR_ERR_INVALID_ARG;
+        return f;
+    }
+    f->status = validate(n, rowptr, col, val);
+    if (f->status) return f;
+    const int K = prm->k;
+    double *D = (double *)calloc((size_t)(n * n), sizeof(double));
+    double *T = (double *)calloc((size_t)(n * n), sizeof(double));
+    int32_t *actl = (int32_t *)malloc(sizeof(int32_t) * (size_t)n);
+    int32_t *cl = (int32_t *)malloc(sizeof(int32_t) * (size_t)n);
+    int32_t *loc = (int32_t *)malloc(sizeof(int32_t) * (size_t)n);
+    int8_t *isact = (int8_t *)malloc((size_t)n);
+    uint32_t *q = coords ? (uint32_t *)malloc(sizeof(uint32_t) * (size_t)(n * dim)) : NULL;
+    f->hdiag = (double *)calloc((size_t)n, sizeof(double));
+    if (!D || !T || !actl || !cl || !loc || !isact || !f->hdiag || (coords && !q)) goto oom;
+    double nrm = 0.0;
+    for (int64_t i = 0; i < n; ++i)
+        for (int64_t e = rowptr[i]; e < rowptr[i + 1]; ++e) {
+            D[i * n + col[e]] = val[e];
+            nrm = nrm + val[e] * val[e];
+        }
+    f->norm_a = sqrt(nrm);
+    if (coords) or_quantize(n, coords, dim, q);
+    for (int64_t i = 0; i < n; ++i) { actl[i] = (int32_t)i; isact[i] = 1; }
+    int64_t s = n;
+    double prev = 0.0;
+    int p = 0;
+    while (s > prm->core_size && (prm->max_stages <= 0 || p < prm->max_stages)) {
+        ++p;
+        if (f->nst == f->cap) {
+            int nc = f->cap ? 2 * f->cap : 16;
+            ostage *ns = (ostage *)realloc(f->st, sizeof(ostage) * (size_t)nc);
+            if (!ns) goto oom;
+            f->st = ns;
+            f->cap = nc;
+        }
+        ostage *st = &f->st[f->nst++];
+        memset(st, 0, sizeof(*st));
+        st->s = s;
+        int64_t mm = 0, esum = 0;
+        int64_t *e = NULL;
+        int cs = stage_clusters(q, dim, coords != NULL, s, actl, p, prm, &mm, &st->coff,
+                                &st->members, &e, cl, loc);
+        if (cs == OR_ERR_INVALID_ARG) { f->status = cs; goto done; }
+        if (cs != OR_OK) goto oom;
+        st->m = mm;
+        for (int64_t u = 0; u < mm; ++u) esum += e[u];
+        st->nrot = esum;
+        st->roff = (int64_t *)calloc((size_t)(mm + 1), sizeof(int64_t));
+        st->rcl = (int32_t *)malloc(sizeof(int32_t) * (size_t)(esum + 1));
+        st->rk = (int32_t *)malloc(sizeof(int32_t) * (size_t)(esum + 1));
+        st->ridx = (int32_t *)malloc(sizeof(int32_t) * (size_t)((esum + 1) * K));
+        st->relim = (int32_t *)malloc(sizeof(int32_t) * (size_t)(esum + 1));
+        st->rO = (double *)malloc(sizeof(double) * (size_t)((esum + 1) * K * K));
+        if (!st->roff || !st->rcl || !st->rk || !st->ridx || !st->relim || !st->rO) { free(e); goto oom; }
+        int64_t cmax = 1;
+        for (int64_t u = 0; u < mm; ++u) {
+            st->roff[u + 1] = st->roff[u] + e[u];
+            if (st->coff[u + 1] - st->coff[u] > cmax) cmax = st->coff[u + 1] - st->coff[u];
+        }
+        /* search: Grams over all n rows (R9 order: ascending row index) */
+        double *G = (double *)malloc(sizeof(double) * (size_t)(cmax * cmax));
+        double *M = (double *)malloc(sizeof(double) * (size_t)(cmax * cmax));
+        if (!G || !M) { free(G); free(M); free(e); goto oom; }
+        int status = OR_OK;
+        for (int64_t u = 0; u < mm && status == OR_OK; ++u) {
+            const int64_t cu = st->coff[u + 1] - st->coff[u];
+            const int32_t *mem = st->members + st->coff[u];
+            for (int64_t a = 0; a < cu; ++a)
+                for (int64_t b = a; b < cu; ++b) {
+                    double acc = 0.0;
+                    for (int64_t r = 0; r < n; ++r)
+                        acc = fma(D[(int64_t)mem[a] * n + r], D[(int64_t)mem[b] * n + r], acc);
+                    const double mv = D[(int64_t)(mem[a] < mem[b] ? mem[a] : mem[b]) * n +
+                                        (mem[a] < mem[b] ? mem[b] : mem[a])];
+                    G[a * cu + b] = G[b * cu + a] = acc;
+                    M[a * cu + b] = M[b * cu + a] = mv;
+                }
+            int64_t rpos = st->roff[u];
+            status = find_rotations(st, u, e[u], G, M, prm, p, K, &rpos);
+        }
+        free(G); free(M); free(e);
+        if (status != OR_OK) { f->status = status; goto done; }
+        /* update of the whole matrix: D <- (D Q^T)^T Q^T (R13), every row */
+        double *dense = (double *)malloc(sizeof(double) * (size_t)cmax);
+        if (!dense) goto oom;
+        for (int pass = 0; pass < 2; ++pass) {
+            for (int64_t r = 0; r < n; ++r) {
+                double *row = D + r * n;
+                for (int64_t u = 0; u < mm; ++u) {
+                    const int64_t base = st->coff[u], cu = st->coff[u + 1] - base;
+                    for (int64_t l = 0; l < cu; ++l) dense[l] = row[st->members[base + l]];
+                    for (int64_t t = st->roff[u]; t < st->roff[u + 1]; ++t) {
+                        const int kk = st->rk[t];
+                        double vin[KMAX], vout[KMAX];
+                        int64_t Tl[KMAX];
+                        for (int a = 0; a < kk; ++a) {
+                            Tl[a] = loc[st->ridx[t * K + a]];
+                            vin[a] = dense[Tl[a]];
+                        }
+                        for (int a = 0; a < kk; ++a) vout[a] = rot_row(st->rO + t * K * K, kk, a, vin);
+                        for (int a = 0; a < kk; ++a) dense[Tl[a]] = vout[a];
+                    }
+                    for (int64_t l = 0; l < cu; ++l) row[st->members[base + l]] = dense[l];
+                }
+            }
+            for (int64_t x = 0; x < n; ++x)
+                for (int64_t y = 0; y < n; ++y) T[y * n + x] = D[x * n + y];
+            double *sw = D; D = T; T = sw;
+        }
+        free(dense);
+        /* eliminations: H's diagonal; the active set shrinks, nothing is dropped */
+        for (int64_t t = 0; t < st->nrot; ++t) {
+            const int32_t x = st->relim[t];
+            f->hdiag[x] = D[(int64_t)x * n + x];
+            isact[x] = 0;
+        }
+        int64_t ns = 0;
+        for (int64_t r = 0; r < s; ++r)
+            if (isact[actl[r]]) actl[ns++] = actl[r];
+        s = ns;
+        const double now = off_structure(D, n, isact);
+        st->contrib = now - prev;
+        prev = now;
+    }
+    f->ncore = s;
+    f->core_idx = (int32_t *)malloc(sizeof(int32_t) * (size_t)(s ? s : 1));
+    f->core = (double *)calloc((size_t)(s > 0 ? s * s : 1), sizeof(double));
+    if (!f->core_idx || !f->core) goto oom;
+    for (int64_t a = 0; a < s; ++a) {
+        f->core_idx[a] = actl[a];
+        for (int64_t b = 0; b < s; ++b) f->core[a * s + b] = D[(int64_t)actl[a] * n + actl[b]];
+        f->hdiag[actl[a]] = D[(int64_t)actl[a] * n + actl[a]];
+    }
+    f->err = f->norm_a > 0.0 ? sqrt(prev) / f->norm_a : 0.0;
+    goto done;
+oom:
+    f->status = OR_ERR_OOM;
+done:
+    free(D); free(T); free(actl); free(cl); free(loc); free(isact); free(q);
+    return f;
+}

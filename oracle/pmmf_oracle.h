@@ -79,6 +79,16 @@ int64_t or_stage_matrix(const or_fact *f, int p, int64_t *rowptr_n1, int32_t *co
 double or_error(const or_fact *f);          /* ||A - U^T H U||_F / ||A||_F */
 int or_threads(void);                        /* host threads a factorization uses */
 
+/* The variant PMMF_ROWS_ALL of the Gram's rows (the literal reading of the
+ * n-row columns of Alg. 2): the matrix is kept whole, every Gram sums over
+ * all n rows and every stage rotates all n rows and columns.  Dense storage,
+ * small n; p->labels and p->max_stages as for or_factor.  The accessors and
+ * or_apply work on the result; each stage's contrib is the change of the
+ * off-structure sum with that stage's survivors as the core. */
+or_fact *or_factor_rows_all(int64_t n, const int64_t *rowptr, const int32_t *col,
+                            const double *val, const double *coords, int dim,
+                            const or_params *p);
+
 /* The steps of one stage one at a time, for running a stage split over
  * several processes (each with a part of the clusters) in tests:
  *   or_step_clusters    stage p's clusters of the active set act[s] and their

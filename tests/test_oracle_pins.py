@@ -457,3 +457,36 @@ def test_openmp_build_gives_the_same_factorization():
         assert threads >= 1
         assert err == f.error
         assert np.array_equal(hd.view(np.uint64), f.hdiag.view(np.uint64))
+
+
+# ---------------------------------------------------------------- all rows in the Gram (R2 variant)
+
+@pytest.mark.parametrize("make,kw", [
+    (lambda: I.knn_laplacian(300, seed=3), dict(k=2, cluster_size=60, core_size=20)),
+    (lambda: I.psd_dense(96, 24, seed=2), dict(k=3, cluster_size=96, core_size=12)),
+    (lambda: I.rbf_mixture(200, components=4, seed=1), dict(k=2, cluster_size=50, core_size=16)),
+], ids=["knn300", "psd96-k3", "rbf200"])
+def test_rows_all_reconstruction_and_first_stage(make, kw):
+    """The variant whose Grams sum over all n rows of the uncompacted matrix:
+    its reported error is ||A - U^T H U||_F / ||A||_F computed explicitly
+    (U^T H U applied to the identity), its rotations are orthogonal, and its
+    first stage equals the default reading's (at stage 1 every row is
+    active)."""
+    a = make()
+    kw = dict(kw, eta=0.5, seed=4)
+    f = O.factor_csr(a, rows_all=True, **kw)
+    g = O.factor_csr(a, **kw)
+    assert f.status == 0 and g.status == 0
+    A = a.to_dense()
+    At = f.apply(O.OP_A, np.eye(a.n))
+    err = np.linalg.norm(A - At) / np.linalg.norm(A)
+    assert abs(err - f.error) <= 1e-12 * max(f.error, 1e-300) + 1e-15
+    for st in f.stages:
+        for t in range(len(st.rot_elim)):
+            kk = st.rot_k[t]
+            Ob = st.rot_O[t][:kk * kk].reshape(kk, kk)
+            assert np.abs(Ob @ Ob.T - np.eye(kk)).max() <= 1e-14
+    s0, t0 = f.stages[0], g.stages[0]
+    assert np.array_equal(s0.rot_idx, t0.rot_idx) and np.array_equal(s0.rot_elim, t0.rot_elim)
+    assert np.array_equal(s0.rot_O, t0.rot_O)
+    assert f.total_rotations() == g.total_rotations()
