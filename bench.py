@@ -781,11 +781,11 @@ def run_gpu_poisson(args):
     build.build()
     pmmf.load()
     dev = torch.device("cuda", 0)
-    a = I.poisson3d(POISSON["nx"], seed=POISSON["gen_seed"])
+    nx = args.nx
+    a = I.poisson3d(nx, seed=POISSON["gen_seed"])
     A = I.SymCSR(a.n, torch.from_numpy(a.rowptr).to(dev), torch.from_numpy(a.col).to(dev),
                  torch.from_numpy(a.val).to(dev))
     co = torch.from_numpy(a.coords).to(dev)
-    nx = POISSON["nx"]
     bricks = torch.from_numpy(I.grid_bricks(nx, nx, nx, 8, 8, 4)).to(dev)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream()
@@ -843,9 +843,9 @@ def run_gpu_poisson(args):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
-        "config": {"workload": "poisson3d 128^3 (7-point FV, log-normal sigma=1, seed 4), FP64 CSR; "
-                               "stage 1: 8x8x4 grid bricks (8,192 clusters), then k-means clusters "
-                               "of 256 on cell centres; k=2, eta=0.5, core 1024",
+        "config": {"workload": f"poisson3d {nx}^3 (7-point FV, log-normal sigma=1, seed 4), FP64 CSR; "
+                               f"stage 1: 8x8x4 grid bricks ({nx ** 3 // 256:,} clusters), then k-means "
+                               "clusters of 256 on cell centres; k=2, eta=0.5, core 1024",
                    "n": a.n, "nnz": a.nnz, "stages": info.stages, "frobenius_error": info.error,
                    "l2": "256 MiB buffer written between timed steps"},
         "pcg": {"nrhs": POISSON["nrhs"], "rtol": POISSON["rtol"], "status": st, "seconds": pcg_s,
@@ -965,7 +965,21 @@ def main():
                          "poisson: 128^3 Poisson factorization and PCG")
     ap.add_argument("--precision", choices=list(PREC), default="fp64",
                     help="Gram precision of the rbf_dense workload")
+    ap.add_argument("--nx", type=int, default=POISSON["nx"],
+                    help="grid edge of the poisson workload (a multiple of 8)")
+    ap.add_argument("--tune", action="append", default=[], metavar="NAME=VALUE",
+                    help="library knob for every cluster size, e.g. dense_tiles=1 (repeatable)")
     args = ap.parse_args()
+    if args.nx <= 0 or args.nx % 8:
+        ap.error("--nx must be a positive multiple of 8")
+    if args.tune and args.impl == "gpu":
+        from paper_1507_04396_gb300 import build, pmmf
+        build.build()
+        for kv in args.tune:
+            name, _, value = kv.partition("=")
+            if name not in pmmf.TUNE_PARAMS or not value.lstrip("-").isdigit():
+                ap.error(f"--tune {kv}: expected one of {sorted(pmmf.TUNE_PARAMS)}=<int>")
+            pmmf.set_tuning(name, int(value))
     if args.workload == "rbf_dense":
         return run_gpu_rbf(args)
     if args.workload == "scaling":

@@ -454,9 +454,9 @@ pmmf_status pmmf_get_stage_matrix(const pmmf_handle *f, int p, int64_t *rowptr_n
  * row segment only the rotations that reach its pattern (clusters of up to
  * 1,024 coordinates); both give the same bits), PMMF_TUNE_DENSE_TILES (the
  * dense update: 1 = the block in cluster order moved in TMA tiles, each CTA
- * staging one cluster's rotations (the default; clusters whose tiles do not
- * fit shared memory fall back to 2), 2 = one CTA per row applying every
- * cluster's rotations; both give the same bits).  A value
+ * staging one cluster's rotations (clusters whose tiles do not fit shared
+ * memory fall back to 2), 2 = one CTA per row applying every cluster's
+ * rotations (the default); both give the same bits).  A value
  * applies to launches whose largest cluster has at most max_size coordinates
  * and no smaller bucket matches; shared-memory limits still halve the row and
  * Gram warps when needed.  Process wide; INVALID_ARG for an unknown param or

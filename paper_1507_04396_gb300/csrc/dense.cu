@@ -375,8 +375,10 @@ __device__ __forceinline__ double &tile_at(double *buf, int i, int c) {
 
 // One CTA per (cluster, row group); see above.  rows: the rows of the tensor
 // (s for the column-permuted block, S for the transposed one).
+constexpr int TILE_WARPS = 8;   // 256 threads
+
 template <int RB>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(TILE_WARPS * 32)
 k_dense_tiles(const __grid_constant__ CUtensorMap tmap, int64_t rows, const int64_t *coff,
               const int64_t *poff, TileRot R, int64_t rows_per_group, unsigned *status) {
     extern __shared__ __align__(1024) unsigned char tsm[];
@@ -476,11 +478,17 @@ k_dense_tiles(const __grid_constant__ CUtensorMap tmap, int64_t rows, const int6
         }
         const int64_t left = r_end - (r_begin + (int64_t)b * RB);
         const int nrows = (int)(left < RB ? left : RB);
+        // warp w owns the tile's rows w, w + 8, ...: the rows are independent
+        // and the rotations of one level are disjoint, so a level ends with a
+        // warp barrier, not a block barrier
+        const int lane = tid & 31, wid = tid >> 5;
+        const int rw = nrows > wid ? (nrows - wid + TILE_WARPS - 1) / TILE_WARPS : 0;
         for (int L = 0; L < nl; ++L) {
             const int s0 = lvo[L], ns = lvo[L + 1] - s0;
-            const int tasks = nrows * ns;
-            for (int q = tid; q < tasks; q += blockDim.x) {
-                const int i = q / ns, slot = s0 + (q - i * ns);
+            const int tasks = rw * ns;
+            for (int q = lane; q < tasks; q += 32) {
+                const int ir = q / ns, slot = s0 + (q - ir * ns);
+                const int i = wid + ir * TILE_WARPS;
                 if (K <= 2) {
                     const Rot2 t = r2[slot];
                     double &ra = tile_at<RB>(cur, i, t.li);
@@ -510,7 +518,7 @@ k_dense_tiles(const __grid_constant__ CUtensorMap tmap, int64_t rows, const int6
                     }
                 }
             }
-            __syncthreads();
+            __syncwarp();
         }
         // the threads' writes before the TMA store reads the tile
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -721,7 +729,7 @@ pmmf_status launch_tiles(const CUtensorMap &map, int64_t rows, int64_t m, const 
     const int64_t gy = (rows + rpg - 1) / rpg;
     PMMF_CUDA_TRY(cudaFuncSetAttribute(k_dense_tiles<RB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)smem));
-    k_dense_tiles<RB><<<dim3((unsigned)m, (unsigned)gy), 256, smem, st>>>(map, rows, coff, poff, R, rpg,
+    k_dense_tiles<RB><<<dim3((unsigned)m, (unsigned)gy), TILE_WARPS * 32, smem, st>>>(map, rows, coff, poff, R, rpg,
                                                                        status);
     return launched("dense_tiles");
 }
@@ -761,7 +769,7 @@ pmmf_status dense_update_tiles(DBuf<double> &D, int64_t s, const StageClusters &
     int rb = 0;
     for (int cand : {16, 8, 4}) {
         const size_t need = 2 * (size_t)cpad_max * cand * sizeof(double) + fixed;
-        if (need <= 200 * 1024) {
+        if (need <= 224 * 1024) {
             rb = cand;
             break;
         }

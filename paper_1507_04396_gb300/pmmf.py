@@ -192,6 +192,12 @@ def apply_tuning(path: str) -> bool:
     return True
 
 
+def set_tuning(name: str, value: int, max_size: int = 1 << 30) -> None:
+    """Set one launch-shape or kernel-choice knob (TUNE_PARAMS) for clusters
+    of up to max_size coordinates."""
+    _check(load().pmmf_set_tuning(TUNE_PARAMS[name], int(max_size), int(value)))
+
+
 FAMILIES = ["partition", "gram", "select", "rows", "apply", "other"]
 
 
