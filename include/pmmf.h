@@ -456,7 +456,18 @@ pmmf_status pmmf_get_stage_matrix(const pmmf_handle *f, int p, int64_t *rowptr_n
  * dense update: 1 = the block in cluster order moved in TMA tiles, each CTA
  * staging one cluster's rotations (clusters whose tiles do not fit shared
  * memory fall back to 2), 2 = one CTA per row applying every cluster's
- * rotations (the default); both give the same bits).  A value
+ * rotations (the default); both give the same bits), PMMF_TUNE_SELECT_DSM
+ * (the k = 2 rotation search: 1 = one CTA per cluster with G and M in
+ * global memory (the default), 2 = a thread-block cluster of 8 CTAs per
+ * cluster holding G and M in their shared memory, row-sliced, for stages
+ * whose clusters have up to ~318 coordinates (larger ones use 1); both give
+ * the same bits), PMMF_TUNE_APPLY_FUSED (the rotation passes of the
+ * matrix-free apply: 1 = one launch per stage (the default), 2 = one
+ * cooperative launch per pass with a grid barrier between stages, where the
+ * device supports cooperative launches and the right-hand sides fit one pass
+ * (else 1); both give the same bits; max_size is the largest cluster of the
+ * factorization).
+ * A value
  * applies to launches whose largest cluster has at most max_size coordinates
  * and no smaller bucket matches; shared-memory limits still halve the row and
  * Gram warps when needed.  Process wide; INVALID_ARG for an unknown param or
@@ -464,7 +475,8 @@ pmmf_status pmmf_get_stage_matrix(const pmmf_handle *f, int p, int64_t *rowptr_n
  * the reach threshold). */
 enum { PMMF_TUNE_ROWS_WARPS = 0, PMMF_TUNE_GRAM_WARPS = 1, PMMF_TUNE_SELECT_WARPS = 2,
        PMMF_TUNE_PASS1_ESTIMATE = 3, PMMF_TUNE_REACH_CLUSTERS = 4, PMMF_TUNE_ROWS_KERNEL = 5,
-       PMMF_TUNE_DENSE_TILES = 6 };
+       PMMF_TUNE_DENSE_TILES = 6, PMMF_TUNE_SELECT_DSM = 7,
+       PMMF_TUNE_APPLY_FUSED = 8 };
 pmmf_status pmmf_set_tuning(int param, int64_t max_size, int value);
 void pmmf_clear_tuning(void);
 

@@ -12,8 +12,12 @@
 //            "not SPD").
 #include "apply.cuh"
 
+#include <cooperative_groups.h>
+
 #include <cmath>
+#include <mutex>
 #include <utility>
+#include <vector>
 #include "rotmath.cuh"
 
 namespace pmmf {
@@ -22,63 +26,132 @@ namespace {
 
 constexpr int AP_THREADS = 256;
 
-// One CTA per cluster: gather x[members][0..nr), apply the levels, scatter.
-// NR > 0: nr is NR, known at compile time (the divisions by nr become shifts).
+// The rotation data of one stage as the apply kernels read it.
+struct StageDesc {
+    const int64_t *coff;
+    const int32_t *members;
+    const int64_t *roff;
+    const int32_t *lvl_off, *nlev;
+    const Rot2 *lvlrot;
+    const int32_t *kidx, *kkv, *lvlidx;
+    const double *kO;
+    int64_t m;
+    int K, pad;
+};
+
+// Shared memory of the apply kernels: the staged rotations of a cluster
+// (rcap slots: its Givens rotations, fewer than its size, and its level
+// offsets, at most its size + 1; rcap 0 reads both from global memory), then
+// the slice of x (cluster size x right-hand sides).  Rotations are staged for
+// clusters of up to APPLY_STAGE_MAX coordinates.
+constexpr int64_t APPLY_STAGE_MAX = 1024;
+
+__host__ __device__ constexpr size_t apply_smem_rot(int64_t rcap) {
+    return (sizeof(Rot2) * (size_t)rcap + sizeof(int32_t) * (size_t)(rcap + 2) + 15) & ~(size_t)15;
+}
+
+// Cluster u of a stage: gather x[members][0..nr) into shared memory together
+// with the cluster's level offsets and (k = 2) its rotations, apply the levels
+// (in reverse, transposed, for U^T), scatter.  Staging the rotations turns
+// the two dependent global loads of every level (its offsets, then each
+// task's rotation) into shared-memory loads.  Ends with the scatter: a caller
+// reusing the shared memory for another cluster syncs first.
 template <bool TRANSPOSE, int NR>
-__global__ void __launch_bounds__(AP_THREADS)
-k_apply_stage(const int64_t *coff, const int32_t *members, const int64_t *roff,
-              const int32_t *lvl_off, const int32_t *nlev, const Rot2 *lvlrot, double *x,
-              int64_t ld, int64_t r0, int nr_rt, int K, const int32_t *kidx, const int32_t *kkv,
-              const int32_t *lvlidx, const double *kO) {
-    extern __shared__ double sx[];
-    const int nr = NR > 0 ? NR : nr_rt;
-    const int64_t u = blockIdx.x;
-    const int64_t base = coff[u];
-    const int c = (int)(coff[u + 1] - base);
-    const int nl = nlev[u];
+__device__ __forceinline__ void apply_cluster(const StageDesc &a, int64_t u, unsigned char *smem,
+                                              int64_t rcap, double *x, int64_t ld, int64_t r0, int nr) {
+    const int64_t base = a.coff[u];
+    const int c = (int)(a.coff[u + 1] - base);
+    const int nl = a.nlev[u];
     if (nl == 0) return;
+    Rot2 *srot = (Rot2 *)smem;
+    int32_t *slo = (int32_t *)(srot + rcap);
+    double *sx = (double *)(smem + apply_smem_rot(rcap));
+    const int32_t *lo = a.lvl_off + a.roff[u] + u;
+    const int rb = lo[0];
+    const int nrot = lo[nl] - rb;
+    const bool staged = nrot <= rcap;   // (the launch sets rcap >= any cluster's rotations, or 0)
+    if (staged) {
+        for (int L = threadIdx.x; L <= nl; L += AP_THREADS) slo[L] = lo[L] - rb;
+        if (a.K == 2)
+            for (int q = threadIdx.x; q < nrot; q += AP_THREADS) srot[q] = a.lvlrot[rb + q];
+    }
     for (int64_t q = threadIdx.x; q < (int64_t)c * nr; q += AP_THREADS) {
         int64_t l = q / nr, r = q - l * nr;
-        sx[q] = x[(int64_t)members[base + l] * ld + r0 + r];
+        sx[q] = x[(int64_t)a.members[base + l] * ld + r0 + r];
     }
     __syncthreads();
-    const int32_t *lo = lvl_off + roff[u] + u;
     for (int Li = 0; Li < nl; ++Li) {
         const int L = TRANSPOSE ? nl - 1 - Li : Li;
-        const int b0 = lo[L], cnt = lo[L + 1] - b0;
+        const int b0 = staged ? slo[L] : lo[L] - rb;
+        const int cnt = (staged ? slo[L + 1] : lo[L + 1] - rb) - b0;
         for (int q = threadIdx.x; q < cnt * nr; q += AP_THREADS) {
             const int t = q / nr, r = q - t * nr;
-            if (K == 2) {
-                const Rot2 rt = lvlrot[b0 + t];
-                double a = sx[rt.li * nr + r], b = sx[rt.lj * nr + r], na, nb;
-                if (TRANSPOSE) rot_pair_t(rt.c, rt.s, a, b, na, nb);
-                else rot_pair(rt.c, rt.s, a, b, na, nb);
+            if (a.K == 2) {
+                const Rot2 rt = staged ? srot[b0 + t] : a.lvlrot[rb + b0 + t];
+                double va = sx[rt.li * nr + r], vb = sx[rt.lj * nr + r], na, nb;
+                if (TRANSPOSE) rot_pair_t(rt.c, rt.s, va, vb, na, nb);
+                else rot_pair(rt.c, rt.s, va, vb, na, nb);
                 sx[rt.li * nr + r] = na;
                 sx[rt.lj * nr + r] = nb;
             } else {
                 // x_T' = O x_T, or x_T = O^T x_T' for the transpose (chains
                 // over the block's rows of O^T, i.e. its columns)
-                const int64_t tt = lvlidx[b0 + t];
-                const int kk = kkv[tt];
-                const int32_t *T = kidx + tt * K;
-                const double *O = kO + tt * K * K;
+                const int64_t tt = a.lvlidx[rb + b0 + t];
+                const int kk = a.kkv[tt];
+                const int32_t *T = a.kidx + tt * a.K;
+                const double *O = a.kO + tt * a.K * a.K;
                 double in[8], out[8], Ot[64];
-                for (int a = 0; a < kk; ++a) in[a] = sx[T[a] * nr + r];
+                for (int k = 0; k < kk; ++k) in[k] = sx[T[k] * nr + r];
                 if (TRANSPOSE) {
-                    for (int a = 0; a < kk; ++a)
-                        for (int b = 0; b < kk; ++b) Ot[a * kk + b] = O[b * kk + a];
-                    for (int a = 0; a < kk; ++a) out[a] = rot_row(Ot, kk, a, in);
+                    for (int k = 0; k < kk; ++k)
+                        for (int l = 0; l < kk; ++l) Ot[k * kk + l] = O[l * kk + k];
+                    for (int k = 0; k < kk; ++k) out[k] = rot_row(Ot, kk, k, in);
                 } else {
-                    for (int a = 0; a < kk; ++a) out[a] = rot_row(O, kk, a, in);
+                    for (int k = 0; k < kk; ++k) out[k] = rot_row(O, kk, k, in);
                 }
-                for (int a = 0; a < kk; ++a) sx[T[a] * nr + r] = out[a];
+                for (int k = 0; k < kk; ++k) sx[T[k] * nr + r] = out[k];
             }
         }
         __syncthreads();
     }
     for (int64_t q = threadIdx.x; q < (int64_t)c * nr; q += AP_THREADS) {
         int64_t l = q / nr, r = q - l * nr;
-        x[(int64_t)members[base + l] * ld + r0 + r] = sx[q];
+        x[(int64_t)a.members[base + l] * ld + r0 + r] = sx[q];
+    }
+}
+
+// One CTA per cluster of one stage.
+// NR > 0: nr is NR, known at compile time (the divisions by nr become shifts).
+template <bool TRANSPOSE, int NR>
+__global__ void __launch_bounds__(AP_THREADS)
+k_apply_stage(const StageDesc a, int64_t rcap, double *x, int64_t ld, int64_t r0, int nr_rt) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    apply_cluster<TRANSPOSE, NR>(a, blockIdx.x, smem, rcap, x, ld, r0, NR > 0 ? NR : nr_rt);
+}
+
+// Every stage of a pass in one cooperative launch: the CTAs take a stage's
+// clusters in turn, and a grid barrier separates the stages (a stage reads
+// what the previous one scattered), so a pass has no launch gaps.
+constexpr int APPLY_MAXST = 40;
+struct StagePass {
+    StageDesc d[APPLY_MAXST];
+    int n;
+};
+
+template <bool TRANSPOSE, int NR>
+__global__ void __launch_bounds__(AP_THREADS, 6)
+k_apply_all(const __grid_constant__ StagePass P, int64_t rcap, double *x, int64_t ld, int64_t r0,
+            int nr_rt) {
+    namespace cg = cooperative_groups;
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int nr = NR > 0 ? NR : nr_rt;
+    for (int pi = 0; pi < P.n; ++pi) {
+        const StageDesc &a = P.d[TRANSPOSE ? P.n - 1 - pi : pi];
+        for (int64_t u = blockIdx.x; u < a.m; u += gridDim.x) {
+            apply_cluster<TRANSPOSE, NR>(a, u, smem, rcap, x, ld, r0, nr);
+            __syncthreads();
+        }
+        if (pi + 1 < P.n) cg::this_grid().sync();
     }
 }
 
@@ -337,8 +410,140 @@ __global__ void k_sub(const double *b, const double *q, double *r, int64_t cnt) 
 
 }  // namespace
 
+namespace {
+
+StageDesc desc_of(const ApplyStage &a) {
+    StageDesc d;
+    d.coff = a.coff;
+    d.members = a.members;
+    d.roff = a.roff;
+    d.lvl_off = a.lvl_off;
+    d.nlev = a.nlev;
+    d.lvlrot = a.lvlrot;
+    d.kidx = a.kidx;
+    d.kkv = a.kkv;
+    d.lvlidx = a.lvlidx;
+    d.kO = a.kO;
+    d.m = a.m;
+    d.K = a.K;
+    d.pad = 0;
+    return d;
+}
+
+// Algorithmic bytes of one stage's rotation pass: the stage's coordinates read
+// and written once per right-hand side, their ids, and the rotations (24 B
+// each) with their level offsets.
+double stage_bytes(const ApplyStage &a, int64_t nr) {
+    return 16.0 * (double)a.s * nr + 4.0 * (double)a.s + 24.0 * (double)a.nrot + 4.0 * (double)(a.nrot + a.m);
+}
+
+// Blocks of `kern` resident per SM with `sh` bytes of shared memory (asked
+// once per kernel, size and device); 0 when cooperative launches are
+// unavailable.
+int coop_per_sm(const void *kern, size_t sh, int *nsm) {
+    static std::mutex mu;
+    struct Entry {
+        int dev;
+        const void *k;
+        size_t sh;
+        int per_sm, nsm;
+    };
+    static std::vector<Entry> seen;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+    std::lock_guard<std::mutex> g(mu);
+    for (const Entry &e : seen)
+        if (e.dev == dev && e.k == kern && e.sh == sh) {
+            *nsm = e.nsm;
+            return e.per_sm;
+        }
+    int coop = 0, per_sm = 0, n = 0;
+    if (cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev) != cudaSuccess) coop = 0;
+    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) n = 0;
+    if (coop && n > 0 &&
+        (sh <= 48 * 1024 ||
+         cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh) == cudaSuccess) &&
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, AP_THREADS, sh) != cudaSuccess)
+        per_sm = 0;
+    if (!coop) per_sm = 0;
+    cudaGetLastError();
+    seen.push_back({dev, kern, sh, per_sm, n});
+    *nsm = n;
+    return per_sm;
+}
+
+// The whole pass in one cooperative launch; *done false when it cannot run.
+pmmf_status apply_fused(const ApplyStages &S, bool transpose, double *x, int64_t ld, int64_t nrhs,
+                        int64_t cmax, cudaStream_t st, bool *done) {
+    *done = false;
+    StagePass P;
+    P.n = 0;
+    int64_t mmax = 0;
+    double bytes = 0.0;
+    for (const ApplyStage &a : S) {
+        if (a.nrot == 0) continue;
+        if (P.n == APPLY_MAXST) return PMMF_OK;
+        P.d[P.n++] = desc_of(a);
+        mmax = std::max(mmax, a.m);
+        bytes += stage_bytes(a, nrhs);
+    }
+    if (P.n == 0) {
+        *done = true;
+        return PMMF_OK;
+    }
+    int64_t rcap = cmax <= APPLY_STAGE_MAX ? cmax : 0;
+    const size_t sh = apply_smem_rot(rcap) + sizeof(double) * (size_t)cmax * (size_t)nrhs;
+    const void *kern = transpose ? (nrhs == 8 ? (const void *)k_apply_all<true, 8>
+                                              : nrhs == 1 ? (const void *)k_apply_all<true, 1>
+                                                          : (const void *)k_apply_all<true, 0>)
+                                 : (nrhs == 8 ? (const void *)k_apply_all<false, 8>
+                                              : nrhs == 1 ? (const void *)k_apply_all<false, 1>
+                                                          : (const void *)k_apply_all<false, 0>);
+    int nsm = 0;
+    const int per_sm = coop_per_sm(kern, sh, &nsm);
+    if (per_sm <= 0) return PMMF_OK;
+    const unsigned g = (unsigned)std::max<int64_t>(1, std::min<int64_t>(mmax, (int64_t)per_sm * nsm));
+    int64_t r0 = 0;
+    int nr_rt = (int)nrhs;
+    void *args[] = {&P, &rcap, &x, &ld, &r0, &nr_rt};
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(g);
+    cfg.blockDim = dim3(AP_THREADS);
+    cfg.dynamicSmemBytes = sh;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    prof_begin(KF_APPLY, st);
+    PMMF_CUDA_TRY(cudaLaunchKernelExC(&cfg, kern, args));
+    prof_end(KF_APPLY, st, bytes, 0.0);
+    PMMF_TRY(launched("apply_all"));
+    *done = true;
+    return PMMF_OK;
+}
+
+}  // namespace
+
 pmmf_status apply_rotations(const ApplyStages &S, bool transpose, double *x, int64_t ld,
                             int64_t nrhs, cudaStream_t st) {
+    int64_t cmax = 0;
+    for (const ApplyStage &a : S)
+        if (a.nrot > 0) cmax = std::max(cmax, a.cmax);
+    if (cmax == 0) return PMMF_OK;
+    // one pass per launch (PMMF_TUNE_APPLY_FUSED = 2) when every right-hand
+    // side fits the shared-memory slice (24 KB per cluster keeps several CTAs
+    // per SM).  Measured on GB300 it is not faster than a launch per stage
+    // (kNN n = 65,536, U^T H U x on 8 columns: 0.234 against 0.232 ms; 128^3
+    // Poisson A~^-1 x: 1.09 against 1.00 ms): a late stage's time is its
+    // clusters' chains of dependency levels, not the launch, so it runs only
+    // when asked for.
+    if (tuned(TUNE_APPLY_FUSED, cmax, 1) == 2 && (int64_t)(24 * 1024) / cmax >= nrhs) {
+        bool done = false;
+        PMMF_TRY(apply_fused(S, transpose, x, ld, nrhs, cmax, st, &done));
+        if (done) return PMMF_OK;
+    }
     for (size_t pi = 0; pi < S.size(); ++pi) {
         const ApplyStage &a = transpose ? S[S.size() - 1 - pi] : S[pi];
         if (a.nrot == 0) continue;
@@ -348,9 +553,11 @@ pmmf_status apply_rotations(const ApplyStages &S, bool transpose, double *x, int
             return PMMF_ERR_UNSUPPORTED;
         }
         if (chunk > nrhs) chunk = nrhs;
+        const StageDesc d = desc_of(a);
         for (int64_t r0 = 0; r0 < nrhs; r0 += chunk) {
             int nr = (int)(nrhs - r0 < chunk ? nrhs - r0 : chunk);
-            size_t sh = sizeof(double) * (size_t)a.cmax * (size_t)nr;
+            const int64_t rcap = a.cmax <= APPLY_STAGE_MAX ? a.cmax : 0;
+            size_t sh = apply_smem_rot(rcap) + sizeof(double) * (size_t)a.cmax * (size_t)nr;
             // one right-hand side and blocks of 8 (PCG's usual widths) get
             // instantiations with the width fixed
             auto kern = transpose ? (nr == 8 ? k_apply_stage<true, 8> : nr == 1 ? k_apply_stage<true, 1>
@@ -360,14 +567,8 @@ pmmf_status apply_rotations(const ApplyStages &S, bool transpose, double *x, int
             prof_begin(KF_APPLY, st);
             if (sh > 48 * 1024)
                 PMMF_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh));
-            kern<<<(unsigned)a.m, AP_THREADS, sh, st>>>(a.coff, a.members, a.roff, a.lvl_off, a.nlev,
-                                                        a.lvlrot, x, ld, r0, nr, a.K, a.kidx, a.kkv,
-                                                        a.lvlidx, a.kO);
-            // the stage's coordinates read and written once per right-hand side,
-            // their ids, and the rotations (24 B each) with their level offsets
-            prof_end(KF_APPLY, st,
-                     16.0 * (double)a.s * nr + 4.0 * (double)a.s + 24.0 * (double)a.nrot +
-                         4.0 * (double)(a.nrot + a.m), 0.0);
+            kern<<<(unsigned)a.m, AP_THREADS, sh, st>>>(d, rcap, x, ld, r0, nr);
+            prof_end(KF_APPLY, st, stage_bytes(a, nr), 0.0);
             PMMF_TRY(launched("apply_stage"));
         }
     }

@@ -724,7 +724,9 @@ pmmf_status pmmf_set_tuning(int param, int64_t max_size, int value) {
         (value > 32 && param != TUNE_REACH_CLUSTERS) ||
         (param == TUNE_SELECT_WARPS && value != 8 && value != 16) ||
         (param == TUNE_ROWS_KERNEL && value != 1 && value != 2) ||
-        (param == TUNE_DENSE_TILES && value != 1 && value != 2)) {
+        (param == TUNE_DENSE_TILES && value != 1 && value != 2) ||
+        (param == TUNE_SELECT_DSM && value != 1 && value != 2) ||
+        (param == TUNE_APPLY_FUSED && value != 1 && value != 2)) {
         set_error("pmmf_set_tuning: unknown parameter or value out of range");
         return PMMF_ERR_INVALID_ARG;
     }

@@ -18,6 +18,8 @@
 // root ~600, so the per-step critical path is arranged around FP64 latency:
 // scores are compared through their (order-preserving) bit patterns, and the
 // angle takes two square roots and two independent divides.
+#include <cooperative_groups.h>
+
 #include <vector>
 
 #include "common.cuh"
@@ -903,6 +905,377 @@ k_select_fast(const int64_t *coff, const int32_t *members, const int64_t *goff, 
     finish_cluster(u, r0, e, s_maxlev, members, base, rec, lcnt, lvlrot, lvl_off, nlev, elimflag, stage);
 }
 
+// Search of one cluster by a thread-block cluster of DSM_CL CTAs that hold G
+// and M in their shared memory, row-sliced: CTA r keeps rows [r R, (r + 1) R)
+// of both (R = ceil(c / DSM_CL)); every CTA keeps the diagonals, the weights,
+// the active mask and the levels, and takes every decision of a step itself
+// (the same inputs, so the same bits everywhere).  A step's loads are
+// shared-memory loads, local or distributed, instead of L2 loads.
+//
+// Step t starts with (i, j, G_ij, M_ij) in every CTA's mailbox and with a1,
+// a2: the active coordinates at positions p and p + 1 (p the position drawn
+// for step t + 1), one of which is the next pivot once the eliminated
+// coordinate is known (le <= a1 ? a2 : a1).  Then:
+//   A  warps 0 and 13: the angle's c and s (the same prefix, the two divides
+//      on two sub-partitions).  Warp 14: the new weights of the previous
+//      step's pair.  Warps 1-4 (5-8) of the CTA holding row a1 (a2), once
+//      those weights are in: the partner search of that row over every
+//      candidate but i and j (its other entries and their weights do not
+//      change in step t).  Warps 9-11: columns i and j of the CTA's rows
+//      loaded.
+//   B  warp 0: the new diagonal entries of the 2 x 2 blocks (lanes 0-3), then
+//      elimination, level, record and the next pivot i'; warps 9-11: the
+//      CTA's rows rotated, the mirrored entries stored into rows i and j
+//      where they are held.
+//   C  the CTA holding
+//      row i' merges the survivor's entry (its score bounded in FP32 first,
+//      so its exact weight is needed only when it could win) and writes the
+//      next (i', j', G, M) into every mailbox.  If i' is the survivor itself
+//      (its row was just rotated everywhere) a cluster barrier comes first
+//      and the row is searched in full.  Warp 15: a1, a2 of step t + 2.
+//   cluster barrier.
+// The arithmetic, and so every bit, is k_select's.  CTA 0 writes the records
+// and finishes the cluster.  The launch keeps 2 R <= DSM_ROT_N (one rotation
+// task per thread).
+constexpr int DSM_CL = 8;
+constexpr int DSM_THREADS = 512;
+constexpr int DSM_WARPS = DSM_THREADS / 32;
+constexpr int DSM_SCORE_WARPS = 4;   // per speculative row: warps 1-4 and 5-8
+constexpr int DSM_ROT_T0 = 288;      // warps 9-11 rotate the CTA's rows
+constexpr int DSM_ROT_N = 96;
+constexpr int DSM_S_WARP = 13;       // the angle's s (warp 0: c), on its own sub-partition
+constexpr int DSM_W_WARP = 14;       // the previous step's new weights
+constexpr int DSM_NEXT_WARP = 15;    // a1, a2 of step t + 2
+
+struct DsmMail {
+    double g, m;
+    int32_t j, pad;
+};
+
+__device__ __forceinline__ void cluster_arrive_release() {
+    asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ void cluster_wait_acquire() {
+    asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
+// Named barrier of `count` threads: wait, or arrive without waiting.
+__device__ __forceinline__ void named_sync(int id, int count) {
+    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void named_arrive(int id, int count) {
+    asm volatile("bar.arrive %0, %1;" ::"r"(id), "r"(count) : "memory");
+}
+
+// A float no larger than the finite double x > 0 (its exponent and top mantissa
+// bits), or -1 when x is outside the normal float range.  Integer pipe only.
+__device__ __forceinline__ float f32_below(double x) {
+    const unsigned long long b = f64_bits(x) & 0x7fffffffffffffffull;
+    const int e = (int)(b >> 52) - 1023;
+    if (e < -125 || e > 126) return -1.0f;
+    return __uint_as_float((unsigned)((e + 127) << 23) | (unsigned)((b >> 29) & 0x7fffffu));
+}
+
+// A float no smaller than |x| for a finite double, or -1 out of range.
+__device__ __forceinline__ float f32_above(double x) {
+    const float f = f32_below(x);
+    return f < 0.0f ? f : __uint_as_float(__float_as_uint(f) + 1u);
+}
+
+// True when a coordinate with entry g and diagonal gss surely scores below
+// the candidate key kb (a non-negative double's bits): |g| / sqrt(gss)
+// bounded above in FP32 with a margin of 2^-18 (the rounding of the exact
+// score, the truncations and rsqrtf's error are far smaller).  False means
+// "maybe not": the caller decides exactly.
+__device__ __forceinline__ bool surely_below(double g, double gss, unsigned long long kb) {
+    if (kb == 0ull || (f64_bits(gss) >> 63)) return false;
+    const float ga = f32_above(g), gd = f32_below(gss), bb = f32_below(f64_from_bits(kb));
+    if (ga < 0.0f || gd <= 0.0f || bb <= 0.0f) return false;
+    return ga * rsqrtf(gd) * (1.0f + 0x1p-18f) < bb;
+}
+
+// Partner search of row x (held by this CTA) over the active candidates but
+// `skip1`, `skip2` and x itself, by the warps [w0, w0 + nw) (thread index
+// tid - 32 w0 of 32 nw); each warp's best goes to wb[warp - w0].
+__device__ __forceinline__ void dsm_score_row(const double *Gx, const double *Mx, const double *w,
+                                              const uint32_t *mask, int c, int x, int skip1, int skip2,
+                                              int w0, int nw, Cand *wb) {
+    const int t = threadIdx.x - 32 * w0;
+    Cand best = cand_none();
+    for (int y = t; y < c; y += 32 * nw) {
+        if (y == x || y == skip1 || y == skip2 || !is_active(mask, y)) continue;
+        cand_merge(best, cand_make(Gx[y], Mx[y], w[y], y));
+    }
+    warp_argmax_to(best, &wb[t >> 5]);
+}
+
+// Best of n (<= 32) candidates, in every lane of the calling warp.
+__device__ __forceinline__ Cand dsm_best_of(const Cand *wb, int n) {
+    const int lane = threadIdx.x & 31;
+    return warp_argmax(lane < n ? wb[lane] : cand_none());
+}
+
+__global__ void __cluster_dims__(DSM_CL, 1, 1) __launch_bounds__(DSM_THREADS, 1)
+k_select_dsm(const int64_t *coff, const int32_t *members, const int64_t *goff, const double *Gall,
+             const double *Mall, const int64_t *roff, uint64_t seed, int64_t stage, RotRec *rec,
+             Rot2 *lvlrot, int32_t *lvl_off, int32_t *nlev, int32_t *elimflag,
+             const int32_t *order, const uint64_t *useed, const int32_t *ords) {
+    namespace cg = cooperative_groups;
+    cg::cluster_group cluster = cg::this_cluster();
+    extern __shared__ double sh[];
+    const int rank = (int)cluster.block_rank();
+    const int64_t q = blockIdx.x / DSM_CL;
+    const int64_t u = order ? order[q] : q;
+    const int64_t base = coff[u];
+    const int c = (int)(coff[u + 1] - base);
+    const int64_t r0 = roff[u];
+    const int e = (int)(roff[u + 1] - r0);
+    const int R = (c + DSM_CL - 1) / DSM_CL;
+    const int row0 = rank * R;
+    const int nrow = max(0, min(c, row0 + R) - row0);
+    const double *G = Gall + goff[u];
+    const double *M = Mall + goff[u];
+    double *Gs = sh;                          // R x c, this CTA's rows of G
+    double *Ms = Gs + (size_t)R * c;          // R x c, of M
+    double *gd = Ms + (size_t)R * c;
+    double *md = gd + c;
+    double *w = md + c;
+    uint64_t *draws = (uint64_t *)(w + c);    // e + 1
+    const int nwords = (c + 31) / 32;
+    uint32_t *mask = (uint32_t *)(draws + e + 1);
+    int32_t *lvl = (int32_t *)(mask + nwords);
+    int32_t *lcnt = lvl + c;                  // e + 2 counters
+    __shared__ DsmMail mail[2];               // by step parity
+    __shared__ Cand wb[DSM_WARPS];            // per-warp bests
+    __shared__ Cand spec[2];                  // partner searches of a1, a2
+    __shared__ int s_a[2], s_le, s_ip, s_maxlev;
+    __shared__ double s_c, s_s, s_blk[4];
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+
+    for (int64_t x = tid; x < (int64_t)nrow * c; x += DSM_THREADS) {
+        Gs[x] = G[(int64_t)row0 * c + x];
+        Ms[x] = M[(int64_t)row0 * c + x];
+    }
+    for (int a = tid; a < c; a += DSM_THREADS) {
+        const double g = G[(int64_t)a * c + a];
+        gd[a] = g;
+        md[a] = M[(int64_t)a * c + a];
+        w[a] = g > 0.0 ? __ddiv_rn(1.0, __dsqrt_rn(g)) : 0.0;
+        lvl[a] = 0;
+    }
+    for (int wi = tid; wi < nwords; wi += DSM_THREADS) {
+        const int rem = c - wi * 32;
+        mask[wi] = rem >= 32 ? 0xffffffffu : ((1u << rem) - 1u);
+    }
+    for (int t = tid; t < e; t += DSM_THREADS)
+        draws[t] = draw(useed ? useed[u] : seed, stage, useed ? 0 : (ords ? ords[u] : u), t);
+    for (int x = tid; x < e + 2; x += DSM_THREADS) lcnt[x] = 0;
+    __syncthreads();
+    int i0 = 0;
+    if (tid == 0) {
+        s_maxlev = 0;
+        s_a[0] = s_a[1] = -1;
+        if (e > 1) {
+            const int64_t p = (int64_t)__umul64hi(draws[1], (uint64_t)(c - 1));
+            s_a[0] = select_bit(mask, nwords, p, -1);
+            s_a[1] = select_bit(mask, nwords, p + 1, -1);
+        }
+        s_ip = e > 0 ? select_bit(mask, nwords, (int64_t)__umul64hi(draws[0], (uint64_t)c), -1) : 0;
+    }
+    __syncthreads();
+    i0 = s_ip < 0 || s_ip >= c ? 0 : s_ip;
+    // every CTA's shared memory is set before the first remote store
+    cluster.sync();
+    // the first pivot's partner, searched in full by the CTA holding its row
+    if (e > 0 && rank == i0 / R) {
+        dsm_score_row(Gs + (size_t)(i0 - row0) * c, Ms + (size_t)(i0 - row0) * c, w, mask, c, i0, -1, -1,
+                      0, DSM_WARPS, wb);
+        __syncthreads();
+        if (wid == 0) {
+            const Cand b = dsm_best_of(wb, DSM_WARPS);
+            if (lane < DSM_CL) {
+                DsmMail *dst = cluster.map_shared_rank(&mail[0], lane);
+                dst->g = b.g;
+                dst->m = b.m;
+                dst->j = b.idx;
+            }
+        }
+    }
+    cluster.sync();
+
+    // rotation task of this thread: G or M, one of the CTA's rows
+    const int task = tid - DSM_ROT_T0;
+    const bool has_task = task >= 0 && task < 2 * nrow;
+    const int ly = has_task ? (task < nrow ? task : task - nrow) : 0;
+    const int y = row0 + ly;
+    double *Xs = (has_task && task >= nrow) ? Ms : Gs;
+    double *Xr = Xs + (size_t)ly * c;
+
+    int i = i0, pi = 0, pj = 0;   // this step's pivot; the previous step's pair
+    for (int t = 0; t < e; ++t) {
+        const int par = t & 1;
+        const DsmMail mv = mail[par];
+        // at least two coordinates are active at every step (e_u <= c_u - 1);
+        // the clamps only keep a corrupted state from indexing out of bounds
+        if (i < 0 || i >= c) i = 0;
+        const int j = (mv.j >= 0 && mv.j < c && mv.j != i) ? mv.j : (i == 0 ? 1 : 0);
+        const bool more = t + 1 < e;
+        const int a1 = s_a[0], a2 = s_a[1];
+        // ---- A
+        const bool live = has_task && y != i && y != j && is_active(mask, y);
+        double xa = 0.0, xb = 0.0;
+        if (live) {
+            xa = Xr[i];
+            xb = Xr[j];
+        }
+        if (wid == 0 || wid == DSM_S_WARP) {
+            if (lane == 0) {
+                double cc, ss;
+                jacobi2(gd[i], mv.g, gd[j], cc, ss);
+                if (wid == 0) s_c = cc;
+                else s_s = ss;
+            }
+        } else if (wid == DSM_W_WARP) {
+            // the previous step's new weights (the eliminated one's is never
+            // read again), before the partner searches read them
+            if (t > 0 && lane < 2) {
+                const double g = s_blk[lane];
+                w[lane == 0 ? pi : pj] = g > 0.0 ? __ddiv_rn(1.0, __dsqrt_rn(g)) : 0.0;
+            }
+            __syncwarp();
+            named_arrive(3, 32 * (1 + 2 * DSM_SCORE_WARPS));
+        } else if (wid <= 2 * DSM_SCORE_WARPS) {
+            named_sync(3, 32 * (1 + 2 * DSM_SCORE_WARPS));
+            const int k = (wid - 1) / DSM_SCORE_WARPS;      // 0: a1, 1: a2
+            const int w0 = 1 + k * DSM_SCORE_WARPS;
+            const int a = k == 0 ? a1 : a2;
+            const bool mine = more && a >= 0 && a < c && a != i && a != j && rank == a / R;
+            if (mine) {
+                dsm_score_row(Gs + (size_t)(a - row0) * c, Ms + (size_t)(a - row0) * c, w, mask, c, a, i, j,
+                              w0, DSM_SCORE_WARPS, wb + w0);
+                named_sync(1 + k, 32 * DSM_SCORE_WARPS);
+                if (wid == w0) {
+                    const Cand b = dsm_best_of(wb + w0, DSM_SCORE_WARPS);
+                    if (lane == 0) spec[k] = b;
+                }
+            }
+        }
+        __syncthreads();
+        const double cc = s_c, ss = s_s;
+        // ---- B
+        if (wid == 0 && lane < 4) {
+            // the new diagonal entries of the 2 x 2 blocks: lanes 0, 1 for G
+            // (a', d'), lanes 2, 3 for M; each is rot_block's chain written as
+            // r1 = fma(p, a, q b), r2 = fma(p, b, q d), v = fma(r1, p, r2 q)
+            // with (p, q) = (c, -s) for a' and (s, c) for d'
+            const bool isM = lane >= 2;
+            const double a = isM ? md[i] : gd[i], b = isM ? mv.m : mv.g, d = isM ? md[j] : gd[j];
+            const double p = (lane & 1) ? ss : cc, qq = (lane & 1) ? cc : -ss;
+            const double r1 = __fma_rn(p, a, __dmul_rn(qq, b));
+            const double r2 = __fma_rn(p, b, __dmul_rn(qq, d));
+            s_blk[lane] = __fma_rn(r1, p, __dmul_rn(r2, qq));
+        }
+        if (wid == 0) {
+            __syncwarp();
+            if (lane == 0) {
+                gd[i] = s_blk[0];
+                gd[j] = s_blk[1];
+                md[i] = s_blk[2];
+                md[j] = s_blk[3];
+                const double di = __dsub_rn(gd[i], __dmul_rn(md[i], md[i]));
+                const double dj = __dsub_rn(gd[j], __dmul_rn(md[j], md[j]));
+                const int le = di < dj ? i : j;
+                const int L = 1 + max(lvl[i], lvl[j]);
+                lvl[i] = L;
+                lvl[j] = L;
+                s_maxlev = max(s_maxlev, L);
+                if (rank == 0) rec[r0 + t] = RotRec{i, j, le, L, cc, ss};
+                mask[le >> 5] &= ~(1u << (le & 31));
+                s_le = le;
+                s_ip = le <= a1 ? a2 : a1;
+            }
+        }
+        if (live && !(is_zero(xa) && is_zero(xb))) {
+            double na, nb;
+            rot_pair(cc, ss, xa, xb, na, nb);
+            Xr[i] = na;
+            Xr[j] = nb;
+            // the mirrored entries: rows i and j at column y
+            const int oi = i / R, oj = j / R;
+            cluster.map_shared_rank(Xs, oi)[(size_t)(i - oi * R) * c + y] = na;
+            cluster.map_shared_rank(Xs, oj)[(size_t)(j - oj * R) * c + y] = nb;
+        }
+        __syncthreads();
+        // ---- C
+        const int le = s_le, sv = le == i ? j : i;   // eliminated, survivor
+        const int ip = s_ip < 0 || s_ip >= c ? 0 : s_ip;
+        if (more && ip == sv) {
+            // the survivor is the next pivot: its row was rotated in every
+            // CTA, so its partner is searched in full after the stores land
+            cluster.sync();
+            if (rank == ip / R) {
+                dsm_score_row(Gs + (size_t)(ip - row0) * c, Ms + (size_t)(ip - row0) * c, w, mask, c, ip, -1, -1,
+                              0, DSM_WARPS, wb);
+                __syncthreads();
+                if (wid == 0) {
+                    const Cand b = dsm_best_of(wb, DSM_WARPS);
+                    if (lane < DSM_CL) {
+                        DsmMail *dst = cluster.map_shared_rank(&mail[par ^ 1], lane);
+                        dst->g = b.g;
+                        dst->m = b.m;
+                        dst->j = b.idx;
+                    }
+                }
+            }
+        } else if (more && wid == 0 && rank == ip / R) {
+            // the partner search of row ip over everything but i and j, merged
+            // with the survivor's rotated entry
+            Cand b = spec[ip == a1 ? 0 : 1];
+            const double gv = Gs[(size_t)(ip - row0) * c + sv];
+            const double mvv = Ms[(size_t)(ip - row0) * c + sv];
+            const double gss = gd[sv];
+            bool take;
+            if (b.idx == 0x7fffffff) {
+                take = true;                            // no other candidate
+            } else if (is_zero(gv) || surely_below(gv, gss, b.key)) {
+                take = is_zero(gv) && b.key == 0ull && sv < b.idx;   // a zero entry scores +0
+            } else {
+                const double ws = gss > 0.0 ? __ddiv_rn(1.0, __dsqrt_rn(gss)) : 0.0;
+                const Cand cs = cand_make(gv, mvv, ws, sv);
+                take = cand_better(cs.key, cs.idx, b.key, b.idx);
+            }
+            if (take) {
+                b.idx = sv;
+                b.g = gv;
+                b.m = mvv;
+            }
+            if (lane < DSM_CL) {
+                DsmMail *dst = cluster.map_shared_rank(&mail[par ^ 1], lane);
+                dst->g = b.g;
+                dst->m = b.m;
+                dst->j = b.idx;
+            }
+        }
+        cluster_arrive_release();
+        if (wid == DSM_NEXT_WARP && lane == 0 && t + 2 < e) {
+            // the two possible pivots of step t + 2
+            const int64_t p = (int64_t)__umul64hi(draws[t + 2], (uint64_t)(c - t - 2));
+            s_a[0] = select_bit(mask, nwords, p, -1);
+            s_a[1] = select_bit(mask, nwords, p + 1, -1);
+        }
+        __syncwarp();
+        cluster_wait_acquire();
+        __syncthreads();
+        pi = i;
+        pj = j;
+        i = ip;
+    }
+    if (rank == 0)
+        finish_cluster(u, r0, e, s_maxlev, members, base, rec, lcnt, lvlrot, lvl_off, nlev, elimflag, stage);
+}
+
 }  // namespace
 
 pmmf_status gram_blocks(const StageClusters &cls, GramBlocks &gb, cudaStream_t st, int64_t total) {
@@ -961,6 +1334,17 @@ pmmf_status gram_and_select(const Csr &A, const int32_t *act_ids, const int32_t 
     return select_stage(cls, cmax, gb, seed, stage, rot, elimflag, st, order, useed, status, ords);
 }
 
+namespace {
+
+// Shared memory of k_select_dsm for clusters of up to cmax coordinates.
+size_t dsm_smem(int64_t cmax) {
+    const size_t R = (size_t)((cmax + DSM_CL - 1) / DSM_CL);
+    return sizeof(double) * (2 * R * (size_t)cmax + 3 * (size_t)cmax) + sizeof(uint64_t) * (size_t)(cmax + 1) +
+           sizeof(uint32_t) * (size_t)((cmax + 31) / 32) + sizeof(int32_t) * (size_t)(2 * cmax + 2);
+}
+
+}  // namespace
+
 pmmf_status select_stage(const StageClusters &cls, int64_t cmax, GramBlocks &gb, uint64_t seed,
                          int64_t stage, StageRotations &rot, int32_t *elimflag, cudaStream_t st,
                          const int32_t *order, const uint64_t *useed, unsigned *status,
@@ -1003,6 +1387,26 @@ pmmf_status select_stage(const StageClusters &cls, int64_t cmax, GramBlocks &gb,
         }
     }
     prof_begin(KF_SELECT, st);
+    // The search by thread-block clusters holding G and M in shared memory
+    // (PMMF_TUNE_SELECT_DSM = 2) for stages whose clusters fit; measured on
+    // GB300 it is slower than the one-CTA search on the late stages of the
+    // kNN workload (clusters ~256: ~7,300 against ~7,100 cycles per step, the
+    // angle's dependent FP64 chain and the per-step cluster barrier on the
+    // critical path), so it runs only when asked for.
+    {
+        const int dsm = tuned(TUNE_SELECT_DSM, cmax, 1);
+        const size_t need = dsm_smem(cmax);
+        const bool fits = need <= 225 * 1024 && 2 * ((cmax + DSM_CL - 1) / DSM_CL) <= DSM_ROT_N;
+        if (fits && m > 0 && m <= INT32_MAX / DSM_CL && dsm == 2) {
+            PMMF_CUDA_TRY(cudaFuncSetAttribute(k_select_dsm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)need));
+            k_select_dsm<<<(unsigned)(m * DSM_CL), DSM_THREADS, need, st>>>(
+                cls.coff.p, cls.members.p, goff.p, G.p, M.p, rot.roff.p, seed, stage, rot.rec.p, rot.lvl.p,
+                rot.lvl_off.p, rot.nlev.p, elimflag, order, useed, ords);
+            prof_end(KF_SELECT, st, 0.0, sel_flops);
+            PMMF_TRY(launched("select"));
+            return PMMF_OK;
+        }
+    }
     // 256 threads (128 column threads) up to 512 coordinates, 512 threads
     // (384 column threads) up to 1,536, the generic kernel beyond.  The wide
     // CTA spreads a step's loads and FP64 work over 12 column warps; measured

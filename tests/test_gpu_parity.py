@@ -365,11 +365,19 @@ def test_wide_search_cta_clusters_above_512():
 def test_generic_search_one_cluster_above_1536():
     """One cluster of 2,048 coordinates (no points: one cluster per stage):
     the first stage runs the generic k = 2 search kernel (beyond 1,536
-    coordinates), later stages the 512- and 256-thread ones."""
+    coordinates), later stages the 512- and 256-thread ones; U, U^T and A~
+    applied bit for bit."""
+    import torch
     a = I.knn_laplacian(2048, seed=14)
     g, o = factor_both(a, coords=None, k=2, eta=0.5, cluster_size=2048, core_size=64, seed=4)
     assert len(o.stages[0].offsets) == 2 and o.stages[0].active == 2048
     assert_same_factorization(g, o)
+    # the apply reads a cluster this large's rotations from global memory
+    # (they are staged in shared memory up to 1,024 coordinates)
+    x = np.random.default_rng(2).standard_normal((a.n, 8))
+    xd = torch.from_numpy(x).cuda()
+    for op in (O.OP_U, O.OP_UT, O.OP_A):
+        assert np.array_equal(g.apply(op, xd).cpu().numpy(), o.apply(op, x)), op
 
 
 @pytest.mark.parametrize("kernel", [1, 2])
@@ -398,6 +406,82 @@ def test_update_kernels_agree_with_oracle(kernel, case):
         assert L.pmmf_set_tuning(pm.TUNE_PARAMS["rows_kernel"], 1 << 30, kernel) == 0
         g, o = factor_both(a, eta=0.5, seed=6, **kw)
         assert_same_factorization(g, o)
+    finally:
+        L.pmmf_clear_tuning()
+        pm.apply_tuning(pm.TUNING_PATH)
+
+
+@pytest.mark.parametrize("mode", [1, 2])
+@pytest.mark.parametrize("case", ["knn-c256", "knn-c300", "poisson-bricks", "small-clusters", "many-clusters"])
+def test_search_by_thread_block_clusters_agrees_with_oracle(mode, case):
+    """The k = 2 search with G and M in global memory, one CTA per cluster (1),
+    and held row-sliced in the shared memory of a thread-block cluster of 8
+    CTAs (2), forced on every stage: the oracle's factorization bit for bit.
+    Clusters of ~256 and of up to 306 (39 rows per CTA), given bricks,
+    clusters of ~8 (CTAs without rows) and a stage of 256 clusters (more
+    thread-block clusters than can be resident at once)."""
+    pm = gpu_lib()
+    L = pm.load()
+    if case == "knn-c256":
+        a, kw = I.knn_laplacian(4096, seed=3), dict(cluster_size=256, core_size=64)
+    elif case == "knn-c300":
+        a, kw = I.knn_laplacian(4500, seed=4), dict(cluster_size=265, core_size=100)
+    elif case == "poisson-bricks":
+        a, kw = I.poisson3d(16, seed=4), dict(cluster_size=128, core_size=64,
+                                               labels=I.grid_bricks(16, 16, 16, 8, 8, 2))
+    elif case == "small-clusters":
+        a, kw = I.knn_laplacian(1200, seed=9), dict(cluster_size=8, core_size=30)
+    else:
+        a, kw = I.knn_laplacian(65536, seed=1), dict(cluster_size=256, core_size=256, max_stages=1)
+    try:
+        assert L.pmmf_set_tuning(pm.TUNE_PARAMS["select_dsm"], 1 << 30, mode) == 0
+        g, o = factor_both(a, k=2, eta=0.5, seed=6, **kw)
+        # every stage's clusters within the shared-memory limit of mode 2
+        # (up to 318 coordinates: 40 rows of G and M per CTA)
+        assert max(int(np.diff(st.offsets).max()) for st in o.stages) <= 318
+        if case == "knn-c300":
+            assert np.diff(o.stages[0].offsets).max() > 300
+        assert_same_factorization(g, o)
+    finally:
+        L.pmmf_clear_tuning()
+        pm.apply_tuning(pm.TUNING_PATH)
+
+
+@pytest.mark.parametrize("mode", [1, 2])
+@pytest.mark.parametrize("case", ["knn-k2", "knn-k3", "poisson-bricks"])
+@pytest.mark.parametrize("nrhs", [1, 3, 8])
+def test_apply_passes_agree_with_oracle(mode, case, nrhs):
+    """The apply's rotation passes as one launch per stage (1) and as one
+    cooperative launch per pass with a grid barrier between stages (2),
+    forced: U, U^T, H, A~ bit for bit with the oracle, A~^-1 to the inverse
+    ops' tolerance, for 1, 3 and 8 right-hand sides; the PCG solve (its
+    iteration replayed as a CUDA graph) agrees with the oracle's."""
+    import torch
+    pm = gpu_lib()
+    L = pm.load()
+    if case == "knn-k2":
+        a, kw = I.knn_laplacian(5000, seed=2), dict(k=2, cluster_size=200, core_size=64)
+    elif case == "knn-k3":
+        a, kw = I.knn_laplacian(3000, seed=5), dict(k=3, cluster_size=150, core_size=60)
+    else:
+        a, kw = I.poisson3d(16, seed=4), dict(k=2, cluster_size=128, core_size=64,
+                                               labels=I.grid_bricks(16, 16, 16, 8, 8, 2))
+    try:
+        assert L.pmmf_set_tuning(pm.TUNE_PARAMS["apply_fused"], 1 << 30, mode) == 0
+        g, o = factor_both(a, eta=0.5, seed=7, **kw)
+        x = np.random.default_rng(nrhs).standard_normal((a.n, nrhs))
+        xd = torch.from_numpy(x).cuda()
+        for op in (O.OP_U, O.OP_UT, O.OP_H, O.OP_A):
+            assert np.array_equal(g.apply(op, xd).cpu().numpy(), o.apply(op, x)), op
+        want = o.apply(O.OP_A_INV, x)
+        got = g.apply(O.OP_A_INV, xd).cpu().numpy()
+        assert np.abs(got - want).max() <= 1e-10 * np.abs(want).max()
+        if nrhs == 8 and case != "knn-k3":
+            st, xs, iters, rel = g.solve(a, xd, rtol=1e-8, maxit=500)
+            ost, ox, oit, orel = o.pcg(a, x, 1e-8, 500)
+            assert st == 0 and ost == 0
+            assert (rel <= 1e-8 * 1.5).all()
+            assert (np.abs(iters - oit) <= 2).all(), (iters, oit)
     finally:
         L.pmmf_clear_tuning()
         pm.apply_tuning(pm.TUNING_PATH)
