@@ -12,6 +12,7 @@
 #include <cooperative_groups.h>
 
 #include <algorithm>
+#include <climits>
 
 #include "common.cuh"
 #include "stage.cuh"
@@ -171,6 +172,92 @@ __global__ void k_assign(const int32_t *act, int64_t s, const int32_t *q, const 
     }
 }
 
+// Candidate centroids kept per warp by nearest_centroid (more: a full scan).
+constexpr int LL_CAND = 128;
+constexpr int LL_WARPS = 8;   // k_lloyd's blocks are 256 threads
+
+// Nearest centroid (squared integer distance, ties to the lower index) of the
+// point p of every live lane of a warp whose points are close together (all
+// 32 lanes call it).  Centroids that cannot be nearest to any point of the
+// warp's bounding box are skipped: with U the smallest, over the centroids, of
+// the largest squared distance from the box, a centroid whose smallest squared
+// distance from the box exceeds U is farther from every point of the box than
+// that centroid.  The candidates, in ascending index, therefore include every
+// nearest centroid of every point, ties included, and the strict comparison
+// in index order keeps the lowest: the result is the full scan's.  Squared
+// distances of 15-bit coordinates fit 32 bits.
+template <int DIM>
+__device__ __forceinline__ int64_t nearest_centroid(const int32_t (&p)[DIM], bool live, const int32_t *sc,
+                                                    int64_t m, int32_t *cand) {
+    const int lane = threadIdx.x & 31;
+    const unsigned full = 0xffffffffu;
+    int32_t lo[DIM], hi[DIM];
+    for (int d = 0; d < DIM; ++d) {
+        lo[d] = __reduce_min_sync(full, live ? p[d] : INT_MAX);
+        hi[d] = __reduce_max_sync(full, live ? p[d] : INT_MIN);
+    }
+    uint32_t U = 0xffffffffu;
+    for (int64_t t = lane; t < m; t += 32) {
+        uint32_t ub = 0;
+        for (int d = 0; d < DIM; ++d) {
+            const int32_t c = sc[t * DIM + d];
+            const int32_t z = max(abs(c - lo[d]), abs(c - hi[d]));
+            ub += (uint32_t)(z * z);
+        }
+        U = min(U, ub);
+    }
+    U = __reduce_min_sync(full, U);
+    int n = 0;
+    for (int64_t t0 = 0; t0 < m; t0 += 32) {
+        const int64_t t = t0 + lane;
+        bool ok = false;
+        if (t < m) {
+            uint32_t lb = 0;
+            for (int d = 0; d < DIM; ++d) {
+                const int32_t c = sc[t * DIM + d];
+                const int32_t z = max(0, max(lo[d] - c, c - hi[d]));
+                lb += (uint32_t)(z * z);
+            }
+            ok = lb <= U;
+        }
+        const unsigned b = __ballot_sync(full, ok);
+        const int at = n + __popc(b & ((1u << lane) - 1u));
+        if (ok && at < LL_CAND) cand[at] = (int32_t)t;
+        n += __popc(b);
+    }
+    __syncwarp();
+    uint32_t best = 0xffffffffu;
+    int64_t bt = 0;
+    if (n <= LL_CAND) {
+        for (int k = 0; k < n; ++k) {
+            const int64_t t = cand[k];
+            uint32_t dd = 0;
+            for (int d = 0; d < DIM; ++d) {
+                const int32_t z = p[d] - sc[t * DIM + d];
+                dd += (uint32_t)(z * z);
+            }
+            if (dd < best) {
+                best = dd;
+                bt = t;
+            }
+        }
+    } else {
+        for (int64_t t = 0; t < m; ++t) {
+            uint32_t dd = 0;
+            for (int d = 0; d < DIM; ++d) {
+                const int32_t z = p[d] - sc[t * DIM + d];
+                dd += (uint32_t)(z * z);
+            }
+            if (dd < best) {
+                best = dd;
+                bt = t;
+            }
+        }
+    }
+    __syncwarp();   // the list is reused by the warp's next points
+    return bt;
+}
+
 // All Lloyd iterations in one cooperative launch (every block resident):
 // per iteration the accumulators are cleared, every point is assigned to its
 // nearest centroid (as k_assign) and, except after the last iteration, the
@@ -184,9 +271,11 @@ __global__ void k_assign(const int32_t *act, int64_t s, const int32_t *q, const 
 // entry).  The last iteration's counts are in buffer (iters - 1) % 3.
 // Points are taken in Morton order (order[r'] = the r'-th active point's id,
 // pos[id] = its active index), so a warp's points are neighbours that mostly
-// share their nearest centroid: lanes with the same centroid add their
-// coordinates and count with one atomic each (integer sums, so the order of
-// the additions does not matter).
+// share their nearest centroid: the warp searches only the centroids that
+// can be nearest to its points' bounding box (nearest_centroid), and lanes
+// with the same centroid add their coordinates and count with one atomic
+// each (integer sums, so the order of the additions does not matter).
+// Shared memory: the centroids, then LL_CAND candidate slots per warp.
 template <int DIM>
 __global__ void k_lloyd(const int32_t *order, const int32_t *pos, int64_t s, const int32_t *q,
                         const int32_t *cen, int64_t m, int iters, int32_t *label,
@@ -215,30 +304,27 @@ __global__ void k_lloyd(const int32_t *order, const int32_t *pos, int64_t s, con
             }
         }
         __syncthreads();
-        for (int64_t r = gt; r < s; r += gs) {
-            const int32_t g = order[r];
+        const int lane = threadIdx.x & 31;
+        int32_t *cand = (int32_t *)(sc + m * DIM) + (threadIdx.x >> 5) * LL_CAND;
+        for (int64_t r0 = gt - lane; r0 < s; r0 += gs) {
+            const int64_t r = r0 + lane;
+            const bool live = r < s;
+            const int32_t g = live ? order[r] : 0;
             int32_t p[DIM];
-            for (int d = 0; d < DIM; ++d) p[d] = q[(int64_t)g * DIM + d];
-            uint32_t best = 0xffffffffu;
-            int64_t bt = 0;
-            for (int64_t t = 0; t < m; ++t) {
-                uint32_t dd = 0;
-                for (int d = 0; d < DIM; ++d) {
-                    const int32_t z = p[d] - sc[t * DIM + d];
-                    dd += (uint32_t)(z * z);
-                }
-                if (dd < best) { best = dd; bt = t; }
-            }
-            label[pos[g]] = (int32_t)bt;
+            for (int d = 0; d < DIM; ++d) p[d] = live ? q[(int64_t)g * DIM + d] : 0;
+            const int64_t bt = nearest_centroid<DIM>(p, live, sc, m, cand);
             // quantized coordinates are below 2^16, so 32 of them sum in 32 bits
-            const unsigned live = __activemask();
-            const unsigned grp = __match_any_sync(live, (int)bt);
-            const bool leader = (threadIdx.x & 31) == __ffs(grp) - 1;
-            for (int d = 0; d < DIM; ++d) {
-                const unsigned v = __reduce_add_sync(grp, (unsigned)p[d]);
-                if (leader) atomicAdd(&sacc[bt * DIM + d], (unsigned long long)v);
+            const unsigned lm = __ballot_sync(0xffffffffu, live);
+            if (live) {
+                label[pos[g]] = (int32_t)bt;
+                const unsigned grp = __match_any_sync(lm, (int)bt);
+                const bool leader = lane == __ffs(grp) - 1;
+                for (int d = 0; d < DIM; ++d) {
+                    const unsigned v = __reduce_add_sync(grp, (unsigned)p[d]);
+                    if (leader) atomicAdd(&sacc[bt * DIM + d], (unsigned long long)v);
+                }
+                if (leader) atomicAdd(&cacc[bt], (unsigned long long)__popc(grp));
             }
-            if (leader) atomicAdd(&cacc[bt], (unsigned long long)__popc(grp));
         }
         grid.sync();
     }
@@ -548,6 +634,7 @@ pmmf_status partition_stage(const PartitionIn &in, int64_t m, int iters, StageCl
     // Lloyd iterations
     PMMF_TRY(label.alloc(s, st));
     size_t sh = sizeof(int32_t) * (size_t)(m * dim);
+    const size_t sh_lloyd = sh + sizeof(int32_t) * LL_WARPS * LL_CAND;
     if (sh > 200 * 1024) {
         set_error("too many clusters for the assignment kernel");
         return PMMF_ERR_UNSUPPORTED;
@@ -559,13 +646,13 @@ pmmf_status partition_stage(const PartitionIn &in, int64_t m, int iters, StageCl
     // one cooperative launch for all iterations when every block fits at once
     const void *lloyd = dim == 1 ? (const void *)k_lloyd<1> : dim == 2 ? (const void *)k_lloyd<2>
                                                                    : (const void *)k_lloyd<3>;
-    if (sh > 48 * 1024)
-        PMMF_CUDA_TRY(cudaFuncSetAttribute(lloyd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh));
+    if (sh_lloyd > 48 * 1024)
+        PMMF_CUDA_TRY(cudaFuncSetAttribute(lloyd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh_lloyd));
     int dev = 0, nsm = 0, per_sm = 0, coop = 0;
     PMMF_CUDA_TRY(cudaGetDevice(&dev));
     PMMF_CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
     PMMF_CUDA_TRY(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev));
-    PMMF_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, lloyd, 256, sh));
+    PMMF_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, lloyd, 32 * LL_WARPS, sh_lloyd));
     DBuf<unsigned long long> lsum, lcnt;
     const unsigned long long *fcnt = cnt.p;   // the last assignment's counts
     if (coop && per_sm > 0) {
@@ -583,7 +670,7 @@ pmmf_status partition_stage(const PartitionIn &in, int64_t m, int iters, StageCl
         unsigned long long *a_sum = lsum.p, *a_cnt = lcnt.p;
         void *args[] = {&a_order, &a_pos, &a_s, &a_q, &a_cen, &a_m, &a_it, &a_label, &a_sum, &a_cnt};
         prof_begin(KF_PARTITION, st);
-        PMMF_CUDA_TRY(cudaLaunchCooperativeKernel(lloyd, dim3(g), dim3(256), args, sh, st));
+        PMMF_CUDA_TRY(cudaLaunchCooperativeKernel(lloyd, dim3(g), dim3(32 * LL_WARPS), args, sh_lloyd, st));
         prof_end(KF_PARTITION, st, (double)iters * (double)s * (8.0 + 4.0 * dim),
                  3.0 * dim * (double)iters * (double)s * (double)m);
         PMMF_TRY(launched("lloyd"));
