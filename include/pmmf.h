@@ -466,17 +466,22 @@ pmmf_status pmmf_get_stage_matrix(const pmmf_handle *f, int p, int64_t *rowptr_n
  * cooperative launch per pass with a grid barrier between stages, where the
  * device supports cooperative launches and the right-hand sides fit one pass
  * (else 1); both give the same bits; max_size is the largest cluster of the
- * factorization).
+ * factorization), PMMF_TUNE_SELECT_BLOCKS (CTAs of the k = 2 search's
+ * 256-thread kernel per SM, 2, 3 or 4, its registers capped to fit; without
+ * a setting 4 for clusters of up to 256 coordinates and 3 up to 512 when a
+ * stage has at least 4 and 6 times as many clusters as SMs, else 2; all give
+ * the same bits).
  * A value
  * applies to launches whose largest cluster has at most max_size coordinates
  * and no smaller bucket matches; shared-memory limits still halve the row and
  * Gram warps when needed.  Process wide; INVALID_ARG for an unknown param or
- * a value outside 1..32 (outside {8, 16} for the search; any positive value for
+ * a value outside 1..32 (outside {8, 16} for the search warps, {1, 2} for the
+ * kernel choices, 2..4 for the search's CTAs per SM; any positive value for
  * the reach threshold). */
 enum { PMMF_TUNE_ROWS_WARPS = 0, PMMF_TUNE_GRAM_WARPS = 1, PMMF_TUNE_SELECT_WARPS = 2,
        PMMF_TUNE_PASS1_ESTIMATE = 3, PMMF_TUNE_REACH_CLUSTERS = 4, PMMF_TUNE_ROWS_KERNEL = 5,
        PMMF_TUNE_DENSE_TILES = 6, PMMF_TUNE_SELECT_DSM = 7,
-       PMMF_TUNE_APPLY_FUSED = 8 };
+       PMMF_TUNE_APPLY_FUSED = 8, PMMF_TUNE_SELECT_BLOCKS = 9 };
 pmmf_status pmmf_set_tuning(int param, int64_t max_size, int value);
 void pmmf_clear_tuning(void);
 

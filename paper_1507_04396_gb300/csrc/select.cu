@@ -539,8 +539,8 @@ __device__ __forceinline__ Cand block_best(const Cand *wb) {
 // and 3 (FP64 warps arrive with the next (i, j), column warps wait); FP64
 // warps also meet at named barrier 1.  The arithmetic, and so every bit, is
 // k_select's.
-template <int KPT, int NT>
-__global__ void __launch_bounds__(NT, NT <= 256 ? 2 : 1)
+template <int KPT, int NT, int MINB = (NT <= 256 ? 2 : 1)>
+__global__ void __launch_bounds__(NT, MINB)
 k_select_fast(const int64_t *coff, const int32_t *members, const int64_t *goff, double *Gall,
               double *Mall, const int64_t *roff, uint64_t seed, int64_t stage, RotRec *rec,
               Rot2 *lvlrot, int32_t *lvl_off, int32_t *nlev, int32_t *elimflag,
@@ -1426,7 +1426,28 @@ pmmf_status select_stage(const StageClusters &cls, int64_t cmax, GramBlocks &gb,
                                            rot.nlev.p, elimflag, order, useed, ords);
         return PMMF_OK;
     };
-    if (fits_fast && sw == 8 && kpt <= 1) PMMF_TRY(launch(k_select_fast<1, 256>, 256));
+    // A stage with many more clusters than SMs is bound by throughput, not by
+    // one cluster's chain: fewer registers per thread fit more CTAs per SM
+    // (PMMF_TUNE_SELECT_BLOCKS: 2, 3 or 4 CTAs of 256 threads per SM).
+    // Measured on GB300 (128^3 Poisson, 8,192 and 4,096 clusters of 256):
+    // 4 CTAs per SM 13.2 -> 9.4 and 7.0 -> 4.9 ms per stage; the largest
+    // instantiation spills at 3 per SM and gains only with thousands of
+    // clusters (2,048: 3.78 -> 3.53 ms), loses on fewer (kNN stages).
+    int nsm = 152;
+    {
+        int dev = 0;
+        if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    }
+    const int occ = tuned(TUNE_SELECT_BLOCKS, cmax, 0);
+    const int minb = occ                         ? occ
+                     : kpt <= 2 && m >= 4 * nsm ? 4
+                     : kpt <= 4 && m >= 6 * nsm ? 3
+                                                : 2;
+    if (fits_fast && sw == 8 && kpt <= 1 && minb >= 3) PMMF_TRY(launch(k_select_fast<1, 256, 4>, 256));
+    else if (fits_fast && sw == 8 && kpt <= 2 && minb == 3) PMMF_TRY(launch(k_select_fast<2, 256, 3>, 256));
+    else if (fits_fast && sw == 8 && kpt <= 2 && minb == 4) PMMF_TRY(launch(k_select_fast<2, 256, 4>, 256));
+    else if (fits_fast && sw == 8 && kpt <= 4 && kpt > 2 && minb >= 3) PMMF_TRY(launch(k_select_fast<4, 256, 3>, 256));
+    else if (fits_fast && sw == 8 && kpt <= 1) PMMF_TRY(launch(k_select_fast<1, 256>, 256));
     else if (fits_fast && sw == 8 && kpt <= 2) PMMF_TRY(launch(k_select_fast<2, 256>, 256));
     else if (fits_fast && sw == 8 && kpt <= 4) PMMF_TRY(launch(k_select_fast<4, 256>, 256));
     else if (fits_fast && kpt512 <= 1) PMMF_TRY(launch(k_select_fast<1, 512>, 512));

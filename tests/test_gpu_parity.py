@@ -485,3 +485,27 @@ def test_apply_passes_agree_with_oracle(mode, case, nrhs):
     finally:
         L.pmmf_clear_tuning()
         pm.apply_tuning(pm.TUNING_PATH)
+
+
+@pytest.mark.parametrize("blocks", [3, 4])
+@pytest.mark.parametrize("case", ["c150", "c300", "c8"])
+def test_search_occupancy_variants_agree_with_oracle(blocks, case):
+    """The k = 2 search with its registers capped for 3 and 4 CTAs per SM
+    (the instantiations a stage with many clusters takes), forced on every
+    stage: the oracle's factorization bit for bit, for clusters of ~150
+    (two columns per thread), ~300 (four) and ~8 (one)."""
+    pm = gpu_lib()
+    L = pm.load()
+    if case == "c150":
+        a, kw = I.knn_laplacian(3000, seed=5), dict(cluster_size=150, core_size=60)
+    elif case == "c300":
+        a, kw = I.knn_laplacian(4800, seed=8), dict(cluster_size=300, core_size=100)
+    else:
+        a, kw = I.knn_laplacian(1200, seed=9), dict(cluster_size=8, core_size=30)
+    try:
+        assert L.pmmf_set_tuning(pm.TUNE_PARAMS["select_blocks"], 1 << 30, blocks) == 0
+        g, o = factor_both(a, k=2, eta=0.5, seed=6, **kw)
+        assert_same_factorization(g, o)
+    finally:
+        L.pmmf_clear_tuning()
+        pm.apply_tuning(pm.TUNING_PATH)
