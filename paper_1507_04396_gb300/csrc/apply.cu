@@ -461,8 +461,7 @@ int coop_per_sm(const void *kern, size_t sh, int *nsm) {
     if (cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev) != cudaSuccess) coop = 0;
     if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) n = 0;
     if (coop && n > 0 &&
-        (sh <= 48 * 1024 ||
-         cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh) == cudaSuccess) &&
+        allow_smem(kern, sh) == cudaSuccess &&
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, AP_THREADS, sh) != cudaSuccess)
         per_sm = 0;
     if (!coop) per_sm = 0;
@@ -565,8 +564,7 @@ pmmf_status apply_rotations(const ApplyStages &S, bool transpose, double *x, int
                                   : (nr == 8 ? k_apply_stage<false, 8> : nr == 1 ? k_apply_stage<false, 1>
                                                                        : k_apply_stage<false, 0>);
             prof_begin(KF_APPLY, st);
-            if (sh > 48 * 1024)
-                PMMF_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh));
+            PMMF_CUDA_TRY(allow_smem(kern, sh));
             kern<<<(unsigned)a.m, AP_THREADS, sh, st>>>(d, rcap, x, ld, r0, nr);
             prof_end(KF_APPLY, st, stage_bytes(a, nr), 0.0);
             PMMF_TRY(launched("apply_stage"));
@@ -643,8 +641,7 @@ pmmf_status invert_core_blocks(const double *core, int64_t nblk, int64_t bs, con
         set_error("core blocks too large to invert in shared memory");
         return PMMF_ERR_UNSUPPORTED;
     }
-    if (sh > 48 * 1024)
-        PMMF_CUDA_TRY(cudaFuncSetAttribute(k_gj_blocks, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh));
+    PMMF_CUDA_TRY(allow_smem(k_gj_blocks, sh));
     k_gj_blocks<<<(unsigned)nblk, 256, sh, st>>>(core, bs, bdim, inv, status);
     return launched("gj_blocks");
 }

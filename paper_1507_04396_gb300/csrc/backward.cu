@@ -548,8 +548,7 @@ pmmf_status apply_backward(const ApplyStages &S, const std::vector<const RotRec 
             if (a.nrot == 0) continue;
             if (K > 2) {
                 const size_t shk = backward_smem_k(a.cmax, a.cmax, K, cur);
-                if (shk > 48 * 1024)
-                    PMMF_CUDA_TRY(cudaFuncSetAttribute(k_backward_stage_k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shk));
+                PMMF_CUDA_TRY(allow_smem(k_backward_stage_k, shk));
                 k_backward_stage_k<<<(unsigned)a.m, BW_THREADS, shk, st>>>(
                     a.coff, a.members, a.roff, K, a.kidx, a.kkv, klvls[p], a.kO, a.nlev,
                     ck.p + coff_ck[p], prb.p, cur, acc, dt + toff[p] * per_rot);
@@ -557,8 +556,7 @@ pmmf_status apply_backward(const ApplyStages &S, const std::vector<const RotRec 
                 continue;
             }
             const size_t sh = backward_smem(a.cmax, a.cmax, cur);
-            if (sh > 48 * 1024)
-                PMMF_CUDA_TRY(cudaFuncSetAttribute(k_backward_stage, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh));
+            PMMF_CUDA_TRY(allow_smem(k_backward_stage, sh));
             k_backward_stage<<<(unsigned)a.m, BW_THREADS, sh, st>>>(
                 a.coff, a.members, a.roff, recs[p], a.nlev, ck.p + coff_ck[p], prb.p, cur, acc,
                 dt + toff[p]);

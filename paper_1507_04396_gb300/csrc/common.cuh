@@ -60,6 +60,18 @@ inline unsigned grid_for(int64_t items, int per_block, int64_t cap = 152 * 64) {
 // Launch parameters that an offline sweep may set per cluster-size bucket
 // (pmmf_set_tuning); tuned(param, size, fallback) returns the value of the
 // smallest bucket whose bound is >= size, else fallback.
+// Opt a kernel in to `bytes` of dynamic shared memory.  The default limit of
+// 48 KB holds static and dynamic shared memory together, so the opt-in is
+// taken from 32 KB on (the kernels' static shared memory is far below 16 KB);
+// a kernel whose dynamic size sits just under 48 KB would otherwise fail to
+// launch.
+template <class K>
+inline cudaError_t allow_smem(K kern, size_t bytes) {
+    return bytes > 32 * 1024
+               ? cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes)
+               : cudaSuccess;
+}
+
 enum TuneParam : int {
     TUNE_ROWS_WARPS = 0, TUNE_GRAM_WARPS = 1, TUNE_SELECT_WARPS = 2, TUNE_PASS1_ESTIMATE = 3,
     TUNE_REACH_CLUSTERS = 4, TUNE_ROWS_KERNEL = 5, TUNE_DENSE_TILES = 6, TUNE_SELECT_DSM = 7,

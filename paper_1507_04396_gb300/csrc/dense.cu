@@ -638,8 +638,7 @@ pmmf_status dense_update(DBuf<double> &D, int64_t s, const DenseLevels &lv, cons
         set_error("dense update: rows too long for shared memory");
         return PMMF_ERR_UNSUPPORTED;
     }
-    if (sh > 48 * 1024)
-        PMMF_CUDA_TRY(cudaFuncSetAttribute(k_dense_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh));
+    PMMF_CUDA_TRY(allow_smem(k_dense_rows, sh));
     DBuf<double> T;
     PMMF_TRY(T.alloc(s * s, st));
     // every pass reads and writes the s x s block once

@@ -646,8 +646,7 @@ pmmf_status partition_stage(const PartitionIn &in, int64_t m, int iters, StageCl
     // one cooperative launch for all iterations when every block fits at once
     const void *lloyd = dim == 1 ? (const void *)k_lloyd<1> : dim == 2 ? (const void *)k_lloyd<2>
                                                                    : (const void *)k_lloyd<3>;
-    if (sh_lloyd > 48 * 1024)
-        PMMF_CUDA_TRY(cudaFuncSetAttribute(lloyd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh_lloyd));
+    PMMF_CUDA_TRY(allow_smem(lloyd, sh_lloyd));
     int dev = 0, nsm = 0, per_sm = 0, coop = 0;
     PMMF_CUDA_TRY(cudaGetDevice(&dev));
     PMMF_CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
@@ -677,8 +676,7 @@ pmmf_status partition_stage(const PartitionIn &in, int64_t m, int iters, StageCl
         fcnt = lcnt.p + (int64_t)((iters - 1) % 3) * m;
     } else {
     auto assign = dim == 1 ? (void *)k_assign<1> : dim == 2 ? (void *)k_assign<2> : (void *)k_assign<3>;
-    if (sh > 48 * 1024)
-        PMMF_CUDA_TRY(cudaFuncSetAttribute(assign, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh));
+    PMMF_CUDA_TRY(allow_smem(assign, sh));
     for (int it = 0; it < iters; ++it) {
         PMMF_CUDA_TRY(cudaMemsetAsync(sum.p, 0, sizeof(unsigned long long) * (size_t)(m * dim), st));
         PMMF_CUDA_TRY(cudaMemsetAsync(cnt.p, 0, sizeof(unsigned long long) * (size_t)m, st));

@@ -357,10 +357,8 @@ pmmf_status stable_sort_by_key(const uint32_t *key, int64_t n, int64_t nbins, in
     DBuf<int64_t> hist;
     PMMF_TRY(hist.alloc(nbins * nblocks + 1, st));
     size_t sh = sizeof(int32_t) * (size_t)nbins;
-    if (sh > 48 * 1024) {
-        PMMF_CUDA_TRY(cudaFuncSetAttribute(k_sort_hist, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh));
-        PMMF_CUDA_TRY(cudaFuncSetAttribute(k_sort_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh));
-    }
+    PMMF_CUDA_TRY(allow_smem(k_sort_hist, sh));
+    PMMF_CUDA_TRY(allow_smem(k_sort_scatter, sh));
     k_sort_hist<<<(unsigned)nblocks, 256, sh, st>>>(key, n, nbins, nblocks, tile, hist.p);
     PMMF_TRY(launched("sort_hist"));
     PMMF_TRY(scan_i64(hist.p, hist.p, nbins * nblocks, st));

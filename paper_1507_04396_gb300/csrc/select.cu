@@ -1320,8 +1320,7 @@ pmmf_status gram_and_select(const Csr &A, const int32_t *act_ids, const int32_t 
     int warps = tuned(TUNE_GRAM_WARPS, cmax, 8);
     while (warps > 1 && sizeof(double) * (size_t)cmax * warps > 96 * 1024) warps >>= 1;
     const size_t gsh = sizeof(double) * (size_t)cmax * warps;
-    if (gsh > 48 * 1024)
-        PMMF_CUDA_TRY(cudaFuncSetAttribute(k_gram_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gsh));
+    PMMF_CUDA_TRY(allow_smem(k_gram_rows, gsh));
     prof_begin(KF_GRAM, st);
     k_gram_rows<<<grid_for(s * 32, 32 * warps), 32 * warps, gsh, st>>>(
         A.rowptr.p, A.col.p, A.val.p, trp.p, tul.p, tv.p, pos, cl, loc, cls.coff.p, cls.members.p,
@@ -1419,8 +1418,7 @@ pmmf_status select_stage(const StageClusters &cls, int64_t cmax, GramBlocks &gb,
     if (sw == 0) sw = 8;
     if (kpt > 4) sw = 16;
     auto launch = [&](auto kern, int nt) -> pmmf_status {
-        if (shf > 48 * 1024)
-            PMMF_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shf));
+        PMMF_CUDA_TRY(allow_smem(kern, shf));
         kern<<<(unsigned)m, nt, shf, st>>>(cls.coff.p, cls.members.p, goff.p, G.p, M.p, rot.roff.p,
                                            seed, stage, rot.rec.p, rot.lvl.p, rot.lvl_off.p,
                                            rot.nlev.p, elimflag, order, useed, ords);
@@ -1454,8 +1452,7 @@ pmmf_status select_stage(const StageClusters &cls, int64_t cmax, GramBlocks &gb,
     else if (fits_fast && kpt512 <= 2) PMMF_TRY(launch(k_select_fast<2, 512>, 512));
     else if (fits_fast && kpt512 <= 4) PMMF_TRY(launch(k_select_fast<4, 512>, 512));
     else {
-        if (shb > 48 * 1024)
-            PMMF_CUDA_TRY(cudaFuncSetAttribute(k_select, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shb));
+        PMMF_CUDA_TRY(allow_smem(k_select, shb));
         k_select<<<(unsigned)m, SEL_THREADS, shb, st>>>(cls.coff.p, cls.members.p, goff.p, G.p, M.p,
                                                         rot.roff.p, seed, stage, rot.rec.p, rot.lvl.p,
                                                         rot.lvl_off.p, rot.nlev.p, elimflag, order,

@@ -300,8 +300,7 @@ pmmf_status select_kpoint(const StageClusters &cls, int64_t cmax, const int64_t 
         set_error("cluster too large for the k-point rotation search");
         return PMMF_ERR_UNSUPPORTED;
     }
-    if (sh > 48 * 1024)
-        PMMF_CUDA_TRY(cudaFuncSetAttribute(k_select_k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh));
+    PMMF_CUDA_TRY(allow_smem(k_select_k, sh));
     prof_begin(KF_SELECT, st);
     k_select_k<<<(unsigned)m, KS_THREADS, sh, st>>>(cls.coff.p, cls.members.p, goff, G, M,
                                                    rot.roff.p, seed, stage, K, rot.kidx.p, rot.kk.p,

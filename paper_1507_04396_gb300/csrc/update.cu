@@ -899,8 +899,7 @@ pmmf_status launch_rows(RowArgs &a, int64_t nnz_in, int64_t nnz_out, cudaStream_
     }
     size_t sh = per * warps;
     auto kern = a.K > 2 ? k_rows<MODE, true> : k_rows<MODE, false>;
-    if (sh > 48 * 1024)
-        PMMF_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh));
+    PMMF_CUDA_TRY(allow_smem(kern, sh));
     unsigned grid = grid_for(a.rows, warps, 152 * 16);
     prof_begin(KF_ROWS, st);
     kern<<<grid, 32 * warps, sh, st>>>(a);
@@ -1005,8 +1004,7 @@ pmmf_status update_stage(const Csr &A, const int32_t *act, int64_t n, const int3
         // sets (32 words per coordinate) and tuples (at most cmax rotations)
         const int KS = rot.K <= 2 ? 2 : rot.K + 1;
         const size_t sh = sizeof(uint32_t) * (32 + (size_t)KS) * (size_t)cmax;
-        if (sh > 48 * 1024)
-            PMMF_CUDA_TRY(cudaFuncSetAttribute(k_reach, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh));
+        PMMF_CUDA_TRY(allow_smem(k_reach, sh));
         k_reach<<<(unsigned)cls.m, 32, sh, st>>>(cls.coff.p, rot.roff.p, rot.rec.p, rot.K, rot.kidx.p,
                                                  rot.kk.p, words, cmax, reach.p);
         PMMF_TRY(launched("reach"));

@@ -509,3 +509,15 @@ def test_search_occupancy_variants_agree_with_oracle(blocks, case):
     finally:
         L.pmmf_clear_tuning()
         pm.apply_tuning(pm.TUNING_PATH)
+
+
+@pytest.mark.parametrize("c", [430, 436, 440])
+def test_search_dynamic_shared_memory_just_under_48k(c):
+    """One cluster of ~436 coordinates: the search's dynamic shared memory is
+    just under 48 KB (48,928 bytes at 436), its static shared memory takes the
+    block over the default limit, so the launch must opt in; bit for bit with
+    the oracle."""
+    a = I.knn_laplacian(c, seed=15)
+    g, o = factor_both(a, coords=None, k=2, eta=0.5, cluster_size=c, core_size=16, seed=80)
+    assert o.stages[0].active == c and len(o.stages[0].offsets) == 2
+    assert_same_factorization(g, o)
