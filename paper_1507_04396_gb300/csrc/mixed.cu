@@ -17,6 +17,7 @@
 // the FP64 diagonal follows the FP64 k x k block.  Only the Gram matrix, its
 // error bound and their rotation are in reduced precision.
 #include <climits>
+#include <cmath>
 
 #include <cooperative_groups.h>
 #include <cuda_bf16.h>
@@ -141,9 +142,22 @@ __global__ void k_local_block(const double *D, int64_t s, const int32_t *pos, co
 //   C c0..c3 = (g, 2t), (g, 2t+1), (g+8, 2t), (g+8, 2t+1);  g = lane / 4, t = lane % 4.
 constexpr int TG = 64;      // output tile
 constexpr int TKB = 32;     // k chunk staged in shared memory (elements)
-constexpr int KFLUSH = 16;  // FP32 accumulation length before the FP64 sum (a
-                            // multiple of the MMA's k step): the FP32 part of the
-                            // certified bound grows with it, the FP64 adds shrink
+constexpr int KFLUSH = 16;  // FP32 accumulation length before the chunk sum is
+                            // added into the compensated sum (a multiple of the
+                            // MMA's k step): the FP32 part of the certified bound
+                            // grows with it, the additions shrink
+
+// s + x kept as the FP32 pair (hi, lo): hi takes the rounded sum, lo gathers
+// the exact rounding errors of those additions (Knuth's TwoSum; the cascaded
+// summation "Sum2" of Ogita, Rump and Oishi, 2005).  FP32 instructions only,
+// where an FP64 add per chunk and output would load the SM's small FP64 pipe.
+__device__ __forceinline__ void two_sum_acc(float &hi, float &lo, float x) {
+    const float s = __fadd_rn(hi, x);
+    const float bp = __fsub_rn(s, hi);
+    const float err = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bp)), __fsub_rn(x, bp));
+    hi = s;
+    lo = __fadd_rn(lo, err);
+}
 
 __device__ __forceinline__ void mma_bf16(float *d, const uint32_t *a, const uint32_t *b) {
     asm volatile(
@@ -179,12 +193,13 @@ k_tc_gram(const void *XH, const void *XL, int64_t sp /* padded row length */,
     const int g = lane >> 2, t = lane & 3;
     const int wm = (warp >> 1) * 32, wn = (warp & 1) * 32;
     float acc[2][4][4];
-    double dacc[2][4][4];
+    float shi[2][4][4], slo[2][4][4];   // compensated sums of the chunk sums
     for (int i = 0; i < 2; ++i)
         for (int j = 0; j < 4; ++j)
             for (int q = 0; q < 4; ++q) {
                 acc[i][j][q] = 0.0f;
-                dacc[i][j][q] = 0.0;
+                shi[i][j][q] = 0.0f;
+                slo[i][j][q] = 0.0f;
             }
     const uint32_t *WH = (const uint32_t *)XH, *WL = (const uint32_t *)XL;
     const int64_t wrow = PREC == PMMF_PREC_BF16 ? sp / 2 : sp;   // words per row
@@ -236,12 +251,12 @@ k_tc_gram(const void *XH, const void *XL, int64_t sp /* padded row length */,
                         mma_tf32(acc[i][j], ah[i], bh[j]);
                     }
                 }
-            // every KFLUSH terms the FP32 sums move into the FP64 ones
+            // every KFLUSH terms the chunk sums move into the compensated sums
             if (((kk + 1) * KSTEP) % KFLUSH == 0) {
                 for (int i = 0; i < 2; ++i)
                     for (int j = 0; j < 4; ++j)
                         for (int q = 0; q < 4; ++q) {
-                            dacc[i][j][q] = __dadd_rn(dacc[i][j][q], (double)acc[i][j][q]);
+                            two_sum_acc(shi[i][j][q], slo[i][j][q], acc[i][j][q]);
                             acc[i][j][q] = 0.0f;
                         }
             }
@@ -250,7 +265,7 @@ k_tc_gram(const void *XH, const void *XL, int64_t sp /* padded row length */,
     }
     for (int i = 0; i < 2; ++i)
         for (int j = 0; j < 4; ++j)
-            for (int q = 0; q < 4; ++q) dacc[i][j][q] = __dadd_rn(dacc[i][j][q], (double)acc[i][j][q]);
+            for (int q = 0; q < 4; ++q) two_sum_acc(shi[i][j][q], slo[i][j][q], acc[i][j][q]);
     float *Gu = G + goff[u];
     for (int i = 0; i < 2; ++i)
         for (int j = 0; j < 4; ++j)
@@ -258,7 +273,8 @@ k_tc_gram(const void *XH, const void *XL, int64_t sp /* padded row length */,
                 const int a = a0 + wm + i * 16 + g + (q >= 2 ? 8 : 0);
                 const int b = b0 + wn + j * 8 + 2 * t + (q & 1);
                 if (a < c && b < c) {
-                    const float f = __double2float_rn(dacc[i][j][q]);
+                    // hi + lo once, in FP64, then rounded to the stored FP32
+                    const float f = __double2float_rn(__dadd_rn((double)shi[i][j][q], (double)slo[i][j][q]));
                     Gu[(int64_t)a * c + b] = f;
                     Gu[(int64_t)b * c + a] = f;
                 }
@@ -818,12 +834,17 @@ pmmf_status mixed_stage_select(const DBuf<double> &D, int64_t s, const int32_t *
     // (u = 2^-11 TF32, 2^-8 BF16), the dropped lo lo^T term is <= u^2 |x||y|,
     // so the three products miss x y by <= 3 u^2 (1 + u) |x||y|; FP32
     // accumulation of 3 KFLUSH products per chunk of KFLUSH terms (taken at
-    // twice the round-to-nearest bound) and the FP64 sum of the chunks and the final
-    // FP32 rounding add the rest; Cauchy-Schwarz turns sum |x||y| into
+    // twice the round-to-nearest bound); the compensated sum of the N chunk
+    // sums (Sum2: |hi + lo - sum| <= gamma_{N-1}^2 sum |chunk|, gamma_n =
+    // n 2^-24 / (1 - n 2^-24), the chunk sums bounded by the terms' |x||y| to
+    // within (1 + 2^-10)), hi + lo taken in FP64 (2^-52 with margin) and the
+    // final FP32 rounding add the rest; Cauchy-Schwarz turns sum |x||y| into
     // sqrt(G_ii G_jj).  10% margin.
     const double uin = precision == PMMF_PREC_BF16 ? 0x1p-8 : 0x1p-11;
+    const double nch = std::ceil((double)sp / KFLUSH) + 1.0;
+    const double gam = nch * 0x1p-24 / (1.0 - nch * 0x1p-24);
     const double eps = 1.1 * (3.0 * uin * uin * (1.0 + uin) + 6.0 * (double)KFLUSH * 0x1p-24 +
-                              ((double)s / KFLUSH + 2.0) * 0x1p-52 + 0x1p-24);
+                              gam * gam * (1.0 + 0x1p-10) + 0x1p-52 + 0x1p-24);
     const int K = rot.K;
     const int64_t nr = std::max<int64_t>(rot.nrot, 1);
     PMMF_TRY(rot.kidx.alloc(nr * K, st));
