@@ -470,18 +470,21 @@ pmmf_status pmmf_get_stage_matrix(const pmmf_handle *f, int p, int64_t *rowptr_n
  * 256-thread kernel per SM, 2, 3 or 4, its registers capped to fit; without
  * a setting 4 for clusters of up to 256 coordinates and 3 up to 512 when a
  * stage has at least 4 and 6 times as many clusters as SMs, else 2; all give
- * the same bits).
+ * the same bits), PMMF_TUNE_MIXED_ACTIVE (with a reduced-precision mode, the
+ * stages with at least this many clusters use the reduced-precision Gram and
+ * shortlist, the others the FP64 Gram and search; 0 = every stage; default
+ * 12).
  * A value
  * applies to launches whose largest cluster has at most max_size coordinates
  * and no smaller bucket matches; shared-memory limits still halve the row and
  * Gram warps when needed.  Process wide; INVALID_ARG for an unknown param or
  * a value outside 1..32 (outside {8, 16} for the search warps, {1, 2} for the
- * kernel choices, 2..4 for the search's CTAs per SM; any positive value for
- * the reach threshold). */
+ * kernel choices, 2..4 for the search's CTAs per SM, 0..32 for the
+ * reduced-precision threshold; any positive value for the reach threshold). */
 enum { PMMF_TUNE_ROWS_WARPS = 0, PMMF_TUNE_GRAM_WARPS = 1, PMMF_TUNE_SELECT_WARPS = 2,
        PMMF_TUNE_PASS1_ESTIMATE = 3, PMMF_TUNE_REACH_CLUSTERS = 4, PMMF_TUNE_ROWS_KERNEL = 5,
        PMMF_TUNE_DENSE_TILES = 6, PMMF_TUNE_SELECT_DSM = 7,
-       PMMF_TUNE_APPLY_FUSED = 8, PMMF_TUNE_SELECT_BLOCKS = 9 };
+       PMMF_TUNE_APPLY_FUSED = 8, PMMF_TUNE_SELECT_BLOCKS = 9, PMMF_TUNE_MIXED_ACTIVE = 10 };
 pmmf_status pmmf_set_tuning(int param, int64_t max_size, int value);
 void pmmf_clear_tuning(void);
 

@@ -687,7 +687,15 @@ pmmf_status factor_dense_impl(const pmmf_matrix *A, const pmmf_params *prm, pmmf
         PMMF_CUDA_TRY(cudaStreamSynchronize(st));
         for (int64_t u = 0; u < S.m; ++u) S.cmax = std::max(S.cmax, hc[u + 1] - hc[u]);
         PMMF_CUDA_TRY(cudaMemsetAsync(status.p, 0, sizeof(unsigned), st));
-        if (prm->precision != PMMF_PREC_FP64) {
+        // the reduced-precision Gram and shortlist only while the stage has
+        // many clusters (at least PMMF_TUNE_MIXED_ACTIVE, default 12): the FP64
+        // Gram costs ~c s^2 = s^2 (s / m), the shortlist search's FP64 rows ~s
+        // per step, and with fewer clusters the FP64 Gram and search are the
+        // faster pair (dense RBF n = 16,384, clusters of 512, per stage FP64
+        // vs TF32: 32 clusters 171 vs 99 ms, 16: 71 vs 58, 8: 39 vs 41, 4: 34
+        // vs 44); both choose the same rotations
+        const int64_t mixed_min = tuned(TUNE_MIXED_ACTIVE, S.cmax, 12);
+        if (prm->precision != PMMF_PREC_FP64 && S.m >= mixed_min) {
             PMMF_TRY(mixed_stage_select(D, s, pos.p, S.cls, hc, S.cmax, prm->precision, prm->seed,
                                         p, S.rot, elimflag.p, pstats.p, status.p, st));
         } else {

@@ -718,7 +718,8 @@ extern "C" {
 
 pmmf_status pmmf_set_tuning(int param, int64_t max_size, int value) {
     using namespace pmmf;
-    if (param < 0 || param >= TUNE_COUNT || max_size < 1 || value < 1 ||
+    if (param < 0 || param >= TUNE_COUNT || max_size < 1 || value < 0 ||
+        (value == 0 && param != TUNE_MIXED_ACTIVE) ||
         (value > 32 && param != TUNE_REACH_CLUSTERS) ||
         (param == TUNE_SELECT_WARPS && value != 8 && value != 16) ||
         (param == TUNE_ROWS_KERNEL && value != 1 && value != 2) ||

@@ -175,7 +175,8 @@ def load(path: str = LIB_PATH):
 TUNING_PATH = os.path.join(_HERE, "tuning.json")
 TUNE_PARAMS = {"rows_warps": 0, "gram_warps": 1, "select_warps": 2, "pass1_estimate": 3,
                "reach_clusters": 4, "rows_kernel": 5, "dense_tiles": 6, "select_dsm": 7,
-               "apply_fused": 8, "select_blocks": 9}
+               "apply_fused": 8, "select_blocks": 9,
+               "mixed_active": 10}
 
 
 def apply_tuning(path: str) -> bool:

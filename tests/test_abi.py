@@ -70,7 +70,9 @@ def test_tuning_table_validation_and_json(tmp_path):
     from paper_1507_04396_gb300 import pmmf
     lib = pmmf.load()
     assert lib.pmmf_set_tuning(0, 256, 4) == pmmf.OK
-    assert lib.pmmf_set_tuning(7, 256, 4) == pmmf.ERR_INVALID_ARG     # unknown parameter
+    assert lib.pmmf_set_tuning(11, 256, 4) == pmmf.ERR_INVALID_ARG    # unknown parameter
+    assert lib.pmmf_set_tuning(10, 256, 0) == pmmf.OK                 # reduced precision on every stage
+    assert lib.pmmf_set_tuning(9, 256, 5) == pmmf.ERR_INVALID_ARG     # 2..4 search CTAs per SM
     assert lib.pmmf_set_tuning(0, 0, 4) == pmmf.ERR_INVALID_ARG       # empty bucket
     assert lib.pmmf_set_tuning(1, 512, 0) == pmmf.ERR_INVALID_ARG     # value out of range
     assert lib.pmmf_set_tuning(2, 512, 16) == pmmf.OK                 # search width

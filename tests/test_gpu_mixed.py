@@ -17,6 +17,19 @@ from paper_1507_04396_gb300 import inputs as I
 pytestmark = gpu
 
 
+@pytest.fixture(autouse=True)
+def _shortlist_on_every_stage():
+    """These inputs are small: without a setting their stages would take the
+    FP64 Gram (a stage uses the reduced-precision one only while it has at
+    least 12 clusters).  Every stage takes the shortlist here (threshold 0)."""
+    pm = gpu_lib()
+    L = pm.load()
+    assert L.pmmf_set_tuning(pm.TUNE_PARAMS["mixed_active"], 1 << 30, 0) == 0
+    yield
+    L.pmmf_clear_tuning()
+    pm.apply_tuning(pm.TUNING_PATH)
+
+
 def _run(a, precision, **kw):
     import torch
     pm = gpu_lib()
@@ -96,3 +109,19 @@ def test_shortlist_rbf_workload_shape(precision):
     a = I.rbf_mixture(2048, components=20, seed=2)
     mp, o = _against_oracle(a, precision, k=3, eta=0.5, cluster_size=512, core_size=512, seed=0)
     assert np.diff(o.stages[0].offsets).max() > 400
+
+
+def test_per_stage_choice_of_the_reduced_precision_gram():
+    """With the default rule (reduced precision while a stage has at least 12
+    clusters) the first stages of an n = 4,096 RBF matrix with clusters of 128
+    (32, then 16 clusters) take the shortlist and the later ones the FP64
+    Gram: the selections still equal the oracle's."""
+    pm = gpu_lib()
+    L = pm.load()
+    L.pmmf_clear_tuning()
+    pm.apply_tuning(pm.TUNING_PATH)
+    a = I.rbf_mixture(4096, components=8, seed=6)
+    mp, o = _against_oracle(a, 1, k=2, eta=0.5, cluster_size=128, core_size=64, seed=3)
+    st = mp.precision_stats()
+    assert st["steps"] > 0                                        # the first stage's shortlist
+    assert st["steps"] < sum(len(x.rot_elim) for x in o.stages)   # not every stage's
