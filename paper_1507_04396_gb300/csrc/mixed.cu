@@ -366,6 +366,7 @@ k_select_mixed(int64_t s, const int64_t *coff, const int32_t *members, const int
     double *pd2 = pd + 2 * CL * c;
     __shared__ int s_T[8], s_kk, s_maxlev, s_nsl, s_fall;
     __shared__ double s_O[64], s_GT[64], s_es[SL_MAX + 8];
+    __shared__ double s_gw[64], s_J[4], s_R[4];   // the warp's Jacobi
     __shared__ int s_wcnt[MX_WARPS];
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     // the CTAs of the cluster meet (one CTA: the block barrier)
@@ -579,19 +580,22 @@ k_select_mixed(int64_t s, const int64_t *coff, const int32_t *members, const int
                     }
             }
         }
-        if (tid == 0) {
-            double O[64];
+        if (wid == 0) {
             if (kk == 2) {
-                double cc, ss;
-                jacobi2(s_GT[0], s_GT[1], s_GT[3], cc, ss);
-                O[0] = cc;
-                O[1] = -ss;
-                O[2] = ss;
-                O[3] = cc;
-            } else if (!jacobi_k(kk, s_GT, O)) {
-                atomicOr(status, ST_NOT_CONVERGED);
+                if (lane == 0) {
+                    double cc, ss;
+                    jacobi2(s_GT[0], s_GT[1], s_GT[3], cc, ss);
+                    s_O[0] = cc;
+                    s_O[1] = -ss;
+                    s_O[2] = ss;
+                    s_O[3] = cc;
+                }
+            } else {
+                // the k x k block diagonalised by the warp
+                for (int a = lane; a < kk * kk; a += 32) s_gw[a] = s_GT[a];
+                __syncwarp();
+                if (!jacobi_k_warp(kk, s_gw, s_O, s_J, s_R) && lane == 0) atomicOr(status, ST_NOT_CONVERGED);
             }
-            for (int a = 0; a < kk * kk; ++a) s_O[a] = O[a];
         }
         __syncthreads();
         // FP64 rows X_T <- O X_T (this CTA's columns)

@@ -57,64 +57,92 @@ __device__ __forceinline__ double rot_row_t(const double *O, int kk, int a, cons
     return acc;
 }
 
-// X <- J X J^T on the pair (p, q) of a small symmetric k x k matrix X
-// (row-major): rows p, q recomputed for every other column and mirrored; the
-// 2 x 2 block as R = J X_TT, then R J^T for a <= b, mirrored.
-__device__ __forceinline__ void sym_rotate_pair(double *X, int k, int p, int q, const double *J) {
-    for (int y = 0; y < k; ++y) {
-        if (y == p || y == q) continue;
-        const double in[2] = {X[p * k + y], X[q * k + y]};
-        const double o0 = rot_row(J, 2, 0, in), o1 = rot_row(J, 2, 1, in);
-        X[p * k + y] = o0;
-        X[y * k + p] = o0;
-        X[q * k + y] = o1;
-        X[y * k + q] = o1;
-    }
-    const int T[2] = {p, q};
-    double R[4];
-    for (int cc = 0; cc < 2; ++cc) {
-        const double in[2] = {X[T[0] * k + T[cc]], X[T[1] * k + T[cc]]};
-        for (int a = 0; a < 2; ++a) R[a * 2 + cc] = rot_row(J, 2, a, in);
-    }
-    for (int a = 0; a < 2; ++a)
-        for (int b = a; b < 2; ++b) {
-            double acc = __dmul_rn(R[a * 2 + 1], J[b * 2 + 1]);
-            acc = __fma_rn(R[a * 2 + 0], J[b * 2 + 0], acc);
-            X[T[a] * k + T[b]] = acc;
-            X[T[b] * k + T[a]] = acc;
-        }
-}
-
-// k x k rotation (k >= 3) diagonalizing a symmetric block g (R7): cyclic
-// Jacobi on a copy, pairs (0,1), (0,2), ..., (k-2,k-1), a pair whose entry is
-// exactly zero skipped; converged before a sweep when the sum of squared
-// off-diagonal entries is at most 1e-30 times the sum of squared diagonal
-// entries; at most 32 sweeps.  O accumulates J O.  Returns false when not
-// converged after 32 sweeps.
-__device__ inline bool jacobi_k(int k, const double *gin, double *O) {
-    double g[64];
-    for (int a = 0; a < k * k; ++a) g[a] = gin[a];
-    for (int a = 0; a < k * k; ++a) O[a] = 0.0;
-    for (int a = 0; a < k; ++a) O[a * k + a] = 1.0;
+// k x k rotation (k >= 3) diagonalizing a symmetric block g (R7), by the 32
+// lanes of one warp (every lane calls it, with g's k x k block in gs): cyclic
+// Jacobi on the block, pairs (0,1), (0,2), ..., (k-2,k-1), a pair whose entry
+// is exactly zero skipped; converged before a sweep when the sum of squared
+// off-diagonal entries (in pair order) is at most 1e-30 times the sum of
+// squared diagonal entries; at most 32 sweeps (false: not converged).  A
+// pair's rotation J = [[c, -s], [s, c]] (jacobi2) updates g <- J g J^T
+// (rows p, q recomputed at the other columns from the old values and
+// mirrored; the 2 x 2 block as R = J g_TT, then R J^T for a <= b, mirrored)
+// and O (starting at I) <- J O on rows p, q.  Lane 0 takes the serial parts (the sweep's sums,
+// each pair's angle); every new entry is fma(P0, Q0, P1 * Q1) of pre-pair
+// values (the rows p, q of g at the other columns, R = J X_TT, the rows p, q
+// of O), one lane per entry (2(k-2) + 4 + 2k <= 32 for k <= 8), then the
+// 2 x 2 block's R J^T by three lanes, each the same operations on the same
+// operands as a sequential evaluation, so the same bits.  gs, os (k x k) and
+// js, rs (4 each) are the warp's shared memory; O is left in os.
+__device__ inline bool jacobi_k_warp(int k, double *gs, double *os, double *js, double *rs) {
+    const int lane = threadIdx.x & 31;
+    const unsigned full = 0xffffffffu;
+    for (int a = lane; a < k * k; a += 32) os[a] = (a / k == a % k) ? 1.0 : 0.0;
+    __syncwarp();
+    const int ny = 2 * (k - 2), nt = ny + 4 + 2 * k;
     for (int sweep = 0;; ++sweep) {
-        double off = 0.0, dg = 0.0;
-        for (int p = 0; p < k; ++p)
-            for (int q = p + 1; q < k; ++q) off = __dadd_rn(off, __dmul_rn(g[p * k + q], g[p * k + q]));
-        for (int p = 0; p < k; ++p) dg = __dadd_rn(dg, __dmul_rn(g[p * k + p], g[p * k + p]));
-        if (off <= __dmul_rn(1e-30, dg)) return true;
-        if (sweep == 32) return false;
+        int state = 0;
+        if (lane == 0) {
+            double off = 0.0, dg = 0.0;
+            for (int p = 0; p < k; ++p)
+                for (int q = p + 1; q < k; ++q) off = __dadd_rn(off, __dmul_rn(gs[p * k + q], gs[p * k + q]));
+            for (int p = 0; p < k; ++p) dg = __dadd_rn(dg, __dmul_rn(gs[p * k + p], gs[p * k + p]));
+            state = off <= __dmul_rn(1e-30, dg) ? 1 : (sweep == 32 ? 2 : 0);
+        }
+        state = __shfl_sync(full, state, 0);
+        if (state) return state == 1;
         for (int p = 0; p < k - 1; ++p) {
             for (int q = p + 1; q < k; ++q) {
-                if (g[p * k + q] == 0.0) continue;
-                double c, s;
-                jacobi2(g[p * k + p], g[p * k + q], g[q * k + q], c, s);
-                const double J[4] = {c, -s, s, c};
-                sym_rotate_pair(g, k, p, q, J);
-                for (int x = 0; x < k; ++x) {
-                    const double in2[2] = {O[p * k + x], O[q * k + x]};
-                    O[p * k + x] = rot_row(J, 2, 0, in2);
-                    O[q * k + x] = rot_row(J, 2, 1, in2);
+                if (gs[p * k + q] == 0.0) continue;   // the same value in every lane
+                if (lane == 0) {
+                    double c, s;
+                    jacobi2(gs[p * k + p], gs[p * k + q], gs[q * k + q], c, s);
+                    js[0] = c;
+                    js[1] = -s;
+                    js[2] = s;
+                    js[3] = c;
                 }
+                __syncwarp();
+                // this lane's entry: fma(J[2a], x_p, J[2a+1] x_q) with (x_p, x_q)
+                // the pair's rows p, q of g at column y (y-entries, R) or of O
+                int a = 0, col = 0;
+                const double *src = gs;
+                if (lane < ny) {
+                    const int yi = lane >> 1;
+                    a = lane & 1;
+                    col = yi + (yi >= p) + (yi + (yi >= p) >= q);   // the yi-th column not in {p, q}
+                } else if (lane < ny + 4) {
+                    const int t = lane - ny;                      // R[a * 2 + cc]
+                    a = t >> 1;
+                    col = (t & 1) ? q : p;
+                } else if (lane < nt) {
+                    const int t = lane - ny - 4;                  // O[T[a]][x]
+                    a = t / k;
+                    col = t - a * k;
+                    src = os;
+                }
+                double v = 0.0;
+                if (lane < nt) v = __fma_rn(js[2 * a], src[p * k + col], __dmul_rn(js[2 * a + 1], src[q * k + col]));
+                __syncwarp();
+                if (lane < ny) {
+                    const int row = a ? q : p;
+                    gs[row * k + col] = v;
+                    gs[col * k + row] = v;
+                } else if (lane < ny + 4) {
+                    rs[lane - ny] = v;
+                } else if (lane < nt) {
+                    os[(a ? q : p) * k + col] = v;
+                }
+                __syncwarp();
+                // the 2 x 2 block: (R J^T)_ab for a <= b, mirrored
+                if (lane < 3) {
+                    const int aa = lane == 2 ? 1 : 0, bb = lane == 0 ? 0 : 1;
+                    double acc = __dmul_rn(rs[aa * 2 + 1], js[bb * 2 + 1]);
+                    acc = __fma_rn(rs[aa * 2 + 0], js[bb * 2 + 0], acc);
+                    const int ra = aa ? q : p, rb = bb ? q : p;
+                    gs[ra * k + rb] = acc;
+                    gs[rb * k + ra] = acc;
+                }
+                __syncwarp();
             }
         }
     }

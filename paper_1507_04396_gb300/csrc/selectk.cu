@@ -86,7 +86,7 @@ k_select_k(const int64_t *coff, const int32_t *members, const int64_t *goff, dou
     int32_t *lvl = (int32_t *)(mask + nwords);
     int32_t *lcnt = lvl + c;   // e + 2
     __shared__ int s_T[8], s_kk, s_maxlev;
-    __shared__ double s_O[64];
+    __shared__ double s_O[64], s_g[64], s_J[4], s_R[4];
     __shared__ unsigned long long s_bk[KS_WARPS];
     __shared__ int s_bi[KS_WARPS];
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
@@ -165,23 +165,24 @@ k_select_k(const int64_t *coff, const int32_t *members, const int64_t *goff, dou
         }
         int T[8];
         for (int a = 0; a < kk; ++a) T[a] = s_T[a];
-        if (tid == 0) {
-            double O[64];
+        if (wid == 0) {
             if (kk == 2) {
-                double cc, ss;
-                jacobi2(G[(int64_t)T[0] * c + T[0]], G[(int64_t)T[0] * c + T[1]],
-                        G[(int64_t)T[1] * c + T[1]], cc, ss);
-                O[0] = cc;
-                O[1] = -ss;
-                O[2] = ss;
-                O[3] = cc;
+                if (lane == 0) {
+                    double cc, ss;
+                    jacobi2(G[(int64_t)T[0] * c + T[0]], G[(int64_t)T[0] * c + T[1]],
+                            G[(int64_t)T[1] * c + T[1]], cc, ss);
+                    s_O[0] = cc;
+                    s_O[1] = -ss;
+                    s_O[2] = ss;
+                    s_O[3] = cc;
+                }
             } else {
-                double sub[64];
-                for (int a = 0; a < kk; ++a)
-                    for (int b = 0; b < kk; ++b) sub[a * kk + b] = G[(int64_t)T[a] * c + T[b]];
-                if (!jacobi_k(kk, sub, O)) atomicOr(status, ST_NOT_CONVERGED);
+                // the k x k block diagonalised by the warp
+                for (int a = lane; a < kk * kk; a += 32) s_g[a] = G[(int64_t)T[a / kk] * c + T[a % kk]];
+                __syncwarp();
+                const bool ok = jacobi_k_warp(kk, s_g, s_O, s_J, s_R);
+                if (lane == 0 && !ok) atomicOr(status, ST_NOT_CONVERGED);
             }
-            for (int a = 0; a < kk * kk; ++a) s_O[a] = O[a];
         }
         __syncthreads();
         // rows and mirrored columns of the tuple, every other active column
