@@ -63,6 +63,23 @@ __device__ __forceinline__ bool better(unsigned long long k1, int i1, unsigned l
     return k1 > k2 || (k1 == k2 && i1 < i2);
 }
 
+// Row a of O x for a tuple of kk <= KM entries held in registers: rot_row's
+// chain (the last column's product, then fmas down to column 0) unrolled over
+// KM, so in[] is never indexed at run time.
+template <int KM>
+__device__ __forceinline__ double rot_row_u(const double *O, int kk, int a, const double (&in)[KM]) {
+    double acc = 0.0;
+#pragma unroll
+    for (int b = KM - 1; b >= 0; --b) {
+        if (b == kk - 1) acc = __dmul_rn(O[a * kk + b], in[b]);
+        else if (b < kk - 1) acc = __fma_rn(O[a * kk + b], in[b], acc);
+    }
+    return acc;
+}
+
+// KM: the largest tuple (3 for k = 3, 8 otherwise); the tuple's arrays are
+// sized by it and their loops unrolled.
+template <int KM>
 __global__ void __launch_bounds__(KS_THREADS)
 k_select_k(const int64_t *coff, const int32_t *members, const int64_t *goff, double *Gall,
            double *Mall, const int64_t *roff, uint64_t seed, int64_t stage, int K, int32_t *kidx,
@@ -86,7 +103,7 @@ k_select_k(const int64_t *coff, const int32_t *members, const int64_t *goff, dou
     int32_t *lvl = (int32_t *)(mask + nwords);
     int32_t *lcnt = lvl + c;   // e + 2
     __shared__ int s_T[8], s_kk, s_maxlev;
-    __shared__ double s_O[64], s_g[64], s_J[4], s_R[4];
+    __shared__ double s_O[64], s_g[64], s_J[4], s_R[4], s_RT[2][64];
     __shared__ unsigned long long s_bk[KS_WARPS];
     __shared__ int s_bi[KS_WARPS];
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
@@ -163,8 +180,9 @@ k_select_k(const int64_t *coff, const int32_t *members, const int64_t *goff, dou
             }
             __syncthreads();
         }
-        int T[8];
-        for (int a = 0; a < kk; ++a) T[a] = s_T[a];
+        int T[KM];
+#pragma unroll
+        for (int a = 0; a < KM; ++a) T[a] = a < kk ? s_T[a] : -1;
         if (wid == 0) {
             if (kk == 2) {
                 if (lane == 0) {
@@ -185,67 +203,91 @@ k_select_k(const int64_t *coff, const int32_t *members, const int64_t *goff, dou
             }
         }
         __syncthreads();
+        // the tuple block of G and M, R = O X_TT then R O^T (upper half,
+        // mirrored), by warp 0 one entry per lane; its inputs are not among
+        // the entries the other warps rotate
+        if (wid == 0) {
+            const int nR = 2 * kk * kk;
+            for (int q = lane; q < nR; q += 32) {
+                const int mat = q / (kk * kk), t = q - mat * kk * kk;
+                const int a = t / kk, cc = t - a * kk;
+                const double *X = mat ? M : G;
+                double in[KM];
+#pragma unroll
+                for (int b = 0; b < KM; ++b) in[b] = b < kk ? X[(int64_t)s_T[b] * c + s_T[cc]] : 0.0;
+                s_RT[mat][a * kk + cc] = rot_row_u<KM>(s_O, kk, a, in);
+            }
+            __syncwarp();
+            const int nup = kk * (kk + 1) / 2;
+            for (int q = lane; q < 2 * nup; q += 32) {
+                const int mat = q / nup;
+                int t = q - mat * nup, a = 0;
+                while (t >= kk - a) {   // (a, b), a <= b, in row order
+                    t -= kk - a;
+                    ++a;
+                }
+                const int b = a + t;
+                const double *R = s_RT[mat];
+                double acc = __dmul_rn(R[a * kk + kk - 1], s_O[b * kk + kk - 1]);
+                for (int cc = kk - 2; cc >= 0; --cc) acc = __fma_rn(R[a * kk + cc], s_O[b * kk + cc], acc);
+                double *X = mat ? M : G;
+                X[(int64_t)s_T[a] * c + s_T[b]] = acc;
+                X[(int64_t)s_T[b] * c + s_T[a]] = acc;
+                if (a == b) (mat ? md : gd)[s_T[a]] = acc;
+            }
+        }
         // rows and mirrored columns of the tuple, every other active column
         for (int y = tid; y < c; y += KS_THREADS) {
             bool inT = false;
-            for (int a = 0; a < kk; ++a) inT |= T[a] == y;
+#pragma unroll
+            for (int a = 0; a < KM; ++a) inT |= a < kk && T[a] == y;
             if (inT || !active_bit(mask, y)) continue;
-            double in[8], out[8];
-            for (int a = 0; a < kk; ++a) in[a] = G[(int64_t)T[a] * c + y];
-            for (int a = 0; a < kk; ++a) out[a] = rot_row(s_O, kk, a, in);
-            for (int a = 0; a < kk; ++a) {
-                G[(int64_t)T[a] * c + y] = out[a];
-                G[(int64_t)y * c + T[a]] = out[a];
+            double gi[KM], mi[KM], go[KM], mo[KM];
+#pragma unroll
+            for (int a = 0; a < KM; ++a) {
+                gi[a] = a < kk ? G[(int64_t)T[a] * c + y] : 0.0;
+                mi[a] = a < kk ? M[(int64_t)T[a] * c + y] : 0.0;
             }
-            for (int a = 0; a < kk; ++a) in[a] = M[(int64_t)T[a] * c + y];
-            for (int a = 0; a < kk; ++a) out[a] = rot_row(s_O, kk, a, in);
-            for (int a = 0; a < kk; ++a) {
-                M[(int64_t)T[a] * c + y] = out[a];
-                M[(int64_t)y * c + T[a]] = out[a];
+#pragma unroll
+            for (int a = 0; a < KM; ++a) {
+                go[a] = a < kk ? rot_row_u<KM>(s_O, kk, a, gi) : 0.0;
+                mo[a] = a < kk ? rot_row_u<KM>(s_O, kk, a, mi) : 0.0;
             }
-        }
-        // the tuple block: R = O X_TT, then R O^T (upper half, mirrored)
-        if (tid < 2) {
-            double *X = tid == 0 ? G : M;
-            double R[64];
-            for (int cc = 0; cc < kk; ++cc) {
-                double in[8];
-                for (int b = 0; b < kk; ++b) in[b] = X[(int64_t)T[b] * c + T[cc]];
-                for (int a = 0; a < kk; ++a) R[a * kk + cc] = rot_row(s_O, kk, a, in);
-            }
-            for (int a = 0; a < kk; ++a)
-                for (int b = a; b < kk; ++b) {
-                    double acc = __dmul_rn(R[a * kk + kk - 1], s_O[b * kk + kk - 1]);
-                    for (int cc = kk - 2; cc >= 0; --cc) acc = __fma_rn(R[a * kk + cc], s_O[b * kk + cc], acc);
-                    X[(int64_t)T[a] * c + T[b]] = acc;
-                    X[(int64_t)T[b] * c + T[a]] = acc;
-                    if (a == b) (tid == 0 ? gd : md)[T[a]] = acc;
+#pragma unroll
+            for (int a = 0; a < KM; ++a)
+                if (a < kk) {
+                    G[(int64_t)T[a] * c + y] = go[a];
+                    G[(int64_t)y * c + T[a]] = go[a];
+                    M[(int64_t)T[a] * c + y] = mo[a];
+                    M[(int64_t)y * c + T[a]] = mo[a];
                 }
         }
         __syncthreads();
         if (tid < kk) {
-            const double g = gd[T[tid]];
-            w[T[tid]] = g > 0.0 ? __ddiv_rn(1.0, __dsqrt_rn(g)) : 0.0;
+            const int x = s_T[tid];
+            const double g = gd[x];
+            w[x] = g > 0.0 ? __ddiv_rn(1.0, __dsqrt_rn(g)) : 0.0;
         }
         if (tid == 0) {
             int bi = 0;
-            double dbest = __dsub_rn(gd[T[0]], __dmul_rn(md[T[0]], md[T[0]]));
+            double dbest = __dsub_rn(gd[s_T[0]], __dmul_rn(md[s_T[0]], md[s_T[0]]));
             for (int a = 1; a < kk; ++a) {
-                const double d = __dsub_rn(gd[T[a]], __dmul_rn(md[T[a]], md[T[a]]));
+                const int x = s_T[a];
+                const double d = __dsub_rn(gd[x], __dmul_rn(md[x], md[x]));
                 if (d <= dbest) {
                     dbest = d;
                     bi = a;
                 }
             }
-            const int le = T[bi];
+            const int le = s_T[bi];
             int L = 0;
-            for (int a = 0; a < kk; ++a) L = max(L, lvl[T[a]]);
+            for (int a = 0; a < kk; ++a) L = max(L, lvl[s_T[a]]);
             ++L;
-            for (int a = 0; a < kk; ++a) lvl[T[a]] = L;
+            for (int a = 0; a < kk; ++a) lvl[s_T[a]] = L;
             s_maxlev = max(s_maxlev, L);
             mask[le >> 5] &= ~(1u << (le & 31));
             const int64_t rr = r0 + t;
-            for (int a = 0; a < K; ++a) kidx[rr * K + a] = a < kk ? T[a] : -1;
+            for (int a = 0; a < K; ++a) kidx[rr * K + a] = a < kk ? s_T[a] : -1;
             for (int a = 0; a < K * K; ++a) kO[rr * K * K + a] = a < kk * kk ? s_O[a] : 0.0;
             kkv[rr] = kk;
             kel[rr] = le;
@@ -301,9 +343,10 @@ pmmf_status select_kpoint(const StageClusters &cls, int64_t cmax, const int64_t 
         set_error("cluster too large for the k-point rotation search");
         return PMMF_ERR_UNSUPPORTED;
     }
-    PMMF_CUDA_TRY(allow_smem(k_select_k, sh));
+    auto kern = K == 3 ? k_select_k<3> : k_select_k<8>;
+    PMMF_CUDA_TRY(allow_smem(kern, sh));
     prof_begin(KF_SELECT, st);
-    k_select_k<<<(unsigned)m, KS_THREADS, sh, st>>>(cls.coff.p, cls.members.p, goff, G, M,
+    kern<<<(unsigned)m, KS_THREADS, sh, st>>>(cls.coff.p, cls.members.p, goff, G, M,
                                                    rot.roff.p, seed, stage, K, rot.kidx.p, rot.kk.p,
                                                    rot.kel.p, rot.klvl.p, rot.kO.p, rot.lvlidx.p,
                                                    rot.lvl_off.p, rot.nlev.p, elimflag, order,
