@@ -326,7 +326,9 @@ __device__ double slice_dots(const double *xi, const double *const *xs, int nb, 
 // (the partial sums go to every CTA's shared memory, double-buffered by step
 // parity, and are added in rank order after one cluster barrier) and rotates
 // its slice of the rows.  Only CTA 0 writes the results.
-template <int CL>
+// KM: the largest tuple (3 for k <= 3, 8 otherwise); the tuple's arrays are
+// sized by it and their loops unrolled, so they stay in registers.
+template <int CL, int KM>
 __global__ void __launch_bounds__(MX_THREADS)
 k_select_mixed(int64_t s, const int64_t *coff, const int32_t *members, const int64_t *goff,
                int64_t gcopy, double *Xs, float *Gt, float *Bd, double *Mall,
@@ -367,6 +369,8 @@ k_select_mixed(int64_t s, const int64_t *coff, const int32_t *members, const int
     __shared__ int s_T[8], s_kk, s_maxlev, s_nsl, s_fall;
     __shared__ double s_O[64], s_GT[64], s_es[SL_MAX + 8];
     __shared__ double s_gw[64], s_J[4], s_R[4];   // the warp's Jacobi
+    __shared__ int s_Tt[8];                          // this step's tuple
+    __shared__ double s_X2[2][64], s_R2[2][64];      // the tuple blocks' scratch
     __shared__ int s_wcnt[MX_WARPS];
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     // the CTAs of the cluster meet (one CTA: the block barrier)
@@ -475,10 +479,11 @@ k_select_mixed(int64_t s, const int64_t *coff, const int32_t *members, const int
         n_rescored += (unsigned long long)nsl;
         sl_max = max(sl_max, (unsigned long long)nsl);
         // FP64 re-score: G_iy = <X_i, X_y>; partners by FP64 score
-        double best_s[8];
-        int best_y[8];
-        double best_g[8];
-        for (int a = 0; a < 8; ++a) {
+        double best_s[KM];
+        int best_y[KM];
+        double best_g[KM];
+#pragma unroll
+        for (int a = 0; a < KM; ++a) {
             best_s[a] = -1.0;
             best_y[a] = 0x7fffffff;
             best_g[a] = 0.0;
@@ -508,46 +513,61 @@ k_select_mixed(int64_t s, const int64_t *coff, const int32_t *members, const int
             for (int r = 1; r < CL; ++r) gv = __dadd_rn(gv, pd[(int64_t)(par * CL + r) * c + q]);
             {
                 const double sc = f64_from_bits(f64_bits(__dmul_rn(gv, w[y])) & F64_ABS);
-                // insert into the top kk-1 (ties to the smaller index)
-                int pos2 = kk - 1;
-                while (pos2 > 0 && (sc > best_s[pos2 - 1] || (sc == best_s[pos2 - 1] && y < best_y[pos2 - 1])))
-                    --pos2;
-                if (pos2 < kk - 1) {
-                    for (int a = kk - 2; a > pos2; --a) {
-                        best_s[a] = best_s[a - 1];
-                        best_y[a] = best_y[a - 1];
-                        best_g[a] = best_g[a - 1];
+                // insert into the top kk-1 (ties to the smaller index): the
+                // candidate takes the first place it beats and each displaced
+                // entry moves one place down, the last one dropping out
+                double cs = sc, cg = gv;
+                int cy = y;
+#pragma unroll
+                for (int a = 0; a < KM - 1; ++a) {
+                    if (a < kk - 1 && (cs > best_s[a] || (cs == best_s[a] && cy < best_y[a]))) {
+                        const double ts = best_s[a], tg = best_g[a];
+                        const int ty = best_y[a];
+                        best_s[a] = cs;
+                        best_y[a] = cy;
+                        best_g[a] = cg;
+                        cs = ts;
+                        cy = ty;
+                        cg = tg;
                     }
-                    best_s[pos2] = sc;
-                    best_y[pos2] = y;
-                    best_g[pos2] = gv;
                 }
             }
         }
-        int T[8];
+        int T[KM];
         T[0] = i;
-        for (int a = 1; a < kk; ++a) {
-            int y = best_y[a - 1];
-            if (y < 0 || y >= c) {
+#pragma unroll
+        for (int a = 1; a < KM; ++a) {
+            int y = a < kk ? best_y[a - 1] : -1;
+            if (a < kk && (y < 0 || y >= c)) {
                 // never taken (the shortlist holds at least kk - 1 candidates);
                 // keeps every index in range: the first active index not used
                 if (tid == 0) atomicOr(status, ST_NOT_CONVERGED);
                 for (y = 0; y < c; ++y) {
                     bool used = !on(mask, y);
+#pragma unroll
                     for (int b = 0; b < a; ++b) used |= T[b] == y;
                     if (!used) break;
                 }
             }
             T[a] = y;
         }
+        // the tuple in shared memory too, for the uses with run-time positions
+        if (tid == 0) {
+#pragma unroll
+            for (int a = 0; a < KM; ++a)
+                if (a < kk) s_Tt[a] = T[a];
+        }
+        __syncthreads();
         // FP64 k x k block: diagonal kept, (i, partner) from the re-score, the
         // partner pairs by further dot products
         if (tid == 0) {
-            for (int a = 0; a < kk; ++a) s_GT[a * kk + a] = gd[T[a]];
-            for (int a = 1; a < kk; ++a) {
-                s_GT[a] = best_g[a - 1];
-                s_GT[a * kk] = best_g[a - 1];
-            }
+            for (int a = 0; a < kk; ++a) s_GT[a * kk + a] = gd[s_Tt[a]];
+#pragma unroll
+            for (int a = 1; a < KM; ++a)
+                if (a < kk) {
+                    s_GT[a] = best_g[a - 1];
+                    s_GT[a * kk] = best_g[a - 1];
+                }
         }
         if (kk >= 3) {
             // the partners' pairs (a < b, both >= 1): partial sums as above
@@ -556,8 +576,8 @@ k_select_mixed(int64_t s, const int64_t *coff, const int32_t *members, const int
                 const int nb = kk - 1 - a;
                 if (nb <= 0) continue;
                 const double *xs[DOT_BATCH];
-                for (int b = 0; b < DOT_BATCH; ++b) xs[b] = X + (int64_t)T[a + 1 + (b < nb ? b : 0)] * s;
-                const double v = slice_dots(X + (int64_t)T[a] * s, xs, nb, cs0, cs1, red);
+                for (int b = 0; b < DOT_BATCH; ++b) xs[b] = X + (int64_t)s_Tt[a + 1 + (b < nb ? b : 0)] * s;
+                const double v = slice_dots(X + (int64_t)s_Tt[a] * s, xs, nb, cs0, cs1, red);
                 if (tid < nb) {
                     const int64_t slot = (int64_t)(par * CL + rank) * PAIRS + pi + tid;
                     if constexpr (CL > 1) {
@@ -600,45 +620,58 @@ k_select_mixed(int64_t s, const int64_t *coff, const int32_t *members, const int
         __syncthreads();
         // FP64 rows X_T <- O X_T (this CTA's columns)
         for (int64_t r = cs0 + tid; r < cs1; r += MX_THREADS) {
-            double in[8], out[8];
-            for (int a = 0; a < kk; ++a) in[a] = X[(int64_t)T[a] * s + r];
-            for (int a = 0; a < kk; ++a) out[a] = rot_row(s_O, kk, a, in);
-            for (int a = 0; a < kk; ++a) X[(int64_t)T[a] * s + r] = out[a];
+            double in[KM], out[KM];
+#pragma unroll
+            for (int a = 0; a < KM; ++a) in[a] = a < kk ? X[(int64_t)T[a] * s + r] : 0.0;
+#pragma unroll
+            for (int a = 0; a < KM; ++a) out[a] = a < kk ? rot_row_u<KM>(s_O, kk, a, in) : 0.0;
+#pragma unroll
+            for (int a = 0; a < KM; ++a)
+                if (a < kk) X[(int64_t)T[a] * s + r] = out[a];
         }
         // reduced-precision Gram rows and their bound; FP64 local block M
         {
-            float Of[64], Oa[64];
-            for (int a = 0; a < kk * kk; ++a) {
-                Of[a] = __double2float_rn(s_O[a]);
-                Oa[a] = fabsf(Of[a]);
-            }
+            float Of[KM * KM], Oa[KM * KM];   // O in FP32 and |O|, stride KM
+#pragma unroll
+            for (int a = 0; a < KM; ++a)
+#pragma unroll
+                for (int b = 0; b < KM; ++b) {
+                    Of[a * KM + b] = a < kk && b < kk ? __double2float_rn(s_O[a * kk + b]) : 0.0f;
+                    Oa[a * KM + b] = fabsf(Of[a * KM + b]);
+                }
             // rounding of one rotated entry: kk products and sums in FP32 plus
             // the FP32 rounding of O itself
             const float gam = (float)(kk + 3) * 0x1p-24f;
             for (int y = tid; y < c; y += MX_THREADS) {
                 bool inT = false;
-                for (int a = 0; a < kk; ++a) inT |= T[a] == y;
+#pragma unroll
+                for (int a = 0; a < KM; ++a) inT |= a < kk && T[a] == y;
                 if (inT || !on(mask, y)) continue;
-                float gin[8], bin[8];
-                double min_[8];
-                for (int a = 0; a < kk; ++a) {
-                    gin[a] = G[(int64_t)T[a] * c + y];
-                    bin[a] = B[(int64_t)T[a] * c + y];
-                    min_[a] = M[(int64_t)T[a] * c + y];
+                float gin[KM], bin[KM];
+                double min_[KM];
+#pragma unroll
+                for (int a = 0; a < KM; ++a) {
+                    gin[a] = a < kk ? G[(int64_t)T[a] * c + y] : 0.0f;
+                    bin[a] = a < kk ? B[(int64_t)T[a] * c + y] : 0.0f;
+                    min_[a] = a < kk ? M[(int64_t)T[a] * c + y] : 0.0;
                 }
-                for (int a = 0; a < kk; ++a) {
+#pragma unroll
+                for (int a = 0; a < KM; ++a) {
+                    if (a >= kk) continue;
                     float gv = 0.0f, bv = 0.0f, mag = 0.0f;
-                    for (int b = 0; b < kk; ++b) {
-                        gv = __fmaf_rn(Of[a * kk + b], gin[b], gv);
-                        bv = __fmaf_ru(Oa[a * kk + b], bin[b], bv);
-                        mag = __fmaf_ru(Oa[a * kk + b], fabsf(gin[b]), mag);
+#pragma unroll
+                    for (int b = 0; b < KM; ++b) {
+                        if (b >= kk) continue;
+                        gv = __fmaf_rn(Of[a * KM + b], gin[b], gv);
+                        bv = __fmaf_ru(Oa[a * KM + b], bin[b], bv);
+                        mag = __fmaf_ru(Oa[a * KM + b], fabsf(gin[b]), mag);
                     }
                     bv = __fmaf_ru(gam, mag, bv);
                     G[(int64_t)T[a] * c + y] = gv;
                     G[(int64_t)y * c + T[a]] = gv;
                     B[(int64_t)T[a] * c + y] = bv;
                     B[(int64_t)y * c + T[a]] = bv;
-                    const double mv = rot_row(s_O, kk, a, min_);
+                    const double mv = rot_row_u<KM>(s_O, kk, a, min_);
                     M[(int64_t)T[a] * c + y] = mv;
                     M[(int64_t)y * c + T[a]] = mv;
                 }
@@ -647,59 +680,63 @@ k_select_mixed(int64_t s, const int64_t *coff, const int32_t *members, const int
         // tuple blocks: G_TT' = O G_TT O^T in FP64 (diagonal kept), M_TT' likewise
         if (tid == 0 || tid == 32) {
             const bool isg = tid == 0;
-            double X2[64], R[64];
+            double *X2 = s_X2[isg ? 0 : 1], *R = s_R2[isg ? 0 : 1];   // scratch of this role
             for (int a = 0; a < kk; ++a)
                 for (int b = 0; b < kk; ++b)
-                    X2[a * kk + b] = isg ? s_GT[a * kk + b] : M[(int64_t)T[a] * c + T[b]];
+                    X2[a * kk + b] = isg ? s_GT[a * kk + b] : M[(int64_t)s_Tt[a] * c + s_Tt[b]];
             for (int cc = 0; cc < kk; ++cc) {
-                double in[8];
-                for (int b = 0; b < kk; ++b) in[b] = X2[b * kk + cc];
-                for (int a = 0; a < kk; ++a) R[a * kk + cc] = rot_row(s_O, kk, a, in);
+                double in[KM];
+#pragma unroll
+                for (int b = 0; b < KM; ++b) in[b] = b < kk ? X2[b * kk + cc] : 0.0;
+                for (int a = 0; a < kk; ++a) R[a * kk + cc] = rot_row_u<KM>(s_O, kk, a, in);
             }
             for (int a = 0; a < kk; ++a)
                 for (int b = a; b < kk; ++b) {
                     double acc = __dmul_rn(R[a * kk + kk - 1], s_O[b * kk + kk - 1]);
                     for (int cc = kk - 2; cc >= 0; --cc) acc = __fma_rn(R[a * kk + cc], s_O[b * kk + cc], acc);
+                    const int ta = s_Tt[a], tb = s_Tt[b];
                     if (isg) {
                         const float f = __double2float_rn(acc);
                         const float bf = __fadd_ru(__fmul_ru(fabsf(f), 0x1p-22f), 1e-30f);
-                        G[(int64_t)T[a] * c + T[b]] = f;
-                        G[(int64_t)T[b] * c + T[a]] = f;
-                        B[(int64_t)T[a] * c + T[b]] = bf;
-                        B[(int64_t)T[b] * c + T[a]] = bf;
-                        if (a == b) gd[T[a]] = acc;
+                        G[(int64_t)ta * c + tb] = f;
+                        G[(int64_t)tb * c + ta] = f;
+                        B[(int64_t)ta * c + tb] = bf;
+                        B[(int64_t)tb * c + ta] = bf;
+                        if (a == b) gd[ta] = acc;
                     } else {
-                        M[(int64_t)T[a] * c + T[b]] = acc;
-                        M[(int64_t)T[b] * c + T[a]] = acc;
-                        if (a == b) md[T[a]] = acc;
+                        M[(int64_t)ta * c + tb] = acc;
+                        M[(int64_t)tb * c + ta] = acc;
+                        if (a == b) md[ta] = acc;
                     }
                 }
         }
         __syncthreads();
         if (tid < kk) {
-            const double gv = gd[T[tid]];
-            w[T[tid]] = gv > 0.0 ? __ddiv_rn(1.0, __dsqrt_rn(gv)) : 0.0;
+            const int x = s_Tt[tid];
+            const double gv = gd[x];
+            w[x] = gv > 0.0 ? __ddiv_rn(1.0, __dsqrt_rn(gv)) : 0.0;
         }
         if (tid == 0) {
             int bi = 0;
-            double dbest = __dsub_rn(gd[T[0]], __dmul_rn(md[T[0]], md[T[0]]));
+            double dbest = __dsub_rn(gd[s_Tt[0]], __dmul_rn(md[s_Tt[0]], md[s_Tt[0]]));
             for (int a = 1; a < kk; ++a) {
-                const double d = __dsub_rn(gd[T[a]], __dmul_rn(md[T[a]], md[T[a]]));
+                const int x = s_Tt[a];
+                const double d = __dsub_rn(gd[x], __dmul_rn(md[x], md[x]));
                 if (d <= dbest) {
                     dbest = d;
                     bi = a;
                 }
             }
-            const int le = T[bi];
+            const int le = s_Tt[bi];
             int L = 0;
-            for (int a = 0; a < kk; ++a) L = max(L, lvl[T[a]]);
+            for (int a = 0; a < kk; ++a) L = max(L, lvl[s_Tt[a]]);
             ++L;
-            for (int a = 0; a < kk; ++a) lvl[T[a]] = L;
+            for (int a = 0; a < kk; ++a) lvl[s_Tt[a]] = L;
             s_maxlev = max(s_maxlev, L);
             mask[le >> 5] &= ~(1u << (le & 31));
             if (lead) {
                 const int64_t rr = r0 + t;
-                for (int a = 0; a < K; ++a) kidx[rr * K + a] = a < kk ? T[a] : -1;
+                for (int a = 0; a < K; ++a) kidx[rr * K + a] = a < kk ? s_Tt[a] : -1;
                 for (int a = 0; a < K * K; ++a) kO[rr * K * K + a] = a < kk * kk ? s_O[a] : 0.0;
                 kkv[rr] = kk;
                 kel[rr] = le;
@@ -899,10 +936,17 @@ pmmf_status mixed_stage_select(const DBuf<double> &D, int64_t s, const int32_t *
         return PMMF_OK;
     };
     prof_begin(KF_SELECT, st);
-    if (CLn == 8) PMMF_TRY(launch(k_select_mixed<8>, 8));
-    else if (CLn == 4) PMMF_TRY(launch(k_select_mixed<4>, 4));
-    else if (CLn == 2) PMMF_TRY(launch(k_select_mixed<2>, 2));
-    else PMMF_TRY(launch(k_select_mixed<1>, 1));
+    if (K <= 3) {
+        if (CLn == 8) PMMF_TRY(launch(k_select_mixed<8, 3>, 8));
+        else if (CLn == 4) PMMF_TRY(launch(k_select_mixed<4, 3>, 4));
+        else if (CLn == 2) PMMF_TRY(launch(k_select_mixed<2, 3>, 2));
+        else PMMF_TRY(launch(k_select_mixed<1, 3>, 1));
+    } else {
+        if (CLn == 8) PMMF_TRY(launch(k_select_mixed<8, 8>, 8));
+        else if (CLn == 4) PMMF_TRY(launch(k_select_mixed<4, 8>, 4));
+        else if (CLn == 2) PMMF_TRY(launch(k_select_mixed<2, 8>, 2));
+        else PMMF_TRY(launch(k_select_mixed<1, 8>, 1));
+    }
     prof_end(KF_SELECT, st, 0.0, 0.0);
     PMMF_TRY(launched("select_mixed"));
     if (K == 2) {

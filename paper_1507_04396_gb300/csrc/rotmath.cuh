@@ -50,6 +50,20 @@ __device__ __forceinline__ double rot_row(const double *O, int kk, int a, const 
     return acc;
 }
 
+// Row a of O x for a tuple of kk <= KM entries held in registers: rot_row's
+// chain (the last column's product, then fmas down to column 0) unrolled over
+// KM, so in[] is never indexed at run time.
+template <int KM>
+__device__ __forceinline__ double rot_row_u(const double *O, int kk, int a, const double (&in)[KM]) {
+    double acc = 0.0;
+#pragma unroll
+    for (int b = KM - 1; b >= 0; --b) {
+        if (b == kk - 1) acc = __dmul_rn(O[a * kk + b], in[b]);
+        else if (b < kk - 1) acc = __fma_rn(O[a * kk + b], in[b], acc);
+    }
+    return acc;
+}
+
 // Row a of x_T' = O^T x_T (the same chain on the transposed block).
 __device__ __forceinline__ double rot_row_t(const double *O, int kk, int a, const double *in) {
     double acc = __dmul_rn(O[(kk - 1) * kk + a], in[kk - 1]);

@@ -63,20 +63,6 @@ __device__ __forceinline__ bool better(unsigned long long k1, int i1, unsigned l
     return k1 > k2 || (k1 == k2 && i1 < i2);
 }
 
-// Row a of O x for a tuple of kk <= KM entries held in registers: rot_row's
-// chain (the last column's product, then fmas down to column 0) unrolled over
-// KM, so in[] is never indexed at run time.
-template <int KM>
-__device__ __forceinline__ double rot_row_u(const double *O, int kk, int a, const double (&in)[KM]) {
-    double acc = 0.0;
-#pragma unroll
-    for (int b = KM - 1; b >= 0; --b) {
-        if (b == kk - 1) acc = __dmul_rn(O[a * kk + b], in[b]);
-        else if (b < kk - 1) acc = __fma_rn(O[a * kk + b], in[b], acc);
-    }
-    return acc;
-}
-
 // KM: the largest tuple (3 for k = 3, 8 otherwise); the tuple's arrays are
 // sized by it and their loops unrolled.
 template <int KM>
