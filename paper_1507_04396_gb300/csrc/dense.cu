@@ -140,6 +140,9 @@ __global__ void k_level_scatter(const int64_t *coff, const int32_t *members, con
 
 // One CTA per row: the row in shared memory, every level's rotations applied
 // in turn (rotations of one level touch disjoint positions).
+// KM: the largest tuple (3 for k <= 3, 8 otherwise); a k-point rotation's
+// inputs and outputs are register arrays of that size.
+template <int KM>
 __global__ void __launch_bounds__(256)
 k_dense_rows(double *D, int64_t s, const int64_t *goffL, int nlv, DenseRotList L) {
     extern __shared__ double row[];
@@ -162,17 +165,23 @@ k_dense_rows(double *D, int64_t s, const int64_t *goffL, int nlv, DenseRotList L
                 const int64_t t = L.gt[q];
                 const int kk = L.kkv[t];
                 const int32_t *P = L.gpos + q * L.K;
-                double in[8];
+                double in[KM];
+                int pa[KM];
                 bool nz = false;
-                for (int a = 0; a < kk; ++a) {
-                    in[a] = row[P[a]];
-                    nz |= nonzero_bits(in[a]);
+#pragma unroll
+                for (int a = 0; a < KM; ++a) {
+                    pa[a] = a < kk ? P[a] : 0;
+                    in[a] = a < kk ? row[pa[a]] : 0.0;
+                    nz |= a < kk && nonzero_bits(in[a]);
                 }
                 if (nz) {
                     const double *O = L.kO + t * L.K * L.K;
-                    double out[8];
-                    for (int a = 0; a < kk; ++a) out[a] = rot_row(O, kk, a, in);
-                    for (int a = 0; a < kk; ++a) row[P[a]] = out[a];
+                    double out[KM];
+#pragma unroll
+                    for (int a = 0; a < KM; ++a) out[a] = a < kk ? rot_row_u<KM>(O, kk, a, in) : 0.0;
+#pragma unroll
+                    for (int a = 0; a < KM; ++a)
+                        if (a < kk) row[pa[a]] = out[a];
                 }
             }
         }
@@ -638,19 +647,20 @@ pmmf_status dense_update(DBuf<double> &D, int64_t s, const DenseLevels &lv, cons
         set_error("dense update: rows too long for shared memory");
         return PMMF_ERR_UNSUPPORTED;
     }
-    PMMF_CUDA_TRY(allow_smem(k_dense_rows, sh));
+    auto rows_kern = lv.L.K <= 3 ? k_dense_rows<3> : k_dense_rows<8>;
+    PMMF_CUDA_TRY(allow_smem(rows_kern, sh));
     DBuf<double> T;
     PMMF_TRY(T.alloc(s * s, st));
     // every pass reads and writes the s x s block once
     prof_begin(KF_ROWS, st);
-    k_dense_rows<<<(unsigned)s, 256, sh, st>>>(D.p, s, lv.goffL.p, lv.nlv, lv.L);
+    rows_kern<<<(unsigned)s, 256, sh, st>>>(D.p, s, lv.goffL.p, lv.nlv, lv.L);
     prof_end(KF_ROWS, st, 16.0 * (double)s * (double)s, 0.0);
     PMMF_TRY(launched("dense_rows"));
     dim3 tg((unsigned)((s + 31) / 32), (unsigned)((s + 31) / 32)), tb(32, 8);
     k_dense_transpose<<<tg, tb, 0, st>>>(D.p, s, T.p);
     PMMF_TRY(launched("dense_transpose"));
     prof_begin(KF_ROWS, st);
-    k_dense_rows<<<(unsigned)s, 256, sh, st>>>(T.p, s, lv.goffL.p, lv.nlv, lv.L);
+    rows_kern<<<(unsigned)s, 256, sh, st>>>(T.p, s, lv.goffL.p, lv.nlv, lv.L);
     prof_end(KF_ROWS, st, 16.0 * (double)s * (double)s, 0.0);
     PMMF_TRY(launched("dense_rows"));
     DBuf<int32_t> el, keep, sidx;
