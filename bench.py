@@ -738,7 +738,7 @@ def run_gpu_rbf(args):
                "identical_tuples": same, "rotations": info.rotations}
         g.close()
     value = n * n * args.steps / (ms / 1e3)
-    if prec != 0:
+    if prec != 0 and st["steps"] > 0:
         if prec == 1:
             pk, pk_kind = tf32_peak(dev)
         else:
@@ -753,6 +753,8 @@ def run_gpu_rbf(args):
                 "traffic": None, "kernel_family": "gram (tensor-core split product, stage 1)",
                 "peak_kind": pk_kind}
     else:
+        # FP64 mode, or a reduced-precision mode whose stages all had fewer
+        # clusters than the shortlist threshold (every Gram in FP64)
         f64, f64_kind = fp64_peak(stream)
         ach = gram["flops"] / (gram["ms"] / 1e3) / 1e12
         roof = {"bound": "alu", "achieved": ach, "peak": f64, "unit": "TFLOP/s",

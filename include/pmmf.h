@@ -473,7 +473,10 @@ pmmf_status pmmf_get_stage_matrix(const pmmf_handle *f, int p, int64_t *rowptr_n
  * the same bits), PMMF_TUNE_MIXED_ACTIVE (with a reduced-precision mode, the
  * stages with at least this many clusters use the reduced-precision Gram and
  * shortlist, the others the FP64 Gram and search; 0 = every stage; default
- * 12).
+ * 12), PMMF_TUNE_TC_GRAM (the reduced-precision Gram: 2 = tcgen05 MMAs with
+ * the accumulators in tensor memory and TMA-loaded operands (the default),
+ * 1 = warp-level mma.sync; the same 16-term FP32 chunks and compensated sums,
+ * so the same certified bound).
  * A value
  * applies to launches whose largest cluster has at most max_size coordinates
  * and no smaller bucket matches; shared-memory limits still halve the row and
@@ -484,7 +487,8 @@ pmmf_status pmmf_get_stage_matrix(const pmmf_handle *f, int p, int64_t *rowptr_n
 enum { PMMF_TUNE_ROWS_WARPS = 0, PMMF_TUNE_GRAM_WARPS = 1, PMMF_TUNE_SELECT_WARPS = 2,
        PMMF_TUNE_PASS1_ESTIMATE = 3, PMMF_TUNE_REACH_CLUSTERS = 4, PMMF_TUNE_ROWS_KERNEL = 5,
        PMMF_TUNE_DENSE_TILES = 6, PMMF_TUNE_SELECT_DSM = 7,
-       PMMF_TUNE_APPLY_FUSED = 8, PMMF_TUNE_SELECT_BLOCKS = 9, PMMF_TUNE_MIXED_ACTIVE = 10 };
+       PMMF_TUNE_APPLY_FUSED = 8, PMMF_TUNE_SELECT_BLOCKS = 9, PMMF_TUNE_MIXED_ACTIVE = 10,
+       PMMF_TUNE_TC_GRAM = 11 };
 pmmf_status pmmf_set_tuning(int param, int64_t max_size, int value);
 void pmmf_clear_tuning(void);
 
@@ -504,6 +508,23 @@ uint64_t pmmf_alloc_count(void);
  * the best of three timed launches (CUDA events on stream, after one
  * warm-up launch) counts 2 flops per fma.  Synchronizes the stream. */
 pmmf_status pmmf_probe_fp64(double *tflops, void *stream);
+
+/* The reduced-precision Gram matrix of the shortlist search (the tensor-core
+ * screen of pattern (1) on the local Grams of Sec. 2.1) for one set of rows,
+ * a diagnostic that exposes the kernel the factorization uses: X is a HOST
+ * rows x s FP64 row-major matrix (1 <= rows <= 4096, 1 <= s <= 2^24), G a HOST
+ * rows x rows FP32 output (row-major, symmetric) receiving
+ * G~ = hi hi^T + hi lo^T + lo hi^T for the split x = hi + lo of every entry
+ * (precision PMMF_PREC_TF32: hi, lo TF32, rounded to nearest with ties away;
+ * PMMF_PREC_BF16: BF16, to nearest even), summed in FP32 chunks of 16 terms
+ * that are added into compensated FP32 sums; the kernel follows
+ * PMMF_TUNE_TC_GRAM.  |G~_ij - (X X^T)_ij| stays within the shortlist's
+ * certified bound eps sqrt(G_ii G_jj).  INVALID_ARG for NULL buffers, sizes
+ * out of range or precision PMMF_PREC_FP64; TIMEOUT if a bounded wait of the
+ * tensor-core pipeline ran out.  The caller owns both buffers; synchronizes
+ * the stream. */
+pmmf_status pmmf_gram_reduced(const double *X, int64_t rows, int64_t s, int precision, float *G,
+                              void *stream);
 
 /* ---- profiling (measurement aid; no counterpart in the paper) -------------
  * Kernel families: 0 partition (k-means assignment), 1 Gram, 2 rotation

@@ -715,7 +715,7 @@ pmmf_status factor_dense_impl(const pmmf_matrix *A, const pmmf_params *prm, pmmf
             if (hs & ST_NOT_CONVERGED)
                 return fail(PMMF_ERR_NOT_CONVERGED, "k x k Jacobi did not converge in 32 sweeps");
             if (hs & ST_TIMEOUT)
-                return fail(PMMF_ERR_TIMEOUT, "dense update: a tile copy did not complete");
+                return fail(PMMF_ERR_TIMEOUT, "a bounded wait of the tensor-core Gram ran out");
             for (int32_t v : nl) nlv = std::max(nlv, v);
             S.max_levels = nlv;
         }

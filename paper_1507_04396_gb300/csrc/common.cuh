@@ -76,7 +76,7 @@ enum TuneParam : int {
     TUNE_ROWS_WARPS = 0, TUNE_GRAM_WARPS = 1, TUNE_SELECT_WARPS = 2, TUNE_PASS1_ESTIMATE = 3,
     TUNE_REACH_CLUSTERS = 4, TUNE_ROWS_KERNEL = 5, TUNE_DENSE_TILES = 6, TUNE_SELECT_DSM = 7,
     TUNE_APPLY_FUSED = 8, TUNE_SELECT_BLOCKS = 9,
-    TUNE_MIXED_ACTIVE = 10, TUNE_COUNT = 11
+    TUNE_MIXED_ACTIVE = 10, TUNE_TC_GRAM = 11, TUNE_COUNT = 12
 };
 int tuned(int param, int64_t size, int fallback);
 

@@ -684,8 +684,6 @@ pmmf_status dense_update(DBuf<double> &D, int64_t s, const DenseLevels &lv, cons
     return launched("dense_compact");
 }
 
-namespace {
-
 // cuTensorMapEncodeTiled from the driver (looked up once).
 PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
     static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
@@ -703,6 +701,8 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
     }
     return fn;
 }
+
+namespace {
 
 // A rows x cols FP64 row-major block as a tensor map with RB x TILE_W boxes.
 pmmf_status tile_map(CUtensorMap *m, double *base, int64_t rows, int64_t cols, int rb) {

@@ -1,6 +1,9 @@
 // dense.cuh -- the stage on a dense active matrix (internal).
 #pragma once
 
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
 #include <vector>
 
 #include "rotmath.cuh"
@@ -55,6 +58,9 @@ pmmf_status dense_update_tiles(DBuf<double> &D, int64_t s, const StageClusters &
                                int64_t stage, double *hdiag, double *contrib, DBuf<double> &Dnext,
                                DBuf<int32_t> &nact, int64_t &s2, unsigned *status, cudaStream_t st,
                                bool *used);
+// cuTensorMapEncodeTiled from the driver, looked up once; nullptr when the
+// driver does not export it.
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn();
 // Number of entries that are not +-0.
 pmmf_status dense_nonzeros(const double *D, int64_t cnt, int64_t *out, cudaStream_t st);
 pmmf_status dense_core(const double *D, int64_t s, const int32_t *act, double *core, double *hdiag,

@@ -147,18 +147,6 @@ constexpr int KFLUSH = 16;  // FP32 accumulation length before the chunk sum is
                             // MMA's k step): the FP32 part of the certified bound
                             // grows with it, the additions shrink
 
-// s + x kept as the FP32 pair (hi, lo): hi takes the rounded sum, lo gathers
-// the exact rounding errors of those additions (Knuth's TwoSum; the cascaded
-// summation "Sum2" of Ogita, Rump and Oishi, 2005).  FP32 instructions only,
-// where an FP64 add per chunk and output would load the SM's small FP64 pipe.
-__device__ __forceinline__ void two_sum_acc(float &hi, float &lo, float x) {
-    const float s = __fadd_rn(hi, x);
-    const float bp = __fsub_rn(s, hi);
-    const float err = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bp)), __fsub_rn(x, bp));
-    hi = s;
-    lo = __fadd_rn(lo, err);
-}
-
 __device__ __forceinline__ void mma_bf16(float *d, const uint32_t *a, const uint32_t *b) {
     asm volatile(
         "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 "
@@ -272,7 +260,10 @@ k_tc_gram(const void *XH, const void *XL, int64_t sp /* padded row length */,
             for (int q = 0; q < 4; ++q) {
                 const int a = a0 + wm + i * 16 + g + (q >= 2 ? 8 : 0);
                 const int b = b0 + wn + j * 8 + 2 * t + (q & 1);
-                if (a < c && b < c) {
+                // on a diagonal tile only a <= b is taken (both positions):
+                // (a, b) and (b, a) are separate sums there, and one of them
+                // must fill both places
+                if (a < c && b < c && (a0 != b0 || a <= b)) {
                     // hi + lo once, in FP64, then rounded to the stored FP32
                     const float f = __double2float_rn(__dadd_rn((double)shi[i][j][q], (double)slo[i][j][q]));
                     Gu[(int64_t)a * c + b] = f;
@@ -794,6 +785,45 @@ __global__ void k_to_givens(const int32_t *kidx, const int32_t *kel, const int32
 
 }  // namespace
 
+// G~ of every cluster by the tcgen05 kernel (the default) or by the
+// warp-level mma.sync kernel (PMMF_TUNE_TC_GRAM = 1); the same chunking and
+// compensated sums, so the same certified bound.
+pmmf_status tc_gram(int precision, const void *XH, const void *XL, int64_t rows, int64_t sp,
+                    const int64_t *coff, const std::vector<int64_t> &hcoff, const int64_t *goff,
+                    float *G, unsigned *status, cudaStream_t st) {
+    int64_t cmax = 0;
+    for (size_t u = 0; u + 1 < hcoff.size(); ++u) cmax = std::max(cmax, hcoff[u + 1] - hcoff[u]);
+    if (tuned(TUNE_TC_GRAM, cmax, 2) == 2)
+        return tc_gram_tcgen05(precision, XH, XL, rows, sp, coff, hcoff, goff, G, status, st);
+    const int64_t m = (int64_t)hcoff.size() - 1;
+    std::vector<int32_t> tu, ta, tb;
+    for (int64_t u = 0; u < m; ++u) {
+        const int64_t c = hcoff[u + 1] - hcoff[u];
+        const int T = (int)((c + TG - 1) / TG);
+        for (int a = 0; a < T; ++a)
+            for (int b = a; b < T; ++b) {
+                tu.push_back((int32_t)u);
+                ta.push_back(a);
+                tb.push_back(b);
+            }
+    }
+    if (tu.empty()) return PMMF_OK;
+    DBuf<int32_t> dtu, dta, dtb;
+    PMMF_TRY(dtu.alloc((int64_t)tu.size(), st));
+    PMMF_TRY(dta.alloc((int64_t)tu.size(), st));
+    PMMF_TRY(dtb.alloc((int64_t)tu.size(), st));
+    PMMF_CUDA_TRY(cudaMemcpyAsync(dtu.p, tu.data(), sizeof(int32_t) * tu.size(), cudaMemcpyHostToDevice, st));
+    PMMF_CUDA_TRY(cudaMemcpyAsync(dta.p, ta.data(), sizeof(int32_t) * ta.size(), cudaMemcpyHostToDevice, st));
+    PMMF_CUDA_TRY(cudaMemcpyAsync(dtb.p, tb.data(), sizeof(int32_t) * tb.size(), cudaMemcpyHostToDevice, st));
+    if (precision == PMMF_PREC_BF16)
+        k_tc_gram<PMMF_PREC_BF16><<<(unsigned)tu.size(), 128, 0, st>>>(XH, XL, sp, coff, goff, dtu.p,
+                                                                      dta.p, dtb.p, G);
+    else
+        k_tc_gram<PMMF_PREC_TF32><<<(unsigned)tu.size(), 128, 0, st>>>(XH, XL, sp, coff, goff, dtu.p,
+                                                                      dta.p, dtb.p, G);
+    return launched("tc_gram");
+}
+
 pmmf_status mixed_stage_select(const DBuf<double> &D, int64_t s, const int32_t *pos,
                                const StageClusters &cls, const std::vector<int64_t> &hcoff,
                                int64_t cmax, int precision, uint64_t seed, int64_t stage,
@@ -807,9 +837,11 @@ pmmf_status mixed_stage_select(const DBuf<double> &D, int64_t s, const int32_t *
     DBuf<double> gd0;
     DBuf<float> Gt, Bd;
     PMMF_TRY(X.alloc(s * s, st));
-    const int64_t sp = precision == PMMF_PREC_BF16 ? s + (s & 1) : s;   // padded row length
-    PMMF_TRY(XH.alloc(precision == PMMF_PREC_BF16 ? s * sp / 2 : s * s, st));
-    PMMF_TRY(XL.alloc(precision == PMMF_PREC_BF16 ? s * sp / 2 : s * s, st));
+    // padded row length: a multiple of 8 elements keeps every row of the split
+    // slab on a 16-byte boundary (the TMA row stride)
+    const int64_t sp = (s + 7) / 8 * 8;
+    PMMF_TRY(XH.alloc(precision == PMMF_PREC_BF16 ? s * sp / 2 : s * sp, st));
+    PMMF_TRY(XL.alloc(precision == PMMF_PREC_BF16 ? s * sp / 2 : s * sp, st));
     PMMF_TRY(gd0.alloc(s, st));
     // CTAs per cluster: as many as the SMs allow (up to the portable 8), so
     // stages with few clusters still spread their FP64 work over the GPU;
@@ -837,39 +869,15 @@ pmmf_status mixed_stage_select(const DBuf<double> &D, int64_t s, const int32_t *
     PMMF_TRY(launched("row_norms"));
     k_local_block<<<(unsigned)m, 256, 0, st>>>(D.p, s, pos, cls.coff.p, cls.members.p, gb.goff.p, gb.M.p);
     PMMF_TRY(launched("local_block"));
-    std::vector<int32_t> tu, ta, tb;
-    for (int64_t u = 0; u < m; ++u) {
-        const int64_t c = hcoff[u + 1] - hcoff[u];
-        const int T = (int)((c + TG - 1) / TG);
-        for (int a = 0; a < T; ++a)
-            for (int b = a; b < T; ++b) {
-                tu.push_back((int32_t)u);
-                ta.push_back(a);
-                tb.push_back(b);
-            }
-    }
-    DBuf<int32_t> dtu, dta, dtb;
-    PMMF_TRY(dtu.alloc((int64_t)tu.size(), st));
-    PMMF_TRY(dta.alloc((int64_t)tu.size(), st));
-    PMMF_TRY(dtb.alloc((int64_t)tu.size(), st));
-    PMMF_CUDA_TRY(cudaMemcpyAsync(dtu.p, tu.data(), sizeof(int32_t) * tu.size(), cudaMemcpyHostToDevice, st));
-    PMMF_CUDA_TRY(cudaMemcpyAsync(dta.p, ta.data(), sizeof(int32_t) * ta.size(), cudaMemcpyHostToDevice, st));
-    PMMF_CUDA_TRY(cudaMemcpyAsync(dtb.p, tb.data(), sizeof(int32_t) * tb.size(), cudaMemcpyHostToDevice, st));
     double flops = 0.0;
     for (int64_t u = 0; u < m; ++u) {
         const double c = (double)(hcoff[u + 1] - hcoff[u]);
         flops += c * (c + 1.0) * (double)s;
     }
     prof_begin(KF_GRAM, st);
-    if (precision == PMMF_PREC_BF16)
-        k_tc_gram<PMMF_PREC_BF16><<<(unsigned)tu.size(), 128, 0, st>>>(XH.p, XL.p, sp, cls.coff.p, gb.goff.p,
-                                                                      dtu.p, dta.p, dtb.p, Gt.p);
-    else
-        k_tc_gram<PMMF_PREC_TF32><<<(unsigned)tu.size(), 128, 0, st>>>(XH.p, XL.p, sp, cls.coff.p, gb.goff.p,
-                                                                      dtu.p, dta.p, dtb.p, Gt.p);
-    prof_end(KF_GRAM, st, (precision == PMMF_PREC_BF16 ? 4.0 : 8.0) * (double)s * (double)s +
+    PMMF_TRY(tc_gram(precision, XH.p, XL.p, s, sp, cls.coff.p, hcoff, gb.goff.p, Gt.p, status, st));
+    prof_end(KF_GRAM, st, (precision == PMMF_PREC_BF16 ? 4.0 : 8.0) * (double)s * (double)sp +
                               4.0 * (double)gb.total, 3.0 * flops);
-    PMMF_TRY(launched("tc_gram"));
 
     // eps, relative to |x||y| per term: the split leaves |x - hi - lo| <= u^2 |x|
     // (u = 2^-11 TF32, 2^-8 BF16), the dropped lo lo^T term is <= u^2 |x||y|,
@@ -961,3 +969,57 @@ pmmf_status mixed_stage_select(const DBuf<double> &D, int64_t s, const int32_t *
 }
 
 }  // namespace pmmf
+
+using namespace pmmf;
+
+extern "C" pmmf_status pmmf_gram_reduced(const double *X, int64_t rows, int64_t s, int precision,
+                                         float *G, void *stream) {
+    set_error("");
+    if (!X || !G || rows < 1 || rows > 4096 || s < 1 || s > ((int64_t)1 << 24) ||
+        (precision != PMMF_PREC_TF32 && precision != PMMF_PREC_BF16)) {
+        set_error("pmmf_gram_reduced: NULL buffer, size out of range or not a reduced precision");
+        return PMMF_ERR_INVALID_ARG;
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    const int64_t sp = (s + 7) / 8 * 8;
+    DBuf<double> D, Xs;
+    DBuf<uint32_t> XH, XL;
+    DBuf<int32_t> iota;
+    DBuf<int64_t> coff, goff;
+    DBuf<float> Gd;
+    DBuf<unsigned> status;
+    PMMF_TRY(D.alloc(rows * s, st));
+    PMMF_TRY(Xs.alloc(rows * s, st));
+    PMMF_TRY(XH.zeros(precision == PMMF_PREC_BF16 ? rows * sp / 2 : rows * sp, st));
+    PMMF_TRY(XL.zeros(precision == PMMF_PREC_BF16 ? rows * sp / 2 : rows * sp, st));
+    PMMF_TRY(iota.alloc(rows, st));
+    PMMF_TRY(coff.alloc(2, st));
+    PMMF_TRY(goff.alloc(1, st));
+    PMMF_TRY(Gd.zeros(rows * rows, st));
+    PMMF_TRY(status.zeros(1, st));
+    std::vector<int32_t> hi((size_t)rows);
+    for (int64_t q = 0; q < rows; ++q) hi[(size_t)q] = (int32_t)q;
+    const int64_t hcoff_a[2] = {0, rows}, hgoff = 0;
+    PMMF_CUDA_TRY(cudaMemcpyAsync(D.p, X, sizeof(double) * (size_t)(rows * s), cudaMemcpyHostToDevice, st));
+    PMMF_CUDA_TRY(cudaMemcpyAsync(iota.p, hi.data(), sizeof(int32_t) * hi.size(), cudaMemcpyHostToDevice, st));
+    PMMF_CUDA_TRY(cudaMemcpyAsync(coff.p, hcoff_a, sizeof(hcoff_a), cudaMemcpyHostToDevice, st));
+    PMMF_CUDA_TRY(cudaMemcpyAsync(goff.p, &hgoff, sizeof(hgoff), cudaMemcpyHostToDevice, st));
+    if (precision == PMMF_PREC_BF16)
+        k_build_slab<PMMF_PREC_BF16><<<(unsigned)rows, 256, 0, st>>>(D.p, s, sp, iota.p, iota.p, Xs.p,
+                                                                     XH.p, XL.p);
+    else
+        k_build_slab<PMMF_PREC_TF32><<<(unsigned)rows, 256, 0, st>>>(D.p, s, sp, iota.p, iota.p, Xs.p,
+                                                                     XH.p, XL.p);
+    PMMF_TRY(launched("build_slab"));
+    const std::vector<int64_t> hcoff = {0, rows};
+    PMMF_TRY(tc_gram(precision, XH.p, XL.p, rows, sp, coff.p, hcoff, goff.p, Gd.p, status.p, st));
+    unsigned hs = 0;
+    PMMF_CUDA_TRY(cudaMemcpyAsync(G, Gd.p, sizeof(float) * (size_t)(rows * rows), cudaMemcpyDeviceToHost, st));
+    PMMF_CUDA_TRY(cudaMemcpyAsync(&hs, status.p, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
+    PMMF_CUDA_TRY(cudaStreamSynchronize(st));
+    if (hs & ST_TIMEOUT) {
+        set_error("pmmf_gram_reduced: a bounded wait in the tensor-core pipeline ran out");
+        return PMMF_ERR_TIMEOUT;
+    }
+    return PMMF_OK;
+}

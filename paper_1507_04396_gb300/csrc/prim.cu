@@ -726,6 +726,7 @@ pmmf_status pmmf_set_tuning(int param, int64_t max_size, int value) {
         (param == TUNE_DENSE_TILES && value != 1 && value != 2) ||
         (param == TUNE_SELECT_DSM && value != 1 && value != 2) ||
         (param == TUNE_APPLY_FUSED && value != 1 && value != 2) ||
+        (param == TUNE_TC_GRAM && value != 1 && value != 2) ||
         (param == TUNE_SELECT_BLOCKS && (value < 2 || value > 4))) {
         set_error("pmmf_set_tuning: unknown parameter or value out of range");
         return PMMF_ERR_INVALID_ARG;

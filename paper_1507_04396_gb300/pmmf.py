@@ -69,7 +69,8 @@ EXPORTS = ["pmmf_factor", "pmmf_apply", "pmmf_solve_precond", "pmmf_free", "pmmf
            "pmmf_profile_begin", "pmmf_profile_end", "pmmf_profile_records", "pmmf_apply_noalloc",
            "pmmf_get_info", "pmmf_get_stage_info", "pmmf_get_stage_clusters",
            "pmmf_get_stage_rotations", "pmmf_get_h", "pmmf_get_stage_matrix",
-           "pmmf_launch_count", "pmmf_alloc_count", "pmmf_probe_fp64", "pmmf_apply_backward", "pmmf_get_angles", "pmmf_set_angles",
+           "pmmf_launch_count", "pmmf_alloc_count", "pmmf_probe_fp64", "pmmf_gram_reduced",
+           "pmmf_apply_backward", "pmmf_get_angles", "pmmf_set_angles",
            "pmmf_set_h", "pmmf_factor_blockdiag", "pmmf_factor_batched", "pmmf_get_batch",
            "pmmf_get_precision_stats", "pmmf_set_tuning", "pmmf_clear_tuning",
            "pmmf_solve_precond_sym", "pmmf_block_angle_grad", "pmmf_shard_create",
@@ -119,6 +120,8 @@ def load(path: str = LIB_PATH):
     L.pmmf_alloc_count.argtypes = []
     L.pmmf_probe_fp64.restype = i32
     L.pmmf_probe_fp64.argtypes = [vp, vp]
+    L.pmmf_gram_reduced.restype = i32
+    L.pmmf_gram_reduced.argtypes = [vp, i64, i64, i32, vp, vp]
     L.pmmf_apply_noalloc.restype = i32
     L.pmmf_apply_noalloc.argtypes = [vp, i32, vp, vp, i64, i64, vp]
     L.pmmf_apply_backward.restype = i32
@@ -176,7 +179,7 @@ TUNING_PATH = os.path.join(_HERE, "tuning.json")
 TUNE_PARAMS = {"rows_warps": 0, "gram_warps": 1, "select_warps": 2, "pass1_estimate": 3,
                "reach_clusters": 4, "rows_kernel": 5, "dense_tiles": 6, "select_dsm": 7,
                "apply_fused": 8, "select_blocks": 9,
-               "mixed_active": 10}
+               "mixed_active": 10, "tc_gram": 11}
 
 
 def apply_tuning(path: str) -> bool:
@@ -364,6 +367,18 @@ def pmmf_probe_fp64(stream=None) -> float:
     v = C.c_double()
     _check(load().pmmf_probe_fp64(C.byref(v), _stream(stream)))
     return float(v.value)
+
+
+def pmmf_gram_reduced(x, precision: int, stream=None) -> np.ndarray:
+    """The reduced-precision Gram matrix the shortlist search screens with,
+    for the rows of x (rows x s, FP64): TF32 (1) or BF16 (2) split, FP32
+    16-term chunks on the tensor cores, compensated sums.  FP32 result."""
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    rows, s = x.shape
+    g = np.empty((rows, rows), dtype=np.float32)
+    _check(load().pmmf_gram_reduced(x.ctypes.data, rows, s, int(precision), g.ctypes.data,
+                                    _stream(stream)))
+    return g
 
 
 # ---------------------------------------------------------------- convenience
