@@ -124,6 +124,32 @@ __device__ __forceinline__ void tmem_wait32(uint32_t (&r)[32]) {
                  : "memory");
 }
 
+// Packed FP32 pairs (Blackwell's f32x2 arithmetic): each half is the IEEE
+// FP32 operation rounded to nearest, so two_sum_acc2 computes exactly what
+// two_sum_acc computes on each half, with half the instructions.
+__device__ __forceinline__ uint64_t f2_add(uint64_t a, uint64_t b) {
+    uint64_t d;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ uint64_t f2_sub(uint64_t a, uint64_t b) {
+    uint64_t d;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ uint64_t f2_pack(uint32_t lo, uint32_t hi) {
+    uint64_t d;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(d) : "r"(lo), "r"(hi));
+    return d;
+}
+__device__ __forceinline__ void two_sum_acc2(uint64_t &hi, uint64_t &lo, uint64_t x) {
+    const uint64_t s = f2_add(hi, x);
+    const uint64_t bp = f2_sub(s, hi);
+    const uint64_t err = f2_add(f2_sub(hi, f2_sub(s, bp)), f2_sub(x, bp));
+    hi = s;
+    lo = f2_add(lo, err);
+}
+
 __device__ __forceinline__ void mbar_init(uint64_t *bar, unsigned count) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(saddr(bar)), "r"(count) : "memory");
 }
@@ -297,11 +323,11 @@ k_tc_gram5(const __grid_constant__ CUtensorMap mah, const __grid_constant__ CUte
         const int quarter = wid & 3;
         const int col0 = ((wid - 2) >> 2) * CW;
         const int r = quarter * 32 + lane;   // tile row
-        float shi[CW], slo[CW];
+        uint64_t shi[CW / 2], slo[CW / 2];   // columns (2i, 2i + 1) per pair
 #pragma unroll
-        for (int i = 0; i < CW; ++i) {
-            shi[i] = 0.0f;
-            slo[i] = 0.0f;
+        for (int i = 0; i < CW / 2; ++i) {
+            shi[i] = 0ull;
+            slo[i] = 0ull;
         }
         const uint32_t tl = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)col0;
         // chunk q: wait for its buffer, issue its load (no wait)
@@ -321,7 +347,7 @@ k_tc_gram5(const __grid_constant__ CUtensorMap mah, const __grid_constant__ CUte
         };
         auto accumulate = [&](const uint32_t (&v)[32]) {
 #pragma unroll
-            for (int i = 0; i < CW; ++i) two_sum_acc(shi[i], slo[i], __uint_as_float(v[i]));
+            for (int i = 0; i < CW / 2; ++i) two_sum_acc2(shi[i], slo[i], f2_pack(v[2 * i], v[2 * i + 1]));
         };
         // two register sets: the next chunk's load is in flight while the
         // current one is summed
@@ -347,9 +373,12 @@ k_tc_gram5(const __grid_constant__ CUtensorMap mah, const __grid_constant__ CUte
         float *T = (float *)sm;   // [TC_M][TC_N + 1]
         if (ok) {
 #pragma unroll
-            for (int i = 0; i < CW; ++i)
-                T[r * (TC_N + 1) + col0 + i] =
-                    __double2float_rn(__dadd_rn((double)shi[i], (double)slo[i]));
+            for (int i = 0; i < CW; ++i) {
+                const int h = (i & 1) * 32;
+                const float fh = __uint_as_float((uint32_t)(shi[i / 2] >> h));
+                const float fl = __uint_as_float((uint32_t)(slo[i / 2] >> h));
+                T[r * (TC_N + 1) + col0 + i] = __double2float_rn(__dadd_rn((double)fh, (double)fl));
+            }
         }
         asm volatile("bar.sync 1, %0;" ::"n"(32 * TC_EPI_WARPS) : "memory");
         if (!*abort) {
