@@ -287,20 +287,48 @@ __device__ __forceinline__ double block_max(double v, double *red) {
 
 // Partial dot products of row xi with the rows xs[0..nb) over the columns
 // [r0, r1) (this CTA's slice), reduced over the CTA in a fixed order; thread b
-// < nb returns the b-th sum (others 0).  Ends with a barrier.
+// < nb returns the b-th sum (others 0).  Ends with a barrier.  Each thread
+// adds its columns in ascending order; the loops over the batch are unrolled
+// (sums and row pointers in registers) and two columns' loads are issued
+// together.
 __device__ double slice_dots(const double *xi, const double *const *xs, int nb, int64_t r0,
                              int64_t r1, double *red) {
     double acc[DOT_BATCH];
-    for (int b = 0; b < DOT_BATCH; ++b) acc[b] = 0.0;
-    for (int64_t r = r0 + threadIdx.x; r < r1; r += MX_THREADS) {
-        const double a = xi[r];
-        for (int b = 0; b < nb; ++b) acc[b] = __fma_rn(a, xs[b][r], acc[b]);
+    const double *p[DOT_BATCH];
+#pragma unroll
+    for (int b = 0; b < DOT_BATCH; ++b) {
+        acc[b] = 0.0;
+        p[b] = xs[b];
+    }
+    int64_t r = r0 + threadIdx.x;
+    for (; r + MX_THREADS < r1; r += 2 * MX_THREADS) {
+        const double a0 = xi[r], a1 = xi[r + MX_THREADS];
+        double v0[DOT_BATCH], v1[DOT_BATCH];
+#pragma unroll
+        for (int b = 0; b < DOT_BATCH; ++b) {
+            v0[b] = b < nb ? p[b][r] : 0.0;
+            v1[b] = b < nb ? p[b][r + MX_THREADS] : 0.0;
+        }
+#pragma unroll
+        for (int b = 0; b < DOT_BATCH; ++b)
+            if (b < nb) {
+                acc[b] = __fma_rn(a0, v0[b], acc[b]);
+                acc[b] = __fma_rn(a1, v1[b], acc[b]);
+            }
+    }
+    if (r < r1) {
+        const double a0 = xi[r];
+#pragma unroll
+        for (int b = 0; b < DOT_BATCH; ++b)
+            if (b < nb) acc[b] = __fma_rn(a0, p[b][r], acc[b]);
     }
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    for (int b = 0; b < nb; ++b) {
-        const double v = warp_sum(acc[b]);
-        if (lane == 0) red[b * MX_WARPS + w] = v;
-    }
+#pragma unroll
+    for (int b = 0; b < DOT_BATCH; ++b)
+        if (b < nb) {
+            const double v = warp_sum(acc[b]);
+            if (lane == 0) red[b * MX_WARPS + w] = v;
+        }
     __syncthreads();
     double v = 0.0;
     if (threadIdx.x < (unsigned)nb)
@@ -609,16 +637,28 @@ k_select_mixed(int64_t s, const int64_t *coff, const int32_t *members, const int
             }
         }
         __syncthreads();
-        // FP64 rows X_T <- O X_T (this CTA's columns)
-        for (int64_t r = cs0 + tid; r < cs1; r += MX_THREADS) {
-            double in[KM], out[KM];
+        // FP64 rows X_T <- O X_T (this CTA's columns); two columns per round,
+        // both loaded before either is stored
+        for (int64_t r = cs0 + tid; r < cs1; r += 2 * MX_THREADS) {
+            const bool two = r + MX_THREADS < cs1;
+            double in0[KM], in1[KM];
 #pragma unroll
-            for (int a = 0; a < KM; ++a) in[a] = a < kk ? X[(int64_t)T[a] * s + r] : 0.0;
+            for (int a = 0; a < KM; ++a) {
+                in0[a] = a < kk ? X[(int64_t)T[a] * s + r] : 0.0;
+                in1[a] = a < kk && two ? X[(int64_t)T[a] * s + r + MX_THREADS] : 0.0;
+            }
+            double out0[KM], out1[KM];
 #pragma unroll
-            for (int a = 0; a < KM; ++a) out[a] = a < kk ? rot_row_u<KM>(s_O, kk, a, in) : 0.0;
+            for (int a = 0; a < KM; ++a) {
+                out0[a] = a < kk ? rot_row_u<KM>(s_O, kk, a, in0) : 0.0;
+                out1[a] = a < kk && two ? rot_row_u<KM>(s_O, kk, a, in1) : 0.0;
+            }
 #pragma unroll
             for (int a = 0; a < KM; ++a)
-                if (a < kk) X[(int64_t)T[a] * s + r] = out[a];
+                if (a < kk) {
+                    X[(int64_t)T[a] * s + r] = out0[a];
+                    if (two) X[(int64_t)T[a] * s + r + MX_THREADS] = out1[a];
+                }
         }
         // reduced-precision Gram rows and their bound; FP64 local block M
         {
