@@ -280,8 +280,11 @@ __device__ __forceinline__ double block_max(double v, double *red) {
     __syncthreads();
     if (lane == 0) red[w] = v;
     __syncthreads();
-    double r = red[0];
-    for (int q = 1; q < MX_WARPS; ++q) r = fmax(r, red[q]);
+    // the MX_WARPS maxima by shuffles (max is exact, so any order gives the
+    // same value) rather than a serial loop in every thread: each FP64
+    // instruction a warp issues holds the SM's FP64 pipe
+    double r = red[lane % MX_WARPS];
+    for (int o = MX_WARPS / 2; o > 0; o >>= 1) r = fmax(r, __shfl_xor_sync(0xffffffffu, r, o));
     return r;
 }
 
@@ -323,12 +326,31 @@ __device__ double slice_dots(const double *xi, const double *const *xs, int nb, 
             if (b < nb) acc[b] = __fma_rn(a0, p[b][r], acc[b]);
     }
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    // the warp's 8 sums by a halving butterfly: at lane distance 16, 8, 4
+    // each lane keeps half of its sums (added to the partner's) and sends the
+    // other half, so lane L ends with the sum b = bits 4, 3, 2 of L over the
+    // lanes that share bits 0-1, completed at distances 2 and 1 (9 FP64 adds
+    // per lane instead of 8 full warp sums of 5)
+    static_assert(DOT_BATCH == 8, "the butterfly below halves 8 sums three times");
+    {
+        const bool h4 = lane & 16, h3 = lane & 8, h2 = lane & 4;
+        double k4[4], k3[2];
 #pragma unroll
-    for (int b = 0; b < DOT_BATCH; ++b)
-        if (b < nb) {
-            const double v = warp_sum(acc[b]);
-            if (lane == 0) red[b * MX_WARPS + w] = v;
+        for (int j = 0; j < 4; ++j) {
+            const double snd = h4 ? acc[j] : acc[4 + j];
+            k4[j] = __dadd_rn(h4 ? acc[4 + j] : acc[j], __shfl_xor_sync(0xffffffffu, snd, 16));
         }
+#pragma unroll
+        for (int j = 0; j < 2; ++j) {
+            const double snd = h3 ? k4[j] : k4[2 + j];
+            k3[j] = __dadd_rn(h3 ? k4[2 + j] : k4[j], __shfl_xor_sync(0xffffffffu, snd, 8));
+        }
+        double k2 = __dadd_rn(h2 ? k3[1] : k3[0], __shfl_xor_sync(0xffffffffu, h2 ? k3[0] : k3[1], 4));
+        k2 = __dadd_rn(k2, __shfl_xor_sync(0xffffffffu, k2, 2));
+        k2 = __dadd_rn(k2, __shfl_xor_sync(0xffffffffu, k2, 1));
+        const int b = (h4 ? 4 : 0) + (h3 ? 2 : 0) + (h2 ? 1 : 0);
+        if ((lane & 3) == 0 && b < nb) red[b * MX_WARPS + w] = k2;
+    }
     __syncthreads();
     double v = 0.0;
     if (threadIdx.x < (unsigned)nb)
@@ -391,6 +413,8 @@ k_select_mixed(int64_t s, const int64_t *coff, const int32_t *members, const int
     __shared__ int s_Tt[8];                          // this step's tuple
     __shared__ double s_X2[2][64], s_R2[2][64];      // the tuple blocks' scratch
     __shared__ int s_wcnt[MX_WARPS];
+    __shared__ double s_bs[8], s_bg[8];              // the partners found by warp 0
+    __shared__ int s_by[8];
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     // the CTAs of the cluster meet (one CTA: the block barrier)
     auto csync = [&]() {
@@ -525,16 +549,19 @@ k_select_mixed(int64_t s, const int64_t *coff, const int32_t *members, const int
             }
         }
         csync();
-        for (int q = 0; q < nsl; ++q) {
-            // the FP64 dot product: the CTAs' partial sums in rank order
-            const int y = sl[q];
-            double gv = pd[(int64_t)(par * CL) * c + q];
-            for (int r = 1; r < CL; ++r) gv = __dadd_rn(gv, pd[(int64_t)(par * CL + r) * c + q]);
-            {
+        if (wid == 0) {
+            // warp 0 alone: lane l scores the candidates l, l + 32, ... (the
+            // FP64 dot product: the CTAs' partial sums in rank order) into its
+            // own sorted top kk-1 (score descending, ties to the smaller
+            // index: a candidate takes the first place it beats, the entries
+            // below move down); then kk-1 rounds of a warp argmax over the
+            // lanes' heads, the winner's lane dropping its head, give the
+            // same list as one insertion pass over all candidates
+            for (int q = lane; q < nsl; q += 32) {
+                const int y = sl[q];
+                double gv = pd[(int64_t)(par * CL) * c + q];
+                for (int r = 1; r < CL; ++r) gv = __dadd_rn(gv, pd[(int64_t)(par * CL + r) * c + q]);
                 const double sc = f64_from_bits(f64_bits(__dmul_rn(gv, w[y])) & F64_ABS);
-                // insert into the top kk-1 (ties to the smaller index): the
-                // candidate takes the first place it beats and each displaced
-                // entry moves one place down, the last one dropping out
                 double cs = sc, cg = gv;
                 int cy = y;
 #pragma unroll
@@ -551,7 +578,48 @@ k_select_mixed(int64_t s, const int64_t *coff, const int32_t *members, const int
                     }
                 }
             }
+#pragma unroll
+            for (int a = 0; a < KM - 1; ++a) {
+                if (a >= kk - 1) break;
+                double hs = best_s[0];
+                int hy = best_y[0];
+                for (int o = 16; o > 0; o >>= 1) {
+                    const double os = __shfl_xor_sync(0xffffffffu, hs, o);
+                    const int oy = __shfl_xor_sync(0xffffffffu, hy, o);
+                    if (os > hs || (os == hs && oy < hy)) {
+                        hs = os;
+                        hy = oy;
+                    }
+                }
+                const unsigned own = __ballot_sync(0xffffffffu, best_y[0] == hy && best_s[0] == hs);
+                const int src = own ? __ffs(own) - 1 : 0;
+                const double hg = __shfl_sync(0xffffffffu, best_g[0], src);
+                if (lane == 0) {
+                    s_bs[a] = hs;
+                    s_by[a] = hy;
+                    s_bg[a] = hg;
+                }
+                if (own && lane == src) {
+#pragma unroll
+                    for (int b = 0; b < KM - 2; ++b) {
+                        best_s[b] = best_s[b + 1];
+                        best_y[b] = best_y[b + 1];
+                        best_g[b] = best_g[b + 1];
+                    }
+                    best_s[KM - 2] = -1.0;
+                    best_y[KM - 2] = 0x7fffffff;
+                    best_g[KM - 2] = 0.0;
+                }
+            }
         }
+        __syncthreads();
+#pragma unroll
+        for (int a = 0; a < KM - 1; ++a)
+            if (a < kk - 1) {
+                best_s[a] = s_bs[a];
+                best_y[a] = s_by[a];
+                best_g[a] = s_bg[a];
+            }
         int T[KM];
         T[0] = i;
 #pragma unroll
