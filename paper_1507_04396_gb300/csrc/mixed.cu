@@ -411,7 +411,7 @@ k_select_mixed(int64_t s, const int64_t *coff, const int32_t *members, const int
     __shared__ double s_O[64], s_GT[64], s_es[SL_MAX + 8];
     __shared__ double s_gw[64], s_J[4], s_R[4];   // the warp's Jacobi
     __shared__ int s_Tt[8];                          // this step's tuple
-    __shared__ double s_X2[2][64], s_R2[2][64];      // the tuple blocks' scratch
+    __shared__ double s_R2[2][64];                   // the tuple blocks' R = O X_TT
     __shared__ int s_wcnt[MX_WARPS];
     __shared__ double s_bs[8], s_bg[8];              // the partners found by warp 0
     __shared__ int s_by[8];
@@ -728,6 +728,50 @@ k_select_mixed(int64_t s, const int64_t *coff, const int32_t *members, const int
                     if (two) X[(int64_t)T[a] * s + r + MX_THREADS] = out1[a];
                 }
         }
+        // tuple blocks: G_TT' = O G_TT O^T in FP64 (from the FP64 block),
+        // M_TT' likewise, by warp 0 one entry per lane (R = O X_TT, then
+        // R O^T for a <= b, mirrored); their inputs are not among the entries
+        // the rows below rotate, so warp 0 joins the rows afterwards
+        if (wid == 0) {
+            const int nR = 2 * kk * kk;
+            for (int q = lane; q < nR; q += 32) {
+                const int mat = q / (kk * kk), t = q - mat * kk * kk;
+                const int a = t / kk, cc = t - a * kk;
+                double in[KM];
+#pragma unroll
+                for (int b = 0; b < KM; ++b)
+                    in[b] = b < kk ? (mat ? M[(int64_t)s_Tt[b] * c + s_Tt[cc]] : s_GT[b * kk + cc]) : 0.0;
+                s_R2[mat][a * kk + cc] = rot_row_u<KM>(s_O, kk, a, in);
+            }
+            __syncwarp();
+            const int nup = kk * (kk + 1) / 2;
+            for (int q = lane; q < 2 * nup; q += 32) {
+                const int mat = q / nup;
+                int t = q - mat * nup, a = 0;
+                while (t >= kk - a) {   // (a, b), a <= b, in row order
+                    t -= kk - a;
+                    ++a;
+                }
+                const int b = a + t;
+                const double *R = s_R2[mat];
+                double acc = __dmul_rn(R[a * kk + kk - 1], s_O[b * kk + kk - 1]);
+                for (int cc = kk - 2; cc >= 0; --cc) acc = __fma_rn(R[a * kk + cc], s_O[b * kk + cc], acc);
+                const int ta = s_Tt[a], tb = s_Tt[b];
+                if (mat == 0) {
+                    const float f = __double2float_rn(acc);
+                    const float bf = __fadd_ru(__fmul_ru(fabsf(f), 0x1p-22f), 1e-30f);
+                    G[(int64_t)ta * c + tb] = f;
+                    G[(int64_t)tb * c + ta] = f;
+                    B[(int64_t)ta * c + tb] = bf;
+                    B[(int64_t)tb * c + ta] = bf;
+                    if (a == b) gd[ta] = acc;
+                } else {
+                    M[(int64_t)ta * c + tb] = acc;
+                    M[(int64_t)tb * c + ta] = acc;
+                    if (a == b) md[ta] = acc;
+                }
+            }
+        }
         // reduced-precision Gram rows and their bound; FP64 local block M
         {
             float Of[KM * KM], Oa[KM * KM];   // O in FP32 and |O|, stride KM
@@ -775,39 +819,6 @@ k_select_mixed(int64_t s, const int64_t *coff, const int32_t *members, const int
                     M[(int64_t)y * c + T[a]] = mv;
                 }
             }
-        }
-        // tuple blocks: G_TT' = O G_TT O^T in FP64 (diagonal kept), M_TT' likewise
-        if (tid == 0 || tid == 32) {
-            const bool isg = tid == 0;
-            double *X2 = s_X2[isg ? 0 : 1], *R = s_R2[isg ? 0 : 1];   // scratch of this role
-            for (int a = 0; a < kk; ++a)
-                for (int b = 0; b < kk; ++b)
-                    X2[a * kk + b] = isg ? s_GT[a * kk + b] : M[(int64_t)s_Tt[a] * c + s_Tt[b]];
-            for (int cc = 0; cc < kk; ++cc) {
-                double in[KM];
-#pragma unroll
-                for (int b = 0; b < KM; ++b) in[b] = b < kk ? X2[b * kk + cc] : 0.0;
-                for (int a = 0; a < kk; ++a) R[a * kk + cc] = rot_row_u<KM>(s_O, kk, a, in);
-            }
-            for (int a = 0; a < kk; ++a)
-                for (int b = a; b < kk; ++b) {
-                    double acc = __dmul_rn(R[a * kk + kk - 1], s_O[b * kk + kk - 1]);
-                    for (int cc = kk - 2; cc >= 0; --cc) acc = __fma_rn(R[a * kk + cc], s_O[b * kk + cc], acc);
-                    const int ta = s_Tt[a], tb = s_Tt[b];
-                    if (isg) {
-                        const float f = __double2float_rn(acc);
-                        const float bf = __fadd_ru(__fmul_ru(fabsf(f), 0x1p-22f), 1e-30f);
-                        G[(int64_t)ta * c + tb] = f;
-                        G[(int64_t)tb * c + ta] = f;
-                        B[(int64_t)ta * c + tb] = bf;
-                        B[(int64_t)tb * c + ta] = bf;
-                        if (a == b) gd[ta] = acc;
-                    } else {
-                        M[(int64_t)ta * c + tb] = acc;
-                        M[(int64_t)tb * c + ta] = acc;
-                        if (a == b) md[ta] = acc;
-                    }
-                }
         }
         __syncthreads();
         if (tid < kk) {
