@@ -523,11 +523,13 @@ __device__ __forceinline__ Cand block_best(const Cand *wb) {
 
 // Restructured search for clusters of up to KPT * NCT coordinates (column
 // thread t owns columns t, t + NCT, ...).  Per step t with pivot i, partner j:
-//   P1   FP64 warps: the angle (prefix computed by warps 0 and 1, then c by
-//        one and s by the other), the four new diagonal entries of the 2x2
-//        blocks (one each); then the new weights of i and j (warps 0 and 1)
-//        beside the elimination and bookkeeping (warp 2) and the candidates
-//        for the pivot of step t + 2 (warp 3).  Column threads: load their
+//   P1   FP64 warps: warp 0 computes the angle (its prefix once, c and s
+//        by two lanes of one divide), the four new diagonal entries of the
+//        2x2 blocks (four lanes) and then the new weights of i and j (two
+//        lanes), beside the elimination and bookkeeping (warp 2) and the
+//        candidates for the pivot of step t + 2 (warp 3); an FP64 instruction
+//        holds the SM's FP64 pipe whatever its lanes do, so one warp's lanes
+//        take what several warps took before, at the same latency.  Column threads: load their
 //        columns of rows i, j and of the two rows a1, a2 that can be the pivot
 //        of step t + 1, classify them and list those that may need FP64 work.
 //   P2   column threads: FP64 work on the listed columns (the survivor's row
@@ -695,10 +697,11 @@ k_select_fast(const int64_t *coff, const int32_t *members, const int64_t *goff, 
                     cc = 1.0;
                     ss = 0.0;
                 } else {
-                    // angle prefix (jacobi2), computed by warps 0 and 1 (each
-                    // needs it for its divide); warps 2 and 3 stay off the
+                    // the angle (jacobi2) by warp 0 alone: its prefix once,
+                    // then c (lane 0) and s (the other lanes) as one divide
+                    // with lane-dependent numerators, so warps 1-3 stay off the
                     // SM's FP64 pipe meanwhile
-                    if (wid < 2) {
+                    if (wid == 0) {
                         double h = __dsub_rn(d, a);
                         double g = __dmul_rn(2.0, gij);
                         const unsigned long long hm = f64_bits(h) & ABS, gm = f64_bits(g) & ABS;
@@ -717,9 +720,9 @@ k_select_fast(const int64_t *coff, const int32_t *members, const int64_t *goff, 
                         const double r = __dsqrt_rn(__dadd_rn(__dmul_rn(h, h), g2v));
                         const double q = __dadd_rn(habs, r);
                         const double den = __dsqrt_rn(__dadd_rn(__dmul_rn(q, q), g2v));
-                        // c by warp 0, s by warp 1
-                        if (wid == 0) s_x[0] = __ddiv_rn(q, den);
-                        else s_x[1] = __ddiv_rn(hnonneg ? g : f64_from_bits(f64_bits(g) ^ ~ABS), den);
+                        const double num = lane == 0 ? q : (hnonneg ? g : f64_from_bits(f64_bits(g) ^ ~ABS));
+                        const double v = __ddiv_rn(num, den);
+                        if (lane < 2) s_x[lane] = v;
                     }
                     fp_sync();
                     cc = s_x[0];
@@ -727,34 +730,31 @@ k_select_fast(const int64_t *coff, const int32_t *members, const int64_t *goff, 
                     fp_sync();
                 }
                 // new diagonal entries of the 2x2 blocks (rot_block's na, nd):
-                // G_ii by warp 0, G_jj by warp 1, M_ii by warp 2, M_jj by warp 3
-                {
-                    const double xa = wid < 2 ? a : ma0;
-                    const double xb = wid < 2 ? gij : mij;
-                    const double xd = wid < 2 ? d : md0;
-                    double v;
-                    if ((wid & 1) == 0) {
-                        const double rii = __fma_rn(cc, xa, -__dmul_rn(ss, xb));
-                        const double rij = __fma_rn(cc, xb, -__dmul_rn(ss, xd));
-                        v = __fma_rn(rii, cc, __dmul_rn(rij, -ss));
-                    } else {
-                        const double rji = __fma_rn(ss, xa, __dmul_rn(cc, xb));
-                        const double rjj = __fma_rn(ss, xb, __dmul_rn(cc, xd));
-                        v = __fma_rn(rji, ss, __dmul_rn(rjj, cc));
-                    }
-                    s_x[wid] = v;
+                // G_ii, G_jj, M_ii, M_jj by lanes 0-3 of warp 0, one formula
+                // with (p, q) = (c, -s) for the i entries and (s, c) for the j
+                // entries: rot_block's operations, the negations exact
+                if (wid == 0 && lane < 4) {
+                    const bool gm = lane < 2, ev = (lane & 1) == 0;
+                    const double xa = gm ? a : ma0;
+                    const double xb = gm ? gij : mij;
+                    const double xd = gm ? d : md0;
+                    const double p = ev ? cc : ss;
+                    const double qv = ev ? -ss : cc;
+                    const double r1 = __fma_rn(p, xa, __dmul_rn(qv, xb));
+                    const double r2 = __fma_rn(p, xb, __dmul_rn(qv, xd));
+                    s_x[lane] = __fma_rn(r1, p, __dmul_rn(r2, qv));
                 }
                 fp_sync();
                 const double na = s_x[0], nd = s_x[1], ma = s_x[2], md2 = s_x[3];
-                if (wid < 2) {
-                    // the new weights of i (warp 0) and j (warp 1), next to the
-                    // elimination rather than after it; the survivor's is
+                if (wid == 0) {
+                    // the new weights of i (lane 0) and j (lane 1), next to
+                    // the elimination rather than after it; the survivor's is
                     // merged in P2 (the eliminated one is never read again)
-                    const double x = wid == 0 ? na : nd;
+                    const double x = lane == 0 ? na : nd;
                     const double wv = pos_bits(x) ? __ddiv_rn(1.0, __dsqrt_rn(x)) : 0.0;
-                    if (lane == 0) {
-                        s_wn[par][wid] = wv;
-                        w[wid == 0 ? i : j] = wv;
+                    if (lane < 2) {
+                        s_wn[par][lane] = wv;
+                        w[lane == 0 ? i : j] = wv;
                     }
                 } else if (wid == 2 && lane == 0) {
                     const double di = __dsub_rn(na, __dmul_rn(ma, ma));
