@@ -347,12 +347,12 @@ def run_gpu(args):
     f = factor()
     if dominant == "select":
         # DRAM bytes per launch of the rotation search, measured with ncu on
-        # this workload's stage-2 launch: 157.7 MB = 1.159 x 16 B per Gram
+        # this workload's stage-2 launch: 157.6 MB = 1.158 x 16 B per Gram
         # entry (G and M streamed once, plus the prefetched rows of candidate
         # partners that were not chosen); scaled to every launch by its Gram
         # entries
         sq = [int((np.diff(f.clusters(p)[0]) ** 2).sum()) for p in range(f.info().stages)]
-        roof["traffic"] = 1.159 * 16.0 * sum(sq) / max(len(sq), 1)
+        roof["traffic"] = 1.158 * 16.0 * sum(sq) / max(len(sq), 1)
         roof["traffic_basis"] = ("ncu DRAM bytes of the stage-2 launch at n=65536 scaled by "
                                  "Gram entries per launch")
     x = torch.randn(a.n, NRHS_APPLY, dtype=torch.float64, device=dev)
