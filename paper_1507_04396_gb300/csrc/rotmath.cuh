@@ -41,6 +41,34 @@ __device__ __forceinline__ void jacobi2(double a, double b, double d, double &c,
     s = __ddiv_rn(hnonneg ? g : f64_from_bits(f64_bits(g) ^ ~ABS), den);
 }
 
+// jacobi2's c (want_s false) or s (want_s true): the same operations as
+// jacobi2 for that value.  Lanes of one warp that call it with different
+// want_s share the prefix's instructions and take both divides as one.
+__device__ __forceinline__ double jacobi2_one(double a, double b, double d, bool want_s) {
+    const unsigned long long ABS = 0x7fffffffffffffffull;
+    if ((f64_bits(b) & ABS) == 0) return want_s ? 0.0 : 1.0;
+    double h = __dsub_rn(d, a);
+    double g = __dmul_rn(2.0, b);
+    const unsigned long long hm = f64_bits(h) & ABS, gm = f64_bits(g) & ABS;
+    const unsigned long long mm = hm > gm ? hm : gm;
+    if (mm > (unsigned long long)__double_as_longlong(0x1p500)) {
+        h = __dmul_rn(h, 0x1p-600);
+        g = __dmul_rn(g, 0x1p-600);
+    } else if (mm < (unsigned long long)__double_as_longlong(0x1p-500)) {
+        h = __dmul_rn(h, 0x1p600);
+        g = __dmul_rn(g, 0x1p600);
+    }
+    const unsigned long long hb = f64_bits(h);
+    const double habs = f64_from_bits(hb & ABS);
+    const bool hnonneg = (hb >> 63) == 0 || (hb & ABS) == 0;
+    const double g2 = __dmul_rn(g, g);
+    const double r = __dsqrt_rn(__dadd_rn(__dmul_rn(h, h), g2));
+    const double q = __dadd_rn(habs, r);
+    const double den = __dsqrt_rn(__dadd_rn(__dmul_rn(q, q), g2));
+    const double num = want_s ? (hnonneg ? g : f64_from_bits(f64_bits(g) ^ ~ABS)) : q;
+    return __ddiv_rn(num, den);
+}
+
 // Row a of x_T' = O x_T for a k x k block O (row-major, stride kk): an fma
 // chain over b from kk-1 down to 0.  For kk = 2 and O = [[c, -s], [s, c]]
 // this is rot_pair.
@@ -80,8 +108,9 @@ __device__ __forceinline__ double rot_row_t(const double *O, int kk, int a, cons
 // pair's rotation J = [[c, -s], [s, c]] (jacobi2) updates g <- J g J^T
 // (rows p, q recomputed at the other columns from the old values and
 // mirrored; the 2 x 2 block as R = J g_TT, then R J^T for a <= b, mirrored)
-// and O (starting at I) <- J O on rows p, q.  Lane 0 takes the serial parts (the sweep's sums,
-// each pair's angle); every new entry is fma(P0, Q0, P1 * Q1) of pre-pair
+// and O (starting at I) <- J O on rows p, q.  Lanes 0 and 1 take the serial
+// parts (the sweep's two sums side by side; each pair's angle, c on lane 0
+// and s on lane 1 from one instruction stream); every new entry is fma(P0, Q0, P1 * Q1) of pre-pair
 // values (the rows p, q of g at the other columns, R = J X_TT, the rows p, q
 // of O), one lane per entry (2(k-2) + 4 + 2k <= 32 for k <= 8), then the
 // 2 x 2 block's R J^T by three lanes, each the same operations on the same
@@ -94,26 +123,33 @@ __device__ inline bool jacobi_k_warp(int k, double *gs, double *os, double *js, 
     __syncwarp();
     const int ny = 2 * (k - 2), nt = ny + 4 + 2 * k;
     for (int sweep = 0;; ++sweep) {
-        int state = 0;
+        // the sweep's two sums side by side: the off-diagonal one on lane 0,
+        // the diagonal one on lane 1 (each the same sequence of operations)
+        double sum = 0.0;
         if (lane == 0) {
-            double off = 0.0, dg = 0.0;
             for (int p = 0; p < k; ++p)
-                for (int q = p + 1; q < k; ++q) off = __dadd_rn(off, __dmul_rn(gs[p * k + q], gs[p * k + q]));
-            for (int p = 0; p < k; ++p) dg = __dadd_rn(dg, __dmul_rn(gs[p * k + p], gs[p * k + p]));
-            state = off <= __dmul_rn(1e-30, dg) ? 1 : (sweep == 32 ? 2 : 0);
+                for (int q = p + 1; q < k; ++q) sum = __dadd_rn(sum, __dmul_rn(gs[p * k + q], gs[p * k + q]));
+        } else if (lane == 1) {
+            for (int p = 0; p < k; ++p) sum = __dadd_rn(sum, __dmul_rn(gs[p * k + p], gs[p * k + p]));
         }
+        const double dg = __shfl_sync(full, sum, 1);
+        int state = 0;
+        if (lane == 0) state = sum <= __dmul_rn(1e-30, dg) ? 1 : (sweep == 32 ? 2 : 0);
         state = __shfl_sync(full, state, 0);
         if (state) return state == 1;
         for (int p = 0; p < k - 1; ++p) {
             for (int q = p + 1; q < k; ++q) {
                 if (gs[p * k + q] == 0.0) continue;   // the same value in every lane
-                if (lane == 0) {
-                    double c, s;
-                    jacobi2(gs[p * k + p], gs[p * k + q], gs[q * k + q], c, s);
-                    js[0] = c;
-                    js[1] = -s;
-                    js[2] = s;
-                    js[3] = c;
+                // the pair's angle: c on lane 0, s on lane 1 (one divide)
+                {
+                    const double v = jacobi2_one(gs[p * k + p], gs[p * k + q], gs[q * k + q], lane == 1);
+                    if (lane == 0) {
+                        js[0] = v;
+                        js[3] = v;
+                    } else if (lane == 1) {
+                        js[1] = -v;
+                        js[2] = v;
+                    }
                 }
                 __syncwarp();
                 // this lane's entry: fma(J[2a], x_p, J[2a+1] x_q) with (x_p, x_q)
