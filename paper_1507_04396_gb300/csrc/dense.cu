@@ -132,10 +132,54 @@ __global__ void k_level_scatter(const int64_t *coff, const int32_t *members, con
                     L.gt[slot] = t;
                     for (int a = 0; a < L.K; ++a)
                         L.gpos[slot * L.K + a] = a < kk ? pos[members[base + L.kidx[t * L.K + a]]] : -1;
+                    if (L.gO3) {
+                        // k = 3: the record in slot order (no load through t)
+                        L.gkk[slot] = kk;
+                        for (int a = 0; a < 3; ++a)
+                            for (int b = 0; b < 3; ++b)
+                                L.gO3[slot * 9 + a * 3 + b] = a < kk && b < kk ? L.kO[t * 9 + a * kk + b] : 0.0;
+                    }
                 }
             }
         }
     }
+}
+
+// A k = 3 slot's record in registers (scalars, so it never needs an address).
+struct Rec3 {
+    int kk, p0, p1, p2;
+    double o0, o1, o2, o3, o4, o5, o6, o7, o8;
+};
+
+__device__ __forceinline__ Rec3 rec3_load(const int32_t *gkk, const int32_t *gpos, const double *gO3,
+                                          int64_t q) {
+    const double *O = gO3 + q * 9;
+    const int32_t *P = gpos + q * 3;
+    return Rec3{gkk[q], P[0], P[1], P[2], O[0], O[1], O[2], O[3], O[4], O[5], O[6], O[7], O[8]};
+}
+
+// Row a of x_T' = O x_T for a tuple of kk <= 3 (O's row a is oa0..oa2): the
+// chain of rot_row_u<3>, the last column's product, then fmas down to column 0.
+__device__ __forceinline__ double rec3_row(double oa0, double oa1, double oa2, int kk, double i0,
+                                           double i1, double i2) {
+    if (kk == 3) return __fma_rn(oa0, i0, __fma_rn(oa1, i1, __dmul_rn(oa2, i2)));
+    if (kk == 2) return __fma_rn(oa0, i0, __dmul_rn(oa1, i1));
+    return __dmul_rn(oa0, i0);
+}
+
+// x_T' = O x_T on the row held in shared memory; a tuple whose inputs are all
+// zero is skipped.
+__device__ __forceinline__ void rec3_apply(double *row, const Rec3 x) {
+    const double i0 = row[x.p0];
+    const double i1 = x.kk > 1 ? row[x.p1] : 0.0;
+    const double i2 = x.kk > 2 ? row[x.p2] : 0.0;
+    if (!(nonzero_bits(i0) || (x.kk > 1 && nonzero_bits(i1)) || (x.kk > 2 && nonzero_bits(i2)))) return;
+    const double n0 = rec3_row(x.o0, x.o1, x.o2, x.kk, i0, i1, i2);
+    const double n1 = rec3_row(x.o3, x.o4, x.o5, x.kk, i0, i1, i2);
+    const double n2 = rec3_row(x.o6, x.o7, x.o8, x.kk, i0, i1, i2);
+    row[x.p0] = n0;
+    if (x.kk > 1) row[x.p1] = n1;
+    if (x.kk > 2) row[x.p2] = n2;
 }
 
 // One CTA per row: the row in shared memory, every level's rotations applied
@@ -150,6 +194,37 @@ k_dense_rows(double *D, int64_t s, const int64_t *goffL, int nlv, DenseRotList L
     double *Dr = D + r * s;
     for (int64_t q = threadIdx.x; q < s; q += blockDim.x) row[q] = Dr[q];
     __syncthreads();
+    if constexpr (KM == 3) {
+        if (L.K == 3 && L.gO3) {
+            // k = 3 with slot-ordered records: the thread's first slot of the
+            // next level (positions, tuple size, block O) is loaded into
+            // registers while this level runs; the same chain per output as
+            // rot_row_u<3>, so the same bits
+            const int32_t *gkk = L.gkk, *gpos = L.gpos;
+            const double *gO3 = L.gO3;
+            if (nlv > 0) {
+                int64_t b0 = goffL[0], b1 = goffL[1];
+                const int64_t q0 = b0 + threadIdx.x;
+                Rec3 cur{};
+                if (q0 < b1) cur = rec3_load(gkk, gpos, gO3, q0);
+                for (int lv = 0; lv < nlv; ++lv) {
+                    const int64_t b2 = lv + 2 <= nlv ? goffL[lv + 2] : b1;
+                    const int64_t qn = b1 + threadIdx.x;
+                    Rec3 nxt{};
+                    if (lv + 1 < nlv && qn < b2) nxt = rec3_load(gkk, gpos, gO3, qn);
+                    if (b0 + threadIdx.x < b1) rec3_apply(row, cur);
+                    for (int64_t q = b0 + threadIdx.x + blockDim.x; q < b1; q += blockDim.x)
+                        rec3_apply(row, rec3_load(gkk, gpos, gO3, q));
+                    __syncthreads();
+                    cur = nxt;
+                    b0 = b1;
+                    b1 = b2;
+                }
+            }
+            for (int64_t q = threadIdx.x; q < s; q += blockDim.x) Dr[q] = row[q];
+            return;
+        }
+    }
     for (int lv = 0; lv < nlv; ++lv) {
         for (int64_t q = goffL[lv] + threadIdx.x; q < goffL[lv + 1]; q += blockDim.x) {
             if (L.K == 2) {
@@ -632,6 +707,12 @@ pmmf_status dense_levels(const StageClusters &cls, const StageRotations &rot, co
         PMMF_TRY(out.gpos.alloc(nr * rot.K, st));
         out.L.gt = out.gt.p;
         out.L.gpos = out.gpos.p;
+        if (rot.K == 3) {
+            PMMF_TRY(out.gkk.alloc(nr, st));
+            PMMF_TRY(out.gO3.alloc(nr * 9, st));
+            out.L.gkk = out.gkk.p;
+            out.L.gO3 = out.gO3.p;
+        }
     }
     k_level_scatter<<<grid_for(m, 128), 128, 0, st>>>(cls.coff.p, cls.members.p, pos, rot.roff.p,
                                                       rot.lvl_off.p, rot.nlev.p, m, out.goffL.p,

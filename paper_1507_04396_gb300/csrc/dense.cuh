@@ -18,6 +18,8 @@ struct DenseRotList {
     Rot2 *g2 = nullptr;               // k = 2: positions and (c, s)
     int64_t *gt = nullptr;            // k >= 3: step-order rotation of each slot
     int32_t *gpos = nullptr;          // k >= 3: K positions per slot (-1 unused)
+    int32_t *gkk = nullptr;           // k = 3: tuple size per slot
+    double *gO3 = nullptr;            // k = 3: the slot's block O, stride 3 (a * 3 + b)
     const Rot2 *lvlrot = nullptr;     // per-cluster sources
     const int32_t *lvlidx = nullptr, *kkv = nullptr, *kidx = nullptr;
     const double *kO = nullptr;
@@ -29,6 +31,8 @@ struct DenseLevels {
     DBuf<Rot2> g2;
     DBuf<int64_t> gt;
     DBuf<int32_t> gpos;
+    DBuf<int32_t> gkk;
+    DBuf<double> gO3;
     DenseRotList L;
 };
 
