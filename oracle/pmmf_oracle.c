@@ -21,6 +21,9 @@
  *  R4  Residual: contrib_p = sum of A_p[x,y]^2 over x != y in S_{p-1} with x or
  *      y eliminated in stage p; error = sqrt(sum_p contrib_p) / ||A||_F.
  *  R5  Random pick (Alg. 2, "uniformly at random"): counter-based splitmix64.
+ *      The generator is pinned by the published known answers; the choice of
+ *      stream is this file's definition (the paper gives none): parity
+ *      unpinned beyond its properties.
  *  R6  Partner score (Sec. 2.2, absolute value per the text): |G_ij| * w_j
  *      with w_j = 1 / sqrt(G_jj) (0 when G_jj is not positive); top k-1 by score,
  *      ties to the smaller local index.
@@ -32,6 +35,8 @@
  *      as a sequential fma chain (rows of the stored matrix).
  *  R10 Clustering (Alg. 1 "cluster", unspecified): k-means on quantized
  *      integer coordinates, Morton-order initialisation, exact integer arithmetic.
+ *      This file's definition (the paper gives none): parity unpinned, checked
+ *      by its properties (a partition, sizes, Lloyd's fixed point) only.
  *  R11 Stage schedule: e_u = floor(eta c_u); trimmed so |S_p| >= core size.
  *  R12 Inverse (Sec. 2.4): 1/H_xx on wavelet coordinates, core by Cholesky.
  *  R13 Blocked update (Alg. 1): A_p = (A_{p-1} Q^T)^T Q^T, i.e. Q applied to
