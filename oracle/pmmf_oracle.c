@@ -36,7 +36,8 @@
  *  R10 Clustering (Alg. 1 "cluster", unspecified): k-means on quantized
  *      integer coordinates, Morton-order initialisation, exact integer arithmetic.
  *      This file's definition (the paper gives none): parity unpinned, checked
- *      by its properties (a partition, sizes, Lloyd's fixed point) only.
+ *      by properties only (well-separated blobs recovered up to relabelling,
+ *      one-dimensional clusters are intervals).
  *  R11 Stage schedule: e_u = floor(eta c_u); trimmed so |S_p| >= core size.
  *  R12 Inverse (Sec. 2.4): 1/H_xx on wavelet coordinates, core by Cholesky.
  *  R13 Blocked update (Alg. 1): A_p = (A_{p-1} Q^T)^T Q^T, i.e. Q applied to
