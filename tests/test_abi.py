@@ -6,6 +6,7 @@ import ctypes as C
 import os
 import re
 
+import numpy as np
 import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
@@ -62,6 +63,15 @@ def test_invalid_parameters_rejected_without_gpu(lib):
     h = C.c_void_p()
     assert lib.pmmf_factor(C.byref(m), C.byref(prm), C.byref(h), None) == pmmf.ERR_INVALID_ARG
     lib.pmmf_free(None)   # NULL-safe
+    # the reduced-precision Gram diagnostic checks its arguments before any
+    # device work
+    x = np.ones((4, 8))
+    g = np.zeros((4, 4), dtype=np.float32)
+    for args in ((None, 4, 8, 1, g.ctypes.data), (x.ctypes.data, 4, 8, 0, g.ctypes.data),
+                 (x.ctypes.data, 0, 8, 1, g.ctypes.data), (x.ctypes.data, 4097, 8, 1, g.ctypes.data),
+                 (x.ctypes.data, 4, 0, 2, g.ctypes.data), (x.ctypes.data, 4, 8, 2, None)):
+        assert lib.pmmf_gram_reduced(*args, None) == pmmf.ERR_INVALID_ARG
+        assert lib.pmmf_last_error()
 
 
 def test_tuning_table_validation_and_json(tmp_path):
@@ -70,7 +80,10 @@ def test_tuning_table_validation_and_json(tmp_path):
     from paper_1507_04396_gb300 import pmmf
     lib = pmmf.load()
     assert lib.pmmf_set_tuning(0, 256, 4) == pmmf.OK
-    assert lib.pmmf_set_tuning(11, 256, 4) == pmmf.ERR_INVALID_ARG    # unknown parameter
+    assert lib.pmmf_set_tuning(12, 256, 4) == pmmf.ERR_INVALID_ARG    # unknown parameter
+    assert lib.pmmf_set_tuning(11, 256, 1) == pmmf.OK                 # warp-level mma.sync Gram
+    assert lib.pmmf_set_tuning(11, 256, 2) == pmmf.OK                 # tcgen05 Gram
+    assert lib.pmmf_set_tuning(11, 256, 3) == pmmf.ERR_INVALID_ARG    # only 1 or 2
     assert lib.pmmf_set_tuning(10, 256, 0) == pmmf.OK                 # reduced precision on every stage
     assert lib.pmmf_set_tuning(9, 256, 5) == pmmf.ERR_INVALID_ARG     # 2..4 search CTAs per SM
     assert lib.pmmf_set_tuning(0, 0, 4) == pmmf.ERR_INVALID_ARG       # empty bucket
